@@ -1,0 +1,187 @@
+"""Pins of the oracle's discretization (Sec. 3.2 - 3.4) against closed forms, exact
+polynomial reproduction, dense brute force and the paper's printed errors."""
+import math
+import os
+
+import numpy as np
+import pytest
+
+import workloads as W
+from oracle import cubature as Q
+from oracle import discretization as D
+from oracle import geometry as G
+from oracle import multigrid as MG
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def _sq_avg(a, h, p):
+    """Average of x^p over [a, a + h] (closed form)."""
+    return ((a + h) ** (p + 1) - a ** (p + 1)) / ((p + 1) * h)
+
+
+@pytest.mark.parametrize("abc", [(1.0, 0.0, 1.0), (1.0, 0.5, 2.0), (1.25, -math.sqrt(3) / 2, 1.75)])
+def test_regular_stencil_exact_on_cell_averages(abc):
+    """eq. stdLap and the iterated eq. stdGrad reproduce <L x^p y^q> exactly for p, q <= 4."""
+    a, b, c = abc
+    h = 0.05
+    st = D.regular_stencil(a, b, c)
+    x0, y0 = 0.3, -0.2
+    for p in range(5):
+        for q in range(5):
+            got = sum(w * _sq_avg(x0 + di * h, h, p) * _sq_avg(y0 + dj * h, h, q)
+                      for (di, dj), w in st.items()) / h ** 2
+            want = 0.0
+            if p >= 2:
+                want += a * p * (p - 1) * _sq_avg(x0, h, p - 2) * _sq_avg(y0, h, q)
+            if p >= 1 and q >= 1:
+                want += b * p * q * _sq_avg(x0, h, p - 1) * _sq_avg(y0, h, q - 1)
+            if q >= 2:
+                want += c * q * (q - 1) * _sq_avg(x0, h, p) * _sq_avg(y0, h, q - 2)
+            assert abs(got - want) <= 1e-9 * (1 + abs(want)), (p, q, got, want)
+
+
+def test_stencil_sign_reading():
+    """The printed last sign of eq. stdLap ('+') would break exactness on constants."""
+    st = D.regular_stencil(1.0, 0.0, 0.0)
+    assert abs(sum(st.values())) < 1e-15
+    assert st[(-2, 0)] == st[(2, 0)] == -1.0 / 12
+
+
+CASES = [("disk", lambda: W.disk_minus(32)), ("star", lambda: W.star(64)),
+         ("ellipses", lambda: W.three_ellipses(64)), ("problem2N", lambda: W.paper_problem2(32, W.NEUMANN))]
+
+
+@pytest.mark.parametrize("name,mk", CASES)
+def test_rows_exact_on_pi4(name, mk):
+    """Every row reproduces <L u> for u in Pi_4 (eq. goalOfApproximation holds exactly):
+    L <u> + N <<N u>> = <L u>, all averages by the independent function cubature."""
+    prob = mk()
+    cg = G.cut_cells(prob)
+    dz = D.discretize(cg, prob.a, prob.b, prob.c)
+    rng = np.random.default_rng(7)
+    poly = W.mms_polynomial(rng.standard_normal(15))
+    ua = Q.cell_averages(cg, poly.u).ravel()
+    fa = Q.cell_averages(cg, poly.f(prob.a, prob.b, prob.c)).ravel()
+    ga = Q.boundary_averages(cg, dz.segs, poly.u, poly.ux, poly.uy)
+    res = dz.L @ ua + dz.N @ ga - fa
+    scale = abs(dz.L) @ np.abs(ua) + abs(dz.N) @ np.abs(ga) + np.abs(fa)
+    ne = (cg.status != G.EMPTY).ravel()
+    assert np.all(np.abs(res[ne]) <= 1e-10 * scale[ne] + 1e-12)
+    # and constants: rows of L sum to -N (Dirichlet) since L 1 + N 1 = <L 1> = 0
+    if all(c.bc == W.DIRICHLET for c in prob.curves) and prob.box_bc != W.NEUMANN:
+        one = np.where(ne, 1.0, 0.0)
+        r1 = dz.L @ one + dz.N @ np.ones(len(dz.segs))
+        assert np.all(np.abs(r1[ne]) <= 1e-10 * (abs(dz.L) @ one)[ne])
+
+
+def test_stencils_poised_and_well_conditioned():
+    """Every PLG stencil has 15 distinct non-empty cells and a moderate condition number
+    (Sec. 2.2 prints 'generally do not exceed 1e4'; the bound here allows one decade)."""
+    for prob in (W.star(64), W.disk_minus(64)):
+        cg = G.cut_cells(prob)
+        dz = D.discretize(cg, prob.a, prob.b, prob.c)
+        conds = np.array([r.cond for r in dz.rows.values()])
+        for lin, r in dz.rows.items():
+            assert len(set(r.cells)) == 15
+            assert all(cg.status[j, i] != G.EMPTY for (i, j) in r.cells)
+            j, i = divmod(lin, cg.nx)
+            assert r.cells[0] == (i, j)
+        assert np.median(conds) < 1e4
+        assert conds.max() < 1e6
+
+
+def test_staircase_lattice_is_poised_in_fd():
+    """Exact rational rank of the FD sample matrix at the cell centres is 15 for every stencil."""
+    from fractions import Fraction
+    cg = G.cut_cells(W.star(32))
+    dz = D.discretize(cg, 1.0, 0.5, 2.0)
+    for lin, r in list(dz.rows.items())[:40]:
+        M = [[Fraction(ci) ** p * Fraction(cj) ** q for (ci, cj) in r.cells] for (p, q) in G.EXPS]
+        n = 15
+        rank = 0
+        for col in range(n):
+            piv = next((k for k in range(rank, n) if M[k][col] != 0), None)
+            if piv is None:
+                continue
+            M[rank], M[piv] = M[piv], M[rank]
+            for k in range(n):
+                if k != rank and M[k][col] != 0:
+                    f = M[k][col] / M[rank][col]
+                    M[k] = [x - f * y for x, y in zip(M[k], M[rank])]
+            rank += 1
+        assert rank == 15
+
+
+def test_dense_brute_force_equals_sparse_direct():
+    prob = W.disk_minus(16)
+    cg = G.cut_cells(prob)
+    dz = D.discretize(cg, prob.a, prob.b, prob.c)
+    ne = np.nonzero((cg.status != G.EMPTY).ravel())[0]
+    rng = np.random.default_rng(3)
+    r = np.zeros(prob.nx * prob.ny)
+    r[ne] = rng.standard_normal(len(ne))
+    u = MG.direct_solve(dz, r)
+    A = dz.L.toarray()[np.ix_(ne, ne)]
+    ud = np.linalg.solve(A, r[ne])
+    assert np.abs(u[ne] - ud).max() <= 1e-12 * np.abs(ud).max()
+
+
+@pytest.mark.parametrize("name,mk", CASES[:3])
+def test_polynomial_solution_reproduced(name, mk):
+    prob = mk()
+    cg = G.cut_cells(prob)
+    dz = D.discretize(cg, prob.a, prob.b, prob.c)
+    poly = W.mms_polynomial([0.3, -1.0, 0.5, 2.0, -0.7, 1.1, 0.2, -0.4, 0.9, 0.1, 0.6, -0.3, 0.25, 0.8, -0.5])
+    ua = Q.cell_averages(cg, poly.u).ravel()
+    fa = Q.cell_averages(cg, poly.f(prob.a, prob.b, prob.c)).ravel()
+    ga = Q.boundary_averages(cg, dz.segs, poly.u, poly.ux, poly.uy)
+    u = MG.direct_solve(dz, fa - dz.N @ ga)
+    ne = (cg.status != G.EMPTY).ravel()
+    assert np.abs(u - ua)[ne].max() <= 1e-9 * np.abs(ua[ne]).max()
+
+
+def _solution_error(prob, mms):
+    cg = G.cut_cells(prob)
+    dz = D.discretize(cg, prob.a, prob.b, prob.c)
+    fa = Q.cell_averages(cg, mms.f(prob.a, prob.b, prob.c)).ravel()
+    ga = Q.boundary_averages(cg, dz.segs, mms.u, mms.ux, mms.uy)
+    u = MG.direct_solve(dz, fa - dz.N @ ga)
+    ua = Q.cell_averages(cg, mms.u).ravel()
+    ne = (cg.status != G.EMPTY).ravel()
+    e = np.abs(u - ua)[ne]
+    v = cg.vol.ravel()[ne]
+    return e.max(), (v * e).sum() / v.sum(), math.sqrt((v * e * e).sum() / v.sum())
+
+
+@pytest.mark.slow
+@pytest.mark.parametrize("mk,mms", [(lambda n: W.star(n), W.mms_star), (lambda n: W.disk_minus(n), W.mms_disk)])
+def test_fourth_order_convergence(mk, mms):
+    """Solution errors converge at fourth order in the max norm (Sec. 5.1)."""
+    e64 = _solution_error(mk(64), mms())[0]
+    e128 = _solution_error(mk(128), mms())[0]
+    assert math.log2(e64 / e128) >= 3.5
+
+
+def _golden_problem2():
+    rows = []
+    with open(os.path.join(GOLDEN, "paper_problem2.txt")) as f:
+        for line in f:
+            if line.startswith("#") or not line.strip():
+                continue
+            case, h, norm, val = line.split()
+            rows.append((case, int(h.split("/")[1]), norm, float(val)))
+    return rows
+
+
+@pytest.mark.slow
+@pytest.mark.parametrize("case", ["DD", "DN"])
+def test_paper_problem2_error_magnitudes(case):
+    """Errors within a factor 5 of the paper's printed Problem 2 errors at h = 1/64 (the
+    PLG stencils differ from the paper's, so only the magnitude is pinned)."""
+    bc = W.DIRICHLET if case == "DD" else W.NEUMANN
+    einf, e1, e2 = _solution_error(W.paper_problem2(64, bc), W.mms_sinsin())
+    got = {"Linf": einf, "L1": e1, "L2": e2}
+    for (c, n, norm, val) in _golden_problem2():
+        if c == case and n == 64:
+            assert val / 5 <= got[norm] <= val * 5, (norm, got[norm], val)

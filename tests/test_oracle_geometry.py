@@ -1,0 +1,133 @@
+"""Pins of the oracle's geometry (cut cells, Green-formula moments, Alg. 1 merging)
+against closed forms and library quadrature (Sec. 2.4, Sec. 3.1)."""
+import math
+
+import numpy as np
+import pytest
+from scipy.integrate import quad
+
+import workloads as W
+from oracle import geometry as G
+
+
+def global_moment(cg, p, q, xg=0.0, yg=0.0):
+    """int_Omega (x - xg)^p (y - yg)^q dA assembled from the per-cell moments."""
+    h = cg.h
+    tot = 0.0
+    pure = np.argwhere(cg.status == G.PURE)
+    k = G.EIDX[(p, q)]
+    for (j, i) in pure:
+        if j * cg.nx + i in cg.mom:
+            continue
+        xc, yc = cg.centre(i, j)
+        m = G.shift_moments(G.PURE_MOM, (xc - xg) / h, (yc - yg) / h)
+        tot += m[k]
+    for lin, m0 in cg.mom.items():
+        j, i = divmod(lin, cg.nx)
+        xc, yc = cg.centre(i, j)
+        tot += G.shift_moments(m0, (xc - xg) / h, (yc - yg) / h)[k]
+    return tot * h ** (2 + p + q)
+
+
+@pytest.mark.parametrize("n", [16, 64])
+def test_disk_hole_area_and_second_moment(n):
+    r = 0.2
+    cg = G.cut_cells(W.disk_minus(n, r))
+    assert abs(cg.vol.sum() * cg.h ** 2 - (1 - math.pi * r * r)) < 1e-13
+    # int (x - 1/2)^2 over box minus disk = 1/12 - pi r^4 / 4
+    assert abs(global_moment(cg, 2, 0, 0.5, 0.5) - (1 / 12 - math.pi * r ** 4 / 4)) < 1e-13
+    assert abs(global_moment(cg, 1, 1, 0.5, 0.5)) < 1e-14
+    assert abs(global_moment(cg, 1, 0, 0.0, 0.0) - 0.5 * (1 - math.pi * r * r)) < 1e-13
+
+
+def test_star_area_and_polar_moment():
+    r0, amp, k = 0.3, 0.08, 5
+    cg = G.cut_cells(W.star(64, r0=r0, amp=amp, k=k))
+    area = math.pi * (r0 ** 2 + amp ** 2 / 2)
+    assert abs(cg.vol.sum() * cg.h ** 2 - area) < 1e-13
+    # int r^2 dA = (1/4) int r(t)^4 dt = (pi/2)(r0^4 + 3 r0^2 amp^2 + 3 amp^4 / 8)
+    J = global_moment(cg, 2, 0, 0.5, 0.5) + global_moment(cg, 0, 2, 0.5, 0.5)
+    assert abs(J - 0.5 * math.pi * (r0 ** 4 + 3 * r0 ** 2 * amp ** 2 + 3 * amp ** 4 / 8)) < 1e-13
+
+
+def test_rotated_ellipse_moments():
+    prob = W.three_ellipses(64)
+    cg = G.cut_cells(prob)
+    area = 1 - sum(math.pi * c.params[2] * c.params[3] for c in prob.curves)
+    assert abs(cg.vol.sum() * cg.h ** 2 - area) < 1e-13
+    # second moment about the box centre: box part minus each ellipse's (parallel axes)
+    want = 1 / 12
+    for c in prob.curves:
+        cx, cy, a, b, phi = c.params
+        A = math.pi * a * b
+        Ixx = A * (a * a * math.cos(phi) ** 2 + b * b * math.sin(phi) ** 2) / 4
+        want -= Ixx + A * (cx - 0.5) ** 2
+    assert abs(global_moment(cg, 2, 0, 0.5, 0.5) - want) < 1e-13
+
+
+def test_boundary_length_and_divergence_identities():
+    """Sum of boundary-piece lengths = perimeter (scipy quad of |gamma'|); the outward
+    normals satisfy int n ds = 0 and int x n_x ds = |Omega| (divergence theorem)."""
+    r0, amp, k = 0.3, 0.08, 5
+    cg = G.cut_cells(W.star(128, r0=r0, amp=amp, k=k))
+    h = cg.h
+    per = quad(lambda t: math.hypot(-amp * k * math.sin(k * t), r0 + amp * math.cos(k * t)),
+               0, 2 * math.pi, limit=200, epsabs=1e-14)[0]
+    L = sum(b[0] for b in cg.bm0.values()) * h
+    assert abs(L - per) < 1e-12
+    nx_ = sum(b[0] for b in cg.bmx.values()) * h
+    ny_ = sum(b[0] for b in cg.bmy.values()) * h
+    assert abs(nx_) < 1e-13 and abs(ny_) < 1e-13
+    # int x n_x ds over the star boundary = area (x about any origin)
+    xn = 0.0
+    for lin, bx in cg.bmx.items():
+        j, i = divmod(lin, cg.nx)
+        xc, _ = cg.centre(i, j)
+        xn += (bx[G.EIDX[(1, 0)]] * h + (xc - 0.5) * bx[0]) * h
+    assert abs(xn - math.pi * (r0 ** 2 + amp ** 2 / 2)) < 1e-13
+
+
+def test_box_walls_are_boundary_pieces():
+    cg = G.cut_cells(W.disk_minus(32))
+    h = cg.h
+    walls = [lin for lin in cg.bpieces if cg.status.ravel()[lin] == G.PURE]
+    assert len(walls) == 4 * 32 - 4
+    L = sum(cg.bm0[lin][0] for lin in walls) * h
+    assert abs(L - 4.0) < 1e-14
+    # left wall cell: outward normal (-1, 0)
+    lin = 10 * 32 + 0
+    assert abs(cg.bmx[lin][0] + 1.0) < 1e-14 and abs(cg.bmy[lin][0]) < 1e-14
+
+
+def test_shift_matches_direct_integration():
+    """Binomial shift of square moments equals the closed-form moments of a shifted square."""
+    dx, dy = 1.5, -2.0
+    got = G.shift_moments(G.PURE_MOM, dx, dy)
+    for k, (p, q) in enumerate(G.EXPS):
+        ix = ((dx + 0.5) ** (p + 1) - (dx - 0.5) ** (p + 1)) / (p + 1)
+        iy = ((dy + 0.5) ** (q + 1) - (dy - 0.5) ** (q + 1)) / (q + 1)
+        assert abs(got[k] - ix * iy) < 1e-12 * max(1.0, abs(ix * iy))
+
+
+@pytest.mark.parametrize("theta", [0.3, 0.5])
+def test_merging_postcondition(theta):
+    """Alg. 1 postcondition: volumes add up and every surviving interface cell exceeds theta h^2."""
+    prob = W.star(64)
+    cg0 = G.cut_cells(prob, theta=0.0)
+    cg = G.cut_cells(prob, theta=theta)
+    assert abs(cg.vol.sum() - cg0.vol.sum()) < 1e-11
+    surv = cg.interface & (cg.status != G.EMPTY)
+    assert np.all(cg.vol[surv] > theta)
+    absorbed = cg.interface & (cg.status == G.EMPTY) & (cg0.vol > 0)
+    assert absorbed.sum() > 0
+    for (j, i) in np.argwhere(absorbed):
+        o = cg.owner[j, i]
+        oj, oi = divmod(int(o), cg.nx)
+        assert cg.status[oj, oi] != G.EMPTY
+
+
+def test_vertex_and_tangent_degeneracies():
+    """The paper's Problem 2 ellipse passes through grid vertices and touches grid lines."""
+    for n in (32, 64):
+        cg = G.cut_cells(W.paper_problem2(n))
+        assert abs(cg.vol.sum() * cg.h ** 2 - (1 - math.pi / 32)) < 1e-13

@@ -1,0 +1,272 @@
+"""Seeded synthetic workloads for the cut-cell elliptic solver.
+
+This module holds problem *data* only: domain descriptions (curve kinds and
+parameters), grid sizes, PDE coefficients, manufactured solutions given in
+closed form, and seeded random draws.  It contains none of the method's
+arithmetic (no cut cells, cubature, stencils, fits or solvers), so both the
+CUDA path and the CPU oracle may import it without sharing any of the method.
+
+Problem statement (Sec. 1, eq. ccEllipticEq): a u_xx + b u_xy + c u_yy = f in
+Omega with b^2 - 4ac < 0; boundary operators (Sec. 3.3): Dirichlet (N = I) and
+Neumann (N = d/dn, n the outward unit normal of Omega).
+
+Curve conventions (shared by every consumer):
+  CIRCLE  p = (cx, cy, r)                 gamma(t) = c + r (cos t, sin t)
+  ELLIPSE p = (cx, cy, a, b, phi)         gamma(t) = c + Rot(phi) (a cos t, b sin t)
+  STAR    p = (cx, cy, r0, amp, k)        gamma(t) = c + (r0 + amp cos(k t)) (cos t, sin t)
+with t in [0, 2 pi), counter-clockwise.  orient = +1 means Omega lies inside the
+curve, -1 means the curve bounds a hole.
+"""
+from __future__ import annotations
+
+import math
+from dataclasses import dataclass, field
+from typing import Callable, List, Optional, Sequence
+
+import numpy as np
+
+CIRCLE, ELLIPSE, STAR = 1, 2, 3
+NONE, DIRICHLET, NEUMANN = 0, 1, 2
+
+
+@dataclass
+class Curve:
+    kind: int
+    params: Sequence[float]
+    orient: int = -1
+    bc: int = DIRICHLET
+
+
+@dataclass
+class Problem:
+    """Box R = [x0, x0 + nx h] x [y0, y0 + ny h] and the curves cut out of it."""
+    a: float
+    b: float
+    c: float
+    x0: float
+    y0: float
+    h: float
+    nx: int
+    ny: int
+    box_bc: int
+    curves: List[Curve] = field(default_factory=list)
+    name: str = ""
+
+
+@dataclass
+class Manufactured:
+    """Closed-form u and its derivatives (vectorised over numpy arrays)."""
+    u: Callable
+    ux: Callable
+    uy: Callable
+    uxx: Callable
+    uxy: Callable
+    uyy: Callable
+    name: str = ""
+
+    def f(self, a: float, b: float, c: float) -> Callable:
+        return lambda x, y: a * self.uxx(x, y) + b * self.uxy(x, y) + c * self.uyy(x, y)
+
+
+# ---------------------------------------------------------------- manufactured solutions
+
+def mms_disk() -> Manufactured:
+    """u = sin(2 pi x) cos(3 pi y) exp(x y)."""
+    P2, P3 = 2 * math.pi, 3 * math.pi
+
+    def u(x, y):
+        return np.sin(P2 * x) * np.cos(P3 * y) * np.exp(x * y)
+
+    def ux(x, y):
+        e = np.exp(x * y)
+        return (P2 * np.cos(P2 * x) + y * np.sin(P2 * x)) * np.cos(P3 * y) * e
+
+    def uy(x, y):
+        e = np.exp(x * y)
+        return np.sin(P2 * x) * (-P3 * np.sin(P3 * y) + x * np.cos(P3 * y)) * e
+
+    def uxx(x, y):
+        e = np.exp(x * y)
+        s, co = np.sin(P2 * x), np.cos(P2 * x)
+        return (-P2 * P2 * s + 2 * y * P2 * co + y * y * s) * np.cos(P3 * y) * e
+
+    def uyy(x, y):
+        e = np.exp(x * y)
+        s, co = np.sin(P3 * y), np.cos(P3 * y)
+        return np.sin(P2 * x) * (-P3 * P3 * co - 2 * x * P3 * s + x * x * co) * e
+
+    def uxy(x, y):
+        e = np.exp(x * y)
+        sx, cx = np.sin(P2 * x), np.cos(P2 * x)
+        sy, cy = np.sin(P3 * y), np.cos(P3 * y)
+        A = P2 * cx + y * sx          # d/dx of (sin(2pi x) e^{xy}) / e^{xy}
+        B = -P3 * sy + x * cy         # d/dy of (cos(3pi y) e^{xy}) / e^{xy}
+        # u = sx*cy*e ; u_x = A cy e ; u_xy = d/dy[A cy e] = sx cy e + A (-P3 sy) e + A cy x e
+        return (sx * cy + A * B) * e
+
+    return Manufactured(u, ux, uy, uxx, uxy, uyy, "sin(2pi x)cos(3pi y)exp(xy)")
+
+
+def mms_star() -> Manufactured:
+    """u = exp(x) sin(pi y) + x^4."""
+    P = math.pi
+    return Manufactured(
+        u=lambda x, y: np.exp(x) * np.sin(P * y) + x ** 4,
+        ux=lambda x, y: np.exp(x) * np.sin(P * y) + 4 * x ** 3,
+        uy=lambda x, y: P * np.exp(x) * np.cos(P * y),
+        uxx=lambda x, y: np.exp(x) * np.sin(P * y) + 12 * x ** 2,
+        uxy=lambda x, y: P * np.exp(x) * np.cos(P * y),
+        uyy=lambda x, y: -P * P * np.exp(x) * np.sin(P * y),
+        name="exp(x)sin(pi y)+x^4")
+
+
+def mms_ellipses() -> Manufactured:
+    """u = cos(pi x) cos(pi y) + x y^3."""
+    P = math.pi
+    return Manufactured(
+        u=lambda x, y: np.cos(P * x) * np.cos(P * y) + x * y ** 3,
+        ux=lambda x, y: -P * np.sin(P * x) * np.cos(P * y) + y ** 3,
+        uy=lambda x, y: -P * np.cos(P * x) * np.sin(P * y) + 3 * x * y ** 2,
+        uxx=lambda x, y: -P * P * np.cos(P * x) * np.cos(P * y),
+        uxy=lambda x, y: P * P * np.sin(P * x) * np.sin(P * y) + 3 * y ** 2,
+        uyy=lambda x, y: -P * P * np.cos(P * x) * np.cos(P * y) + 6 * x * y,
+        name="cos(pi x)cos(pi y)+x y^3")
+
+
+def mms_polynomial(coef: Sequence[float]) -> Manufactured:
+    """u = sum_{p+q<=4} coef[k] x^p y^q (graded order (0,0),(1,0),(0,1),(2,0),...)."""
+    exps = [(d - q, q) for d in range(5) for q in range(d + 1)]
+    coef = list(coef) + [0.0] * (15 - len(coef))
+
+    def mk(dx, dy):
+        def g(x, y):
+            out = np.zeros(np.broadcast(x, y).shape)
+            for cf, (p, q) in zip(coef, exps):
+                if cf == 0.0 or p < dx or q < dy:
+                    continue
+                fp = math.perm(p, dx)
+                fq = math.perm(q, dy)
+                out = out + cf * fp * fq * np.power(x, p - dx) * np.power(y, q - dy)
+            return out
+        return g
+
+    return Manufactured(mk(0, 0), mk(1, 0), mk(0, 1), mk(2, 0), mk(1, 1), mk(0, 2), "poly4")
+
+
+# ---------------------------------------------------------------- domains
+
+def disk_minus(n: int, r: float = 0.2) -> Problem:
+    """Unit square minus a disk of radius r centred at (0.5, 0.5); Dirichlet everywhere."""
+    return Problem(1.0, 0.0, 1.0, 0.0, 0.0, 1.0 / n, n, n, DIRICHLET,
+                   [Curve(CIRCLE, (0.5, 0.5, r), -1, DIRICHLET)], name=f"disk_minus_{n}")
+
+
+def star(n: int, abc=(1.0, 0.5, 2.0), r0=0.3, amp=0.08, k=5, centre=(0.5, 0.5)) -> Problem:
+    """Interior of the star r(t) = r0 + amp cos(k t) inside [0,1]^2; Dirichlet on the curve."""
+    a, b, c = abc
+    return Problem(a, b, c, 0.0, 0.0, 1.0 / n, n, n, NONE,
+                   [Curve(STAR, (centre[0], centre[1], r0, amp, float(k)), +1, DIRICHLET)],
+                   name=f"star_{n}")
+
+
+def three_ellipses(n: int, seed: int = 0, abc=(1.0, 0.0, 1.0), curve_bc: int = NEUMANN,
+                   gap_cells: float = 4.0) -> Problem:
+    """Unit square minus three disjoint ellipses (semi-axes 0.10x0.06, 0.08x0.08, 0.12x0.05).
+
+    Centres (uniform in the unit square) and rotations (uniform in [0, pi)) are drawn with
+    numpy's PCG64(seed) by rejection, so that every pair of ellipses and every ellipse and
+    the box keep a gap of at least max(gap_cells*h, 1/16), checked on 720 samples per
+    curve.  The 1/16 floor keeps the geometry the same for every n >= 64 and leaves the
+    curves separated on the coarse multigrid levels too."""
+    h = 1.0 / n
+    rng = np.random.Generator(np.random.PCG64(seed))
+    axes = [(0.10, 0.06), (0.08, 0.08), (0.12, 0.05)]
+    gap = max(gap_cells * h, 1.0 / 16)
+    ts = np.linspace(0.0, 2 * math.pi, 721)
+    placed, params = [], []
+    for (ea, eb) in axes:
+        for _ in range(100000):
+            cx, cy = rng.uniform(0.0, 1.0, size=2)
+            phi = rng.uniform(0.0, math.pi)
+            px = cx + ea * np.cos(ts) * math.cos(phi) - eb * np.sin(ts) * math.sin(phi)
+            py = cy + ea * np.cos(ts) * math.sin(phi) + eb * np.sin(ts) * math.cos(phi)
+            if px.min() < gap or py.min() < gap or px.max() > 1 - gap or py.max() > 1 - gap:
+                continue
+            ok = True
+            for (qx, qy, qc) in placed:
+                d = np.sqrt((px[:, None] - qx[None, :]) ** 2 + (py[:, None] - qy[None, :]) ** 2)
+                if d.min() < gap:
+                    ok = False
+                    break
+            if ok:
+                placed.append((px, py, (cx, cy)))
+                params.append((float(cx), float(cy), ea, eb, float(phi)))
+                break
+        else:  # pragma: no cover
+            raise RuntimeError("could not place ellipses")
+    a, b, c = abc
+    curves = [Curve(ELLIPSE, p, -1, curve_bc) for p in params]
+    return Problem(a, b, c, 0.0, 0.0, h, n, n, DIRICHLET, curves, name=f"three_ellipses_{n}")
+
+
+def random_geometry(seed: int) -> tuple:
+    """One geometry of the many-geometry batch: a star or a three-ellipse domain.
+
+    Returns (problem, manufactured).  Grids are drawn from {128, 256, 512, 1024}."""
+    rng = np.random.Generator(np.random.PCG64(1000 + seed))
+    n = int(rng.choice([128, 256, 512, 1024]))
+    if seed % 2 == 0:
+        k = int(rng.integers(3, 8))
+        r0 = float(rng.uniform(0.25, 0.32))
+        amp = float(rng.uniform(0.05, 0.1))
+        return star(n, (1.0, 0.5, 2.0), r0, amp, k), mms_star()
+    return three_ellipses(n, seed=seed, abc=(1.0, 0.0, 1.0)), mms_ellipses()
+
+
+def smoothed_normal_rhs(n: int, nrhs: int, mask: np.ndarray, seed: int = 0) -> np.ndarray:
+    """nrhs fields of i.i.d. N(0,1) cell values smoothed by three sweeps of
+    v <- v/2 + (sum of the 4 neighbours)/8 restricted to the cells where mask is true.
+    Returns an array [nrhs, n, n] (zero outside mask)."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    v = rng.standard_normal((nrhs, n, n)) * mask[None]
+    m = mask.astype(np.float64)[None]
+    for _ in range(3):
+        s = np.zeros_like(v)
+        s[:, 1:, :] += v[:, :-1, :]
+        s[:, :-1, :] += v[:, 1:, :]
+        s[:, :, 1:] += v[:, :, :-1]
+        s[:, :, :-1] += v[:, :, 1:]
+        v = (0.5 * v + 0.125 * s) * m
+    return v
+
+
+CONFIGS = {
+    "disk64": lambda: (disk_minus(64), mms_disk()),
+    "star256": lambda: (star(256), mms_star()),
+    "star1024": lambda: (star(1024), mms_star()),
+    "star4096": lambda: (star(4096), mms_star()),
+    "ellipses2048": lambda: (three_ellipses(2048), mms_ellipses()),
+    "disk512": lambda: (disk_minus(512), mms_disk()),
+    "star2048_adj": lambda: (star(2048, (1.0, 0.3, 1.0)), mms_star()),
+}
+
+
+def mms_sinsin() -> Manufactured:
+    """u = sin(pi x) sin(pi y) (the exact solution of the paper's Problem 2)."""
+    P = math.pi
+    return Manufactured(
+        u=lambda x, y: np.sin(P * x) * np.sin(P * y),
+        ux=lambda x, y: P * np.cos(P * x) * np.sin(P * y),
+        uy=lambda x, y: P * np.sin(P * x) * np.cos(P * y),
+        uxx=lambda x, y: -P * P * np.sin(P * x) * np.sin(P * y),
+        uxy=lambda x, y: P * P * np.cos(P * x) * np.cos(P * y),
+        uyy=lambda x, y: -P * P * np.sin(P * x) * np.sin(P * y),
+        name="sin(pi x)sin(pi y)")
+
+
+def paper_problem2(n: int, curve_bc: int = DIRICHLET) -> Problem:
+    """The paper's Problem 2 (Sec. 5.1): Poisson on [0,1]^2 minus the ellipse with centre
+    (1/2, 1/2) and semi-axes (1/8, 1/4); Dirichlet on the box."""
+    return Problem(1.0, 0.0, 1.0, 0.0, 0.0, 1.0 / n, n, n, DIRICHLET,
+                   [Curve(ELLIPSE, (0.5, 0.5, 0.125, 0.25, 0.0), -1, curve_bc)],
+                   name=f"paper_problem2_{n}")
