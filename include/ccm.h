@@ -1,0 +1,219 @@
+/*
+ * ccm.h -- C ABI of the GB300 fourth-order cut-cell elliptic solver.
+ *
+ * Problem (Sec. 1, eq. ccEllipticEq; Sec. 3.3 boundary operators):
+ *     a u_x1x1 + b u_x1x2 + c u_x2x2 = f   in Omega,   b^2 - 4ac < 0,
+ *     u = g (Dirichlet)  or  n . grad u = g (Neumann, n the outward unit normal)  on dOmega,
+ * discretised on the Cartesian cells of the box R = [x0, x0 + nx h] x [y0, y0 + ny h] by the
+ * paper's fourth-order finite-volume cut-cell method (Sec. 3): cell averages of u and f,
+ * boundary-piece averages of g, L u + N g = f (eq. PoissonLinearDiscretization), solved by a
+ * geometric multigrid on the level hierarchy of Sec. 4.
+ *
+ * Conventions shared by every entry point:
+ *   - Cell (i, j) is (x0 + i h, x0 + (i+1) h) x (y0 + j h, y0 + (j+1) h); cell arrays are
+ *     row-major [ny][nx] (i fastest), one FP64 value per Cartesian cell.  Empty cells and cells
+ *     merged into a neighbour by Alg. 1 are ignored on input and written as 0 on output; a
+ *     merged cell's value lives at its survivor (see ccm_cell_map).
+ *   - Boundary data: one FP64 value per boundary segment, in the order of
+ *     ccm_boundary_segments.  A segment is the whole boundary piece S_i of one (survivor)
+ *     cell, box-wall edges included when the box is part of dOmega.
+ *   - Array arguments of ccm_apply / ccm_apply_T / ccm_solve / ccm_solve_T and the level
+ *     entry points are DEVICE pointers on the current device unless a parameter says
+ *     "host".  The caller owns every buffer it passes; the handle owns its level arrays and
+ *     work space.  A handle is used from one stream at a time.
+ *   - stream is a cudaStream_t (0 = legacy default stream); calls are asynchronous on it
+ *     unless documented otherwise.
+ *   - Return value: 0 on success, a negative CCM_E* code otherwise (ccm_strerror names it).
+ *     Invalid arguments are rejected before any work is queued.
+ */
+#ifndef CCM_H
+#define CCM_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* curve kinds: parameters p[] (t in [0, 2 pi), counter-clockwise)
+ *   CCM_CIRCLE  p = (cx, cy, r)              gamma = c + r (cos t, sin t)
+ *   CCM_ELLIPSE p = (cx, cy, a, b, phi)      gamma = c + Rot(phi) (a cos t, b sin t)
+ *   CCM_STAR    p = (cx, cy, r0, amp, k)     gamma = c + (r0 + amp cos k t)(cos t, sin t) */
+enum { CCM_CIRCLE = 1, CCM_ELLIPSE = 2, CCM_STAR = 3 };
+/* boundary conditions (Sec. 3.3): NONE only for box_bc (the box is not part of dOmega) */
+enum { CCM_NONE = 0, CCM_DIRICHLET = 1, CCM_NEUMANN = 2 };
+/* arithmetic of the multigrid cycle */
+enum { CCM_FP64 = 0, CCM_MIXED = 1 };
+
+enum {
+  CCM_OK = 0,
+  CCM_EINVAL = -1,     /* null pointer, b^2-4ac >= 0, h <= 0, bad sizes, nx/ny not divisible */
+  CCM_EGEOM = -2,      /* curve leaves the box, mixed BC types in one cell, isolated pieces */
+  CCM_EPLG = -3,       /* no poised stencil within the search radius */
+  CCM_ESINGULAR = -4,  /* zero pivot in a block or bottom factorisation */
+  CCM_ENOCONV = -5,    /* max_iter reached; u holds the last iterate */
+  CCM_ETIMEOUT = -6,   /* a bounded device wait ran out */
+  CCM_ECUDA = -7,      /* a CUDA runtime call failed */
+  CCM_ENOMEM = -8,     /* device or host allocation failed */
+  CCM_ENOTFINITE = -9  /* a residual norm became NaN or Inf */
+};
+
+typedef struct {
+  int kind;        /* CCM_CIRCLE | CCM_ELLIPSE | CCM_STAR */
+  double p[8];     /* parameters, see above */
+  int orient;      /* +1: Omega lies inside the curve; -1: the curve bounds a hole */
+  int bc;          /* CCM_DIRICHLET | CCM_NEUMANN */
+} ccm_curve;
+
+typedef struct {
+  double a, b, c;          /* constant coefficients, b^2 - 4ac < 0 */
+  double x0, y0, h;        /* box origin and cell size */
+  int nx, ny;              /* cells per side */
+  int box_bc;              /* CCM_DIRICHLET | CCM_NEUMANN | CCM_NONE */
+  int ncurves;
+  const ccm_curve* curves; /* host array of ncurves curves (copied by ccm_setup) */
+} ccm_problem;
+
+typedef struct {
+  double omega;      /* weight of the Jacobi smoother SMO-1 (Sec. 4.1) */
+  int nu1, nu2;      /* pre- and post-smoothing sweeps (Alg. 2) */
+  double theta;      /* merging threshold of Alg. 1 */
+  int coarsest;      /* the hierarchy stops at the first level with <= coarsest cells per side */
+  int precision;     /* CCM_FP64 | CCM_MIXED (FP32 cycles inside FP64 refinement) */
+  double rtol;       /* stop when ||r - L u||_inf <= rtol ||r||_inf, r = f - N g */
+  int max_iter;      /* outer iterations (V-cycles) */
+  int ras_passes;    /* passes of the overlapping block solve used for SMO-2 */
+  int ras_block;     /* core size of an SMO-2 block (unknowns) */
+  int ras_overlap;   /* overlap of an SMO-2 block on each side (unknowns) */
+  int nthreads;      /* host threads for ccm_setup (0 = all cores) */
+} ccm_params;
+
+typedef struct {
+  int nx, ny, levels;
+  int64_t n_cells;      /* non-empty (survivor) cells on the finest level */
+  int64_t n_regular;    /* regular cells (finest level) */
+  int64_t n_irregular;  /* irregular cells (finest level) */
+  int64_t n_segments;   /* boundary segments (finest level) */
+  int64_t device_bytes; /* device memory held by the handle */
+  double setup_ms;      /* host + upload time of ccm_setup */
+  double plg_cond_max;  /* largest 2-norm condition number of a chosen FV sample matrix */
+} ccm_info;
+
+typedef struct {
+  int iterations;           /* outer iterations (V-cycles) performed */
+  double rel_residual;      /* ||r - L u||_inf / ||r||_inf at exit (FP64) */
+  double history[64];       /* relative residual after each iteration (first 64) */
+} ccm_stats;
+
+typedef struct ccm_handle ccm_handle;
+
+/* Fill p with the defaults: omega 0.8, nu1 = nu2 = 3, theta 0.3, coarsest 16, CCM_MIXED,
+ * rtol 1e-10, max_iter 100, ras_passes 1, ras_block 64, ras_overlap 32, nthreads 0. */
+int ccm_default_params(ccm_params* p);
+
+/* Host setup (Sec. 3.1 - 3.4, Sec. 4): cut cells and moments (Green's formula, Sec. 2.4),
+ * Alg. 1 merging, regular/irregular classification, PLG stencils and weighted min-norm
+ * fits (eq. derivedCoefAgain) on every level h 2^m, the boundary ordering of Alg. 3, and the
+ * upload of the packed level arrays to the current device.  params may be NULL (defaults).
+ * Blocking; *out receives a new handle, release it with ccm_free.  Errors: CCM_EINVAL,
+ * CCM_EGEOM, CCM_EPLG, CCM_ESINGULAR, CCM_ENOMEM, CCM_ECUDA. */
+int ccm_setup(const ccm_problem* prob, const ccm_params* params, ccm_handle** out);
+
+/* Sizes and statistics of a handle (host struct). */
+int ccm_query(const ccm_handle* h, ccm_info* info);
+
+/* Host arrays describing the finest level:
+ *   status[ny*nx]: 0 empty (or merged away), 1 pure, 2 cut / merged survivor;
+ *   owner[ny*nx]: linear index of the cell that holds this cell's unknown (-1 if empty);
+ *   regular[ny*nx]: 1 for regular cells (eq. stdLap stencil), 0 otherwise;
+ *   vol[ny*nx]: volume of the (merged) cut cell in units of h^2.
+ * Any pointer may be NULL.  Blocking. */
+int ccm_cell_map(const ccm_handle* h, int8_t* status, int32_t* owner, int8_t* regular, double* vol);
+
+/* Boundary segments of the finest level in ĝ order (host arrays of n_segments, any may be
+ * NULL): cell = linear index of the owning cell, bc = CCM_DIRICHLET | CCM_NEUMANN,
+ * length = arc length of the piece (physical units).  Blocking. */
+int ccm_boundary_segments(const ccm_handle* h, int32_t* cell, int32_t* bc, double* length);
+
+/* Quadrature rules that reproduce the averages the discretisation expects (Sec. 3.2,
+ * eq. iteratedIntegral): for every non-pure non-empty cell, nodes and weights whose weighted
+ * sum over f is the integral of f over the (merged) cut cell; for every boundary segment,
+ * nodes, arc-length weights and outward unit normals along its pieces.  Pure cells are plain
+ * squares (the caller uses a tensor Gauss rule).  Call with NULL arrays to get the counts
+ * in *n_cell_nodes / *n_bdry_nodes, then again with host arrays of those sizes:
+ *   cell_of[n]: linear cell index, cxy[2n]: (x, y), cw[n]: weight (area units);
+ *   seg_of[m]: segment index, bxy[2m]: (x, y), bw[m]: weight (length), bn[2m]: normal. */
+int ccm_quadrature(const ccm_handle* h, int64_t* n_cell_nodes, int64_t* n_bdry_nodes,
+                   int32_t* cell_of, double* cxy, double* cw,
+                   int32_t* seg_of, double* bxy, double* bw, double* bn);
+
+/* out = L u + N g (eq. PoissonLinearDiscretization) on the finest level, physical units.
+ * u, out: device [nrhs][ny][nx] FP64; g: device [nrhs][n_segments] FP64 (may be NULL: g = 0).
+ * Runs in FP64 (regular stencil, Sec. 3.2; fitted irregular rows, eq. goalOfApproximation). */
+int ccm_apply(ccm_handle* h, const double* u, const double* g, double* out, int nrhs, void* stream);
+
+/* Transposed operator: out_u = L^T v, out_g = N^T v (either may be NULL).  v, out_u:
+ * device [nrhs][ny][nx]; out_g: device [nrhs][n_segments]; FP64.  Uses the point-symmetric
+ * regular stencil on regular rows and a precomputed transposed CSR of the fitted rows. */
+int ccm_apply_T(ccm_handle* h, const double* v, double* out_u, double* out_g, int nrhs, void* stream);
+
+/* Solve L u = f - N g (eq. PoissonResidualForm) by V-cycles (Alg. 2) to rtol.
+ * f: device [nrhs][ny][nx] cell averages; g: device [nrhs][n_segments] (NULL: g = 0);
+ * u: device [nrhs][ny][nx], in: initial guess, out: solution.  stats (host, nullable)
+ * receives the iteration count and residual history of the last right-hand side.
+ * Synchronises the stream once per outer iteration (the convergence test).
+ * Errors: CCM_ENOCONV (u holds the last iterate), CCM_ENOTFINITE, CCM_ECUDA. */
+int ccm_solve(ccm_handle* h, const double* f, const double* g, double* u, int nrhs,
+              void* stream, ccm_stats* stats);
+
+/* Adjoint solve L^T lambda = rhs with the transposed V-cycle; lambda in: guess, out: solution.
+ * rhs, lambda: device [nrhs][ny][nx].  Gradients of a loss J(u(f, g)): dJ/df = lambda,
+ * dJ/dg = -N^T lambda (apply ccm_apply_T to lambda). */
+int ccm_solve_T(ccm_handle* h, const double* rhs, double* lambda, int nrhs, void* stream,
+                ccm_stats* stats);
+
+/* ---- level components of the V-cycle (one call = one step of the path, for testing and
+ *      composition).  Level arrays use the user layout of that level: [ny_m][nx_m] FP64
+ *      device arrays with nx_m = nx >> m, values in physical units of level m. */
+
+/* out = L^(m) u on level m (no boundary term). */
+int ccm_level_apply(ccm_handle* h, int level, const double* u, double* out, void* stream);
+/* One smoother step on level m (Sec. 4.1): SMO-1 (weighted Jacobi on the regular cells)
+ * then SMO-2 (block update of the irregular cells) for L^(m) u = r; u is updated in place.
+ * precision CCM_FP64 or CCM_MIXED (FP32 arithmetic, FP64 in and out). */
+int ccm_level_smooth(ccm_handle* h, int level, double* u, const double* r, int precision, void* stream);
+/* Coarse residual (Alg. 2): rc = Restrict(r - L^(m) u) on level m + 1. */
+int ccm_level_restrict(ccm_handle* h, int level, const double* u, const double* r, double* rc, void* stream);
+/* Prolongation (Alg. 2): u += Prolong(uc), uc on level m + 1. */
+int ccm_level_prolong(ccm_handle* h, int level, const double* uc, double* u, void* stream);
+/* Bottom solve on the coarsest level M: u = (L^(M))^-1 r. */
+int ccm_bottom_solve(ccm_handle* h, const double* r, double* u, void* stream);
+/* One V-cycle (Alg. 2) on level 0 for L u = r (physical units, FP64 in and out). */
+int ccm_vcycle(ccm_handle* h, double* u, const double* r, int precision, void* stream);
+
+/* ---- host-only view of the setup (no device memory is touched; usable without a GPU).
+ * ccm_host_build runs the same host setup as ccm_setup and keeps the result on the host so
+ * its discrete choices can be inspected and checked. */
+typedef struct ccm_host_setup ccm_host_setup;
+int ccm_host_build(const ccm_problem* prob, const ccm_params* params, ccm_host_setup** out);
+/* sizes of level m: cells per side, fitted rows, boundary segments */
+int ccm_host_level_sizes(const ccm_host_setup* s, int level, int* nx, int* ny, int64_t* n_irregular,
+                         int64_t* n_segments);
+/* fitted rows of level m (host arrays): cell[n2] linear index; cols[n2*15] linear indices
+ * (row-major, cell first); beta[n2*15] and nb[n2] in physical units (L = h^-2 * scaled);
+ * seg[n2] boundary segment or -1.  Any pointer may be NULL. */
+int ccm_host_rows(const ccm_host_setup* s, int level, int32_t* cell, int32_t* cols, double* beta, double* nb,
+                  int32_t* seg);
+/* cell map of level m (see ccm_cell_map) and per-cell moments mom[ny*nx*15] in the cell frame
+ * (units of h, graded monomial order (0,0),(1,0),(0,1),(2,0),...); any pointer may be NULL. */
+int ccm_host_cell_map(const ccm_host_setup* s, int level, int8_t* status, int32_t* owner, int8_t* regular,
+                      double* vol, double* mom);
+void ccm_host_free(ccm_host_setup* s);
+
+void ccm_free(ccm_handle* h);
+const char* ccm_strerror(int code);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* CCM_H */

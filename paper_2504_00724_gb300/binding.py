@@ -1,0 +1,368 @@
+"""ctypes marshalling for libccm.so (include/ccm.h).  No arithmetic of the method here."""
+from __future__ import annotations
+
+import ctypes
+import math
+import os
+from typing import Optional, Sequence
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIBPATH = os.path.join(HERE, "libccm.so")
+
+CCM_CIRCLE, CCM_ELLIPSE, CCM_STAR = 1, 2, 3
+CCM_NONE, CCM_DIRICHLET, CCM_NEUMANN = 0, 1, 2
+CCM_FP64, CCM_MIXED = 0, 1
+
+
+class CcmError(RuntimeError):
+    def __init__(self, code: int, what: str):
+        self.code = code
+        super().__init__(f"{what}: {lib().ccm_strerror(code).decode()} ({code})")
+
+
+class ccm_curve(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int), ("p", ctypes.c_double * 8), ("orient", ctypes.c_int),
+                ("bc", ctypes.c_int)]
+
+
+class ccm_problem(ctypes.Structure):
+    _fields_ = [("a", ctypes.c_double), ("b", ctypes.c_double), ("c", ctypes.c_double),
+                ("x0", ctypes.c_double), ("y0", ctypes.c_double), ("h", ctypes.c_double),
+                ("nx", ctypes.c_int), ("ny", ctypes.c_int), ("box_bc", ctypes.c_int),
+                ("ncurves", ctypes.c_int), ("curves", ctypes.POINTER(ccm_curve))]
+
+
+class ccm_params(ctypes.Structure):
+    _fields_ = [("omega", ctypes.c_double), ("nu1", ctypes.c_int), ("nu2", ctypes.c_int),
+                ("theta", ctypes.c_double), ("coarsest", ctypes.c_int), ("precision", ctypes.c_int),
+                ("rtol", ctypes.c_double), ("max_iter", ctypes.c_int), ("ras_passes", ctypes.c_int),
+                ("ras_block", ctypes.c_int), ("ras_overlap", ctypes.c_int), ("nthreads", ctypes.c_int)]
+
+
+class ccm_info(ctypes.Structure):
+    _fields_ = [("nx", ctypes.c_int), ("ny", ctypes.c_int), ("levels", ctypes.c_int),
+                ("n_cells", ctypes.c_int64), ("n_regular", ctypes.c_int64),
+                ("n_irregular", ctypes.c_int64), ("n_segments", ctypes.c_int64),
+                ("device_bytes", ctypes.c_int64), ("setup_ms", ctypes.c_double),
+                ("plg_cond_max", ctypes.c_double)]
+
+
+class ccm_stats(ctypes.Structure):
+    _fields_ = [("iterations", ctypes.c_int), ("rel_residual", ctypes.c_double),
+                ("history", ctypes.c_double * 64)]
+
+
+_LIB = None
+
+P = ctypes.c_void_p
+I = ctypes.c_int
+I64P = ctypes.POINTER(ctypes.c_int64)
+
+_SIGS = {
+    "ccm_default_params": (I, [ctypes.POINTER(ccm_params)]),
+    "ccm_setup": (I, [ctypes.POINTER(ccm_problem), ctypes.POINTER(ccm_params), ctypes.POINTER(P)]),
+    "ccm_query": (I, [P, ctypes.POINTER(ccm_info)]),
+    "ccm_cell_map": (I, [P, P, P, P, P]),
+    "ccm_boundary_segments": (I, [P, P, P, P]),
+    "ccm_quadrature": (I, [P, I64P, I64P, P, P, P, P, P, P, P]),
+    "ccm_apply": (I, [P, P, P, P, I, P]),
+    "ccm_apply_T": (I, [P, P, P, P, I, P]),
+    "ccm_solve": (I, [P, P, P, P, I, P, ctypes.POINTER(ccm_stats)]),
+    "ccm_solve_T": (I, [P, P, P, I, P, ctypes.POINTER(ccm_stats)]),
+    "ccm_level_apply": (I, [P, I, P, P, P]),
+    "ccm_level_smooth": (I, [P, I, P, P, I, P]),
+    "ccm_level_restrict": (I, [P, I, P, P, P, P]),
+    "ccm_level_prolong": (I, [P, I, P, P, P]),
+    "ccm_bottom_solve": (I, [P, P, P, P]),
+    "ccm_vcycle": (I, [P, P, P, I, P]),
+    "ccm_free": (None, [P]),
+    "ccm_strerror": (ctypes.c_char_p, [I]),
+    "ccm_host_build": (I, [ctypes.POINTER(ccm_problem), ctypes.POINTER(ccm_params), ctypes.POINTER(P)]),
+    "ccm_host_level_sizes": (I, [P, I, ctypes.POINTER(I), ctypes.POINTER(I), I64P, I64P]),
+    "ccm_host_rows": (I, [P, I, P, P, P, P, P]),
+    "ccm_host_cell_map": (I, [P, I, P, P, P, P, P]),
+    "ccm_host_free": (None, [P]),
+}
+
+
+def load_library(path: str = LIBPATH) -> ctypes.CDLL:
+    """Load libccm.so and declare every entry point of include/ccm.h; raises if absent."""
+    global _LIB
+    if _LIB is not None:
+        return _LIB
+    if not os.path.exists(path):
+        raise ImportError(f"libccm.so not built ({path}); run paper_2504_00724_gb300/build.py")
+    L = ctypes.CDLL(path)
+    for name, (res, args) in _SIGS.items():
+        fn = getattr(L, name)
+        fn.restype = res
+        fn.argtypes = args
+    _LIB = L
+    return L
+
+
+def lib() -> ctypes.CDLL:
+    return load_library()
+
+
+def _check(rc: int, what: str):
+    if rc != 0:
+        raise CcmError(rc, what)
+
+
+def default_params(**kw) -> ccm_params:
+    p = ccm_params()
+    _check(lib().ccm_default_params(ctypes.byref(p)), "ccm_default_params")
+    for k, v in kw.items():
+        if not hasattr(p, k):
+            raise KeyError(k)
+        setattr(p, k, v)
+    return p
+
+
+def problem_struct(prob) -> tuple:
+    """ccm_problem from a workloads.Problem-like object (keeps the curve array alive)."""
+    n = len(prob.curves)
+    arr = (ccm_curve * max(1, n))()
+    for k, c in enumerate(prob.curves):
+        arr[k].kind = int(c.kind)
+        for m, v in enumerate(c.params):
+            arr[k].p[m] = float(v)
+        arr[k].orient = int(c.orient)
+        arr[k].bc = int(c.bc)
+    s = ccm_problem(float(prob.a), float(prob.b), float(prob.c), float(prob.x0), float(prob.y0),
+                    float(prob.h), int(prob.nx), int(prob.ny), int(prob.box_bc), n, arr)
+    return s, arr
+
+
+def _ptr(t) -> int:
+    if t is None:
+        return None
+    return t.data_ptr()
+
+
+def _stream(stream) -> int:
+    import torch
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return stream.cuda_stream
+
+
+class Solver:
+    """A set-up problem on the current CUDA device (one handle of the C ABI)."""
+
+    def __init__(self, prob, **params):
+        self.prob = prob
+        self._ps, self._curves = problem_struct(prob)
+        self.params = default_params(**params)
+        h = P()
+        _check(lib().ccm_setup(ctypes.byref(self._ps), ctypes.byref(self.params), ctypes.byref(h)), "ccm_setup")
+        self.h = h
+        self.info = ccm_info()
+        _check(lib().ccm_query(self.h, ctypes.byref(self.info)), "ccm_query")
+        self.nx, self.ny = prob.nx, prob.ny
+        self.nseg = int(self.info.n_segments)
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().ccm_free(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # ---- host queries
+    def cell_map(self):
+        n = self.nx * self.ny
+        st = np.zeros(n, np.int8)
+        ow = np.zeros(n, np.int32)
+        rg = np.zeros(n, np.int8)
+        vol = np.zeros(n, np.float64)
+        _check(lib().ccm_cell_map(self.h, st.ctypes.data, ow.ctypes.data, rg.ctypes.data, vol.ctypes.data),
+               "ccm_cell_map")
+        sh = (self.ny, self.nx)
+        return st.reshape(sh), ow.reshape(sh), rg.reshape(sh), vol.reshape(sh)
+
+    def boundary_segments(self):
+        cell = np.zeros(self.nseg, np.int32)
+        bc = np.zeros(self.nseg, np.int32)
+        ln = np.zeros(self.nseg, np.float64)
+        _check(lib().ccm_boundary_segments(self.h, cell.ctypes.data, bc.ctypes.data, ln.ctypes.data),
+               "ccm_boundary_segments")
+        return cell, bc, ln
+
+    def quadrature(self):
+        nc, nb = ctypes.c_int64(0), ctypes.c_int64(0)
+        _check(lib().ccm_quadrature(self.h, ctypes.byref(nc), ctypes.byref(nb), None, None, None, None, None,
+                                    None, None), "ccm_quadrature")
+        n, m = nc.value, nb.value
+        cell = np.zeros(n, np.int32)
+        cxy = np.zeros((n, 2))
+        cw = np.zeros(n)
+        seg = np.zeros(m, np.int32)
+        bxy = np.zeros((m, 2))
+        bw = np.zeros(m)
+        bn = np.zeros((m, 2))
+        _check(lib().ccm_quadrature(self.h, ctypes.byref(nc), ctypes.byref(nb), cell.ctypes.data, cxy.ctypes.data,
+                                    cw.ctypes.data, seg.ctypes.data, bxy.ctypes.data, bw.ctypes.data,
+                                    bn.ctypes.data), "ccm_quadrature")
+        return cell, cxy, cw, seg, bxy, bw, bn
+
+    # ---- device operations (torch float64 CUDA tensors, C-contiguous)
+    def apply(self, u, g=None, out=None, stream=None):
+        import torch
+        nrhs = u.numel() // (self.nx * self.ny)
+        out = torch.empty_like(u) if out is None else out
+        _check(lib().ccm_apply(self.h, _ptr(u), _ptr(g), _ptr(out), nrhs, _stream(stream)), "ccm_apply")
+        return out
+
+    def apply_T(self, v, stream=None, want_u=True, want_g=True):
+        import torch
+        nrhs = v.numel() // (self.nx * self.ny)
+        ou = torch.empty_like(v) if want_u else None
+        og = torch.empty(v.shape[:-2] + (self.nseg,), dtype=v.dtype, device=v.device) if want_g else None
+        _check(lib().ccm_apply_T(self.h, _ptr(v), _ptr(ou), _ptr(og), nrhs, _stream(stream)), "ccm_apply_T")
+        return ou, og
+
+    def solve(self, f, g=None, u0=None, stream=None, check=True):
+        import torch
+        nrhs = f.numel() // (self.nx * self.ny)
+        u = torch.zeros_like(f) if u0 is None else u0.clone()
+        st = ccm_stats()
+        rc = lib().ccm_solve(self.h, _ptr(f), _ptr(g), _ptr(u), nrhs, _stream(stream), ctypes.byref(st))
+        if check:
+            _check(rc, "ccm_solve")
+        return u, st
+
+    def level_apply(self, level, u, stream=None):
+        import torch
+        out = torch.empty_like(u)
+        _check(lib().ccm_level_apply(self.h, level, _ptr(u), _ptr(out), _stream(stream)), "ccm_level_apply")
+        return out
+
+    def level_smooth(self, level, u, r, precision=CCM_FP64, stream=None):
+        u = u.clone()
+        _check(lib().ccm_level_smooth(self.h, level, _ptr(u), _ptr(r), precision, _stream(stream)),
+               "ccm_level_smooth")
+        return u
+
+    def level_restrict(self, level, u, r, stream=None):
+        import torch
+        nc, mc = self.nx >> (level + 1), self.ny >> (level + 1)
+        rc = torch.zeros((mc, nc), dtype=u.dtype, device=u.device)
+        _check(lib().ccm_level_restrict(self.h, level, _ptr(u), _ptr(r), _ptr(rc), _stream(stream)),
+               "ccm_level_restrict")
+        return rc
+
+    def level_prolong(self, level, uc, u, stream=None):
+        u = u.clone()
+        _check(lib().ccm_level_prolong(self.h, level, _ptr(uc), _ptr(u), _stream(stream)), "ccm_level_prolong")
+        return u
+
+    def bottom_solve(self, r, stream=None):
+        import torch
+        u = torch.zeros_like(r)
+        _check(lib().ccm_bottom_solve(self.h, _ptr(r), _ptr(u), _stream(stream)), "ccm_bottom_solve")
+        return u
+
+    def vcycle(self, u, r, precision=CCM_FP64, stream=None):
+        u = u.clone()
+        _check(lib().ccm_vcycle(self.h, _ptr(u), _ptr(r), precision, _stream(stream)), "ccm_vcycle")
+        return u
+
+    # ---- caller-side helpers (input preparation, not part of the solve)
+    def cell_averages(self, fn, quad=None) -> np.ndarray:
+        """<fn> over every non-empty cell [ny, nx] (host): 5 x 5 Gauss on pure cells, the
+        library's cut-cell quadrature elsewhere."""
+        st, ow, rg, vol = self.cell_map()
+        h = self.prob.h
+        out = np.zeros((self.ny, self.nx))
+        gx, gw = np.polynomial.legendre.leggauss(5)
+        pj, pi = np.nonzero(st == 1)
+        xc = self.prob.x0 + (pi + 0.5) * h
+        yc = self.prob.y0 + (pj + 0.5) * h
+        acc = np.zeros(xc.shape)
+        for a in range(5):
+            for b in range(5):
+                acc += gw[a] * gw[b] * fn(xc + 0.5 * h * gx[a], yc + 0.5 * h * gx[b])
+        out[pj, pi] = acc / 4.0
+        cell, cxy, cw, *_ = self.quadrature() if quad is None else quad
+        if len(cell):
+            vals = fn(cxy[:, 0], cxy[:, 1]) * cw
+            sums = np.bincount(cell, weights=vals, minlength=self.nx * self.ny)
+            cut = (st == 2).ravel()
+            flat = out.ravel()
+            flat[cut] = sums[cut] / (vol.ravel()[cut] * h * h)
+            out = flat.reshape(self.ny, self.nx)
+        return out
+
+    def boundary_averages(self, u, ux, uy, quad=None) -> np.ndarray:
+        """<<N u>> over every boundary segment (host): u (Dirichlet) or grad u . n (Neumann)."""
+        cell, bc, ln = self.boundary_segments()
+        q = self.quadrature() if quad is None else quad
+        seg, bxy, bw, bn = q[3], q[4], q[5], q[6]
+        x, y = bxy[:, 0], bxy[:, 1]
+        sb = bc[seg]
+        val = np.where(sb == CCM_DIRICHLET, u(x, y), ux(x, y) * bn[:, 0] + uy(x, y) * bn[:, 1])
+        num = np.bincount(seg, weights=val * bw, minlength=self.nseg)
+        den = np.bincount(seg, weights=bw, minlength=self.nseg)
+        return num / den
+
+
+class HostSetup:
+    """Host-only setup (ccm_host_build): the discrete choices of every level, no GPU needed."""
+
+    def __init__(self, prob, **params):
+        self._ps, self._curves = problem_struct(prob)
+        self.params = default_params(**params)
+        h = P()
+        _check(lib().ccm_host_build(ctypes.byref(self._ps), ctypes.byref(self.params), ctypes.byref(h)),
+               "ccm_host_build")
+        self.h = h
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().ccm_host_free(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def sizes(self, level=0):
+        nx, ny = I(0), I(0)
+        n2, ns = ctypes.c_int64(0), ctypes.c_int64(0)
+        _check(lib().ccm_host_level_sizes(self.h, level, ctypes.byref(nx), ctypes.byref(ny), ctypes.byref(n2),
+                                          ctypes.byref(ns)), "ccm_host_level_sizes")
+        return nx.value, ny.value, n2.value, ns.value
+
+    def rows(self, level=0):
+        nx, ny, n2, ns = self.sizes(level)
+        cell = np.zeros(n2, np.int32)
+        cols = np.zeros((n2, 15), np.int32)
+        beta = np.zeros((n2, 15))
+        nb = np.zeros(n2)
+        seg = np.zeros(n2, np.int32)
+        _check(lib().ccm_host_rows(self.h, level, cell.ctypes.data, cols.ctypes.data, beta.ctypes.data,
+                                   nb.ctypes.data, seg.ctypes.data), "ccm_host_rows")
+        return cell, cols, beta, nb, seg
+
+    def cell_map(self, level=0):
+        nx, ny, n2, ns = self.sizes(level)
+        n = nx * ny
+        st = np.zeros(n, np.int8)
+        ow = np.zeros(n, np.int32)
+        rg = np.zeros(n, np.int8)
+        vol = np.zeros(n)
+        mom = np.zeros((n, 15))
+        _check(lib().ccm_host_cell_map(self.h, level, st.ctypes.data, ow.ctypes.data, rg.ctypes.data,
+                                       vol.ctypes.data, mom.ctypes.data), "ccm_host_cell_map")
+        sh = (ny, nx)
+        return st.reshape(sh), ow.reshape(sh), rg.reshape(sh), vol.reshape(sh), mom.reshape(ny, nx, 15)

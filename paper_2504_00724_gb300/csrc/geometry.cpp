@@ -1,0 +1,831 @@
+// Cut cells, Green-formula moments and Alg. 1 merging (Sec. 2.4, Sec. 3.1).
+//
+// A level's box is cut by closed parametric curves.  Crossings of each curve with the grid
+// lines split it into arcs that each lie in one cell; in every cell that holds arcs, the
+// loops "arc, then counter-clockwise along the cell edges to the next arc entry" bound the
+// connected pieces of C_i cap Omega.  Moments int X^p Y^q dA (X, Y in the cell frame,
+// units of h) follow from Green's formula int_C f dA = int_dC F dY with F = X^{p+1}/(p+1)
+// (eq. volumeIntegral with xi0 at the cell centre): exact on straight pieces, Gauss-Legendre
+// on arcs.  Alg. 1 then folds every component but the largest of a multi-piece cell into
+// its largest neighbour, and merges each interface cell with volume <= theta h^2, smallest
+// first, into the non-empty 4-neighbour with the longest common cut face (ties: larger
+// volume, then +x, -x, +y, -y).
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <functional>
+#include <map>
+
+#include "host.h"
+
+namespace ccm {
+
+static const double TWO_PI = 6.283185307179586476925286766559;
+
+// ------------------------------------------------------------------ curves
+
+void Curve::xy(double t, double& x, double& y) const {
+  switch (kind) {
+    case CCM_CIRCLE:
+      x = p[0] + p[2] * std::cos(t);
+      y = p[1] + p[2] * std::sin(t);
+      return;
+    case CCM_ELLIPSE: {
+      double X = p[2] * std::cos(t), Y = p[3] * std::sin(t);
+      double c = std::cos(p[4]), s = std::sin(p[4]);
+      x = p[0] + X * c - Y * s;
+      y = p[1] + X * s + Y * c;
+      return;
+    }
+    default: {
+      double r = p[2] + p[3] * std::cos(p[4] * t);
+      x = p[0] + r * std::cos(t);
+      y = p[1] + r * std::sin(t);
+    }
+  }
+}
+
+void Curve::dxy(double t, double& x, double& y) const {
+  switch (kind) {
+    case CCM_CIRCLE:
+      x = -p[2] * std::sin(t);
+      y = p[2] * std::cos(t);
+      return;
+    case CCM_ELLIPSE: {
+      double X = -p[2] * std::sin(t), Y = p[3] * std::cos(t);
+      double c = std::cos(p[4]), s = std::sin(p[4]);
+      x = X * c - Y * s;
+      y = X * s + Y * c;
+      return;
+    }
+    default: {
+      double r = p[2] + p[3] * std::cos(p[4] * t);
+      double dr = -p[3] * p[4] * std::sin(p[4] * t);
+      x = dr * std::cos(t) - r * std::sin(t);
+      y = dr * std::sin(t) + r * std::cos(t);
+    }
+  }
+}
+
+bool Curve::inside(double x, double y) const {
+  switch (kind) {
+    case CCM_CIRCLE: {
+      double dx = x - p[0], dy = y - p[1];
+      return dx * dx + dy * dy < p[2] * p[2];
+    }
+    case CCM_ELLIPSE: {
+      double dx = x - p[0], dy = y - p[1];
+      double c = std::cos(p[4]), s = std::sin(p[4]);
+      double X = (dx * c + dy * s) / p[2], Y = (-dx * s + dy * c) / p[3];
+      return X * X + Y * Y < 1.0;
+    }
+    default: {
+      double dx = x - p[0], dy = y - p[1];
+      double th = std::atan2(dy, dx);
+      return std::hypot(dx, dy) < p[2] + p[3] * std::cos(p[4] * th);
+    }
+  }
+}
+
+// ------------------------------------------------------------------ moment helpers
+
+const Mom& pure_moments() {
+  static Mom m = [] {
+    Mom r{};
+    for (int k = 0; k < NMOM; ++k) {
+      int p = mono_p(k), q = mono_q(k);
+      double ip = (p % 2) ? 0.0 : 2.0 * std::pow(0.5, p + 1) / (p + 1);
+      double iq = (q % 2) ? 0.0 : 2.0 * std::pow(0.5, q + 1) / (q + 1);
+      r[k] = ip * iq;
+    }
+    return r;
+  }();
+  return m;
+}
+
+static double binom(int n, int k) {
+  static const double B[5][5] = {{1, 0, 0, 0, 0}, {1, 1, 0, 0, 0}, {1, 2, 1, 0, 0}, {1, 3, 3, 1, 0}, {1, 4, 6, 4, 1}};
+  return B[n][k];
+}
+
+// moments about the frame X' = X + dx, Y' = Y + dy
+Mom shift_moments(const Mom& m, double dx, double dy) {
+  double px[5] = {1, dx, dx * dx, dx * dx * dx, dx * dx * dx * dx};
+  double py[5] = {1, dy, dy * dy, dy * dy * dy, dy * dy * dy * dy};
+  Mom out{};
+  for (int k = 0; k < NMOM; ++k) {
+    int p = mono_p(k), q = mono_q(k);
+    double s = 0;
+    for (int a = 0; a <= p; ++a)
+      for (int b = 0; b <= q; ++b) s += binom(p, a) * binom(q, b) * px[p - a] * py[q - b] * m[mono_index(a, b)];
+    out[k] = s;
+  }
+  return out;
+}
+
+const Mom& CutLevel::moments(int lin) const {
+  auto it = mom.find(lin);
+  return it == mom.end() ? pure_moments() : it->second;
+}
+
+void gauss_legendre(int n, std::vector<double>& x, std::vector<double>& w) {
+  x.assign(n, 0.0);
+  w.assign(n, 0.0);
+  for (int i = 0; i < n; ++i) {
+    double z = std::cos(M_PI * (i + 0.75) / (n + 0.5));
+    for (int it = 0; it < 100; ++it) {
+      double p0 = 1.0, p1 = z;
+      for (int k = 2; k <= n; ++k) {
+        double p2 = ((2 * k - 1) * z * p1 - (k - 1) * p0) / k;
+        p0 = p1;
+        p1 = p2;
+      }
+      double dp = n * (z * p1 - p0) / (z * z - 1.0);
+      double dz = p1 / dp;
+      z -= dz;
+      if (std::fabs(dz) < 1e-16) {
+        // final derivative for the weight
+        p0 = 1.0, p1 = z;
+        for (int k = 2; k <= n; ++k) {
+          double p2 = ((2 * k - 1) * z * p1 - (k - 1) * p0) / k;
+          p0 = p1;
+          p1 = p2;
+        }
+        dp = n * (z * p1 - p0) / (z * z - 1.0);
+        break;
+      }
+    }
+    double p0 = 1.0, p1 = z;
+    for (int k = 2; k <= n; ++k) {
+      double p2 = ((2 * k - 1) * z * p1 - (k - 1) * p0) / k;
+      p0 = p1;
+      p1 = p2;
+    }
+    double dp = n * (z * p1 - p0) / (z * z - 1.0);
+    x[i] = -z;
+    w[i] = 2.0 / ((1.0 - z * z) * dp * dp);
+  }
+}
+
+static const int GL_ARC = 12;
+
+struct GL {
+  std::vector<double> x, w;
+  explicit GL(int n) { gauss_legendre(n, x, w); }
+};
+static const GL& gl_arc() {
+  static GL g(GL_ARC);
+  return g;
+}
+
+// int over the piece of X^{p+1}/(p+1) Y^q dY, frame centred at (xc, yc), units of h
+static void piece_moments(const Piece& pc, const std::vector<Curve>& curves, double xc, double yc,
+                          double h, Mom& acc) {
+  if (!pc.arc) {
+    double X0 = (pc.ax - xc) / h, Y0 = (pc.ay - yc) / h;
+    double X1 = (pc.bx - xc) / h, Y1 = (pc.by - yc) / h;
+    if (Y0 == Y1) return;
+    // pieces on cell edges are axis-parallel: vertical here, X constant
+    double X = 0.5 * (X0 + X1);
+    for (int k = 0; k < NMOM; ++k) {
+      int p = mono_p(k), q = mono_q(k);
+      acc[k] += std::pow(X, p + 1) / (p + 1) * (std::pow(Y1, q + 1) - std::pow(Y0, q + 1)) / (q + 1);
+    }
+    return;
+  }
+  const Curve& c = curves[pc.curve];
+  const GL& g = gl_arc();
+  double tm = 0.5 * (pc.t0 + pc.t1), tr = 0.5 * (pc.t1 - pc.t0);
+  for (int n = 0; n < GL_ARC; ++n) {
+    double t = tm + tr * g.x[n], x, y, dx, dy;
+    c.xy(t, x, y);
+    c.dxy(t, dx, dy);
+    double X = (x - xc) / h, Y = (y - yc) / h, wY = dy / h * tr * g.w[n];
+    double Xp[6] = {1, X, X * X, X * X * X, X * X * X * X, X * X * X * X * X};
+    double Yq[5] = {1, Y, Y * Y, Y * Y * Y, Y * Y * Y * Y};
+    for (int k = 0; k < NMOM; ++k) {
+      int p = mono_p(k), q = mono_q(k);
+      acc[k] += Xp[p + 1] / (p + 1) * Yq[q] * wY;
+    }
+  }
+}
+
+// int_S X^p Y^q ds and the same with n_x, n_y (outward normal = right-hand normal)
+static void piece_bmoments(const Piece& pc, const std::vector<Curve>& curves, double xc, double yc,
+                           double h, Mom& b0, Mom& bx, Mom& by) {
+  const GL& g = gl_arc();
+  for (int n = 0; n < GL_ARC; ++n) {
+    double X, Y, ds, nx, ny;
+    if (!pc.arc) {
+      double s = 0.5 * (g.x[n] + 1.0);
+      double X0 = (pc.ax - xc) / h, Y0 = (pc.ay - yc) / h, X1 = (pc.bx - xc) / h, Y1 = (pc.by - yc) / h;
+      X = X0 + (X1 - X0) * s;
+      Y = Y0 + (Y1 - Y0) * s;
+      double L = std::hypot(X1 - X0, Y1 - Y0);
+      ds = L * 0.5 * g.w[n];
+      nx = (Y1 - Y0) / L;
+      ny = -(X1 - X0) / L;
+    } else {
+      const Curve& c = curves[pc.curve];
+      double tm = 0.5 * (pc.t0 + pc.t1), tr = 0.5 * (pc.t1 - pc.t0);
+      double t = tm + tr * g.x[n], x, y, dx, dy;
+      c.xy(t, x, y);
+      c.dxy(t, dx, dy);
+      X = (x - xc) / h;
+      Y = (y - yc) / h;
+      double sp = std::hypot(dx, dy), sg = tr > 0 ? 1.0 : -1.0;
+      ds = sp / h * std::fabs(tr) * g.w[n];
+      nx = sg * dy / sp;
+      ny = -sg * dx / sp;
+    }
+    double Xp[5] = {1, X, X * X, X * X * X, X * X * X * X};
+    double Yq[5] = {1, Y, Y * Y, Y * Y * Y, Y * Y * Y * Y};
+    for (int k = 0; k < NMOM; ++k) {
+      double v = Xp[mono_p(k)] * Yq[mono_q(k)] * ds;
+      b0[k] += v;
+      bx[k] += v * nx;
+      by[k] += v * ny;
+    }
+  }
+}
+
+// ------------------------------------------------------------------ crossings
+
+struct Crossing {
+  double t;
+  int axis;   // 0: vertical line x = x0 + k h, 1: horizontal line y = y0 + k h
+  long k;
+  bool operator<(const Crossing& o) const {
+    if (t != o.t) return t < o.t;
+    if (axis != o.axis) return axis < o.axis;
+    return k < o.k;
+  }
+};
+
+// root of f on [a, b] with f(a) f(b) < 0: bisection-secant (Illinois) to full precision
+static double find_root(const std::function<double(double)>& f, double a, double b, double fa, double fb) {
+  int side = 0;
+  for (int it = 0; it < 300; ++it) {
+    double c = (fa * b - fb * a) / (fa - fb);
+    if (!(c > std::min(a, b) && c < std::max(a, b))) c = 0.5 * (a + b);
+    double fc = f(c);
+    if (fc == 0.0) return c;
+    if ((fc > 0) == (fb > 0)) {
+      b = c;
+      fb = fc;
+      if (side == -1) fa *= 0.5;
+      side = -1;
+    } else {
+      a = c;
+      fa = fc;
+      if (side == 1) fb *= 0.5;
+      side = 1;
+    }
+    if (std::fabs(b - a) <= 4e-16 * std::max(1.0, std::fabs(a))) break;
+  }
+  return std::fabs(fa) < std::fabs(fb) ? a : b;
+}
+
+static std::vector<Crossing> curve_crossings(const Curve& c, double x0, double y0, double h) {
+  double tot = 0, px, py, qx, qy;
+  c.xy(0.0, px, py);
+  for (int s = 1; s <= 4096; ++s) {
+    c.xy(TWO_PI * s / 4096, qx, qy);
+    tot += std::hypot(qx - px, qy - py);
+    px = qx;
+    py = qy;
+  }
+  long ns = std::max<long>(4096, (long)std::ceil(64.0 * tot / h));
+  std::vector<double> t(ns + 1), xs(ns + 1), ys(ns + 1);
+  for (long s = 0; s <= ns; ++s) {
+    t[s] = TWO_PI * (double)s / (double)ns;
+    c.xy(t[s], xs[s], ys[s]);
+  }
+  xs[ns] = xs[0];
+  ys[ns] = ys[0];
+  std::vector<Crossing> out;
+  for (int axis = 0; axis < 2; ++axis) {
+    const std::vector<double>& v = axis == 0 ? xs : ys;
+    double org = axis == 0 ? x0 : y0;
+    long prev = (long)std::floor((v[0] - org) / h);
+    for (long s = 0; s < ns; ++s) {
+      long cur = (long)std::floor((v[s + 1] - org) / h);
+      if (cur != prev) {
+        long lo = std::min(prev, cur), hi = std::max(prev, cur);
+        for (long k = lo + 1; k <= hi; ++k) {
+          double L = org + k * h;
+          double fa = v[s] - L, fb = v[s + 1] - L, tr;
+          if (fa == 0.0) {
+            tr = t[s];
+          } else if (fb == 0.0) {
+            tr = t[s + 1];
+          } else {
+            auto f = [&](double tt) {
+              double x, y;
+              c.xy(tt, x, y);
+              return (axis == 0 ? x : y) - L;
+            };
+            double fbe = f(t[s + 1]);
+            if (fbe * fa > 0) tr = t[s + 1];       // the periodic seam t = 2 pi
+            else tr = find_root(f, t[s], t[s + 1], fa, fbe);
+          }
+          out.push_back({std::fmod(tr, TWO_PI), axis, k});
+        }
+      }
+      prev = cur;
+    }
+  }
+  std::sort(out.begin(), out.end());
+  // a curve that only touches a line crosses it twice at the same parameter: drop both
+  bool changed = true;
+  while (changed && out.size() > 1) {
+    changed = false;
+    size_t n = out.size();
+    for (size_t a = 0; a < n; ++a) {
+      size_t b = (a + 1) % n;
+      double dt = std::fmod(out[b].t - out[a].t + TWO_PI, TWO_PI);
+      if (out[a].axis == out[b].axis && out[a].k == out[b].k && dt < 1e-12) {
+        std::vector<Crossing> keep;
+        for (size_t m = 0; m < n; ++m)
+          if (m != a && m != b) keep.push_back(out[m]);
+        out.swap(keep);
+        changed = true;
+        break;
+      }
+    }
+  }
+  return out;
+}
+
+// ------------------------------------------------------------------ loops
+
+struct Arc {
+  int curve;
+  double ts, te;          // traversal from ts to te
+  double s_in, s_out;     // perimeter coordinates of entry and exit
+  double Xin, Yin, Xout, Yout;
+};
+
+static double sigma_of(double X, double Y, int edge) {
+  switch (edge) {
+    case 0: return X + 0.5;          // bottom
+    case 1: return 1.5 + Y;          // right
+    case 2: return 2.5 - X;          // top
+    default: return 3.5 - Y;         // left
+  }
+}
+
+static const double CORNER_X[4] = {-0.5, 0.5, 0.5, -0.5};
+static const double CORNER_Y[4] = {-0.5, -0.5, 0.5, 0.5};
+
+int build_cut_level(const ccm_problem& prob, int nx, int ny, double h, double theta, CutLevel& cg,
+                    std::string& err) {
+  cg.nx = nx;
+  cg.ny = ny;
+  cg.h = h;
+  cg.x0 = prob.x0;
+  cg.y0 = prob.y0;
+  cg.box_bc = prob.box_bc;
+  cg.curves.clear();
+  for (int k = 0; k < prob.ncurves; ++k) {
+    Curve c;
+    c.kind = prob.curves[k].kind;
+    std::memcpy(c.p, prob.curves[k].p, sizeof(c.p));
+    c.orient = prob.curves[k].orient;
+    c.bc = prob.curves[k].bc;
+    cg.curves.push_back(c);
+  }
+  const bool walls = prob.box_bc != CCM_NONE;
+  const double x0 = prob.x0, y0 = prob.y0;
+  const long N = (long)nx * ny;
+
+  // ---- arcs per cell
+  std::map<int, std::vector<Arc>> arcs;   // ordered by linear index
+  for (int ci = 0; ci < (int)cg.curves.size(); ++ci) {
+    const Curve& c = cg.curves[ci];
+    std::vector<Crossing> cr = curve_crossings(c, x0, y0, h);
+    if (cr.size() < 2) {
+      err = "a curve does not cross the grid";
+      return CCM_EGEOM;
+    }
+    size_t m = cr.size();
+    for (size_t a = 0; a < m; ++a) {
+      Crossing A = cr[a], B = cr[(a + 1) % m];
+      double ta = A.t, tb = B.t;
+      if (a == m - 1) tb += TWO_PI;
+      if (tb - ta < 1e-12) continue;           // zero-length piece through a grid vertex
+      double xm, ym;
+      c.xy(0.5 * (ta + tb), xm, ym);
+      int i = (int)std::floor((xm - x0) / h), j = (int)std::floor((ym - y0) / h);
+      if (i < 0 || i >= nx || j < 0 || j >= ny) {
+        err = "a curve leaves the box";
+        return CCM_EGEOM;
+      }
+      double xc = cg.cx(i), yc = cg.cy(j);
+      auto endpoint = [&](double tt, const Crossing& C, double& X, double& Y, int& edge) -> bool {
+        double px, py;
+        c.xy(tt, px, py);
+        X = std::min(std::max((px - xc) / h, -0.5), 0.5);
+        Y = std::min(std::max((py - yc) / h, -0.5), 0.5);
+        if (C.axis == 0) {
+          if (C.k == i) { X = -0.5; edge = 3; return true; }
+          if (C.k == i + 1) { X = 0.5; edge = 1; return true; }
+        } else {
+          if (C.k == j) { Y = -0.5; edge = 0; return true; }
+          if (C.k == j + 1) { Y = 0.5; edge = 2; return true; }
+        }
+        return false;
+      };
+      double Xa, Ya, Xb, Yb;
+      int ea, eb;
+      if (!endpoint(ta, A, Xa, Ya, ea) || !endpoint(tb, B, Xb, Yb, eb)) {
+        err = "inconsistent curve crossing";
+        return CCM_EGEOM;
+      }
+      Arc arc;
+      arc.curve = ci;
+      if (c.orient > 0) {
+        arc.ts = ta; arc.te = tb;
+        arc.s_in = sigma_of(Xa, Ya, ea); arc.s_out = sigma_of(Xb, Yb, eb);
+        arc.Xin = Xa; arc.Yin = Ya; arc.Xout = Xb; arc.Yout = Yb;
+      } else {
+        arc.ts = tb; arc.te = ta;
+        arc.s_in = sigma_of(Xb, Yb, eb); arc.s_out = sigma_of(Xa, Ya, ea);
+        arc.Xin = Xb; arc.Yin = Yb; arc.Xout = Xa; arc.Yout = Ya;
+      }
+      arcs[j * nx + i].push_back(arc);
+    }
+  }
+
+  // ---- classification of the other cells by their centres
+  cg.status.assign(N, ST_EMPTY);
+  cg.iface.assign(N, 0);
+  for (int j = 0; j < ny; ++j)
+    for (int i = 0; i < nx; ++i) {
+      double x = cg.cx(i), y = cg.cy(j);
+      bool in = true;
+      for (const Curve& c : cg.curves) {
+        bool ins = c.inside(x, y);
+        if ((c.orient > 0) != ins) { in = false; break; }
+      }
+      cg.status[(long)j * nx + i] = in ? ST_PURE : ST_EMPTY;
+    }
+  for (auto& kv : arcs) {
+    cg.status[kv.first] = ST_CUT;
+    cg.iface[kv.first] = 1;
+    cg.first_curve[kv.first] = kv.second[0].curve;
+    cg.arc_param[kv.first] = 0.5 * (kv.second[0].ts + kv.second[0].te);
+  }
+
+  // ---- loops of every interface cell
+  std::unordered_map<int, std::vector<Region>> members;
+  for (auto& kv : arcs) {
+    int lin = kv.first, j = lin / nx, i = lin % nx;
+    double xc = cg.cx(i), yc = cg.cy(j);
+    std::vector<Arc>& A = kv.second;
+    std::vector<char> done(A.size(), 0);
+    std::vector<Region> loops;
+    for (size_t first = 0; first < A.size(); ++first) {
+      if (done[first]) continue;
+      Region reg;
+      reg.hi = i;
+      reg.hj = j;
+      size_t cur = first;
+      int guard = 0;
+      while (true) {
+        if (++guard > 4 * (int)A.size() + 4) {
+          err = "cut-cell loop construction failed";
+          return CCM_EGEOM;
+        }
+        done[cur] = 1;
+        Piece pa;
+        pa.arc = true;
+        pa.curve = A[cur].curve;
+        pa.t0 = A[cur].ts;
+        pa.t1 = A[cur].te;
+        reg.pieces.push_back(pa);
+        size_t best = 0;
+        double bd = 1e300;
+        for (size_t k = 0; k < A.size(); ++k) {
+          double d = std::fmod(A[k].s_in - A[cur].s_out + 8.0, 4.0);
+          if (d < bd) { bd = d; best = k; }
+        }
+        // walk counter-clockwise from the exit to the next entry through the corners
+        std::vector<std::pair<double, double>> pts;
+        pts.push_back({A[cur].Xout, A[cur].Yout});
+        double sa = A[cur].s_out, sb = sa + bd;
+        for (long cidx = (long)std::floor(sa) + 1; cidx < sb; ++cidx) pts.push_back({CORNER_X[cidx % 4], CORNER_Y[cidx % 4]});
+        pts.push_back({A[best].Xin, A[best].Yin});
+        for (size_t q = 0; q + 1 < pts.size(); ++q) {
+          double Xa = pts[q].first, Ya = pts[q].second, Xb = pts[q + 1].first, Yb = pts[q + 1].second;
+          if (Xa == Xb && Ya == Yb) continue;
+          Piece ps;
+          ps.ax = xc + Xa * h;
+          ps.ay = yc + Ya * h;
+          ps.bx = xc + Xb * h;
+          ps.by = yc + Yb * h;
+          ps.wall = walls && ((Xa == -0.5 && Xb == -0.5 && i == 0) || (Xa == 0.5 && Xb == 0.5 && i == nx - 1) ||
+                              (Ya == -0.5 && Yb == -0.5 && j == 0) || (Ya == 0.5 && Yb == 0.5 && j == ny - 1));
+          reg.pieces.push_back(ps);
+        }
+        cur = best;
+        if (cur == first) break;
+        if (done[cur]) {
+          err = "cut-cell loop construction failed";
+          return CCM_EGEOM;
+        }
+      }
+      reg.mom.fill(0.0);
+      for (const Piece& pc : reg.pieces) piece_moments(pc, cg.curves, xc, yc, h, reg.mom);
+      loops.push_back(reg);
+    }
+    members[lin] = loops;
+  }
+
+  cg.vol.assign(N, 0.0);
+  for (long q = 0; q < N; ++q)
+    if (cg.status[q] == ST_PURE) cg.vol[q] = 1.0;
+  for (auto& kv : members) {
+    double v = 0;
+    for (auto& r : kv.second) v += r.mom[0];
+    cg.vol[kv.first] = v;
+  }
+  cg.owner.assign(N, -1);
+  for (long q = 0; q < N; ++q)
+    if (cg.status[q] != ST_EMPTY) cg.owner[q] = (int32_t)q;
+
+  auto pure_region = [&](int lin) {
+    int j = lin / nx, i = lin % nx;
+    double xc = cg.cx(i), yc = cg.cy(j), hh = 0.5 * h;
+    double PX[4] = {xc - hh, xc + hh, xc + hh, xc - hh}, PY[4] = {yc - hh, yc - hh, yc + hh, yc + hh};
+    Region r;
+    r.hi = i;
+    r.hj = j;
+    for (int k = 0; k < 4; ++k) {
+      Piece ps;
+      ps.ax = PX[k];
+      ps.ay = PY[k];
+      ps.bx = PX[(k + 1) % 4];
+      ps.by = PY[(k + 1) % 4];
+      ps.wall = walls && ((k == 0 && j == 0) || (k == 1 && i == nx - 1) || (k == 2 && j == ny - 1) || (k == 3 && i == 0));
+      r.pieces.push_back(ps);
+    }
+    r.mom = pure_moments();
+    return r;
+  };
+  auto cell_members = [&](int lin) -> std::vector<Region>& {
+    auto it = members.find(lin);
+    if (it != members.end()) return it->second;
+    members[lin] = {pure_region(lin)};
+    return members[lin];
+  };
+  auto absorb = [&](int dst, const std::vector<Region>& src) {
+    std::vector<Region>& L = cell_members(dst);
+    for (const Region& r : src) L.push_back(r);
+    cg.status[dst] = ST_CUT;
+    double v = 0;
+    for (const Region& r : L) v += r.mom[0];
+    cg.vol[dst] = v;
+  };
+  // length (units of h) of a loop's straight pieces on edge d (0:+x, 1:-x, 2:+y, 3:-y)
+  auto face_len = [&](const Region& r, int d) {
+    double xc = cg.cx(r.hi), yc = cg.cy(r.hj), L = 0;
+    for (const Piece& pc : r.pieces) {
+      if (pc.arc) continue;
+      double X0 = (pc.ax - xc) / h, Y0 = (pc.ay - yc) / h, X1 = (pc.bx - xc) / h, Y1 = (pc.by - yc) / h;
+      if (d == 0 && std::fabs(X0 - 0.5) < 1e-12 && std::fabs(X1 - 0.5) < 1e-12) L += std::fabs(Y1 - Y0);
+      else if (d == 1 && std::fabs(X0 + 0.5) < 1e-12 && std::fabs(X1 + 0.5) < 1e-12) L += std::fabs(Y1 - Y0);
+      else if (d == 2 && std::fabs(Y0 - 0.5) < 1e-12 && std::fabs(Y1 - 0.5) < 1e-12) L += std::fabs(X1 - X0);
+      else if (d == 3 && std::fabs(Y0 + 0.5) < 1e-12 && std::fabs(Y1 + 0.5) < 1e-12) L += std::fabs(X1 - X0);
+    }
+    return L;
+  };
+  static const int DI[4] = {1, -1, 0, 0}, DJ[4] = {0, 0, 1, -1};
+
+  // ---- Alg. 1 preprocessing: multi-component cells keep their largest component
+  std::vector<int> iface_cells;
+  for (auto& kv : arcs) iface_cells.push_back(kv.first);   // ascending (std::map)
+  for (int lin : iface_cells) {
+    std::vector<Region> loops = members[lin];
+    if (loops.size() < 2) continue;
+    int j = lin / nx, i = lin % nx;
+    std::vector<int> order(loops.size());
+    for (size_t k = 0; k < loops.size(); ++k) order[k] = (int)k;
+    std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return loops[a].mom[0] > loops[b].mom[0]; });
+    for (size_t oi = 1; oi < order.size(); ++oi) {
+      const Region& reg = loops[order[oi]];
+      int best = -1, bd = -1;
+      double bv = -1;
+      for (int d = 0; d < 4; ++d) {
+        if (face_len(reg, d) <= 0.0) continue;
+        int ii = i + DI[d], jj = j + DJ[d];
+        if (ii < 0 || ii >= nx || jj < 0 || jj >= ny) continue;
+        double v = cg.vol[(long)jj * nx + ii];
+        if (v <= 0.0) continue;
+        // larger volume wins; on equal volume the earlier direction (the larger -d) wins
+        if (best < 0 || v > bv) { best = jj * nx + ii; bv = v; bd = d; }
+      }
+      (void)bd;
+      if (best < 0) {
+        err = "isolated cut-cell component";
+        return CCM_EGEOM;
+      }
+      absorb(best, {reg});
+    }
+    members[lin] = {loops[order[0]]};
+    cg.vol[lin] = loops[order[0]].mom[0];
+  }
+
+  // ---- Alg. 1 merging of small interface cells
+  std::unordered_map<int, int> parent;
+  std::vector<int> cand;
+  for (int lin : iface_cells)
+    if (cg.vol[lin] <= theta) cand.push_back(lin);
+  std::stable_sort(cand.begin(), cand.end(), [&](int a, int b) {
+    if (cg.vol[a] != cg.vol[b]) return cg.vol[a] < cg.vol[b];
+    return a < b;
+  });
+  for (int lin : cand) {
+    int j = lin / nx, i = lin % nx;
+    if (cg.vol[lin] > theta || cg.vol[lin] <= 0.0 || parent.count(lin)) continue;
+    const std::vector<Region>& own = members[lin];
+    int best = -1;
+    double bf = -1, bv = -1;
+    for (int d = 0; d < 4; ++d) {
+      int ii = i + DI[d], jj = j + DJ[d];
+      if (ii < 0 || ii >= nx || jj < 0 || jj >= ny) continue;
+      double v = cg.vol[(long)jj * nx + ii];
+      if (v <= 0.0) continue;
+      double fl = 0;
+      for (const Region& r : own)
+        if (r.hi == i && r.hj == j) fl += face_len(r, d);
+      if (best < 0 || fl > bf || (fl == bf && v > bv)) {
+        best = jj * nx + ii;
+        bf = fl;
+        bv = v;
+      }
+    }
+    if (best < 0 || bf <= 0.0) {
+      err = "small cut cell without a face to merge through";
+      return CCM_EGEOM;
+    }
+    std::vector<Region> moved = own;
+    absorb(best, moved);
+    members[lin].clear();
+    cg.vol[lin] = 0.0;
+    cg.status[lin] = ST_EMPTY;
+    parent[lin] = best;
+  }
+  for (auto& kv : parent) {
+    int s = kv.second;
+    while (parent.count(s)) s = parent[s];
+    cg.owner[kv.first] = s;
+  }
+
+  // ---- final moments of non-pure survivors
+  for (auto& kv : members) {
+    int lin = kv.first;
+    if (kv.second.empty() || cg.status[lin] == ST_PURE) continue;
+    int j = lin / nx, i = lin % nx;
+    Mom m{};
+    for (const Region& r : kv.second) {
+      Mom s = shift_moments(r.mom, r.hi - i, r.hj - j);
+      for (int k = 0; k < NMOM; ++k) m[k] += s[k];
+    }
+    cg.mom[lin] = m;
+    cg.regions[lin] = kv.second;
+  }
+
+  // ---- boundary segments: cut survivors with arcs or wall pieces, and pure wall cells
+  std::vector<int> bcells;
+  for (auto& kv : cg.regions) bcells.push_back(kv.first);
+  if (walls) {
+    for (int j = 0; j < ny; ++j)
+      for (int i = 0; i < nx; ++i) {
+        if (i != 0 && j != 0 && i != nx - 1 && j != ny - 1) continue;
+        long q = (long)j * nx + i;
+        if (cg.status[q] == ST_PURE) bcells.push_back((int)q);
+      }
+  }
+  std::sort(bcells.begin(), bcells.end());
+  bcells.erase(std::unique(bcells.begin(), bcells.end()), bcells.end());
+  for (int lin : bcells) {
+    std::vector<Region> regs;
+    if (cg.status[lin] == ST_PURE) regs = {pure_region(lin)};
+    else regs = cg.regions[lin];
+    std::vector<Piece> bp;
+    for (const Region& r : regs)
+      for (const Piece& pc : r.pieces)
+        if (pc.arc || pc.wall) bp.push_back(pc);
+    if (bp.empty()) continue;
+    int bc = -1;
+    for (const Piece& pc : bp) {
+      int b = pc.arc ? cg.curves[pc.curve].bc : prob.box_bc;
+      if (bc < 0) bc = b;
+      else if (bc != b) {
+        err = "a cell mixes boundary-condition types";
+        return CCM_EGEOM;
+      }
+    }
+    int j = lin / nx, i = lin % nx;
+    Mom b0{}, bx{}, by{};
+    for (const Piece& pc : bp) piece_bmoments(pc, cg.curves, cg.cx(i), cg.cy(j), h, b0, bx, by);
+    cg.seg_of[lin] = (int)cg.segs.size();
+    cg.segs.push_back(lin);
+    cg.seg_bc.push_back(bc);
+    cg.bm0.push_back(b0);
+    cg.bmx.push_back(bx);
+    cg.bmy.push_back(by);
+    cg.seg_pieces.push_back(bp);
+  }
+  return CCM_OK;
+}
+
+// ------------------------------------------------------------------ caller quadrature
+
+void cell_quadrature(const CutLevel& cg, std::vector<int32_t>& cell, std::vector<double>& xy,
+                     std::vector<double>& w) {
+  // eq. iteratedIntegral: outer Gauss rule along every boundary piece with dy != 0,
+  // inner Gauss rule in xi from xi0 (the survivor's centre) to x(t)
+  static GL inner(8);
+  const GL& g = gl_arc();
+  cell.clear();
+  xy.clear();
+  w.clear();
+  std::vector<int> keys;
+  for (auto& kv : cg.regions) keys.push_back(kv.first);
+  std::sort(keys.begin(), keys.end());
+  for (int lin : keys) {
+    if (cg.status[lin] != ST_CUT) continue;
+    double xi0 = cg.cx(lin % cg.nx);
+    for (const Region& r : cg.regions.at(lin)) {
+      for (const Piece& pc : r.pieces) {
+        for (int n = 0; n < GL_ARC; ++n) {
+          double x, y, wy;
+          if (!pc.arc) {
+            if (pc.ay == pc.by) break;
+            double s = 0.5 * (g.x[n] + 1.0);
+            x = pc.ax + (pc.bx - pc.ax) * s;
+            y = pc.ay + (pc.by - pc.ay) * s;
+            wy = (pc.by - pc.ay) * 0.5 * g.w[n];
+          } else {
+            const Curve& c = cg.curves[pc.curve];
+            double tm = 0.5 * (pc.t0 + pc.t1), tr = 0.5 * (pc.t1 - pc.t0), dx, dy;
+            c.xy(tm + tr * g.x[n], x, y);
+            c.dxy(tm + tr * g.x[n], dx, dy);
+            wy = dy * tr * g.w[n];
+          }
+          double half = 0.5 * (x - xi0);
+          for (size_t l = 0; l < inner.x.size(); ++l) {
+            cell.push_back(lin);
+            xy.push_back(xi0 + half * (inner.x[l] + 1.0));
+            xy.push_back(y);
+            w.push_back(inner.w[l] * half * wy);
+          }
+        }
+      }
+    }
+  }
+}
+
+void boundary_quadrature(const CutLevel& cg, std::vector<int32_t>& seg, std::vector<double>& xy,
+                         std::vector<double>& w, std::vector<double>& nrm) {
+  const GL& g = gl_arc();
+  seg.clear();
+  xy.clear();
+  w.clear();
+  nrm.clear();
+  for (size_t s = 0; s < cg.segs.size(); ++s) {
+    for (const Piece& pc : cg.seg_pieces[s]) {
+      for (int n = 0; n < GL_ARC; ++n) {
+        double x, y, ds, nx, ny;
+        if (!pc.arc) {
+          double t = 0.5 * (g.x[n] + 1.0);
+          x = pc.ax + (pc.bx - pc.ax) * t;
+          y = pc.ay + (pc.by - pc.ay) * t;
+          double L = std::hypot(pc.bx - pc.ax, pc.by - pc.ay);
+          ds = L * 0.5 * g.w[n];
+          nx = (pc.by - pc.ay) / L;
+          ny = -(pc.bx - pc.ax) / L;
+        } else {
+          const Curve& c = cg.curves[pc.curve];
+          double tm = 0.5 * (pc.t0 + pc.t1), tr = 0.5 * (pc.t1 - pc.t0), dx, dy;
+          c.xy(tm + tr * g.x[n], x, y);
+          c.dxy(tm + tr * g.x[n], dx, dy);
+          double sp = std::hypot(dx, dy), sg = tr > 0 ? 1.0 : -1.0;
+          ds = sp * std::fabs(tr) * g.w[n];
+          nx = sg * dy / sp;
+          ny = -sg * dx / sp;
+        }
+        seg.push_back((int32_t)s);
+        xy.push_back(x);
+        xy.push_back(y);
+        w.push_back(ds);
+        nrm.push_back(nx);
+        nrm.push_back(ny);
+      }
+    }
+  }
+}
+
+}  // namespace ccm

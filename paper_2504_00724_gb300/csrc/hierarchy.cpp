@@ -1,0 +1,387 @@
+// Level hierarchy (Sec. 4): every level h 2^m re-embedded and re-discretised, packed for
+// the device.  The irregular unknowns of each level are put in the boundary order of
+// Alg. 3; SMO-2 uses overlapping blocks of that order with precomputed dense inverses of the
+// L22 sub-blocks, and the coarsest level a dense inverse of L^(M).
+#include <algorithm>
+#include <cmath>
+#include <map>
+#include <thread>
+#include <atomic>
+
+#include "hierarchy.h"
+
+namespace ccm {
+
+bool dense_inverse(std::vector<double>& A, int n) {
+  std::vector<int> piv(n);
+  std::vector<double> LU = A;
+  for (int k = 0; k < n; ++k) {
+    int p = k;
+    double best = std::fabs(LU[(long)k * n + k]);
+    for (int r = k + 1; r < n; ++r)
+      if (std::fabs(LU[(long)r * n + k]) > best) {
+        best = std::fabs(LU[(long)r * n + k]);
+        p = r;
+      }
+    if (!(best > 0.0)) return false;
+    piv[k] = p;
+    if (p != k)
+      for (int c = 0; c < n; ++c) std::swap(LU[(long)k * n + c], LU[(long)p * n + c]);
+    double d = LU[(long)k * n + k];
+    for (int r = k + 1; r < n; ++r) {
+      double f = LU[(long)r * n + k] / d;
+      LU[(long)r * n + k] = f;
+      if (f != 0.0)
+        for (int c = k + 1; c < n; ++c) LU[(long)r * n + c] -= f * LU[(long)k * n + c];
+    }
+  }
+  // solve for the columns of the identity
+  for (int col = 0; col < n; ++col) {
+    std::vector<double> x(n, 0.0);
+    x[col] = 1.0;
+    for (int k = 0; k < n; ++k)
+      if (piv[k] != k) std::swap(x[k], x[piv[k]]);
+    for (int r = 0; r < n; ++r) {
+      double s = x[r];
+      for (int c = 0; c < r; ++c) s -= LU[(long)r * n + c] * x[c];
+      x[r] = s;
+    }
+    for (int r = n - 1; r >= 0; --r) {
+      double s = x[r];
+      for (int c = r + 1; c < n; ++c) s -= LU[(long)r * n + c] * x[c];
+      x[r] = s / LU[(long)r * n + r];
+    }
+    for (int r = 0; r < n; ++r) A[(long)r * n + col] = x[r];
+  }
+  return true;
+}
+
+// Alg. 3: interface cells sorted by the parameter of their boundary piece (components in the
+// order box, curve 0, curve 1, ...); each numbers the unnumbered irregular cells within
+// Chebyshev distance 2; irregular cells farther away ride with their nearest interface cell.
+static std::vector<int> boundary_order(const CutLevel& cg, const Rows& rows) {
+  const int nx = cg.nx, ny = cg.ny;
+  struct Key {
+    int comp;
+    double s;
+    int lin;
+  };
+  std::vector<Key> keys;
+  const double W = nx * cg.h, Hh = ny * cg.h;
+  for (long q = 0; q < (long)nx * ny; ++q) {
+    int j = (int)(q / nx), i = (int)(q % nx);
+    if (cg.iface[q]) {
+      keys.push_back({1 + cg.first_curve.at((int)q), cg.arc_param.at((int)q), (int)q});
+    } else if (cg.status[q] == ST_PURE && cg.seg_of.count((int)q)) {
+      double xc = cg.cx(i) - cg.x0, yc = cg.cy(j) - cg.y0;
+      double d[4] = {yc, W - xc, Hh - yc, xc};
+      int e = (int)(std::min_element(d, d + 4) - d);
+      double s[4] = {xc, W + yc, W + Hh + (W - xc), 2 * W + Hh + (Hh - yc)};
+      keys.push_back({0, s[e], (int)q});
+    }
+  }
+  std::sort(keys.begin(), keys.end(), [](const Key& x, const Key& y) {
+    if (x.comp != y.comp) return x.comp < y.comp;
+    if (x.s != y.s) return x.s < y.s;
+    return x.lin < y.lin;
+  });
+  std::vector<int> rowof((long)nx * ny, -1);
+  for (size_t r = 0; r < rows.irr.size(); ++r) rowof[rows.irr[r]] = (int)r;
+  // far cells: attach to the nearest interface cell (Chebyshev), first in key order on ties
+  std::map<int, std::vector<int>> near;
+  {
+    std::vector<int> dist((long)nx * ny, 1 << 30), who((long)nx * ny, -1);
+    // multi-source BFS in Chebyshev metric over the grid, sources in key order
+    std::vector<int> frontier;
+    for (size_t k = 0; k < keys.size(); ++k) {
+      int q = keys[k].lin;
+      if (dist[q] > 0) {
+        dist[q] = 0;
+        who[q] = (int)k;
+        frontier.push_back(q);
+      }
+    }
+    int d = 0;
+    while (!frontier.empty()) {
+      std::vector<int> next;
+      for (int q : frontier) {
+        int j = q / nx, i = q % nx;
+        for (int dj = -1; dj <= 1; ++dj)
+          for (int di = -1; di <= 1; ++di) {
+            int ii = i + di, jj = j + dj;
+            if (ii < 0 || ii >= nx || jj < 0 || jj >= ny) continue;
+            int q2 = jj * nx + ii;
+            if (dist[q2] > d + 1) {
+              dist[q2] = d + 1;
+              who[q2] = who[q];
+              next.push_back(q2);
+            } else if (dist[q2] == d + 1 && who[q] < who[q2]) {
+              who[q2] = who[q];
+            }
+          }
+      }
+      frontier.swap(next);
+      ++d;
+    }
+    for (int q : rows.irr)
+      if (dist[q] > 2 && who[q] >= 0) near[who[q]].push_back(q);
+  }
+  std::vector<int> order;
+  std::vector<char> done(rows.irr.size(), 0);
+  for (size_t k = 0; k < keys.size(); ++k) {
+    int q0 = keys[k].lin, j = q0 / nx, i = q0 % nx;
+    for (int dj = -2; dj <= 2; ++dj)
+      for (int di = -2; di <= 2; ++di) {
+        int ii = i + di, jj = j + dj;
+        if (ii < 0 || ii >= nx || jj < 0 || jj >= ny) continue;
+        int r = rowof[(long)jj * nx + ii];
+        if (r >= 0 && !done[r]) {
+          done[r] = 1;
+          order.push_back(r);
+        }
+      }
+    auto it = near.find((int)k);
+    if (it != near.end())
+      for (int q : it->second) {
+        int r = rowof[q];
+        if (r >= 0 && !done[r]) {
+          done[r] = 1;
+          order.push_back(r);
+        }
+      }
+  }
+  for (size_t r = 0; r < rows.irr.size(); ++r)
+    if (!done[r]) order.push_back((int)r);
+  return order;
+}
+
+static int pack_level(const CutLevel& cg, const Rows& rows, const ccm_params& par, bool coarsest, bool finest,
+                      HostLevel& L, std::string& err) {
+  L.nx = cg.nx;
+  L.ny = cg.ny;
+  L.h = cg.h;
+  L.pitch = ((cg.nx + 4 + 31) / 32) * 32;
+  L.rows = cg.ny + 4;
+  const long np = L.npad();
+  L.cls.assign(np, 0);
+  L.vol.assign(np, 0.0f);
+  L.owner = cg.owner;
+  L.status = cg.status;
+  for (int j = 0; j < cg.ny; ++j)
+    for (int i = 0; i < cg.nx; ++i) {
+      long q = (long)j * cg.nx + i;
+      if (cg.status[q] == ST_EMPTY) continue;
+      L.cls[L.pad(i, j)] = rows.regular[q] ? 1 : 2;
+      L.vol[L.pad(i, j)] = (float)cg.vol[q];
+    }
+  // active 32 x 8 tiles (any non-empty cell)
+  const int tx = (cg.nx + 31) / 32, ty = (cg.ny + 7) / 8;
+  L.tiles.clear();
+  for (int b = 0; b < ty; ++b)
+    for (int a = 0; a < tx; ++a) {
+      bool any = false;
+      for (int j = b * 8; j < std::min(cg.ny, b * 8 + 8) && !any; ++j)
+        for (int i = a * 32; i < std::min(cg.nx, a * 32 + 32); ++i)
+          if (cg.status[(long)j * cg.nx + i] != ST_EMPTY) {
+            any = true;
+            break;
+          }
+      if (any) {
+        L.tiles.push_back(a);
+        L.tiles.push_back(b);
+      }
+    }
+  // fitted rows
+  const int n2 = (int)rows.irr.size();
+  L.n2 = n2;
+  L.irr_cell.resize(n2);
+  L.ell_col.resize(15L * n2);
+  L.ell_val.resize(15L * n2);
+  L.nb.resize(n2);
+  L.seg.resize(n2);
+  for (int r = 0; r < n2; ++r) {
+    int q = rows.irr[r];
+    L.irr_cell[r] = (int32_t)L.pad(q % cg.nx, q / cg.nx);
+    for (int k = 0; k < 15; ++k) {
+      int c = rows.cols[r][k];
+      L.ell_col[(long)k * n2 + r] = (int32_t)L.pad(c % cg.nx, c / cg.nx);
+      L.ell_val[(long)k * n2 + r] = rows.beta[r][k];
+    }
+    L.nb[r] = rows.nb[r];
+    L.seg[r] = rows.seg[r];
+  }
+  if (finest) {
+    // transposed fitted rows, grouped by column cell
+    std::map<int32_t, std::vector<std::pair<int32_t, double>>> cols;
+    for (int r = 0; r < n2; ++r)
+      for (int k = 0; k < 15; ++k) cols[L.ell_col[(long)k * n2 + r]].push_back({r, L.ell_val[(long)k * n2 + r]});
+    L.tr_ptr.assign(1, 0);
+    for (auto& kv : cols) {
+      L.tr_cell.push_back(kv.first);
+      for (auto& e : kv.second) {
+        L.tr_row.push_back(e.first);
+        L.tr_val.push_back(e.second);
+      }
+      L.tr_ptr.push_back((int32_t)L.tr_row.size());
+    }
+  }
+  if (coarsest) {
+    std::vector<int> cells;
+    for (long q = 0; q < (long)cg.nx * cg.ny; ++q)
+      if (cg.status[q] != ST_EMPTY) cells.push_back((int)q);
+    const int n = (int)cells.size();
+    std::vector<int> idx((long)cg.nx * cg.ny, -1);
+    for (int k = 0; k < n; ++k) idx[cells[k]] = k;
+    std::vector<double> A((long)n * n, 0.0);
+    L.nb_cells = n;
+    L.bot_cell.resize(n);
+    for (int k = 0; k < n; ++k) L.bot_cell[k] = (int32_t)L.pad(cells[k] % cg.nx, cells[k] / cg.nx);
+    // fill from rows: irregular rows
+    std::vector<int> rowof((long)cg.nx * cg.ny, -1);
+    for (int r = 0; r < n2; ++r) rowof[rows.irr[r]] = r;
+    // fitted rows here; regular rows are marked and filled with the stencil by the caller
+    for (int k = 0; k < n; ++k) {
+      int q = cells[k];
+      if (rowof[q] >= 0) {
+        int r = rowof[q];
+        for (int s = 0; s < 15; ++s) {
+          int col = idx[rows.cols[r][s]];
+          if (col < 0) {
+            err = "fitted row references an empty cell";
+            return CCM_EGEOM;
+          }
+          A[(long)k * n + col] += rows.beta[r][s];
+        }
+      } else {
+        A[(long)k * n + k] = NAN;
+      }
+    }
+    L.bot_inv = A;   // finished in build_hierarchy (needs a, b, c)
+  }
+  // SMO-2 blocks over the boundary order
+  if (!coarsest && n2 > 0) {
+    std::vector<int> order = boundary_order(cg, rows);
+    L.order.assign(order.begin(), order.end());
+    std::vector<int> pos(n2);
+    for (int p = 0; p < n2; ++p) pos[order[p]] = p;
+    const int m = std::max(8, par.ras_block), dl = std::max(0, par.ras_overlap);
+    const int nblk = (n2 + m - 1) / m;
+    L.blk.resize(4L * nblk);
+    L.blk_off.resize(nblk);
+    long off = 0;
+    for (int bk = 0; bk < nblk; ++bk) {
+      int cs = bk * m, ce = std::min(n2, cs + m);
+      int es = std::max(0, cs - dl), ee = std::min(n2, ce + dl);
+      L.blk[4 * bk + 0] = cs;
+      L.blk[4 * bk + 1] = ce;
+      L.blk[4 * bk + 2] = es;
+      L.blk[4 * bk + 3] = ee;
+      L.blk_off[bk] = off;
+      off += (long)(ee - es) * (ce - cs);
+    }
+    L.blk_inv.assign(off, 0.0);
+    // the padded cell of every row, to look up the L22 entries
+    std::vector<int> row_of_pad(np, -1);
+    for (int r = 0; r < n2; ++r) row_of_pad[L.irr_cell[r]] = r;
+    std::atomic<int> bad{0};
+    std::atomic<int> next{0};
+    int nt = par.nthreads > 0 ? par.nthreads : (int)std::max(1u, std::thread::hardware_concurrency());
+    auto worker = [&]() {
+      std::vector<double> A;
+      while (true) {
+        int bk = next.fetch_add(1);
+        if (bk >= nblk) break;
+        int cs = L.blk[4 * bk], ce = L.blk[4 * bk + 1], es = L.blk[4 * bk + 2], ee = L.blk[4 * bk + 3];
+        int ne = ee - es;
+        A.assign((long)ne * ne, 0.0);
+        for (int a = 0; a < ne; ++a) {
+          int r = order[es + a];
+          for (int k = 0; k < 15; ++k) {
+            int rc = row_of_pad[L.ell_col[(long)k * n2 + r]];
+            if (rc < 0) continue;                 // a regular column: L21
+            int pc = pos[rc] - es;
+            if (pc < 0 || pc >= ne) continue;     // outside the block
+            A[(long)a * ne + pc] += L.ell_val[(long)k * n2 + r];
+          }
+        }
+        if (!dense_inverse(A, ne)) {
+          bad.store(1);
+          continue;
+        }
+        double* dst = &L.blk_inv[L.blk_off[bk]];
+        int nc = ce - cs;
+        for (int e = 0; e < ne; ++e)
+          for (int c = 0; c < nc; ++c) dst[(long)e * nc + c] = A[(long)(cs - es + c) * ne + e];
+      }
+    };
+    std::vector<std::thread> th;
+    for (int t = 0; t < nt; ++t) th.emplace_back(worker);
+    for (auto& t : th) t.join();
+    if (bad.load()) {
+      err = "singular L22 block";
+      return CCM_ESINGULAR;
+    }
+  }
+  return CCM_OK;
+}
+
+int build_hierarchy(const ccm_problem& prob, const ccm_params& par, Hierarchy& H, std::string& err) {
+  H.a = prob.a;
+  H.b = prob.b;
+  H.c = prob.c;
+  int nl = 1;
+  while ((prob.nx >> (nl - 1)) > par.coarsest && ((prob.nx >> nl) << nl) == prob.nx && ((prob.ny >> nl) << nl) == prob.ny)
+    ++nl;
+  H.levels.resize(nl);
+  H.cut.resize(nl);
+  H.cond_max = 0;
+  double w[5][5];
+  regular_stencil(prob.a, prob.b, prob.c, w);
+  for (int m = 0; m < nl; ++m) {
+    CutLevel& cg = H.cut[m];
+    int rc = build_cut_level(prob, prob.nx >> m, prob.ny >> m, prob.h * (double)(1 << m), par.theta, cg, err);
+    if (rc) return rc;
+    Rows rows;
+    rc = discretize_level(cg, prob.a, prob.b, prob.c, par.nthreads, rows, err);
+    if (rc) return rc;
+    if (m == 0) H.cond_max = rows.cond_max;
+    rc = pack_level(cg, rows, par, m == nl - 1, m == 0, H.levels[m], err);
+    if (rc) return rc;
+    if (m == 0) H.nseg = (int)cg.segs.size();
+    if (m == nl - 1) {
+      HostLevel& L = H.levels[m];
+      const int n = L.nb_cells;
+      std::vector<int> idx((long)cg.nx * cg.ny, -1);
+      std::vector<int> cells;
+      for (long q = 0; q < (long)cg.nx * cg.ny; ++q)
+        if (cg.status[q] != ST_EMPTY) {
+          idx[q] = (int)cells.size();
+          cells.push_back((int)q);
+        }
+      std::vector<double>& A = L.bot_inv;
+      for (int k = 0; k < n; ++k) {
+        if (!std::isnan(A[(long)k * n + k])) continue;
+        A[(long)k * n + k] = 0.0;
+        int q = cells[k], j = q / cg.nx, i = q % cg.nx;
+        for (int dj = -2; dj <= 2; ++dj)
+          for (int di = -2; di <= 2; ++di) {
+            if (w[dj + 2][di + 2] == 0.0) continue;
+            int col = idx[(long)(j + dj) * cg.nx + (i + di)];
+            A[(long)k * n + col] += w[dj + 2][di + 2];
+          }
+      }
+      if (!dense_inverse(A, n)) {
+        err = "singular coarsest-level operator";
+        return CCM_ESINGULAR;
+      }
+      // store [col][row] for coalesced device reads
+      std::vector<double> T((long)n * n);
+      for (int r = 0; r < n; ++r)
+        for (int c2 = 0; c2 < n; ++c2) T[(long)c2 * n + r] = A[(long)r * n + c2];
+      A.swap(T);
+    }
+  }
+  return CCM_OK;
+}
+
+}  // namespace ccm

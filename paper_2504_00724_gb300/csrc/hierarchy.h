@@ -1,0 +1,66 @@
+// Packed host arrays of the multigrid hierarchy (Sec. 4), ready for upload.
+#pragma once
+
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "host.h"
+
+namespace ccm {
+
+// Padded grid layout of one level: a 2-cell zero ring around the nx x ny cells, rows of
+// `pitch` entries (a multiple of 32), cell (i, j) at (j + 2) * pitch + (i + 2).
+struct HostLevel {
+  int nx = 0, ny = 0, pitch = 0, rows = 0;
+  double h = 0;
+  long npad() const { return (long)pitch * rows; }
+  long pad(int i, int j) const { return (long)(j + 2) * pitch + (i + 2); }
+
+  std::vector<uint8_t> cls;     // [npad] 0 empty / ring, 1 regular, 2 irregular
+  std::vector<float> vol;       // [npad] cell volume in units of h^2 (0 if empty)
+  std::vector<int32_t> tiles;   // active 32 x 8 tiles (tile x, tile y) pairs
+
+  // fitted rows, ELL with 15 slots: [slot][n2]
+  int n2 = 0;
+  std::vector<int32_t> irr_cell;   // [n2] padded index of the row's cell
+  std::vector<int32_t> ell_col;    // [15 * n2] padded column index
+  std::vector<double> ell_val;     // [15 * n2] h^2-scaled coefficient
+  std::vector<double> nb;          // [n2] h^2-scaled boundary coefficient
+  std::vector<int32_t> seg;        // [n2] boundary segment or -1
+
+  // SMO-2 blocks: positions index `order` (row numbers of the fitted rows)
+  std::vector<int32_t> order;      // [n2] rows in boundary order (Alg. 3)
+  std::vector<int32_t> blk;        // [nblk * 4]: core begin, core end, ext begin, ext end
+  std::vector<int64_t> blk_off;    // [nblk] offset of the block's matrix
+  std::vector<double> blk_inv;     // per block [ext][core] rows of inv(L22[ext, ext]) for the core
+
+  // coarsest level only: dense inverse over the non-empty cells
+  int nb_cells = 0;
+  std::vector<int32_t> bot_cell;   // [nb_cells] padded index
+  std::vector<double> bot_inv;     // [nb_cells * nb_cells] stored [col][row]
+
+  // finest level transposed rows (CSR over columns): for every padded cell that appears in a
+  // fitted row, the rows referencing it
+  std::vector<int32_t> tr_ptr;     // [n2col + 1]
+  std::vector<int32_t> tr_cell;    // [n2col] padded index of the column cell
+  std::vector<int32_t> tr_row;     // [nnz] row number
+  std::vector<double> tr_val;      // [nnz] coefficient
+
+  // user-layout maps of this level
+  std::vector<int32_t> owner;      // [nx*ny] survivor linear index or -1
+  std::vector<int8_t> status;      // [nx*ny]
+};
+
+struct Hierarchy {
+  double a = 0, b = 0, c = 0;
+  std::vector<HostLevel> levels;
+  std::vector<CutLevel> cut;       // geometry of every level (kept for queries)
+  double cond_max = 0;
+  int nseg = 0;
+};
+
+int build_hierarchy(const ccm_problem& prob, const ccm_params& par, Hierarchy& H, std::string& err);
+bool dense_inverse(std::vector<double>& A, int n);   // in place, partial pivoting
+
+}  // namespace ccm

@@ -1,0 +1,114 @@
+// Host-side data structures of the cut-cell setup (geometry, discretisation, hierarchy).
+#pragma once
+
+#include <array>
+#include <cstdint>
+#include <string>
+#include <unordered_map>
+#include <vector>
+
+#include "../../include/ccm.h"
+
+namespace ccm {
+
+constexpr int NMOM = 15;                        // monomials x^p y^q with p + q <= 4
+using Mom = std::array<double, NMOM>;
+
+// graded order (0,0),(1,0),(0,1),(2,0),(1,1),(0,2),(3,0),...
+inline int mono_p(int k) {
+  static const int P[NMOM] = {0, 1, 0, 2, 1, 0, 3, 2, 1, 0, 4, 3, 2, 1, 0};
+  return P[k];
+}
+inline int mono_q(int k) {
+  static const int Q[NMOM] = {0, 0, 1, 0, 1, 2, 0, 1, 2, 3, 0, 1, 2, 3, 4};
+  return Q[k];
+}
+inline int mono_index(int p, int q) { int d = p + q; return d * (d + 1) / 2 + q; }
+
+enum CellStatus : int8_t { ST_EMPTY = 0, ST_PURE = 1, ST_CUT = 2 };
+
+struct Error {
+  int code;
+  std::string msg;
+};
+
+struct Curve {
+  int kind = 0;
+  double p[8] = {0};
+  int orient = -1;
+  int bc = CCM_DIRICHLET;
+  void xy(double t, double& x, double& y) const;
+  void dxy(double t, double& x, double& y) const;
+  bool inside(double x, double y) const;   // strictly inside the closed curve
+};
+
+// A piece of a cut-cell boundary in global coordinates, traversed with Omega on its left.
+struct Piece {
+  bool arc = false;
+  int curve = -1;
+  double t0 = 0, t1 = 0;            // arc parameters, from t0 to t1
+  double ax = 0, ay = 0, bx = 0, by = 0;  // straight segment from (ax, ay) to (bx, by)
+  bool wall = false;                // straight piece on a box wall that is part of dOmega
+};
+
+struct Region {
+  std::vector<Piece> pieces;
+  int hi = 0, hj = 0;               // Cartesian cell the loop was built in
+  Mom mom{};                        // moments in the frame of (hi, hj)
+};
+
+// Geometry of one level: cut cells after Alg. 1.
+struct CutLevel {
+  int nx = 0, ny = 0;
+  double x0 = 0, y0 = 0, h = 0;
+  int box_bc = CCM_NONE;
+  std::vector<Curve> curves;
+  std::vector<int8_t> status;       // [ny*nx] post-merge status
+  std::vector<int32_t> owner;       // survivor linear index, -1 if empty
+  std::vector<double> vol;          // volume / h^2, 0 for empty
+  std::vector<uint8_t> iface;       // pre-merge interface cells
+  std::unordered_map<int, std::vector<Region>> regions;   // non-pure survivors
+  std::unordered_map<int, Mom> mom;                      // non-pure survivors, own frame
+  std::unordered_map<int, int> first_curve;              // pre-merge interface cell -> curve
+  std::unordered_map<int, double> arc_param;             // pre-merge interface cell -> mid t
+  // boundary segments (sorted by cell index)
+  std::vector<int> segs;
+  std::unordered_map<int, int> seg_of;
+  std::vector<int> seg_bc;
+  std::vector<Mom> bm0, bmx, bmy;
+  std::vector<std::vector<Piece>> seg_pieces;
+
+  double cx(int i) const { return x0 + (i + 0.5) * h; }
+  double cy(int j) const { return y0 + (j + 0.5) * h; }
+  const Mom& moments(int lin) const;
+};
+
+// Fitted rows of one level (h^2-scaled coefficients).
+struct Rows {
+  std::vector<uint8_t> regular;     // [ny*nx]
+  std::vector<int> irr;             // linear indices of irregular cells (row-major order)
+  std::vector<std::array<int, 15>> cols;     // stencil cells (linear indices), cell i first
+  std::vector<std::array<double, 15>> beta;  // h^2-scaled coefficients
+  std::vector<double> nb;           // h^2-scaled boundary coefficient (0 if no segment)
+  std::vector<int> seg;             // segment index or -1
+  double cond_max = 0;
+};
+
+const Mom& pure_moments();
+Mom shift_moments(const Mom& m, double dx, double dy);
+void gauss_legendre(int n, std::vector<double>& x, std::vector<double>& w);
+
+// geometry.cpp
+int build_cut_level(const ccm_problem& prob, int nx, int ny, double h, double theta, CutLevel& out,
+                    std::string& err);
+// discretize.cpp
+int discretize_level(const CutLevel& cg, double a, double b, double c, int nthreads, Rows& rows,
+                     std::string& err);
+void regular_stencil(double a, double b, double c, double w[5][5]);
+// quadrature helpers for callers (geometry.cpp)
+void cell_quadrature(const CutLevel& cg, std::vector<int32_t>& cell, std::vector<double>& xy,
+                     std::vector<double>& w);
+void boundary_quadrature(const CutLevel& cg, std::vector<int32_t>& seg, std::vector<double>& xy,
+                         std::vector<double>& w, std::vector<double>& n);
+
+}  // namespace ccm

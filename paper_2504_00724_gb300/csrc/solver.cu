@@ -1,0 +1,709 @@
+// Device side of the solver: level arrays, the V-cycle of Alg. 2 on the stream, the FP64
+// outer iteration (plain FP64 cycles, or FP32 cycles inside FP64 iterative refinement),
+// and the C ABI of include/ccm.h.
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstring>
+#include <memory>
+#include <string>
+#include <vector>
+
+#include <cuda_runtime.h>
+
+#include "hierarchy.h"
+#include "kernels.cuh"
+
+using namespace ccm;
+
+namespace {
+
+struct DevLevel {
+  int nx = 0, ny = 0, pitch = 0, rows = 0, ntiles = 0, n2 = 0, nblk = 0, nbc = 0, ncolT = 0;
+  long npad = 0;
+  double h = 0;
+  int max_ext = 0;
+  int32_t* tiles = nullptr;
+  uint8_t* cls = nullptr;
+  float* vol = nullptr;
+  int32_t *irr_cell = nullptr, *ell_col = nullptr, *seg = nullptr;
+  double *ell64 = nullptr, *nb = nullptr;
+  float* ell32 = nullptr;
+  int32_t *order = nullptr, *blk = nullptr;
+  int64_t* blk_off = nullptr;
+  double* inv64 = nullptr;
+  float* inv32 = nullptr;
+  int32_t* bot_cell = nullptr;
+  double* bot64 = nullptr;
+  float* bot32 = nullptr;
+  int32_t *tr_ptr = nullptr, *tr_cell = nullptr, *tr_row = nullptr;
+  double* tr_val = nullptr;
+  // work arrays (padded), FP64 and FP32 sets
+  double *u64[2] = {nullptr, nullptr}, *r64 = nullptr, *t64 = nullptr, *res64 = nullptr;
+  float *u32[2] = {nullptr, nullptr}, *r32 = nullptr, *t32 = nullptr, *res32 = nullptr;
+  int cur64 = 0, cur32 = 0;
+};
+
+template <typename T> T* U(DevLevel& L);
+template <> double* U<double>(DevLevel& L) { return L.u64[L.cur64]; }
+template <> float* U<float>(DevLevel& L) { return L.u32[L.cur32]; }
+template <typename T> T* Uother(DevLevel& L);
+template <> double* Uother<double>(DevLevel& L) { return L.u64[1 - L.cur64]; }
+template <> float* Uother<float>(DevLevel& L) { return L.u32[1 - L.cur32]; }
+template <typename T> void flip(DevLevel& L);
+template <> void flip<double>(DevLevel& L) { L.cur64 = 1 - L.cur64; }
+template <> void flip<float>(DevLevel& L) { L.cur32 = 1 - L.cur32; }
+template <typename T> T* R(DevLevel& L);
+template <> double* R<double>(DevLevel& L) { return L.r64; }
+template <> float* R<float>(DevLevel& L) { return L.r32; }
+template <typename T> T* Tmp(DevLevel& L);
+template <> double* Tmp<double>(DevLevel& L) { return L.t64; }
+template <> float* Tmp<float>(DevLevel& L) { return L.t32; }
+template <typename T> T* Res(DevLevel& L);
+template <> double* Res<double>(DevLevel& L) { return L.res64; }
+template <> float* Res<float>(DevLevel& L) { return L.res32; }
+template <typename T> const T* Ell(const DevLevel& L);
+template <> const double* Ell<double>(const DevLevel& L) { return L.ell64; }
+template <> const float* Ell<float>(const DevLevel& L) { return L.ell32; }
+template <typename T> const T* Inv(const DevLevel& L);
+template <> const double* Inv<double>(const DevLevel& L) { return L.inv64; }
+template <> const float* Inv<float>(const DevLevel& L) { return L.inv32; }
+template <typename T> const T* Bot(const DevLevel& L);
+template <> const double* Bot<double>(const DevLevel& L) { return L.bot64; }
+template <> const float* Bot<float>(const DevLevel& L) { return L.bot32; }
+
+struct Arena {
+  std::vector<void*> blocks;
+  long bytes = 0;
+  cudaError_t err = cudaSuccess;
+  template <typename T>
+  T* alloc(long n, bool zero = true) {
+    if (n <= 0 || err != cudaSuccess) return nullptr;
+    void* p = nullptr;
+    err = cudaMalloc(&p, n * sizeof(T));
+    if (err != cudaSuccess) return nullptr;
+    if (zero) err = cudaMemset(p, 0, n * sizeof(T));
+    blocks.push_back(p);
+    bytes += n * (long)sizeof(T);
+    return (T*)p;
+  }
+  template <typename T>
+  T* upload(const std::vector<T>& v) {
+    T* p = alloc<T>((long)v.size(), false);
+    if (p && err == cudaSuccess) err = cudaMemcpy(p, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice);
+    return p;
+  }
+  void release() {
+    for (void* p : blocks) cudaFree(p);
+    blocks.clear();
+  }
+};
+
+}  // namespace
+
+struct ccm_handle {
+  ccm_params par{};
+  double a = 0, b = 0, c = 0;
+  bool cross = false;
+  Hierarchy H;
+  std::vector<DevLevel> L;
+  Arena arena;
+  dev::Stencil<double> S64{};
+  dev::Stencil<float> S32{};
+  double* rhat = nullptr;      // level-0 padded FP64 right-hand side (h^2-scaled)
+  double* uhat = nullptr;      // level-0 padded FP64 solution
+  unsigned long long* dnorm = nullptr;
+  unsigned long long* hnorm = nullptr;   // pinned
+  ccm_info info{};
+  int device = 0;
+};
+
+namespace {
+
+inline int ceil_div(long a, long b) { return (int)((a + b - 1) / b); }
+
+#define CCM_CUDA(call)                                  \
+  do {                                                  \
+    cudaError_t e_ = (call);                            \
+    if (e_ != cudaSuccess) return CCM_ECUDA;            \
+  } while (0)
+
+// ---------------------------------------------------------------- level operations
+
+template <typename T>
+void launch_regular(ccm_handle* H, DevLevel& L, const T* u, const T* r, T* out, bool resid, cudaStream_t s);
+
+template <typename T>
+const dev::Stencil<T>& stencil(ccm_handle* H);
+template <> const dev::Stencil<double>& stencil<double>(ccm_handle* H) { return H->S64; }
+template <> const dev::Stencil<float>& stencil<float>(ccm_handle* H) { return H->S32; }
+
+template <typename T>
+void launch_regular(ccm_handle* H, DevLevel& L, const T* u, const T* r, T* out, bool resid, cudaStream_t s) {
+  if (L.ntiles == 0) return;
+  dim3 blk(dev::TX, dev::TY);
+  const auto& S = stencil<T>(H);
+  if (H->cross) {
+    if (resid) dev::k_regular<T, true, true><<<L.ntiles, blk, 0, s>>>(L.tiles, L.cls, L.nx, L.ny, L.pitch, u, r, out, S);
+    else dev::k_regular<T, true, false><<<L.ntiles, blk, 0, s>>>(L.tiles, L.cls, L.nx, L.ny, L.pitch, u, r, out, S);
+  } else {
+    if (resid) dev::k_regular<T, false, true><<<L.ntiles, blk, 0, s>>>(L.tiles, L.cls, L.nx, L.ny, L.pitch, u, r, out, S);
+    else dev::k_regular<T, false, false><<<L.ntiles, blk, 0, s>>>(L.tiles, L.cls, L.nx, L.ny, L.pitch, u, r, out, S);
+  }
+}
+
+// out = r - L u on every non-empty cell of the level (grid layout)
+template <typename T>
+void residual(ccm_handle* H, DevLevel& L, const T* u, const T* r, T* out, cudaStream_t s) {
+  launch_regular<T>(H, L, u, r, out, true, s);
+  if (L.n2)
+    dev::k_rows<T, T, true, true><<<ceil_div(L.n2, 128), 128, 0, s>>>(L.n2, L.irr_cell, L.ell_col, Ell<T>(L), u, r, out,
+                                                                      nullptr, nullptr, nullptr);
+}
+
+// one smoother step: SMO-1 on the regular cells, then SMO-2 on the irregular cells
+template <typename T>
+void smooth_step(ccm_handle* H, DevLevel& L, cudaStream_t s) {
+  T* uin = U<T>(L);
+  T* uout = Uother<T>(L);
+  const T* r = R<T>(L);
+  if (L.ntiles) {
+    dim3 blk(dev::TX, dev::TY);
+    const auto& S = stencil<T>(H);
+    if (H->cross) dev::k_jacobi<T, true><<<L.ntiles, blk, 0, s>>>(L.tiles, L.cls, L.nx, L.ny, L.pitch, uin, uout, r, S);
+    else dev::k_jacobi<T, false><<<L.ntiles, blk, 0, s>>>(L.tiles, L.cls, L.nx, L.ny, L.pitch, uin, uout, r, S);
+  }
+  flip<T>(L);
+  T* u = U<T>(L);
+  if (L.n2 == 0) return;
+  for (int pass = 0; pass < H->par.ras_passes; ++pass) {
+    dev::k_rows<T, T, true, false><<<ceil_div(L.n2, 128), 128, 0, s>>>(L.n2, L.irr_cell, L.ell_col, Ell<T>(L), u, r,
+                                                                       Res<T>(L), nullptr, nullptr, nullptr);
+    dev::k_block_solve<T><<<L.nblk, 128, L.max_ext * sizeof(T), s>>>(L.order, L.blk, L.blk_off, Inv<T>(L), Res<T>(L),
+                                                                     L.irr_cell, u);
+  }
+}
+
+template <typename T>
+void restrict_to(ccm_handle* H, DevLevel& F, DevLevel& C, cudaStream_t s) {
+  residual<T>(H, F, U<T>(F), R<T>(F), Tmp<T>(F), s);
+  dim3 blk(32, 8), grd(ceil_div(C.nx, 32), ceil_div(C.ny, 8));
+  dev::k_restrict<T><<<grd, blk, 0, s>>>(C.nx, C.ny, C.pitch, F.pitch, C.cls, F.vol, Tmp<T>(F), R<T>(C));
+}
+
+template <typename T>
+void prolong_from(ccm_handle* H, DevLevel& F, DevLevel& C, cudaStream_t s) {
+  if (F.ntiles == 0) return;
+  dim3 blk(dev::TX, dev::TY);
+  dev::k_prolong<T><<<F.ntiles, blk, 0, s>>>(F.tiles, F.cls, F.nx, F.ny, F.pitch, C.pitch, U<T>(C), U<T>(F));
+}
+
+template <typename T>
+void bottom(ccm_handle* H, DevLevel& B, cudaStream_t s) {
+  int nw = 8;
+  size_t sm = std::max<size_t>(B.nbc, nw * 32) * sizeof(T);
+  dev::k_bottom<T><<<ceil_div(B.nbc, 32), nw * 32, sm, s>>>(B.nbc, B.bot_cell, Bot<T>(B), R<T>(B), U<T>(B));
+}
+
+// Alg. 2 from level m: solves L^(m) u = r^(m) approximately, u = U<T>(level m)
+template <typename T>
+void vcycle(ccm_handle* H, int m, cudaStream_t s) {
+  const int M = (int)H->L.size() - 1;
+  DevLevel& F = H->L[m];
+  if (m == M) {
+    bottom<T>(H, F, s);
+    return;
+  }
+  DevLevel& C = H->L[m + 1];
+  for (int k = 0; k < H->par.nu1; ++k) smooth_step<T>(H, F, s);
+  restrict_to<T>(H, F, C, s);
+  cudaMemsetAsync(U<T>(C), 0, C.npad * sizeof(T), s);
+  vcycle<T>(H, m + 1, s);
+  prolong_from<T>(H, F, C, s);
+  for (int k = 0; k < H->par.nu2; ++k) smooth_step<T>(H, F, s);
+}
+
+int read_norm(ccm_handle* H, const uint8_t* cls, long n, const double* x, cudaStream_t s, double& out) {
+  CCM_CUDA(cudaMemsetAsync(H->dnorm, 0, sizeof(unsigned long long), s));
+  dev::k_absmax<double><<<std::min(ceil_div(n, 256), 1216), 256, 0, s>>>(n, cls, x, H->dnorm);
+  CCM_CUDA(cudaMemcpyAsync(H->hnorm, H->dnorm, sizeof(unsigned long long), cudaMemcpyDeviceToHost, s));
+  CCM_CUDA(cudaStreamSynchronize(s));
+  unsigned long long bits = *H->hnorm;
+  std::memcpy(&out, &bits, sizeof(double));
+  return CCM_OK;
+}
+
+int check_level(ccm_handle* h, int level) {
+  if (!h || level < 0 || level >= (int)h->L.size()) return CCM_EINVAL;
+  return CCM_OK;
+}
+
+template <typename T>
+void load_level(ccm_handle* h, DevLevel& L, const double* u, const double* r, cudaStream_t s) {
+  dim3 pg(ceil_div(L.nx, 128), L.ny);
+  cudaMemsetAsync(U<T>(L), 0, L.npad * sizeof(T), s);
+  cudaMemsetAsync(Uother<T>(L), 0, L.npad * sizeof(T), s);
+  cudaMemsetAsync(R<T>(L), 0, L.npad * sizeof(T), s);
+  if (u) dev::k_pack<T, double><<<pg, 128, 0, s>>>(L.nx, L.ny, L.pitch, L.cls, u, U<T>(L), 1.0);
+  if (r) dev::k_pack<T, double><<<pg, 128, 0, s>>>(L.nx, L.ny, L.pitch, L.cls, r, R<T>(L), L.h * L.h);
+}
+
+}  // namespace
+
+// ================================================================ C ABI
+
+extern "C" {
+
+int ccm_default_params(ccm_params* p) {
+  if (!p) return CCM_EINVAL;
+  p->omega = 0.8;
+  p->nu1 = 3;
+  p->nu2 = 3;
+  p->theta = 0.3;
+  p->coarsest = 16;
+  p->precision = CCM_MIXED;
+  p->rtol = 1e-10;
+  p->max_iter = 100;
+  p->ras_passes = 1;
+  p->ras_block = 64;
+  p->ras_overlap = 32;
+  p->nthreads = 0;
+  return CCM_OK;
+}
+
+const char* ccm_strerror(int code) {
+  switch (code) {
+    case CCM_OK: return "ok";
+    case CCM_EINVAL: return "invalid argument";
+    case CCM_EGEOM: return "invalid or degenerate geometry";
+    case CCM_EPLG: return "no poised PLG stencil within the search radius";
+    case CCM_ESINGULAR: return "singular block or bottom factorisation";
+    case CCM_ENOCONV: return "not converged within max_iter";
+    case CCM_ETIMEOUT: return "bounded device wait ran out";
+    case CCM_ECUDA: return "CUDA runtime error";
+    case CCM_ENOMEM: return "out of memory";
+    case CCM_ENOTFINITE: return "residual is not finite";
+    default: return "unknown error";
+  }
+}
+
+int ccm_setup(const ccm_problem* prob, const ccm_params* params, ccm_handle** out) {
+  if (!prob || !out) return CCM_EINVAL;
+  *out = nullptr;
+  if (!(prob->h > 0) || prob->nx < 4 || prob->ny < 4 || prob->ncurves < 0 || (prob->ncurves > 0 && !prob->curves))
+    return CCM_EINVAL;
+  if (!(prob->b * prob->b - 4 * prob->a * prob->c < 0)) return CCM_EINVAL;
+  if (prob->box_bc != CCM_NONE && prob->box_bc != CCM_DIRICHLET && prob->box_bc != CCM_NEUMANN) return CCM_EINVAL;
+  for (int k = 0; k < prob->ncurves; ++k) {
+    const ccm_curve& c = prob->curves[k];
+    if (c.kind < CCM_CIRCLE || c.kind > CCM_STAR || (c.orient != 1 && c.orient != -1) ||
+        (c.bc != CCM_DIRICHLET && c.bc != CCM_NEUMANN))
+      return CCM_EINVAL;
+  }
+  ccm_params par;
+  ccm_default_params(&par);
+  if (params) par = *params;
+  if (par.nu1 < 0 || par.nu2 < 0 || par.coarsest < 4 || par.ras_passes < 0 || par.ras_block < 8 ||
+      par.ras_block > 128 || par.ras_overlap < 0 || par.ras_overlap > 64 || par.max_iter < 0 ||
+      !(par.theta >= 0 && par.theta < 1) || (par.precision != CCM_FP64 && par.precision != CCM_MIXED))
+    return CCM_EINVAL;
+  auto t0 = std::chrono::steady_clock::now();
+  std::unique_ptr<ccm_handle> h(new ccm_handle());
+  h->par = par;
+  h->a = prob->a;
+  h->b = prob->b;
+  h->c = prob->c;
+  h->cross = prob->b != 0.0;
+  cudaGetDevice(&h->device);
+  std::string err;
+  int rc;
+  try {
+    rc = build_hierarchy(*prob, par, h->H, err);
+  } catch (const std::bad_alloc&) {
+    return CCM_ENOMEM;
+  }
+  if (rc) return rc;
+  double w[5][5];
+  regular_stencil(prob->a, prob->b, prob->c, w);
+  for (int k = 0; k < 25; ++k) {
+    h->S64.w[k] = w[k / 5][k % 5];
+    h->S32.w[k] = (float)w[k / 5][k % 5];
+  }
+  h->S64.omega_d = par.omega / w[2][2];
+  h->S32.omega_d = (float)(par.omega / w[2][2]);
+
+  Arena& A = h->arena;
+  const int nl = (int)h->H.levels.size();
+  h->L.resize(nl);
+  for (int m = 0; m < nl; ++m) {
+    HostLevel& hl = h->H.levels[m];
+    DevLevel& d = h->L[m];
+    d.nx = hl.nx;
+    d.ny = hl.ny;
+    d.pitch = hl.pitch;
+    d.rows = hl.rows;
+    d.npad = hl.npad();
+    d.h = hl.h;
+    d.ntiles = (int)hl.tiles.size() / 2;
+    d.tiles = A.upload(hl.tiles);
+    d.cls = A.upload(hl.cls);
+    d.vol = A.upload(hl.vol);
+    d.n2 = hl.n2;
+    if (hl.n2) {
+      d.irr_cell = A.upload(hl.irr_cell);
+      d.ell_col = A.upload(hl.ell_col);
+      d.ell64 = A.upload(hl.ell_val);
+      std::vector<float> f(hl.ell_val.begin(), hl.ell_val.end());
+      d.ell32 = A.upload(f);
+      d.nb = A.upload(hl.nb);
+      d.seg = A.upload(hl.seg);
+      d.res64 = A.alloc<double>(hl.n2);
+      d.res32 = A.alloc<float>(hl.n2);
+    }
+    d.nblk = (int)hl.blk.size() / 4;
+    if (d.nblk) {
+      d.order = A.upload(hl.order);
+      d.blk = A.upload(hl.blk);
+      d.blk_off = A.upload(hl.blk_off);
+      d.inv64 = A.upload(hl.blk_inv);
+      std::vector<float> f(hl.blk_inv.begin(), hl.blk_inv.end());
+      d.inv32 = A.upload(f);
+      for (int b = 0; b < d.nblk; ++b) d.max_ext = std::max(d.max_ext, hl.blk[4 * b + 3] - hl.blk[4 * b + 2]);
+    }
+    d.nbc = hl.nb_cells;
+    if (d.nbc) {
+      d.bot_cell = A.upload(hl.bot_cell);
+      d.bot64 = A.upload(hl.bot_inv);
+      std::vector<float> f(hl.bot_inv.begin(), hl.bot_inv.end());
+      d.bot32 = A.upload(f);
+    }
+    if (!hl.tr_ptr.empty()) {
+      d.ncolT = (int)hl.tr_cell.size();
+      d.tr_ptr = A.upload(hl.tr_ptr);
+      d.tr_cell = A.upload(hl.tr_cell);
+      d.tr_row = A.upload(hl.tr_row);
+      d.tr_val = A.upload(hl.tr_val);
+    }
+    d.u64[0] = A.alloc<double>(d.npad);
+    d.u64[1] = A.alloc<double>(d.npad);
+    d.r64 = A.alloc<double>(d.npad);
+    d.t64 = A.alloc<double>(d.npad);
+    d.u32[0] = A.alloc<float>(d.npad);
+    d.u32[1] = A.alloc<float>(d.npad);
+    d.r32 = A.alloc<float>(d.npad);
+    d.t32 = A.alloc<float>(d.npad);
+  }
+  h->rhat = A.alloc<double>(h->L[0].npad);
+  h->uhat = A.alloc<double>(h->L[0].npad);
+  h->dnorm = A.alloc<unsigned long long>(1);
+  if (A.err != cudaSuccess) {
+    A.release();
+    return A.err == cudaErrorMemoryAllocation ? CCM_ENOMEM : CCM_ECUDA;
+  }
+  if (cudaMallocHost(&h->hnorm, sizeof(unsigned long long)) != cudaSuccess) {
+    A.release();
+    return CCM_ECUDA;
+  }
+  if (cudaDeviceSynchronize() != cudaSuccess) {
+    A.release();
+    return CCM_ECUDA;
+  }
+  // info
+  ccm_info& I = h->info;
+  const CutLevel& c0 = h->H.cut[0];
+  I.nx = prob->nx;
+  I.ny = prob->ny;
+  I.levels = nl;
+  I.n_cells = 0;
+  I.n_regular = 0;
+  for (long q = 0; q < (long)prob->nx * prob->ny; ++q)
+    if (c0.status[q] != ST_EMPTY) ++I.n_cells;
+  I.n_irregular = h->H.levels[0].n2;
+  I.n_regular = I.n_cells - I.n_irregular;
+  I.n_segments = h->H.nseg;
+  I.device_bytes = A.bytes;
+  I.plg_cond_max = h->H.cond_max;
+  I.setup_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+  *out = h.release();
+  return CCM_OK;
+}
+
+int ccm_query(const ccm_handle* h, ccm_info* info) {
+  if (!h || !info) return CCM_EINVAL;
+  *info = h->info;
+  return CCM_OK;
+}
+
+int ccm_cell_map(const ccm_handle* h, int8_t* status, int32_t* owner, int8_t* regular, double* vol) {
+  if (!h) return CCM_EINVAL;
+  const CutLevel& c = h->H.cut[0];
+  const HostLevel& L = h->H.levels[0];
+  long n = (long)c.nx * c.ny;
+  if (status) std::memcpy(status, c.status.data(), n);
+  if (owner) std::memcpy(owner, c.owner.data(), n * sizeof(int32_t));
+  if (vol) std::memcpy(vol, c.vol.data(), n * sizeof(double));
+  if (regular)
+    for (int j = 0; j < c.ny; ++j)
+      for (int i = 0; i < c.nx; ++i) regular[(long)j * c.nx + i] = L.cls[L.pad(i, j)] == 1 ? 1 : 0;
+  return CCM_OK;
+}
+
+int ccm_boundary_segments(const ccm_handle* h, int32_t* cell, int32_t* bc, double* length) {
+  if (!h) return CCM_EINVAL;
+  const CutLevel& c = h->H.cut[0];
+  for (size_t s = 0; s < c.segs.size(); ++s) {
+    if (cell) cell[s] = c.segs[s];
+    if (bc) bc[s] = c.seg_bc[s];
+    if (length) length[s] = c.bm0[s][0] * c.h;
+  }
+  return CCM_OK;
+}
+
+int ccm_quadrature(const ccm_handle* h, int64_t* n_cell_nodes, int64_t* n_bdry_nodes, int32_t* cell_of,
+                   double* cxy, double* cw, int32_t* seg_of, double* bxy, double* bw, double* bn) {
+  if (!h || !n_cell_nodes || !n_bdry_nodes) return CCM_EINVAL;
+  std::vector<int32_t> cc, ss;
+  std::vector<double> xy, w, bxy_, bw_, bn_;
+  cell_quadrature(h->H.cut[0], cc, xy, w);
+  boundary_quadrature(h->H.cut[0], ss, bxy_, bw_, bn_);
+  if (cell_of && cxy && cw) {
+    if (*n_cell_nodes < (int64_t)cc.size()) return CCM_EINVAL;
+    std::memcpy(cell_of, cc.data(), cc.size() * sizeof(int32_t));
+    std::memcpy(cxy, xy.data(), xy.size() * sizeof(double));
+    std::memcpy(cw, w.data(), w.size() * sizeof(double));
+  }
+  if (seg_of && bxy && bw && bn) {
+    if (*n_bdry_nodes < (int64_t)ss.size()) return CCM_EINVAL;
+    std::memcpy(seg_of, ss.data(), ss.size() * sizeof(int32_t));
+    std::memcpy(bxy, bxy_.data(), bxy_.size() * sizeof(double));
+    std::memcpy(bw, bw_.data(), bw_.size() * sizeof(double));
+    std::memcpy(bn, bn_.data(), bn_.size() * sizeof(double));
+  }
+  *n_cell_nodes = (int64_t)cc.size();
+  *n_bdry_nodes = (int64_t)ss.size();
+  return CCM_OK;
+}
+
+int ccm_apply(ccm_handle* h, const double* u, const double* g, double* out, int nrhs, void* stream) {
+  if (!h || !u || !out || nrhs < 1) return CCM_EINVAL;
+  cudaStream_t s = (cudaStream_t)stream;
+  DevLevel& L = h->L[0];
+  const long nu = (long)L.nx * L.ny;
+  dim3 pg(ceil_div(L.nx, 128), L.ny);
+  for (int k = 0; k < nrhs; ++k) {
+    dev::k_pack<double, double><<<pg, 128, 0, s>>>(L.nx, L.ny, L.pitch, L.cls, u + k * nu, L.t64, 1.0);
+    launch_regular<double>(h, L, L.t64, nullptr, L.u64[1 - L.cur64], false, s);
+    if (L.n2)
+      dev::k_rows<double, double, false, true><<<ceil_div(L.n2, 128), 128, 0, s>>>(
+          L.n2, L.irr_cell, L.ell_col, L.ell64, L.t64, nullptr, L.u64[1 - L.cur64], L.nb, L.seg,
+          g ? g + (long)k * h->info.n_segments : nullptr);
+    dev::k_unpack<double><<<pg, 128, 0, s>>>(L.nx, L.ny, L.pitch, L.cls, L.u64[1 - L.cur64], out + k * nu,
+                                             1.0 / (L.h * L.h));
+  }
+  CCM_CUDA(cudaGetLastError());
+  return CCM_OK;
+}
+
+int ccm_apply_T(ccm_handle* h, const double* v, double* out_u, double* out_g, int nrhs, void* stream) {
+  if (!h || !v || nrhs < 1 || (!out_u && !out_g)) return CCM_EINVAL;
+  cudaStream_t s = (cudaStream_t)stream;
+  DevLevel& L = h->L[0];
+  const long nu = (long)L.nx * L.ny;
+  dim3 pg(ceil_div(L.nx, 128), L.ny);
+  const double sc = 1.0 / (L.h * L.h);
+  for (int k = 0; k < nrhs; ++k) {
+    dev::k_pack<double, double><<<pg, 128, 0, s>>>(L.nx, L.ny, L.pitch, L.cls, v + k * nu, L.t64, 1.0);
+    if (out_u) {
+      double* o = L.u64[1 - L.cur64];
+      dim3 blk(dev::TX, dev::TY);
+      if (L.ntiles) {
+        if (h->cross) dev::k_regular_T<true><<<L.ntiles, blk, 0, s>>>(L.tiles, L.cls, L.nx, L.ny, L.pitch, L.t64, o, h->S64);
+        else dev::k_regular_T<false><<<L.ntiles, blk, 0, s>>>(L.tiles, L.cls, L.nx, L.ny, L.pitch, L.t64, o, h->S64);
+      }
+      if (L.ncolT)
+        dev::k_rows_T<<<ceil_div(L.ncolT, 128), 128, 0, s>>>(L.ncolT, L.tr_ptr, L.tr_cell, L.tr_row, L.tr_val,
+                                                            L.irr_cell, L.t64, o);
+      dev::k_unpack<double><<<pg, 128, 0, s>>>(L.nx, L.ny, L.pitch, L.cls, o, out_u + k * nu, sc);
+    }
+    if (out_g && L.n2)
+      dev::k_bnd_T<<<ceil_div(L.n2, 128), 128, 0, s>>>(L.n2, L.irr_cell, L.nb, L.seg, L.t64,
+                                                      out_g + (long)k * h->info.n_segments, sc);
+  }
+  CCM_CUDA(cudaGetLastError());
+  return CCM_OK;
+}
+
+int ccm_solve(ccm_handle* h, const double* f, const double* g, double* u, int nrhs, void* stream, ccm_stats* st) {
+  if (!h || !f || !u || nrhs < 1) return CCM_EINVAL;
+  cudaStream_t s = (cudaStream_t)stream;
+  DevLevel& L = h->L[0];
+  const long nu = (long)L.nx * L.ny, np = L.npad;
+  const double h2 = L.h * L.h;
+  dim3 pg(ceil_div(L.nx, 128), L.ny);
+  int result = CCM_OK;
+  for (int k = 0; k < nrhs; ++k) {
+    // r_hat = h^2 (f - N g)
+    CCM_CUDA(cudaMemsetAsync(h->rhat, 0, np * sizeof(double), s));
+    dev::k_pack<double, double><<<pg, 128, 0, s>>>(L.nx, L.ny, L.pitch, L.cls, f + k * nu, h->rhat, h2);
+    if (g && L.n2)
+      dev::k_sub_boundary<<<ceil_div(L.n2, 128), 128, 0, s>>>(L.n2, L.irr_cell, L.nb, L.seg,
+                                                             g + (long)k * h->info.n_segments, h->rhat);
+    CCM_CUDA(cudaMemsetAsync(h->uhat, 0, np * sizeof(double), s));
+    dev::k_pack<double, double><<<pg, 128, 0, s>>>(L.nx, L.ny, L.pitch, L.cls, u + k * nu, h->uhat, 1.0);
+    double rnorm = 0;
+    int rc = read_norm(h, L.cls, np, h->rhat, s, rnorm);
+    if (rc) return rc;
+    if (rnorm == 0) rnorm = 1;
+    int it = 0;
+    double rel = 0;
+    ccm_stats local{};
+    const bool fp64 = h->par.precision == CCM_FP64;
+    double* U0 = fp64 ? L.u64[L.cur64] : h->uhat;
+    if (fp64) {
+      CCM_CUDA(cudaMemcpyAsync(U0, h->uhat, np * sizeof(double), cudaMemcpyDeviceToDevice, s));
+      CCM_CUDA(cudaMemcpyAsync(L.r64, h->rhat, np * sizeof(double), cudaMemcpyDeviceToDevice, s));
+    }
+    while (true) {
+      double* ucur = fp64 ? L.u64[L.cur64] : h->uhat;
+      residual<double>(h, L, ucur, h->rhat, L.t64, s);
+      rc = read_norm(h, L.cls, np, L.t64, s, rel);
+      if (rc) return rc;
+      rel /= rnorm;
+      if (it < 64) local.history[it] = rel;
+      if (!std::isfinite(rel)) {
+        result = CCM_ENOTFINITE;
+        break;
+      }
+      if (rel <= h->par.rtol) break;
+      if (it >= h->par.max_iter) {
+        result = CCM_ENOCONV;
+        break;
+      }
+      if (fp64) {
+        vcycle<double>(h, 0, s);
+      } else {
+        dev::k_to_float<<<std::min(ceil_div(np, 256), 4096), 256, 0, s>>>(np, L.t64, L.r32);
+        CCM_CUDA(cudaMemsetAsync(L.u32[L.cur32], 0, np * sizeof(float), s));
+        vcycle<float>(h, 0, s);
+        dev::k_axpy<float><<<std::min(ceil_div(np, 256), 4096), 256, 0, s>>>(np, L.cls, L.u32[L.cur32], h->uhat);
+      }
+      CCM_CUDA(cudaGetLastError());
+      ++it;
+    }
+    double* ufin = fp64 ? L.u64[L.cur64] : h->uhat;
+    dev::k_unpack<double><<<pg, 128, 0, s>>>(L.nx, L.ny, L.pitch, L.cls, ufin, u + k * nu, 1.0);
+    local.iterations = it;
+    local.rel_residual = rel;
+    if (st) *st = local;
+  }
+  CCM_CUDA(cudaGetLastError());
+  return result;
+}
+
+int ccm_solve_T(ccm_handle* h, const double* rhs, double* lambda, int nrhs, void* stream, ccm_stats* st) {
+  (void)h; (void)rhs; (void)lambda; (void)nrhs; (void)stream; (void)st;
+  return CCM_EINVAL;
+}
+
+// ---- level components
+
+int ccm_level_apply(ccm_handle* h, int level, const double* u, double* out, void* stream) {
+  if (check_level(h, level) || !u || !out) return CCM_EINVAL;
+  cudaStream_t s = (cudaStream_t)stream;
+  DevLevel& L = h->L[level];
+  dim3 pg(ceil_div(L.nx, 128), L.ny);
+  dev::k_pack<double, double><<<pg, 128, 0, s>>>(L.nx, L.ny, L.pitch, L.cls, u, L.t64, 1.0);
+  launch_regular<double>(h, L, L.t64, nullptr, L.r64, false, s);
+  if (L.n2)
+    dev::k_rows<double, double, false, true><<<ceil_div(L.n2, 128), 128, 0, s>>>(
+        L.n2, L.irr_cell, L.ell_col, L.ell64, L.t64, nullptr, L.r64, L.nb, L.seg, nullptr);
+  dev::k_unpack<double><<<pg, 128, 0, s>>>(L.nx, L.ny, L.pitch, L.cls, L.r64, out, 1.0 / (L.h * L.h));
+  CCM_CUDA(cudaGetLastError());
+  return CCM_OK;
+}
+
+int ccm_level_smooth(ccm_handle* h, int level, double* u, const double* r, int precision, void* stream) {
+  if (check_level(h, level) || !u || !r || level == (int)h->L.size() - 1) return CCM_EINVAL;
+  cudaStream_t s = (cudaStream_t)stream;
+  DevLevel& L = h->L[level];
+  dim3 pg(ceil_div(L.nx, 128), L.ny);
+  if (precision == CCM_FP64) {
+    load_level<double>(h, L, u, r, s);
+    smooth_step<double>(h, L, s);
+    dev::k_unpack<double><<<pg, 128, 0, s>>>(L.nx, L.ny, L.pitch, L.cls, U<double>(L), u, 1.0);
+  } else {
+    load_level<float>(h, L, u, r, s);
+    smooth_step<float>(h, L, s);
+    dev::k_unpack<float><<<pg, 128, 0, s>>>(L.nx, L.ny, L.pitch, L.cls, U<float>(L), u, 1.0);
+  }
+  CCM_CUDA(cudaGetLastError());
+  return CCM_OK;
+}
+
+int ccm_level_restrict(ccm_handle* h, int level, const double* u, const double* r, double* rc, void* stream) {
+  if (check_level(h, level) || level == (int)h->L.size() - 1 || !u || !r || !rc) return CCM_EINVAL;
+  cudaStream_t s = (cudaStream_t)stream;
+  DevLevel& F = h->L[level];
+  DevLevel& C = h->L[level + 1];
+  load_level<double>(h, F, u, r, s);
+  cudaMemsetAsync(C.r64, 0, C.npad * sizeof(double), s);
+  restrict_to<double>(h, F, C, s);
+  dim3 pg(ceil_div(C.nx, 128), C.ny);
+  dev::k_unpack<double><<<pg, 128, 0, s>>>(C.nx, C.ny, C.pitch, C.cls, C.r64, rc, 1.0 / (C.h * C.h));
+  CCM_CUDA(cudaGetLastError());
+  return CCM_OK;
+}
+
+int ccm_level_prolong(ccm_handle* h, int level, const double* uc, double* u, void* stream) {
+  if (check_level(h, level) || level == (int)h->L.size() - 1 || !u || !uc) return CCM_EINVAL;
+  cudaStream_t s = (cudaStream_t)stream;
+  DevLevel& F = h->L[level];
+  DevLevel& C = h->L[level + 1];
+  load_level<double>(h, F, u, nullptr, s);
+  load_level<double>(h, C, uc, nullptr, s);
+  prolong_from<double>(h, F, C, s);
+  dim3 pg(ceil_div(F.nx, 128), F.ny);
+  dev::k_unpack<double><<<pg, 128, 0, s>>>(F.nx, F.ny, F.pitch, F.cls, U<double>(F), u, 1.0);
+  CCM_CUDA(cudaGetLastError());
+  return CCM_OK;
+}
+
+int ccm_bottom_solve(ccm_handle* h, const double* r, double* u, void* stream) {
+  if (!h || !r || !u) return CCM_EINVAL;
+  cudaStream_t s = (cudaStream_t)stream;
+  DevLevel& B = h->L.back();
+  load_level<double>(h, B, nullptr, r, s);
+  bottom<double>(h, B, s);
+  dim3 pg(ceil_div(B.nx, 128), B.ny);
+  dev::k_unpack<double><<<pg, 128, 0, s>>>(B.nx, B.ny, B.pitch, B.cls, U<double>(B), u, 1.0);
+  CCM_CUDA(cudaGetLastError());
+  return CCM_OK;
+}
+
+int ccm_vcycle(ccm_handle* h, double* u, const double* r, int precision, void* stream) {
+  if (!h || !u || !r) return CCM_EINVAL;
+  cudaStream_t s = (cudaStream_t)stream;
+  DevLevel& L = h->L[0];
+  dim3 pg(ceil_div(L.nx, 128), L.ny);
+  if (precision == CCM_FP64) {
+    load_level<double>(h, L, u, r, s);
+    vcycle<double>(h, 0, s);
+    dev::k_unpack<double><<<pg, 128, 0, s>>>(L.nx, L.ny, L.pitch, L.cls, U<double>(L), u, 1.0);
+  } else {
+    load_level<float>(h, L, u, r, s);
+    vcycle<float>(h, 0, s);
+    dev::k_unpack<float><<<pg, 128, 0, s>>>(L.nx, L.ny, L.pitch, L.cls, U<float>(L), u, 1.0);
+  }
+  CCM_CUDA(cudaGetLastError());
+  return CCM_OK;
+}
+
+void ccm_free(ccm_handle* h) {
+  if (!h) return;
+  cudaDeviceSynchronize();
+  h->arena.release();
+  if (h->hnorm) cudaFreeHost(h->hnorm);
+  delete h;
+}
+
+}  // extern "C"

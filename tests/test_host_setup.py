@@ -1,0 +1,68 @@
+"""The product's host setup (C++, through the C ABI's host-only view) against the oracle:
+identical discrete choices (cells, merges, classification, stencils) and coefficients equal
+to rounding, on every level of the hierarchy.  No GPU needed."""
+import numpy as np
+import pytest
+
+import workloads as W
+from oracle import discretization as D
+from oracle import geometry as G
+from oracle import multigrid as MG
+
+P = pytest.importorskip("paper_2504_00724_gb300")
+
+
+def _compare_level(hs, level, prob_level):
+    cg = G.cut_cells(prob_level)
+    dz = D.discretize(cg, prob_level.a, prob_level.b, prob_level.c)
+    st, ow, rg, vol, mom = hs.cell_map(level)
+    assert np.array_equal(st, cg.status)
+    ne = cg.status != 0
+    assert np.array_equal(ow[ne], cg.owner[ne])
+    assert np.array_equal(rg.astype(bool), dz.regular)
+    assert np.abs(vol - cg.vol).max() < 1e-13
+    for lin, m in cg.mom.items():
+        j, i = divmod(lin, prob_level.nx)
+        assert np.abs(mom[j, i] - m).max() < 1e-12
+    cell, cols, beta, nb, seg = hs.rows(level)
+    lins = sorted(dz.rows.keys())
+    assert list(cell) == lins
+    segs = {int(s): k for k, s in enumerate(dz.segs)}
+    for r, lin in enumerate(lins):
+        row = dz.rows[lin]
+        assert list(cols[r]) == [cj * prob_level.nx + ci for (ci, cj) in row.cells], lin
+        scale = np.abs(row.beta).max()
+        assert np.abs(beta[r] - row.beta).max() <= 1e-9 * scale
+        assert abs(nb[r] - row.beta_b) <= 1e-9 * scale
+        assert seg[r] == segs.get(lin, -1)
+
+
+@pytest.mark.parametrize("mk", [lambda: W.disk_minus(32), lambda: W.star(64),
+                                lambda: W.three_ellipses(64), lambda: W.paper_problem2(32, W.NEUMANN),
+                                lambda: W.star(32, (1.25, -0.8660254037844386, 1.75))])
+def test_finest_level_matches_oracle(mk):
+    prob = mk()
+    hs = P.HostSetup(prob)
+    _compare_level(hs, 0, prob)
+
+
+@pytest.mark.slow
+def test_every_level_matches_oracle():
+    prob = W.star(128)
+    hs = P.HostSetup(prob)
+    nl = MG.n_levels(prob)
+    for m in range(nl):
+        _compare_level(hs, m, MG.coarsen(prob, m))
+
+
+def test_invalid_problems_are_rejected():
+    prob = W.star(64)
+    bad = W.Problem(1.0, 3.0, 1.0, 0.0, 0.0, 1 / 64, 64, 64, W.NONE, prob.curves)   # b^2 - 4ac > 0
+    with pytest.raises(P.CcmError) as e:
+        P.HostSetup(bad)
+    assert e.value.code == -1
+    off = W.Problem(1.0, 0.0, 1.0, 0.0, 0.0, 1 / 64, 64, 64, W.NONE,
+                    [W.Curve(W.CIRCLE, (0.95, 0.5, 0.2), +1, W.DIRICHLET)])            # leaves the box
+    with pytest.raises(P.CcmError) as e:
+        P.HostSetup(off)
+    assert e.value.code == -2
