@@ -1,0 +1,338 @@
+#!/usr/bin/env python
+"""Benchmark: fine-grid unknowns solved per second to a 1e-10 relative residual.
+
+Workload: the interior of the 5-petal star r(t) = 0.3 + 0.08 cos 5t centred at (0.5, 0.5),
+(a, b, c) = (1, 0.5, 2), Dirichlet data and cell averages of f from the manufactured solution
+u = exp(x) sin(pi y) + x^4 (inputs synthetic, computed once before timing).  One step = one
+full solve (V-cycles of Alg. 2 with SMO-1/SMO-2, residual, restriction, prolongation, bottom
+solve, outer FP64 residual) from the resident right-hand side to ||r - L u|| <= rtol ||r||.
+
+value:  mixed form (FP32 cycles in FP64 refinement), inputs resident in HBM, CUDA events.
+e2e:    the same through the C ABI with host buffers, H2D of f, g and D2H of u inside the timing.
+fp64:   the plain FP64 form, same workload and tolerance.
+roofline: the dominant kernel class, timed live with CUDA events during the timed steps.
+cpu_baseline / --impl reference: the CPU oracle (NumPy/SciPy) on a bounded sample of the
+same workload (same domain, coefficients and data at a smaller grid).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import threading
+import time
+
+os.environ.setdefault("OPENBLAS_NUM_THREADS", "1")
+os.environ.setdefault("OMP_NUM_THREADS", "1")
+os.environ.setdefault("MKL_NUM_THREADS", "1")
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+METRIC = "fine-grid unknowns solved/s to 1e-10 rel. residual"
+UNIT = "unknowns/s"
+RTOL = 1e-10
+SM_COUNT = 152
+FP64_FMA_PER_CLK_SM = 2          # FP64 FMA issue rate per SM (4 flop / clk / SM)
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--n", type=int, default=4096)
+    ap.add_argument("--sample-n", type=int, default=256)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-fp64", action="store_true")
+    ap.add_argument("--profile-run", action="store_true",
+                    help="only setup, warm-up and the timed solves (for an ncu launch list)")
+    return ap.parse_args()
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), float(d.get("sm_max_mhz", 2070.0)), "measured"
+    except Exception:
+        return 6800.0, 2070.0, "fallback"
+
+
+class Clocks:
+    """nvidia-smi samples of SM clock and throttle reasons during the timed region."""
+
+    def __init__(self, index: int):
+        self.index = index
+        self.samples = []
+        self.proc = None
+
+    def __enter__(self):
+        q = ("clocks.sm,clocks.max.sm,clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.samples.append([v.strip() for v in line.split(",")])
+
+    def __exit__(self, *a):
+        if self.proc:
+            time.sleep(0.25)
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=2)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        if not self.samples:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        sm = [float(s[0]) for s in self.samples if s[0].replace(".", "").isdigit()]
+        mx = [float(s[1]) for s in self.samples if s[1].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for s in self.samples for k in range(4)
+                          if len(s) > 2 + k and s[2 + k].lower() == "active"})
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(self.samples)}
+
+
+# ------------------------------------------------------------------ CPU oracle leg
+
+def oracle_sample(n: int, steps: int):
+    """Time the oracle's multigrid solve (paper parameters) on the star workload at n x n."""
+    import workloads as W
+    from oracle import cubature as Q
+    from oracle import multigrid as MG
+    prob, mms = W.star(n), W.mms_star()
+    H = MG.build_hierarchy(prob)
+    lv = H.levels[0]
+    fa = Q.cell_averages(lv.cg, mms.f(prob.a, prob.b, prob.c)).ravel()
+    ga = Q.boundary_averages(lv.cg, lv.dz.segs, mms.u, mms.ux, mms.uy)
+    r = fa - lv.dz.N @ ga
+    r[~lv.ne] = 0.0
+    ncell = int(lv.ne.sum())
+    times, iters = [], []
+    for _ in range(steps):
+        hist = []
+        t0 = time.perf_counter()
+        MG.solve(H, r, rtol=RTOL, max_iter=400, history=hist)
+        times.append(time.perf_counter() - t0)
+        iters.append(len(hist) - 1)
+    tot = sum(times)
+    return {"value": ncell * steps / tot, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"star {n}x{n} ({ncell} unknowns), oracle V-cycles (omega 0.5, nu 3) to rtol {RTOL}, "
+                      f"{steps} solve(s), {np.mean(iters):.0f} cycles each, {tot:.1f} s",
+            "seconds": tot}
+
+
+def run_reference(args, rank: int):
+    if rank != 0:
+        return
+    steps = max(1, args.steps)
+    for _ in range(max(0, min(args.warmup, 1))):
+        oracle_sample(args.sample_n, 1)
+    cb = oracle_sample(args.sample_n, steps)
+    line = {"impl": "reference", "metric": METRIC, "value": cb["value"], "unit": UNIT, "n_gpus": args.gpus,
+            "steps": steps, "warmup": args.warmup, "ms_per_step": 1000 * cb["seconds"] / steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": f"star (1,0.5,2) {args.n}x{args.n}, oracle on a "
+                                                       f"{args.sample_n}x{args.sample_n} sample",
+                                            "rtol": RTOL},
+            "cpu_baseline": {k: cb[k] for k in ("value", "unit", "cores", "kind", "sample")},
+            "e2e": {"value": cb["value"], "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ------------------------------------------------------------------ GPU leg
+
+def main():
+    args = parse()
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    if args.impl == "reference":
+        run_reference(args, rank)
+        return
+    import torch
+    import paper_2504_00724_gb300 as P
+    import workloads as W
+
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+
+    prob, mms = W.star(args.n), W.mms_star()
+    t0 = time.time()
+    solver = P.Solver(prob, precision=P.CCM_MIXED, rtol=RTOL, max_iter=200)
+    setup_s = time.time() - t0
+    info = solver.info
+    q = solver.quadrature()
+    fa = solver.cell_averages(mms.f(prob.a, prob.b, prob.c), quad=q)
+    ga = solver.boundary_averages(mms.u, mms.ux, mms.uy, quad=q)
+    ua = solver.cell_averages(mms.u, quad=q)
+    ne = solver.cell_map()[0] != 0
+    f = torch.tensor(fa, dtype=torch.float64, device="cuda")
+    g = torch.tensor(ga, dtype=torch.float64, device="cuda")
+    ncell = int(info.n_cells)
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")   # 256 MB > L2
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    def timed_solves(sv, steps, profile_class=0):
+        per, stats = [], None
+        sv.profile(profile_class)
+        sv.solve(f, g, stream=stream)            # (re)captures the iteration graph, untimed
+        sv.profile(profile_class)                # same class: graphs kept, counters cleared
+        torch.cuda.synchronize()
+        for _ in range(steps):
+            flush.zero_()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            u, st = sv.solve(f, g, stream=stream)
+            e1.record(stream)
+            e1.synchronize()
+            per.append(e0.elapsed_time(e1))
+            stats = (u, st)
+        prof = sv.profile_read() if profile_class else (0.0, 0)
+        return per, stats, prof
+
+    # warm-up (with the profiled class of the timed region, so its graph is captured here)
+    solver.profile(P.binding.CCM_PROF_RESID_FP64)
+    for _ in range(args.warmup):
+        solver.solve(f, g)
+    barrier()
+    launches0 = P.binding.launch_count()
+    clocks = Clocks(local)
+    with clocks:
+        per, (u, st), prof_res = timed_solves(solver, args.steps, P.binding.CCM_PROF_RESID_FP64)
+    launches = P.binding.launch_count() - launches0
+    barrier()
+    ms_step = float(np.mean(per))
+    tot = torch.tensor([sum(per)], dtype=torch.float64, device="cuda")
+    if dist is not None:
+        dist.all_reduce(tot, op=dist.ReduceOp.MAX)
+    value = world * ncell * args.steps / (tot.item() / 1000.0)
+    err = float(np.abs(u.cpu().numpy() - ua)[ne].max())
+    iters = st.iterations
+
+    if args.profile_run:
+        if rank == 0:
+            print(json.dumps({"profile_run": True, "ms_per_step": ms_step, "launches": int(launches)}), flush=True)
+        solver.close()
+        return
+
+    # secondary profiles on extra (untimed for value) solves: SMO-1 FP32 and whole V-cycles
+    _, _, prof_smo = timed_solves(solver, 1, P.binding.CCM_PROF_SMO1_FP32)
+    _, _, prof_vc = timed_solves(solver, 1, P.binding.CCM_PROF_VCYCLE)
+
+    # e2e: host buffers through the C ABI, copies inside the timing
+    fh = torch.tensor(fa, dtype=torch.float64).pin_memory()
+    gh = torch.tensor(ga, dtype=torch.float64).pin_memory()
+    uh = torch.empty_like(fh).pin_memory()
+    fd, gd = torch.empty_like(f), torch.empty_like(g)
+    e2e = []
+    for _ in range(max(1, args.steps)):
+        flush.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        fd.copy_(fh, non_blocking=True)
+        gd.copy_(gh, non_blocking=True)
+        ud, _ = solver.solve(fd, gd, stream=stream)
+        uh.copy_(ud, non_blocking=True)
+        e1.record(stream)
+        e1.synchronize()
+        e2e.append(e0.elapsed_time(e1))
+    e2e_value = world * ncell / (float(np.mean(e2e)) / 1000.0)
+
+    # plain FP64 form, same workload and tolerance
+    fp64 = None
+    if not args.no_fp64:
+        s64 = P.Solver(prob, precision=P.CCM_FP64, rtol=RTOL, max_iter=200)
+        s64.solve(f, g)
+        per64, (u64, st64), _ = timed_solves(s64, max(1, min(args.steps, 2)))
+        err64 = float(np.abs(u64.cpu().numpy() - ua)[ne].max())
+        fp64 = {"value": ncell / (float(np.mean(per64)) / 1000.0), "ms_per_step": float(np.mean(per64)),
+                "iterations": st64.iterations, "rel_residual": st64.rel_residual, "max_error": err64}
+        s64.close()
+
+    # roofline of the dominant kernel class (largest total time per step)
+    hbm, sm_max, src = peaks()
+    clk = clocks.summary()
+    n_reg = int(info.n_regular)
+    taps = 25 if prob.b != 0 else 9
+    classes = []
+    ms, nl = prof_res
+    if nl:
+        flop = n_reg * 2.0 * (taps + 1)
+        classes.append(("fp64 residual (regular cells, level 0)", ms / args.steps, ms / nl, nl / args.steps,
+                        "alu", flop, "TFLOP/s"))
+    ms2, nl2 = prof_smo
+    if nl2:
+        byts = ncell * 13.0        # read u, r (4 B each), class (1 B); write u (4 B)
+        classes.append(("fp32 SMO-1 sweep (level 0)", ms2, ms2 / nl2, nl2, "hbm", byts, "GB/s"))
+    classes.sort(key=lambda c: -c[1])
+    roof = None
+    if classes:
+        name, ms_step_cls, avg_ms, per_step, bound, work, unit = classes[0]
+        if bound == "alu":
+            peak = SM_COUNT * FP64_FMA_PER_CLK_SM * 2 * sm_max * 1e6 / 1e12
+            achieved = work / (avg_ms / 1000.0) / 1e12
+        else:
+            peak = hbm
+            achieved = work / (avg_ms / 1000.0) / 1e9
+        roof = {"bound": bound, "achieved": achieved, "peak": peak, "unit": unit, "frac": achieved / peak,
+                "traffic": None, "kernel": name, "avg_launch_us": avg_ms * 1000.0,
+                "launches_per_step": per_step,
+                "peak_source": ("derived: 152 SMs x 4 FP64 flop/clk x max SM clock" if bound == "alu"
+                                else f"{src} copy bandwidth"),
+                "others": [{"kernel": c[0], "ms_per_step": c[1], "avg_launch_us": c[2] * 1000.0} for c in classes[1:]]}
+
+    cpu = None
+    if not args.no_cpu_baseline and rank == 0 and world == 1:
+        cpu = oracle_sample(args.sample_n, 1)
+        cpu = {k: cpu[k] for k in ("value", "unit", "cores", "kind", "sample")}
+
+    vc_ms, vc_n = prof_vc
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64+f32", "data": "synthetic",
+            "config": {"workload": f"star r=0.3+0.08cos5t, (a,b,c)=(1,0.5,2), {args.n}x{args.n} cells, Dirichlet, "
+                                   f"u=exp(x)sin(pi y)+x^4", "unknowns": ncell, "irregular": int(info.n_irregular),
+                       "levels": int(info.levels), "rtol": RTOL, "precision": "FP32 V-cycles in FP64 refinement",
+                       "l2": "flushed (256 MB write) before every step", "parallelism": f"replicas x{world}"},
+            "iterations": iters, "rel_residual": st.rel_residual, "max_error_vs_exact": err,
+            "vcycle_ms": (vc_ms / vc_n) if vc_n else None, "setup_s": setup_s,
+            "fp64": fp64, "mixed_over_fp64": (value / world / fp64["value"]) if fp64 else None,
+            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(fh.numel() * 8 + gh.numel() * 8),
+                    "d2h_bytes_per_step": int(uh.numel() * 8), "ms_per_step": float(np.mean(e2e))},
+            "gpu_launches": int(launches), "roofline": roof, "cpu_baseline": cpu, "clocks": clk}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    solver.close()
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

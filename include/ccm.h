@@ -86,6 +86,8 @@ typedef struct {
   int ras_block;     /* core size of an SMO-2 block (unknowns) */
   int ras_overlap;   /* overlap of an SMO-2 block on each side (unknowns) */
   int nthreads;      /* host threads for ccm_setup (0 = all cores) */
+  int ras_exact;     /* levels with at most this many irregular cells use one exact block */
+  int inner_cycles;  /* CCM_MIXED: FP32 V-cycles per FP64 residual evaluation */
 } ccm_params;
 
 typedef struct {
@@ -108,7 +110,8 @@ typedef struct {
 typedef struct ccm_handle ccm_handle;
 
 /* Fill p with the defaults: omega 0.8, nu1 = nu2 = 3, theta 0.3, coarsest 16, CCM_MIXED,
- * rtol 1e-10, max_iter 100, ras_passes 1, ras_block 64, ras_overlap 32, nthreads 0. */
+ * rtol 1e-10, max_iter 100, ras_passes 1, ras_block 64, ras_overlap 32, nthreads 0,
+ * ras_exact 1024, inner_cycles 3. */
 int ccm_default_params(ccm_params* p);
 
 /* Host setup (Sec. 3.1 - 3.4, Sec. 4): cut cells and moments (Green's formula, Sec. 2.4),
@@ -157,11 +160,15 @@ int ccm_apply(ccm_handle* h, const double* u, const double* g, double* out, int 
  * regular stencil on regular rows and a precomputed transposed CSR of the fitted rows. */
 int ccm_apply_T(ccm_handle* h, const double* v, double* out_u, double* out_g, int nrhs, void* stream);
 
-/* Solve L u = f - N g (eq. PoissonResidualForm) by V-cycles (Alg. 2) to rtol.
+/* Solve L u = f - N g (eq. PoissonResidualForm) by V-cycles (Alg. 2) to rtol.  One outer
+ * iteration (CCM_FP64: one FP64 V-cycle; CCM_MIXED: inner_cycles FP32 V-cycles on the FP32
+ * image of the FP64 residual, then u += e in FP64) runs as one CUDA graph, captured on the
+ * first call; the FP64 residual norm is read back after every outer iteration.
  * f: device [nrhs][ny][nx] cell averages; g: device [nrhs][n_segments] (NULL: g = 0);
  * u: device [nrhs][ny][nx], in: initial guess, out: solution.  stats (host, nullable)
- * receives the iteration count and residual history of the last right-hand side.
- * Synchronises the stream once per outer iteration (the convergence test).
+ * receives the outer iteration count and residual history of the last right-hand side.
+ * Synchronises the stream once per outer iteration (the convergence test).  The first call
+ * captures the graphs, so make it outside any caller's stream capture.
  * Errors: CCM_ENOCONV (u holds the last iterate), CCM_ENOTFINITE, CCM_ECUDA. */
 int ccm_solve(ccm_handle* h, const double* f, const double* g, double* u, int nrhs,
               void* stream, ccm_stats* stats);
@@ -190,6 +197,20 @@ int ccm_level_prolong(ccm_handle* h, int level, const double* uc, double* u, voi
 int ccm_bottom_solve(ccm_handle* h, const double* r, double* u, void* stream);
 /* One V-cycle (Alg. 2) on level 0 for L u = r (physical units, FP64 in and out). */
 int ccm_vcycle(ccm_handle* h, double* u, const double* r, int precision, void* stream);
+
+/* ---- accounting and profiling (not part of the method).
+ * ccm_launch_count: kernels launched by this library in this process so far (all handles).
+ * ccm_profile: record CUDA events on the handle's stream around every launch of one class:
+ *   CCM_PROF_RESID_FP64  level-0 FP64 residual of the regular cells (outer iteration),
+ *   CCM_PROF_SMO1_FP32   level-0 SMO-1 sweep in FP32, CCM_PROF_SMO1_FP64 the same in FP64,
+ *   CCM_PROF_VCYCLE      one whole V-cycle; 0 switches profiling off.
+ * ccm_profile_read: total device time (ms) and launch count recorded since the last read;
+ * waits for the recorded events. */
+enum { CCM_PROF_OFF = 0, CCM_PROF_RESID_FP64 = 1, CCM_PROF_SMO1_FP32 = 2, CCM_PROF_SMO1_FP64 = 3,
+       CCM_PROF_VCYCLE = 4 };
+int64_t ccm_launch_count(void);
+int ccm_profile(ccm_handle* h, int kernel_class);
+int ccm_profile_read(ccm_handle* h, double* ms, int64_t* launches);
 
 /* ---- host-only view of the setup (no device memory is touched; usable without a GPU).
  * ccm_host_build runs the same host setup as ccm_setup and keeps the result on the host so

@@ -14,6 +14,7 @@ LIBPATH = os.path.join(HERE, "libccm.so")
 CCM_CIRCLE, CCM_ELLIPSE, CCM_STAR = 1, 2, 3
 CCM_NONE, CCM_DIRICHLET, CCM_NEUMANN = 0, 1, 2
 CCM_FP64, CCM_MIXED = 0, 1
+CCM_PROF_OFF, CCM_PROF_RESID_FP64, CCM_PROF_SMO1_FP32, CCM_PROF_SMO1_FP64, CCM_PROF_VCYCLE = 0, 1, 2, 3, 4
 
 
 class CcmError(RuntimeError):
@@ -38,7 +39,8 @@ class ccm_params(ctypes.Structure):
     _fields_ = [("omega", ctypes.c_double), ("nu1", ctypes.c_int), ("nu2", ctypes.c_int),
                 ("theta", ctypes.c_double), ("coarsest", ctypes.c_int), ("precision", ctypes.c_int),
                 ("rtol", ctypes.c_double), ("max_iter", ctypes.c_int), ("ras_passes", ctypes.c_int),
-                ("ras_block", ctypes.c_int), ("ras_overlap", ctypes.c_int), ("nthreads", ctypes.c_int)]
+                ("ras_block", ctypes.c_int), ("ras_overlap", ctypes.c_int), ("nthreads", ctypes.c_int),
+                ("ras_exact", ctypes.c_int), ("inner_cycles", ctypes.c_int)]
 
 
 class ccm_info(ctypes.Structure):
@@ -84,6 +86,9 @@ _SIGS = {
     "ccm_host_rows": (I, [P, I, P, P, P, P, P]),
     "ccm_host_cell_map": (I, [P, I, P, P, P, P, P]),
     "ccm_host_free": (None, [P]),
+    "ccm_launch_count": (ctypes.c_int64, []),
+    "ccm_profile": (I, [P, I]),
+    "ccm_profile_read": (I, [P, ctypes.POINTER(ctypes.c_double), I64P]),
 }
 
 
@@ -105,6 +110,11 @@ def load_library(path: str = LIBPATH) -> ctypes.CDLL:
 
 def lib() -> ctypes.CDLL:
     return load_library()
+
+
+def launch_count() -> int:
+    """Kernels launched by libccm.so in this process so far."""
+    return int(lib().ccm_launch_count())
 
 
 def _check(rc: int, what: str):
@@ -274,6 +284,15 @@ class Solver:
         u = u.clone()
         _check(lib().ccm_vcycle(self.h, _ptr(u), _ptr(r), precision, _stream(stream)), "ccm_vcycle")
         return u
+
+    # ---- accounting
+    def profile(self, kernel_class: int):
+        _check(lib().ccm_profile(self.h, kernel_class), "ccm_profile")
+
+    def profile_read(self):
+        ms, n = ctypes.c_double(0), ctypes.c_int64(0)
+        _check(lib().ccm_profile_read(self.h, ctypes.byref(ms), ctypes.byref(n)), "ccm_profile_read")
+        return ms.value, n.value
 
     # ---- caller-side helpers (input preparation, not part of the solve)
     def cell_averages(self, fn, quad=None) -> np.ndarray:

@@ -164,7 +164,7 @@ static int pack_level(const CutLevel& cg, const Rows& rows, const ccm_params& pa
   L.rows = cg.ny + 4;
   const long np = L.npad();
   L.cls.assign(np, 0);
-  L.vol.assign(np, 0.0f);
+  L.vol.assign(np, 0.0);
   L.owner = cg.owner;
   L.status = cg.status;
   for (int j = 0; j < cg.ny; ++j)
@@ -172,7 +172,7 @@ static int pack_level(const CutLevel& cg, const Rows& rows, const ccm_params& pa
       long q = (long)j * cg.nx + i;
       if (cg.status[q] == ST_EMPTY) continue;
       L.cls[L.pad(i, j)] = rows.regular[q] ? 1 : 2;
-      L.vol[L.pad(i, j)] = (float)cg.vol[q];
+      L.vol[L.pad(i, j)] = cg.vol[q];
     }
   // active 32 x 8 tiles (any non-empty cell)
   const int tx = (cg.nx + 31) / 32, ty = (cg.ny + 7) / 8;
@@ -264,7 +264,9 @@ static int pack_level(const CutLevel& cg, const Rows& rows, const ccm_params& pa
     L.order.assign(order.begin(), order.end());
     std::vector<int> pos(n2);
     for (int p = 0; p < n2; ++p) pos[order[p]] = p;
-    const int m = std::max(8, par.ras_block), dl = std::max(0, par.ras_overlap);
+    // one exact block when the level is small, else overlapping blocks of the order
+    const bool exact = n2 <= par.ras_exact;
+    const int m = exact ? n2 : std::max(8, par.ras_block), dl = exact ? 0 : std::max(0, par.ras_overlap);
     const int nblk = (n2 + m - 1) / m;
     L.blk.resize(4L * nblk);
     L.blk_off.resize(nblk);

@@ -18,7 +18,7 @@ struct HostLevel {
   long pad(int i, int j) const { return (long)(j + 2) * pitch + (i + 2); }
 
   std::vector<uint8_t> cls;     // [npad] 0 empty / ring, 1 regular, 2 irregular
-  std::vector<float> vol;       // [npad] cell volume in units of h^2 (0 if empty)
+  std::vector<double> vol;      // [npad] cell volume in units of h^2 (0 if empty)
   std::vector<int32_t> tiles;   // active 32 x 8 tiles (tile x, tile y) pairs
 
   // fitted rows, ELL with 15 slots: [slot][n2]

@@ -104,40 +104,149 @@ __global__ void k_rows(int n2, const int32_t* __restrict__ cell, const int32_t* 
 
 // SMO-2 (Sec. 4.1) as one pass of overlapping block solves: for every block, the core
 // unknowns get inv(L22[ext, ext])[core, :] applied to the residuals of the extended block.
+// Grid (block, chunk of 32 core rows); the 4 warps of a CTA split the extended range.
 template <typename T>
 __global__ void k_block_solve(const int32_t* __restrict__ order, const int32_t* __restrict__ blk,
                               const int64_t* __restrict__ blk_off, const T* __restrict__ inv,
                               const T* __restrict__ res2, const int32_t* __restrict__ cell, T* __restrict__ u) {
   extern __shared__ unsigned char smem_raw[];
   T* s = reinterpret_cast<T*>(smem_raw);
+  __shared__ T part[4][32];
   const int b = blockIdx.x;
   const int cs = blk[4 * b], ce = blk[4 * b + 1], es = blk[4 * b + 2], ee = blk[4 * b + 3];
   const int ne = ee - es, nc = ce - cs;
+  const int c0 = blockIdx.y * 32;
+  if (c0 >= nc) return;
   for (int e = threadIdx.x; e < ne; e += blockDim.x) s[e] = res2[order[es + e]];
   __syncthreads();
   const T* A = inv + blk_off[b];
-  for (int c = threadIdx.x; c < nc; c += blockDim.x) {
-    T acc = 0;
-    for (int e = 0; e < ne; ++e) acc += A[(long)e * nc + c] * s[e];
-    long q = cell[order[cs + c]];
-    u[q] += acc;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int c = c0 + lane;
+  T acc = 0;
+  if (c < nc)
+    for (int e = warp; e < ne; e += 4) acc += A[(long)e * nc + c] * s[e];
+  part[warp][lane] = acc;
+  __syncthreads();
+  if (warp == 0 && c < nc) {
+    T tot = part[0][lane] + part[1][lane] + part[2][lane] + part[3][lane];
+    u[cell[order[cs + c]]] += tot;
   }
 }
 
-// residual restriction (Sec. 4.1), h^2-scaled: rc = 4 sum(vol t) / sum(vol) over the children
+// SMO-1 with the prolongation fused in (first post-smoothing sweep after Alg. 2's
+// "Prolong the correction"): v = u + P uc on regular cells, then u_out = v + omega D^-1 (r - L v)
+// on regular cells.  Irregular cells are left to the SMO-2 kernel that follows.
+template <typename T, bool CROSS, bool PROLONG>
+__global__ void k_jacobi2(const int32_t* __restrict__ tiles, const uint8_t* __restrict__ cls, int nx, int ny,
+                          int pitch, int pitchc, const T* __restrict__ u_in, const T* __restrict__ uc,
+                          T* __restrict__ u_out, const T* __restrict__ r, Stencil<T> S) {
+  int i, j;
+  long p;
+  if (!tile_cell(tiles, nx, ny, pitch, i, j, p)) return;
+  if (cls[p] != 1) return;
+  T acc = 0;
+  T vp = 0;
+#pragma unroll
+  for (int dj = -2; dj <= 2; ++dj)
+#pragma unroll
+    for (int di = -2; di <= 2; ++di) {
+      if (!CROSS && dj != 0 && di != 0) continue;
+      long q = p + (long)dj * pitch + di;
+      T v = u_in[q];
+      if (PROLONG && cls[q] == 1) v += uc[(long)((j + dj) / 2 + 2) * pitchc + ((i + di) / 2 + 2)];
+      acc += S.w[(dj + 2) * 5 + di + 2] * v;
+      if (dj == 0 && di == 0) vp = v;
+    }
+  u_out[p] = vp + S.omega_d * (r[p] - acc);
+}
+
+// SMO-2 fused with the residual of the fitted rows: the residual of row e uses the new
+// regular values (u_new, written by SMO-1) and the old irregular values (u_old); the core
+// rows of the block then get u_new = u_old + inv(L22[ext, ext])[core, :] res[ext].  Every
+// irregular cell is the core of exactly one block, and no kernel writes what it reads.
 template <typename T>
-__global__ void k_restrict(int nxc, int nyc, int pitchc, int pitchf, const uint8_t* __restrict__ clsc,
-                           const float* __restrict__ volf, const T* __restrict__ t, T* __restrict__ rc) {
+__global__ void k_block_fused(const int32_t* __restrict__ order, const int32_t* __restrict__ blk,
+                              const int64_t* __restrict__ blk_off, const T* __restrict__ inv,
+                              int n2, const int32_t* __restrict__ cell, const int32_t* __restrict__ col,
+                              const T* __restrict__ val, const uint8_t* __restrict__ cls,
+                              const T* __restrict__ r, const T* __restrict__ u_old, T* __restrict__ u_new) {
+  extern __shared__ unsigned char smem_raw[];
+  T* s = reinterpret_cast<T*>(smem_raw);
+  __shared__ T part[4][32];
+  const int b = blockIdx.x;
+  const int cs = blk[4 * b], ce = blk[4 * b + 1], es = blk[4 * b + 2], ee = blk[4 * b + 3];
+  const int ne = ee - es, nc = ce - cs;
+  const int c0 = blockIdx.y * 32;
+  if (c0 >= nc) return;
+  for (int e = threadIdx.x; e < ne; e += blockDim.x) {
+    int row = order[es + e];
+    T acc = 0;
+#pragma unroll
+    for (int k = 0; k < 15; ++k) {
+      int q = col[(long)k * n2 + row];
+      T v = cls[q] == 1 ? u_new[q] : u_old[q];
+      acc += val[(long)k * n2 + row] * v;
+    }
+    s[e] = r[cell[row]] - acc;
+  }
+  __syncthreads();
+  const T* A = inv + blk_off[b];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int c = c0 + lane;
+  T acc = 0;
+  if (c < nc)
+    for (int e = warp; e < ne; e += 4) acc += A[(long)e * nc + c] * s[e];
+  part[warp][lane] = acc;
+  __syncthreads();
+  if (warp == 0 && c < nc) {
+    long q = cell[order[cs + c]];
+    u_new[q] = u_old[q] + part[0][lane] + part[1][lane] + part[2][lane] + part[3][lane];
+  }
+}
+
+// residual + restriction + zeroing of the coarse iterate (Alg. 2 "compute the coarse
+// residual by restriction" and "u^(m+1) = 0"): regular children's residuals are computed
+// here, irregular children's are read from t (written by k_rows).
+template <typename T, bool CROSS>
+__global__ void k_restrict_fused(int nxc, int nyc, int pitchc, int pitchf, const uint8_t* __restrict__ clsc,
+                                 const uint8_t* __restrict__ clsf, const T* __restrict__ volf,
+                                 const T* __restrict__ u, const T* __restrict__ r, const T* __restrict__ t,
+                                 T* __restrict__ rc, T* __restrict__ uc, Stencil<T> S) {
   int I = blockIdx.x * blockDim.x + threadIdx.x;
   int J = blockIdx.y * blockDim.y + threadIdx.y;
   if (I >= nxc || J >= nyc) return;
   long pc = (long)(J + 2) * pitchc + (I + 2);
   if (clsc[pc] == 0) return;
   long f0 = (long)(2 * J + 2) * pitchf + (2 * I + 2);
-  float v0 = volf[f0], v1 = volf[f0 + 1], v2 = volf[f0 + pitchf], v3 = volf[f0 + pitchf + 1];
-  T s = (T)v0 * t[f0] + (T)v1 * t[f0 + 1] + (T)v2 * t[f0 + pitchf] + (T)v3 * t[f0 + pitchf + 1];
-  float sv = v0 + v1 + v2 + v3;
-  rc[pc] = sv > 0.f ? (T)4 * s / (T)sv : (T)0;
+  T s = 0, sv = 0;
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    long q = f0 + (k >> 1) * (long)pitchf + (k & 1);
+    uint8_t c = clsf[q];
+    if (c == 0) continue;
+    T res = c == 1 ? r[q] - stencil_apply<T, CROSS>(u, q, pitchf, S) : t[q];
+    T v = volf[q];
+    s += v * res;
+    sv += v;
+  }
+  rc[pc] = sv > (T)0 ? (T)4 * s / sv : (T)0;
+  uc[pc] = (T)0;
+}
+
+// residual restriction (Sec. 4.1), h^2-scaled: rc = 4 sum(vol t) / sum(vol) over the children
+template <typename T>
+__global__ void k_restrict(int nxc, int nyc, int pitchc, int pitchf, const uint8_t* __restrict__ clsc,
+                           const T* __restrict__ volf, const T* __restrict__ t, T* __restrict__ rc) {
+  int I = blockIdx.x * blockDim.x + threadIdx.x;
+  int J = blockIdx.y * blockDim.y + threadIdx.y;
+  if (I >= nxc || J >= nyc) return;
+  long pc = (long)(J + 2) * pitchc + (I + 2);
+  if (clsc[pc] == 0) return;
+  long f0 = (long)(2 * J + 2) * pitchf + (2 * I + 2);
+  T v0 = volf[f0], v1 = volf[f0 + 1], v2 = volf[f0 + pitchf], v3 = volf[f0 + pitchf + 1];
+  T s = v0 * t[f0] + v1 * t[f0 + 1] + v2 * t[f0 + pitchf] + v3 * t[f0 + pitchf + 1];
+  T sv = v0 + v1 + v2 + v3;
+  rc[pc] = sv > (T)0 ? (T)4 * s / sv : (T)0;
 }
 
 // prolongation (Sec. 4.1): u += uc[parent] on fine regular cells

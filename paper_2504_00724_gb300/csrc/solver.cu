@@ -2,6 +2,7 @@
 // outer iteration (plain FP64 cycles, or FP32 cycles inside FP64 iterative refinement),
 // and the C ABI of include/ccm.h.
 #include <algorithm>
+#include <atomic>
 #include <chrono>
 #include <cmath>
 #include <cstring>
@@ -22,10 +23,11 @@ struct DevLevel {
   int nx = 0, ny = 0, pitch = 0, rows = 0, ntiles = 0, n2 = 0, nblk = 0, nbc = 0, ncolT = 0;
   long npad = 0;
   double h = 0;
-  int max_ext = 0;
+  int max_ext = 0, max_core = 0;
   int32_t* tiles = nullptr;
   uint8_t* cls = nullptr;
-  float* vol = nullptr;
+  double* vol64 = nullptr;
+  float* vol32 = nullptr;
   int32_t *irr_cell = nullptr, *ell_col = nullptr, *seg = nullptr;
   double *ell64 = nullptr, *nb = nullptr;
   float* ell32 = nullptr;
@@ -68,6 +70,9 @@ template <> const float* Ell<float>(const DevLevel& L) { return L.ell32; }
 template <typename T> const T* Inv(const DevLevel& L);
 template <> const double* Inv<double>(const DevLevel& L) { return L.inv64; }
 template <> const float* Inv<float>(const DevLevel& L) { return L.inv32; }
+template <typename T> const T* Vol(const DevLevel& L);
+template <> const double* Vol<double>(const DevLevel& L) { return L.vol64; }
+template <> const float* Vol<float>(const DevLevel& L) { return L.vol32; }
 template <typename T> const T* Bot(const DevLevel& L);
 template <> const double* Bot<double>(const DevLevel& L) { return L.bot64; }
 template <> const float* Bot<float>(const DevLevel& L) { return L.bot32; }
@@ -116,11 +121,72 @@ struct ccm_handle {
   unsigned long long* hnorm = nullptr;   // pinned
   ccm_info info{};
   int device = 0;
+  // kernel-class profiling (ccm_profile): event pairs around the chosen class of launches
+  int prof_class = 0;
+  std::vector<cudaEvent_t> prof_ev;   // stream-mode pairs (read at ccm_profile_read)
+  int prof_used = 0;
+  std::vector<cudaEvent_t> gprof_ev;  // pairs baked into the iteration graphs
+  double prof_ms = 0;                 // accumulated from graph replays
+  long long prof_n = 0;
+  // one CUDA graph per outer iteration and precision (captured on first use, on a private
+  // stream: the legacy default stream cannot be captured)
+  cudaStream_t cap_stream = nullptr;
+  bool capturing = false;
+  long long cap_launches = 0;
+  struct Graph {
+    cudaGraphExec_t exec = nullptr;
+    long long launches = 0;
+    std::vector<int> prof_pairs;      // indices into gprof_ev (pairs at 2k, 2k + 1)
+    double* u0 = nullptr;             // the level-0 FP64 iterate the graph updates
+  } graph[2];
 };
 
 namespace {
 
 inline int ceil_div(long a, long b) { return (int)((a + b - 1) / b); }
+
+std::atomic<long long> g_launches{0};
+// every kernel launch of the library goes through KL so that launches can be counted
+#define KL(...) (g_launches.fetch_add(1, std::memory_order_relaxed), __VA_ARGS__)
+
+// event pair around the launches of the profiled class
+struct ProfScope {
+  ccm_handle* H;
+  cudaStream_t s;
+  bool on;
+  int gidx = -1;
+  ProfScope(ccm_handle* H_, int cls, cudaStream_t s_) : H(H_), s(s_), on(cls != 0 && H_->prof_class == cls) {
+    if (!on) return;
+    if (H->capturing) {
+      cudaEvent_t a, b;
+      cudaEventCreate(&a);
+      cudaEventCreate(&b);
+      gidx = (int)H->gprof_ev.size();
+      H->gprof_ev.push_back(a);
+      H->gprof_ev.push_back(b);
+      cudaEventRecordWithFlags(a, s, cudaEventRecordExternal);   // a real record node in the graph
+      return;
+    }
+    if (H->prof_used + 2 > (int)H->prof_ev.size()) {
+      for (int k = 0; k < 512; ++k) {
+        cudaEvent_t e;
+        cudaEventCreate(&e);
+        H->prof_ev.push_back(e);
+      }
+    }
+    cudaEventRecord(H->prof_ev[H->prof_used], s);
+  }
+  ~ProfScope() {
+    if (!on) return;
+    if (gidx >= 0) {
+      cudaEventRecordWithFlags(H->gprof_ev[gidx + 1], s, cudaEventRecordExternal);
+      return;
+    }
+    cudaEventRecord(H->prof_ev[H->prof_used + 1], s);
+    H->prof_used += 2;
+  }
+};
+
 
 #define CCM_CUDA(call)                                  \
   do {                                                  \
@@ -144,11 +210,11 @@ void launch_regular(ccm_handle* H, DevLevel& L, const T* u, const T* r, T* out, 
   dim3 blk(dev::TX, dev::TY);
   const auto& S = stencil<T>(H);
   if (H->cross) {
-    if (resid) dev::k_regular<T, true, true><<<L.ntiles, blk, 0, s>>>(L.tiles, L.cls, L.nx, L.ny, L.pitch, u, r, out, S);
-    else dev::k_regular<T, true, false><<<L.ntiles, blk, 0, s>>>(L.tiles, L.cls, L.nx, L.ny, L.pitch, u, r, out, S);
+    if (resid) KL(dev::k_regular<T, true, true><<<L.ntiles, blk, 0, s>>>(L.tiles, L.cls, L.nx, L.ny, L.pitch, u, r, out, S));
+    else KL(dev::k_regular<T, true, false><<<L.ntiles, blk, 0, s>>>(L.tiles, L.cls, L.nx, L.ny, L.pitch, u, r, out, S));
   } else {
-    if (resid) dev::k_regular<T, false, true><<<L.ntiles, blk, 0, s>>>(L.tiles, L.cls, L.nx, L.ny, L.pitch, u, r, out, S);
-    else dev::k_regular<T, false, false><<<L.ntiles, blk, 0, s>>>(L.tiles, L.cls, L.nx, L.ny, L.pitch, u, r, out, S);
+    if (resid) KL(dev::k_regular<T, false, true><<<L.ntiles, blk, 0, s>>>(L.tiles, L.cls, L.nx, L.ny, L.pitch, u, r, out, S));
+    else KL(dev::k_regular<T, false, false><<<L.ntiles, blk, 0, s>>>(L.tiles, L.cls, L.nx, L.ny, L.pitch, u, r, out, S));
   }
 }
 
@@ -157,52 +223,73 @@ template <typename T>
 void residual(ccm_handle* H, DevLevel& L, const T* u, const T* r, T* out, cudaStream_t s) {
   launch_regular<T>(H, L, u, r, out, true, s);
   if (L.n2)
-    dev::k_rows<T, T, true, true><<<ceil_div(L.n2, 128), 128, 0, s>>>(L.n2, L.irr_cell, L.ell_col, Ell<T>(L), u, r, out,
-                                                                      nullptr, nullptr, nullptr);
+    KL(dev::k_rows<T, T, true, true><<<ceil_div(L.n2, 128), 128, 0, s>>>(L.n2, L.irr_cell, L.ell_col, Ell<T>(L), u, r, out,
+                                                                      nullptr, nullptr, nullptr));
 }
 
-// one smoother step: SMO-1 on the regular cells, then SMO-2 on the irregular cells
+// one smoother step: SMO-1 on the regular cells, then SMO-2 on the irregular cells.
+// uc != nullptr fuses the prolongation u += P uc into the SMO-1 sweep (regular cells).
 template <typename T>
-void smooth_step(ccm_handle* H, DevLevel& L, cudaStream_t s) {
+void smooth_step(ccm_handle* H, DevLevel& L, cudaStream_t s, const T* uc = nullptr, int pitchc = 0) {
   T* uin = U<T>(L);
   T* uout = Uother<T>(L);
   const T* r = R<T>(L);
   if (L.ntiles) {
     dim3 blk(dev::TX, dev::TY);
     const auto& S = stencil<T>(H);
-    if (H->cross) dev::k_jacobi<T, true><<<L.ntiles, blk, 0, s>>>(L.tiles, L.cls, L.nx, L.ny, L.pitch, uin, uout, r, S);
-    else dev::k_jacobi<T, false><<<L.ntiles, blk, 0, s>>>(L.tiles, L.cls, L.nx, L.ny, L.pitch, uin, uout, r, S);
+    ProfScope ps(H, (&L == &H->L[0]) ? (sizeof(T) == 4 ? CCM_PROF_SMO1_FP32 : CCM_PROF_SMO1_FP64) : 0, s);
+    if (uc) {
+      if (H->cross) KL(dev::k_jacobi2<T, true, true><<<L.ntiles, blk, 0, s>>>(L.tiles, L.cls, L.nx, L.ny, L.pitch, pitchc, uin, uc, uout, r, S));
+      else KL(dev::k_jacobi2<T, false, true><<<L.ntiles, blk, 0, s>>>(L.tiles, L.cls, L.nx, L.ny, L.pitch, pitchc, uin, uc, uout, r, S));
+    } else {
+      if (H->cross) KL(dev::k_jacobi2<T, true, false><<<L.ntiles, blk, 0, s>>>(L.tiles, L.cls, L.nx, L.ny, L.pitch, 0, uin, nullptr, uout, r, S));
+      else KL(dev::k_jacobi2<T, false, false><<<L.ntiles, blk, 0, s>>>(L.tiles, L.cls, L.nx, L.ny, L.pitch, 0, uin, nullptr, uout, r, S));
+    }
+  }
+  if (L.n2) {
+    dim3 grd(L.nblk, ceil_div(L.max_core, 32));
+    KL(dev::k_block_fused<T><<<grd, 128, L.max_ext * sizeof(T), s>>>(L.order, L.blk, L.blk_off, Inv<T>(L), L.n2,
+                                                                  L.irr_cell, L.ell_col, Ell<T>(L), L.cls, r, uin, uout));
   }
   flip<T>(L);
   T* u = U<T>(L);
-  if (L.n2 == 0) return;
-  for (int pass = 0; pass < H->par.ras_passes; ++pass) {
-    dev::k_rows<T, T, true, false><<<ceil_div(L.n2, 128), 128, 0, s>>>(L.n2, L.irr_cell, L.ell_col, Ell<T>(L), u, r,
-                                                                       Res<T>(L), nullptr, nullptr, nullptr);
-    dev::k_block_solve<T><<<L.nblk, 128, L.max_ext * sizeof(T), s>>>(L.order, L.blk, L.blk_off, Inv<T>(L), Res<T>(L),
-                                                                     L.irr_cell, u);
+  for (int pass = 1; pass < H->par.ras_passes && L.n2; ++pass) {
+    KL(dev::k_rows<T, T, true, false><<<ceil_div(L.n2, 128), 128, 0, s>>>(L.n2, L.irr_cell, L.ell_col, Ell<T>(L), u, r,
+                                                                       Res<T>(L), nullptr, nullptr, nullptr));
+    dim3 grd(L.nblk, ceil_div(L.max_core, 32));
+    KL(dev::k_block_solve<T><<<grd, 128, L.max_ext * sizeof(T), s>>>(L.order, L.blk, L.blk_off, Inv<T>(L), Res<T>(L),
+                                                                  L.irr_cell, u));
   }
 }
 
+// residual, restriction and zeroing of the coarse iterate
 template <typename T>
 void restrict_to(ccm_handle* H, DevLevel& F, DevLevel& C, cudaStream_t s) {
-  residual<T>(H, F, U<T>(F), R<T>(F), Tmp<T>(F), s);
+  if (F.n2)
+    KL(dev::k_rows<T, T, true, true><<<ceil_div(F.n2, 128), 128, 0, s>>>(F.n2, F.irr_cell, F.ell_col, Ell<T>(F), U<T>(F),
+                                                                      R<T>(F), Tmp<T>(F), nullptr, nullptr, nullptr));
   dim3 blk(32, 8), grd(ceil_div(C.nx, 32), ceil_div(C.ny, 8));
-  dev::k_restrict<T><<<grd, blk, 0, s>>>(C.nx, C.ny, C.pitch, F.pitch, C.cls, F.vol, Tmp<T>(F), R<T>(C));
+  const auto& S = stencil<T>(H);
+  if (H->cross)
+    KL(dev::k_restrict_fused<T, true><<<grd, blk, 0, s>>>(C.nx, C.ny, C.pitch, F.pitch, C.cls, F.cls, Vol<T>(F), U<T>(F),
+                                                        R<T>(F), Tmp<T>(F), R<T>(C), U<T>(C), S));
+  else
+    KL(dev::k_restrict_fused<T, false><<<grd, blk, 0, s>>>(C.nx, C.ny, C.pitch, F.pitch, C.cls, F.cls, Vol<T>(F), U<T>(F),
+                                                         R<T>(F), Tmp<T>(F), R<T>(C), U<T>(C), S));
 }
 
 template <typename T>
 void prolong_from(ccm_handle* H, DevLevel& F, DevLevel& C, cudaStream_t s) {
   if (F.ntiles == 0) return;
   dim3 blk(dev::TX, dev::TY);
-  dev::k_prolong<T><<<F.ntiles, blk, 0, s>>>(F.tiles, F.cls, F.nx, F.ny, F.pitch, C.pitch, U<T>(C), U<T>(F));
+  KL(dev::k_prolong<T><<<F.ntiles, blk, 0, s>>>(F.tiles, F.cls, F.nx, F.ny, F.pitch, C.pitch, U<T>(C), U<T>(F)));
 }
 
 template <typename T>
 void bottom(ccm_handle* H, DevLevel& B, cudaStream_t s) {
   int nw = 8;
   size_t sm = std::max<size_t>(B.nbc, nw * 32) * sizeof(T);
-  dev::k_bottom<T><<<ceil_div(B.nbc, 32), nw * 32, sm, s>>>(B.nbc, B.bot_cell, Bot<T>(B), R<T>(B), U<T>(B));
+  KL(dev::k_bottom<T><<<ceil_div(B.nbc, 32), nw * 32, sm, s>>>(B.nbc, B.bot_cell, Bot<T>(B), R<T>(B), U<T>(B)));
 }
 
 // Alg. 2 from level m: solves L^(m) u = r^(m) approximately, u = U<T>(level m)
@@ -217,15 +304,18 @@ void vcycle(ccm_handle* H, int m, cudaStream_t s) {
   DevLevel& C = H->L[m + 1];
   for (int k = 0; k < H->par.nu1; ++k) smooth_step<T>(H, F, s);
   restrict_to<T>(H, F, C, s);
-  cudaMemsetAsync(U<T>(C), 0, C.npad * sizeof(T), s);
   vcycle<T>(H, m + 1, s);
-  prolong_from<T>(H, F, C, s);
-  for (int k = 0; k < H->par.nu2; ++k) smooth_step<T>(H, F, s);
+  if (H->par.nu2 == 0) {
+    prolong_from<T>(H, F, C, s);
+    return;
+  }
+  smooth_step<T>(H, F, s, U<T>(C), C.pitch);
+  for (int k = 1; k < H->par.nu2; ++k) smooth_step<T>(H, F, s);
 }
 
 int read_norm(ccm_handle* H, const uint8_t* cls, long n, const double* x, cudaStream_t s, double& out) {
   CCM_CUDA(cudaMemsetAsync(H->dnorm, 0, sizeof(unsigned long long), s));
-  dev::k_absmax<double><<<std::min(ceil_div(n, 256), 1216), 256, 0, s>>>(n, cls, x, H->dnorm);
+  KL(dev::k_absmax<double><<<std::min(ceil_div(n, 256), 1216), 256, 0, s>>>(n, cls, x, H->dnorm));
   CCM_CUDA(cudaMemcpyAsync(H->hnorm, H->dnorm, sizeof(unsigned long long), cudaMemcpyDeviceToHost, s));
   CCM_CUDA(cudaStreamSynchronize(s));
   unsigned long long bits = *H->hnorm;
@@ -244,8 +334,8 @@ void load_level(ccm_handle* h, DevLevel& L, const double* u, const double* r, cu
   cudaMemsetAsync(U<T>(L), 0, L.npad * sizeof(T), s);
   cudaMemsetAsync(Uother<T>(L), 0, L.npad * sizeof(T), s);
   cudaMemsetAsync(R<T>(L), 0, L.npad * sizeof(T), s);
-  if (u) dev::k_pack<T, double><<<pg, 128, 0, s>>>(L.nx, L.ny, L.pitch, L.cls, u, U<T>(L), 1.0);
-  if (r) dev::k_pack<T, double><<<pg, 128, 0, s>>>(L.nx, L.ny, L.pitch, L.cls, r, R<T>(L), L.h * L.h);
+  if (u) KL(dev::k_pack<T, double><<<pg, 128, 0, s>>>(L.nx, L.ny, L.pitch, L.cls, u, U<T>(L), 1.0));
+  if (r) KL(dev::k_pack<T, double><<<pg, 128, 0, s>>>(L.nx, L.ny, L.pitch, L.cls, r, R<T>(L), L.h * L.h));
 }
 
 }  // namespace
@@ -268,6 +358,8 @@ int ccm_default_params(ccm_params* p) {
   p->ras_block = 64;
   p->ras_overlap = 32;
   p->nthreads = 0;
+  p->ras_exact = 1024;
+  p->inner_cycles = 3;
   return CCM_OK;
 }
 
@@ -305,6 +397,7 @@ int ccm_setup(const ccm_problem* prob, const ccm_params* params, ccm_handle** ou
   if (params) par = *params;
   if (par.nu1 < 0 || par.nu2 < 0 || par.coarsest < 4 || par.ras_passes < 0 || par.ras_block < 8 ||
       par.ras_block > 128 || par.ras_overlap < 0 || par.ras_overlap > 64 || par.max_iter < 0 ||
+      par.ras_exact < 0 || par.ras_exact > 6000 || par.inner_cycles < 1 || par.inner_cycles > 16 ||
       !(par.theta >= 0 && par.theta < 1) || (par.precision != CCM_FP64 && par.precision != CCM_MIXED))
     return CCM_EINVAL;
   auto t0 = std::chrono::steady_clock::now();
@@ -347,7 +440,12 @@ int ccm_setup(const ccm_problem* prob, const ccm_params* params, ccm_handle** ou
     d.ntiles = (int)hl.tiles.size() / 2;
     d.tiles = A.upload(hl.tiles);
     d.cls = A.upload(hl.cls);
-    d.vol = A.upload(hl.vol);
+    {
+      std::vector<double> v64(hl.vol.begin(), hl.vol.end());
+      d.vol64 = A.upload(v64);
+      std::vector<float> v32(hl.vol.begin(), hl.vol.end());
+      d.vol32 = A.upload(v32);
+    }
     d.n2 = hl.n2;
     if (hl.n2) {
       d.irr_cell = A.upload(hl.irr_cell);
@@ -368,7 +466,14 @@ int ccm_setup(const ccm_problem* prob, const ccm_params* params, ccm_handle** ou
       d.inv64 = A.upload(hl.blk_inv);
       std::vector<float> f(hl.blk_inv.begin(), hl.blk_inv.end());
       d.inv32 = A.upload(f);
-      for (int b = 0; b < d.nblk; ++b) d.max_ext = std::max(d.max_ext, hl.blk[4 * b + 3] - hl.blk[4 * b + 2]);
+      for (int b = 0; b < d.nblk; ++b) {
+        d.max_ext = std::max(d.max_ext, hl.blk[4 * b + 3] - hl.blk[4 * b + 2]);
+        d.max_core = std::max(d.max_core, hl.blk[4 * b + 1] - hl.blk[4 * b]);
+      }
+      if ((long)d.max_ext * (long)sizeof(double) > 48 * 1024) {
+        A.release();
+        return CCM_EINVAL;
+      }
     }
     d.nbc = hl.nb_cells;
     if (d.nbc) {
@@ -491,14 +596,14 @@ int ccm_apply(ccm_handle* h, const double* u, const double* g, double* out, int 
   const long nu = (long)L.nx * L.ny;
   dim3 pg(ceil_div(L.nx, 128), L.ny);
   for (int k = 0; k < nrhs; ++k) {
-    dev::k_pack<double, double><<<pg, 128, 0, s>>>(L.nx, L.ny, L.pitch, L.cls, u + k * nu, L.t64, 1.0);
+    KL(dev::k_pack<double, double><<<pg, 128, 0, s>>>(L.nx, L.ny, L.pitch, L.cls, u + k * nu, L.t64, 1.0));
     launch_regular<double>(h, L, L.t64, nullptr, L.u64[1 - L.cur64], false, s);
     if (L.n2)
-      dev::k_rows<double, double, false, true><<<ceil_div(L.n2, 128), 128, 0, s>>>(
+      KL(dev::k_rows<double, double, false, true><<<ceil_div(L.n2, 128), 128, 0, s>>>(
           L.n2, L.irr_cell, L.ell_col, L.ell64, L.t64, nullptr, L.u64[1 - L.cur64], L.nb, L.seg,
-          g ? g + (long)k * h->info.n_segments : nullptr);
-    dev::k_unpack<double><<<pg, 128, 0, s>>>(L.nx, L.ny, L.pitch, L.cls, L.u64[1 - L.cur64], out + k * nu,
-                                             1.0 / (L.h * L.h));
+          g ? g + (long)k * h->info.n_segments : nullptr));
+    KL(dev::k_unpack<double><<<pg, 128, 0, s>>>(L.nx, L.ny, L.pitch, L.cls, L.u64[1 - L.cur64], out + k * nu,
+                                             1.0 / (L.h * L.h)));
   }
   CCM_CUDA(cudaGetLastError());
   return CCM_OK;
@@ -512,25 +617,108 @@ int ccm_apply_T(ccm_handle* h, const double* v, double* out_u, double* out_g, in
   dim3 pg(ceil_div(L.nx, 128), L.ny);
   const double sc = 1.0 / (L.h * L.h);
   for (int k = 0; k < nrhs; ++k) {
-    dev::k_pack<double, double><<<pg, 128, 0, s>>>(L.nx, L.ny, L.pitch, L.cls, v + k * nu, L.t64, 1.0);
+    KL(dev::k_pack<double, double><<<pg, 128, 0, s>>>(L.nx, L.ny, L.pitch, L.cls, v + k * nu, L.t64, 1.0));
     if (out_u) {
       double* o = L.u64[1 - L.cur64];
       dim3 blk(dev::TX, dev::TY);
       if (L.ntiles) {
-        if (h->cross) dev::k_regular_T<true><<<L.ntiles, blk, 0, s>>>(L.tiles, L.cls, L.nx, L.ny, L.pitch, L.t64, o, h->S64);
-        else dev::k_regular_T<false><<<L.ntiles, blk, 0, s>>>(L.tiles, L.cls, L.nx, L.ny, L.pitch, L.t64, o, h->S64);
+        if (h->cross) KL(dev::k_regular_T<true><<<L.ntiles, blk, 0, s>>>(L.tiles, L.cls, L.nx, L.ny, L.pitch, L.t64, o, h->S64));
+        else KL(dev::k_regular_T<false><<<L.ntiles, blk, 0, s>>>(L.tiles, L.cls, L.nx, L.ny, L.pitch, L.t64, o, h->S64));
       }
       if (L.ncolT)
-        dev::k_rows_T<<<ceil_div(L.ncolT, 128), 128, 0, s>>>(L.ncolT, L.tr_ptr, L.tr_cell, L.tr_row, L.tr_val,
-                                                            L.irr_cell, L.t64, o);
-      dev::k_unpack<double><<<pg, 128, 0, s>>>(L.nx, L.ny, L.pitch, L.cls, o, out_u + k * nu, sc);
+        KL(dev::k_rows_T<<<ceil_div(L.ncolT, 128), 128, 0, s>>>(L.ncolT, L.tr_ptr, L.tr_cell, L.tr_row, L.tr_val,
+                                                            L.irr_cell, L.t64, o));
+      KL(dev::k_unpack<double><<<pg, 128, 0, s>>>(L.nx, L.ny, L.pitch, L.cls, o, out_u + k * nu, sc));
     }
     if (out_g && L.n2)
-      dev::k_bnd_T<<<ceil_div(L.n2, 128), 128, 0, s>>>(L.n2, L.irr_cell, L.nb, L.seg, L.t64,
-                                                      out_g + (long)k * h->info.n_segments, sc);
+      KL(dev::k_bnd_T<<<ceil_div(L.n2, 128), 128, 0, s>>>(L.n2, L.irr_cell, L.nb, L.seg, L.t64,
+                                                      out_g + (long)k * h->info.n_segments, sc));
   }
   CCM_CUDA(cudaGetLastError());
   return CCM_OK;
+}
+
+// One outer iteration on the stream (also the body captured into the iteration graph):
+// mixed: FP32 V-cycles on the FP32 image of the FP64 residual, u_hat += e, new FP64 residual;
+// fp64:  one FP64 V-cycle in place, new FP64 residual; then the residual norm to the host.
+static void iteration_body(ccm_handle* h, bool fp64, cudaStream_t s) {
+  DevLevel& L = h->L[0];
+  const long np = L.npad;
+  double* ucur;
+  if (fp64) {
+    double* start = L.u64[L.cur64];
+    {
+      ProfScope ps(h, CCM_PROF_VCYCLE, s);
+      vcycle<double>(h, 0, s);
+    }
+    if (L.u64[L.cur64] != start) {
+      cudaMemcpyAsync(start, L.u64[L.cur64], np * sizeof(double), cudaMemcpyDeviceToDevice, s);
+      L.cur64 = 1 - L.cur64;
+    }
+    ucur = start;
+  } else {
+    KL(dev::k_to_float<<<std::min(ceil_div(np, 256), 4096), 256, 0, s>>>(np, L.t64, L.r32));
+    cudaMemsetAsync(L.u32[L.cur32], 0, np * sizeof(float), s);
+    for (int c = 0; c < std::max(1, h->par.inner_cycles); ++c) {
+      ProfScope ps(h, CCM_PROF_VCYCLE, s);
+      vcycle<float>(h, 0, s);
+    }
+    KL(dev::k_axpy<float><<<std::min(ceil_div(np, 256), 4096), 256, 0, s>>>(np, L.cls, L.u32[L.cur32], h->uhat));
+    ucur = h->uhat;
+  }
+  {
+    ProfScope ps(h, CCM_PROF_RESID_FP64, s);
+    launch_regular<double>(h, L, ucur, h->rhat, L.t64, true, s);
+  }
+  if (L.n2)
+    KL(dev::k_rows<double, double, true, true><<<ceil_div(L.n2, 128), 128, 0, s>>>(
+        L.n2, L.irr_cell, L.ell_col, L.ell64, ucur, h->rhat, L.t64, nullptr, nullptr, nullptr));
+  cudaMemsetAsync(h->dnorm, 0, sizeof(unsigned long long), s);
+  KL(dev::k_absmax<double><<<std::min(ceil_div(np, 256), 1216), 256, 0, s>>>(np, L.cls, L.t64, h->dnorm));
+  cudaMemcpyAsync(h->hnorm, h->dnorm, sizeof(unsigned long long), cudaMemcpyDeviceToHost, s);
+}
+
+static int capture_iteration(ccm_handle* h, bool fp64, cudaStream_t user) {
+  ccm_handle::Graph& G = h->graph[fp64 ? 1 : 0];
+  if (G.exec) return CCM_OK;
+  if (!h->cap_stream) CCM_CUDA(cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking));
+  CCM_CUDA(cudaStreamSynchronize(user));
+  cudaStream_t s = h->cap_stream;
+  // the body leaves every ping-pong buffer where it found it only for an even number of
+  // sweeps per level; odd counts are handled inside the body (fp64) or by resetting the
+  // level-0 FP32 buffer at the start of every replay (mixed)
+  const int cur64 = h->L[0].cur64;
+  cudaGraph_t graph;
+  CCM_CUDA(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+  h->capturing = true;
+  size_t ev0 = h->gprof_ev.size();
+  long long l0 = g_launches.load();
+  iteration_body(h, fp64, s);
+  G.launches = g_launches.load() - l0;
+  g_launches.fetch_sub(G.launches);
+  h->capturing = false;
+  cudaError_t e = cudaStreamEndCapture(s, &graph);
+  if (e != cudaSuccess) return CCM_ECUDA;
+  for (size_t k = ev0; k < h->gprof_ev.size(); k += 2) G.prof_pairs.push_back((int)k);
+  e = cudaGraphInstantiate(&G.exec, graph, 0);
+  cudaGraphDestroy(graph);
+  if (e != cudaSuccess) {
+    G.exec = nullptr;
+    return CCM_ECUDA;
+  }
+  h->L[0].cur64 = cur64;
+  G.u0 = fp64 ? h->L[0].u64[cur64] : h->uhat;
+  return CCM_OK;
+}
+
+static void drop_graphs(ccm_handle* h) {
+  for (auto& G : h->graph) {
+    if (G.exec) cudaGraphExecDestroy(G.exec);
+    G.exec = nullptr;
+    G.prof_pairs.clear();
+  }
+  for (cudaEvent_t e : h->gprof_ev) cudaEventDestroy(e);
+  h->gprof_ev.clear();
 }
 
 int ccm_solve(ccm_handle* h, const double* f, const double* g, double* u, int nrhs, void* stream, ccm_stats* st) {
@@ -540,58 +728,57 @@ int ccm_solve(ccm_handle* h, const double* f, const double* g, double* u, int nr
   const long nu = (long)L.nx * L.ny, np = L.npad;
   const double h2 = L.h * L.h;
   dim3 pg(ceil_div(L.nx, 128), L.ny);
+  const bool fp64 = h->par.precision == CCM_FP64;
   int result = CCM_OK;
+  int rc = capture_iteration(h, fp64, s);
+  if (rc) return rc;
+  ccm_handle::Graph& G = h->graph[fp64 ? 1 : 0];
   for (int k = 0; k < nrhs; ++k) {
-    // r_hat = h^2 (f - N g)
+    // r_hat = h^2 (f - N g); u_hat = initial guess
     CCM_CUDA(cudaMemsetAsync(h->rhat, 0, np * sizeof(double), s));
-    dev::k_pack<double, double><<<pg, 128, 0, s>>>(L.nx, L.ny, L.pitch, L.cls, f + k * nu, h->rhat, h2);
+    KL(dev::k_pack<double, double><<<pg, 128, 0, s>>>(L.nx, L.ny, L.pitch, L.cls, f + k * nu, h->rhat, h2));
     if (g && L.n2)
-      dev::k_sub_boundary<<<ceil_div(L.n2, 128), 128, 0, s>>>(L.n2, L.irr_cell, L.nb, L.seg,
-                                                             g + (long)k * h->info.n_segments, h->rhat);
-    CCM_CUDA(cudaMemsetAsync(h->uhat, 0, np * sizeof(double), s));
-    dev::k_pack<double, double><<<pg, 128, 0, s>>>(L.nx, L.ny, L.pitch, L.cls, u + k * nu, h->uhat, 1.0);
-    double rnorm = 0;
-    int rc = read_norm(h, L.cls, np, h->rhat, s, rnorm);
+      KL(dev::k_sub_boundary<<<ceil_div(L.n2, 128), 128, 0, s>>>(L.n2, L.irr_cell, L.nb, L.seg,
+                                                             g + (long)k * h->info.n_segments, h->rhat));
+    double* U0 = G.u0;
+    CCM_CUDA(cudaMemsetAsync(U0, 0, np * sizeof(double), s));
+    KL(dev::k_pack<double, double><<<pg, 128, 0, s>>>(L.nx, L.ny, L.pitch, L.cls, u + k * nu, U0, 1.0));
+    if (fp64) CCM_CUDA(cudaMemcpyAsync(L.r64, h->rhat, np * sizeof(double), cudaMemcpyDeviceToDevice, s));
+    double rnorm = 0, rel = 0;
+    rc = read_norm(h, L.cls, np, h->rhat, s, rnorm);
     if (rc) return rc;
     if (rnorm == 0) rnorm = 1;
-    int it = 0;
-    double rel = 0;
+    // initial residual
+    launch_regular<double>(h, L, U0, h->rhat, L.t64, true, s);
+    if (L.n2)
+      KL(dev::k_rows<double, double, true, true><<<ceil_div(L.n2, 128), 128, 0, s>>>(
+          L.n2, L.irr_cell, L.ell_col, L.ell64, U0, h->rhat, L.t64, nullptr, nullptr, nullptr));
+    rc = read_norm(h, L.cls, np, L.t64, s, rel);
+    if (rc) return rc;
+    rel /= rnorm;
     ccm_stats local{};
-    const bool fp64 = h->par.precision == CCM_FP64;
-    double* U0 = fp64 ? L.u64[L.cur64] : h->uhat;
-    if (fp64) {
-      CCM_CUDA(cudaMemcpyAsync(U0, h->uhat, np * sizeof(double), cudaMemcpyDeviceToDevice, s));
-      CCM_CUDA(cudaMemcpyAsync(L.r64, h->rhat, np * sizeof(double), cudaMemcpyDeviceToDevice, s));
-    }
-    while (true) {
-      double* ucur = fp64 ? L.u64[L.cur64] : h->uhat;
-      residual<double>(h, L, ucur, h->rhat, L.t64, s);
-      rc = read_norm(h, L.cls, np, L.t64, s, rel);
-      if (rc) return rc;
+    local.history[0] = rel;
+    int it = 0;
+    while (std::isfinite(rel) && rel > h->par.rtol && it < h->par.max_iter) {
+      CCM_CUDA(cudaGraphLaunch(G.exec, s));
+      g_launches.fetch_add(G.launches);
+      CCM_CUDA(cudaStreamSynchronize(s));
+      unsigned long long bits = *h->hnorm;
+      std::memcpy(&rel, &bits, sizeof(double));
       rel /= rnorm;
-      if (it < 64) local.history[it] = rel;
-      if (!std::isfinite(rel)) {
-        result = CCM_ENOTFINITE;
-        break;
-      }
-      if (rel <= h->par.rtol) break;
-      if (it >= h->par.max_iter) {
-        result = CCM_ENOCONV;
-        break;
-      }
-      if (fp64) {
-        vcycle<double>(h, 0, s);
-      } else {
-        dev::k_to_float<<<std::min(ceil_div(np, 256), 4096), 256, 0, s>>>(np, L.t64, L.r32);
-        CCM_CUDA(cudaMemsetAsync(L.u32[L.cur32], 0, np * sizeof(float), s));
-        vcycle<float>(h, 0, s);
-        dev::k_axpy<float><<<std::min(ceil_div(np, 256), 4096), 256, 0, s>>>(np, L.cls, L.u32[L.cur32], h->uhat);
-      }
-      CCM_CUDA(cudaGetLastError());
       ++it;
+      if (it < 64) local.history[it] = rel;
+      for (int p : G.prof_pairs) {
+        float t = 0;
+        if (cudaEventElapsedTime(&t, h->gprof_ev[p], h->gprof_ev[p + 1]) == cudaSuccess) {
+          h->prof_ms += t;
+          h->prof_n += 1;
+        }
+      }
     }
-    double* ufin = fp64 ? L.u64[L.cur64] : h->uhat;
-    dev::k_unpack<double><<<pg, 128, 0, s>>>(L.nx, L.ny, L.pitch, L.cls, ufin, u + k * nu, 1.0);
+    if (!std::isfinite(rel)) result = CCM_ENOTFINITE;
+    else if (rel > h->par.rtol) result = CCM_ENOCONV;
+    KL(dev::k_unpack<double><<<pg, 128, 0, s>>>(L.nx, L.ny, L.pitch, L.cls, U0, u + k * nu, 1.0));
     local.iterations = it;
     local.rel_residual = rel;
     if (st) *st = local;
@@ -612,12 +799,12 @@ int ccm_level_apply(ccm_handle* h, int level, const double* u, double* out, void
   cudaStream_t s = (cudaStream_t)stream;
   DevLevel& L = h->L[level];
   dim3 pg(ceil_div(L.nx, 128), L.ny);
-  dev::k_pack<double, double><<<pg, 128, 0, s>>>(L.nx, L.ny, L.pitch, L.cls, u, L.t64, 1.0);
+  KL(dev::k_pack<double, double><<<pg, 128, 0, s>>>(L.nx, L.ny, L.pitch, L.cls, u, L.t64, 1.0));
   launch_regular<double>(h, L, L.t64, nullptr, L.r64, false, s);
   if (L.n2)
-    dev::k_rows<double, double, false, true><<<ceil_div(L.n2, 128), 128, 0, s>>>(
-        L.n2, L.irr_cell, L.ell_col, L.ell64, L.t64, nullptr, L.r64, L.nb, L.seg, nullptr);
-  dev::k_unpack<double><<<pg, 128, 0, s>>>(L.nx, L.ny, L.pitch, L.cls, L.r64, out, 1.0 / (L.h * L.h));
+    KL(dev::k_rows<double, double, false, true><<<ceil_div(L.n2, 128), 128, 0, s>>>(
+        L.n2, L.irr_cell, L.ell_col, L.ell64, L.t64, nullptr, L.r64, L.nb, L.seg, nullptr));
+  KL(dev::k_unpack<double><<<pg, 128, 0, s>>>(L.nx, L.ny, L.pitch, L.cls, L.r64, out, 1.0 / (L.h * L.h)));
   CCM_CUDA(cudaGetLastError());
   return CCM_OK;
 }
@@ -630,11 +817,11 @@ int ccm_level_smooth(ccm_handle* h, int level, double* u, const double* r, int p
   if (precision == CCM_FP64) {
     load_level<double>(h, L, u, r, s);
     smooth_step<double>(h, L, s);
-    dev::k_unpack<double><<<pg, 128, 0, s>>>(L.nx, L.ny, L.pitch, L.cls, U<double>(L), u, 1.0);
+    KL(dev::k_unpack<double><<<pg, 128, 0, s>>>(L.nx, L.ny, L.pitch, L.cls, U<double>(L), u, 1.0));
   } else {
     load_level<float>(h, L, u, r, s);
     smooth_step<float>(h, L, s);
-    dev::k_unpack<float><<<pg, 128, 0, s>>>(L.nx, L.ny, L.pitch, L.cls, U<float>(L), u, 1.0);
+    KL(dev::k_unpack<float><<<pg, 128, 0, s>>>(L.nx, L.ny, L.pitch, L.cls, U<float>(L), u, 1.0));
   }
   CCM_CUDA(cudaGetLastError());
   return CCM_OK;
@@ -649,7 +836,7 @@ int ccm_level_restrict(ccm_handle* h, int level, const double* u, const double* 
   cudaMemsetAsync(C.r64, 0, C.npad * sizeof(double), s);
   restrict_to<double>(h, F, C, s);
   dim3 pg(ceil_div(C.nx, 128), C.ny);
-  dev::k_unpack<double><<<pg, 128, 0, s>>>(C.nx, C.ny, C.pitch, C.cls, C.r64, rc, 1.0 / (C.h * C.h));
+  KL(dev::k_unpack<double><<<pg, 128, 0, s>>>(C.nx, C.ny, C.pitch, C.cls, C.r64, rc, 1.0 / (C.h * C.h)));
   CCM_CUDA(cudaGetLastError());
   return CCM_OK;
 }
@@ -663,7 +850,7 @@ int ccm_level_prolong(ccm_handle* h, int level, const double* uc, double* u, voi
   load_level<double>(h, C, uc, nullptr, s);
   prolong_from<double>(h, F, C, s);
   dim3 pg(ceil_div(F.nx, 128), F.ny);
-  dev::k_unpack<double><<<pg, 128, 0, s>>>(F.nx, F.ny, F.pitch, F.cls, U<double>(F), u, 1.0);
+  KL(dev::k_unpack<double><<<pg, 128, 0, s>>>(F.nx, F.ny, F.pitch, F.cls, U<double>(F), u, 1.0));
   CCM_CUDA(cudaGetLastError());
   return CCM_OK;
 }
@@ -675,7 +862,7 @@ int ccm_bottom_solve(ccm_handle* h, const double* r, double* u, void* stream) {
   load_level<double>(h, B, nullptr, r, s);
   bottom<double>(h, B, s);
   dim3 pg(ceil_div(B.nx, 128), B.ny);
-  dev::k_unpack<double><<<pg, 128, 0, s>>>(B.nx, B.ny, B.pitch, B.cls, U<double>(B), u, 1.0);
+  KL(dev::k_unpack<double><<<pg, 128, 0, s>>>(B.nx, B.ny, B.pitch, B.cls, U<double>(B), u, 1.0));
   CCM_CUDA(cudaGetLastError());
   return CCM_OK;
 }
@@ -688,19 +875,54 @@ int ccm_vcycle(ccm_handle* h, double* u, const double* r, int precision, void* s
   if (precision == CCM_FP64) {
     load_level<double>(h, L, u, r, s);
     vcycle<double>(h, 0, s);
-    dev::k_unpack<double><<<pg, 128, 0, s>>>(L.nx, L.ny, L.pitch, L.cls, U<double>(L), u, 1.0);
+    KL(dev::k_unpack<double><<<pg, 128, 0, s>>>(L.nx, L.ny, L.pitch, L.cls, U<double>(L), u, 1.0));
   } else {
     load_level<float>(h, L, u, r, s);
     vcycle<float>(h, 0, s);
-    dev::k_unpack<float><<<pg, 128, 0, s>>>(L.nx, L.ny, L.pitch, L.cls, U<float>(L), u, 1.0);
+    KL(dev::k_unpack<float><<<pg, 128, 0, s>>>(L.nx, L.ny, L.pitch, L.cls, U<float>(L), u, 1.0));
   }
   CCM_CUDA(cudaGetLastError());
+  return CCM_OK;
+}
+
+int64_t ccm_launch_count(void) { return (int64_t)g_launches.load(); }
+
+int ccm_profile(ccm_handle* h, int kernel_class) {
+  if (!h || kernel_class < 0 || kernel_class > CCM_PROF_VCYCLE) return CCM_EINVAL;
+  if (kernel_class != h->prof_class) {
+    cudaDeviceSynchronize();
+    drop_graphs(h);
+  }
+  h->prof_class = kernel_class;
+  h->prof_used = 0;
+  h->prof_ms = 0;
+  h->prof_n = 0;
+  return CCM_OK;
+}
+
+int ccm_profile_read(ccm_handle* h, double* ms, int64_t* launches) {
+  if (!h || !ms || !launches) return CCM_EINVAL;
+  double tot = 0;
+  for (int k = 0; k + 1 < h->prof_used; k += 2) {
+    CCM_CUDA(cudaEventSynchronize(h->prof_ev[k + 1]));
+    float t = 0;
+    CCM_CUDA(cudaEventElapsedTime(&t, h->prof_ev[k], h->prof_ev[k + 1]));
+    tot += t;
+  }
+  *ms = tot + h->prof_ms;
+  *launches = h->prof_used / 2 + h->prof_n;
+  h->prof_used = 0;
+  h->prof_ms = 0;
+  h->prof_n = 0;
   return CCM_OK;
 }
 
 void ccm_free(ccm_handle* h) {
   if (!h) return;
   cudaDeviceSynchronize();
+  drop_graphs(h);
+  if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
+  for (cudaEvent_t e : h->prof_ev) cudaEventDestroy(e);
   h->arena.release();
   if (h->hnorm) cudaFreeHost(h->hnorm);
   delete h;
