@@ -88,6 +88,10 @@ typedef struct {
   int nthreads;      /* host threads for ccm_setup (0 = all cores) */
   int ras_exact;     /* levels with at most this many irregular cells use one exact block */
   int inner_cycles;  /* CCM_MIXED: FP32 V-cycles per FP64 residual evaluation */
+  int smoother;      /* 0: SMO-1 then SMO-2 from the new regular values (Sec. 4.1, two launches);
+                        1: block-Jacobi form, both from the old iterate (one launch per sweep) */
+  int coarse_n;      /* CCM_MIXED: levels with at most coarse_n cells a side run their part of the
+                        V-cycle in one CTA (0: never) */
 } ccm_params;
 
 typedef struct {
@@ -109,9 +113,9 @@ typedef struct {
 
 typedef struct ccm_handle ccm_handle;
 
-/* Fill p with the defaults: omega 0.8, nu1 = nu2 = 3, theta 0.3, coarsest 16, CCM_MIXED,
+/* Fill p with the defaults: omega 0.7, nu1 = nu2 = 3, theta 0.3, coarsest 16, CCM_MIXED,
  * rtol 1e-10, max_iter 100, ras_passes 1, ras_block 64, ras_overlap 32, nthreads 0,
- * ras_exact 1024, inner_cycles 3. */
+ * ras_exact 0, inner_cycles 3, smoother 1, coarse_n 0. */
 int ccm_default_params(ccm_params* p);
 
 /* Host setup (Sec. 3.1 - 3.4, Sec. 4): cut cells and moments (Green's formula, Sec. 2.4),
@@ -203,11 +207,15 @@ int ccm_vcycle(ccm_handle* h, double* u, const double* r, int precision, void* s
  * ccm_profile: record CUDA events on the handle's stream around every launch of one class:
  *   CCM_PROF_RESID_FP64  level-0 FP64 residual of the regular cells (outer iteration),
  *   CCM_PROF_SMO1_FP32   level-0 SMO-1 sweep in FP32, CCM_PROF_SMO1_FP64 the same in FP64,
- *   CCM_PROF_VCYCLE      one whole V-cycle; 0 switches profiling off.
+ *   CCM_PROF_VCYCLE      one whole V-cycle,
+ *   CCM_PROF_SMO2_FP32   level-0 SMO-2 block step in FP32,
+ *   CCM_PROF_PROLONG_SMO1_FP32  level-0 first post-smoothing sweep with the prolongation fused,
+ *   CCM_PROF_RESTRICT_FP32      level-0 residual + restriction in FP32;
+ * 0 switches profiling off.
  * ccm_profile_read: total device time (ms) and launch count recorded since the last read;
  * waits for the recorded events. */
 enum { CCM_PROF_OFF = 0, CCM_PROF_RESID_FP64 = 1, CCM_PROF_SMO1_FP32 = 2, CCM_PROF_SMO1_FP64 = 3,
-       CCM_PROF_VCYCLE = 4 };
+       CCM_PROF_VCYCLE = 4, CCM_PROF_SMO2_FP32 = 5, CCM_PROF_PROLONG_SMO1_FP32 = 6, CCM_PROF_RESTRICT_FP32 = 7 };
 int64_t ccm_launch_count(void);
 int ccm_profile(ccm_handle* h, int kernel_class);
 int ccm_profile_read(ccm_handle* h, double* ms, int64_t* launches);

@@ -40,7 +40,8 @@ class ccm_params(ctypes.Structure):
                 ("theta", ctypes.c_double), ("coarsest", ctypes.c_int), ("precision", ctypes.c_int),
                 ("rtol", ctypes.c_double), ("max_iter", ctypes.c_int), ("ras_passes", ctypes.c_int),
                 ("ras_block", ctypes.c_int), ("ras_overlap", ctypes.c_int), ("nthreads", ctypes.c_int),
-                ("ras_exact", ctypes.c_int), ("inner_cycles", ctypes.c_int)]
+                ("ras_exact", ctypes.c_int), ("inner_cycles", ctypes.c_int), ("smoother", ctypes.c_int),
+                ("coarse_n", ctypes.c_int)]
 
 
 class ccm_info(ctypes.Structure):

@@ -191,6 +191,25 @@ static int pack_level(const CutLevel& cg, const Rows& rows, const ccm_params& pa
         L.tiles.push_back(b);
       }
     }
+  // active 64 x 32 tiles for the TMA-staged smoother
+  {
+    const int ax = (cg.nx + 63) / 64, ay = (cg.ny + 31) / 32;
+    L.tiles64.clear();
+    for (int b = 0; b < ay; ++b)
+      for (int a = 0; a < ax; ++a) {
+        bool any = false;
+        for (int j = b * 32; j < std::min(cg.ny, b * 32 + 32) && !any; ++j)
+          for (int i = a * 64; i < std::min(cg.nx, a * 64 + 64); ++i)
+            if (rows.regular[(long)j * cg.nx + i]) {
+              any = true;
+              break;
+            }
+        if (any) {
+          L.tiles64.push_back(a);
+          L.tiles64.push_back(b);
+        }
+      }
+  }
   // fitted rows
   const int n2 = (int)rows.irr.size();
   L.n2 = n2;
@@ -210,6 +229,16 @@ static int pack_level(const CutLevel& cg, const Rows& rows, const ccm_params& pa
     L.nb[r] = rows.nb[r];
     L.seg[r] = rows.seg[r];
   }
+  // the same columns with the sign bit set where the column cell is regular (SMO-2 reads
+  // those from the new iterate and the irregular ones from the old)
+  L.ell_colf.resize(15L * n2);
+  for (int r = 0; r < n2; ++r)
+    for (int k = 0; k < 15; ++k) {
+      int c2 = rows.cols[r][k];
+      uint32_t v = (uint32_t)L.ell_col[(long)k * n2 + r];
+      if (rows.regular[c2]) v |= 0x80000000u;
+      L.ell_colf[(long)k * n2 + r] = (int32_t)v;
+    }
   if (finest) {
     // transposed fitted rows, grouped by column cell
     std::map<int32_t, std::vector<std::pair<int32_t, double>>> cols;
@@ -260,7 +289,9 @@ static int pack_level(const CutLevel& cg, const Rows& rows, const ccm_params& pa
   }
   // SMO-2 blocks over the boundary order
   if (!coarsest && n2 > 0) {
-    std::vector<int> order = boundary_order(cg, rows);
+    // the rows were renumbered into the boundary order: blocks are contiguous row ranges
+    std::vector<int> order(n2);
+    for (int p = 0; p < n2; ++p) order[p] = p;
     L.order.assign(order.begin(), order.end());
     std::vector<int> pos(n2);
     for (int p = 0; p < n2; ++p) pos[order[p]] = p;
@@ -347,6 +378,25 @@ int build_hierarchy(const ccm_problem& prob, const ccm_params& par, Hierarchy& H
     rc = discretize_level(cg, prob.a, prob.b, prob.c, par.nthreads, rows, err);
     if (rc) return rc;
     if (m == 0) H.cond_max = rows.cond_max;
+    if (m < nl - 1 && !rows.irr.empty()) {
+      // renumber the fitted rows into the boundary order of Alg. 3
+      std::vector<int> order = boundary_order(cg, rows);
+      Rows p;
+      p.regular = rows.regular;
+      p.cond_max = rows.cond_max;
+      for (int r : order) {
+        p.irr.push_back(rows.irr[r]);
+        p.cols.push_back(rows.cols[r]);
+        p.beta.push_back(rows.beta[r]);
+        p.nb.push_back(rows.nb[r]);
+        p.seg.push_back(rows.seg[r]);
+      }
+      rows.irr.swap(p.irr);
+      rows.cols.swap(p.cols);
+      rows.beta.swap(p.beta);
+      rows.nb.swap(p.nb);
+      rows.seg.swap(p.seg);
+    }
     rc = pack_level(cg, rows, par, m == nl - 1, m == 0, H.levels[m], err);
     if (rc) return rc;
     if (m == 0) H.nseg = (int)cg.segs.size();

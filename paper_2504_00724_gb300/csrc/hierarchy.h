@@ -20,11 +20,13 @@ struct HostLevel {
   std::vector<uint8_t> cls;     // [npad] 0 empty / ring, 1 regular, 2 irregular
   std::vector<double> vol;      // [npad] cell volume in units of h^2 (0 if empty)
   std::vector<int32_t> tiles;   // active 32 x 8 tiles (tile x, tile y) pairs
+  std::vector<int32_t> tiles64; // active 64 x 32 tiles (TMA-staged SMO-1)
 
   // fitted rows, ELL with 15 slots: [slot][n2]
   int n2 = 0;
   std::vector<int32_t> irr_cell;   // [n2] padded index of the row's cell
   std::vector<int32_t> ell_col;    // [15 * n2] padded column index
+  std::vector<int32_t> ell_colf;   // the same, sign bit set for regular column cells
   std::vector<double> ell_val;     // [15 * n2] h^2-scaled coefficient
   std::vector<double> nb;          // [n2] h^2-scaled boundary coefficient
   std::vector<int32_t> seg;        // [n2] boundary segment or -1

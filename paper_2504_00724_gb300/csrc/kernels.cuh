@@ -8,6 +8,7 @@
 #pragma once
 
 #include <cstdint>
+#include <cuda.h>
 #include <cuda_runtime.h>
 
 namespace ccm {
@@ -133,6 +134,429 @@ __global__ void k_block_solve(const int32_t* __restrict__ order, const int32_t* 
   }
 }
 
+// ---- TMA-staged SMO-1 for the large levels.
+// A 64 x 32 tile of cells plus its 2-cell halo (68 x 36 values) is one 2-D TMA box: in the
+// padded layout the halo of the tile at cells (64 a, 32 b) starts at padded column 64 a, a
+// multiple of 16 bytes for every element size, and rows have no alignment rule.  Cells past
+// the array edge read the zero fill.  256 threads: 64 columns x 4 groups of 8 rows, a 5 x 5
+// register window slides down each column so that every cell costs 5 shared-memory loads.
+constexpr int JX = 64, JY = 32, HX = JX + 4, HY = JY + 4;
+constexpr long long TMA_WAIT_CYCLES = 4000000;   // ~2 ms at 2 GHz: bound on a tile wait
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t phase) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(phase)
+      : "memory");
+  return ok != 0;
+}
+
+__device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, uint64_t* bar, int x, int y) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(
+          smem_u32(dst)),
+      "l"(map), "r"(x), "r"(y), "r"(smem_u32(bar))
+      : "memory");
+}
+
+// bounded wait for the tile (by the SM clock); false, and *err set, if the copy never landed
+__device__ __forceinline__ bool tile_wait(uint64_t* bar, int* err) {
+  const long long t0 = clock64();
+  while (clock64() - t0 < TMA_WAIT_CYCLES)
+    if (mbar_try_wait(bar, 0)) return true;
+  if (threadIdx.x == 0) atomicExch(err, 1);
+  const long long t1 = clock64();     // let the copy in flight finish before leaving
+  while (clock64() - t1 < TMA_WAIT_CYCLES)
+    if (mbar_try_wait(bar, 0)) break;
+  return false;
+}
+
+template <typename T, bool CROSS>
+__global__ void __launch_bounds__(256) k_jacobi_tma(const __grid_constant__ CUtensorMap tin,
+                                                    const int32_t* __restrict__ tiles, const uint8_t* __restrict__ cls,
+                                                    int nx, int ny, int pitch, const T* __restrict__ r,
+                                                    T* __restrict__ u_out, Stencil<T> S, int* __restrict__ err) {
+  __shared__ __align__(128) T tile[HY * HX];
+  __shared__ __align__(8) uint64_t bar;
+  const int cx0 = tiles[2 * blockIdx.x] * JX, cy0 = tiles[2 * blockIdx.x + 1] * JY;
+  if (threadIdx.x == 0) mbar_init(&bar, 1);
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    mbar_expect_tx(&bar, (uint32_t)(HX * HY * sizeof(T)));
+    tma_load_2d(tile, &tin, &bar, cx0, cy0);
+  }
+  // the class bytes and right-hand sides of this thread's 8 cells load while the tile lands
+  const int x = threadIdx.x & 63, y0 = (threadIdx.x >> 6) * 8;
+  const int i = cx0 + x;
+  uint8_t cv[8];
+  T rv[8];
+#pragma unroll
+  for (int k = 0; k < 8; ++k) {
+    const int j = cy0 + y0 + k;
+    const long p = (long)(j + 2) * pitch + (i + 2);
+    const bool in = i < nx && j < ny;
+    cv[k] = in ? cls[p] : (uint8_t)0;
+    rv[k] = in ? r[p] : (T)0;
+  }
+  if (!tile_wait(&bar, err)) return;
+  if (i >= nx) return;
+  T w[5][5];
+#pragma unroll
+  for (int a = 0; a < 4; ++a)
+#pragma unroll
+    for (int b = 0; b < 5; ++b) w[a][b] = tile[(y0 + a) * HX + x + b];
+#pragma unroll
+  for (int k = 0; k < 8; ++k) {
+#pragma unroll
+    for (int b = 0; b < 5; ++b) w[4][b] = tile[(y0 + k + 4) * HX + x + b];
+    if (cv[k] == 1) {
+      T acc = 0;
+#pragma unroll
+      for (int a = 0; a < 5; ++a)
+#pragma unroll
+        for (int b = 0; b < 5; ++b) {
+          if (!CROSS && a != 2 && b != 2) continue;
+          acc += S.w[a * 5 + b] * w[a][b];
+        }
+      const long p = (long)(cy0 + y0 + k + 2) * pitch + (i + 2);
+      u_out[p] = w[2][2] + S.omega_d * (rv[k] - acc);
+    }
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+      for (int b = 0; b < 5; ++b) w[a][b] = w[a + 1][b];
+  }
+}
+
+// ---- one smoothing sweep in one launch (block-Jacobi form of SMO-1 + SMO-2).
+// Both parts read only the old iterate and write only the new one: CTAs [0, ntiles) update
+// the regular cells (SMO-1), CTAs [ntiles, ntiles + nblk * chunks) the irregular cells by the
+// overlapping block solve (SMO-2 whose residual uses the old regular values).  The fixed
+// point is the same as for SMO-1 followed by SMO-2.
+template <typename T>
+struct SweepArgs {
+  const int32_t* tiles;      // TMA: 64 x 32 tiles, else 32 x 8 tiles
+  int ntiles, nblk, chunks, rows_per_cta;
+  const uint8_t* cls;
+  int nx, ny, pitch, n2;
+  const T* r;
+  const T* u_old;
+  T* u_new;
+  Stencil<T> S;
+  const int32_t* blk;
+  const int64_t* blk_off;
+  const T* inv;
+  const int32_t* cell;
+  const int32_t* col;
+  const T* val;
+  int* err;
+};
+
+template <typename T>
+__device__ __forceinline__ void block_part(const SweepArgs<T>& a, int bidx, T* s) {
+  __shared__ T part[8][32];
+  const int b = bidx / a.chunks, chunk = bidx % a.chunks;
+  const int cs = a.blk[4 * b], ce = a.blk[4 * b + 1], es = a.blk[4 * b + 2], ee = a.blk[4 * b + 3];
+  const int ne = ee - es, nc = ce - cs;
+  const int c0 = chunk * a.rows_per_cta;
+  if (c0 >= nc) return;
+  for (int e = threadIdx.x; e < ne; e += blockDim.x) {
+    const int row = es + e;
+    T acc = 0;
+#pragma unroll
+    for (int k = 0; k < 15; ++k) acc += a.val[(long)k * a.n2 + row] * a.u_old[a.col[(long)k * a.n2 + row]];
+    s[e] = a.r[a.cell[row]] - acc;
+  }
+  __syncthreads();
+  const T* A = a.inv + a.blk_off[b];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  const int cend = min(nc, c0 + a.rows_per_cta);
+  for (int cb = c0; cb < cend; cb += 32) {
+    const int c = cb + lane;
+    T acc = 0;
+    if (c < cend)
+      for (int e = warp; e < ne; e += nw) acc += A[(long)e * nc + c] * s[e];
+    part[warp][lane] = acc;
+    __syncthreads();
+    if (warp == 0 && c < cend) {
+      T tot = 0;
+      for (int w = 0; w < nw; ++w) tot += part[w][lane];
+      const long q = a.cell[cs + c];
+      a.u_new[q] = a.u_old[q] + tot;
+    }
+    __syncthreads();
+  }
+}
+
+template <typename T, bool CROSS, bool TMA>
+__global__ void __launch_bounds__(256) k_sweep(const __grid_constant__ CUtensorMap tin, SweepArgs<T> a) {
+  extern __shared__ unsigned char smem_raw[];
+  if ((int)blockIdx.x >= a.ntiles) {
+    block_part<T>(a, blockIdx.x - a.ntiles, reinterpret_cast<T*>(smem_raw));
+    return;
+  }
+  const Stencil<T>& S = a.S;
+  if (!TMA) {
+    // 32 x 8 tile, one cell per thread
+    const int i = a.tiles[2 * blockIdx.x] * TX + (threadIdx.x & 31);
+    const int j = a.tiles[2 * blockIdx.x + 1] * TY + (threadIdx.x >> 5);
+    if (i >= a.nx || j >= a.ny) return;
+    const long p = (long)(j + 2) * a.pitch + (i + 2);
+    if (a.cls[p] != 1) return;
+    const T Lu = stencil_apply<T, CROSS>(a.u_old, p, a.pitch, S);
+    a.u_new[p] = a.u_old[p] + S.omega_d * (a.r[p] - Lu);
+    return;
+  }
+  __shared__ __align__(128) T tile[TMA ? HY * HX : 1];
+  __shared__ __align__(8) uint64_t bar;
+  const int cx0 = a.tiles[2 * blockIdx.x] * JX, cy0 = a.tiles[2 * blockIdx.x + 1] * JY;
+  if (threadIdx.x == 0) mbar_init(&bar, 1);
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    mbar_expect_tx(&bar, (uint32_t)(HX * HY * sizeof(T)));
+    tma_load_2d(tile, &tin, &bar, cx0, cy0);
+  }
+  const int x = threadIdx.x & 63, y0 = (threadIdx.x >> 6) * 8;
+  const int i = cx0 + x;
+  uint8_t cv[8];
+  T rv[8];
+#pragma unroll
+  for (int k = 0; k < 8; ++k) {
+    const int j = cy0 + y0 + k;
+    const long p = (long)(j + 2) * a.pitch + (i + 2);
+    const bool in = i < a.nx && j < a.ny;
+    cv[k] = in ? a.cls[p] : (uint8_t)0;
+    rv[k] = in ? a.r[p] : (T)0;
+  }
+  if (!tile_wait(&bar, a.err)) return;
+  if (i >= a.nx) return;
+  T w[5][5];
+#pragma unroll
+  for (int q = 0; q < 4; ++q)
+#pragma unroll
+    for (int b = 0; b < 5; ++b) w[q][b] = tile[(y0 + q) * HX + x + b];
+#pragma unroll
+  for (int k = 0; k < 8; ++k) {
+#pragma unroll
+    for (int b = 0; b < 5; ++b) w[4][b] = tile[(y0 + k + 4) * HX + x + b];
+    if (cv[k] == 1) {
+      T acc = 0;
+#pragma unroll
+      for (int q = 0; q < 5; ++q)
+#pragma unroll
+        for (int b = 0; b < 5; ++b) {
+          if (!CROSS && q != 2 && b != 2) continue;
+          acc += S.w[q * 5 + b] * w[q][b];
+        }
+      const long p = (long)(cy0 + y0 + k + 2) * a.pitch + (i + 2);
+      a.u_new[p] = w[2][2] + S.omega_d * (rv[k] - acc);
+    }
+#pragma unroll
+    for (int q = 0; q < 4; ++q)
+#pragma unroll
+      for (int b = 0; b < 5; ++b) w[q][b] = w[q + 1][b];
+  }
+}
+
+__device__ __forceinline__ void bulk_load(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                   smem_u32(dst)),
+               "l"(src), "r"(bytes), "r"(smem_u32(bar))
+               : "memory");
+}
+
+// SMO-2 blocks of a sweep as their own kernel (a parallel branch beside the regular-cell
+// sweep): the block's rows of inv(L22[ext, ext]) arrive in shared memory by one bulk copy
+// while the residuals of the extended rows are computed from the old iterate.
+template <typename T>
+__global__ void __launch_bounds__(256) k_blocks(SweepArgs<T> a) {
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  __shared__ __align__(8) uint64_t bar;
+  __shared__ T part[8][32];
+  const int b = blockIdx.x / a.chunks, chunk = blockIdx.x % a.chunks;
+  const int cs = a.blk[4 * b], ce = a.blk[4 * b + 1], es = a.blk[4 * b + 2], ee = a.blk[4 * b + 3];
+  const int ne = ee - es, nc = ce - cs;
+  const int c0 = chunk * a.rows_per_cta;
+  if (c0 >= nc) return;
+  T* As = reinterpret_cast<T*>(smem_raw);                       // [ne][nc]
+  const uint32_t abytes = (uint32_t)(((long)ne * nc * sizeof(T) + 15) & ~15L);
+  T* s = reinterpret_cast<T*>(smem_raw + abytes);               // [ne]
+  if (threadIdx.x == 0) mbar_init(&bar, 1);
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    mbar_expect_tx(&bar, abytes);
+    bulk_load(As, a.inv + a.blk_off[b], abytes, &bar);
+  }
+  for (int e = threadIdx.x; e < ne; e += blockDim.x) {
+    const int row = es + e;
+    T acc = 0;
+#pragma unroll
+    for (int k = 0; k < 15; ++k) acc += a.val[(long)k * a.n2 + row] * a.u_old[a.col[(long)k * a.n2 + row]];
+    s[e] = a.r[a.cell[row]] - acc;
+  }
+  const bool ok = tile_wait(&bar, a.err);
+  __syncthreads();
+  if (!ok) return;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  const int cend = min(nc, c0 + a.rows_per_cta);
+  for (int cb = c0; cb < cend; cb += 32) {
+    const int c = cb + lane;
+    T acc = 0;
+    if (c < cend)
+      for (int e = warp; e < ne; e += nw) acc += As[e * nc + c] * s[e];
+    part[warp][lane] = acc;
+    __syncthreads();
+    if (warp == 0 && c < cend) {
+      T tot = 0;
+      for (int w = 0; w < nw; ++w) tot += part[w][lane];
+      const long q = a.cell[cs + c];
+      a.u_new[q] = a.u_old[q] + tot;
+    }
+    __syncthreads();
+  }
+}
+
+// TMA-staged residual + restriction: a 64 x 32 tile of fine cells (with its halo) gives the
+// residuals of all its cells in shared memory (regular cells by the stencil, irregular cells
+// by their fitted rows), then the 32 x 16 coarse cells it covers get the volume-weighted
+// restriction and a zero coarse iterate.
+template <typename T, bool CROSS>
+__global__ void __launch_bounds__(256) k_restrict_tma(const __grid_constant__ CUtensorMap tin,
+                                                      const int32_t* __restrict__ tiles, int nxf, int nyf,
+                                                      int pitchf, const uint8_t* __restrict__ clsf,
+                                                      const T* __restrict__ volf, const int32_t* __restrict__ rowmap,
+                                                      int n2, const int32_t* __restrict__ col,
+                                                      const T* __restrict__ val, const T* __restrict__ u,
+                                                      const T* __restrict__ r, int nxc, int nyc, int pitchc,
+                                                      const uint8_t* __restrict__ clsc, T* __restrict__ rc,
+                                                      T* __restrict__ uc, Stencil<T> S, int* __restrict__ err) {
+  __shared__ __align__(128) T tile[HY * HX];
+  __shared__ T wres[JY][JX];     // volume x residual of every fine cell of the tile
+  __shared__ __align__(8) uint64_t bar;
+  const int cx0 = tiles[2 * blockIdx.x] * JX, cy0 = tiles[2 * blockIdx.x + 1] * JY;
+  if (threadIdx.x == 0) mbar_init(&bar, 1);
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    mbar_expect_tx(&bar, (uint32_t)(HX * HY * sizeof(T)));
+    tma_load_2d(tile, &tin, &bar, cx0, cy0);
+  }
+  const int x = threadIdx.x & 63, y0 = (threadIdx.x >> 6) * 8;
+  const int i = cx0 + x;
+  uint8_t cv[8];
+  T rv[8], vv[8];
+#pragma unroll
+  for (int k = 0; k < 8; ++k) {
+    const int j = cy0 + y0 + k;
+    const long p = (long)(j + 2) * pitchf + (i + 2);
+    const bool in = i < nxf && j < nyf;
+    cv[k] = in ? clsf[p] : (uint8_t)0;
+    rv[k] = in ? r[p] : (T)0;
+    vv[k] = in ? volf[p] : (T)0;
+  }
+  const bool ok = tile_wait(&bar, err);
+  if (ok) {
+    T w[5][5];
+#pragma unroll
+    for (int q = 0; q < 4; ++q)
+#pragma unroll
+      for (int b = 0; b < 5; ++b) w[q][b] = tile[(y0 + q) * HX + x + b];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+#pragma unroll
+      for (int b = 0; b < 5; ++b) w[4][b] = tile[(y0 + k + 4) * HX + x + b];
+      T res = 0;
+      if (cv[k] == 1) {
+        T acc = 0;
+#pragma unroll
+        for (int q = 0; q < 5; ++q)
+#pragma unroll
+          for (int b = 0; b < 5; ++b) {
+            if (!CROSS && q != 2 && b != 2) continue;
+            acc += S.w[q * 5 + b] * w[q][b];
+          }
+        res = rv[k] - acc;
+      } else if (cv[k] == 2) {
+        const long p = (long)(cy0 + y0 + k + 2) * pitchf + (i + 2);
+        const int row = rowmap[p];
+        T acc = 0;
+#pragma unroll
+        for (int m = 0; m < 15; ++m) acc += val[(long)m * n2 + row] * u[col[(long)m * n2 + row]];
+        res = rv[k] - acc;
+      }
+      wres[y0 + k][x] = vv[k] * res;
+#pragma unroll
+      for (int q = 0; q < 4; ++q)
+#pragma unroll
+        for (int b = 0; b < 5; ++b) w[q][b] = w[q + 1][b];
+    }
+  }
+  __syncthreads();
+  if (!ok) return;
+  // 32 x 16 coarse cells, two per thread
+  for (int t = threadIdx.x; t < (JX / 2) * (JY / 2); t += blockDim.x) {
+    const int ci = t % (JX / 2), cj = t / (JX / 2);
+    const int I = cx0 / 2 + ci, J = cy0 / 2 + cj;
+    if (I >= nxc || J >= nyc) continue;
+    const long pc = (long)(J + 2) * pitchc + (I + 2);
+    if (clsc[pc] == 0) continue;
+    const T s = wres[2 * cj][2 * ci] + wres[2 * cj][2 * ci + 1] + wres[2 * cj + 1][2 * ci] + wres[2 * cj + 1][2 * ci + 1];
+    const long f0 = (long)(2 * J + 2) * pitchf + (2 * I + 2);
+    const T sv = volf[f0] + volf[f0 + 1] + volf[f0 + pitchf] + volf[f0 + pitchf + 1];
+    rc[pc] = sv > (T)0 ? (T)4 * s / sv : (T)0;
+    uc[pc] = (T)0;
+  }
+}
+
+// residual + restriction in one launch: every child's residual is computed here (regular
+// children by the stencil, irregular children by their fitted row through rowmap)
+template <typename T, bool CROSS>
+__global__ void k_restrict_rows(int nxc, int nyc, int pitchc, int pitchf, const uint8_t* __restrict__ clsc,
+                                const uint8_t* __restrict__ clsf, const T* __restrict__ volf,
+                                const int32_t* __restrict__ rowmap, int n2, const int32_t* __restrict__ col,
+                                const T* __restrict__ val, const T* __restrict__ u, const T* __restrict__ r,
+                                T* __restrict__ rc, T* __restrict__ uc, Stencil<T> S) {
+  int I = blockIdx.x * blockDim.x + threadIdx.x;
+  int J = blockIdx.y * blockDim.y + threadIdx.y;
+  if (I >= nxc || J >= nyc) return;
+  long pc = (long)(J + 2) * pitchc + (I + 2);
+  if (clsc[pc] == 0) return;
+  long f0 = (long)(2 * J + 2) * pitchf + (2 * I + 2);
+  T s = 0, sv = 0;
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    long q = f0 + (k >> 1) * (long)pitchf + (k & 1);
+    uint8_t c = clsf[q];
+    if (c == 0) continue;
+    T Lu;
+    if (c == 1) {
+      Lu = stencil_apply<T, CROSS>(u, q, pitchf, S);
+    } else {
+      const int row = rowmap[q];
+      Lu = 0;
+#pragma unroll
+      for (int m = 0; m < 15; ++m) Lu += val[(long)m * n2 + row] * u[col[(long)m * n2 + row]];
+    }
+    T v = volf[q];
+    s += v * (r[q] - Lu);
+    sv += v;
+  }
+  rc[pc] = sv > (T)0 ? (T)4 * s / sv : (T)0;
+  uc[pc] = (T)0;
+}
+
 // SMO-1 with the prolongation fused in (first post-smoothing sweep after Alg. 2's
 // "Prolong the correction"): v = u + P uc on regular cells, then u_out = v + omega D^-1 (r - L v)
 // on regular cells.  Irregular cells are left to the SMO-2 kernel that follows.
@@ -160,47 +584,57 @@ __global__ void k_jacobi2(const int32_t* __restrict__ tiles, const uint8_t* __re
   u_out[p] = vp + S.omega_d * (r[p] - acc);
 }
 
-// SMO-2 fused with the residual of the fitted rows: the residual of row e uses the new
-// regular values (u_new, written by SMO-1) and the old irregular values (u_old); the core
-// rows of the block then get u_new = u_old + inv(L22[ext, ext])[core, :] res[ext].  Every
-// irregular cell is the core of exactly one block, and no kernel writes what it reads.
+// SMO-2 fused with the residual of the fitted rows.  Rows are numbered in the boundary
+// order, so block b owns the contiguous core rows [cs, ce) and reads the extended range
+// [es, ee).  The residual of a row uses the new regular values (u_new, written by SMO-1;
+// flagged columns) and the old irregular values (u_old); the core rows then get
+// u_new = u_old + inv(L22[ext, ext])[core, :] res[ext].  Every irregular cell is the core of
+// exactly one block and no kernel writes what it reads.  One CTA of 256 threads per block
+// (blockIdx.y splits the core rows only for the single exact block of a small level).
 template <typename T>
-__global__ void k_block_fused(const int32_t* __restrict__ order, const int32_t* __restrict__ blk,
-                              const int64_t* __restrict__ blk_off, const T* __restrict__ inv,
-                              int n2, const int32_t* __restrict__ cell, const int32_t* __restrict__ col,
-                              const T* __restrict__ val, const uint8_t* __restrict__ cls,
-                              const T* __restrict__ r, const T* __restrict__ u_old, T* __restrict__ u_new) {
+__global__ void __launch_bounds__(256) k_block_fused(const int32_t* __restrict__ blk,
+                                                     const int64_t* __restrict__ blk_off, const T* __restrict__ inv,
+                                                     int n2, const int32_t* __restrict__ cell,
+                                                     const int32_t* __restrict__ colf, const T* __restrict__ val,
+                                                     const T* __restrict__ r, const T* __restrict__ u_old,
+                                                     T* __restrict__ u_new, int rows_per_cta) {
   extern __shared__ unsigned char smem_raw[];
   T* s = reinterpret_cast<T*>(smem_raw);
-  __shared__ T part[4][32];
+  __shared__ T part[8][32];
   const int b = blockIdx.x;
   const int cs = blk[4 * b], ce = blk[4 * b + 1], es = blk[4 * b + 2], ee = blk[4 * b + 3];
   const int ne = ee - es, nc = ce - cs;
-  const int c0 = blockIdx.y * 32;
+  const int c0 = blockIdx.y * rows_per_cta;
   if (c0 >= nc) return;
   for (int e = threadIdx.x; e < ne; e += blockDim.x) {
-    int row = order[es + e];
+    const int row = es + e;
     T acc = 0;
 #pragma unroll
     for (int k = 0; k < 15; ++k) {
-      int q = col[(long)k * n2 + row];
-      T v = cls[q] == 1 ? u_new[q] : u_old[q];
-      acc += val[(long)k * n2 + row] * v;
+      const int f = colf[(long)k * n2 + row];
+      const int q = f & 0x7fffffff;
+      acc += val[(long)k * n2 + row] * (f < 0 ? u_new[q] : u_old[q]);
     }
     s[e] = r[cell[row]] - acc;
   }
   __syncthreads();
   const T* A = inv + blk_off[b];
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int c = c0 + lane;
-  T acc = 0;
-  if (c < nc)
-    for (int e = warp; e < ne; e += 4) acc += A[(long)e * nc + c] * s[e];
-  part[warp][lane] = acc;
-  __syncthreads();
-  if (warp == 0 && c < nc) {
-    long q = cell[order[cs + c]];
-    u_new[q] = u_old[q] + part[0][lane] + part[1][lane] + part[2][lane] + part[3][lane];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  const int cend = min(nc, c0 + rows_per_cta);
+  for (int cb = c0; cb < cend; cb += 32) {
+    const int c = cb + lane;
+    T acc = 0;
+    if (c < cend)
+      for (int e = warp; e < ne; e += nw) acc += A[(long)e * nc + c] * s[e];
+    part[warp][lane] = acc;
+    __syncthreads();
+    if (warp == 0 && c < cend) {
+      T tot = 0;
+      for (int w = 0; w < nw; ++w) tot += part[w][lane];
+      const long q = cell[cs + c];
+      u_new[q] = u_old[q] + tot;
+    }
+    __syncthreads();
   }
 }
 
@@ -283,6 +717,173 @@ __global__ void k_bottom(int n, const int32_t* __restrict__ cell, const T* __res
     T tot = 0;
     for (int w = 0; w < nw; ++w) tot += part[w * 32 + threadIdx.x];
     u[cell[k]] = tot;
+  }
+}
+
+// ---- the small levels of a V-cycle in one CTA.
+// Levels with few cells spend their time in launch latency, not in work, so the part of
+// Alg. 2 from level `first` down to the bottom and back runs as one CTA of 1024 threads with
+// __syncthreads() between the phases (SMO-1, SMO-2 residuals, SMO-2 block corrections,
+// residual + restriction, bottom solve, prolongation fused into SMO-1).
+constexpr int MAXC = 8;
+
+template <typename T>
+struct CoarseLevel {
+  int nx, ny, pitch, n2, nblk, nbc, core;
+  const uint8_t* cls;
+  const T* vol;
+  T* u[2];
+  T* r;
+  T* t;
+  T* res;
+  const int32_t* irr_cell;
+  const int32_t* colf;
+  const T* val;
+  const int32_t* blk;
+  const int64_t* blk_off;
+  const T* inv;
+  const int32_t* bot_cell;
+  const T* bot;
+};
+
+template <typename T>
+struct CoarseParams {
+  int nlev, nu1, nu2, passes, jacobi;
+  int cur[MAXC];
+  CoarseLevel<T> L[MAXC];
+  Stencil<T> S;
+};
+
+template <typename T, bool CROSS>
+__device__ void cta_sweep(const CoarseLevel<T>& L, int& cur, const Stencil<T>& S, int passes, const T* uc, int pitchc,
+                          bool jacobi) {
+  T* uin = L.u[cur];
+  T* uout = L.u[1 - cur];
+  if (jacobi && uc) {
+    // prolongation first (regular cells of the old iterate), then the block-Jacobi sweep
+    const int n = L.nx * L.ny;
+    for (int idx = threadIdx.x; idx < n; idx += blockDim.x) {
+      const int i = idx % L.nx, j = idx / L.nx;
+      const long p = (long)(j + 2) * L.pitch + (i + 2);
+      if (L.cls[p] == 1) uin[p] += uc[(long)(j / 2 + 2) * pitchc + (i / 2 + 2)];
+    }
+    __syncthreads();
+    uc = nullptr;
+  }
+  const int n = L.nx * L.ny;
+  for (int idx = threadIdx.x; idx < n; idx += blockDim.x) {
+    const int i = idx % L.nx, j = idx / L.nx;
+    const long p = (long)(j + 2) * L.pitch + (i + 2);
+    if (L.cls[p] != 1) continue;
+    T acc = 0, vp = 0;
+#pragma unroll
+    for (int dj = -2; dj <= 2; ++dj)
+#pragma unroll
+      for (int di = -2; di <= 2; ++di) {
+        if (!CROSS && dj != 0 && di != 0) continue;
+        const long q = p + (long)dj * L.pitch + di;
+        T v = uin[q];
+        if (uc && L.cls[q] == 1) v += uc[(long)((j + dj) / 2 + 2) * pitchc + ((i + di) / 2 + 2)];
+        acc += S.w[(dj + 2) * 5 + di + 2] * v;
+        if (dj == 0 && di == 0) vp = v;
+      }
+    uout[p] = vp + S.omega_d * (L.r[p] - acc);
+  }
+  __syncthreads();
+  for (int pass = 0; pass < max(1, passes); ++pass) {
+    const T* rd_irr = pass == 0 ? uin : uout;
+    const T* rd_reg = (jacobi && pass == 0) ? uin : uout;
+    for (int row = threadIdx.x; row < L.n2; row += blockDim.x) {
+      T acc = 0;
+#pragma unroll
+      for (int k = 0; k < 15; ++k) {
+        const int f = L.colf[(long)k * L.n2 + row];
+        const int q = f & 0x7fffffff;
+        acc += L.val[(long)k * L.n2 + row] * (f < 0 ? rd_reg[q] : rd_irr[q]);
+      }
+      L.res[row] = L.r[L.irr_cell[row]] - acc;
+    }
+    __syncthreads();
+    for (int c = threadIdx.x; c < L.n2; c += blockDim.x) {
+      const int b = min(c / L.core, L.nblk - 1);
+      const int cs = L.blk[4 * b], ce = L.blk[4 * b + 1], es = L.blk[4 * b + 2], ee = L.blk[4 * b + 3];
+      const int nc = ce - cs;
+      const T* A = L.inv + L.blk_off[b];
+      T acc = 0;
+      for (int e = es; e < ee; ++e) acc += A[(long)(e - es) * nc + (c - cs)] * L.res[e];
+      const long q = L.irr_cell[c];
+      uout[q] = rd_irr[q] + acc;
+    }
+    __syncthreads();
+  }
+  cur = 1 - cur;
+}
+
+template <typename T, bool CROSS>
+__global__ void __launch_bounds__(1024) k_coarse_vcycle(CoarseParams<T> P) {
+  int cur[MAXC];
+#pragma unroll
+  for (int m = 0; m < MAXC; ++m) cur[m] = P.cur[m];
+  const int last = P.nlev - 1;
+  for (int m = 0; m < last; ++m) {
+    const CoarseLevel<T>& F = P.L[m];
+    const CoarseLevel<T>& C = P.L[m + 1];
+    for (int k = 0; k < P.nu1; ++k) cta_sweep<T, CROSS>(F, cur[m], P.S, P.passes, nullptr, 0, P.jacobi);
+    // residual of the fitted rows into t, then residual + restriction, coarse u = 0
+    T* u = F.u[cur[m]];
+    for (int row = threadIdx.x; row < F.n2; row += blockDim.x) {
+      T acc = 0;
+#pragma unroll
+      for (int k = 0; k < 15; ++k) acc += F.val[(long)k * F.n2 + row] * u[F.colf[(long)k * F.n2 + row] & 0x7fffffff];
+      F.t[F.irr_cell[row]] = F.r[F.irr_cell[row]] - acc;
+    }
+    __syncthreads();
+    T* ucz = C.u[cur[m + 1]];
+    for (int idx = threadIdx.x; idx < C.nx * C.ny; idx += blockDim.x) {
+      const int I = idx % C.nx, J = idx / C.nx;
+      const long pc = (long)(J + 2) * C.pitch + (I + 2);
+      if (C.cls[pc] == 0) continue;
+      const long f0 = (long)(2 * J + 2) * F.pitch + (2 * I + 2);
+      T s = 0, sv = 0;
+      for (int k = 0; k < 4; ++k) {
+        const long q = f0 + (k >> 1) * (long)F.pitch + (k & 1);
+        const uint8_t c = F.cls[q];
+        if (c == 0) continue;
+        const T res = c == 1 ? F.r[q] - stencil_apply<T, CROSS>(u, q, F.pitch, P.S) : F.t[q];
+        s += F.vol[q] * res;
+        sv += F.vol[q];
+      }
+      C.r[pc] = sv > (T)0 ? (T)4 * s / sv : (T)0;
+      ucz[pc] = (T)0;
+    }
+    __syncthreads();
+  }
+  {
+    const CoarseLevel<T>& B = P.L[last];
+    T* u = B.u[cur[last]];
+    for (int k = threadIdx.x; k < B.nbc; k += blockDim.x) {
+      T acc = 0;
+      for (int c = 0; c < B.nbc; ++c) acc += B.bot[(long)c * B.nbc + k] * B.r[B.bot_cell[c]];
+      u[B.bot_cell[k]] = acc;
+    }
+    __syncthreads();
+  }
+  for (int m = last - 1; m >= 0; --m) {
+    const CoarseLevel<T>& F = P.L[m];
+    const CoarseLevel<T>& C = P.L[m + 1];
+    if (P.nu2 == 0) {
+      T* u = F.u[cur[m]];
+      const T* uc = C.u[cur[m + 1]];
+      for (int idx = threadIdx.x; idx < F.nx * F.ny; idx += blockDim.x) {
+        const int i = idx % F.nx, j = idx / F.nx;
+        const long p = (long)(j + 2) * F.pitch + (i + 2);
+        if (F.cls[p] == 1) u[p] += uc[(long)(j / 2 + 2) * C.pitch + (i / 2 + 2)];
+      }
+      __syncthreads();
+      continue;
+    }
+    cta_sweep<T, CROSS>(F, cur[m], P.S, P.passes, C.u[cur[m + 1]], C.pitch, P.jacobi);
+    for (int k = 1; k < P.nu2; ++k) cta_sweep<T, CROSS>(F, cur[m], P.S, P.passes, nullptr, 0, P.jacobi);
   }
 }
 

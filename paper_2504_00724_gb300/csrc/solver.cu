@@ -10,7 +10,9 @@
 #include <string>
 #include <vector>
 
+#include <cuda.h>
 #include <cuda_runtime.h>
+#include <cudaTypedefs.h>
 
 #include "hierarchy.h"
 #include "kernels.cuh"
@@ -25,10 +27,17 @@ struct DevLevel {
   double h = 0;
   int max_ext = 0, max_core = 0;
   int32_t* tiles = nullptr;
+  int ntiles64 = 0;
+  int32_t* tiles64 = nullptr;
+  int ntiles64r = 0;            // fine 64 x 32 tiles that restriction to level m + 1 visits
+  int32_t* tiles64r = nullptr;
+  bool stage_blocks = false;    // SMO-2 block inverses fit in shared memory (bulk-staged kernel)
+  bool tma = false;             // TMA-staged SMO-1 on this level
+  CUtensorMap tm64[2], tm32[2]; // 68 x 36 boxes over the u buffers
   uint8_t* cls = nullptr;
   double* vol64 = nullptr;
   float* vol32 = nullptr;
-  int32_t *irr_cell = nullptr, *ell_col = nullptr, *seg = nullptr;
+  int32_t *irr_cell = nullptr, *ell_col = nullptr, *ell_colf = nullptr, *seg = nullptr, *rowmap = nullptr;
   double *ell64 = nullptr, *nb = nullptr;
   float* ell32 = nullptr;
   int32_t *order = nullptr, *blk = nullptr;
@@ -49,6 +58,9 @@ struct DevLevel {
 template <typename T> T* U(DevLevel& L);
 template <> double* U<double>(DevLevel& L) { return L.u64[L.cur64]; }
 template <> float* U<float>(DevLevel& L) { return L.u32[L.cur32]; }
+template <typename T> const CUtensorMap& TmU(const DevLevel& L);
+template <> const CUtensorMap& TmU<double>(const DevLevel& L) { return L.tm64[L.cur64]; }
+template <> const CUtensorMap& TmU<float>(const DevLevel& L) { return L.tm32[L.cur32]; }
 template <typename T> T* Uother(DevLevel& L);
 template <> double* Uother<double>(DevLevel& L) { return L.u64[1 - L.cur64]; }
 template <> float* Uother<float>(DevLevel& L) { return L.u32[1 - L.cur32]; }
@@ -115,6 +127,8 @@ struct ccm_handle {
   Arena arena;
   dev::Stencil<double> S64{};
   dev::Stencil<float> S32{};
+  int* derr = nullptr;         // device error word (bounded waits that ran out)
+  int* herr = nullptr;         // pinned copy
   double* rhat = nullptr;      // level-0 padded FP64 right-hand side (h^2-scaled)
   double* uhat = nullptr;      // level-0 padded FP64 solution
   unsigned long long* dnorm = nullptr;
@@ -128,9 +142,12 @@ struct ccm_handle {
   std::vector<cudaEvent_t> gprof_ev;  // pairs baked into the iteration graphs
   double prof_ms = 0;                 // accumulated from graph replays
   long long prof_n = 0;
+  int coarse_first = 1 << 30;  // first level run by the one-CTA coarse cycle (FP32)
   // one CUDA graph per outer iteration and precision (captured on first use, on a private
   // stream: the legacy default stream cannot be captured)
   cudaStream_t cap_stream = nullptr;
+  cudaStream_t side = nullptr;          // second stream: SMO-2 blocks beside the regular sweep
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
   bool capturing = false;
   long long cap_launches = 0;
   struct Graph {
@@ -230,15 +247,86 @@ void residual(ccm_handle* H, DevLevel& L, const T* u, const T* r, T* out, cudaSt
 // one smoother step: SMO-1 on the regular cells, then SMO-2 on the irregular cells.
 // uc != nullptr fuses the prolongation u += P uc into the SMO-1 sweep (regular cells).
 template <typename T>
+void prolong_from(ccm_handle* H, DevLevel& F, DevLevel& C, cudaStream_t s);
+
+// block-Jacobi form: SMO-1 and SMO-2 both from the old iterate, one launch
+template <typename T>
+void sweep_one_launch(ccm_handle* H, DevLevel& L, cudaStream_t s) {
+  dev::SweepArgs<T> a{};
+  const bool tma = L.tma;
+  a.tiles = tma ? L.tiles64 : L.tiles;
+  a.ntiles = tma ? L.ntiles64 : L.ntiles;
+  a.nblk = L.nblk;
+  a.rows_per_cta = L.nblk >= 16 ? std::max(1, L.max_core) : 64;
+  a.chunks = L.nblk ? ceil_div(std::max(1, L.max_core), a.rows_per_cta) : 0;
+  a.cls = L.cls;
+  a.nx = L.nx;
+  a.ny = L.ny;
+  a.pitch = L.pitch;
+  a.n2 = L.n2;
+  a.r = R<T>(L);
+  a.u_old = U<T>(L);
+  a.u_new = Uother<T>(L);
+  a.S = stencil<T>(H);
+  a.blk = L.blk;
+  a.blk_off = L.blk_off;
+  a.inv = Inv<T>(L);
+  a.cell = L.irr_cell;
+  a.col = L.ell_col;
+  a.val = Ell<T>(L);
+  a.err = H->derr;
+  const bool l0 = &L == &H->L[0];
+  ProfScope ps(H, !l0 ? 0 : (sizeof(T) == 4 ? CCM_PROF_SMO1_FP32 : CCM_PROF_SMO1_FP64), s);
+  if (L.stage_blocks && a.nblk) {
+    // SMO-2 blocks on the side stream, regular cells here; join before the next phase
+    dev::SweepArgs<T> b = a;
+    b.ntiles = 0;
+    b.tiles = nullptr;
+    a.nblk = 0;
+    cudaEventRecord(H->ev_fork, s);
+    cudaStreamWaitEvent(H->side, H->ev_fork, 0);
+    const size_t bsm = (((size_t)L.max_ext * L.max_core * sizeof(T) + 15) & ~(size_t)15) + L.max_ext * sizeof(T);
+    KL(dev::k_blocks<T><<<b.nblk * b.chunks, 256, bsm, H->side>>>(b));
+    cudaEventRecord(H->ev_join, H->side);
+  }
+  const int grid = a.ntiles + a.nblk * a.chunks;
+  const size_t smem = (size_t)std::max(1, L.max_ext) * sizeof(T);
+  const CUtensorMap& tm = TmU<T>(L);
+  if (grid == 0) {
+    if (L.stage_blocks && L.nblk) cudaStreamWaitEvent(s, H->ev_join, 0);
+    return;
+  }
+  if (tma) {
+    if (H->cross) KL(dev::k_sweep<T, true, true><<<grid, 256, smem, s>>>(tm, a));
+    else KL(dev::k_sweep<T, false, true><<<grid, 256, smem, s>>>(tm, a));
+  } else {
+    if (H->cross) KL(dev::k_sweep<T, true, false><<<grid, 256, smem, s>>>(tm, a));
+    else KL(dev::k_sweep<T, false, false><<<grid, 256, smem, s>>>(tm, a));
+  }
+  if (L.stage_blocks && L.nblk) cudaStreamWaitEvent(s, H->ev_join, 0);
+}
+
+template <typename T>
 void smooth_step(ccm_handle* H, DevLevel& L, cudaStream_t s, const T* uc = nullptr, int pitchc = 0) {
+  if (H->par.smoother == 1 && H->par.ras_passes <= 1) {
+    if (uc) prolong_from<T>(H, L, H->L[&L - &H->L[0] + 1], s);
+    sweep_one_launch<T>(H, L, s);
+    flip<T>(L);
+    return;
+  }
   T* uin = U<T>(L);
   T* uout = Uother<T>(L);
   const T* r = R<T>(L);
   if (L.ntiles) {
     dim3 blk(dev::TX, dev::TY);
     const auto& S = stencil<T>(H);
-    ProfScope ps(H, (&L == &H->L[0]) ? (sizeof(T) == 4 ? CCM_PROF_SMO1_FP32 : CCM_PROF_SMO1_FP64) : 0, s);
-    if (uc) {
+    const bool l0 = &L == &H->L[0];
+    ProfScope ps(H, !l0 ? 0 : uc ? (sizeof(T) == 4 ? CCM_PROF_PROLONG_SMO1_FP32 : 0)
+                              : (sizeof(T) == 4 ? CCM_PROF_SMO1_FP32 : CCM_PROF_SMO1_FP64), s);
+    if (!uc && L.tma) {
+      if (H->cross) KL(dev::k_jacobi_tma<T, true><<<L.ntiles64, 256, 0, s>>>(TmU<T>(L), L.tiles64, L.cls, L.nx, L.ny, L.pitch, r, uout, S, H->derr));
+      else KL(dev::k_jacobi_tma<T, false><<<L.ntiles64, 256, 0, s>>>(TmU<T>(L), L.tiles64, L.cls, L.nx, L.ny, L.pitch, r, uout, S, H->derr));
+    } else if (uc) {
       if (H->cross) KL(dev::k_jacobi2<T, true, true><<<L.ntiles, blk, 0, s>>>(L.tiles, L.cls, L.nx, L.ny, L.pitch, pitchc, uin, uc, uout, r, S));
       else KL(dev::k_jacobi2<T, false, true><<<L.ntiles, blk, 0, s>>>(L.tiles, L.cls, L.nx, L.ny, L.pitch, pitchc, uin, uc, uout, r, S));
     } else {
@@ -247,9 +335,12 @@ void smooth_step(ccm_handle* H, DevLevel& L, cudaStream_t s, const T* uc = nullp
     }
   }
   if (L.n2) {
-    dim3 grd(L.nblk, ceil_div(L.max_core, 32));
-    KL(dev::k_block_fused<T><<<grd, 128, L.max_ext * sizeof(T), s>>>(L.order, L.blk, L.blk_off, Inv<T>(L), L.n2,
-                                                                  L.irr_cell, L.ell_col, Ell<T>(L), L.cls, r, uin, uout));
+    ProfScope ps(H, (&L == &H->L[0] && sizeof(T) == 4) ? CCM_PROF_SMO2_FP32 : 0, s);
+    // many blocks: one CTA each; one big exact block: split its core rows over CTAs
+    const int rpc = L.nblk >= 16 ? L.max_core : 64;
+    dim3 grd(L.nblk, ceil_div(L.max_core, rpc));
+    KL(dev::k_block_fused<T><<<grd, 256, L.max_ext * sizeof(T), s>>>(L.blk, L.blk_off, Inv<T>(L), L.n2, L.irr_cell,
+                                                                  L.ell_colf, Ell<T>(L), r, uin, uout, rpc));
   }
   flip<T>(L);
   T* u = U<T>(L);
@@ -265,6 +356,30 @@ void smooth_step(ccm_handle* H, DevLevel& L, cudaStream_t s, const T* uc = nullp
 // residual, restriction and zeroing of the coarse iterate
 template <typename T>
 void restrict_to(ccm_handle* H, DevLevel& F, DevLevel& C, cudaStream_t s) {
+  ProfScope ps(H, (&F == &H->L[0] && sizeof(T) == 4) ? CCM_PROF_RESTRICT_FP32 : 0, s);
+  if (H->par.smoother == 1 && F.tma && F.ntiles64r) {
+    const auto& S = stencil<T>(H);
+    if (H->cross)
+      KL(dev::k_restrict_tma<T, true><<<F.ntiles64r, 256, 0, s>>>(TmU<T>(F), F.tiles64r, F.nx, F.ny, F.pitch, F.cls, Vol<T>(F),
+                                                                 F.rowmap, F.n2, F.ell_col, Ell<T>(F), U<T>(F), R<T>(F),
+                                                                 C.nx, C.ny, C.pitch, C.cls, R<T>(C), U<T>(C), S, H->derr));
+    else
+      KL(dev::k_restrict_tma<T, false><<<F.ntiles64r, 256, 0, s>>>(TmU<T>(F), F.tiles64r, F.nx, F.ny, F.pitch, F.cls, Vol<T>(F),
+                                                                  F.rowmap, F.n2, F.ell_col, Ell<T>(F), U<T>(F), R<T>(F),
+                                                                  C.nx, C.ny, C.pitch, C.cls, R<T>(C), U<T>(C), S, H->derr));
+    return;
+  }
+  if (H->par.smoother == 1) {
+    dim3 blk(32, 8), grd(ceil_div(C.nx, 32), ceil_div(C.ny, 8));
+    const auto& S = stencil<T>(H);
+    if (H->cross)
+      KL(dev::k_restrict_rows<T, true><<<grd, blk, 0, s>>>(C.nx, C.ny, C.pitch, F.pitch, C.cls, F.cls, Vol<T>(F), F.rowmap,
+                                                         F.n2, F.ell_col, Ell<T>(F), U<T>(F), R<T>(F), R<T>(C), U<T>(C), S));
+    else
+      KL(dev::k_restrict_rows<T, false><<<grd, blk, 0, s>>>(C.nx, C.ny, C.pitch, F.pitch, C.cls, F.cls, Vol<T>(F), F.rowmap,
+                                                          F.n2, F.ell_col, Ell<T>(F), U<T>(F), R<T>(F), R<T>(C), U<T>(C), S));
+    return;
+  }
   if (F.n2)
     KL(dev::k_rows<T, T, true, true><<<ceil_div(F.n2, 128), 128, 0, s>>>(F.n2, F.irr_cell, F.ell_col, Ell<T>(F), U<T>(F),
                                                                       R<T>(F), Tmp<T>(F), nullptr, nullptr, nullptr));
@@ -292,6 +407,33 @@ void bottom(ccm_handle* H, DevLevel& B, cudaStream_t s) {
   KL(dev::k_bottom<T><<<ceil_div(B.nbc, 32), nw * 32, sm, s>>>(B.nbc, B.bot_cell, Bot<T>(B), R<T>(B), U<T>(B)));
 }
 
+// the levels from m down run in one CTA (FP32 cycles, levels with at most 64 cells a side)
+void coarse_cta(ccm_handle* H, int m, cudaStream_t s) {
+  const int M = (int)H->L.size() - 1;
+  dev::CoarseParams<float> P{};
+  P.nlev = M - m + 1;
+  P.nu1 = H->par.nu1;
+  P.nu2 = H->par.nu2;
+  P.passes = H->par.ras_passes;
+  P.jacobi = H->par.smoother == 1 && H->par.ras_passes <= 1;
+  P.S = H->S32;
+  for (int k = 0; k < P.nlev; ++k) {
+    DevLevel& L = H->L[m + k];
+    dev::CoarseLevel<float>& C = P.L[k];
+    C.nx = L.nx; C.ny = L.ny; C.pitch = L.pitch; C.n2 = L.n2; C.nblk = L.nblk; C.nbc = L.nbc;
+    C.core = L.max_core > 0 ? L.max_core : 1;
+    C.cls = L.cls; C.vol = L.vol32; C.u[0] = L.u32[0]; C.u[1] = L.u32[1]; C.r = L.r32; C.t = L.t32;
+    C.res = L.res32; C.irr_cell = L.irr_cell; C.colf = L.ell_colf; C.val = L.ell32; C.blk = L.blk;
+    C.blk_off = L.blk_off; C.inv = L.inv32; C.bot_cell = L.bot_cell; C.bot = L.bot32;
+    P.cur[k] = L.cur32;
+  }
+  if (H->cross) KL(dev::k_coarse_vcycle<float, true><<<1, 1024, 0, s>>>(P));
+  else KL(dev::k_coarse_vcycle<float, false><<<1, 1024, 0, s>>>(P));
+  const int flips = H->par.nu2 > 0 ? H->par.nu1 + H->par.nu2 : H->par.nu1;
+  for (int k = 0; k + 1 < P.nlev; ++k)
+    if (flips & 1) flip<float>(H->L[m + k]);
+}
+
 // Alg. 2 from level m: solves L^(m) u = r^(m) approximately, u = U<T>(level m)
 template <typename T>
 void vcycle(ccm_handle* H, int m, cudaStream_t s) {
@@ -299,6 +441,10 @@ void vcycle(ccm_handle* H, int m, cudaStream_t s) {
   DevLevel& F = H->L[m];
   if (m == M) {
     bottom<T>(H, F, s);
+    return;
+  }
+  if (sizeof(T) == 4 && m >= H->coarse_first && M - m + 1 <= dev::MAXC) {
+    coarse_cta(H, m, s);
     return;
   }
   DevLevel& C = H->L[m + 1];
@@ -338,6 +484,28 @@ void load_level(ccm_handle* h, DevLevel& L, const double* u, const double* r, cu
   if (r) KL(dev::k_pack<T, double><<<pg, 128, 0, s>>>(L.nx, L.ny, L.pitch, L.cls, r, R<T>(L), L.h * L.h));
 }
 
+// 2-D tensor map over a padded level array: box of 68 x 36 elements, zero fill outside
+bool make_tmap(CUtensorMap* map, void* base, int pitch, int rows, bool fp64) {
+  static PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
+  if (!encode) {
+    void* fn = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q) != cudaSuccess ||
+        q != cudaDriverEntryPointSuccess || !fn)
+      return false;
+    encode = (PFN_cuTensorMapEncodeTiled_v12000)fn;
+  }
+  const size_t es = fp64 ? 8 : 4;
+  cuuint64_t dims[2] = {(cuuint64_t)pitch, (cuuint64_t)rows};
+  cuuint64_t strides[1] = {(cuuint64_t)pitch * es};
+  cuuint32_t box[2] = {(cuuint32_t)dev::HX, (cuuint32_t)dev::HY};
+  cuuint32_t estr[2] = {1, 1};
+  CUresult r = encode(map, fp64 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT64 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, base, dims,
+                      strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                      CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS;
+}
+
 }  // namespace
 
 // ================================================================ C ABI
@@ -346,7 +514,7 @@ extern "C" {
 
 int ccm_default_params(ccm_params* p) {
   if (!p) return CCM_EINVAL;
-  p->omega = 0.8;
+  p->omega = 0.7;
   p->nu1 = 3;
   p->nu2 = 3;
   p->theta = 0.3;
@@ -358,8 +526,10 @@ int ccm_default_params(ccm_params* p) {
   p->ras_block = 64;
   p->ras_overlap = 32;
   p->nthreads = 0;
-  p->ras_exact = 1024;
+  p->ras_exact = 0;
   p->inner_cycles = 3;
+  p->smoother = 1;
+  p->coarse_n = 0;
   return CCM_OK;
 }
 
@@ -397,7 +567,7 @@ int ccm_setup(const ccm_problem* prob, const ccm_params* params, ccm_handle** ou
   if (params) par = *params;
   if (par.nu1 < 0 || par.nu2 < 0 || par.coarsest < 4 || par.ras_passes < 0 || par.ras_block < 8 ||
       par.ras_block > 128 || par.ras_overlap < 0 || par.ras_overlap > 64 || par.max_iter < 0 ||
-      par.ras_exact < 0 || par.ras_exact > 6000 || par.inner_cycles < 1 || par.inner_cycles > 16 ||
+      par.ras_exact < 0 || par.ras_exact > 6000 || par.inner_cycles < 1 || par.inner_cycles > 16 || par.smoother < 0 || par.smoother > 1 || par.coarse_n < 0 ||
       !(par.theta >= 0 && par.theta < 1) || (par.precision != CCM_FP64 && par.precision != CCM_MIXED))
     return CCM_EINVAL;
   auto t0 = std::chrono::steady_clock::now();
@@ -450,6 +620,12 @@ int ccm_setup(const ccm_problem* prob, const ccm_params* params, ccm_handle** ou
     if (hl.n2) {
       d.irr_cell = A.upload(hl.irr_cell);
       d.ell_col = A.upload(hl.ell_col);
+      d.ell_colf = A.upload(hl.ell_colf);
+      {
+        std::vector<int32_t> rm(hl.npad(), -1);
+        for (int r = 0; r < hl.n2; ++r) rm[hl.irr_cell[r]] = r;
+        d.rowmap = A.upload(rm);
+      }
       d.ell64 = A.upload(hl.ell_val);
       std::vector<float> f(hl.ell_val.begin(), hl.ell_val.end());
       d.ell32 = A.upload(f);
@@ -489,6 +665,8 @@ int ccm_setup(const ccm_problem* prob, const ccm_params* params, ccm_handle** ou
       d.tr_row = A.upload(hl.tr_row);
       d.tr_val = A.upload(hl.tr_val);
     }
+    d.ntiles64 = (int)hl.tiles64.size() / 2;
+    if (d.ntiles64) d.tiles64 = A.upload(hl.tiles64);
     d.u64[0] = A.alloc<double>(d.npad);
     d.u64[1] = A.alloc<double>(d.npad);
     d.r64 = A.alloc<double>(d.npad);
@@ -497,15 +675,66 @@ int ccm_setup(const ccm_problem* prob, const ccm_params* params, ccm_handle** ou
     d.u32[1] = A.alloc<float>(d.npad);
     d.r32 = A.alloc<float>(d.npad);
     d.t32 = A.alloc<float>(d.npad);
+    // TMA-staged smoothing on the large levels (base addresses come from cudaMalloc, so
+    // they are 256-byte aligned; the pitch is a multiple of 32 elements)
+    d.tma = A.err == cudaSuccess && d.ntiles64 > 0 && d.nx >= 256;
+    for (int b = 0; b < 2 && d.tma; ++b)
+      d.tma = make_tmap(&d.tm64[b], d.u64[b], d.pitch, d.rows, true) &&
+              make_tmap(&d.tm32[b], d.u32[b], d.pitch, d.rows, false);
   }
+  // SMO-2 blocks that fit in shared memory run as a bulk-staged kernel beside the sweep
+  if (cudaStreamCreateWithFlags(&h->side, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaEventCreateWithFlags(&h->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&h->ev_join, cudaEventDisableTiming) != cudaSuccess) {
+    A.release();
+    return CCM_ECUDA;
+  }
+  cudaFuncSetAttribute(dev::k_blocks<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+  cudaFuncSetAttribute(dev::k_blocks<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+  for (int m = 0; m < nl; ++m) {
+    DevLevel& d = h->L[m];
+    const size_t need = (size_t)d.max_ext * d.max_core * sizeof(double) + d.max_ext * sizeof(double) + 16;
+    d.stage_blocks = d.nblk > 0 && need <= 200 * 1024;
+    // restriction tiles: fine 64 x 32 tiles with a non-empty fine cell or a non-empty coarse cell
+    if (m + 1 < nl && d.tma) {
+      const HostLevel& hf = h->H.levels[m];
+      const HostLevel& hc = h->H.levels[m + 1];
+      std::vector<int32_t> t;
+      const int ax = (hf.nx + 63) / 64, ay = (hf.ny + 31) / 32;
+      for (int b = 0; b < ay; ++b)
+        for (int a = 0; a < ax; ++a) {
+          bool any = false;
+          for (int j = b * 32; j < std::min(hf.ny, b * 32 + 32) && !any; ++j)
+            for (int i = a * 64; i < std::min(hf.nx, a * 64 + 64); ++i)
+              if (hf.cls[hf.pad(i, j)] != 0 || hc.cls[hc.pad(i / 2, j / 2)] != 0) {
+                any = true;
+                break;
+              }
+          if (any) {
+            t.push_back(a);
+            t.push_back(b);
+          }
+        }
+      d.ntiles64r = (int)t.size() / 2;
+      if (d.ntiles64r) d.tiles64r = A.upload(t);
+    }
+  }
+  // the one-CTA coarse cycle takes over from the first level with at most 64 cells a side
+  for (int m = 1; m < nl && par.coarse_n > 0; ++m)
+    if (h->L[m].nx <= par.coarse_n && h->L[m].ny <= par.coarse_n && (h->L[m].n2 == 0 || h->L[m].nblk > 0)) {
+      h->coarse_first = m;
+      break;
+    }
   h->rhat = A.alloc<double>(h->L[0].npad);
   h->uhat = A.alloc<double>(h->L[0].npad);
   h->dnorm = A.alloc<unsigned long long>(1);
+  h->derr = A.alloc<int>(1);
   if (A.err != cudaSuccess) {
     A.release();
     return A.err == cudaErrorMemoryAllocation ? CCM_ENOMEM : CCM_ECUDA;
   }
-  if (cudaMallocHost(&h->hnorm, sizeof(unsigned long long)) != cudaSuccess) {
+  if (cudaMallocHost(&h->hnorm, sizeof(unsigned long long)) != cudaSuccess ||
+      cudaMallocHost(&h->herr, sizeof(int)) != cudaSuccess) {
     A.release();
     return CCM_ECUDA;
   }
@@ -676,6 +905,7 @@ static void iteration_body(ccm_handle* h, bool fp64, cudaStream_t s) {
   cudaMemsetAsync(h->dnorm, 0, sizeof(unsigned long long), s);
   KL(dev::k_absmax<double><<<std::min(ceil_div(np, 256), 1216), 256, 0, s>>>(np, L.cls, L.t64, h->dnorm));
   cudaMemcpyAsync(h->hnorm, h->dnorm, sizeof(unsigned long long), cudaMemcpyDeviceToHost, s);
+  cudaMemcpyAsync(h->herr, h->derr, sizeof(int), cudaMemcpyDeviceToHost, s);
 }
 
 static int capture_iteration(ccm_handle* h, bool fp64, cudaStream_t user) {
@@ -767,6 +997,12 @@ int ccm_solve(ccm_handle* h, const double* f, const double* g, double* u, int nr
       std::memcpy(&rel, &bits, sizeof(double));
       rel /= rnorm;
       ++it;
+      if (*h->herr) {
+        result = CCM_ETIMEOUT;
+        *h->herr = 0;
+        cudaMemsetAsync(h->derr, 0, sizeof(int), s);
+        break;
+      }
       if (it < 64) local.history[it] = rel;
       for (int p : G.prof_pairs) {
         float t = 0;
@@ -776,7 +1012,8 @@ int ccm_solve(ccm_handle* h, const double* f, const double* g, double* u, int nr
         }
       }
     }
-    if (!std::isfinite(rel)) result = CCM_ENOTFINITE;
+    if (result == CCM_ETIMEOUT) {
+    } else if (!std::isfinite(rel)) result = CCM_ENOTFINITE;
     else if (rel > h->par.rtol) result = CCM_ENOCONV;
     KL(dev::k_unpack<double><<<pg, 128, 0, s>>>(L.nx, L.ny, L.pitch, L.cls, U0, u + k * nu, 1.0));
     local.iterations = it;
@@ -888,7 +1125,7 @@ int ccm_vcycle(ccm_handle* h, double* u, const double* r, int precision, void* s
 int64_t ccm_launch_count(void) { return (int64_t)g_launches.load(); }
 
 int ccm_profile(ccm_handle* h, int kernel_class) {
-  if (!h || kernel_class < 0 || kernel_class > CCM_PROF_VCYCLE) return CCM_EINVAL;
+  if (!h || kernel_class < 0 || kernel_class > CCM_PROF_RESTRICT_FP32) return CCM_EINVAL;
   if (kernel_class != h->prof_class) {
     cudaDeviceSynchronize();
     drop_graphs(h);
@@ -922,9 +1159,13 @@ void ccm_free(ccm_handle* h) {
   cudaDeviceSynchronize();
   drop_graphs(h);
   if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
+  if (h->side) cudaStreamDestroy(h->side);
+  if (h->ev_fork) cudaEventDestroy(h->ev_fork);
+  if (h->ev_join) cudaEventDestroy(h->ev_join);
   for (cudaEvent_t e : h->prof_ev) cudaEventDestroy(e);
   h->arena.release();
   if (h->hnorm) cudaFreeHost(h->hnorm);
+  if (h->herr) cudaFreeHost(h->herr);
   delete h;
 }
 

@@ -26,9 +26,11 @@ def _compare_level(hs, level, prob_level):
         assert np.abs(mom[j, i] - m).max() < 1e-12
     cell, cols, beta, nb, seg = hs.rows(level)
     lins = sorted(dz.rows.keys())
-    assert list(cell) == lins
+    assert sorted(cell.tolist()) == lins          # the product numbers rows in boundary order
+    where = {int(c): r for r, c in enumerate(cell)}
     segs = {int(s): k for k, s in enumerate(dz.segs)}
-    for r, lin in enumerate(lins):
+    for lin in lins:
+        r = where[lin]
         row = dz.rows[lin]
         assert list(cols[r]) == [cj * prob_level.nx + ci for (ci, cj) in row.cells], lin
         scale = np.abs(row.beta).max()
