@@ -55,7 +55,8 @@ enum {
   CCM_ETIMEOUT = -6,   /* a bounded device wait ran out */
   CCM_ECUDA = -7,      /* a CUDA runtime call failed */
   CCM_ENOMEM = -8,     /* device or host allocation failed */
-  CCM_ENOTFINITE = -9  /* a residual norm became NaN or Inf */
+  CCM_ENOTFINITE = -9, /* a residual norm became NaN or Inf */
+  CCM_ETOOLARGE = -10  /* the grid does not fit the fixed scratch of ccm_apply_noalloc */
 };
 
 typedef struct {
@@ -158,6 +159,26 @@ int ccm_quadrature(const ccm_handle* h, int64_t* n_cell_nodes, int64_t* n_bdry_n
  * u, out: device [nrhs][ny][nx] FP64; g: device [nrhs][n_segments] FP64 (may be NULL: g = 0).
  * Runs in FP64 (regular stencil, Sec. 3.2; fitted irregular rows, eq. goalOfApproximation). */
 int ccm_apply(ccm_handle* h, const double* u, const double* g, double* out, int nrhs, void* stream);
+
+/* Allocation-free operator application.  Same result as ccm_apply with nrhs = 1
+ * (out = L u + N g on the finest level, physical units; u, out: device [ny][nx] FP64, g:
+ * device [n_segments] FP64 or NULL), for callers that cannot allocate device memory at call
+ * time: code running inside a CUDA stream capture, which cudaMalloc would break, or under a
+ * host framework whose allocator owns all device memory.  The handle is set up beforehand.
+ * Unlike ccm_apply, this call does not use the handle's work arrays.  It uses a fixed
+ * file-scope device array (the library keeps CCM_NOALLOC_SCRATCH_BYTES = 16 MiB on every
+ * device that loads it, until the process exits).  That array holds two padded FP64 grids of
+ * at most CCM_NOALLOC_MAX_PADDED cells each, where the padded size is
+ * ((nx + 4) rounded up to a multiple of 32) * (ny + 4); larger grids are rejected with
+ * CCM_ETOOLARGE before any work is queued.  It calls no cudaMalloc, cudaFree or allocating
+ * library routine.  The first call on a device looks up the array's device address (once per
+ * device): make that first call outside any stream capture.  Every call shares the array,
+ * so calls that overlap on the GPU (other streams, other handles) race; the call clears the
+ * part of the array it uses before filling it.  The paper has no counterpart of this entry
+ * point: it exists for the memory model of its callers. */
+#define CCM_NOALLOC_MAX_PADDED (1L << 20)
+#define CCM_NOALLOC_SCRATCH_BYTES (2L * CCM_NOALLOC_MAX_PADDED * 8L)
+int ccm_apply_noalloc(const ccm_handle* h, const double* u, const double* g, double* out, void* stream);
 
 /* Transposed operator: out_u = L^T v, out_g = N^T v (either may be NULL).  v, out_u:
  * device [nrhs][ny][nx]; out_g: device [nrhs][n_segments]; FP64.  Uses the point-symmetric

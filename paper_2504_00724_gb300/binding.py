@@ -88,6 +88,7 @@ _SIGS = {
     "ccm_host_cell_map": (I, [P, I, P, P, P, P, P]),
     "ccm_host_free": (None, [P]),
     "ccm_launch_count": (ctypes.c_int64, []),
+    "ccm_apply_noalloc": (I, [P, P, P, P, P]),
     "ccm_profile": (I, [P, I]),
     "ccm_profile_read": (I, [P, ctypes.POINTER(ctypes.c_double), I64P]),
 }

@@ -7,6 +7,7 @@
 #include <cmath>
 #include <cstring>
 #include <memory>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -545,6 +546,7 @@ const char* ccm_strerror(int code) {
     case CCM_ECUDA: return "CUDA runtime error";
     case CCM_ENOMEM: return "out of memory";
     case CCM_ENOTFINITE: return "residual is not finite";
+    case CCM_ETOOLARGE: return "grid exceeds the fixed scratch of the allocation-free entry point";
     default: return "unknown error";
   }
 }
@@ -834,6 +836,63 @@ int ccm_apply(ccm_handle* h, const double* u, const double* g, double* out, int 
     KL(dev::k_unpack<double><<<pg, 128, 0, s>>>(L.nx, L.ny, L.pitch, L.cls, L.u64[1 - L.cur64], out + k * nu,
                                              1.0 / (L.h * L.h)));
   }
+  CCM_CUDA(cudaGetLastError());
+  return CCM_OK;
+}
+
+}  // extern "C"
+
+// Scratch of ccm_apply_noalloc: two padded FP64 grids, held by every device that loads the
+// library.  Host code only ever uses the device address looked up below.
+static __device__ __align__(256) double g_noalloc_scratch[2 * CCM_NOALLOC_MAX_PADDED];
+
+namespace {
+std::mutex g_noalloc_mu;
+double* g_noalloc_ptr[256] = {nullptr};
+
+// device address of the scratch array on the current device (looked up once per device)
+int noalloc_scratch(double** out) {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 256) return CCM_ECUDA;
+  std::lock_guard<std::mutex> lock(g_noalloc_mu);
+  if (!g_noalloc_ptr[dev]) {
+    void* p = nullptr;
+    if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) return CCM_ECUDA;
+    g_noalloc_ptr[dev] = (double*)p;
+  }
+  *out = g_noalloc_ptr[dev];
+  return CCM_OK;
+}
+}  // namespace
+
+extern "C" {
+
+int ccm_apply_noalloc(const ccm_handle* hc, const double* u, const double* g, double* out, void* stream) {
+  if (!hc || !u || !out) return CCM_EINVAL;
+  ccm_handle* h = const_cast<ccm_handle*>(hc);
+  const DevLevel& L = h->L[0];
+  if (L.npad > CCM_NOALLOC_MAX_PADDED) return CCM_ETOOLARGE;
+  double* scratch = nullptr;
+  int rc = noalloc_scratch(&scratch);
+  if (rc) return rc;
+  cudaStream_t s = (cudaStream_t)stream;
+  double* up = scratch;                              // padded u
+  double* op = scratch + CCM_NOALLOC_MAX_PADDED;     // padded L u + N g
+  CCM_CUDA(cudaMemsetAsync(up, 0, L.npad * sizeof(double), s));
+  CCM_CUDA(cudaMemsetAsync(op, 0, L.npad * sizeof(double), s));
+  dim3 pg(ceil_div(L.nx, 128), L.ny);
+  KL(dev::k_pack<double, double><<<pg, 128, 0, s>>>(L.nx, L.ny, L.pitch, L.cls, u, up, 1.0));
+  if (L.ntiles) {
+    dim3 blk(dev::TX, dev::TY);
+    if (h->cross)
+      KL(dev::k_regular<double, true, false><<<L.ntiles, blk, 0, s>>>(L.tiles, L.cls, L.nx, L.ny, L.pitch, up, nullptr, op, h->S64));
+    else
+      KL(dev::k_regular<double, false, false><<<L.ntiles, blk, 0, s>>>(L.tiles, L.cls, L.nx, L.ny, L.pitch, up, nullptr, op, h->S64));
+  }
+  if (L.n2)
+    KL(dev::k_rows<double, double, false, true><<<ceil_div(L.n2, 128), 128, 0, s>>>(
+        L.n2, L.irr_cell, L.ell_col, L.ell64, up, nullptr, op, L.nb, L.seg, g));
+  KL(dev::k_unpack<double><<<pg, 128, 0, s>>>(L.nx, L.ny, L.pitch, L.cls, op, out, 1.0 / (L.h * L.h)));
   CCM_CUDA(cudaGetLastError());
   return CCM_OK;
 }
