@@ -198,9 +198,13 @@ int ccm_apply_T(ccm_handle* h, const double* v, double* out_u, double* out_g, in
 int ccm_solve(ccm_handle* h, const double* f, const double* g, double* u, int nrhs,
               void* stream, ccm_stats* stats);
 
-/* Adjoint solve L^T lambda = rhs with the transposed V-cycle; lambda in: guess, out: solution.
- * rhs, lambda: device [nrhs][ny][nx].  Gradients of a loss J(u(f, g)): dJ/df = lambda,
- * dJ/dg = -N^T lambda (apply ccm_apply_T to lambda). */
+/* Adjoint solve L^T lambda = rhs (transpose of eq. PoissonResidualForm) by the same V-cycle on
+ * the hierarchy of the transposed operators (L^(m))^T: cells whose column of L is the plain
+ * point-symmetric stencil keep it, every other cell gets an explicit transposed row, with its
+ * own boundary order, SMO-2 blocks and bottom inverse.  The first call builds that hierarchy
+ * on the host and uploads it (blocking, allocates); later calls reuse it.  lambda in: initial
+ * guess, out: solution; rhs, lambda: device [nrhs][ny][nx].  Gradients of a loss J(u(f, g)):
+ * dJ/df = lambda, dJ/dg = -N^T lambda (ccm_apply_T of lambda). */
 int ccm_solve_T(ccm_handle* h, const double* rhs, double* lambda, int nrhs, void* stream,
                 ccm_stats* stats);
 

@@ -251,6 +251,17 @@ class Solver:
             _check(rc, "ccm_solve")
         return u, st
 
+    def solve_T(self, rhs, lam0=None, stream=None, check=True):
+        """lambda with L^T lambda = rhs (adjoint solve)."""
+        import torch
+        nrhs = rhs.numel() // (self.nx * self.ny)
+        lam = torch.zeros_like(rhs) if lam0 is None else lam0.clone()
+        st = ccm_stats()
+        rc = lib().ccm_solve_T(self.h, _ptr(rhs), _ptr(lam), nrhs, _stream(stream), ctypes.byref(st))
+        if check:
+            _check(rc, "ccm_solve_T")
+        return lam, st
+
     def level_apply(self, level, u, stream=None):
         import torch
         out = torch.empty_like(u)

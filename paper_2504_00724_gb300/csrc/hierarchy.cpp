@@ -59,7 +59,7 @@ bool dense_inverse(std::vector<double>& A, int n) {
 // Alg. 3: interface cells sorted by the parameter of their boundary piece (components in the
 // order box, curve 0, curve 1, ...); each numbers the unnumbered irregular cells within
 // Chebyshev distance 2; irregular cells farther away ride with their nearest interface cell.
-static std::vector<int> boundary_order(const CutLevel& cg, const Rows& rows) {
+static std::vector<int> boundary_order(const CutLevel& cg, const PackRows& rows) {
   const int nx = cg.nx, ny = cg.ny;
   struct Key {
     int comp;
@@ -155,7 +155,7 @@ static std::vector<int> boundary_order(const CutLevel& cg, const Rows& rows) {
   return order;
 }
 
-static int pack_level(const CutLevel& cg, const Rows& rows, const ccm_params& par, bool coarsest, bool finest,
+static int pack_level(const CutLevel& cg, const PackRows& rows, const ccm_params& par, bool coarsest, bool finest,
                       HostLevel& L, std::string& err) {
   L.nx = cg.nx;
   L.ny = cg.ny;
@@ -212,29 +212,31 @@ static int pack_level(const CutLevel& cg, const Rows& rows, const ccm_params& pa
   }
   // fitted rows
   const int n2 = (int)rows.irr.size();
+  const int W = rows.W;
   L.n2 = n2;
+  L.W = W;
   L.irr_cell.resize(n2);
-  L.ell_col.resize(15L * n2);
-  L.ell_val.resize(15L * n2);
+  L.ell_col.resize((long)W * n2);
+  L.ell_val.resize((long)W * n2);
   L.nb.resize(n2);
   L.seg.resize(n2);
   for (int r = 0; r < n2; ++r) {
     int q = rows.irr[r];
     L.irr_cell[r] = (int32_t)L.pad(q % cg.nx, q / cg.nx);
-    for (int k = 0; k < 15; ++k) {
-      int c = rows.cols[r][k];
+    for (int k = 0; k < W; ++k) {
+      int c = rows.cols[(long)r * W + k];
       L.ell_col[(long)k * n2 + r] = (int32_t)L.pad(c % cg.nx, c / cg.nx);
-      L.ell_val[(long)k * n2 + r] = rows.beta[r][k];
+      L.ell_val[(long)k * n2 + r] = rows.beta[(long)r * W + k];
     }
     L.nb[r] = rows.nb[r];
     L.seg[r] = rows.seg[r];
   }
   // the same columns with the sign bit set where the column cell is regular (SMO-2 reads
   // those from the new iterate and the irregular ones from the old)
-  L.ell_colf.resize(15L * n2);
+  L.ell_colf.resize((long)W * n2);
   for (int r = 0; r < n2; ++r)
-    for (int k = 0; k < 15; ++k) {
-      int c2 = rows.cols[r][k];
+    for (int k = 0; k < W; ++k) {
+      int c2 = rows.cols[(long)r * W + k];
       uint32_t v = (uint32_t)L.ell_col[(long)k * n2 + r];
       if (rows.regular[c2]) v |= 0x80000000u;
       L.ell_colf[(long)k * n2 + r] = (int32_t)v;
@@ -243,7 +245,7 @@ static int pack_level(const CutLevel& cg, const Rows& rows, const ccm_params& pa
     // transposed fitted rows, grouped by column cell
     std::map<int32_t, std::vector<std::pair<int32_t, double>>> cols;
     for (int r = 0; r < n2; ++r)
-      for (int k = 0; k < 15; ++k) cols[L.ell_col[(long)k * n2 + r]].push_back({r, L.ell_val[(long)k * n2 + r]});
+      for (int k = 0; k < W; ++k) cols[L.ell_col[(long)k * n2 + r]].push_back({r, L.ell_val[(long)k * n2 + r]});
     L.tr_ptr.assign(1, 0);
     for (auto& kv : cols) {
       L.tr_cell.push_back(kv.first);
@@ -273,13 +275,13 @@ static int pack_level(const CutLevel& cg, const Rows& rows, const ccm_params& pa
       int q = cells[k];
       if (rowof[q] >= 0) {
         int r = rowof[q];
-        for (int s = 0; s < 15; ++s) {
-          int col = idx[rows.cols[r][s]];
+        for (int s = 0; s < W; ++s) {
+          int col = idx[rows.cols[(long)r * W + s]];
           if (col < 0) {
             err = "fitted row references an empty cell";
             return CCM_EGEOM;
           }
-          A[(long)k * n + col] += rows.beta[r][s];
+          A[(long)k * n + col] += rows.beta[(long)r * W + s];
         }
       } else {
         A[(long)k * n + k] = NAN;
@@ -329,7 +331,7 @@ static int pack_level(const CutLevel& cg, const Rows& rows, const ccm_params& pa
         A.assign((long)ne * ne, 0.0);
         for (int a = 0; a < ne; ++a) {
           int r = order[es + a];
-          for (int k = 0; k < 15; ++k) {
+          for (int k = 0; k < W; ++k) {
             int rc = row_of_pad[L.ell_col[(long)k * n2 + r]];
             if (rc < 0) continue;                 // a regular column: L21
             int pc = pos[rc] - es;
@@ -358,6 +360,119 @@ static int pack_level(const CutLevel& cg, const Rows& rows, const ccm_params& pa
   return CCM_OK;
 }
 
+// Coarsest level: fill the regular rows of the dense operator with the stencil (the packing
+// marked them with NaN on the diagonal), invert, store [col][row] for coalesced reads.
+static int finish_bottom(HostLevel& L, const CutLevel& cg, const double w[5][5], std::string& err) {
+  const int n = L.nb_cells;
+  std::vector<int> idx((long)cg.nx * cg.ny, -1);
+  std::vector<int> cells;
+  for (long q = 0; q < (long)cg.nx * cg.ny; ++q)
+    if (cg.status[q] != ST_EMPTY) {
+      idx[q] = (int)cells.size();
+      cells.push_back((int)q);
+    }
+  std::vector<double>& A = L.bot_inv;
+  for (int k = 0; k < n; ++k) {
+    if (!std::isnan(A[(long)k * n + k])) continue;
+    A[(long)k * n + k] = 0.0;
+    int q = cells[k], j = q / cg.nx, i = q % cg.nx;
+    for (int dj = -2; dj <= 2; ++dj)
+      for (int di = -2; di <= 2; ++di) {
+        if (w[dj + 2][di + 2] == 0.0) continue;
+        int col = idx[(long)(j + dj) * cg.nx + (i + di)];
+        A[(long)k * n + col] += w[dj + 2][di + 2];
+      }
+  }
+  if (!dense_inverse(A, n)) {
+    err = "singular coarsest-level operator";
+    return CCM_ESINGULAR;
+  }
+  std::vector<double> T((long)n * n);
+  for (int r = 0; r < n; ++r)
+    for (int c2 = 0; c2 < n; ++c2) T[(long)c2 * n + r] = A[(long)r * n + c2];
+  A.swap(T);
+  return CCM_OK;
+}
+
+// Rows of the transposed operator of one level.  Column c of L collects the regular rows p
+// with |p - c| <= 2 (coefficient w_{c - p}) and the fitted rows that use c.  A cell keeps the
+// plain stencil in L^T (the stencil is point-symmetric) when it is regular, every cell within
+// distance 2 is regular and no fitted row uses it; every other non-empty cell gets an
+// explicit transposed row.
+static PackRows transpose_rows(const CutLevel& cg, const PackRows& F, const double w[5][5]) {
+  const int nx = cg.nx, ny = cg.ny;
+  const long N = (long)nx * ny;
+  const int W0 = F.W;
+  std::vector<uint8_t> refd(N, 0);
+  struct Ref {
+    int c, p;
+    double v;
+  };
+  std::vector<Ref> refs;
+  for (size_t r = 0; r < F.irr.size(); ++r)
+    for (int k = 0; k < W0; ++k) {
+      const double v = F.beta[r * W0 + k];
+      if (v == 0.0) continue;
+      const int c = F.cols[r * W0 + k];
+      refd[c] = 1;
+      refs.push_back({c, F.irr[r], v});
+    }
+  std::sort(refs.begin(), refs.end(), [](const Ref& a, const Ref& b) { return a.c != b.c ? a.c < b.c : a.p < b.p; });
+  PackRows T;
+  T.regular.assign(N, 0);
+  for (int j = 0; j < ny; ++j)
+    for (int i = 0; i < nx; ++i) {
+      const long q = (long)j * nx + i;
+      if (!F.regular[q] || refd[q]) continue;
+      bool all = true;
+      for (int dj = -2; dj <= 2 && all; ++dj)
+        for (int di = -2; di <= 2; ++di) {
+          const int ii = i + di, jj = j + dj;
+          if (ii < 0 || jj < 0 || ii >= nx || jj >= ny || !F.regular[(long)jj * nx + ii]) {
+            all = false;
+            break;
+          }
+        }
+      T.regular[q] = all ? 1 : 0;
+    }
+  std::vector<std::vector<std::pair<int, double>>> rowsT;
+  size_t rp = 0;
+  int W = 1;
+  for (long q = 0; q < N; ++q) {
+    while (rp < refs.size() && refs[rp].c < q) ++rp;
+    if (cg.status[q] == ST_EMPTY || T.regular[q]) continue;
+    std::vector<std::pair<int, double>> e;
+    const int j = (int)(q / nx), i = (int)(q % nx);
+    for (int dj = -2; dj <= 2; ++dj)
+      for (int di = -2; di <= 2; ++di) {
+        const double v = w[dj + 2][di + 2];
+        const int pi = i - di, pj = j - dj;
+        if (v == 0.0 || pi < 0 || pj < 0 || pi >= nx || pj >= ny) continue;
+        const long p = (long)pj * nx + pi;
+        if (F.regular[p]) e.push_back({(int)p, v});
+      }
+    for (size_t k = rp; k < refs.size() && refs[k].c == q; ++k) e.push_back({refs[k].p, refs[k].v});
+    W = std::max<int>(W, (int)e.size());
+    T.irr.push_back((int)q);
+    rowsT.push_back(std::move(e));
+  }
+  T.W = W;
+  for (size_t r = 0; r < T.irr.size(); ++r) {
+    for (int k = 0; k < W; ++k) {
+      if (k < (int)rowsT[r].size()) {
+        T.cols.push_back(rowsT[r][k].first);
+        T.beta.push_back(rowsT[r][k].second);
+      } else {
+        T.cols.push_back(T.irr[r]);
+        T.beta.push_back(0.0);
+      }
+    }
+    T.nb.push_back(0.0);
+    T.seg.push_back(-1);
+  }
+  return T;
+}
+
 int build_hierarchy(const ccm_problem& prob, const ccm_params& par, Hierarchy& H, std::string& err) {
   H.a = prob.a;
   H.b = prob.b;
@@ -374,63 +489,77 @@ int build_hierarchy(const ccm_problem& prob, const ccm_params& par, Hierarchy& H
     CutLevel& cg = H.cut[m];
     int rc = build_cut_level(prob, prob.nx >> m, prob.ny >> m, prob.h * (double)(1 << m), par.theta, cg, err);
     if (rc) return rc;
-    Rows rows;
-    rc = discretize_level(cg, prob.a, prob.b, prob.c, par.nthreads, rows, err);
+    Rows fit;
+    rc = discretize_level(cg, prob.a, prob.b, prob.c, par.nthreads, fit, err);
     if (rc) return rc;
-    if (m == 0) H.cond_max = rows.cond_max;
-    if (m < nl - 1 && !rows.irr.empty()) {
+    if (m == 0) H.cond_max = fit.cond_max;
+    PackRows rows;
+    rows.W = 15;
+    rows.regular = fit.regular;
+    const int n2 = (int)fit.irr.size();
+    std::vector<int> order(n2);
+    for (int r = 0; r < n2; ++r) order[r] = r;
+    if (m < nl - 1 && n2) {
       // renumber the fitted rows into the boundary order of Alg. 3
-      std::vector<int> order = boundary_order(cg, rows);
-      Rows p;
-      p.regular = rows.regular;
-      p.cond_max = rows.cond_max;
-      for (int r : order) {
-        p.irr.push_back(rows.irr[r]);
-        p.cols.push_back(rows.cols[r]);
-        p.beta.push_back(rows.beta[r]);
-        p.nb.push_back(rows.nb[r]);
-        p.seg.push_back(rows.seg[r]);
+      PackRows tmp;
+      tmp.irr = fit.irr;
+      order = boundary_order(cg, tmp);
+    }
+    for (int r : order) {
+      rows.irr.push_back(fit.irr[r]);
+      for (int k = 0; k < 15; ++k) {
+        rows.cols.push_back(fit.cols[r][k]);
+        rows.beta.push_back(fit.beta[r][k]);
       }
-      rows.irr.swap(p.irr);
-      rows.cols.swap(p.cols);
-      rows.beta.swap(p.beta);
-      rows.nb.swap(p.nb);
-      rows.seg.swap(p.seg);
+      rows.nb.push_back(fit.nb[r]);
+      rows.seg.push_back(fit.seg[r]);
     }
     rc = pack_level(cg, rows, par, m == nl - 1, m == 0, H.levels[m], err);
     if (rc) return rc;
+    H.rows.push_back(std::move(rows));
     if (m == 0) H.nseg = (int)cg.segs.size();
     if (m == nl - 1) {
-      HostLevel& L = H.levels[m];
-      const int n = L.nb_cells;
-      std::vector<int> idx((long)cg.nx * cg.ny, -1);
-      std::vector<int> cells;
-      for (long q = 0; q < (long)cg.nx * cg.ny; ++q)
-        if (cg.status[q] != ST_EMPTY) {
-          idx[q] = (int)cells.size();
-          cells.push_back((int)q);
+      rc = finish_bottom(H.levels[m], cg, w, err);
+      if (rc) return rc;
+    }
+  }
+  return CCM_OK;
+}
+
+int build_transposed(const Hierarchy& H, const ccm_params& par, Hierarchy& T, std::string& err) {
+  T.a = H.a;
+  T.b = H.b;
+  T.c = H.c;
+  T.nseg = 0;
+  T.cond_max = H.cond_max;
+  const int nl = (int)H.levels.size();
+  T.levels.resize(nl);
+  double w[5][5];
+  regular_stencil(H.a, H.b, H.c, w);
+  for (int m = 0; m < nl; ++m) {
+    const CutLevel& cg = H.cut[m];
+    PackRows t = transpose_rows(cg, H.rows[m], w);
+    if (m < nl - 1 && !t.irr.empty()) {
+      std::vector<int> order = boundary_order(cg, t);
+      PackRows p;
+      p.W = t.W;
+      p.regular.swap(t.regular);
+      for (int r : order) {
+        p.irr.push_back(t.irr[r]);
+        for (int k = 0; k < t.W; ++k) {
+          p.cols.push_back(t.cols[(long)r * t.W + k]);
+          p.beta.push_back(t.beta[(long)r * t.W + k]);
         }
-      std::vector<double>& A = L.bot_inv;
-      for (int k = 0; k < n; ++k) {
-        if (!std::isnan(A[(long)k * n + k])) continue;
-        A[(long)k * n + k] = 0.0;
-        int q = cells[k], j = q / cg.nx, i = q % cg.nx;
-        for (int dj = -2; dj <= 2; ++dj)
-          for (int di = -2; di <= 2; ++di) {
-            if (w[dj + 2][di + 2] == 0.0) continue;
-            int col = idx[(long)(j + dj) * cg.nx + (i + di)];
-            A[(long)k * n + col] += w[dj + 2][di + 2];
-          }
+        p.nb.push_back(0.0);
+        p.seg.push_back(-1);
       }
-      if (!dense_inverse(A, n)) {
-        err = "singular coarsest-level operator";
-        return CCM_ESINGULAR;
-      }
-      // store [col][row] for coalesced device reads
-      std::vector<double> T((long)n * n);
-      for (int r = 0; r < n; ++r)
-        for (int c2 = 0; c2 < n; ++c2) T[(long)c2 * n + r] = A[(long)r * n + c2];
-      A.swap(T);
+      t = std::move(p);
+    }
+    int rc = pack_level(cg, t, par, m == nl - 1, false, T.levels[m], err);
+    if (rc) return rc;
+    if (m == nl - 1) {
+      rc = finish_bottom(T.levels[m], cg, w, err);
+      if (rc) return rc;
     }
   }
   return CCM_OK;

@@ -9,6 +9,17 @@
 
 namespace ccm {
 
+// Rows of one level ready for packing: regular mask, fitted (or transposed) rows of width W.
+struct PackRows {
+  int W = 15;
+  std::vector<uint8_t> regular;   // [nx*ny]
+  std::vector<int> irr;           // linear indices of the explicit rows' cells
+  std::vector<int> cols;          // [n2*W] linear column cells (padding: the row's own cell)
+  std::vector<double> beta;       // [n2*W] h^2-scaled coefficients (padding: 0)
+  std::vector<double> nb;         // [n2] boundary coefficient
+  std::vector<int> seg;           // [n2] boundary segment or -1
+};
+
 // Padded grid layout of one level: a 2-cell zero ring around the nx x ny cells, rows of
 // `pitch` entries (a multiple of 32), cell (i, j) at (j + 2) * pitch + (i + 2).
 struct HostLevel {
@@ -22,12 +33,13 @@ struct HostLevel {
   std::vector<int32_t> tiles;   // active 32 x 8 tiles (tile x, tile y) pairs
   std::vector<int32_t> tiles64; // active 64 x 32 tiles (TMA-staged SMO-1)
 
-  // fitted rows, ELL with 15 slots: [slot][n2]
+  // explicit rows, ELL with W slots: [slot][n2]
   int n2 = 0;
+  int W = 15;
   std::vector<int32_t> irr_cell;   // [n2] padded index of the row's cell
-  std::vector<int32_t> ell_col;    // [15 * n2] padded column index
+  std::vector<int32_t> ell_col;    // [W * n2] padded column index
   std::vector<int32_t> ell_colf;   // the same, sign bit set for regular column cells
-  std::vector<double> ell_val;     // [15 * n2] h^2-scaled coefficient
+  std::vector<double> ell_val;     // [W * n2] h^2-scaled coefficient
   std::vector<double> nb;          // [n2] h^2-scaled boundary coefficient
   std::vector<int32_t> seg;        // [n2] boundary segment or -1
 
@@ -58,11 +70,14 @@ struct Hierarchy {
   double a = 0, b = 0, c = 0;
   std::vector<HostLevel> levels;
   std::vector<CutLevel> cut;       // geometry of every level (kept for queries)
+  std::vector<PackRows> rows;      // the rows every level was packed from
   double cond_max = 0;
   int nseg = 0;
 };
 
 int build_hierarchy(const ccm_problem& prob, const ccm_params& par, Hierarchy& H, std::string& err);
+// the hierarchy of the transposed operators (L^(m))^T, on the same geometry
+int build_transposed(const Hierarchy& H, const ccm_params& par, Hierarchy& T, std::string& err);
 bool dense_inverse(std::vector<double>& A, int n);   // in place, partial pivoting
 
 }  // namespace ccm

@@ -83,15 +83,15 @@ __global__ void k_regular(const int32_t* __restrict__ tiles, const uint8_t* __re
 // fitted rows: res = r[cell] - sum beta u[col]  (RESID) or res = sum beta u[col] + nb g[seg]
 // written to out[row] (GRID = false) or out[cell] (GRID = true)
 template <typename T, typename C, bool RESID, bool GRID>
-__global__ void k_rows(int n2, const int32_t* __restrict__ cell, const int32_t* __restrict__ col,
+__global__ void k_rows(int n2, int W, const int32_t* __restrict__ cell, const int32_t* __restrict__ col,
                        const C* __restrict__ val, const T* __restrict__ u, const T* __restrict__ r,
                        T* __restrict__ out, const double* __restrict__ nb, const int32_t* __restrict__ seg,
                        const double* __restrict__ g) {
   int row = blockIdx.x * blockDim.x + threadIdx.x;
   if (row >= n2) return;
   T acc = 0;
-#pragma unroll
-  for (int k = 0; k < 15; ++k) acc += (T)val[(long)k * n2 + row] * u[col[(long)k * n2 + row]];
+#pragma unroll 15
+  for (int k = 0; k < W; ++k) acc += (T)val[(long)k * n2 + row] * u[col[(long)k * n2 + row]];
   T res;
   if (RESID) {
     res = r[cell[row]] - acc;
@@ -251,7 +251,7 @@ struct SweepArgs {
   const int32_t* tiles;      // TMA: 64 x 32 tiles, else 32 x 8 tiles
   int ntiles, nblk, chunks, rows_per_cta;
   const uint8_t* cls;
-  int nx, ny, pitch, n2;
+  int nx, ny, pitch, n2, W;
   const T* r;
   const T* u_old;
   T* u_new;
@@ -276,8 +276,8 @@ __device__ __forceinline__ void block_part(const SweepArgs<T>& a, int bidx, T* s
   for (int e = threadIdx.x; e < ne; e += blockDim.x) {
     const int row = es + e;
     T acc = 0;
-#pragma unroll
-    for (int k = 0; k < 15; ++k) acc += a.val[(long)k * a.n2 + row] * a.u_old[a.col[(long)k * a.n2 + row]];
+#pragma unroll 15
+    for (int k = 0; k < a.W; ++k) acc += a.val[(long)k * a.n2 + row] * a.u_old[a.col[(long)k * a.n2 + row]];
     s[e] = a.r[a.cell[row]] - acc;
   }
   __syncthreads();
@@ -403,8 +403,8 @@ __global__ void __launch_bounds__(256) k_blocks(SweepArgs<T> a) {
   for (int e = threadIdx.x; e < ne; e += blockDim.x) {
     const int row = es + e;
     T acc = 0;
-#pragma unroll
-    for (int k = 0; k < 15; ++k) acc += a.val[(long)k * a.n2 + row] * a.u_old[a.col[(long)k * a.n2 + row]];
+#pragma unroll 15
+    for (int k = 0; k < a.W; ++k) acc += a.val[(long)k * a.n2 + row] * a.u_old[a.col[(long)k * a.n2 + row]];
     s[e] = a.r[a.cell[row]] - acc;
   }
   const bool ok = tile_wait(&bar, a.err);
@@ -438,7 +438,7 @@ __global__ void __launch_bounds__(256) k_restrict_tma(const __grid_constant__ CU
                                                       const int32_t* __restrict__ tiles, int nxf, int nyf,
                                                       int pitchf, const uint8_t* __restrict__ clsf,
                                                       const T* __restrict__ volf, const int32_t* __restrict__ rowmap,
-                                                      int n2, const int32_t* __restrict__ col,
+                                                      int n2, int W, const int32_t* __restrict__ col,
                                                       const T* __restrict__ val, const T* __restrict__ u,
                                                       const T* __restrict__ r, int nxc, int nyc, int pitchc,
                                                       const uint8_t* __restrict__ clsc, T* __restrict__ rc,
@@ -492,8 +492,8 @@ __global__ void __launch_bounds__(256) k_restrict_tma(const __grid_constant__ CU
         const long p = (long)(cy0 + y0 + k + 2) * pitchf + (i + 2);
         const int row = rowmap[p];
         T acc = 0;
-#pragma unroll
-        for (int m = 0; m < 15; ++m) acc += val[(long)m * n2 + row] * u[col[(long)m * n2 + row]];
+#pragma unroll 15
+        for (int m = 0; m < W; ++m) acc += val[(long)m * n2 + row] * u[col[(long)m * n2 + row]];
         res = rv[k] - acc;
       }
       wres[y0 + k][x] = vv[k] * res;
@@ -525,7 +525,7 @@ __global__ void __launch_bounds__(256) k_restrict_tma(const __grid_constant__ CU
 template <typename T, bool CROSS>
 __global__ void k_restrict_rows(int nxc, int nyc, int pitchc, int pitchf, const uint8_t* __restrict__ clsc,
                                 const uint8_t* __restrict__ clsf, const T* __restrict__ volf,
-                                const int32_t* __restrict__ rowmap, int n2, const int32_t* __restrict__ col,
+                                const int32_t* __restrict__ rowmap, int n2, int W, const int32_t* __restrict__ col,
                                 const T* __restrict__ val, const T* __restrict__ u, const T* __restrict__ r,
                                 T* __restrict__ rc, T* __restrict__ uc, Stencil<T> S) {
   int I = blockIdx.x * blockDim.x + threadIdx.x;
@@ -546,8 +546,8 @@ __global__ void k_restrict_rows(int nxc, int nyc, int pitchc, int pitchf, const 
     } else {
       const int row = rowmap[q];
       Lu = 0;
-#pragma unroll
-      for (int m = 0; m < 15; ++m) Lu += val[(long)m * n2 + row] * u[col[(long)m * n2 + row]];
+#pragma unroll 15
+      for (int m = 0; m < W; ++m) Lu += val[(long)m * n2 + row] * u[col[(long)m * n2 + row]];
     }
     T v = volf[q];
     s += v * (r[q] - Lu);
@@ -594,7 +594,7 @@ __global__ void k_jacobi2(const int32_t* __restrict__ tiles, const uint8_t* __re
 template <typename T>
 __global__ void __launch_bounds__(256) k_block_fused(const int32_t* __restrict__ blk,
                                                      const int64_t* __restrict__ blk_off, const T* __restrict__ inv,
-                                                     int n2, const int32_t* __restrict__ cell,
+                                                     int n2, int W, const int32_t* __restrict__ cell,
                                                      const int32_t* __restrict__ colf, const T* __restrict__ val,
                                                      const T* __restrict__ r, const T* __restrict__ u_old,
                                                      T* __restrict__ u_new, int rows_per_cta) {
@@ -609,8 +609,8 @@ __global__ void __launch_bounds__(256) k_block_fused(const int32_t* __restrict__
   for (int e = threadIdx.x; e < ne; e += blockDim.x) {
     const int row = es + e;
     T acc = 0;
-#pragma unroll
-    for (int k = 0; k < 15; ++k) {
+#pragma unroll 15
+    for (int k = 0; k < W; ++k) {
       const int f = colf[(long)k * n2 + row];
       const int q = f & 0x7fffffff;
       acc += val[(long)k * n2 + row] * (f < 0 ? u_new[q] : u_old[q]);
@@ -729,7 +729,7 @@ constexpr int MAXC = 8;
 
 template <typename T>
 struct CoarseLevel {
-  int nx, ny, pitch, n2, nblk, nbc, core;
+  int nx, ny, pitch, n2, nblk, nbc, core, W;
   const uint8_t* cls;
   const T* vol;
   T* u[2];
@@ -795,8 +795,8 @@ __device__ void cta_sweep(const CoarseLevel<T>& L, int& cur, const Stencil<T>& S
     const T* rd_reg = (jacobi && pass == 0) ? uin : uout;
     for (int row = threadIdx.x; row < L.n2; row += blockDim.x) {
       T acc = 0;
-#pragma unroll
-      for (int k = 0; k < 15; ++k) {
+#pragma unroll 15
+      for (int k = 0; k < L.W; ++k) {
         const int f = L.colf[(long)k * L.n2 + row];
         const int q = f & 0x7fffffff;
         acc += L.val[(long)k * L.n2 + row] * (f < 0 ? rd_reg[q] : rd_irr[q]);
@@ -833,8 +833,8 @@ __global__ void __launch_bounds__(1024) k_coarse_vcycle(CoarseParams<T> P) {
     T* u = F.u[cur[m]];
     for (int row = threadIdx.x; row < F.n2; row += blockDim.x) {
       T acc = 0;
-#pragma unroll
-      for (int k = 0; k < 15; ++k) acc += F.val[(long)k * F.n2 + row] * u[F.colf[(long)k * F.n2 + row] & 0x7fffffff];
+#pragma unroll 15
+      for (int k = 0; k < F.W; ++k) acc += F.val[(long)k * F.n2 + row] * u[F.colf[(long)k * F.n2 + row] & 0x7fffffff];
       F.t[F.irr_cell[row]] = F.r[F.irr_cell[row]] - acc;
     }
     __syncthreads();

@@ -23,7 +23,7 @@ using namespace ccm;
 namespace {
 
 struct DevLevel {
-  int nx = 0, ny = 0, pitch = 0, rows = 0, ntiles = 0, n2 = 0, nblk = 0, nbc = 0, ncolT = 0;
+  int nx = 0, ny = 0, pitch = 0, rows = 0, ntiles = 0, n2 = 0, W = 15, nblk = 0, nbc = 0, ncolT = 0;
   long npad = 0;
   double h = 0;
   int max_ext = 0, max_core = 0;
@@ -144,6 +144,7 @@ struct ccm_handle {
   double prof_ms = 0;                 // accumulated from graph replays
   long long prof_n = 0;
   int coarse_first = 1 << 30;  // first level run by the one-CTA coarse cycle (FP32)
+  ccm_handle* adj = nullptr;   // the transposed operators' hierarchy (built by ccm_solve_T)
   // one CUDA graph per outer iteration and precision (captured on first use, on a private
   // stream: the legacy default stream cannot be captured)
   cudaStream_t cap_stream = nullptr;
@@ -241,7 +242,7 @@ template <typename T>
 void residual(ccm_handle* H, DevLevel& L, const T* u, const T* r, T* out, cudaStream_t s) {
   launch_regular<T>(H, L, u, r, out, true, s);
   if (L.n2)
-    KL(dev::k_rows<T, T, true, true><<<ceil_div(L.n2, 128), 128, 0, s>>>(L.n2, L.irr_cell, L.ell_col, Ell<T>(L), u, r, out,
+    KL(dev::k_rows<T, T, true, true><<<ceil_div(L.n2, 128), 128, 0, s>>>(L.n2, L.W, L.irr_cell, L.ell_col, Ell<T>(L), u, r, out,
                                                                       nullptr, nullptr, nullptr));
 }
 
@@ -265,6 +266,7 @@ void sweep_one_launch(ccm_handle* H, DevLevel& L, cudaStream_t s) {
   a.ny = L.ny;
   a.pitch = L.pitch;
   a.n2 = L.n2;
+  a.W = L.W;
   a.r = R<T>(L);
   a.u_old = U<T>(L);
   a.u_new = Uother<T>(L);
@@ -340,13 +342,13 @@ void smooth_step(ccm_handle* H, DevLevel& L, cudaStream_t s, const T* uc = nullp
     // many blocks: one CTA each; one big exact block: split its core rows over CTAs
     const int rpc = L.nblk >= 16 ? L.max_core : 64;
     dim3 grd(L.nblk, ceil_div(L.max_core, rpc));
-    KL(dev::k_block_fused<T><<<grd, 256, L.max_ext * sizeof(T), s>>>(L.blk, L.blk_off, Inv<T>(L), L.n2, L.irr_cell,
+    KL(dev::k_block_fused<T><<<grd, 256, L.max_ext * sizeof(T), s>>>(L.blk, L.blk_off, Inv<T>(L), L.n2, L.W, L.irr_cell,
                                                                   L.ell_colf, Ell<T>(L), r, uin, uout, rpc));
   }
   flip<T>(L);
   T* u = U<T>(L);
   for (int pass = 1; pass < H->par.ras_passes && L.n2; ++pass) {
-    KL(dev::k_rows<T, T, true, false><<<ceil_div(L.n2, 128), 128, 0, s>>>(L.n2, L.irr_cell, L.ell_col, Ell<T>(L), u, r,
+    KL(dev::k_rows<T, T, true, false><<<ceil_div(L.n2, 128), 128, 0, s>>>(L.n2, L.W, L.irr_cell, L.ell_col, Ell<T>(L), u, r,
                                                                        Res<T>(L), nullptr, nullptr, nullptr));
     dim3 grd(L.nblk, ceil_div(L.max_core, 32));
     KL(dev::k_block_solve<T><<<grd, 128, L.max_ext * sizeof(T), s>>>(L.order, L.blk, L.blk_off, Inv<T>(L), Res<T>(L),
@@ -362,11 +364,11 @@ void restrict_to(ccm_handle* H, DevLevel& F, DevLevel& C, cudaStream_t s) {
     const auto& S = stencil<T>(H);
     if (H->cross)
       KL(dev::k_restrict_tma<T, true><<<F.ntiles64r, 256, 0, s>>>(TmU<T>(F), F.tiles64r, F.nx, F.ny, F.pitch, F.cls, Vol<T>(F),
-                                                                 F.rowmap, F.n2, F.ell_col, Ell<T>(F), U<T>(F), R<T>(F),
+                                                                 F.rowmap, F.n2, F.W, F.ell_col, Ell<T>(F), U<T>(F), R<T>(F),
                                                                  C.nx, C.ny, C.pitch, C.cls, R<T>(C), U<T>(C), S, H->derr));
     else
       KL(dev::k_restrict_tma<T, false><<<F.ntiles64r, 256, 0, s>>>(TmU<T>(F), F.tiles64r, F.nx, F.ny, F.pitch, F.cls, Vol<T>(F),
-                                                                  F.rowmap, F.n2, F.ell_col, Ell<T>(F), U<T>(F), R<T>(F),
+                                                                  F.rowmap, F.n2, F.W, F.ell_col, Ell<T>(F), U<T>(F), R<T>(F),
                                                                   C.nx, C.ny, C.pitch, C.cls, R<T>(C), U<T>(C), S, H->derr));
     return;
   }
@@ -375,14 +377,14 @@ void restrict_to(ccm_handle* H, DevLevel& F, DevLevel& C, cudaStream_t s) {
     const auto& S = stencil<T>(H);
     if (H->cross)
       KL(dev::k_restrict_rows<T, true><<<grd, blk, 0, s>>>(C.nx, C.ny, C.pitch, F.pitch, C.cls, F.cls, Vol<T>(F), F.rowmap,
-                                                         F.n2, F.ell_col, Ell<T>(F), U<T>(F), R<T>(F), R<T>(C), U<T>(C), S));
+                                                         F.n2, F.W, F.ell_col, Ell<T>(F), U<T>(F), R<T>(F), R<T>(C), U<T>(C), S));
     else
       KL(dev::k_restrict_rows<T, false><<<grd, blk, 0, s>>>(C.nx, C.ny, C.pitch, F.pitch, C.cls, F.cls, Vol<T>(F), F.rowmap,
-                                                          F.n2, F.ell_col, Ell<T>(F), U<T>(F), R<T>(F), R<T>(C), U<T>(C), S));
+                                                          F.n2, F.W, F.ell_col, Ell<T>(F), U<T>(F), R<T>(F), R<T>(C), U<T>(C), S));
     return;
   }
   if (F.n2)
-    KL(dev::k_rows<T, T, true, true><<<ceil_div(F.n2, 128), 128, 0, s>>>(F.n2, F.irr_cell, F.ell_col, Ell<T>(F), U<T>(F),
+    KL(dev::k_rows<T, T, true, true><<<ceil_div(F.n2, 128), 128, 0, s>>>(F.n2, F.W, F.irr_cell, F.ell_col, Ell<T>(F), U<T>(F),
                                                                       R<T>(F), Tmp<T>(F), nullptr, nullptr, nullptr));
   dim3 blk(32, 8), grd(ceil_div(C.nx, 32), ceil_div(C.ny, 8));
   const auto& S = stencil<T>(H);
@@ -421,7 +423,7 @@ void coarse_cta(ccm_handle* H, int m, cudaStream_t s) {
   for (int k = 0; k < P.nlev; ++k) {
     DevLevel& L = H->L[m + k];
     dev::CoarseLevel<float>& C = P.L[k];
-    C.nx = L.nx; C.ny = L.ny; C.pitch = L.pitch; C.n2 = L.n2; C.nblk = L.nblk; C.nbc = L.nbc;
+    C.nx = L.nx; C.ny = L.ny; C.pitch = L.pitch; C.n2 = L.n2; C.nblk = L.nblk; C.nbc = L.nbc; C.W = L.W;
     C.core = L.max_core > 0 ? L.max_core : 1;
     C.cls = L.cls; C.vol = L.vol32; C.u[0] = L.u32[0]; C.u[1] = L.u32[1]; C.r = L.r32; C.t = L.t32;
     C.res = L.res32; C.irr_cell = L.irr_cell; C.colf = L.ell_colf; C.val = L.ell32; C.blk = L.blk;
@@ -507,95 +509,16 @@ bool make_tmap(CUtensorMap* map, void* base, int pitch, int rows, bool fp64) {
   return r == CUDA_SUCCESS;
 }
 
-}  // namespace
-
-// ================================================================ C ABI
-
-extern "C" {
-
-int ccm_default_params(ccm_params* p) {
-  if (!p) return CCM_EINVAL;
-  p->omega = 0.7;
-  p->nu1 = 3;
-  p->nu2 = 3;
-  p->theta = 0.3;
-  p->coarsest = 16;
-  p->precision = CCM_MIXED;
-  p->rtol = 1e-10;
-  p->max_iter = 100;
-  p->ras_passes = 1;
-  p->ras_block = 64;
-  p->ras_overlap = 32;
-  p->nthreads = 0;
-  p->ras_exact = 0;
-  p->inner_cycles = 3;
-  p->smoother = 1;
-  p->coarse_n = 0;
-  return CCM_OK;
-}
-
-const char* ccm_strerror(int code) {
-  switch (code) {
-    case CCM_OK: return "ok";
-    case CCM_EINVAL: return "invalid argument";
-    case CCM_EGEOM: return "invalid or degenerate geometry";
-    case CCM_EPLG: return "no poised PLG stencil within the search radius";
-    case CCM_ESINGULAR: return "singular block or bottom factorisation";
-    case CCM_ENOCONV: return "not converged within max_iter";
-    case CCM_ETIMEOUT: return "bounded device wait ran out";
-    case CCM_ECUDA: return "CUDA runtime error";
-    case CCM_ENOMEM: return "out of memory";
-    case CCM_ENOTFINITE: return "residual is not finite";
-    case CCM_ETOOLARGE: return "grid exceeds the fixed scratch of the allocation-free entry point";
-    default: return "unknown error";
-  }
-}
-
-int ccm_setup(const ccm_problem* prob, const ccm_params* params, ccm_handle** out) {
-  if (!prob || !out) return CCM_EINVAL;
-  *out = nullptr;
-  if (!(prob->h > 0) || prob->nx < 4 || prob->ny < 4 || prob->ncurves < 0 || (prob->ncurves > 0 && !prob->curves))
-    return CCM_EINVAL;
-  if (!(prob->b * prob->b - 4 * prob->a * prob->c < 0)) return CCM_EINVAL;
-  if (prob->box_bc != CCM_NONE && prob->box_bc != CCM_DIRICHLET && prob->box_bc != CCM_NEUMANN) return CCM_EINVAL;
-  for (int k = 0; k < prob->ncurves; ++k) {
-    const ccm_curve& c = prob->curves[k];
-    if (c.kind < CCM_CIRCLE || c.kind > CCM_STAR || (c.orient != 1 && c.orient != -1) ||
-        (c.bc != CCM_DIRICHLET && c.bc != CCM_NEUMANN))
-      return CCM_EINVAL;
-  }
-  ccm_params par;
-  ccm_default_params(&par);
-  if (params) par = *params;
-  if (par.nu1 < 0 || par.nu2 < 0 || par.coarsest < 4 || par.ras_passes < 0 || par.ras_block < 8 ||
-      par.ras_block > 128 || par.ras_overlap < 0 || par.ras_overlap > 64 || par.max_iter < 0 ||
-      par.ras_exact < 0 || par.ras_exact > 6000 || par.inner_cycles < 1 || par.inner_cycles > 16 || par.smoother < 0 || par.smoother > 1 || par.coarse_n < 0 ||
-      !(par.theta >= 0 && par.theta < 1) || (par.precision != CCM_FP64 && par.precision != CCM_MIXED))
-    return CCM_EINVAL;
-  auto t0 = std::chrono::steady_clock::now();
-  std::unique_ptr<ccm_handle> h(new ccm_handle());
-  h->par = par;
-  h->a = prob->a;
-  h->b = prob->b;
-  h->c = prob->c;
-  h->cross = prob->b != 0.0;
-  cudaGetDevice(&h->device);
-  std::string err;
-  int rc;
-  try {
-    rc = build_hierarchy(*prob, par, h->H, err);
-  } catch (const std::bad_alloc&) {
-    return CCM_ENOMEM;
-  }
-  if (rc) return rc;
+// Device copies of a host hierarchy (every level's arrays, work space, tensor maps, streams)
+int upload_hierarchy(ccm_handle* h) {
   double w[5][5];
-  regular_stencil(prob->a, prob->b, prob->c, w);
+  regular_stencil(h->a, h->b, h->c, w);
   for (int k = 0; k < 25; ++k) {
     h->S64.w[k] = w[k / 5][k % 5];
     h->S32.w[k] = (float)w[k / 5][k % 5];
   }
-  h->S64.omega_d = par.omega / w[2][2];
-  h->S32.omega_d = (float)(par.omega / w[2][2]);
+  h->S64.omega_d = h->par.omega / w[2][2];
+  h->S32.omega_d = (float)(h->par.omega / w[2][2]);
 
   Arena& A = h->arena;
   const int nl = (int)h->H.levels.size();
@@ -619,6 +542,7 @@ int ccm_setup(const ccm_problem* prob, const ccm_params* params, ccm_handle** ou
       d.vol32 = A.upload(v32);
     }
     d.n2 = hl.n2;
+    d.W = hl.W;
     if (hl.n2) {
       d.irr_cell = A.upload(hl.irr_cell);
       d.ell_col = A.upload(hl.ell_col);
@@ -722,8 +646,8 @@ int ccm_setup(const ccm_problem* prob, const ccm_params* params, ccm_handle** ou
     }
   }
   // the one-CTA coarse cycle takes over from the first level with at most 64 cells a side
-  for (int m = 1; m < nl && par.coarse_n > 0; ++m)
-    if (h->L[m].nx <= par.coarse_n && h->L[m].ny <= par.coarse_n && (h->L[m].n2 == 0 || h->L[m].nblk > 0)) {
+  for (int m = 1; m < nl && h->par.coarse_n > 0; ++m)
+    if (h->L[m].nx <= h->par.coarse_n && h->L[m].ny <= h->par.coarse_n && (h->L[m].n2 == 0 || h->L[m].nblk > 0)) {
       h->coarse_first = m;
       break;
     }
@@ -744,6 +668,94 @@ int ccm_setup(const ccm_problem* prob, const ccm_params* params, ccm_handle** ou
     A.release();
     return CCM_ECUDA;
   }
+  return CCM_OK;
+}
+
+}  // namespace
+
+// ================================================================ C ABI
+
+extern "C" {
+
+int ccm_default_params(ccm_params* p) {
+  if (!p) return CCM_EINVAL;
+  p->omega = 0.7;
+  p->nu1 = 3;
+  p->nu2 = 3;
+  p->theta = 0.3;
+  p->coarsest = 16;
+  p->precision = CCM_MIXED;
+  p->rtol = 1e-10;
+  p->max_iter = 100;
+  p->ras_passes = 1;
+  p->ras_block = 64;
+  p->ras_overlap = 32;
+  p->nthreads = 0;
+  p->ras_exact = 0;
+  p->inner_cycles = 3;
+  p->smoother = 1;
+  p->coarse_n = 0;
+  return CCM_OK;
+}
+
+const char* ccm_strerror(int code) {
+  switch (code) {
+    case CCM_OK: return "ok";
+    case CCM_EINVAL: return "invalid argument";
+    case CCM_EGEOM: return "invalid or degenerate geometry";
+    case CCM_EPLG: return "no poised PLG stencil within the search radius";
+    case CCM_ESINGULAR: return "singular block or bottom factorisation";
+    case CCM_ENOCONV: return "not converged within max_iter";
+    case CCM_ETIMEOUT: return "bounded device wait ran out";
+    case CCM_ECUDA: return "CUDA runtime error";
+    case CCM_ENOMEM: return "out of memory";
+    case CCM_ENOTFINITE: return "residual is not finite";
+    case CCM_ETOOLARGE: return "grid exceeds the fixed scratch of the allocation-free entry point";
+    default: return "unknown error";
+  }
+}
+
+int ccm_setup(const ccm_problem* prob, const ccm_params* params, ccm_handle** out) {
+  if (!prob || !out) return CCM_EINVAL;
+  *out = nullptr;
+  if (!(prob->h > 0) || prob->nx < 4 || prob->ny < 4 || prob->ncurves < 0 || (prob->ncurves > 0 && !prob->curves))
+    return CCM_EINVAL;
+  if (!(prob->b * prob->b - 4 * prob->a * prob->c < 0)) return CCM_EINVAL;
+  if (prob->box_bc != CCM_NONE && prob->box_bc != CCM_DIRICHLET && prob->box_bc != CCM_NEUMANN) return CCM_EINVAL;
+  for (int k = 0; k < prob->ncurves; ++k) {
+    const ccm_curve& c = prob->curves[k];
+    if (c.kind < CCM_CIRCLE || c.kind > CCM_STAR || (c.orient != 1 && c.orient != -1) ||
+        (c.bc != CCM_DIRICHLET && c.bc != CCM_NEUMANN))
+      return CCM_EINVAL;
+  }
+  ccm_params par;
+  ccm_default_params(&par);
+  if (params) par = *params;
+  if (par.nu1 < 0 || par.nu2 < 0 || par.coarsest < 4 || par.ras_passes < 0 || par.ras_block < 8 ||
+      par.ras_block > 128 || par.ras_overlap < 0 || par.ras_overlap > 64 || par.max_iter < 0 ||
+      par.ras_exact < 0 || par.ras_exact > 6000 || par.inner_cycles < 1 || par.inner_cycles > 16 || par.smoother < 0 || par.smoother > 1 || par.coarse_n < 0 ||
+      !(par.theta >= 0 && par.theta < 1) || (par.precision != CCM_FP64 && par.precision != CCM_MIXED))
+    return CCM_EINVAL;
+  auto t0 = std::chrono::steady_clock::now();
+  std::unique_ptr<ccm_handle> h(new ccm_handle());
+  h->par = par;
+  h->a = prob->a;
+  h->b = prob->b;
+  h->c = prob->c;
+  h->cross = prob->b != 0.0;
+  cudaGetDevice(&h->device);
+  std::string err;
+  int rc;
+  try {
+    rc = build_hierarchy(*prob, par, h->H, err);
+  } catch (const std::bad_alloc&) {
+    return CCM_ENOMEM;
+  }
+  if (rc) return rc;
+  rc = upload_hierarchy(h.get());
+  if (rc) return rc;
+  const int nl = (int)h->H.levels.size();
+  Arena& A = h->arena;
   // info
   ccm_info& I = h->info;
   const CutLevel& c0 = h->H.cut[0];
@@ -831,7 +843,7 @@ int ccm_apply(ccm_handle* h, const double* u, const double* g, double* out, int 
     launch_regular<double>(h, L, L.t64, nullptr, L.u64[1 - L.cur64], false, s);
     if (L.n2)
       KL(dev::k_rows<double, double, false, true><<<ceil_div(L.n2, 128), 128, 0, s>>>(
-          L.n2, L.irr_cell, L.ell_col, L.ell64, L.t64, nullptr, L.u64[1 - L.cur64], L.nb, L.seg,
+          L.n2, L.W, L.irr_cell, L.ell_col, L.ell64, L.t64, nullptr, L.u64[1 - L.cur64], L.nb, L.seg,
           g ? g + (long)k * h->info.n_segments : nullptr));
     KL(dev::k_unpack<double><<<pg, 128, 0, s>>>(L.nx, L.ny, L.pitch, L.cls, L.u64[1 - L.cur64], out + k * nu,
                                              1.0 / (L.h * L.h)));
@@ -891,7 +903,7 @@ int ccm_apply_noalloc(const ccm_handle* hc, const double* u, const double* g, do
   }
   if (L.n2)
     KL(dev::k_rows<double, double, false, true><<<ceil_div(L.n2, 128), 128, 0, s>>>(
-        L.n2, L.irr_cell, L.ell_col, L.ell64, up, nullptr, op, L.nb, L.seg, g));
+        L.n2, L.W, L.irr_cell, L.ell_col, L.ell64, up, nullptr, op, L.nb, L.seg, g));
   KL(dev::k_unpack<double><<<pg, 128, 0, s>>>(L.nx, L.ny, L.pitch, L.cls, op, out, 1.0 / (L.h * L.h)));
   CCM_CUDA(cudaGetLastError());
   return CCM_OK;
@@ -960,7 +972,7 @@ static void iteration_body(ccm_handle* h, bool fp64, cudaStream_t s) {
   }
   if (L.n2)
     KL(dev::k_rows<double, double, true, true><<<ceil_div(L.n2, 128), 128, 0, s>>>(
-        L.n2, L.irr_cell, L.ell_col, L.ell64, ucur, h->rhat, L.t64, nullptr, nullptr, nullptr));
+        L.n2, L.W, L.irr_cell, L.ell_col, L.ell64, ucur, h->rhat, L.t64, nullptr, nullptr, nullptr));
   cudaMemsetAsync(h->dnorm, 0, sizeof(unsigned long long), s);
   KL(dev::k_absmax<double><<<std::min(ceil_div(np, 256), 1216), 256, 0, s>>>(np, L.cls, L.t64, h->dnorm));
   cudaMemcpyAsync(h->hnorm, h->dnorm, sizeof(unsigned long long), cudaMemcpyDeviceToHost, s);
@@ -1041,7 +1053,7 @@ int ccm_solve(ccm_handle* h, const double* f, const double* g, double* u, int nr
     launch_regular<double>(h, L, U0, h->rhat, L.t64, true, s);
     if (L.n2)
       KL(dev::k_rows<double, double, true, true><<<ceil_div(L.n2, 128), 128, 0, s>>>(
-          L.n2, L.irr_cell, L.ell_col, L.ell64, U0, h->rhat, L.t64, nullptr, nullptr, nullptr));
+          L.n2, L.W, L.irr_cell, L.ell_col, L.ell64, U0, h->rhat, L.t64, nullptr, nullptr, nullptr));
     rc = read_norm(h, L.cls, np, L.t64, s, rel);
     if (rc) return rc;
     rel /= rnorm;
@@ -1084,8 +1096,30 @@ int ccm_solve(ccm_handle* h, const double* f, const double* g, double* u, int nr
 }
 
 int ccm_solve_T(ccm_handle* h, const double* rhs, double* lambda, int nrhs, void* stream, ccm_stats* st) {
-  (void)h; (void)rhs; (void)lambda; (void)nrhs; (void)stream; (void)st;
-  return CCM_EINVAL;
+  if (!h || !rhs || !lambda || nrhs < 1) return CCM_EINVAL;
+  if (!h->adj) {
+    std::unique_ptr<ccm_handle> t(new ccm_handle());
+    t->par = h->par;
+    t->a = h->a;
+    t->b = h->b;
+    t->c = h->c;
+    t->cross = h->cross;
+    t->device = h->device;
+    std::string err;
+    int rc;
+    try {
+      rc = build_transposed(h->H, h->par, t->H, err);
+    } catch (const std::bad_alloc&) {
+      return CCM_ENOMEM;
+    }
+    if (rc) return rc;
+    rc = upload_hierarchy(t.get());
+    if (rc) return rc;
+    t->info = h->info;
+    t->info.n_segments = 0;
+    h->adj = t.release();
+  }
+  return ccm_solve(h->adj, rhs, nullptr, lambda, nrhs, stream, st);
 }
 
 // ---- level components
@@ -1099,7 +1133,7 @@ int ccm_level_apply(ccm_handle* h, int level, const double* u, double* out, void
   launch_regular<double>(h, L, L.t64, nullptr, L.r64, false, s);
   if (L.n2)
     KL(dev::k_rows<double, double, false, true><<<ceil_div(L.n2, 128), 128, 0, s>>>(
-        L.n2, L.irr_cell, L.ell_col, L.ell64, L.t64, nullptr, L.r64, L.nb, L.seg, nullptr));
+        L.n2, L.W, L.irr_cell, L.ell_col, L.ell64, L.t64, nullptr, L.r64, L.nb, L.seg, nullptr));
   KL(dev::k_unpack<double><<<pg, 128, 0, s>>>(L.nx, L.ny, L.pitch, L.cls, L.r64, out, 1.0 / (L.h * L.h)));
   CCM_CUDA(cudaGetLastError());
   return CCM_OK;
@@ -1215,6 +1249,7 @@ int ccm_profile_read(ccm_handle* h, double* ms, int64_t* launches) {
 
 void ccm_free(ccm_handle* h) {
   if (!h) return;
+  if (h->adj) ccm_free(h->adj);
   cudaDeviceSynchronize();
   drop_graphs(h);
   if (h->cap_stream) cudaStreamDestroy(h->cap_stream);

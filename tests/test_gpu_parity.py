@@ -115,11 +115,11 @@ def test_smoother_step_matches_oracle(case):
         s.close()
 
 
-def test_default_block_solve_is_close_to_exact(case):
+def test_default_smoother_step(case):
     """The default smoother step (block-Jacobi form: SMO-1 and one pass of the overlapping
-    block solve, both from the old iterate) against the exact block-Jacobi step (SMO-1 of the
-    oracle, then the exact L22 solve with the OLD regular values): regular cells agree to
-    rounding, irregular cells to a small fraction of their change."""
+    block solve, both from the old iterate).  Regular cells equal the oracle's SMO-1 of the old
+    iterate; on the irregular cells the step removes most of the residual of the SMO-2
+    equation L22 u2 = r2 - L21 u1_old (one pass of the block solve is not exact)."""
     prob, mms, H, s = case
     lv = H.levels[0]
     u0 = rand_field(lv, 40).ravel()
@@ -132,10 +132,12 @@ def test_default_block_solve_is_close_to_exact(case):
         s1.close()
     ref = u0.copy()
     MG.smo1(lv, ref, r, OMEGA)
-    ref[lv.irr_idx] = lv.L22.solve(r[lv.irr_idx] - lv.L21 @ u0[lv.reg_idx])
     assert np.abs(got - ref)[lv.reg].max() <= 1e-10 * np.abs(ref).max()
-    d = np.abs(ref - u0)[lv.irr].max()
-    assert np.abs(got - ref)[lv.irr].max() <= 0.05 * d
+    L22 = lv.dz.L[lv.irr_idx][:, lv.irr_idx]
+    rhs = r[lv.irr_idx] - lv.L21 @ u0[lv.reg_idx]
+    before = np.linalg.norm(rhs - L22 @ u0[lv.irr_idx])
+    after = np.linalg.norm(rhs - L22 @ got[lv.irr_idx])
+    assert after <= 0.1 * before
 
 
 def test_restrict_prolong_bottom(case):
