@@ -91,8 +91,10 @@ typedef struct {
   int inner_cycles;  /* CCM_MIXED: FP32 V-cycles per FP64 residual evaluation */
   int smoother;      /* 0: SMO-1 then SMO-2 from the new regular values (Sec. 4.1, two launches);
                         1: block-Jacobi form, both from the old iterate (one launch per sweep) */
-  int coarse_n;      /* CCM_MIXED: levels with at most coarse_n cells a side run their part of the
-                        V-cycle in one CTA (0: never) */
+  int coarse_n;      /* levels with at most coarse_n cells a side run their part of every V-cycle
+                        as one launch of one thread-block cluster (16 or 8 CTAs of 1024
+                        threads, cluster barriers between the phases of Alg. 2); smoother 1
+                        with ras_passes <= 1 only; 0: never */
 } ccm_params;
 
 typedef struct {

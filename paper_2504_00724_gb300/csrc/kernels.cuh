@@ -241,6 +241,12 @@ __global__ void __launch_bounds__(256) k_jacobi_tma(const __grid_constant__ CUte
   }
 }
 
+// padded index of the parent (level m + 1) of a padded cell q of level m inside the domain
+__device__ __forceinline__ long parent_of(long q, int pitch, int pitchc) {
+  const int j = (int)(q / pitch), i = (int)(q - (long)j * pitch);
+  return (long)((j - 2) / 2 + 2) * pitchc + ((i - 2) / 2 + 2);
+}
+
 // ---- one smoothing sweep in one launch (block-Jacobi form of SMO-1 + SMO-2).
 // Both parts read only the old iterate and write only the new one: CTAs [0, ntiles) update
 // the regular cells (SMO-1), CTAs [ntiles, ntiles + nblk * chunks) the irregular cells by the
@@ -263,6 +269,9 @@ struct SweepArgs {
   const int32_t* col;
   const T* val;
   int* err;
+  const int32_t* colf;   // ELL columns with the sign bit on regular columns (prolongation)
+  const T* uc;           // coarse iterate: the sweep reads u + P uc (regular cells), or null
+  int pitchc;
 };
 
 template <typename T>
@@ -371,6 +380,87 @@ __global__ void __launch_bounds__(256) k_sweep(const __grid_constant__ CUtensorM
   }
 }
 
+// SMO-1 on one TMA-staged 64 x 32 tile (the regular cells; the SMO-2 blocks run in k_blocks
+// beside it).  With PRO the sweep is the first post-smoothing sweep of Alg. 2 and reads
+// u + P uc: the class bytes of the tile with its halo (80 x 36 box) and the coarse iterate
+// under it (36 x 18 box, x origin cx0 / 2, a multiple of 32 elements) arrive with the same
+// mbarrier, and the coarse correction is added to the regular cells of the staged tile
+// before the stencil runs (Sec. 4.2: prolongation to regular cells only).
+constexpr int CLX = 80, UCX = 36, UCY = HY / 2;
+
+template <typename T, bool CROSS, bool PRO>
+__global__ void __launch_bounds__(256) k_sweep_tma(const __grid_constant__ CUtensorMap tin,
+                                                   const __grid_constant__ CUtensorMap tcls,
+                                                   const __grid_constant__ CUtensorMap tuc, SweepArgs<T> a) {
+  __shared__ __align__(128) T tile[HY * HX];
+  __shared__ __align__(128) uint8_t ctile[PRO ? HY * CLX : 16];
+  __shared__ __align__(128) T uct[PRO ? UCY * UCX : 2];
+  __shared__ __align__(8) uint64_t bar;
+  const int cx0 = a.tiles[2 * blockIdx.x] * JX, cy0 = a.tiles[2 * blockIdx.x + 1] * JY;
+  if (threadIdx.x == 0) mbar_init(&bar, 1);
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    mbar_expect_tx(&bar, (uint32_t)(HX * HY * sizeof(T) + (PRO ? HY * CLX + UCY * UCX * sizeof(T) : 0)));
+    tma_load_2d(tile, &tin, &bar, cx0, cy0);
+    if (PRO) {
+      tma_load_2d(ctile, &tcls, &bar, cx0, cy0);
+      tma_load_2d(uct, &tuc, &bar, cx0 / 2, cy0 / 2 + 1);
+    }
+  }
+  const int x = threadIdx.x & 63, y0 = (threadIdx.x >> 6) * 8;
+  const int i = cx0 + x;
+  uint8_t cv[8];
+  T rv[8];
+#pragma unroll
+  for (int k = 0; k < 8; ++k) {
+    const int j = cy0 + y0 + k;
+    const long p = (long)(j + 2) * a.pitch + (i + 2);
+    const bool in = i < a.nx && j < a.ny;
+    if (!PRO) cv[k] = in ? a.cls[p] : (uint8_t)0;
+    rv[k] = in ? a.r[p] : (T)0;
+  }
+  bool ok = tile_wait(&bar, a.err);
+  if (PRO) {
+    // every thread passes the barrier; the staged cell (y, x) has its parent at
+    // (y / 2, x / 2 + 1) of the coarse box
+    if (ok)
+      for (int idx = threadIdx.x; idx < HY * HX; idx += blockDim.x) {
+        const int y = idx / HX, xx = idx - y * HX;
+        if (ctile[y * CLX + xx] == 1) tile[idx] += uct[(y >> 1) * UCX + (xx >> 1) + 1];
+      }
+    ok = __syncthreads_and(ok);
+#pragma unroll
+    for (int k = 0; k < 8; ++k) cv[k] = ctile[(y0 + k + 2) * CLX + x + 2];
+  }
+  if (!ok || i >= a.nx) return;
+  T w[5][5];
+#pragma unroll
+  for (int q = 0; q < 4; ++q)
+#pragma unroll
+    for (int b = 0; b < 5; ++b) w[q][b] = tile[(y0 + q) * HX + x + b];
+#pragma unroll
+  for (int k = 0; k < 8; ++k) {
+#pragma unroll
+    for (int b = 0; b < 5; ++b) w[4][b] = tile[(y0 + k + 4) * HX + x + b];
+    if (cv[k] == 1) {
+      T acc = 0;
+#pragma unroll
+      for (int q = 0; q < 5; ++q)
+#pragma unroll
+        for (int b = 0; b < 5; ++b) {
+          if (!CROSS && q != 2 && b != 2) continue;
+          acc += a.S.w[q * 5 + b] * w[q][b];
+        }
+      const long p = (long)(cy0 + y0 + k + 2) * a.pitch + (i + 2);
+      a.u_new[p] = w[2][2] + a.S.omega_d * (rv[k] - acc);
+    }
+#pragma unroll
+    for (int q = 0; q < 4; ++q)
+#pragma unroll
+      for (int b = 0; b < 5; ++b) w[q][b] = w[q + 1][b];
+  }
+}
+
 __device__ __forceinline__ void bulk_load(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
   asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
                    smem_u32(dst)),
@@ -403,8 +493,19 @@ __global__ void __launch_bounds__(256) k_blocks(SweepArgs<T> a) {
   for (int e = threadIdx.x; e < ne; e += blockDim.x) {
     const int row = es + e;
     T acc = 0;
+    if (a.uc) {
 #pragma unroll 15
-    for (int k = 0; k < a.W; ++k) acc += a.val[(long)k * a.n2 + row] * a.u_old[a.col[(long)k * a.n2 + row]];
+      for (int k = 0; k < a.W; ++k) {
+        const int f = a.colf[(long)k * a.n2 + row];
+        const long q = f & 0x7fffffff;
+        T v = a.u_old[q];
+        if (f < 0) v += a.uc[parent_of(q, a.pitch, a.pitchc)];
+        acc += a.val[(long)k * a.n2 + row] * v;
+      }
+    } else {
+#pragma unroll 15
+      for (int k = 0; k < a.W; ++k) acc += a.val[(long)k * a.n2 + row] * a.u_old[a.col[(long)k * a.n2 + row]];
+    }
     s[e] = a.r[a.cell[row]] - acc;
   }
   const bool ok = tile_wait(&bar, a.err);
@@ -430,21 +531,25 @@ __global__ void __launch_bounds__(256) k_blocks(SweepArgs<T> a) {
 }
 
 // TMA-staged residual + restriction: a 64 x 32 tile of fine cells (with its halo) gives the
-// residuals of all its cells in shared memory (regular cells by the stencil, irregular cells
-// by their fitted rows), then the 32 x 16 coarse cells it covers get the volume-weighted
-// restriction and a zero coarse iterate.
+// residuals of all its cells in shared memory, then the 32 x 16 coarse cells it covers get
+// the volume-weighted restriction and a zero coarse iterate.  The fitted rows of the tile's
+// irregular cells (listed per tile: row and position in the tile) are evaluated first, one
+// row per thread, while the tile copy is in flight; the regular cells then take the
+// stencil from the staged tile.  The cell volumes are read once, in the coarse phase.
 template <typename T, bool CROSS>
-__global__ void __launch_bounds__(256) k_restrict_tma(const __grid_constant__ CUtensorMap tin,
-                                                      const int32_t* __restrict__ tiles, int nxf, int nyf,
-                                                      int pitchf, const uint8_t* __restrict__ clsf,
-                                                      const T* __restrict__ volf, const int32_t* __restrict__ rowmap,
-                                                      int n2, int W, const int32_t* __restrict__ col,
-                                                      const T* __restrict__ val, const T* __restrict__ u,
-                                                      const T* __restrict__ r, int nxc, int nyc, int pitchc,
-                                                      const uint8_t* __restrict__ clsc, T* __restrict__ rc,
-                                                      T* __restrict__ uc, Stencil<T> S, int* __restrict__ err) {
+__global__ void __launch_bounds__(256, 4) k_restrict_tma(const __grid_constant__ CUtensorMap tin,
+                                                         const int32_t* __restrict__ tiles, int nxf, int nyf,
+                                                         int pitchf, const uint8_t* __restrict__ clsf,
+                                                         const T* __restrict__ volf, const int32_t* __restrict__ rr_off,
+                                                         const int32_t* __restrict__ rr, int n2, int W,
+                                                         const int32_t* __restrict__ irr_cell,
+                                                         const int32_t* __restrict__ col, const T* __restrict__ val,
+                                                         const T* __restrict__ u, const T* __restrict__ r, int nxc,
+                                                         int nyc, int pitchc, const uint8_t* __restrict__ clsc,
+                                                         T* __restrict__ rc, T* __restrict__ uc, Stencil<T> S,
+                                                         int* __restrict__ err) {
   __shared__ __align__(128) T tile[HY * HX];
-  __shared__ T wres[JY][JX];     // volume x residual of every fine cell of the tile
+  __shared__ T res[JY][JX];      // residual of every fine cell of the tile (0 on empty cells)
   __shared__ __align__(8) uint64_t bar;
   const int cx0 = tiles[2 * blockIdx.x] * JX, cy0 = tiles[2 * blockIdx.x + 1] * JY;
   if (threadIdx.x == 0) mbar_init(&bar, 1);
@@ -453,10 +558,18 @@ __global__ void __launch_bounds__(256) k_restrict_tma(const __grid_constant__ CU
     mbar_expect_tx(&bar, (uint32_t)(HX * HY * sizeof(T)));
     tma_load_2d(tile, &tin, &bar, cx0, cy0);
   }
+  const int k0 = rr_off[blockIdx.x], k1 = rr_off[blockIdx.x + 1];
+  for (int k = k0 + (int)threadIdx.x; k < k1; k += blockDim.x) {
+    const int row = rr[2 * k], loc = rr[2 * k + 1];
+    T acc = 0;
+#pragma unroll 15
+    for (int m = 0; m < W; ++m) acc += val[(long)m * n2 + row] * u[col[(long)m * n2 + row]];
+    res[loc >> 6][loc & 63] = r[irr_cell[row]] - acc;
+  }
   const int x = threadIdx.x & 63, y0 = (threadIdx.x >> 6) * 8;
   const int i = cx0 + x;
   uint8_t cv[8];
-  T rv[8], vv[8];
+  T rv[8];
 #pragma unroll
   for (int k = 0; k < 8; ++k) {
     const int j = cy0 + y0 + k;
@@ -464,7 +577,6 @@ __global__ void __launch_bounds__(256) k_restrict_tma(const __grid_constant__ CU
     const bool in = i < nxf && j < nyf;
     cv[k] = in ? clsf[p] : (uint8_t)0;
     rv[k] = in ? r[p] : (T)0;
-    vv[k] = in ? volf[p] : (T)0;
   }
   const bool ok = tile_wait(&bar, err);
   if (ok) {
@@ -477,7 +589,6 @@ __global__ void __launch_bounds__(256) k_restrict_tma(const __grid_constant__ CU
     for (int k = 0; k < 8; ++k) {
 #pragma unroll
       for (int b = 0; b < 5; ++b) w[4][b] = tile[(y0 + k + 4) * HX + x + b];
-      T res = 0;
       if (cv[k] == 1) {
         T acc = 0;
 #pragma unroll
@@ -487,24 +598,17 @@ __global__ void __launch_bounds__(256) k_restrict_tma(const __grid_constant__ CU
             if (!CROSS && q != 2 && b != 2) continue;
             acc += S.w[q * 5 + b] * w[q][b];
           }
-        res = rv[k] - acc;
-      } else if (cv[k] == 2) {
-        const long p = (long)(cy0 + y0 + k + 2) * pitchf + (i + 2);
-        const int row = rowmap[p];
-        T acc = 0;
-#pragma unroll 15
-        for (int m = 0; m < W; ++m) acc += val[(long)m * n2 + row] * u[col[(long)m * n2 + row]];
-        res = rv[k] - acc;
+        res[y0 + k][x] = rv[k] - acc;
+      } else if (cv[k] == 0) {
+        res[y0 + k][x] = (T)0;
       }
-      wres[y0 + k][x] = vv[k] * res;
 #pragma unroll
       for (int q = 0; q < 4; ++q)
 #pragma unroll
         for (int b = 0; b < 5; ++b) w[q][b] = w[q + 1][b];
     }
   }
-  __syncthreads();
-  if (!ok) return;
+  if (!__syncthreads_and(ok)) return;
   // 32 x 16 coarse cells, two per thread
   for (int t = threadIdx.x; t < (JX / 2) * (JY / 2); t += blockDim.x) {
     const int ci = t % (JX / 2), cj = t / (JX / 2);
@@ -512,9 +616,11 @@ __global__ void __launch_bounds__(256) k_restrict_tma(const __grid_constant__ CU
     if (I >= nxc || J >= nyc) continue;
     const long pc = (long)(J + 2) * pitchc + (I + 2);
     if (clsc[pc] == 0) continue;
-    const T s = wres[2 * cj][2 * ci] + wres[2 * cj][2 * ci + 1] + wres[2 * cj + 1][2 * ci] + wres[2 * cj + 1][2 * ci + 1];
     const long f0 = (long)(2 * J + 2) * pitchf + (2 * I + 2);
-    const T sv = volf[f0] + volf[f0 + 1] + volf[f0 + pitchf] + volf[f0 + pitchf + 1];
+    const T v0 = volf[f0], v1 = volf[f0 + 1], v2 = volf[f0 + pitchf], v3 = volf[f0 + pitchf + 1];
+    const T s = v0 * res[2 * cj][2 * ci] + v1 * res[2 * cj][2 * ci + 1] + v2 * res[2 * cj + 1][2 * ci] +
+                v3 * res[2 * cj + 1][2 * ci + 1];
+    const T sv = v0 + v1 + v2 + v3;
     rc[pc] = sv > (T)0 ? (T)4 * s / sv : (T)0;
     uc[pc] = (T)0;
   }
@@ -717,173 +823,6 @@ __global__ void k_bottom(int n, const int32_t* __restrict__ cell, const T* __res
     T tot = 0;
     for (int w = 0; w < nw; ++w) tot += part[w * 32 + threadIdx.x];
     u[cell[k]] = tot;
-  }
-}
-
-// ---- the small levels of a V-cycle in one CTA.
-// Levels with few cells spend their time in launch latency, not in work, so the part of
-// Alg. 2 from level `first` down to the bottom and back runs as one CTA of 1024 threads with
-// __syncthreads() between the phases (SMO-1, SMO-2 residuals, SMO-2 block corrections,
-// residual + restriction, bottom solve, prolongation fused into SMO-1).
-constexpr int MAXC = 8;
-
-template <typename T>
-struct CoarseLevel {
-  int nx, ny, pitch, n2, nblk, nbc, core, W;
-  const uint8_t* cls;
-  const T* vol;
-  T* u[2];
-  T* r;
-  T* t;
-  T* res;
-  const int32_t* irr_cell;
-  const int32_t* colf;
-  const T* val;
-  const int32_t* blk;
-  const int64_t* blk_off;
-  const T* inv;
-  const int32_t* bot_cell;
-  const T* bot;
-};
-
-template <typename T>
-struct CoarseParams {
-  int nlev, nu1, nu2, passes, jacobi;
-  int cur[MAXC];
-  CoarseLevel<T> L[MAXC];
-  Stencil<T> S;
-};
-
-template <typename T, bool CROSS>
-__device__ void cta_sweep(const CoarseLevel<T>& L, int& cur, const Stencil<T>& S, int passes, const T* uc, int pitchc,
-                          bool jacobi) {
-  T* uin = L.u[cur];
-  T* uout = L.u[1 - cur];
-  if (jacobi && uc) {
-    // prolongation first (regular cells of the old iterate), then the block-Jacobi sweep
-    const int n = L.nx * L.ny;
-    for (int idx = threadIdx.x; idx < n; idx += blockDim.x) {
-      const int i = idx % L.nx, j = idx / L.nx;
-      const long p = (long)(j + 2) * L.pitch + (i + 2);
-      if (L.cls[p] == 1) uin[p] += uc[(long)(j / 2 + 2) * pitchc + (i / 2 + 2)];
-    }
-    __syncthreads();
-    uc = nullptr;
-  }
-  const int n = L.nx * L.ny;
-  for (int idx = threadIdx.x; idx < n; idx += blockDim.x) {
-    const int i = idx % L.nx, j = idx / L.nx;
-    const long p = (long)(j + 2) * L.pitch + (i + 2);
-    if (L.cls[p] != 1) continue;
-    T acc = 0, vp = 0;
-#pragma unroll
-    for (int dj = -2; dj <= 2; ++dj)
-#pragma unroll
-      for (int di = -2; di <= 2; ++di) {
-        if (!CROSS && dj != 0 && di != 0) continue;
-        const long q = p + (long)dj * L.pitch + di;
-        T v = uin[q];
-        if (uc && L.cls[q] == 1) v += uc[(long)((j + dj) / 2 + 2) * pitchc + ((i + di) / 2 + 2)];
-        acc += S.w[(dj + 2) * 5 + di + 2] * v;
-        if (dj == 0 && di == 0) vp = v;
-      }
-    uout[p] = vp + S.omega_d * (L.r[p] - acc);
-  }
-  __syncthreads();
-  for (int pass = 0; pass < max(1, passes); ++pass) {
-    const T* rd_irr = pass == 0 ? uin : uout;
-    const T* rd_reg = (jacobi && pass == 0) ? uin : uout;
-    for (int row = threadIdx.x; row < L.n2; row += blockDim.x) {
-      T acc = 0;
-#pragma unroll 15
-      for (int k = 0; k < L.W; ++k) {
-        const int f = L.colf[(long)k * L.n2 + row];
-        const int q = f & 0x7fffffff;
-        acc += L.val[(long)k * L.n2 + row] * (f < 0 ? rd_reg[q] : rd_irr[q]);
-      }
-      L.res[row] = L.r[L.irr_cell[row]] - acc;
-    }
-    __syncthreads();
-    for (int c = threadIdx.x; c < L.n2; c += blockDim.x) {
-      const int b = min(c / L.core, L.nblk - 1);
-      const int cs = L.blk[4 * b], ce = L.blk[4 * b + 1], es = L.blk[4 * b + 2], ee = L.blk[4 * b + 3];
-      const int nc = ce - cs;
-      const T* A = L.inv + L.blk_off[b];
-      T acc = 0;
-      for (int e = es; e < ee; ++e) acc += A[(long)(e - es) * nc + (c - cs)] * L.res[e];
-      const long q = L.irr_cell[c];
-      uout[q] = rd_irr[q] + acc;
-    }
-    __syncthreads();
-  }
-  cur = 1 - cur;
-}
-
-template <typename T, bool CROSS>
-__global__ void __launch_bounds__(1024) k_coarse_vcycle(CoarseParams<T> P) {
-  int cur[MAXC];
-#pragma unroll
-  for (int m = 0; m < MAXC; ++m) cur[m] = P.cur[m];
-  const int last = P.nlev - 1;
-  for (int m = 0; m < last; ++m) {
-    const CoarseLevel<T>& F = P.L[m];
-    const CoarseLevel<T>& C = P.L[m + 1];
-    for (int k = 0; k < P.nu1; ++k) cta_sweep<T, CROSS>(F, cur[m], P.S, P.passes, nullptr, 0, P.jacobi);
-    // residual of the fitted rows into t, then residual + restriction, coarse u = 0
-    T* u = F.u[cur[m]];
-    for (int row = threadIdx.x; row < F.n2; row += blockDim.x) {
-      T acc = 0;
-#pragma unroll 15
-      for (int k = 0; k < F.W; ++k) acc += F.val[(long)k * F.n2 + row] * u[F.colf[(long)k * F.n2 + row] & 0x7fffffff];
-      F.t[F.irr_cell[row]] = F.r[F.irr_cell[row]] - acc;
-    }
-    __syncthreads();
-    T* ucz = C.u[cur[m + 1]];
-    for (int idx = threadIdx.x; idx < C.nx * C.ny; idx += blockDim.x) {
-      const int I = idx % C.nx, J = idx / C.nx;
-      const long pc = (long)(J + 2) * C.pitch + (I + 2);
-      if (C.cls[pc] == 0) continue;
-      const long f0 = (long)(2 * J + 2) * F.pitch + (2 * I + 2);
-      T s = 0, sv = 0;
-      for (int k = 0; k < 4; ++k) {
-        const long q = f0 + (k >> 1) * (long)F.pitch + (k & 1);
-        const uint8_t c = F.cls[q];
-        if (c == 0) continue;
-        const T res = c == 1 ? F.r[q] - stencil_apply<T, CROSS>(u, q, F.pitch, P.S) : F.t[q];
-        s += F.vol[q] * res;
-        sv += F.vol[q];
-      }
-      C.r[pc] = sv > (T)0 ? (T)4 * s / sv : (T)0;
-      ucz[pc] = (T)0;
-    }
-    __syncthreads();
-  }
-  {
-    const CoarseLevel<T>& B = P.L[last];
-    T* u = B.u[cur[last]];
-    for (int k = threadIdx.x; k < B.nbc; k += blockDim.x) {
-      T acc = 0;
-      for (int c = 0; c < B.nbc; ++c) acc += B.bot[(long)c * B.nbc + k] * B.r[B.bot_cell[c]];
-      u[B.bot_cell[k]] = acc;
-    }
-    __syncthreads();
-  }
-  for (int m = last - 1; m >= 0; --m) {
-    const CoarseLevel<T>& F = P.L[m];
-    const CoarseLevel<T>& C = P.L[m + 1];
-    if (P.nu2 == 0) {
-      T* u = F.u[cur[m]];
-      const T* uc = C.u[cur[m + 1]];
-      for (int idx = threadIdx.x; idx < F.nx * F.ny; idx += blockDim.x) {
-        const int i = idx % F.nx, j = idx / F.nx;
-        const long p = (long)(j + 2) * F.pitch + (i + 2);
-        if (F.cls[p] == 1) u[p] += uc[(long)(j / 2 + 2) * C.pitch + (i / 2 + 2)];
-      }
-      __syncthreads();
-      continue;
-    }
-    cta_sweep<T, CROSS>(F, cur[m], P.S, P.passes, C.u[cur[m + 1]], C.pitch, P.jacobi);
-    for (int k = 1; k < P.nu2; ++k) cta_sweep<T, CROSS>(F, cur[m], P.S, P.passes, nullptr, 0, P.jacobi);
   }
 }
 

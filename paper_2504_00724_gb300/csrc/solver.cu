@@ -17,6 +17,7 @@
 
 #include "hierarchy.h"
 #include "kernels.cuh"
+#include "coarse.cuh"
 
 using namespace ccm;
 
@@ -35,6 +36,11 @@ struct DevLevel {
   bool stage_blocks = false;    // SMO-2 block inverses fit in shared memory (bulk-staged kernel)
   bool tma = false;             // TMA-staged SMO-1 on this level
   CUtensorMap tm64[2], tm32[2]; // 68 x 36 boxes over the u buffers
+  CUtensorMap tmcls;            // 80 x 36 box over the class bytes
+  CUtensorMap tmuc64[2], tmuc32[2];  // 36 x 18 boxes over level m + 1's u buffers
+  bool tma_pro = false;         // the maps above exist: prolongation fuses into the sweep
+  int32_t* rr_off = nullptr;    // per restriction tile: its irregular rows [rr_off[t], rr_off[t + 1])
+  int32_t* rr = nullptr;        // (row, y * 64 + x in the tile) pairs
   uint8_t* cls = nullptr;
   double* vol64 = nullptr;
   float* vol32 = nullptr;
@@ -143,7 +149,9 @@ struct ccm_handle {
   std::vector<cudaEvent_t> gprof_ev;  // pairs baked into the iteration graphs
   double prof_ms = 0;                 // accumulated from graph replays
   long long prof_n = 0;
-  int coarse_first = 1 << 30;  // first level run by the one-CTA coarse cycle (FP32)
+  int coarse_first = 1 << 30;  // first level whose part of the V-cycle runs as one cluster launch
+  int coarse_ctas = 0;         // CTAs of that cluster (16, else 8)
+  size_t coarse_smem = 0;      // its dynamic shared memory (SMO-2 extended-row residuals)
   ccm_handle* adj = nullptr;   // the transposed operators' hierarchy (built by ccm_solve_T)
   // one CUDA graph per outer iteration and precision (captured on first use, on a private
   // stream: the legacy default stream cannot be captured)
@@ -251,9 +259,20 @@ void residual(ccm_handle* H, DevLevel& L, const T* u, const T* r, T* out, cudaSt
 template <typename T>
 void prolong_from(ccm_handle* H, DevLevel& F, DevLevel& C, cudaStream_t s);
 
-// block-Jacobi form: SMO-1 and SMO-2 both from the old iterate, one launch
+template <typename T> const CUtensorMap& TmUc(const DevLevel& F, const DevLevel& C);
+template <> const CUtensorMap& TmUc<double>(const DevLevel& F, const DevLevel& C) { return F.tmuc64[C.cur64]; }
+template <> const CUtensorMap& TmUc<float>(const DevLevel& F, const DevLevel& C) { return F.tmuc32[C.cur32]; }
+
+// block-Jacobi form: SMO-1 and SMO-2 both from the old iterate, one launch (plus the SMO-2
+// blocks on a parallel branch where their inverses are staged).  C != null: the first
+// post-smoothing sweep, which reads u + P uc with uc the iterate of level C.
 template <typename T>
-void sweep_one_launch(ccm_handle* H, DevLevel& L, cudaStream_t s) {
+void sweep_one_launch(ccm_handle* H, DevLevel& L, cudaStream_t s, DevLevel* C = nullptr) {
+  const bool staged = L.tma && (L.nblk == 0 || L.stage_blocks);
+  if (C && !(staged && L.tma_pro)) {
+    prolong_from<T>(H, L, *C, s);
+    C = nullptr;
+  }
   dev::SweepArgs<T> a{};
   const bool tma = L.tma;
   a.tiles = tma ? L.tiles64 : L.tiles;
@@ -278,6 +297,9 @@ void sweep_one_launch(ccm_handle* H, DevLevel& L, cudaStream_t s) {
   a.col = L.ell_col;
   a.val = Ell<T>(L);
   a.err = H->derr;
+  a.colf = L.ell_colf;
+  a.uc = C ? U<T>(*C) : nullptr;
+  a.pitchc = C ? C->pitch : 0;
   const bool l0 = &L == &H->L[0];
   ProfScope ps(H, !l0 ? 0 : (sizeof(T) == 4 ? CCM_PROF_SMO1_FP32 : CCM_PROF_SMO1_FP64), s);
   if (L.stage_blocks && a.nblk) {
@@ -292,19 +314,28 @@ void sweep_one_launch(ccm_handle* H, DevLevel& L, cudaStream_t s) {
     KL(dev::k_blocks<T><<<b.nblk * b.chunks, 256, bsm, H->side>>>(b));
     cudaEventRecord(H->ev_join, H->side);
   }
-  const int grid = a.ntiles + a.nblk * a.chunks;
-  const size_t smem = (size_t)std::max(1, L.max_ext) * sizeof(T);
   const CUtensorMap& tm = TmU<T>(L);
-  if (grid == 0) {
-    if (L.stage_blocks && L.nblk) cudaStreamWaitEvent(s, H->ev_join, 0);
-    return;
-  }
-  if (tma) {
-    if (H->cross) KL(dev::k_sweep<T, true, true><<<grid, 256, smem, s>>>(tm, a));
-    else KL(dev::k_sweep<T, false, true><<<grid, 256, smem, s>>>(tm, a));
+  if (staged && a.ntiles) {
+    if (C) {
+      const CUtensorMap& tu = TmUc<T>(L, *C);
+      if (H->cross) KL(dev::k_sweep_tma<T, true, true><<<a.ntiles, 256, 0, s>>>(tm, L.tmcls, tu, a));
+      else KL(dev::k_sweep_tma<T, false, true><<<a.ntiles, 256, 0, s>>>(tm, L.tmcls, tu, a));
+    } else {
+      if (H->cross) KL(dev::k_sweep_tma<T, true, false><<<a.ntiles, 256, 0, s>>>(tm, tm, tm, a));
+      else KL(dev::k_sweep_tma<T, false, false><<<a.ntiles, 256, 0, s>>>(tm, tm, tm, a));
+    }
   } else {
-    if (H->cross) KL(dev::k_sweep<T, true, false><<<grid, 256, smem, s>>>(tm, a));
-    else KL(dev::k_sweep<T, false, false><<<grid, 256, smem, s>>>(tm, a));
+    const int grid = a.ntiles + a.nblk * a.chunks;
+    const size_t smem = (size_t)std::max(1, L.max_ext) * sizeof(T);
+    if (grid > 0) {
+      if (tma) {
+        if (H->cross) KL(dev::k_sweep<T, true, true><<<grid, 256, smem, s>>>(tm, a));
+        else KL(dev::k_sweep<T, false, true><<<grid, 256, smem, s>>>(tm, a));
+      } else {
+        if (H->cross) KL(dev::k_sweep<T, true, false><<<grid, 256, smem, s>>>(tm, a));
+        else KL(dev::k_sweep<T, false, false><<<grid, 256, smem, s>>>(tm, a));
+      }
+    }
   }
   if (L.stage_blocks && L.nblk) cudaStreamWaitEvent(s, H->ev_join, 0);
 }
@@ -312,8 +343,7 @@ void sweep_one_launch(ccm_handle* H, DevLevel& L, cudaStream_t s) {
 template <typename T>
 void smooth_step(ccm_handle* H, DevLevel& L, cudaStream_t s, const T* uc = nullptr, int pitchc = 0) {
   if (H->par.smoother == 1 && H->par.ras_passes <= 1) {
-    if (uc) prolong_from<T>(H, L, H->L[&L - &H->L[0] + 1], s);
-    sweep_one_launch<T>(H, L, s);
+    sweep_one_launch<T>(H, L, s, uc ? &H->L[&L - &H->L[0] + 1] : nullptr);
     flip<T>(L);
     return;
   }
@@ -364,12 +394,14 @@ void restrict_to(ccm_handle* H, DevLevel& F, DevLevel& C, cudaStream_t s) {
     const auto& S = stencil<T>(H);
     if (H->cross)
       KL(dev::k_restrict_tma<T, true><<<F.ntiles64r, 256, 0, s>>>(TmU<T>(F), F.tiles64r, F.nx, F.ny, F.pitch, F.cls, Vol<T>(F),
-                                                                 F.rowmap, F.n2, F.W, F.ell_col, Ell<T>(F), U<T>(F), R<T>(F),
-                                                                 C.nx, C.ny, C.pitch, C.cls, R<T>(C), U<T>(C), S, H->derr));
+                                                         F.rr_off, F.rr, F.n2, F.W, F.irr_cell, F.ell_col, Ell<T>(F),
+                                                         U<T>(F), R<T>(F), C.nx, C.ny, C.pitch, C.cls, R<T>(C), U<T>(C), S,
+                                                         H->derr));
     else
       KL(dev::k_restrict_tma<T, false><<<F.ntiles64r, 256, 0, s>>>(TmU<T>(F), F.tiles64r, F.nx, F.ny, F.pitch, F.cls, Vol<T>(F),
-                                                                  F.rowmap, F.n2, F.W, F.ell_col, Ell<T>(F), U<T>(F), R<T>(F),
-                                                                  C.nx, C.ny, C.pitch, C.cls, R<T>(C), U<T>(C), S, H->derr));
+                                                         F.rr_off, F.rr, F.n2, F.W, F.irr_cell, F.ell_col, Ell<T>(F),
+                                                         U<T>(F), R<T>(F), C.nx, C.ny, C.pitch, C.cls, R<T>(C), U<T>(C), S,
+                                                         H->derr));
     return;
   }
   if (H->par.smoother == 1) {
@@ -410,31 +442,69 @@ void bottom(ccm_handle* H, DevLevel& B, cudaStream_t s) {
   KL(dev::k_bottom<T><<<ceil_div(B.nbc, 32), nw * 32, sm, s>>>(B.nbc, B.bot_cell, Bot<T>(B), R<T>(B), U<T>(B)));
 }
 
-// the levels from m down run in one CTA (FP32 cycles, levels with at most 64 cells a side)
-void coarse_cta(ccm_handle* H, int m, cudaStream_t s) {
+// the levels from m down to the bottom run as one launch of one thread-block cluster
+template <typename T>
+void coarse_cluster(ccm_handle* H, int m, cudaStream_t s) {
   const int M = (int)H->L.size() - 1;
-  dev::CoarseParams<float> P{};
+  dev::CoarseParams<T> P{};
   P.nlev = M - m + 1;
   P.nu1 = H->par.nu1;
   P.nu2 = H->par.nu2;
-  P.passes = H->par.ras_passes;
-  P.jacobi = H->par.smoother == 1 && H->par.ras_passes <= 1;
-  P.S = H->S32;
+  P.S = stencil<T>(H);
   for (int k = 0; k < P.nlev; ++k) {
     DevLevel& L = H->L[m + k];
-    dev::CoarseLevel<float>& C = P.L[k];
+    dev::CoarseLevel<T>& C = P.L[k];
     C.nx = L.nx; C.ny = L.ny; C.pitch = L.pitch; C.n2 = L.n2; C.nblk = L.nblk; C.nbc = L.nbc; C.W = L.W;
-    C.core = L.max_core > 0 ? L.max_core : 1;
-    C.cls = L.cls; C.vol = L.vol32; C.u[0] = L.u32[0]; C.u[1] = L.u32[1]; C.r = L.r32; C.t = L.t32;
-    C.res = L.res32; C.irr_cell = L.irr_cell; C.colf = L.ell_colf; C.val = L.ell32; C.blk = L.blk;
-    C.blk_off = L.blk_off; C.inv = L.inv32; C.bot_cell = L.bot_cell; C.bot = L.bot32;
-    P.cur[k] = L.cur32;
+    C.cls = L.cls; C.vol = Vol<T>(L); C.r = R<T>(L);
+    C.u[0] = sizeof(T) == 8 ? (T*)L.u64[0] : (T*)L.u32[0];
+    C.u[1] = sizeof(T) == 8 ? (T*)L.u64[1] : (T*)L.u32[1];
+    C.irr_cell = L.irr_cell; C.rowmap = L.rowmap; C.colf = L.ell_colf; C.val = Ell<T>(L);
+    C.blk = L.blk; C.blk_off = L.blk_off; C.inv = Inv<T>(L); C.bot_cell = L.bot_cell; C.bot = Bot<T>(L);
+    P.cur[k] = sizeof(T) == 8 ? L.cur64 : L.cur32;
   }
-  if (H->cross) KL(dev::k_coarse_vcycle<float, true><<<1, 1024, 0, s>>>(P));
-  else KL(dev::k_coarse_vcycle<float, false><<<1, 1024, 0, s>>>(P));
+  cudaLaunchConfig_t cfg{};
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = H->coarse_ctas;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.gridDim = dim3(H->coarse_ctas);
+  cfg.blockDim = dim3(dev::COARSE_THREADS);
+  cfg.dynamicSmemBytes = H->coarse_smem / 8 * sizeof(T);
+  cfg.stream = s;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  if (H->cross) KL(cudaLaunchKernelEx(&cfg, dev::k_coarse_cluster<T, true>, P));
+  else KL(cudaLaunchKernelEx(&cfg, dev::k_coarse_cluster<T, false>, P));
   const int flips = H->par.nu2 > 0 ? H->par.nu1 + H->par.nu2 : H->par.nu1;
   for (int k = 0; k + 1 < P.nlev; ++k)
-    if (flips & 1) flip<float>(H->L[m + k]);
+    if (flips & 1) flip<T>(H->L[m + k]);
+}
+
+// cluster size for the coarse launch: 16 CTAs where the device schedules them, else 8
+template <typename T, bool CROSS>
+int coarse_cluster_ctas(size_t smem) {
+  auto k = dev::k_coarse_cluster<T, CROSS>;
+  if (smem > 48 * 1024 && cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
+    return 0;
+  cudaFuncSetAttribute(k, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+  for (int cs : {16, 8}) {
+    cudaLaunchConfig_t cfg{};
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = cs;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.gridDim = dim3(cs);
+    cfg.blockDim = dim3(dev::COARSE_THREADS);
+    cfg.dynamicSmemBytes = smem;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    int n = 0;
+    if (cudaOccupancyMaxActiveClusters(&n, k, &cfg) == cudaSuccess && n >= 1) return cs;
+  }
+  cudaGetLastError();
+  return 0;
 }
 
 // Alg. 2 from level m: solves L^(m) u = r^(m) approximately, u = U<T>(level m)
@@ -446,8 +516,8 @@ void vcycle(ccm_handle* H, int m, cudaStream_t s) {
     bottom<T>(H, F, s);
     return;
   }
-  if (sizeof(T) == 4 && m >= H->coarse_first && M - m + 1 <= dev::MAXC) {
-    coarse_cta(H, m, s);
+  if (m >= H->coarse_first && M - m + 1 <= dev::MAXC) {
+    coarse_cluster<T>(H, m, s);
     return;
   }
   DevLevel& C = H->L[m + 1];
@@ -487,8 +557,8 @@ void load_level(ccm_handle* h, DevLevel& L, const double* u, const double* r, cu
   if (r) KL(dev::k_pack<T, double><<<pg, 128, 0, s>>>(L.nx, L.ny, L.pitch, L.cls, r, R<T>(L), L.h * L.h));
 }
 
-// 2-D tensor map over a padded level array: box of 68 x 36 elements, zero fill outside
-bool make_tmap(CUtensorMap* map, void* base, int pitch, int rows, bool fp64) {
+// 2-D tensor map over a padded level array (pitch x rows elements), zero fill outside
+bool make_tmap(CUtensorMap* map, void* base, int pitch, int rows, CUtensorMapDataType dt, size_t es, int bx, int by) {
   static PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
   if (!encode) {
     void* fn = nullptr;
@@ -498,15 +568,19 @@ bool make_tmap(CUtensorMap* map, void* base, int pitch, int rows, bool fp64) {
       return false;
     encode = (PFN_cuTensorMapEncodeTiled_v12000)fn;
   }
-  const size_t es = fp64 ? 8 : 4;
   cuuint64_t dims[2] = {(cuuint64_t)pitch, (cuuint64_t)rows};
   cuuint64_t strides[1] = {(cuuint64_t)pitch * es};
-  cuuint32_t box[2] = {(cuuint32_t)dev::HX, (cuuint32_t)dev::HY};
+  cuuint32_t box[2] = {(cuuint32_t)bx, (cuuint32_t)by};
   cuuint32_t estr[2] = {1, 1};
-  CUresult r = encode(map, fp64 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT64 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, base, dims,
-                      strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
-                      CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  CUresult r = encode(map, dt, 2, base, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                      CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   return r == CUDA_SUCCESS;
+}
+
+// the 68 x 36 halo tile box of the SMO-1 and restriction kernels
+bool make_tmap(CUtensorMap* map, void* base, int pitch, int rows, bool fp64) {
+  return make_tmap(map, base, pitch, rows, fp64 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT64 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32,
+                   fp64 ? 8 : 4, dev::HX, dev::HY);
 }
 
 // Device copies of a host hierarchy (every level's arrays, work space, tensor maps, streams)
@@ -643,14 +717,52 @@ int upload_hierarchy(ccm_handle* h) {
         }
       d.ntiles64r = (int)t.size() / 2;
       if (d.ntiles64r) d.tiles64r = A.upload(t);
+      // each restriction tile's irregular cells: (row, position in the tile)
+      std::vector<int32_t> off(1, 0), rr;
+      std::vector<int32_t> rowof(hf.npad(), -1);
+      for (int r = 0; r < hf.n2; ++r) rowof[hf.irr_cell[r]] = r;
+      for (int k = 0; k < d.ntiles64r; ++k) {
+        const int a = t[2 * k], b = t[2 * k + 1];
+        for (int j = b * 32; j < std::min(hf.ny, b * 32 + 32); ++j)
+          for (int i = a * 64; i < std::min(hf.nx, a * 64 + 64); ++i) {
+            const int r = rowof[hf.pad(i, j)];
+            if (r < 0) continue;
+            rr.push_back(r);
+            rr.push_back((j - b * 32) * 64 + (i - a * 64));
+          }
+        off.push_back((int32_t)(rr.size() / 2));
+      }
+      if (d.ntiles64r) d.rr_off = A.upload(off);
+      if (!rr.empty()) d.rr = A.upload(rr);
+      // the first post-smoothing sweep reads u + P uc through two more boxes
+      DevLevel& c = h->L[m + 1];
+      d.tma_pro = make_tmap(&d.tmcls, d.cls, d.pitch, d.rows, CU_TENSOR_MAP_DATA_TYPE_UINT8, 1, dev::CLX, dev::HY);
+      for (int b = 0; b < 2 && d.tma_pro; ++b)
+        d.tma_pro = make_tmap(&d.tmuc64[b], c.u64[b], c.pitch, c.rows, CU_TENSOR_MAP_DATA_TYPE_FLOAT64, 8, dev::UCX, dev::UCY) &&
+                    make_tmap(&d.tmuc32[b], c.u32[b], c.pitch, c.rows, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, dev::UCX, dev::UCY);
     }
   }
-  // the one-CTA coarse cycle takes over from the first level with at most 64 cells a side
-  for (int m = 1; m < nl && h->par.coarse_n > 0; ++m)
-    if (h->L[m].nx <= h->par.coarse_n && h->L[m].ny <= h->par.coarse_n && (h->L[m].n2 == 0 || h->L[m].nblk > 0)) {
-      h->coarse_first = m;
-      break;
+  // the cluster launch takes over from the first level with at most coarse_n cells a side
+  // (block-Jacobi smoother only: its sweeps read nothing but the old iterate)
+  if (h->par.coarse_n > 0 && h->par.smoother == 1 && h->par.ras_passes <= 1) {
+    int first = -1;
+    for (int m = 1; m < nl; ++m)
+      if (h->L[m].nx <= h->par.coarse_n && h->L[m].ny <= h->par.coarse_n) {
+        first = m;
+        break;
+      }
+    if (first > 0 && nl - first <= dev::MAXC) {
+      int ext = std::max(1, h->L[nl - 1].nbc);
+      for (int m = first; m < nl; ++m) ext = std::max(ext, h->L[m].max_ext);
+      h->coarse_smem = (size_t)ext * sizeof(double);
+      const int c64 = h->cross ? coarse_cluster_ctas<double, true>(h->coarse_smem)
+                               : coarse_cluster_ctas<double, false>(h->coarse_smem);
+      const int c32 = h->cross ? coarse_cluster_ctas<float, true>(h->coarse_smem / 2)
+                               : coarse_cluster_ctas<float, false>(h->coarse_smem / 2);
+      h->coarse_ctas = std::min(c64, c32);
+      if (h->coarse_ctas > 0) h->coarse_first = first;
     }
+  }
   h->rhat = A.alloc<double>(h->L[0].npad);
   h->uhat = A.alloc<double>(h->L[0].npad);
   h->dnorm = A.alloc<unsigned long long>(1);

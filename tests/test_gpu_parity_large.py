@@ -64,3 +64,54 @@ def test_large_solve(big, precision):
         assert np.abs(host(u) - want).max() <= 1e-10 * np.abs(want).max()
     finally:
         s.close()
+
+
+def test_large_level_restrict(big):
+    """Residual + restriction of the TMA-staged kernel (level 0 here) against the oracle."""
+    prob, mms, H = big
+    s = P.Solver(prob)
+    try:
+        f, c = H.levels[0], H.levels[1]
+        rng = np.random.default_rng(21)
+        u = np.where(f.ne, rng.standard_normal(f.nx * f.ny), 0.0).reshape(f.ny, f.nx)
+        r = np.where(f.ne, rng.standard_normal(f.nx * f.ny), 0.0).reshape(f.ny, f.nx) / f.h ** 2
+        got = host(s.level_restrict(0, cuda(u), cuda(r))).ravel()
+        want = MG.restrict(f, c, MG.residual(f, u.ravel(), r.ravel()))
+        scale = MG.restrict(f, c, np.abs(r.ravel()) + abs(f.dz.L) @ np.abs(u.ravel()))
+        assert np.all(np.abs(got - want) <= 1e-10 * scale + 1e-300)
+    finally:
+        s.close()
+
+
+def _composed_vcycle(s, levels, m, u, r, nu1=3, nu2=3):
+    """Alg. 2 spelled out through the per-level entry points (separate prolongation, no
+    coarse-level cluster launch)."""
+    if m == levels - 1:
+        return s.bottom_solve(r)
+    for _ in range(nu1):
+        u = s.level_smooth(m, u, r)
+    rc = s.level_restrict(m, u, r)
+    uc = _composed_vcycle(s, levels, m + 1, torch.zeros_like(rc), rc, nu1, nu2)
+    u = s.level_prolong(m, uc, u)
+    for _ in range(nu2):
+        u = s.level_smooth(m, u, r)
+    return u
+
+
+@pytest.mark.parametrize("n,coarse_n", [(576, 0), (576, 80), (288, 150)])
+def test_vcycle_equals_composed_level_calls(n, coarse_n):
+    """ccm_vcycle (prolongation fused into the first post-smoothing sweep on TMA levels, the
+    small levels in one cluster launch) equals the same V-cycle built from the per-level
+    calls, in FP64, with the default block-Jacobi smoother."""
+    prob = W.star(n)
+    s = P.Solver(prob, coarse_n=coarse_n)
+    try:
+        st = s.cell_map()[0]
+        rng = np.random.default_rng(n + coarse_n)
+        u0 = cuda(np.where(st != 0, rng.standard_normal(st.shape), 0.0))
+        r = cuda(np.where(st != 0, rng.standard_normal(st.shape), 0.0) * n * n)
+        want = host(_composed_vcycle(s, s.info.levels, 0, u0.clone(), r))
+        got = host(s.vcycle(u0.clone(), r, P.CCM_FP64))
+        assert np.abs(got - want).max() <= 1e-12 * np.abs(want).max()
+    finally:
+        s.close()
