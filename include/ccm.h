@@ -233,7 +233,9 @@ int ccm_vcycle(ccm_handle* h, double* u, const double* r, int precision, void* s
  * ccm_launch_count: kernels launched by this library in this process so far (all handles).
  * ccm_profile: record CUDA events on the handle's stream around every launch of one class:
  *   CCM_PROF_RESID_FP64  level-0 FP64 residual of the regular cells (outer iteration),
- *   CCM_PROF_SMO1_FP32   level-0 SMO-1 sweep in FP32, CCM_PROF_SMO1_FP64 the same in FP64,
+ *   CCM_PROF_SMO1_FP32   level-0 smoothing sweep in FP32 (SMO-1 with the SMO-2 blocks of the
+ *                        block-Jacobi smoother), except the first post-smoothing sweep;
+ *                        CCM_PROF_SMO1_FP64 the same in FP64,
  *   CCM_PROF_VCYCLE      one whole V-cycle,
  *   CCM_PROF_SMO2_FP32   level-0 SMO-2 block step in FP32,
  *   CCM_PROF_PROLONG_SMO1_FP32  level-0 first post-smoothing sweep with the prolongation fused,

@@ -15,6 +15,7 @@ CCM_CIRCLE, CCM_ELLIPSE, CCM_STAR = 1, 2, 3
 CCM_NONE, CCM_DIRICHLET, CCM_NEUMANN = 0, 1, 2
 CCM_FP64, CCM_MIXED = 0, 1
 CCM_PROF_OFF, CCM_PROF_RESID_FP64, CCM_PROF_SMO1_FP32, CCM_PROF_SMO1_FP64, CCM_PROF_VCYCLE = 0, 1, 2, 3, 4
+CCM_PROF_SMO2_FP32, CCM_PROF_PROLONG_SMO1_FP32, CCM_PROF_RESTRICT_FP32 = 5, 6, 7
 
 
 class CcmError(RuntimeError):

@@ -172,6 +172,10 @@ __device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, u
       : "memory");
 }
 
+// orders this thread's earlier shared-memory accesses before later async-proxy (TMA, bulk)
+// writes into the same buffer
+__device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+
 // bounded wait for the tile (by the SM clock); false, and *err set, if the copy never landed
 __device__ __forceinline__ bool tile_wait(uint64_t* bar, int* err) {
   const long long t0 = clock64();

@@ -1,0 +1,207 @@
+// One block-Jacobi smoothing sweep of a level (SMO-1 on the regular cells and the SMO-2
+// overlapping-block corrections of the irregular cells, both from the old iterate, Sec. 4.1)
+// as one persistent launch.
+//
+// Work items: the SMO-2 blocks first, then the 64 x 32 cell tiles with a regular cell.  CTA c
+// takes items c, c + G, c + 2G, ... (G = grid size, a multiple of the SM count where the
+// level is large).  Every item's operands arrive in one of two shared-memory stages, so the
+// copy of item k + 1 is in flight while item k computes:
+//   tile item:  the 68 x 36 halo tile of u, the 68 x 32 box of r over the tile's rows and the
+//               80 x 36 class bytes (one 2-D TMA box each; x origin 64a, 16-byte aligned),
+//               and with PRO the 36 x 18 box of the coarse iterate under the tile;
+//   block item: the block's rows of inv(L22[ext, ext]) by one bulk copy (cp.async.bulk); the
+//               residuals of its extended rows are gathered from global memory meanwhile.
+// With PRO the sweep is the first post-smoothing sweep of Alg. 2 and reads u + P uc, the
+// coarse correction added to regular cells only (Sec. 4.2).
+// Waits are bounded by the SM clock; a wait that runs out sets the error word, waits (again
+// bounded) for every copy still in flight, and the CTA leaves, all threads together.
+#pragma once
+
+#include "kernels.cuh"
+
+namespace ccm {
+namespace dev {
+
+template <typename T>
+struct SmoothArgs {
+  SweepArgs<T> a;      // level arrays, stencil, iterates, blocks (chunks == 1)
+  int nbi;             // block items (= a.nblk)
+  int nitems;          // nbi + a.ntiles
+  uint32_t stage;      // bytes per stage (multiple of 128)
+};
+
+// offsets inside a stage of a tile item
+template <typename T>
+struct TileStage {
+  static constexpr uint32_t al(uint32_t b) { return (b + 127u) & ~127u; }
+  static constexpr uint32_t u_bytes = HY * HX * sizeof(T);
+  static constexpr uint32_t r_bytes = JY * HX * sizeof(T);
+  static constexpr uint32_t c_bytes = HY * CLX;
+  static constexpr uint32_t uc_bytes = UCY * UCX * sizeof(T);
+  static constexpr uint32_t r_off = al(u_bytes);
+  static constexpr uint32_t c_off = r_off + al(r_bytes);
+  static constexpr uint32_t uc_off = c_off + al(c_bytes);
+  static constexpr uint32_t bytes(bool pro) { return pro ? uc_off + uc_bytes : c_off + c_bytes; }
+};
+
+__device__ __forceinline__ bool wait_parity(uint64_t* bar, uint32_t parity) {
+  const long long t0 = clock64();
+  while (clock64() - t0 < TMA_WAIT_CYCLES)
+    if (mbar_try_wait(bar, parity)) return true;
+  return false;
+}
+
+template <typename T, bool PRO>
+__device__ __forceinline__ void smooth_issue(const SmoothArgs<T>& A, const CUtensorMap* tin, const CUtensorMap* tr,
+                                             const CUtensorMap* tcls, const CUtensorMap* tuc, int item,
+                                             unsigned char* st, uint64_t* bar) {
+  const SweepArgs<T>& a = A.a;
+  if (item < A.nbi) {
+    const int b = item;
+    const int nc = a.blk[4 * b + 1] - a.blk[4 * b], ne = a.blk[4 * b + 3] - a.blk[4 * b + 2];
+    const uint32_t abytes = (uint32_t)(((long)ne * nc * sizeof(T) + 15) & ~15L);
+    mbar_expect_tx(bar, abytes);
+    bulk_load(st, a.inv + a.blk_off[b], abytes, bar);
+  } else {
+    using S = TileStage<T>;
+    const int t = item - A.nbi;
+    const int cx0 = a.tiles[2 * t] * JX, cy0 = a.tiles[2 * t + 1] * JY;
+    mbar_expect_tx(bar, S::u_bytes + S::r_bytes + S::c_bytes + (PRO ? S::uc_bytes : 0));
+    tma_load_2d(st, tin, bar, cx0, cy0);
+    tma_load_2d(st + S::r_off, tr, bar, cx0, cy0 + 2);
+    tma_load_2d(st + S::c_off, tcls, bar, cx0, cy0);
+    if (PRO) tma_load_2d(st + S::uc_off, tuc, bar, cx0 / 2, cy0 / 2 + 1);
+  }
+}
+
+template <typename T, bool CROSS, bool PRO>
+__global__ void __launch_bounds__(256) k_smooth(const __grid_constant__ CUtensorMap tin,
+                                                const __grid_constant__ CUtensorMap tr,
+                                                const __grid_constant__ CUtensorMap tcls,
+                                                const __grid_constant__ CUtensorMap tuc, SmoothArgs<T> A) {
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  __shared__ __align__(8) uint64_t bar[2];
+  __shared__ T part[8][32];
+  const SweepArgs<T>& a = A.a;
+  T* sres = reinterpret_cast<T*>(smem_raw + 2 * A.stage);
+  const int G = gridDim.x;
+  const int K = (A.nitems - (int)blockIdx.x + G - 1) / G;   // items of this CTA (>= 1)
+  if (threadIdx.x == 0) {
+    mbar_init(&bar[0], 1);
+    mbar_init(&bar[1], 1);
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    smooth_issue<T, PRO>(A, &tin, &tr, &tcls, &tuc, blockIdx.x, smem_raw, &bar[0]);
+    if (K > 1) smooth_issue<T, PRO>(A, &tin, &tr, &tcls, &tuc, blockIdx.x + G, smem_raw + A.stage, &bar[1]);
+  }
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int k = 0; k < K; ++k) {
+    const int item = blockIdx.x + k * G;
+    const int sb = k & 1;
+    const uint32_t parity = (k >> 1) & 1;
+    int cs = 0, nc = 0, ne = 0;
+    if (item < A.nbi) {
+      // residuals of the block's extended rows from the old iterate (u + P uc with PRO)
+      const int b = item;
+      cs = a.blk[4 * b];
+      nc = a.blk[4 * b + 1] - cs;
+      const int es = a.blk[4 * b + 2];
+      ne = a.blk[4 * b + 3] - es;
+      for (int e = threadIdx.x; e < ne; e += blockDim.x) {
+        const int row = es + e;
+        T acc = 0;
+#pragma unroll 15
+        for (int m = 0; m < a.W; ++m) {
+          const int f = a.colf[(long)m * a.n2 + row];
+          const long q = f & 0x7fffffff;
+          T v = a.u_old[q];
+          if (PRO && f < 0) v += a.uc[parent_of(q, a.pitch, a.pitchc)];
+          acc += a.val[(long)m * a.n2 + row] * v;
+        }
+        sres[e] = a.r[a.cell[row]] - acc;
+      }
+    }
+    const bool ok = __syncthreads_and(wait_parity(&bar[sb], parity));
+    if (!ok) {
+      // this copy and the other stage's (if one was issued) must land before the CTA leaves
+      wait_parity(&bar[sb], parity);
+      if (k + 1 < K) wait_parity(&bar[sb ^ 1], ((k + 1) >> 1) & 1);
+      if (threadIdx.x == 0) atomicExch(a.err, 1);
+      return;
+    }
+    if (item < A.nbi) {
+      const T* As = reinterpret_cast<const T*>((smem_raw + sb * A.stage));      // [ne][nc]
+      for (int cb = 0; cb < nc; cb += 32) {
+        const int c = cb + lane;
+        T acc = 0;
+        if (c < nc)
+          for (int e = warp; e < ne; e += 8) acc += As[e * nc + c] * sres[e];
+        part[warp][lane] = acc;
+        __syncthreads();
+        if (warp == 0 && c < nc) {
+          T tot = 0;
+#pragma unroll
+          for (int w = 0; w < 8; ++w) tot += part[w][lane];
+          const long q = a.cell[cs + c];
+          a.u_new[q] = a.u_old[q] + tot;
+        }
+        __syncthreads();
+      }
+    } else {
+      using S = TileStage<T>;
+      const int t = item - A.nbi;
+      const int cx0 = a.tiles[2 * t] * JX, cy0 = a.tiles[2 * t + 1] * JY;
+      T* tile = reinterpret_cast<T*>((smem_raw + sb * A.stage));
+      const T* rt = reinterpret_cast<const T*>((smem_raw + sb * A.stage) + S::r_off);
+      const uint8_t* ct = (smem_raw + sb * A.stage) + S::c_off;
+      if (PRO) {
+        // staged cell (y, x) has its parent at (y / 2, x / 2 + 1) of the coarse box
+        const T* uct = reinterpret_cast<const T*>((smem_raw + sb * A.stage) + S::uc_off);
+        for (int idx = threadIdx.x; idx < HY * HX; idx += blockDim.x) {
+          const int y = idx / HX, xx = idx - y * HX;
+          if (ct[y * CLX + xx] == 1) tile[idx] += uct[(y >> 1) * UCX + (xx >> 1) + 1];
+        }
+        __syncthreads();
+      }
+      const int x = threadIdx.x & 63, y0 = (threadIdx.x >> 6) * 8;
+      const int i = cx0 + x;
+      if (i < a.nx) {
+        T w[5][5];
+#pragma unroll
+        for (int q = 0; q < 4; ++q)
+#pragma unroll
+          for (int b = 0; b < 5; ++b) w[q][b] = tile[(y0 + q) * HX + x + b];
+#pragma unroll
+        for (int kk = 0; kk < 8; ++kk) {
+#pragma unroll
+          for (int b = 0; b < 5; ++b) w[4][b] = tile[(y0 + kk + 4) * HX + x + b];
+          if (ct[(y0 + kk + 2) * CLX + x + 2] == 1) {
+            T acc = 0;
+#pragma unroll
+            for (int q = 0; q < 5; ++q)
+#pragma unroll
+              for (int b = 0; b < 5; ++b) {
+                if (!CROSS && q != 2 && b != 2) continue;
+                acc += a.S.w[q * 5 + b] * w[q][b];
+              }
+            const long p = (long)(cy0 + y0 + kk + 2) * a.pitch + (i + 2);
+            a.u_new[p] = w[2][2] + a.S.omega_d * (rt[(y0 + kk) * HX + x + 2] - acc);
+          }
+#pragma unroll
+          for (int q = 0; q < 4; ++q)
+#pragma unroll
+            for (int b = 0; b < 5; ++b) w[q][b] = w[q + 1][b];
+        }
+      }
+    }
+    __syncthreads();      // stage sb is free
+    if (threadIdx.x == 0 && k + 2 < K) {
+      fence_proxy_async();
+      smooth_issue<T, PRO>(A, &tin, &tr, &tcls, &tuc, item + 2 * G, (smem_raw + sb * A.stage), &bar[sb]);
+    }
+  }
+}
+
+}  // namespace dev
+}  // namespace ccm

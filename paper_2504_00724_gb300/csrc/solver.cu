@@ -18,6 +18,7 @@
 #include "hierarchy.h"
 #include "kernels.cuh"
 #include "coarse.cuh"
+#include "smooth.cuh"
 
 using namespace ccm;
 
@@ -39,6 +40,11 @@ struct DevLevel {
   CUtensorMap tmcls;            // 80 x 36 box over the class bytes
   CUtensorMap tmuc64[2], tmuc32[2];  // 36 x 18 boxes over level m + 1's u buffers
   bool tma_pro = false;         // the maps above exist: prolongation fuses into the sweep
+  CUtensorMap tmr64, tmr32;     // 68 x 32 boxes over r
+  bool smooth_ok[2] = {false, false};  // persistent sweep (k_smooth) usable, [0] FP64, [1] FP32
+  uint32_t smooth_stage[2] = {0, 0};
+  size_t smooth_smem[2] = {0, 0};
+  int smooth_grid[2] = {0, 0};
   int32_t* rr_off = nullptr;    // per restriction tile: its irregular rows [rr_off[t], rr_off[t + 1])
   int32_t* rr = nullptr;        // (row, y * 64 + x in the tile) pairs
   uint8_t* cls = nullptr;
@@ -152,6 +158,7 @@ struct ccm_handle {
   int coarse_first = 1 << 30;  // first level whose part of the V-cycle runs as one cluster launch
   int coarse_ctas = 0;         // CTAs of that cluster (16, else 8)
   size_t coarse_smem = 0;      // its dynamic shared memory (SMO-2 extended-row residuals)
+  bool persistent = true;      // block-Jacobi sweeps of TMA levels as one persistent launch
   ccm_handle* adj = nullptr;   // the transposed operators' hierarchy (built by ccm_solve_T)
   // one CUDA graph per outer iteration and precision (captured on first use, on a private
   // stream: the legacy default stream cannot be captured)
@@ -266,8 +273,70 @@ template <> const CUtensorMap& TmUc<float>(const DevLevel& F, const DevLevel& C)
 // block-Jacobi form: SMO-1 and SMO-2 both from the old iterate, one launch (plus the SMO-2
 // blocks on a parallel branch where their inverses are staged).  C != null: the first
 // post-smoothing sweep, which reads u + P uc with uc the iterate of level C.
+template <typename T> const CUtensorMap& TmR(const DevLevel& L);
+template <> const CUtensorMap& TmR<double>(const DevLevel& L) { return L.tmr64; }
+template <> const CUtensorMap& TmR<float>(const DevLevel& L) { return L.tmr32; }
+
+// the persistent sweep (k_smooth): SMO-2 block items and TMA tile items in one launch
+template <typename T>
+void sweep_persistent(ccm_handle* H, DevLevel& L, cudaStream_t s, DevLevel* C) {
+  const int k = sizeof(T) == 8 ? 0 : 1;
+  dev::SmoothArgs<T> A{};
+  dev::SweepArgs<T>& a = A.a;
+  a.tiles = L.tiles64;
+  a.ntiles = L.ntiles64;
+  a.nblk = L.nblk;
+  a.chunks = 1;
+  a.cls = L.cls;
+  a.nx = L.nx;
+  a.ny = L.ny;
+  a.pitch = L.pitch;
+  a.n2 = L.n2;
+  a.W = L.W;
+  a.r = R<T>(L);
+  a.u_old = U<T>(L);
+  a.u_new = Uother<T>(L);
+  a.S = stencil<T>(H);
+  a.blk = L.blk;
+  a.blk_off = L.blk_off;
+  a.inv = Inv<T>(L);
+  a.cell = L.irr_cell;
+  a.col = L.ell_col;
+  a.val = Ell<T>(L);
+  a.err = H->derr;
+  a.colf = L.ell_colf;
+  a.uc = C ? U<T>(*C) : nullptr;
+  a.pitchc = C ? C->pitch : 0;
+  A.nbi = L.nblk;
+  A.nitems = L.nblk + L.ntiles64;
+  A.stage = L.smooth_stage[k];
+  const bool l0 = &L == &H->L[0];
+  ProfScope ps(H, !l0 ? 0 : C ? (sizeof(T) == 4 ? CCM_PROF_PROLONG_SMO1_FP32 : 0)
+                              : (sizeof(T) == 4 ? CCM_PROF_SMO1_FP32 : CCM_PROF_SMO1_FP64), s);
+  const CUtensorMap& tm = TmU<T>(L);
+  const CUtensorMap& tr = TmR<T>(L);
+  const int grid = L.smooth_grid[k];
+  const size_t smem = L.smooth_smem[k];
+  if (C) {
+    const CUtensorMap& tu = TmUc<T>(L, *C);
+    if (H->cross) KL(dev::k_smooth<T, true, true><<<grid, 256, smem, s>>>(tm, tr, L.tmcls, tu, A));
+    else KL(dev::k_smooth<T, false, true><<<grid, 256, smem, s>>>(tm, tr, L.tmcls, tu, A));
+  } else {
+    if (H->cross) KL(dev::k_smooth<T, true, false><<<grid, 256, smem, s>>>(tm, tr, L.tmcls, tm, A));
+    else KL(dev::k_smooth<T, false, false><<<grid, 256, smem, s>>>(tm, tr, L.tmcls, tm, A));
+  }
+}
+
 template <typename T>
 void sweep_one_launch(ccm_handle* H, DevLevel& L, cudaStream_t s, DevLevel* C = nullptr) {
+  if (L.smooth_ok[sizeof(T) == 8 ? 0 : 1] && H->persistent) {
+    if (C && !L.tma_pro) {
+      prolong_from<T>(H, L, *C, s);
+      C = nullptr;
+    }
+    sweep_persistent<T>(H, L, s, C);
+    return;
+  }
   const bool staged = L.tma && (L.nblk == 0 || L.stage_blocks);
   if (C && !(staged && L.tma_pro)) {
     prolong_from<T>(H, L, *C, s);
@@ -301,7 +370,8 @@ void sweep_one_launch(ccm_handle* H, DevLevel& L, cudaStream_t s, DevLevel* C = 
   a.uc = C ? U<T>(*C) : nullptr;
   a.pitchc = C ? C->pitch : 0;
   const bool l0 = &L == &H->L[0];
-  ProfScope ps(H, !l0 ? 0 : (sizeof(T) == 4 ? CCM_PROF_SMO1_FP32 : CCM_PROF_SMO1_FP64), s);
+  ProfScope ps(H, !l0 ? 0 : C ? (sizeof(T) == 4 ? CCM_PROF_PROLONG_SMO1_FP32 : 0)
+                              : (sizeof(T) == 4 ? CCM_PROF_SMO1_FP32 : CCM_PROF_SMO1_FP64), s);
   if (L.stage_blocks && a.nblk) {
     // SMO-2 blocks on the side stream, regular cells here; join before the next phase
     dev::SweepArgs<T> b = a;
@@ -639,8 +709,11 @@ int upload_hierarchy(ccm_handle* h) {
       d.order = A.upload(hl.order);
       d.blk = A.upload(hl.blk);
       d.blk_off = A.upload(hl.blk_off);
-      d.inv64 = A.upload(hl.blk_inv);
-      std::vector<float> f(hl.blk_inv.begin(), hl.blk_inv.end());
+      // 4 trailing zeros: bulk copies round a block's bytes up to a multiple of 16
+      std::vector<double> g(hl.blk_inv.begin(), hl.blk_inv.end());
+      g.resize(g.size() + 4, 0.0);
+      d.inv64 = A.upload(g);
+      std::vector<float> f(g.begin(), g.end());
       d.inv32 = A.upload(f);
       for (int b = 0; b < d.nblk; ++b) {
         d.max_ext = std::max(d.max_ext, hl.blk[4 * b + 3] - hl.blk[4 * b + 2]);
@@ -681,6 +754,9 @@ int upload_hierarchy(ccm_handle* h) {
     for (int b = 0; b < 2 && d.tma; ++b)
       d.tma = make_tmap(&d.tm64[b], d.u64[b], d.pitch, d.rows, true) &&
               make_tmap(&d.tm32[b], d.u32[b], d.pitch, d.rows, false);
+    d.tma = d.tma && make_tmap(&d.tmcls, d.cls, d.pitch, d.rows, CU_TENSOR_MAP_DATA_TYPE_UINT8, 1, dev::CLX, dev::HY) &&
+            make_tmap(&d.tmr64, d.r64, d.pitch, d.rows, CU_TENSOR_MAP_DATA_TYPE_FLOAT64, 8, dev::HX, dev::JY) &&
+            make_tmap(&d.tmr32, d.r32, d.pitch, d.rows, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, dev::HX, dev::JY);
   }
   // SMO-2 blocks that fit in shared memory run as a bulk-staged kernel beside the sweep
   if (cudaStreamCreateWithFlags(&h->side, cudaStreamNonBlocking) != cudaSuccess ||
@@ -691,10 +767,45 @@ int upload_hierarchy(ccm_handle* h) {
   }
   cudaFuncSetAttribute(dev::k_blocks<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
   cudaFuncSetAttribute(dev::k_blocks<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+  int nsm = 0;
+  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, h->device);
   for (int m = 0; m < nl; ++m) {
     DevLevel& d = h->L[m];
     const size_t need = (size_t)d.max_ext * d.max_core * sizeof(double) + d.max_ext * sizeof(double) + 16;
     d.stage_blocks = d.nblk > 0 && need <= 200 * 1024;
+    // the persistent sweep: two stages that hold a tile item or a block item, one CTA-wide
+    // item at a time (blocks with more core rows than one CTA covers keep the older path)
+    const int rows_per_cta = d.nblk >= 16 ? std::max(1, d.max_core) : 64;
+    const bool one_chunk = d.nblk == 0 || d.max_core <= rows_per_cta;
+    const int nitems = d.nblk + d.ntiles64;
+    for (int k = 0; k < 2 && d.tma && one_chunk && nitems > 0; ++k) {
+      const size_t es = k == 0 ? sizeof(double) : sizeof(float);
+      const size_t tile = k == 0 ? dev::TileStage<double>::bytes(true) : dev::TileStage<float>::bytes(true);
+      const size_t blk = ((size_t)d.max_ext * d.max_core * es + 15) & ~(size_t)15;
+      const size_t stage = (std::max(tile, blk) + 127) & ~(size_t)127;
+      const size_t smem = 2 * stage + (((size_t)std::max(1, d.max_ext) * es + 15) & ~(size_t)15);
+      if (smem > 200 * 1024) continue;
+      int occ = 0;
+      if (k == 0) {
+        auto fn = h->cross ? dev::k_smooth<double, true, true> : dev::k_smooth<double, false, true>;
+        cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, 256, smem);
+        for (auto g : {h->cross ? dev::k_smooth<double, true, false> : dev::k_smooth<double, false, false>})
+          cudaFuncSetAttribute(g, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+      } else {
+        auto fn = h->cross ? dev::k_smooth<float, true, true> : dev::k_smooth<float, false, true>;
+        cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, 256, smem);
+        for (auto g : {h->cross ? dev::k_smooth<float, true, false> : dev::k_smooth<float, false, false>})
+          cudaFuncSetAttribute(g, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+      }
+      if (occ < 1 || nsm < 1) continue;
+      d.smooth_ok[k] = true;
+      d.smooth_stage[k] = (uint32_t)stage;
+      d.smooth_smem[k] = smem;
+      d.smooth_grid[k] = std::min(nitems, nsm * occ);
+    }
+    cudaGetLastError();
     // restriction tiles: fine 64 x 32 tiles with a non-empty fine cell or a non-empty coarse cell
     if (m + 1 < nl && d.tma) {
       const HostLevel& hf = h->H.levels[m];
@@ -736,7 +847,7 @@ int upload_hierarchy(ccm_handle* h) {
       if (!rr.empty()) d.rr = A.upload(rr);
       // the first post-smoothing sweep reads u + P uc through two more boxes
       DevLevel& c = h->L[m + 1];
-      d.tma_pro = make_tmap(&d.tmcls, d.cls, d.pitch, d.rows, CU_TENSOR_MAP_DATA_TYPE_UINT8, 1, dev::CLX, dev::HY);
+      d.tma_pro = true;
       for (int b = 0; b < 2 && d.tma_pro; ++b)
         d.tma_pro = make_tmap(&d.tmuc64[b], c.u64[b], c.pitch, c.rows, CU_TENSOR_MAP_DATA_TYPE_FLOAT64, 8, dev::UCX, dev::UCY) &&
                     make_tmap(&d.tmuc32[b], c.u32[b], c.pitch, c.rows, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, dev::UCX, dev::UCY);

@@ -42,3 +42,22 @@ def test_null_arguments_rejected_without_gpu():
     assert lib.ccm_apply(None, None, None, None, 1, None) == -1
     assert lib.ccm_solve(None, None, None, None, 1, None, None) == -1
     assert lib.ccm_query(None, None) == -1
+
+
+def test_binding_constants_match_header_and_bench():
+    """Every CCM_* enum value of the header that the binding re-exports has the header's value,
+    and every binding constant bench.py uses exists."""
+    import re
+    from pathlib import Path
+    root = Path(__file__).resolve().parents[1]
+    hdr = (root / "include" / "ccm.h").read_text()
+    values = {m.group(1): int(m.group(2)) for m in re.finditer(r"\b(CCM_[A-Z0-9_]+)\s*=\s*(-?\d+)", hdr)}
+    from paper_2504_00724_gb300 import binding as B
+    exported = [n for n in dir(B) if n.startswith("CCM_")]
+    assert exported
+    for n in exported:
+        if n in values:
+            assert getattr(B, n) == values[n], n
+    used = set(re.findall(r"binding\.(CCM_[A-Z0-9_]+)", (root / "bench.py").read_text()))
+    for n in used:
+        assert hasattr(B, n), n

@@ -115,3 +115,44 @@ def test_vcycle_equals_composed_level_calls(n, coarse_n):
         assert np.abs(got - want).max() <= 1e-12 * np.abs(want).max()
     finally:
         s.close()
+
+
+def _block_jacobi_sweep(lv, cells, u, r, omega, block=64, overlap=32):
+    """One sweep of the device's default smoother written out from its definition: SMO-1 on
+    the regular cells and, for each block of `block` consecutive fitted rows (in the product's
+    row order, which is Alg. 3's boundary order) widened by `overlap` rows on each side, the
+    exact solve of L22 on the widened rows, kept on the core rows; both from the old iterate."""
+    L = lv.dz.L.tocsr()
+    res = r - L @ u
+    out = u.copy()
+    out[lv.reg] += omega / lv.diag * res[lv.reg]
+    n2 = len(cells)
+    L22 = L[cells][:, cells].toarray()
+    for cs in range(0, n2, block):
+        ce = min(n2, cs + block)
+        es, ee = max(0, cs - overlap), min(n2, ce + overlap)
+        x = np.linalg.solve(L22[es:ee, es:ee], res[cells[es:ee]])
+        out[cells[cs:ce]] = u[cells[cs:ce]] + x[cs - es:ce - es]
+    return out
+
+
+@pytest.mark.parametrize("precision,tol", [(0, 1e-10), (1, 2e-4)])
+def test_large_default_smoother_matches_block_jacobi(big, precision, tol):
+    """The persistent sweep kernel (SMO-2 block items and TMA tile items in one launch) on the
+    first level of star 288 equals the block-Jacobi sweep computed on the oracle's operator."""
+    prob, mms, H = big
+    hs = P.HostSetup(prob)
+    s = P.Solver(prob, omega=OMEGA)
+    try:
+        lv = H.levels[0]
+        cells = hs.rows(0)[0].astype(np.int64)
+        rng = np.random.default_rng(31)
+        u0 = np.where(lv.ne, rng.standard_normal(lv.nx * lv.ny), 0.0)
+        r = np.where(lv.ne, rng.standard_normal(lv.nx * lv.ny), 0.0) / lv.h ** 2
+        want = _block_jacobi_sweep(lv, cells, u0, r, OMEGA)
+        got = host(s.level_smooth(0, cuda(u0.reshape(lv.ny, lv.nx)), cuda(r.reshape(lv.ny, lv.nx)),
+                                  precision)).ravel()
+        assert np.abs(got - want).max() <= tol * np.abs(want).max()
+    finally:
+        s.close()
+        hs.close()
