@@ -35,6 +35,7 @@ struct CoarseLevel {
   const int32_t* irr_cell;
   const int32_t* rowmap;   // padded cell -> fitted row, -1 elsewhere
   const int32_t* colf;     // ELL columns (slot-major), sign bit set on regular columns
+  const int32_t* par;      // per ELL slot: padded parent of a regular column, else -1
   const T* val;
   const int32_t* blk;      // per block: core rows [cs, ce), extended rows [es, ee)
   const int64_t* blk_off;
@@ -116,7 +117,10 @@ __device__ void cl_sweep(const CoarseLevel<T>& L, int cur, const Stencil<T>& S, 
         const int f = L.colf[(long)k * L.n2 + row];
         const long q = f & 0x7fffffff;
         T v = __ldcg(uin + q);
-        if (uc && f < 0) v += __ldcg(uc + parent_of(q, L.pitch, pitchc));
+        if (uc) {
+          const int pq = L.par[(long)k * L.n2 + row];
+          if (pq >= 0) v += __ldcg(uc + pq);
+        }
         acc += L.val[(long)k * L.n2 + row] * v;
       }
       sres[e] = __ldcg(L.r + L.irr_cell[row]) - acc;

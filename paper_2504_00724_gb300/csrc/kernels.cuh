@@ -16,6 +16,15 @@ namespace dev {
 
 constexpr int TX = 32, TY = 8;
 
+// Programmatic dependent launch: a kernel launched with programmatic stream serialization
+// may start while the preceding kernel of its stream drains.  Every kernel of the solve path
+// first waits for that kernel (and sees its writes) before it touches global memory, then
+// lets the next kernel's CTAs be scheduled.  Without the launch attribute both are no-ops.
+__device__ __forceinline__ void pdl_enter() {
+  asm volatile("griddepcontrol.wait;" ::: "memory");
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+
 template <typename T>
 struct Stencil {
   T w[25];        // [dj + 2][di + 2]
@@ -72,6 +81,7 @@ template <typename T, bool CROSS, bool RESID>
 __global__ void k_regular(const int32_t* __restrict__ tiles, const uint8_t* __restrict__ cls, int nx, int ny,
                           int pitch, const T* __restrict__ u, const T* __restrict__ r, T* __restrict__ out,
                           Stencil<T> S) {
+  pdl_enter();
   int i, j;
   long p;
   if (!tile_cell(tiles, nx, ny, pitch, i, j, p)) return;
@@ -83,10 +93,11 @@ __global__ void k_regular(const int32_t* __restrict__ tiles, const uint8_t* __re
 // fitted rows: res = r[cell] - sum beta u[col]  (RESID) or res = sum beta u[col] + nb g[seg]
 // written to out[row] (GRID = false) or out[cell] (GRID = true)
 template <typename T, typename C, bool RESID, bool GRID>
-__global__ void k_rows(int n2, int W, const int32_t* __restrict__ cell, const int32_t* __restrict__ col,
+__global__ void __launch_bounds__(128, 8) k_rows(int n2, int W, const int32_t* __restrict__ cell, const int32_t* __restrict__ col,
                        const C* __restrict__ val, const T* __restrict__ u, const T* __restrict__ r,
                        T* __restrict__ out, const double* __restrict__ nb, const int32_t* __restrict__ seg,
                        const double* __restrict__ g) {
+  pdl_enter();
   int row = blockIdx.x * blockDim.x + threadIdx.x;
   if (row >= n2) return;
   T acc = 0;
@@ -154,12 +165,19 @@ __device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
   asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
 }
 
+// plain arrival (no transaction bytes): completes the phase of a barrier initialised with count 1
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
+// test for the completion of the phase with the given parity; the thread may stay suspended
+// in the instruction for up to 100 us while the phase is pending (no issue slots spent)
 __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t phase) {
   uint32_t ok;
   asm volatile(
-      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n selp.u32 %0, 1, 0, p;\n}\n"
       : "=r"(ok)
-      : "r"(smem_u32(bar)), "r"(phase)
+      : "r"(smem_u32(bar)), "r"(phase), "r"(100000u)
       : "memory");
   return ok != 0;
 }
@@ -245,12 +263,6 @@ __global__ void __launch_bounds__(256) k_jacobi_tma(const __grid_constant__ CUte
   }
 }
 
-// padded index of the parent (level m + 1) of a padded cell q of level m inside the domain
-__device__ __forceinline__ long parent_of(long q, int pitch, int pitchc) {
-  const int j = (int)(q / pitch), i = (int)(q - (long)j * pitch);
-  return (long)((j - 2) / 2 + 2) * pitchc + ((i - 2) / 2 + 2);
-}
-
 // ---- one smoothing sweep in one launch (block-Jacobi form of SMO-1 + SMO-2).
 // Both parts read only the old iterate and write only the new one: CTAs [0, ntiles) update
 // the regular cells (SMO-1), CTAs [ntiles, ntiles + nblk * chunks) the irregular cells by the
@@ -273,9 +285,8 @@ struct SweepArgs {
   const int32_t* col;
   const T* val;
   int* err;
-  const int32_t* colf;   // ELL columns with the sign bit on regular columns (prolongation)
+  const int32_t* par;    // per ELL slot: padded parent (level m + 1) of a regular column, else -1
   const T* uc;           // coarse iterate: the sweep reads u + P uc (regular cells), or null
-  int pitchc;
 };
 
 template <typename T>
@@ -316,6 +327,7 @@ __device__ __forceinline__ void block_part(const SweepArgs<T>& a, int bidx, T* s
 
 template <typename T, bool CROSS, bool TMA>
 __global__ void __launch_bounds__(256) k_sweep(const __grid_constant__ CUtensorMap tin, SweepArgs<T> a) {
+  pdl_enter();
   extern __shared__ unsigned char smem_raw[];
   if ((int)blockIdx.x >= a.ntiles) {
     block_part<T>(a, blockIdx.x - a.ntiles, reinterpret_cast<T*>(smem_raw));
@@ -396,6 +408,7 @@ template <typename T, bool CROSS, bool PRO>
 __global__ void __launch_bounds__(256) k_sweep_tma(const __grid_constant__ CUtensorMap tin,
                                                    const __grid_constant__ CUtensorMap tcls,
                                                    const __grid_constant__ CUtensorMap tuc, SweepArgs<T> a) {
+  pdl_enter();
   __shared__ __align__(128) T tile[HY * HX];
   __shared__ __align__(128) uint8_t ctile[PRO ? HY * CLX : 16];
   __shared__ __align__(128) T uct[PRO ? UCY * UCX : 2];
@@ -500,10 +513,9 @@ __global__ void __launch_bounds__(256) k_blocks(SweepArgs<T> a) {
     if (a.uc) {
 #pragma unroll 15
       for (int k = 0; k < a.W; ++k) {
-        const int f = a.colf[(long)k * a.n2 + row];
-        const long q = f & 0x7fffffff;
-        T v = a.u_old[q];
-        if (f < 0) v += a.uc[parent_of(q, a.pitch, a.pitchc)];
+        const int pq = a.par[(long)k * a.n2 + row];
+        T v = a.u_old[a.col[(long)k * a.n2 + row]];
+        if (pq >= 0) v += a.uc[pq];
         acc += a.val[(long)k * a.n2 + row] * v;
       }
     } else {
@@ -552,6 +564,7 @@ __global__ void __launch_bounds__(256, 4) k_restrict_tma(const __grid_constant__
                                                          int nyc, int pitchc, const uint8_t* __restrict__ clsc,
                                                          T* __restrict__ rc, T* __restrict__ uc, Stencil<T> S,
                                                          int* __restrict__ err) {
+  pdl_enter();
   __shared__ __align__(128) T tile[HY * HX];
   __shared__ T res[JY][JX];      // residual of every fine cell of the tile (0 on empty cells)
   __shared__ __align__(8) uint64_t bar;
@@ -638,6 +651,7 @@ __global__ void k_restrict_rows(int nxc, int nyc, int pitchc, int pitchf, const 
                                 const int32_t* __restrict__ rowmap, int n2, int W, const int32_t* __restrict__ col,
                                 const T* __restrict__ val, const T* __restrict__ u, const T* __restrict__ r,
                                 T* __restrict__ rc, T* __restrict__ uc, Stencil<T> S) {
+  pdl_enter();
   int I = blockIdx.x * blockDim.x + threadIdx.x;
   int J = blockIdx.y * blockDim.y + threadIdx.y;
   if (I >= nxc || J >= nyc) return;
@@ -797,6 +811,7 @@ __global__ void k_restrict(int nxc, int nyc, int pitchc, int pitchf, const uint8
 template <typename T>
 __global__ void k_prolong(const int32_t* __restrict__ tiles, const uint8_t* __restrict__ cls, int nx, int ny,
                           int pitch, int pitchc, const T* __restrict__ uc, T* __restrict__ u) {
+  pdl_enter();
   int i, j;
   long p;
   if (!tile_cell(tiles, nx, ny, pitch, i, j, p)) return;
@@ -808,6 +823,7 @@ __global__ void k_prolong(const int32_t* __restrict__ tiles, const uint8_t* __re
 template <typename T>
 __global__ void k_bottom(int n, const int32_t* __restrict__ cell, const T* __restrict__ inv,
                          const T* __restrict__ r, T* __restrict__ u) {
+  pdl_enter();
   extern __shared__ unsigned char smem_raw[];
   T* s = reinterpret_cast<T*>(smem_raw);
   for (int c = threadIdx.x; c < n; c += blockDim.x) s[c] = r[cell[c]];
@@ -864,6 +880,7 @@ __global__ void k_sub_boundary(int n2, const int32_t* __restrict__ cell, const d
 template <typename T>
 __global__ void k_absmax(long n, const uint8_t* __restrict__ cls, const T* __restrict__ x,
                          unsigned long long* __restrict__ out) {
+  pdl_enter();
   double m = 0.0;
   for (long p = blockIdx.x * (long)blockDim.x + threadIdx.x; p < n; p += (long)gridDim.x * blockDim.x)
     if (cls[p] != 0) {
@@ -878,10 +895,12 @@ __global__ void k_absmax(long n, const uint8_t* __restrict__ cls, const T* __res
 // u64 += e on non-empty cells;  r32 = (float) r64
 template <typename TE>
 __global__ void k_axpy(long n, const uint8_t* __restrict__ cls, const TE* __restrict__ e, double* __restrict__ u) {
+  pdl_enter();
   for (long p = blockIdx.x * (long)blockDim.x + threadIdx.x; p < n; p += (long)gridDim.x * blockDim.x)
     if (cls[p] != 0) u[p] += (double)e[p];
 }
 __global__ void k_to_float(long n, const double* __restrict__ a, float* __restrict__ b) {
+  pdl_enter();
   for (long p = blockIdx.x * (long)blockDim.x + threadIdx.x; p < n; p += (long)gridDim.x * blockDim.x)
     b[p] = (float)a[p];
 }

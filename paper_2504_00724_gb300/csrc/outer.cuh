@@ -1,0 +1,145 @@
+// The FP64 part of one outer iteration of the mixed-precision solve (eq.
+// PoissonResidualForm): u_hat += e on the non-empty cells, then t = r_hat - (h^2 L) u_hat in
+// FP64, the FP32 image of t as the next right-hand side of the FP32 V-cycles, and max |t|.
+//
+// The regular stencil (Sec. 3.2) is the sum of eq. stdLap along x and along y and the
+// iterated eq. stdGrad for the mixed term, so its 25 weights factor as
+//   w[dj][di] = a lap[di] / 12 [dj = 0] + c lap[dj] / 12 [di = 0] + (b grad[dj] / 12)(grad[di] / 12)
+// with lap = (-1, 16, -30, 16, -1), grad = (1, -8, 0, 8, -1).  The kernel forms the x
+// derivative grad_x u of every row of the staged tile once (4 FMA per cell) and combines
+// four of them per cell, so a regular cell costs 4 + 4 + 9 FMA instead of 25 (FP64 issue is
+// the bound of this kernel on GB300).  The evaluation order differs from the 25-tap sum, so
+// the result agrees with it to rounding, not bit for bit.
+#pragma once
+
+#include "kernels.cuh"
+
+namespace ccm {
+namespace dev {
+
+struct SepStencil {
+  double lx[5];    // a lap / 12 along x
+  double ly[5];    // c lap / 12 along y
+  double gx[5];    // grad / 12 along x
+  double gy[5];    // b grad / 12 along y
+};
+
+__device__ __forceinline__ double nan_to_inf(double v) {
+  return v <= 1.7976931348623157e308 ? v : __longlong_as_double(0x7ff0000000000000ULL);
+}
+
+// dynamic shared memory of k_resid64 (offsets are multiples of 128 bytes)
+struct Resid64Smem {
+  static constexpr uint32_t u_bytes = HY * HX * 8, r_bytes = JY * HX * 8, c_bytes = HY * CLX;
+  static constexpr uint32_t rt_off = u_bytes;                          // 19584
+  static constexpr uint32_t ct_off = rt_off + r_bytes;                 // 36992
+  static constexpr uint32_t dx_off = ct_off + ((c_bytes + 127) / 128) * 128;
+  static constexpr uint32_t tx = u_bytes + r_bytes + c_bytes;
+  static constexpr uint32_t bytes(bool cross) { return cross ? dx_off + HY * JX * 8 : dx_off; }
+};
+
+// regular cells of one 64 x 32 tile: u_hat (68 x 36 halo), r_hat (68 x 32) and the class
+// bytes (80 x 36) by TMA; writes r32 and folds max |t| into *norm
+template <bool CROSS>
+__global__ void __launch_bounds__(256, 3) k_resid64(const __grid_constant__ CUtensorMap tu,
+                                                 const __grid_constant__ CUtensorMap tr,
+                                                 const __grid_constant__ CUtensorMap tcls,
+                                                 const int32_t* __restrict__ tiles, int nx, int pitch,
+                                                 float* __restrict__ r32, unsigned long long* __restrict__ norm,
+                                                 SepStencil S, int* __restrict__ err) {
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  double* ut = reinterpret_cast<double*>(smem_raw);                               // [HY][HX]
+  double* rt = reinterpret_cast<double*>(smem_raw + Resid64Smem::rt_off);         // [JY][HX]
+  uint8_t* ct = smem_raw + Resid64Smem::ct_off;                                   // [HY][CLX]
+  double* dx = reinterpret_cast<double*>(smem_raw + Resid64Smem::dx_off);         // [HY][JX]
+  __shared__ __align__(8) uint64_t bar;
+  pdl_enter();
+  const int cx0 = tiles[2 * blockIdx.x] * JX, cy0 = tiles[2 * blockIdx.x + 1] * JY;
+  if (threadIdx.x == 0) mbar_init(&bar, 1);
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    mbar_expect_tx(&bar, Resid64Smem::tx);
+    tma_load_2d(ut, &tu, &bar, cx0, cy0);
+    tma_load_2d(rt, &tr, &bar, cx0, cy0 + 2);
+    tma_load_2d(ct, &tcls, &bar, cx0, cy0);
+  }
+  const bool ok = __syncthreads_and(tile_wait(&bar, err));
+  if (!ok) return;
+  if (CROSS) {
+    for (int idx = threadIdx.x; idx < HY * JX; idx += blockDim.x) {
+      const int y = idx >> 6, x = idx & 63;
+      const double* row = ut + y * HX + x + 2;
+      dx[idx] = S.gx[0] * row[-2] + S.gx[1] * row[-1] + S.gx[3] * row[1] + S.gx[4] * row[2];
+    }
+    __syncthreads();
+  }
+  // the 8 cells of a thread are independent: their arithmetic runs unconditionally (three
+  // separate FMA chains each) so that it interleaves; only the store depends on the class
+  const int x = threadIdx.x & 63, y0 = (threadIdx.x >> 6) * 8;
+  const int i = cx0 + x;
+  double m = 0.0;
+#pragma unroll
+  for (int k = 0; k < 8; ++k) {
+    const int y = y0 + k;                 // own row; staged row y + 2
+    const double* c = ut + (y + 2) * HX + x + 2;
+    double ax = (S.lx[2] + S.ly[2]) * c[0];
+    ax = fma(S.lx[0], c[-2], ax);
+    ax = fma(S.lx[1], c[-1], ax);
+    ax = fma(S.lx[3], c[1], ax);
+    ax = fma(S.lx[4], c[2], ax);
+    double ay = S.ly[0] * c[-2 * HX];
+    ay = fma(S.ly[1], c[-HX], ay);
+    ay = fma(S.ly[3], c[HX], ay);
+    ay = fma(S.ly[4], c[2 * HX], ay);
+    double az = 0.0;
+    if (CROSS) {
+      const double* d = dx + (y + 2) * JX + x;
+      az = S.gy[0] * d[-2 * JX];
+      az = fma(S.gy[1], d[-JX], az);
+      az = fma(S.gy[3], d[JX], az);
+      az = fma(S.gy[4], d[2 * JX], az);
+    }
+    const double t = rt[y * HX + x + 2] - (ax + ay + az);
+    if (i < nx && ct[(y + 2) * CLX + x + 2] == 1) {
+      r32[(long)(cy0 + y + 2) * pitch + (i + 2)] = (float)t;
+      m = fmax(m, nan_to_inf(fabs(t)));
+    }
+  }
+  for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+  if ((threadIdx.x & 31) == 0 && m > 0.0) atomicMax(norm, (unsigned long long)__double_as_longlong(m));
+}
+
+// fitted rows of the irregular cells: t = r_hat - sum_k beta_k u_hat(col_k); r32 and max |t|
+__global__ void __launch_bounds__(128, 8) k_rows_r32(int n2, int W, const int32_t* __restrict__ cell, const int32_t* __restrict__ col,
+                           const double* __restrict__ val, const double* __restrict__ u,
+                           const double* __restrict__ r, float* __restrict__ r32,
+                           unsigned long long* __restrict__ norm) {
+  pdl_enter();
+  const int row = blockIdx.x * blockDim.x + threadIdx.x;
+  double m = 0.0;
+  if (row < n2) {
+    double acc = 0.0;
+#pragma unroll 15
+    for (int k = 0; k < W; ++k) acc += val[(long)k * n2 + row] * u[col[(long)k * n2 + row]];
+    const int q = cell[row];
+    const double t = r[q] - acc;
+    r32[q] = (float)t;
+    m = nan_to_inf(fabs(t));
+  }
+  for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+  if ((threadIdx.x & 31) == 0 && m > 0.0) atomicMax(norm, (unsigned long long)__double_as_longlong(m));
+}
+
+// u_hat += e on the non-empty cells of the 32 x 8 tiles that hold one
+__global__ void k_axpy_tiles(const int32_t* __restrict__ tiles, const uint8_t* __restrict__ cls, int nx, int ny,
+                             int pitch, const float* __restrict__ e, double* __restrict__ u) {
+  pdl_enter();
+  const int i = tiles[2 * blockIdx.x] * TX + threadIdx.x;
+  const int j = tiles[2 * blockIdx.x + 1] * TY + threadIdx.y;
+  if (i >= nx || j >= ny) return;
+  const long p = (long)(j + 2) * pitch + (i + 2);
+  if (cls[p] != 0) u[p] += (double)e[p];
+}
+
+}  // namespace dev
+}  // namespace ccm

@@ -75,13 +75,14 @@ __device__ __forceinline__ void smooth_issue(const SmoothArgs<T>& A, const CUten
 }
 
 template <typename T, bool CROSS, bool PRO>
-__global__ void __launch_bounds__(256) k_smooth(const __grid_constant__ CUtensorMap tin,
+__global__ void __launch_bounds__(256, 3) k_smooth(const __grid_constant__ CUtensorMap tin,
                                                 const __grid_constant__ CUtensorMap tr,
                                                 const __grid_constant__ CUtensorMap tcls,
                                                 const __grid_constant__ CUtensorMap tuc, SmoothArgs<T> A) {
   extern __shared__ __align__(128) unsigned char smem_raw[];
   __shared__ __align__(8) uint64_t bar[2];
   __shared__ T part[8][32];
+  pdl_enter();
   const SweepArgs<T>& a = A.a;
   T* sres = reinterpret_cast<T*>(smem_raw + 2 * A.stage);
   const int G = gridDim.x;
@@ -113,10 +114,11 @@ __global__ void __launch_bounds__(256) k_smooth(const __grid_constant__ CUtensor
         T acc = 0;
 #pragma unroll 15
         for (int m = 0; m < a.W; ++m) {
-          const int f = a.colf[(long)m * a.n2 + row];
-          const long q = f & 0x7fffffff;
-          T v = a.u_old[q];
-          if (PRO && f < 0) v += a.uc[parent_of(q, a.pitch, a.pitchc)];
+          T v = a.u_old[a.col[(long)m * a.n2 + row]];
+          if (PRO) {
+            const int pq = a.par[(long)m * a.n2 + row];
+            if (pq >= 0) v += a.uc[pq];
+          }
           acc += a.val[(long)m * a.n2 + row] * v;
         }
         sres[e] = a.r[a.cell[row]] - acc;
@@ -131,7 +133,7 @@ __global__ void __launch_bounds__(256) k_smooth(const __grid_constant__ CUtensor
       return;
     }
     if (item < A.nbi) {
-      const T* As = reinterpret_cast<const T*>((smem_raw + sb * A.stage));      // [ne][nc]
+      const T* As = reinterpret_cast<const T*>(smem_raw + sb * A.stage);      // [ne][nc]
       for (int cb = 0; cb < nc; cb += 32) {
         const int c = cb + lane;
         T acc = 0;
@@ -156,12 +158,20 @@ __global__ void __launch_bounds__(256) k_smooth(const __grid_constant__ CUtensor
       const T* rt = reinterpret_cast<const T*>((smem_raw + sb * A.stage) + S::r_off);
       const uint8_t* ct = (smem_raw + sb * A.stage) + S::c_off;
       if (PRO) {
-        // staged cell (y, x) has its parent at (y / 2, x / 2 + 1) of the coarse box
+        // staged cell (y, x) has its parent at (y / 2, x / 2 + 1) of the coarse box; four
+        // cells (one 32-bit word of class bytes, two parents) per step
         const T* uct = reinterpret_cast<const T*>((smem_raw + sb * A.stage) + S::uc_off);
-        for (int idx = threadIdx.x; idx < HY * HX; idx += blockDim.x) {
-          const int y = idx / HX, xx = idx - y * HX;
-          if (ct[y * CLX + xx] == 1) tile[idx] += uct[(y >> 1) * UCX + (xx >> 1) + 1];
-        }
+        for (int y = warp; y < HY; y += 8)
+          if (lane < HX / 4) {
+            const int x0 = 4 * lane;
+            const uint32_t c4 = *reinterpret_cast<const uint32_t*>(ct + y * CLX + x0);
+            const T p0 = uct[(y >> 1) * UCX + 2 * lane + 1], p1 = uct[(y >> 1) * UCX + 2 * lane + 2];
+            T* tr4 = tile + y * HX + x0;
+            if ((c4 & 0xffu) == 1u) tr4[0] += p0;
+            if (((c4 >> 8) & 0xffu) == 1u) tr4[1] += p0;
+            if (((c4 >> 16) & 0xffu) == 1u) tr4[2] += p1;
+            if ((c4 >> 24) == 1u) tr4[3] += p1;
+          }
         __syncthreads();
       }
       const int x = threadIdx.x & 63, y0 = (threadIdx.x >> 6) * 8;

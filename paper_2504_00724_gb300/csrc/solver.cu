@@ -19,6 +19,7 @@
 #include "kernels.cuh"
 #include "coarse.cuh"
 #include "smooth.cuh"
+#include "outer.cuh"
 
 using namespace ccm;
 
@@ -51,6 +52,7 @@ struct DevLevel {
   double* vol64 = nullptr;
   float* vol32 = nullptr;
   int32_t *irr_cell = nullptr, *ell_col = nullptr, *ell_colf = nullptr, *seg = nullptr, *rowmap = nullptr;
+  int32_t* ell_par = nullptr;   // per ELL slot: padded parent of a regular column (level m + 1), else -1
   double *ell64 = nullptr, *nb = nullptr;
   float* ell32 = nullptr;
   int32_t *order = nullptr, *blk = nullptr;
@@ -144,6 +146,9 @@ struct ccm_handle {
   int* herr = nullptr;         // pinned copy
   double* rhat = nullptr;      // level-0 padded FP64 right-hand side (h^2-scaled)
   double* uhat = nullptr;      // level-0 padded FP64 solution
+  bool fused_outer = false;    // mixed form: TMA-tiled FP64 residual writing r32 and the norm
+  CUtensorMap tm_uhat, tm_rhat;  // 68 x 36 box over uhat, 68 x 32 box over rhat
+  dev::SepStencil sep{};       // the regular stencil in factored form
   unsigned long long* dnorm = nullptr;
   unsigned long long* hnorm = nullptr;   // pinned
   ccm_info info{};
@@ -228,6 +233,23 @@ struct ProfScope {
     if (e_ != cudaSuccess) return CCM_ECUDA;            \
   } while (0)
 
+// kernel launch with programmatic stream serialization (the kernel may start while the
+// previous kernel of the stream drains; it waits for it inside, see pdl_enter)
+template <typename... KArgs, typename... Args>
+cudaError_t launch_k(void (*k)(KArgs...), dim3 g, dim3 b, size_t smem, cudaStream_t s, Args... args) {
+  cudaLaunchConfig_t cfg{};
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.gridDim = g;
+  cfg.blockDim = b;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, k, args...);
+}
+
 // ---------------------------------------------------------------- level operations
 
 template <typename T>
@@ -244,11 +266,11 @@ void launch_regular(ccm_handle* H, DevLevel& L, const T* u, const T* r, T* out, 
   dim3 blk(dev::TX, dev::TY);
   const auto& S = stencil<T>(H);
   if (H->cross) {
-    if (resid) KL(dev::k_regular<T, true, true><<<L.ntiles, blk, 0, s>>>(L.tiles, L.cls, L.nx, L.ny, L.pitch, u, r, out, S));
-    else KL(dev::k_regular<T, true, false><<<L.ntiles, blk, 0, s>>>(L.tiles, L.cls, L.nx, L.ny, L.pitch, u, r, out, S));
+    if (resid) KL(launch_k(dev::k_regular<T, true, true>, L.ntiles, blk, 0, s, L.tiles, L.cls, L.nx, L.ny, L.pitch, u, r, out, S));
+    else KL(launch_k(dev::k_regular<T, true, false>, L.ntiles, blk, 0, s, L.tiles, L.cls, L.nx, L.ny, L.pitch, u, r, out, S));
   } else {
-    if (resid) KL(dev::k_regular<T, false, true><<<L.ntiles, blk, 0, s>>>(L.tiles, L.cls, L.nx, L.ny, L.pitch, u, r, out, S));
-    else KL(dev::k_regular<T, false, false><<<L.ntiles, blk, 0, s>>>(L.tiles, L.cls, L.nx, L.ny, L.pitch, u, r, out, S));
+    if (resid) KL(launch_k(dev::k_regular<T, false, true>, L.ntiles, blk, 0, s, L.tiles, L.cls, L.nx, L.ny, L.pitch, u, r, out, S));
+    else KL(launch_k(dev::k_regular<T, false, false>, L.ntiles, blk, 0, s, L.tiles, L.cls, L.nx, L.ny, L.pitch, u, r, out, S));
   }
 }
 
@@ -257,7 +279,7 @@ template <typename T>
 void residual(ccm_handle* H, DevLevel& L, const T* u, const T* r, T* out, cudaStream_t s) {
   launch_regular<T>(H, L, u, r, out, true, s);
   if (L.n2)
-    KL(dev::k_rows<T, T, true, true><<<ceil_div(L.n2, 128), 128, 0, s>>>(L.n2, L.W, L.irr_cell, L.ell_col, Ell<T>(L), u, r, out,
+    KL(launch_k(dev::k_rows<T, T, true, true>, ceil_div(L.n2, 128), 128, 0, s, L.n2, L.W, L.irr_cell, L.ell_col, Ell<T>(L), u, r, out,
                                                                       nullptr, nullptr, nullptr));
 }
 
@@ -304,9 +326,8 @@ void sweep_persistent(ccm_handle* H, DevLevel& L, cudaStream_t s, DevLevel* C) {
   a.col = L.ell_col;
   a.val = Ell<T>(L);
   a.err = H->derr;
-  a.colf = L.ell_colf;
+  a.par = L.ell_par;
   a.uc = C ? U<T>(*C) : nullptr;
-  a.pitchc = C ? C->pitch : 0;
   A.nbi = L.nblk;
   A.nitems = L.nblk + L.ntiles64;
   A.stage = L.smooth_stage[k];
@@ -319,11 +340,11 @@ void sweep_persistent(ccm_handle* H, DevLevel& L, cudaStream_t s, DevLevel* C) {
   const size_t smem = L.smooth_smem[k];
   if (C) {
     const CUtensorMap& tu = TmUc<T>(L, *C);
-    if (H->cross) KL(dev::k_smooth<T, true, true><<<grid, 256, smem, s>>>(tm, tr, L.tmcls, tu, A));
-    else KL(dev::k_smooth<T, false, true><<<grid, 256, smem, s>>>(tm, tr, L.tmcls, tu, A));
+    if (H->cross) KL(launch_k(dev::k_smooth<T, true, true>, grid, 256, smem, s, tm, tr, L.tmcls, tu, A));
+    else KL(launch_k(dev::k_smooth<T, false, true>, grid, 256, smem, s, tm, tr, L.tmcls, tu, A));
   } else {
-    if (H->cross) KL(dev::k_smooth<T, true, false><<<grid, 256, smem, s>>>(tm, tr, L.tmcls, tm, A));
-    else KL(dev::k_smooth<T, false, false><<<grid, 256, smem, s>>>(tm, tr, L.tmcls, tm, A));
+    if (H->cross) KL(launch_k(dev::k_smooth<T, true, false>, grid, 256, smem, s, tm, tr, L.tmcls, tm, A));
+    else KL(launch_k(dev::k_smooth<T, false, false>, grid, 256, smem, s, tm, tr, L.tmcls, tm, A));
   }
 }
 
@@ -366,9 +387,8 @@ void sweep_one_launch(ccm_handle* H, DevLevel& L, cudaStream_t s, DevLevel* C = 
   a.col = L.ell_col;
   a.val = Ell<T>(L);
   a.err = H->derr;
-  a.colf = L.ell_colf;
+  a.par = L.ell_par;
   a.uc = C ? U<T>(*C) : nullptr;
-  a.pitchc = C ? C->pitch : 0;
   const bool l0 = &L == &H->L[0];
   ProfScope ps(H, !l0 ? 0 : C ? (sizeof(T) == 4 ? CCM_PROF_PROLONG_SMO1_FP32 : 0)
                               : (sizeof(T) == 4 ? CCM_PROF_SMO1_FP32 : CCM_PROF_SMO1_FP64), s);
@@ -388,22 +408,22 @@ void sweep_one_launch(ccm_handle* H, DevLevel& L, cudaStream_t s, DevLevel* C = 
   if (staged && a.ntiles) {
     if (C) {
       const CUtensorMap& tu = TmUc<T>(L, *C);
-      if (H->cross) KL(dev::k_sweep_tma<T, true, true><<<a.ntiles, 256, 0, s>>>(tm, L.tmcls, tu, a));
-      else KL(dev::k_sweep_tma<T, false, true><<<a.ntiles, 256, 0, s>>>(tm, L.tmcls, tu, a));
+      if (H->cross) KL(launch_k(dev::k_sweep_tma<T, true, true>, a.ntiles, 256, 0, s, tm, L.tmcls, tu, a));
+      else KL(launch_k(dev::k_sweep_tma<T, false, true>, a.ntiles, 256, 0, s, tm, L.tmcls, tu, a));
     } else {
-      if (H->cross) KL(dev::k_sweep_tma<T, true, false><<<a.ntiles, 256, 0, s>>>(tm, tm, tm, a));
-      else KL(dev::k_sweep_tma<T, false, false><<<a.ntiles, 256, 0, s>>>(tm, tm, tm, a));
+      if (H->cross) KL(launch_k(dev::k_sweep_tma<T, true, false>, a.ntiles, 256, 0, s, tm, tm, tm, a));
+      else KL(launch_k(dev::k_sweep_tma<T, false, false>, a.ntiles, 256, 0, s, tm, tm, tm, a));
     }
   } else {
     const int grid = a.ntiles + a.nblk * a.chunks;
     const size_t smem = (size_t)std::max(1, L.max_ext) * sizeof(T);
     if (grid > 0) {
       if (tma) {
-        if (H->cross) KL(dev::k_sweep<T, true, true><<<grid, 256, smem, s>>>(tm, a));
-        else KL(dev::k_sweep<T, false, true><<<grid, 256, smem, s>>>(tm, a));
+        if (H->cross) KL(launch_k(dev::k_sweep<T, true, true>, grid, 256, smem, s, tm, a));
+        else KL(launch_k(dev::k_sweep<T, false, true>, grid, 256, smem, s, tm, a));
       } else {
-        if (H->cross) KL(dev::k_sweep<T, true, false><<<grid, 256, smem, s>>>(tm, a));
-        else KL(dev::k_sweep<T, false, false><<<grid, 256, smem, s>>>(tm, a));
+        if (H->cross) KL(launch_k(dev::k_sweep<T, true, false>, grid, 256, smem, s, tm, a));
+        else KL(launch_k(dev::k_sweep<T, false, false>, grid, 256, smem, s, tm, a));
       }
     }
   }
@@ -448,7 +468,7 @@ void smooth_step(ccm_handle* H, DevLevel& L, cudaStream_t s, const T* uc = nullp
   flip<T>(L);
   T* u = U<T>(L);
   for (int pass = 1; pass < H->par.ras_passes && L.n2; ++pass) {
-    KL(dev::k_rows<T, T, true, false><<<ceil_div(L.n2, 128), 128, 0, s>>>(L.n2, L.W, L.irr_cell, L.ell_col, Ell<T>(L), u, r,
+    KL(launch_k(dev::k_rows<T, T, true, false>, ceil_div(L.n2, 128), 128, 0, s, L.n2, L.W, L.irr_cell, L.ell_col, Ell<T>(L), u, r,
                                                                        Res<T>(L), nullptr, nullptr, nullptr));
     dim3 grd(L.nblk, ceil_div(L.max_core, 32));
     KL(dev::k_block_solve<T><<<grd, 128, L.max_ext * sizeof(T), s>>>(L.order, L.blk, L.blk_off, Inv<T>(L), Res<T>(L),
@@ -463,12 +483,12 @@ void restrict_to(ccm_handle* H, DevLevel& F, DevLevel& C, cudaStream_t s) {
   if (H->par.smoother == 1 && F.tma && F.ntiles64r) {
     const auto& S = stencil<T>(H);
     if (H->cross)
-      KL(dev::k_restrict_tma<T, true><<<F.ntiles64r, 256, 0, s>>>(TmU<T>(F), F.tiles64r, F.nx, F.ny, F.pitch, F.cls, Vol<T>(F),
+      KL(launch_k(dev::k_restrict_tma<T, true>, F.ntiles64r, 256, 0, s, TmU<T>(F), F.tiles64r, F.nx, F.ny, F.pitch, F.cls, Vol<T>(F),
                                                          F.rr_off, F.rr, F.n2, F.W, F.irr_cell, F.ell_col, Ell<T>(F),
                                                          U<T>(F), R<T>(F), C.nx, C.ny, C.pitch, C.cls, R<T>(C), U<T>(C), S,
                                                          H->derr));
     else
-      KL(dev::k_restrict_tma<T, false><<<F.ntiles64r, 256, 0, s>>>(TmU<T>(F), F.tiles64r, F.nx, F.ny, F.pitch, F.cls, Vol<T>(F),
+      KL(launch_k(dev::k_restrict_tma<T, false>, F.ntiles64r, 256, 0, s, TmU<T>(F), F.tiles64r, F.nx, F.ny, F.pitch, F.cls, Vol<T>(F),
                                                          F.rr_off, F.rr, F.n2, F.W, F.irr_cell, F.ell_col, Ell<T>(F),
                                                          U<T>(F), R<T>(F), C.nx, C.ny, C.pitch, C.cls, R<T>(C), U<T>(C), S,
                                                          H->derr));
@@ -478,15 +498,15 @@ void restrict_to(ccm_handle* H, DevLevel& F, DevLevel& C, cudaStream_t s) {
     dim3 blk(32, 8), grd(ceil_div(C.nx, 32), ceil_div(C.ny, 8));
     const auto& S = stencil<T>(H);
     if (H->cross)
-      KL(dev::k_restrict_rows<T, true><<<grd, blk, 0, s>>>(C.nx, C.ny, C.pitch, F.pitch, C.cls, F.cls, Vol<T>(F), F.rowmap,
+      KL(launch_k(dev::k_restrict_rows<T, true>, grd, blk, 0, s, C.nx, C.ny, C.pitch, F.pitch, C.cls, F.cls, Vol<T>(F), F.rowmap,
                                                          F.n2, F.W, F.ell_col, Ell<T>(F), U<T>(F), R<T>(F), R<T>(C), U<T>(C), S));
     else
-      KL(dev::k_restrict_rows<T, false><<<grd, blk, 0, s>>>(C.nx, C.ny, C.pitch, F.pitch, C.cls, F.cls, Vol<T>(F), F.rowmap,
+      KL(launch_k(dev::k_restrict_rows<T, false>, grd, blk, 0, s, C.nx, C.ny, C.pitch, F.pitch, C.cls, F.cls, Vol<T>(F), F.rowmap,
                                                           F.n2, F.W, F.ell_col, Ell<T>(F), U<T>(F), R<T>(F), R<T>(C), U<T>(C), S));
     return;
   }
   if (F.n2)
-    KL(dev::k_rows<T, T, true, true><<<ceil_div(F.n2, 128), 128, 0, s>>>(F.n2, F.W, F.irr_cell, F.ell_col, Ell<T>(F), U<T>(F),
+    KL(launch_k(dev::k_rows<T, T, true, true>, ceil_div(F.n2, 128), 128, 0, s, F.n2, F.W, F.irr_cell, F.ell_col, Ell<T>(F), U<T>(F),
                                                                       R<T>(F), Tmp<T>(F), nullptr, nullptr, nullptr));
   dim3 blk(32, 8), grd(ceil_div(C.nx, 32), ceil_div(C.ny, 8));
   const auto& S = stencil<T>(H);
@@ -502,14 +522,14 @@ template <typename T>
 void prolong_from(ccm_handle* H, DevLevel& F, DevLevel& C, cudaStream_t s) {
   if (F.ntiles == 0) return;
   dim3 blk(dev::TX, dev::TY);
-  KL(dev::k_prolong<T><<<F.ntiles, blk, 0, s>>>(F.tiles, F.cls, F.nx, F.ny, F.pitch, C.pitch, U<T>(C), U<T>(F)));
+  KL(launch_k(dev::k_prolong<T>, F.ntiles, blk, 0, s, F.tiles, F.cls, F.nx, F.ny, F.pitch, C.pitch, U<T>(C), U<T>(F)));
 }
 
 template <typename T>
 void bottom(ccm_handle* H, DevLevel& B, cudaStream_t s) {
   int nw = 8;
   size_t sm = std::max<size_t>(B.nbc, nw * 32) * sizeof(T);
-  KL(dev::k_bottom<T><<<ceil_div(B.nbc, 32), nw * 32, sm, s>>>(B.nbc, B.bot_cell, Bot<T>(B), R<T>(B), U<T>(B)));
+  KL(launch_k(dev::k_bottom<T>, ceil_div(B.nbc, 32), nw * 32, sm, s, B.nbc, B.bot_cell, Bot<T>(B), R<T>(B), U<T>(B)));
 }
 
 // the levels from m down to the bottom run as one launch of one thread-block cluster
@@ -528,7 +548,7 @@ void coarse_cluster(ccm_handle* H, int m, cudaStream_t s) {
     C.cls = L.cls; C.vol = Vol<T>(L); C.r = R<T>(L);
     C.u[0] = sizeof(T) == 8 ? (T*)L.u64[0] : (T*)L.u32[0];
     C.u[1] = sizeof(T) == 8 ? (T*)L.u64[1] : (T*)L.u32[1];
-    C.irr_cell = L.irr_cell; C.rowmap = L.rowmap; C.colf = L.ell_colf; C.val = Ell<T>(L);
+    C.irr_cell = L.irr_cell; C.rowmap = L.rowmap; C.colf = L.ell_colf; C.par = L.ell_par; C.val = Ell<T>(L);
     C.blk = L.blk; C.blk_off = L.blk_off; C.inv = Inv<T>(L); C.bot_cell = L.bot_cell; C.bot = Bot<T>(L);
     P.cur[k] = sizeof(T) == 8 ? L.cur64 : L.cur32;
   }
@@ -604,12 +624,30 @@ void vcycle(ccm_handle* H, int m, cudaStream_t s) {
 
 int read_norm(ccm_handle* H, const uint8_t* cls, long n, const double* x, cudaStream_t s, double& out) {
   CCM_CUDA(cudaMemsetAsync(H->dnorm, 0, sizeof(unsigned long long), s));
-  KL(dev::k_absmax<double><<<std::min(ceil_div(n, 256), 1216), 256, 0, s>>>(n, cls, x, H->dnorm));
+  KL(launch_k(dev::k_absmax<double>, std::min(ceil_div(n, 256), 1216), 256, 0, s, n, cls, x, H->dnorm));
   CCM_CUDA(cudaMemcpyAsync(H->hnorm, H->dnorm, sizeof(unsigned long long), cudaMemcpyDeviceToHost, s));
   CCM_CUDA(cudaStreamSynchronize(s));
   unsigned long long bits = *H->hnorm;
   std::memcpy(&out, &bits, sizeof(double));
   return CCM_OK;
+}
+
+// mixed form: t = rhat - L uhat on level 0 into the FP32 right-hand side, max |t| into dnorm
+void outer_residual32(ccm_handle* H, cudaStream_t s) {
+  DevLevel& L = H->L[0];
+  cudaMemsetAsync(H->dnorm, 0, sizeof(unsigned long long), s);
+  {
+    ProfScope ps(H, CCM_PROF_RESID_FP64, s);
+    if (H->cross)
+      KL(launch_k(dev::k_resid64<true>, L.ntiles64, 256, dev::Resid64Smem::bytes(true), s, H->tm_uhat, H->tm_rhat, L.tmcls, L.tiles64, L.nx, L.pitch,
+                  L.r32, H->dnorm, H->sep, H->derr));
+    else
+      KL(launch_k(dev::k_resid64<false>, L.ntiles64, 256, dev::Resid64Smem::bytes(false), s, H->tm_uhat, H->tm_rhat, L.tmcls, L.tiles64, L.nx, L.pitch,
+                  L.r32, H->dnorm, H->sep, H->derr));
+  }
+  if (L.n2)
+    KL(launch_k(dev::k_rows_r32, ceil_div(L.n2, 128), 128, 0, s, L.n2, L.W, L.irr_cell, L.ell_col, L.ell64,
+                (const double*)H->uhat, (const double*)H->rhat, L.r32, H->dnorm));
 }
 
 int check_level(ccm_handle* h, int level) {
@@ -750,7 +788,7 @@ int upload_hierarchy(ccm_handle* h) {
     d.t32 = A.alloc<float>(d.npad);
     // TMA-staged smoothing on the large levels (base addresses come from cudaMalloc, so
     // they are 256-byte aligned; the pitch is a multiple of 32 elements)
-    d.tma = A.err == cudaSuccess && d.ntiles64 > 0 && d.nx >= 256;
+    d.tma = A.err == cudaSuccess && d.ntiles64 > 0 && d.nx >= 64;
     for (int b = 0; b < 2 && d.tma; ++b)
       d.tma = make_tmap(&d.tm64[b], d.u64[b], d.pitch, d.rows, true) &&
               make_tmap(&d.tm32[b], d.u32[b], d.pitch, d.rows, false);
@@ -806,6 +844,19 @@ int upload_hierarchy(ccm_handle* h) {
       d.smooth_grid[k] = std::min(nitems, nsm * occ);
     }
     cudaGetLastError();
+    // parents of the fitted rows' regular columns (the prolongation read by SMO-2 residuals)
+    if (m + 1 < nl && h->H.levels[m].n2) {
+      const HostLevel& hf = h->H.levels[m];
+      const int pc = h->L[m + 1].pitch;
+      std::vector<int32_t> par(hf.ell_colf.size(), -1);
+      for (size_t k = 0; k < par.size(); ++k) {
+        const int f = hf.ell_colf[k];
+        if (f >= 0) continue;
+        const int q = f & 0x7fffffff, j = q / hf.pitch, i = q - j * hf.pitch;
+        par[k] = ((j - 2) / 2 + 2) * pc + ((i - 2) / 2 + 2);
+      }
+      d.ell_par = A.upload(par);
+    }
     // restriction tiles: fine 64 x 32 tiles with a non-empty fine cell or a non-empty coarse cell
     if (m + 1 < nl && d.tma) {
       const HostLevel& hf = h->H.levels[m];
@@ -876,6 +927,22 @@ int upload_hierarchy(ccm_handle* h) {
   }
   h->rhat = A.alloc<double>(h->L[0].npad);
   h->uhat = A.alloc<double>(h->L[0].npad);
+  {
+    static const double lap[5] = {-1.0, 16.0, -30.0, 16.0, -1.0};
+    static const double grad[5] = {1.0, -8.0, 0.0, 8.0, -1.0};
+    for (int k = 0; k < 5; ++k) {
+      h->sep.lx[k] = h->a * lap[k] / 12.0;
+      h->sep.ly[k] = h->c * lap[k] / 12.0;
+      h->sep.gx[k] = grad[k] / 12.0;
+      h->sep.gy[k] = h->b * grad[k] / 12.0;
+    }
+    const DevLevel& d0 = h->L[0];
+    cudaFuncSetAttribute(dev::k_resid64<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, dev::Resid64Smem::bytes(true));
+    cudaFuncSetAttribute(dev::k_resid64<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, dev::Resid64Smem::bytes(false));
+    h->fused_outer = A.err == cudaSuccess && d0.tma && d0.ntiles64 > 0 &&
+                     make_tmap(&h->tm_uhat, h->uhat, d0.pitch, d0.rows, true) &&
+                     make_tmap(&h->tm_rhat, h->rhat, d0.pitch, d0.rows, CU_TENSOR_MAP_DATA_TYPE_FLOAT64, 8, dev::HX, dev::JY);
+  }
   h->dnorm = A.alloc<unsigned long long>(1);
   h->derr = A.alloc<int>(1);
   if (A.err != cudaSuccess) {
@@ -1065,7 +1132,7 @@ int ccm_apply(ccm_handle* h, const double* u, const double* g, double* out, int 
     KL(dev::k_pack<double, double><<<pg, 128, 0, s>>>(L.nx, L.ny, L.pitch, L.cls, u + k * nu, L.t64, 1.0));
     launch_regular<double>(h, L, L.t64, nullptr, L.u64[1 - L.cur64], false, s);
     if (L.n2)
-      KL(dev::k_rows<double, double, false, true><<<ceil_div(L.n2, 128), 128, 0, s>>>(
+      KL(launch_k(dev::k_rows<double, double, false, true>, ceil_div(L.n2, 128), 128, 0, s, 
           L.n2, L.W, L.irr_cell, L.ell_col, L.ell64, L.t64, nullptr, L.u64[1 - L.cur64], L.nb, L.seg,
           g ? g + (long)k * h->info.n_segments : nullptr));
     KL(dev::k_unpack<double><<<pg, 128, 0, s>>>(L.nx, L.ny, L.pitch, L.cls, L.u64[1 - L.cur64], out + k * nu,
@@ -1120,12 +1187,12 @@ int ccm_apply_noalloc(const ccm_handle* hc, const double* u, const double* g, do
   if (L.ntiles) {
     dim3 blk(dev::TX, dev::TY);
     if (h->cross)
-      KL(dev::k_regular<double, true, false><<<L.ntiles, blk, 0, s>>>(L.tiles, L.cls, L.nx, L.ny, L.pitch, up, nullptr, op, h->S64));
+      KL(launch_k(dev::k_regular<double, true, false>, L.ntiles, blk, 0, s, L.tiles, L.cls, L.nx, L.ny, L.pitch, up, nullptr, op, h->S64));
     else
-      KL(dev::k_regular<double, false, false><<<L.ntiles, blk, 0, s>>>(L.tiles, L.cls, L.nx, L.ny, L.pitch, up, nullptr, op, h->S64));
+      KL(launch_k(dev::k_regular<double, false, false>, L.ntiles, blk, 0, s, L.tiles, L.cls, L.nx, L.ny, L.pitch, up, nullptr, op, h->S64));
   }
   if (L.n2)
-    KL(dev::k_rows<double, double, false, true><<<ceil_div(L.n2, 128), 128, 0, s>>>(
+    KL(launch_k(dev::k_rows<double, double, false, true>, ceil_div(L.n2, 128), 128, 0, s, 
         L.n2, L.W, L.irr_cell, L.ell_col, L.ell64, up, nullptr, op, L.nb, L.seg, g));
   KL(dev::k_unpack<double><<<pg, 128, 0, s>>>(L.nx, L.ny, L.pitch, L.cls, op, out, 1.0 / (L.h * L.h)));
   CCM_CUDA(cudaGetLastError());
@@ -1179,14 +1246,28 @@ static void iteration_body(ccm_handle* h, bool fp64, cudaStream_t s) {
       L.cur64 = 1 - L.cur64;
     }
     ucur = start;
-  } else {
-    KL(dev::k_to_float<<<std::min(ceil_div(np, 256), 4096), 256, 0, s>>>(np, L.t64, L.r32));
+  } else if (h->fused_outer) {
+    // r32 holds the FP32 image of the residual (previous iteration or the initial one)
     cudaMemsetAsync(L.u32[L.cur32], 0, np * sizeof(float), s);
     for (int c = 0; c < std::max(1, h->par.inner_cycles); ++c) {
       ProfScope ps(h, CCM_PROF_VCYCLE, s);
       vcycle<float>(h, 0, s);
     }
-    KL(dev::k_axpy<float><<<std::min(ceil_div(np, 256), 4096), 256, 0, s>>>(np, L.cls, L.u32[L.cur32], h->uhat));
+    dim3 blk(dev::TX, dev::TY);
+    KL(launch_k(dev::k_axpy_tiles, L.ntiles, blk, 0, s, L.tiles, L.cls, L.nx, L.ny, L.pitch,
+                (const float*)L.u32[L.cur32], h->uhat));
+    outer_residual32(h, s);
+    cudaMemcpyAsync(h->hnorm, h->dnorm, sizeof(unsigned long long), cudaMemcpyDeviceToHost, s);
+    cudaMemcpyAsync(h->herr, h->derr, sizeof(int), cudaMemcpyDeviceToHost, s);
+    return;
+  } else {
+    KL(launch_k(dev::k_to_float, std::min(ceil_div(np, 256), 4096), 256, 0, s, np, L.t64, L.r32));
+    cudaMemsetAsync(L.u32[L.cur32], 0, np * sizeof(float), s);
+    for (int c = 0; c < std::max(1, h->par.inner_cycles); ++c) {
+      ProfScope ps(h, CCM_PROF_VCYCLE, s);
+      vcycle<float>(h, 0, s);
+    }
+    KL(launch_k(dev::k_axpy<float>, std::min(ceil_div(np, 256), 4096), 256, 0, s, np, L.cls, L.u32[L.cur32], h->uhat));
     ucur = h->uhat;
   }
   {
@@ -1194,10 +1275,10 @@ static void iteration_body(ccm_handle* h, bool fp64, cudaStream_t s) {
     launch_regular<double>(h, L, ucur, h->rhat, L.t64, true, s);
   }
   if (L.n2)
-    KL(dev::k_rows<double, double, true, true><<<ceil_div(L.n2, 128), 128, 0, s>>>(
+    KL(launch_k(dev::k_rows<double, double, true, true>, ceil_div(L.n2, 128), 128, 0, s, 
         L.n2, L.W, L.irr_cell, L.ell_col, L.ell64, ucur, h->rhat, L.t64, nullptr, nullptr, nullptr));
   cudaMemsetAsync(h->dnorm, 0, sizeof(unsigned long long), s);
-  KL(dev::k_absmax<double><<<std::min(ceil_div(np, 256), 1216), 256, 0, s>>>(np, L.cls, L.t64, h->dnorm));
+  KL(launch_k(dev::k_absmax<double>, std::min(ceil_div(np, 256), 1216), 256, 0, s, np, L.cls, L.t64, h->dnorm));
   cudaMemcpyAsync(h->hnorm, h->dnorm, sizeof(unsigned long long), cudaMemcpyDeviceToHost, s);
   cudaMemcpyAsync(h->herr, h->derr, sizeof(int), cudaMemcpyDeviceToHost, s);
 }
@@ -1273,12 +1354,20 @@ int ccm_solve(ccm_handle* h, const double* f, const double* g, double* u, int nr
     if (rc) return rc;
     if (rnorm == 0) rnorm = 1;
     // initial residual
-    launch_regular<double>(h, L, U0, h->rhat, L.t64, true, s);
-    if (L.n2)
-      KL(dev::k_rows<double, double, true, true><<<ceil_div(L.n2, 128), 128, 0, s>>>(
-          L.n2, L.W, L.irr_cell, L.ell_col, L.ell64, U0, h->rhat, L.t64, nullptr, nullptr, nullptr));
-    rc = read_norm(h, L.cls, np, L.t64, s, rel);
-    if (rc) return rc;
+    if (!fp64 && h->fused_outer) {
+      outer_residual32(h, s);
+      CCM_CUDA(cudaMemcpyAsync(h->hnorm, h->dnorm, sizeof(unsigned long long), cudaMemcpyDeviceToHost, s));
+      CCM_CUDA(cudaStreamSynchronize(s));
+      unsigned long long bits = *h->hnorm;
+      std::memcpy(&rel, &bits, sizeof(double));
+    } else {
+      launch_regular<double>(h, L, U0, h->rhat, L.t64, true, s);
+      if (L.n2)
+        KL(launch_k(dev::k_rows<double, double, true, true>, ceil_div(L.n2, 128), 128, 0, s, 
+            L.n2, L.W, L.irr_cell, L.ell_col, L.ell64, U0, h->rhat, L.t64, nullptr, nullptr, nullptr));
+      rc = read_norm(h, L.cls, np, L.t64, s, rel);
+      if (rc) return rc;
+    }
     rel /= rnorm;
     ccm_stats local{};
     local.history[0] = rel;
@@ -1355,7 +1444,7 @@ int ccm_level_apply(ccm_handle* h, int level, const double* u, double* out, void
   KL(dev::k_pack<double, double><<<pg, 128, 0, s>>>(L.nx, L.ny, L.pitch, L.cls, u, L.t64, 1.0));
   launch_regular<double>(h, L, L.t64, nullptr, L.r64, false, s);
   if (L.n2)
-    KL(dev::k_rows<double, double, false, true><<<ceil_div(L.n2, 128), 128, 0, s>>>(
+    KL(launch_k(dev::k_rows<double, double, false, true>, ceil_div(L.n2, 128), 128, 0, s, 
         L.n2, L.W, L.irr_cell, L.ell_col, L.ell64, L.t64, nullptr, L.r64, L.nb, L.seg, nullptr));
   KL(dev::k_unpack<double><<<pg, 128, 0, s>>>(L.nx, L.ny, L.pitch, L.cls, L.r64, out, 1.0 / (L.h * L.h)));
   CCM_CUDA(cudaGetLastError());
