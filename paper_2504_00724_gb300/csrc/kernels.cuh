@@ -165,11 +165,6 @@ __device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
   asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
 }
 
-// plain arrival (no transaction bytes): completes the phase of a barrier initialised with count 1
-__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
-  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
-}
-
 // test for the completion of the phase with the given parity; the thread may stay suspended
 // in the instruction for up to 100 us while the phase is pending (no issue slots spent)
 __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t phase) {

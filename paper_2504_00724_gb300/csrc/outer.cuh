@@ -8,7 +8,7 @@
 // with lap = (-1, 16, -30, 16, -1), grad = (1, -8, 0, 8, -1).  The kernel forms the x
 // derivative grad_x u of every row of the staged tile once (4 FMA per cell) and combines
 // four of them per cell, so a regular cell costs 4 + 4 + 9 FMA instead of 25 (FP64 issue is
-// the bound of this kernel on GB300).  The evaluation order differs from the 25-tap sum, so
+// the bound of this kernel on GB300; the max-norm runs on the integer pipe).  The evaluation order differs from the 25-tap sum, so
 // the result agrees with it to rounding, not bit for bit.
 #pragma once
 
@@ -22,10 +22,14 @@ struct SepStencil {
   double ly[5];    // c lap / 12 along y
   double gx[5];    // grad / 12 along x
   double gy[5];    // b grad / 12 along y
+  double cc;       // the centre weight (a + c) lap[2] / 12
 };
 
-__device__ __forceinline__ double nan_to_inf(double v) {
-  return v <= 1.7976931348623157e308 ? v : __longlong_as_double(0x7ff0000000000000ULL);
+// |t| as the bit pattern of a non-negative double, NaN mapped to +Inf: non-negative doubles
+// order like their patterns, so the max-norm runs on the integer pipe
+__device__ __forceinline__ unsigned long long abs_bits(double t) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(t) & 0x7fffffffffffffffULL;
+  return b > 0x7ff0000000000000ULL ? 0x7ff0000000000000ULL : b;
 }
 
 // dynamic shared memory of k_resid64 (offsets are multiples of 128 bytes)
@@ -73,40 +77,39 @@ __global__ void __launch_bounds__(256, 3) k_resid64(const __grid_constant__ CUte
     }
     __syncthreads();
   }
-  // the 8 cells of a thread are independent: their arithmetic runs unconditionally (three
-  // separate FMA chains each) so that it interleaves; only the store depends on the class
+  // the 8 cells of a thread are independent: their arithmetic runs unconditionally, one FMA
+  // chain each, so that the chains interleave; only the store depends on the class
   const int x = threadIdx.x & 63, y0 = (threadIdx.x >> 6) * 8;
   const int i = cx0 + x;
-  double m = 0.0;
+  unsigned long long m = 0;
 #pragma unroll
   for (int k = 0; k < 8; ++k) {
     const int y = y0 + k;                 // own row; staged row y + 2
     const double* c = ut + (y + 2) * HX + x + 2;
-    double ax = (S.lx[2] + S.ly[2]) * c[0];
-    ax = fma(S.lx[0], c[-2], ax);
-    ax = fma(S.lx[1], c[-1], ax);
-    ax = fma(S.lx[3], c[1], ax);
-    ax = fma(S.lx[4], c[2], ax);
-    double ay = S.ly[0] * c[-2 * HX];
-    ay = fma(S.ly[1], c[-HX], ay);
-    ay = fma(S.ly[3], c[HX], ay);
-    ay = fma(S.ly[4], c[2 * HX], ay);
-    double az = 0.0;
+    double acc = S.cc * c[0];
+    acc = fma(S.lx[0], c[-2], acc);
+    acc = fma(S.lx[1], c[-1], acc);
+    acc = fma(S.lx[3], c[1], acc);
+    acc = fma(S.lx[4], c[2], acc);
+    acc = fma(S.ly[0], c[-2 * HX], acc);
+    acc = fma(S.ly[1], c[-HX], acc);
+    acc = fma(S.ly[3], c[HX], acc);
+    acc = fma(S.ly[4], c[2 * HX], acc);
     if (CROSS) {
       const double* d = dx + (y + 2) * JX + x;
-      az = S.gy[0] * d[-2 * JX];
-      az = fma(S.gy[1], d[-JX], az);
-      az = fma(S.gy[3], d[JX], az);
-      az = fma(S.gy[4], d[2 * JX], az);
+      acc = fma(S.gy[0], d[-2 * JX], acc);
+      acc = fma(S.gy[1], d[-JX], acc);
+      acc = fma(S.gy[3], d[JX], acc);
+      acc = fma(S.gy[4], d[2 * JX], acc);
     }
-    const double t = rt[y * HX + x + 2] - (ax + ay + az);
+    const double t = rt[y * HX + x + 2] - acc;
     if (i < nx && ct[(y + 2) * CLX + x + 2] == 1) {
       r32[(long)(cy0 + y + 2) * pitch + (i + 2)] = (float)t;
-      m = fmax(m, nan_to_inf(fabs(t)));
+      m = max(m, abs_bits(t));
     }
   }
-  for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
-  if ((threadIdx.x & 31) == 0 && m > 0.0) atomicMax(norm, (unsigned long long)__double_as_longlong(m));
+  for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
+  if ((threadIdx.x & 31) == 0 && m > 0) atomicMax(norm, m);
 }
 
 // fitted rows of the irregular cells: t = r_hat - sum_k beta_k u_hat(col_k); r32 and max |t|
@@ -116,7 +119,7 @@ __global__ void __launch_bounds__(128, 8) k_rows_r32(int n2, int W, const int32_
                            unsigned long long* __restrict__ norm) {
   pdl_enter();
   const int row = blockIdx.x * blockDim.x + threadIdx.x;
-  double m = 0.0;
+  unsigned long long m = 0;
   if (row < n2) {
     double acc = 0.0;
 #pragma unroll 15
@@ -124,10 +127,10 @@ __global__ void __launch_bounds__(128, 8) k_rows_r32(int n2, int W, const int32_
     const int q = cell[row];
     const double t = r[q] - acc;
     r32[q] = (float)t;
-    m = nan_to_inf(fabs(t));
+    m = abs_bits(t);
   }
-  for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
-  if ((threadIdx.x & 31) == 0 && m > 0.0) atomicMax(norm, (unsigned long long)__double_as_longlong(m));
+  for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
+  if ((threadIdx.x & 31) == 0 && m > 0) atomicMax(norm, m);
 }
 
 // u_hat += e on the non-empty cells of the 32 x 8 tiles that hold one

@@ -215,3 +215,169 @@ __global__ void __launch_bounds__(256, 3) k_smooth(const __grid_constant__ CUten
 
 }  // namespace dev
 }  // namespace ccm
+
+namespace ccm {
+namespace dev {
+
+// ---- residual + restriction of a level (Alg. 2: the coarse right-hand side and a zero coarse
+// iterate) as one persistent launch over the fine 64 x 32 tiles that restriction visits.
+// A tile item's halo tile of u, its boxes of r and of the cell volumes (68 x 32 over the
+// tile's rows) and its class bytes (80 x 36) arrive by TMA in one of two stages while the
+// previous item computes.  The fitted rows of the tile's irregular cells (listed per tile:
+// row and position) are gathered from global memory before the wait, and so are the class
+// bytes of the coarse cells the thread restricts to; regular cells take the stencil from the
+// staged tile; then the 32 x 16 coarse cells get the volume-weighted 2 x 2 sums.
+template <typename T>
+struct RestrictArgs {
+  const int32_t* tiles;
+  int ntiles, nxf, nyf, pitchf;
+  const int32_t* rr_off;
+  const int32_t* rr;
+  int n2, W;
+  const int32_t* irr_cell;
+  const int32_t* col;
+  const T* val;
+  const T* u;
+  const T* r;
+  int nxc, nyc, pitchc;
+  const uint8_t* clsc;
+  T* rc;
+  T* uc;
+  Stencil<T> S;
+  int* err;
+  uint32_t stage;
+};
+
+template <typename T>
+struct RestrictStage {
+  static constexpr uint32_t al(uint32_t b) { return (b + 127u) & ~127u; }
+  static constexpr uint32_t u_bytes = HY * HX * sizeof(T);
+  static constexpr uint32_t r_bytes = JY * HX * sizeof(T);
+  static constexpr uint32_t c_bytes = HY * CLX;
+  static constexpr uint32_t r_off = al(u_bytes);
+  static constexpr uint32_t c_off = r_off + al(r_bytes);
+  static constexpr uint32_t v_off = c_off + al(c_bytes);
+  static constexpr uint32_t bytes = al(v_off + r_bytes);
+  static constexpr uint32_t tx = u_bytes + 2 * r_bytes + c_bytes;
+};
+
+template <typename T, bool CROSS>
+__global__ void __launch_bounds__(256, 3) k_restrict_p(const __grid_constant__ CUtensorMap tin,
+                                                       const __grid_constant__ CUtensorMap tr,
+                                                       const __grid_constant__ CUtensorMap tcls,
+                                                       const __grid_constant__ CUtensorMap tvol, RestrictArgs<T> A) {
+  using S = RestrictStage<T>;
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  __shared__ T res[JY][JX];      // residual of every fine cell of the tile (0 on empty cells)
+  __shared__ __align__(8) uint64_t bar[2];
+  pdl_enter();
+  const int G = gridDim.x;
+  const int K = (A.ntiles - (int)blockIdx.x + G - 1) / G;
+  if (threadIdx.x == 0) {
+    mbar_init(&bar[0], 1);
+    mbar_init(&bar[1], 1);
+  }
+  __syncthreads();
+  auto issue = [&](int t, int sb) {
+    unsigned char* st = smem_raw + sb * A.stage;
+    const int cx0 = A.tiles[2 * t] * JX, cy0 = A.tiles[2 * t + 1] * JY;
+    mbar_expect_tx(&bar[sb], S::tx);
+    tma_load_2d(st, &tin, &bar[sb], cx0, cy0);
+    tma_load_2d(st + S::r_off, &tr, &bar[sb], cx0, cy0 + 2);
+    tma_load_2d(st + S::c_off, &tcls, &bar[sb], cx0, cy0);
+    tma_load_2d(st + S::v_off, &tvol, &bar[sb], cx0, cy0 + 2);
+  };
+  if (threadIdx.x == 0) {
+    issue(blockIdx.x, 0);
+    if (K > 1) issue(blockIdx.x + G, 1);
+  }
+  const int x = threadIdx.x & 63, y0 = (threadIdx.x >> 6) * 8;
+  for (int k = 0; k < K; ++k) {
+    const int t = blockIdx.x + k * G;
+    const int sb = k & 1;
+    const uint32_t parity = (k >> 1) & 1;
+    const int cx0 = A.tiles[2 * t] * JX, cy0 = A.tiles[2 * t + 1] * JY;
+    const int k0 = A.rr_off[t], k1 = A.rr_off[t + 1];
+    for (int q = k0 + (int)threadIdx.x; q < k1; q += blockDim.x) {
+      const int row = A.rr[2 * q], loc = A.rr[2 * q + 1];
+      T acc = 0;
+#pragma unroll 15
+      for (int m = 0; m < A.W; ++m) acc += A.val[(long)m * A.n2 + row] * A.u[A.col[(long)m * A.n2 + row]];
+      res[loc >> 6][loc & 63] = A.r[A.irr_cell[row]] - acc;
+    }
+    // class bytes of this thread's two coarse cells (0 outside the coarse level)
+    uint8_t cc[2];
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const int c = threadIdx.x + h * 256;
+      const int I = cx0 / 2 + c % (JX / 2), J = cy0 / 2 + c / (JX / 2);
+      cc[h] = (I < A.nxc && J < A.nyc) ? A.clsc[(long)(J + 2) * A.pitchc + (I + 2)] : (uint8_t)0;
+    }
+    const bool ok = __syncthreads_and(wait_parity(&bar[sb], parity));
+    if (!ok) {
+      wait_parity(&bar[sb], parity);
+      if (k + 1 < K) wait_parity(&bar[sb ^ 1], ((k + 1) >> 1) & 1);
+      if (threadIdx.x == 0) atomicExch(A.err, 1);
+      return;
+    }
+    const unsigned char* st = smem_raw + sb * A.stage;
+    const T* tile = reinterpret_cast<const T*>(st);
+    const T* rt = reinterpret_cast<const T*>(st + S::r_off);
+    const uint8_t* ct = st + S::c_off;
+    const T* vt = reinterpret_cast<const T*>(st + S::v_off);
+    {
+      T w[5][5];
+#pragma unroll
+      for (int q = 0; q < 4; ++q)
+#pragma unroll
+        for (int b = 0; b < 5; ++b) w[q][b] = tile[(y0 + q) * HX + x + b];
+#pragma unroll
+      for (int kk = 0; kk < 8; ++kk) {
+#pragma unroll
+        for (int b = 0; b < 5; ++b) w[4][b] = tile[(y0 + kk + 4) * HX + x + b];
+        const uint8_t cv = ct[(y0 + kk + 2) * CLX + x + 2];
+        if (cv == 1) {
+          T acc = 0;
+#pragma unroll
+          for (int q = 0; q < 5; ++q)
+#pragma unroll
+            for (int b = 0; b < 5; ++b) {
+              if (!CROSS && q != 2 && b != 2) continue;
+              acc += A.S.w[q * 5 + b] * w[q][b];
+            }
+          res[y0 + kk][x] = rt[(y0 + kk) * HX + x + 2] - acc;
+        } else if (cv == 0) {
+          res[y0 + kk][x] = (T)0;
+        }
+#pragma unroll
+        for (int q = 0; q < 4; ++q)
+#pragma unroll
+          for (int b = 0; b < 5; ++b) w[q][b] = w[q + 1][b];
+      }
+    }
+    __syncthreads();
+    // 32 x 16 coarse cells, two per thread
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      if (cc[h] == 0) continue;
+      const int c = threadIdx.x + h * 256;
+      const int ci = c % (JX / 2), cj = c / (JX / 2);
+      const long pc = (long)(cy0 / 2 + cj + 2) * A.pitchc + (cx0 / 2 + ci + 2);
+      const T* v = vt + (2 * cj) * HX + 2 * ci + 2;
+      const T v0 = v[0], v1 = v[1], v2 = v[HX], v3 = v[HX + 1];
+      const T s = v0 * res[2 * cj][2 * ci] + v1 * res[2 * cj][2 * ci + 1] + v2 * res[2 * cj + 1][2 * ci] +
+                  v3 * res[2 * cj + 1][2 * ci + 1];
+      const T sv = v0 + v1 + v2 + v3;
+      A.rc[pc] = sv > (T)0 ? (T)4 * s / sv : (T)0;
+      A.uc[pc] = (T)0;
+    }
+    __syncthreads();      // res and stage sb are free
+    if (threadIdx.x == 0 && k + 2 < K) {
+      fence_proxy_async();
+      issue(t + 2 * G, sb);
+    }
+  }
+}
+
+}  // namespace dev
+}  // namespace ccm

@@ -46,6 +46,10 @@ struct DevLevel {
   uint32_t smooth_stage[2] = {0, 0};
   size_t smooth_smem[2] = {0, 0};
   int smooth_grid[2] = {0, 0};
+  CUtensorMap tmv64, tmv32;     // 68 x 32 boxes over the cell volumes
+  bool restrict_ok[2] = {false, false};  // persistent restriction (k_restrict_p), [0] FP64, [1] FP32
+  uint32_t restrict_stage[2] = {0, 0};
+  int restrict_grid[2] = {0, 0};
   int32_t* rr_off = nullptr;    // per restriction tile: its irregular rows [rr_off[t], rr_off[t + 1])
   int32_t* rr = nullptr;        // (row, y * 64 + x in the tile) pairs
   uint8_t* cls = nullptr;
@@ -480,6 +484,40 @@ void smooth_step(ccm_handle* H, DevLevel& L, cudaStream_t s, const T* uc = nullp
 template <typename T>
 void restrict_to(ccm_handle* H, DevLevel& F, DevLevel& C, cudaStream_t s) {
   ProfScope ps(H, (&F == &H->L[0] && sizeof(T) == 4) ? CCM_PROF_RESTRICT_FP32 : 0, s);
+  const int kk = sizeof(T) == 8 ? 0 : 1;
+  if (H->par.smoother == 1 && F.tma && F.ntiles64r && F.restrict_ok[kk] && H->persistent) {
+    dev::RestrictArgs<T> A{};
+    A.tiles = F.tiles64r;
+    A.ntiles = F.ntiles64r;
+    A.nxf = F.nx;
+    A.nyf = F.ny;
+    A.pitchf = F.pitch;
+    A.rr_off = F.rr_off;
+    A.rr = F.rr;
+    A.n2 = F.n2;
+    A.W = F.W;
+    A.irr_cell = F.irr_cell;
+    A.col = F.ell_col;
+    A.val = Ell<T>(F);
+    A.u = U<T>(F);
+    A.r = R<T>(F);
+    A.nxc = C.nx;
+    A.nyc = C.ny;
+    A.pitchc = C.pitch;
+    A.clsc = C.cls;
+    A.rc = R<T>(C);
+    A.uc = U<T>(C);
+    A.S = stencil<T>(H);
+    A.err = H->derr;
+    A.stage = F.restrict_stage[kk];
+    const CUtensorMap& tv = kk == 0 ? F.tmv64 : F.tmv32;
+    const size_t smem = 2 * (size_t)A.stage;
+    if (H->cross)
+      KL(launch_k(dev::k_restrict_p<T, true>, F.restrict_grid[kk], 256, smem, s, TmU<T>(F), TmR<T>(F), F.tmcls, tv, A));
+    else
+      KL(launch_k(dev::k_restrict_p<T, false>, F.restrict_grid[kk], 256, smem, s, TmU<T>(F), TmR<T>(F), F.tmcls, tv, A));
+    return;
+  }
   if (H->par.smoother == 1 && F.tma && F.ntiles64r) {
     const auto& S = stencil<T>(H);
     if (H->cross)
@@ -793,6 +831,8 @@ int upload_hierarchy(ccm_handle* h) {
       d.tma = make_tmap(&d.tm64[b], d.u64[b], d.pitch, d.rows, true) &&
               make_tmap(&d.tm32[b], d.u32[b], d.pitch, d.rows, false);
     d.tma = d.tma && make_tmap(&d.tmcls, d.cls, d.pitch, d.rows, CU_TENSOR_MAP_DATA_TYPE_UINT8, 1, dev::CLX, dev::HY) &&
+            make_tmap(&d.tmv64, d.vol64, d.pitch, d.rows, CU_TENSOR_MAP_DATA_TYPE_FLOAT64, 8, dev::HX, dev::JY) &&
+            make_tmap(&d.tmv32, d.vol32, d.pitch, d.rows, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, dev::HX, dev::JY) &&
             make_tmap(&d.tmr64, d.r64, d.pitch, d.rows, CU_TENSOR_MAP_DATA_TYPE_FLOAT64, 8, dev::HX, dev::JY) &&
             make_tmap(&d.tmr32, d.r32, d.pitch, d.rows, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, dev::HX, dev::JY);
   }
@@ -902,6 +942,26 @@ int upload_hierarchy(ccm_handle* h) {
       for (int b = 0; b < 2 && d.tma_pro; ++b)
         d.tma_pro = make_tmap(&d.tmuc64[b], c.u64[b], c.pitch, c.rows, CU_TENSOR_MAP_DATA_TYPE_FLOAT64, 8, dev::UCX, dev::UCY) &&
                     make_tmap(&d.tmuc32[b], c.u32[b], c.pitch, c.rows, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, dev::UCX, dev::UCY);
+      // the persistent restriction: two stages of u, r, class bytes and volumes per tile
+      for (int k = 0; k < 2 && d.ntiles64r > 0; ++k) {
+        const uint32_t stage = k == 0 ? dev::RestrictStage<double>::bytes : dev::RestrictStage<float>::bytes;
+        const size_t smem = 2 * (size_t)stage;
+        int occ = 0;
+        if (k == 0) {
+          auto fn = h->cross ? dev::k_restrict_p<double, true> : dev::k_restrict_p<double, false>;
+          cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+          cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, 256, smem);
+        } else {
+          auto fn = h->cross ? dev::k_restrict_p<float, true> : dev::k_restrict_p<float, false>;
+          cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+          cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, 256, smem);
+        }
+        if (occ < 1 || nsm < 1) continue;
+        d.restrict_ok[k] = true;
+        d.restrict_stage[k] = stage;
+        d.restrict_grid[k] = std::min(d.ntiles64r, nsm * occ);
+      }
+      cudaGetLastError();
     }
   }
   // the cluster launch takes over from the first level with at most coarse_n cells a side
@@ -936,6 +996,7 @@ int upload_hierarchy(ccm_handle* h) {
       h->sep.gx[k] = grad[k] / 12.0;
       h->sep.gy[k] = h->b * grad[k] / 12.0;
     }
+    h->sep.cc = h->sep.lx[2] + h->sep.ly[2];
     const DevLevel& d0 = h->L[0];
     cudaFuncSetAttribute(dev::k_resid64<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, dev::Resid64Smem::bytes(true));
     cudaFuncSetAttribute(dev::k_resid64<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, dev::Resid64Smem::bytes(false));
