@@ -40,6 +40,32 @@ RTOL = 1e-10
 SM_COUNT = 152
 FP64_FMA_PER_CLK_SM = 2          # FP64 FMA issue rate per SM (4 flop / clk / SM)
 
+# DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) per launch of a reported kernel
+# class on the default 4096^2 workload, from one ncu capture (the command is in profiles/).
+# A figure is reported only while the device sources hash to the value it was taken on.
+KERNEL_SOURCES = ("kernels.cuh", "smooth.cuh", "outer.cuh")
+NCU_TRAFFIC = {        # class name -> (source hash, bytes per launch)
+    "fp32 sweep, level 0 (SMO-1 regular cells + SMO-2 blocks)": ("b70895564f2d52c7", 74.12e6),
+    "fp32 residual + restriction, level 0": ("b70895564f2d52c7", 78.91e6),
+    "fp64 outer residual, level 0 (regular cells, separable stencil)": ("b70895564f2d52c7", 96.12e6),
+}
+
+
+def source_hash():
+    import hashlib
+    h = hashlib.sha256()
+    for name in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, "paper_2504_00724_gb300", "csrc", name), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def traffic_of(name, n):
+    if n != 4096 or name not in NCU_TRAFFIC:
+        return None
+    sha, byts = NCU_TRAFFIC[name]
+    return byts if sha == source_hash() else None
+
 
 def parse():
     ap = argparse.ArgumentParser()
@@ -306,12 +332,13 @@ def main():
             peak = hbm
             achieved = work / (avg_ms / 1000.0) / 1e9
         roof = {"bound": bound, "achieved": achieved, "peak": peak, "unit": unit, "frac": achieved / peak,
-                "traffic": None, "kernel": name, "avg_launch_us": avg_ms * 1000.0,
+                "traffic": traffic_of(name, args.n), "kernel": name, "avg_launch_us": avg_ms * 1000.0,
                 "launches_per_step": per_step, "algorithmic_per_launch": work,
                 "peak_source": ("derived: 152 SMs x 4 FP64 flop/clk x max SM clock" if bound == "alu"
                                 else f"{src} copy bandwidth"),
                 "others": [{"kernel": c[0], "ms_per_step": c[1], "avg_launch_us": c[2] * 1000.0, "bound": c[4],
-                            "achieved": (c[5] / (c[2] / 1000.0) / (1e12 if c[4] == "alu" else 1e9))}
+                            "achieved": (c[5] / (c[2] / 1000.0) / (1e12 if c[4] == "alu" else 1e9)),
+                            "traffic": traffic_of(c[0], args.n)}
                            for c in classes if c[0] != name]}
 
     cpu = None
