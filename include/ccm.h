@@ -95,6 +95,13 @@ typedef struct {
                         as one launch of one thread-block cluster (16 or 8 CTAs of 1024
                         threads, cluster barriers between the phases of Alg. 2); smoother 1
                         with ras_passes <= 1 only; 0: never */
+  int batch;         /* CCM_MIXED: right-hand sides ccm_solve advances together (1 - 4096).
+                        The handle's FP32 work arrays and its level-0 FP64 iterate and
+                        right-hand side hold `batch` copies, and every kernel launch of an
+                        outer iteration covers all of them (the right-hand side is the
+                        grid's y index).  Needs the persistent kernels on every level of
+                        64^2 cells or more, the block-Jacobi smoother and coarse_n 0; else
+                        the handle runs one right-hand side at a time (ccm_info.batch). */
 } ccm_params;
 
 typedef struct {
@@ -106,6 +113,8 @@ typedef struct {
   int64_t device_bytes; /* device memory held by the handle */
   double setup_ms;      /* host + upload time of ccm_setup */
   double plg_cond_max;  /* largest 2-norm condition number of a chosen FV sample matrix */
+  int batch;            /* right-hand sides ccm_solve advances together (1 unless params.batch > 1
+                           and the conditions stated there hold) */
 } ccm_info;
 
 typedef struct {
@@ -118,7 +127,7 @@ typedef struct ccm_handle ccm_handle;
 
 /* Fill p with the defaults: omega 0.7, nu1 = nu2 = 3, theta 0.3, coarsest 16, CCM_MIXED,
  * rtol 1e-10, max_iter 100, ras_passes 1, ras_block 64, ras_overlap 32, nthreads 0,
- * ras_exact 0, inner_cycles 3, smoother 1, coarse_n 0. */
+ * ras_exact 0, inner_cycles 3, smoother 1, coarse_n 0, batch 1. */
 int ccm_default_params(ccm_params* p);
 
 /* Host setup (Sec. 3.1 - 3.4, Sec. 4): cut cells and moments (Green's formula, Sec. 2.4),
@@ -192,8 +201,11 @@ int ccm_apply_T(ccm_handle* h, const double* v, double* out_u, double* out_g, in
  * image of the FP64 residual, then u += e in FP64) runs as one CUDA graph, captured on the
  * first call; the FP64 residual norm is read back after every outer iteration.
  * f: device [nrhs][ny][nx] cell averages; g: device [nrhs][n_segments] (NULL: g = 0);
- * u: device [nrhs][ny][nx], in: initial guess, out: solution.  stats (host, nullable)
- * receives the outer iteration count and residual history of the last right-hand side.
+ * u: device [nrhs][ny][nx], in: initial guess, out: solution.  CCM_MIXED handles with
+ * ccm_info.batch > 1 advance up to that many right-hand sides per graph replay, until the
+ * worst of them meets rtol (the others iterate on).  stats (host, nullable) receives the
+ * outer iteration count of the last group and, per iteration, the largest relative residual
+ * of its right-hand sides.
  * Synchronises the stream once per outer iteration (the convergence test).  The first call
  * captures the graphs, so make it outside any caller's stream capture.
  * Errors: CCM_ENOCONV (u holds the last iterate), CCM_ENOTFINITE, CCM_ECUDA. */

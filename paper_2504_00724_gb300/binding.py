@@ -42,7 +42,7 @@ class ccm_params(ctypes.Structure):
                 ("rtol", ctypes.c_double), ("max_iter", ctypes.c_int), ("ras_passes", ctypes.c_int),
                 ("ras_block", ctypes.c_int), ("ras_overlap", ctypes.c_int), ("nthreads", ctypes.c_int),
                 ("ras_exact", ctypes.c_int), ("inner_cycles", ctypes.c_int), ("smoother", ctypes.c_int),
-                ("coarse_n", ctypes.c_int)]
+                ("coarse_n", ctypes.c_int), ("batch", ctypes.c_int)]
 
 
 class ccm_info(ctypes.Structure):
@@ -50,7 +50,7 @@ class ccm_info(ctypes.Structure):
                 ("n_cells", ctypes.c_int64), ("n_regular", ctypes.c_int64),
                 ("n_irregular", ctypes.c_int64), ("n_segments", ctypes.c_int64),
                 ("device_bytes", ctypes.c_int64), ("setup_ms", ctypes.c_double),
-                ("plg_cond_max", ctypes.c_double)]
+                ("plg_cond_max", ctypes.c_double), ("batch", ctypes.c_int)]
 
 
 class ccm_stats(ctypes.Structure):

@@ -185,6 +185,16 @@ __device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, u
       : "memory");
 }
 
+// 3-D box (x, y, right-hand side z): the iterate and right-hand-side maps of a level cover
+// all right-hand sides of a batch, one padded level array after the other
+__device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* map, uint64_t* bar, int x, int y, int z) {
+  asm volatile(
+      "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], [%5];" ::"r"(
+          smem_u32(dst)),
+      "l"(map), "r"(x), "r"(y), "r"(z), "r"(smem_u32(bar))
+      : "memory");
+}
+
 // orders this thread's earlier shared-memory accesses before later async-proxy (TMA, bulk)
 // writes into the same buffer
 __device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
@@ -213,7 +223,7 @@ __global__ void __launch_bounds__(256) k_jacobi_tma(const __grid_constant__ CUte
   __syncthreads();
   if (threadIdx.x == 0) {
     mbar_expect_tx(&bar, (uint32_t)(HX * HY * sizeof(T)));
-    tma_load_2d(tile, &tin, &bar, cx0, cy0);
+    tma_load_3d(tile, &tin, &bar, cx0, cy0, 0);
   }
   // the class bytes and right-hand sides of this thread's 8 cells load while the tile lands
   const int x = threadIdx.x & 63, y0 = (threadIdx.x >> 6) * 8;
@@ -282,6 +292,7 @@ struct SweepArgs {
   int* err;
   const int32_t* par;    // per ELL slot: padded parent (level m + 1) of a regular column, else -1
   const T* uc;           // coarse iterate: the sweep reads u + P uc (regular cells), or null
+  long bs, bsc;          // batch strides (elements) of this level's and the coarse level's arrays
 };
 
 template <typename T>
@@ -324,6 +335,9 @@ template <typename T, bool CROSS, bool TMA>
 __global__ void __launch_bounds__(256) k_sweep(const __grid_constant__ CUtensorMap tin, SweepArgs<T> a) {
   pdl_enter();
   extern __shared__ unsigned char smem_raw[];
+  a.u_old += (long)blockIdx.y * a.bs;      // right-hand side blockIdx.y of the batch
+  a.u_new += (long)blockIdx.y * a.bs;
+  a.r += (long)blockIdx.y * a.bs;
   if ((int)blockIdx.x >= a.ntiles) {
     block_part<T>(a, blockIdx.x - a.ntiles, reinterpret_cast<T*>(smem_raw));
     return;
@@ -347,7 +361,7 @@ __global__ void __launch_bounds__(256) k_sweep(const __grid_constant__ CUtensorM
   __syncthreads();
   if (threadIdx.x == 0) {
     mbar_expect_tx(&bar, (uint32_t)(HX * HY * sizeof(T)));
-    tma_load_2d(tile, &tin, &bar, cx0, cy0);
+    tma_load_3d(tile, &tin, &bar, cx0, cy0, 0);
   }
   const int x = threadIdx.x & 63, y0 = (threadIdx.x >> 6) * 8;
   const int i = cx0 + x;
@@ -413,10 +427,10 @@ __global__ void __launch_bounds__(256) k_sweep_tma(const __grid_constant__ CUten
   __syncthreads();
   if (threadIdx.x == 0) {
     mbar_expect_tx(&bar, (uint32_t)(HX * HY * sizeof(T) + (PRO ? HY * CLX + UCY * UCX * sizeof(T) : 0)));
-    tma_load_2d(tile, &tin, &bar, cx0, cy0);
+    tma_load_3d(tile, &tin, &bar, cx0, cy0, 0);
     if (PRO) {
       tma_load_2d(ctile, &tcls, &bar, cx0, cy0);
-      tma_load_2d(uct, &tuc, &bar, cx0 / 2, cy0 / 2 + 1);
+      tma_load_3d(uct, &tuc, &bar, cx0 / 2, cy0 / 2 + 1, 0);
     }
   }
   const int x = threadIdx.x & 63, y0 = (threadIdx.x >> 6) * 8;
@@ -488,6 +502,10 @@ __global__ void __launch_bounds__(256) k_blocks(SweepArgs<T> a) {
   extern __shared__ __align__(128) unsigned char smem_raw[];
   __shared__ __align__(8) uint64_t bar;
   __shared__ T part[8][32];
+  a.u_old += (long)blockIdx.y * a.bs;      // right-hand side blockIdx.y of the batch
+  a.u_new += (long)blockIdx.y * a.bs;
+  a.r += (long)blockIdx.y * a.bs;
+  if (a.uc) a.uc += (long)blockIdx.y * a.bsc;
   const int b = blockIdx.x / a.chunks, chunk = blockIdx.x % a.chunks;
   const int cs = a.blk[4 * b], ce = a.blk[4 * b + 1], es = a.blk[4 * b + 2], ee = a.blk[4 * b + 3];
   const int ne = ee - es, nc = ce - cs;
@@ -568,7 +586,7 @@ __global__ void __launch_bounds__(256, 4) k_restrict_tma(const __grid_constant__
   __syncthreads();
   if (threadIdx.x == 0) {
     mbar_expect_tx(&bar, (uint32_t)(HX * HY * sizeof(T)));
-    tma_load_2d(tile, &tin, &bar, cx0, cy0);
+    tma_load_3d(tile, &tin, &bar, cx0, cy0, 0);
   }
   const int k0 = rr_off[blockIdx.x], k1 = rr_off[blockIdx.x + 1];
   for (int k = k0 + (int)threadIdx.x; k < k1; k += blockDim.x) {
@@ -645,8 +663,12 @@ __global__ void k_restrict_rows(int nxc, int nyc, int pitchc, int pitchf, const 
                                 const uint8_t* __restrict__ clsf, const T* __restrict__ volf,
                                 const int32_t* __restrict__ rowmap, int n2, int W, const int32_t* __restrict__ col,
                                 const T* __restrict__ val, const T* __restrict__ u, const T* __restrict__ r,
-                                T* __restrict__ rc, T* __restrict__ uc, Stencil<T> S) {
+                                T* __restrict__ rc, T* __restrict__ uc, Stencil<T> S, long bs, long bsc) {
   pdl_enter();
+  u += blockIdx.z * bs;       // right-hand side blockIdx.z of the batch
+  r += blockIdx.z * bs;
+  rc += blockIdx.z * bsc;
+  uc += blockIdx.z * bsc;
   int I = blockIdx.x * blockDim.x + threadIdx.x;
   int J = blockIdx.y * blockDim.y + threadIdx.y;
   if (I >= nxc || J >= nyc) return;
@@ -805,8 +827,10 @@ __global__ void k_restrict(int nxc, int nyc, int pitchc, int pitchf, const uint8
 // prolongation (Sec. 4.1): u += uc[parent] on fine regular cells
 template <typename T>
 __global__ void k_prolong(const int32_t* __restrict__ tiles, const uint8_t* __restrict__ cls, int nx, int ny,
-                          int pitch, int pitchc, const T* __restrict__ uc, T* __restrict__ u) {
+                          int pitch, int pitchc, const T* __restrict__ uc, T* __restrict__ u, long bs, long bsc) {
   pdl_enter();
+  uc += blockIdx.y * bsc;     // right-hand side blockIdx.y of the batch
+  u += blockIdx.y * bs;
   int i, j;
   long p;
   if (!tile_cell(tiles, nx, ny, pitch, i, j, p)) return;
@@ -817,8 +841,10 @@ __global__ void k_prolong(const int32_t* __restrict__ tiles, const uint8_t* __re
 // bottom solve: u[cell_k] = sum_c inv[c][k] r[cell_c]
 template <typename T>
 __global__ void k_bottom(int n, const int32_t* __restrict__ cell, const T* __restrict__ inv,
-                         const T* __restrict__ r, T* __restrict__ u) {
+                         const T* __restrict__ r, T* __restrict__ u, long bs) {
   pdl_enter();
+  r += blockIdx.y * bs;       // right-hand side blockIdx.y of the batch
+  u += blockIdx.y * bs;
   extern __shared__ unsigned char smem_raw[];
   T* s = reinterpret_cast<T*>(smem_raw);
   for (int c = threadIdx.x; c < n; c += blockDim.x) s[c] = r[cell[c]];
@@ -874,8 +900,10 @@ __global__ void k_sub_boundary(int n2, const int32_t* __restrict__ cell, const d
 // max |x| over the non-empty cells (non-negative doubles order like their bit patterns)
 template <typename T>
 __global__ void k_absmax(long n, const uint8_t* __restrict__ cls, const T* __restrict__ x,
-                         unsigned long long* __restrict__ out) {
+                         unsigned long long* __restrict__ out, long bs) {
   pdl_enter();
+  x += blockIdx.y * bs;       // right-hand side blockIdx.y of the batch: its own word
+  out += blockIdx.y;
   double m = 0.0;
   for (long p = blockIdx.x * (long)blockDim.x + threadIdx.x; p < n; p += (long)gridDim.x * blockDim.x)
     if (cls[p] != 0) {

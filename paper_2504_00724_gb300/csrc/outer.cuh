@@ -50,7 +50,7 @@ __global__ void __launch_bounds__(256, 3) k_resid64(const __grid_constant__ CUte
                                                  const __grid_constant__ CUtensorMap tcls,
                                                  const int32_t* __restrict__ tiles, int nx, int pitch,
                                                  float* __restrict__ r32, unsigned long long* __restrict__ norm,
-                                                 SepStencil S, int* __restrict__ err) {
+                                                 SepStencil S, int* __restrict__ err, long bs) {
   extern __shared__ __align__(128) unsigned char smem_raw[];
   double* ut = reinterpret_cast<double*>(smem_raw);                               // [HY][HX]
   double* rt = reinterpret_cast<double*>(smem_raw + Resid64Smem::rt_off);         // [JY][HX]
@@ -58,13 +58,16 @@ __global__ void __launch_bounds__(256, 3) k_resid64(const __grid_constant__ CUte
   double* dx = reinterpret_cast<double*>(smem_raw + Resid64Smem::dx_off);         // [HY][JX]
   __shared__ __align__(8) uint64_t bar;
   pdl_enter();
+  const int z = blockIdx.y;          // right-hand side of the batch
+  r32 += (long)z * bs;
+  norm += z;
   const int cx0 = tiles[2 * blockIdx.x] * JX, cy0 = tiles[2 * blockIdx.x + 1] * JY;
   if (threadIdx.x == 0) mbar_init(&bar, 1);
   __syncthreads();
   if (threadIdx.x == 0) {
     mbar_expect_tx(&bar, Resid64Smem::tx);
-    tma_load_2d(ut, &tu, &bar, cx0, cy0);
-    tma_load_2d(rt, &tr, &bar, cx0, cy0 + 2);
+    tma_load_3d(ut, &tu, &bar, cx0, cy0, z);
+    tma_load_3d(rt, &tr, &bar, cx0, cy0 + 2, z);
     tma_load_2d(ct, &tcls, &bar, cx0, cy0);
   }
   const bool ok = __syncthreads_and(tile_wait(&bar, err));
@@ -116,8 +119,12 @@ __global__ void __launch_bounds__(256, 3) k_resid64(const __grid_constant__ CUte
 __global__ void __launch_bounds__(128, 8) k_rows_r32(int n2, int W, const int32_t* __restrict__ cell, const int32_t* __restrict__ col,
                            const double* __restrict__ val, const double* __restrict__ u,
                            const double* __restrict__ r, float* __restrict__ r32,
-                           unsigned long long* __restrict__ norm) {
+                           unsigned long long* __restrict__ norm, long bs) {
   pdl_enter();
+  u += blockIdx.y * bs;       // right-hand side blockIdx.y of the batch
+  r += blockIdx.y * bs;
+  r32 += blockIdx.y * bs;
+  norm += blockIdx.y;
   const int row = blockIdx.x * blockDim.x + threadIdx.x;
   unsigned long long m = 0;
   if (row < n2) {
@@ -135,8 +142,10 @@ __global__ void __launch_bounds__(128, 8) k_rows_r32(int n2, int W, const int32_
 
 // u_hat += e on the non-empty cells of the 32 x 8 tiles that hold one
 __global__ void k_axpy_tiles(const int32_t* __restrict__ tiles, const uint8_t* __restrict__ cls, int nx, int ny,
-                             int pitch, const float* __restrict__ e, double* __restrict__ u) {
+                             int pitch, const float* __restrict__ e, double* __restrict__ u, long bs) {
   pdl_enter();
+  e += blockIdx.y * bs;       // right-hand side blockIdx.y of the batch
+  u += blockIdx.y * bs;
   const int i = tiles[2 * blockIdx.x] * TX + threadIdx.x;
   const int j = tiles[2 * blockIdx.x + 1] * TY + threadIdx.y;
   if (i >= nx || j >= ny) return;

@@ -55,6 +55,7 @@ template <typename T, bool PRO>
 __device__ __forceinline__ void smooth_issue(const SmoothArgs<T>& A, const CUtensorMap* tin, const CUtensorMap* tr,
                                              const CUtensorMap* tcls, const CUtensorMap* tuc, int item,
                                              unsigned char* st, uint64_t* bar) {
+  const int z = blockIdx.y;      // right-hand side of the batch
   const SweepArgs<T>& a = A.a;
   if (item < A.nbi) {
     const int b = item;
@@ -67,10 +68,10 @@ __device__ __forceinline__ void smooth_issue(const SmoothArgs<T>& A, const CUten
     const int t = item - A.nbi;
     const int cx0 = a.tiles[2 * t] * JX, cy0 = a.tiles[2 * t + 1] * JY;
     mbar_expect_tx(bar, S::u_bytes + S::r_bytes + S::c_bytes + (PRO ? S::uc_bytes : 0));
-    tma_load_2d(st, tin, bar, cx0, cy0);
-    tma_load_2d(st + S::r_off, tr, bar, cx0, cy0 + 2);
+    tma_load_3d(st, tin, bar, cx0, cy0, z);
+    tma_load_3d(st + S::r_off, tr, bar, cx0, cy0 + 2, z);
     tma_load_2d(st + S::c_off, tcls, bar, cx0, cy0);
-    if (PRO) tma_load_2d(st + S::uc_off, tuc, bar, cx0 / 2, cy0 / 2 + 1);
+    if (PRO) tma_load_3d(st + S::uc_off, tuc, bar, cx0 / 2, cy0 / 2 + 1, z);
   }
 }
 
@@ -84,6 +85,12 @@ __global__ void __launch_bounds__(256, 3) k_smooth(const __grid_constant__ CUten
   __shared__ T part[8][32];
   pdl_enter();
   const SweepArgs<T>& a = A.a;
+  // this CTA's right-hand side of the batch (blockIdx.y)
+  const long bo = (long)blockIdx.y * a.bs;
+  const T* __restrict__ u_old = a.u_old + bo;
+  T* __restrict__ u_new = a.u_new + bo;
+  const T* __restrict__ rhs = a.r + bo;
+  const T* __restrict__ ucs = PRO ? a.uc + (long)blockIdx.y * a.bsc : nullptr;
   T* sres = reinterpret_cast<T*>(smem_raw + 2 * A.stage);
   const int G = gridDim.x;
   const int K = (A.nitems - (int)blockIdx.x + G - 1) / G;   // items of this CTA (>= 1)
@@ -114,14 +121,14 @@ __global__ void __launch_bounds__(256, 3) k_smooth(const __grid_constant__ CUten
         T acc = 0;
 #pragma unroll 15
         for (int m = 0; m < a.W; ++m) {
-          T v = a.u_old[a.col[(long)m * a.n2 + row]];
+          T v = u_old[a.col[(long)m * a.n2 + row]];
           if (PRO) {
             const int pq = a.par[(long)m * a.n2 + row];
-            if (pq >= 0) v += a.uc[pq];
+            if (pq >= 0) v += ucs[pq];
           }
           acc += a.val[(long)m * a.n2 + row] * v;
         }
-        sres[e] = a.r[a.cell[row]] - acc;
+        sres[e] = rhs[a.cell[row]] - acc;
       }
     }
     const bool ok = __syncthreads_and(wait_parity(&bar[sb], parity));
@@ -146,7 +153,7 @@ __global__ void __launch_bounds__(256, 3) k_smooth(const __grid_constant__ CUten
 #pragma unroll
           for (int w = 0; w < 8; ++w) tot += part[w][lane];
           const long q = a.cell[cs + c];
-          a.u_new[q] = a.u_old[q] + tot;
+          u_new[q] = u_old[q] + tot;
         }
         __syncthreads();
       }
@@ -196,7 +203,7 @@ __global__ void __launch_bounds__(256, 3) k_smooth(const __grid_constant__ CUten
                 acc += a.S.w[q * 5 + b] * w[q][b];
               }
             const long p = (long)(cy0 + y0 + kk + 2) * a.pitch + (i + 2);
-            a.u_new[p] = w[2][2] + a.S.omega_d * (rt[(y0 + kk) * HX + x + 2] - acc);
+            u_new[p] = w[2][2] + a.S.omega_d * (rt[(y0 + kk) * HX + x + 2] - acc);
           }
 #pragma unroll
           for (int q = 0; q < 4; ++q)
@@ -246,6 +253,7 @@ struct RestrictArgs {
   Stencil<T> S;
   int* err;
   uint32_t stage;
+  long bs, bsc;        // batch strides (elements) of the fine and the coarse level arrays
 };
 
 template <typename T>
@@ -278,12 +286,18 @@ __global__ void __launch_bounds__(256, 3) k_restrict_p(const __grid_constant__ C
     mbar_init(&bar[1], 1);
   }
   __syncthreads();
+  // this CTA's right-hand side of the batch (blockIdx.y)
+  const int z = blockIdx.y;
+  const T* __restrict__ uf = A.u + (long)z * A.bs;
+  const T* __restrict__ rf = A.r + (long)z * A.bs;
+  T* __restrict__ rcz = A.rc + (long)z * A.bsc;
+  T* __restrict__ ucz = A.uc + (long)z * A.bsc;
   auto issue = [&](int t, int sb) {
     unsigned char* st = smem_raw + sb * A.stage;
     const int cx0 = A.tiles[2 * t] * JX, cy0 = A.tiles[2 * t + 1] * JY;
     mbar_expect_tx(&bar[sb], S::tx);
-    tma_load_2d(st, &tin, &bar[sb], cx0, cy0);
-    tma_load_2d(st + S::r_off, &tr, &bar[sb], cx0, cy0 + 2);
+    tma_load_3d(st, &tin, &bar[sb], cx0, cy0, z);
+    tma_load_3d(st + S::r_off, &tr, &bar[sb], cx0, cy0 + 2, z);
     tma_load_2d(st + S::c_off, &tcls, &bar[sb], cx0, cy0);
     tma_load_2d(st + S::v_off, &tvol, &bar[sb], cx0, cy0 + 2);
   };
@@ -302,8 +316,8 @@ __global__ void __launch_bounds__(256, 3) k_restrict_p(const __grid_constant__ C
       const int row = A.rr[2 * q], loc = A.rr[2 * q + 1];
       T acc = 0;
 #pragma unroll 15
-      for (int m = 0; m < A.W; ++m) acc += A.val[(long)m * A.n2 + row] * A.u[A.col[(long)m * A.n2 + row]];
-      res[loc >> 6][loc & 63] = A.r[A.irr_cell[row]] - acc;
+      for (int m = 0; m < A.W; ++m) acc += A.val[(long)m * A.n2 + row] * uf[A.col[(long)m * A.n2 + row]];
+      res[loc >> 6][loc & 63] = rf[A.irr_cell[row]] - acc;
     }
     // class bytes of this thread's two coarse cells (0 outside the coarse level)
     uint8_t cc[2];
@@ -368,8 +382,8 @@ __global__ void __launch_bounds__(256, 3) k_restrict_p(const __grid_constant__ C
       const T s = v0 * res[2 * cj][2 * ci] + v1 * res[2 * cj][2 * ci + 1] + v2 * res[2 * cj + 1][2 * ci] +
                   v3 * res[2 * cj + 1][2 * ci + 1];
       const T sv = v0 + v1 + v2 + v3;
-      A.rc[pc] = sv > (T)0 ? (T)4 * s / sv : (T)0;
-      A.uc[pc] = (T)0;
+      rcz[pc] = sv > (T)0 ? (T)4 * s / sv : (T)0;
+      ucz[pc] = (T)0;
     }
     __syncthreads();      // res and stage sb are free
     if (threadIdx.x == 0 && k + 2 < K) {

@@ -46,10 +46,12 @@ struct DevLevel {
   uint32_t smooth_stage[2] = {0, 0};
   size_t smooth_smem[2] = {0, 0};
   int smooth_grid[2] = {0, 0};
+  int smooth_cap[2] = {0, 0};   // resident CTAs of the persistent sweep over the whole GPU
   CUtensorMap tmv64, tmv32;     // 68 x 32 boxes over the cell volumes
   bool restrict_ok[2] = {false, false};  // persistent restriction (k_restrict_p), [0] FP64, [1] FP32
   uint32_t restrict_stage[2] = {0, 0};
   int restrict_grid[2] = {0, 0};
+  int restrict_cap[2] = {0, 0};
   int32_t* rr_off = nullptr;    // per restriction tile: its irregular rows [rr_off[t], rr_off[t + 1])
   int32_t* rr = nullptr;        // (row, y * 64 + x in the tile) pairs
   uint8_t* cls = nullptr;
@@ -151,6 +153,9 @@ struct ccm_handle {
   double* rhat = nullptr;      // level-0 padded FP64 right-hand side (h^2-scaled)
   double* uhat = nullptr;      // level-0 padded FP64 solution
   bool fused_outer = false;    // mixed form: TMA-tiled FP64 residual writing r32 and the norm
+  int B = 1;                   // right-hand sides the FP32 work arrays and level-0 FP64 arrays hold
+  int bmax = 1;                // right-hand sides one graph replay advances (B where batching applies)
+  int nb = 1;                  // right-hand sides of the launches being issued (<= bmax)
   CUtensorMap tm_uhat, tm_rhat;  // 68 x 36 box over uhat, 68 x 32 box over rhat
   dev::SepStencil sep{};       // the regular stencil in factored form
   unsigned long long* dnorm = nullptr;
@@ -181,6 +186,7 @@ struct ccm_handle {
     long long launches = 0;
     std::vector<int> prof_pairs;      // indices into gprof_ev (pairs at 2k, 2k + 1)
     double* u0 = nullptr;             // the level-0 FP64 iterate the graph updates
+    int nb = 1;                       // right-hand sides its launches cover
   } graph[2];
 };
 
@@ -340,7 +346,10 @@ void sweep_persistent(ccm_handle* H, DevLevel& L, cudaStream_t s, DevLevel* C) {
                               : (sizeof(T) == 4 ? CCM_PROF_SMO1_FP32 : CCM_PROF_SMO1_FP64), s);
   const CUtensorMap& tm = TmU<T>(L);
   const CUtensorMap& tr = TmR<T>(L);
-  const int grid = L.smooth_grid[k];
+  a.bs = L.npad;
+  a.bsc = C ? C->npad : 0;
+  // with a batch, fewer CTAs per right-hand side so that the whole launch stays resident
+  const dim3 grid(std::min(L.smooth_grid[k], std::max(1, ceil_div(L.smooth_cap[k], H->nb))), H->nb);
   const size_t smem = L.smooth_smem[k];
   if (C) {
     const CUtensorMap& tu = TmUc<T>(L, *C);
@@ -393,6 +402,8 @@ void sweep_one_launch(ccm_handle* H, DevLevel& L, cudaStream_t s, DevLevel* C = 
   a.err = H->derr;
   a.par = L.ell_par;
   a.uc = C ? U<T>(*C) : nullptr;
+  a.bs = L.npad;
+  a.bsc = C ? C->npad : 0;
   const bool l0 = &L == &H->L[0];
   ProfScope ps(H, !l0 ? 0 : C ? (sizeof(T) == 4 ? CCM_PROF_PROLONG_SMO1_FP32 : 0)
                               : (sizeof(T) == 4 ? CCM_PROF_SMO1_FP32 : CCM_PROF_SMO1_FP64), s);
@@ -405,7 +416,7 @@ void sweep_one_launch(ccm_handle* H, DevLevel& L, cudaStream_t s, DevLevel* C = 
     cudaEventRecord(H->ev_fork, s);
     cudaStreamWaitEvent(H->side, H->ev_fork, 0);
     const size_t bsm = (((size_t)L.max_ext * L.max_core * sizeof(T) + 15) & ~(size_t)15) + L.max_ext * sizeof(T);
-    KL(dev::k_blocks<T><<<b.nblk * b.chunks, 256, bsm, H->side>>>(b));
+    KL(dev::k_blocks<T><<<dim3(b.nblk * b.chunks, H->nb), 256, bsm, H->side>>>(b));
     cudaEventRecord(H->ev_join, H->side);
   }
   const CUtensorMap& tm = TmU<T>(L);
@@ -426,8 +437,8 @@ void sweep_one_launch(ccm_handle* H, DevLevel& L, cudaStream_t s, DevLevel* C = 
         if (H->cross) KL(launch_k(dev::k_sweep<T, true, true>, grid, 256, smem, s, tm, a));
         else KL(launch_k(dev::k_sweep<T, false, true>, grid, 256, smem, s, tm, a));
       } else {
-        if (H->cross) KL(launch_k(dev::k_sweep<T, true, false>, grid, 256, smem, s, tm, a));
-        else KL(launch_k(dev::k_sweep<T, false, false>, grid, 256, smem, s, tm, a));
+        if (H->cross) KL(launch_k(dev::k_sweep<T, true, false>, dim3(grid, H->nb), 256, smem, s, tm, a));
+        else KL(launch_k(dev::k_sweep<T, false, false>, dim3(grid, H->nb), 256, smem, s, tm, a));
       }
     }
   }
@@ -510,12 +521,15 @@ void restrict_to(ccm_handle* H, DevLevel& F, DevLevel& C, cudaStream_t s) {
     A.S = stencil<T>(H);
     A.err = H->derr;
     A.stage = F.restrict_stage[kk];
+    A.bs = F.npad;
+    A.bsc = C.npad;
     const CUtensorMap& tv = kk == 0 ? F.tmv64 : F.tmv32;
     const size_t smem = 2 * (size_t)A.stage;
+    const dim3 rgrid(std::min(F.restrict_grid[kk], std::max(1, ceil_div(F.restrict_cap[kk], H->nb))), H->nb);
     if (H->cross)
-      KL(launch_k(dev::k_restrict_p<T, true>, F.restrict_grid[kk], 256, smem, s, TmU<T>(F), TmR<T>(F), F.tmcls, tv, A));
+      KL(launch_k(dev::k_restrict_p<T, true>, rgrid, 256, smem, s, TmU<T>(F), TmR<T>(F), F.tmcls, tv, A));
     else
-      KL(launch_k(dev::k_restrict_p<T, false>, F.restrict_grid[kk], 256, smem, s, TmU<T>(F), TmR<T>(F), F.tmcls, tv, A));
+      KL(launch_k(dev::k_restrict_p<T, false>, rgrid, 256, smem, s, TmU<T>(F), TmR<T>(F), F.tmcls, tv, A));
     return;
   }
   if (H->par.smoother == 1 && F.tma && F.ntiles64r) {
@@ -533,14 +547,14 @@ void restrict_to(ccm_handle* H, DevLevel& F, DevLevel& C, cudaStream_t s) {
     return;
   }
   if (H->par.smoother == 1) {
-    dim3 blk(32, 8), grd(ceil_div(C.nx, 32), ceil_div(C.ny, 8));
+    dim3 blk(32, 8), grd(ceil_div(C.nx, 32), ceil_div(C.ny, 8), H->nb);
     const auto& S = stencil<T>(H);
     if (H->cross)
       KL(launch_k(dev::k_restrict_rows<T, true>, grd, blk, 0, s, C.nx, C.ny, C.pitch, F.pitch, C.cls, F.cls, Vol<T>(F), F.rowmap,
-                                                         F.n2, F.W, F.ell_col, Ell<T>(F), U<T>(F), R<T>(F), R<T>(C), U<T>(C), S));
+                  F.n2, F.W, F.ell_col, Ell<T>(F), U<T>(F), R<T>(F), R<T>(C), U<T>(C), S, F.npad, C.npad));
     else
       KL(launch_k(dev::k_restrict_rows<T, false>, grd, blk, 0, s, C.nx, C.ny, C.pitch, F.pitch, C.cls, F.cls, Vol<T>(F), F.rowmap,
-                                                          F.n2, F.W, F.ell_col, Ell<T>(F), U<T>(F), R<T>(F), R<T>(C), U<T>(C), S));
+                  F.n2, F.W, F.ell_col, Ell<T>(F), U<T>(F), R<T>(F), R<T>(C), U<T>(C), S, F.npad, C.npad));
     return;
   }
   if (F.n2)
@@ -560,14 +574,16 @@ template <typename T>
 void prolong_from(ccm_handle* H, DevLevel& F, DevLevel& C, cudaStream_t s) {
   if (F.ntiles == 0) return;
   dim3 blk(dev::TX, dev::TY);
-  KL(launch_k(dev::k_prolong<T>, F.ntiles, blk, 0, s, F.tiles, F.cls, F.nx, F.ny, F.pitch, C.pitch, U<T>(C), U<T>(F)));
+  KL(launch_k(dev::k_prolong<T>, dim3(F.ntiles, H->nb), blk, 0, s, F.tiles, F.cls, F.nx, F.ny, F.pitch, C.pitch, U<T>(C),
+              U<T>(F), F.npad, C.npad));
 }
 
 template <typename T>
 void bottom(ccm_handle* H, DevLevel& B, cudaStream_t s) {
   int nw = 8;
   size_t sm = std::max<size_t>(B.nbc, nw * 32) * sizeof(T);
-  KL(launch_k(dev::k_bottom<T>, ceil_div(B.nbc, 32), nw * 32, sm, s, B.nbc, B.bot_cell, Bot<T>(B), R<T>(B), U<T>(B)));
+  KL(launch_k(dev::k_bottom<T>, dim3(ceil_div(B.nbc, 32), H->nb), nw * 32, sm, s, B.nbc, B.bot_cell, Bot<T>(B), R<T>(B),
+              U<T>(B), B.npad));
 }
 
 // the levels from m down to the bottom run as one launch of one thread-block cluster
@@ -662,7 +678,7 @@ void vcycle(ccm_handle* H, int m, cudaStream_t s) {
 
 int read_norm(ccm_handle* H, const uint8_t* cls, long n, const double* x, cudaStream_t s, double& out) {
   CCM_CUDA(cudaMemsetAsync(H->dnorm, 0, sizeof(unsigned long long), s));
-  KL(launch_k(dev::k_absmax<double>, std::min(ceil_div(n, 256), 1216), 256, 0, s, n, cls, x, H->dnorm));
+  KL(launch_k(dev::k_absmax<double>, std::min(ceil_div(n, 256), 1216), 256, 0, s, n, cls, x, H->dnorm, 0L));
   CCM_CUDA(cudaMemcpyAsync(H->hnorm, H->dnorm, sizeof(unsigned long long), cudaMemcpyDeviceToHost, s));
   CCM_CUDA(cudaStreamSynchronize(s));
   unsigned long long bits = *H->hnorm;
@@ -673,19 +689,20 @@ int read_norm(ccm_handle* H, const uint8_t* cls, long n, const double* x, cudaSt
 // mixed form: t = rhat - L uhat on level 0 into the FP32 right-hand side, max |t| into dnorm
 void outer_residual32(ccm_handle* H, cudaStream_t s) {
   DevLevel& L = H->L[0];
-  cudaMemsetAsync(H->dnorm, 0, sizeof(unsigned long long), s);
+  const int nb = H->nb;
+  cudaMemsetAsync(H->dnorm, 0, nb * sizeof(unsigned long long), s);
   {
     ProfScope ps(H, CCM_PROF_RESID_FP64, s);
     if (H->cross)
-      KL(launch_k(dev::k_resid64<true>, L.ntiles64, 256, dev::Resid64Smem::bytes(true), s, H->tm_uhat, H->tm_rhat, L.tmcls, L.tiles64, L.nx, L.pitch,
-                  L.r32, H->dnorm, H->sep, H->derr));
+      KL(launch_k(dev::k_resid64<true>, dim3(L.ntiles64, nb), 256, dev::Resid64Smem::bytes(true), s, H->tm_uhat, H->tm_rhat,
+                  L.tmcls, L.tiles64, L.nx, L.pitch, L.r32, H->dnorm, H->sep, H->derr, L.npad));
     else
-      KL(launch_k(dev::k_resid64<false>, L.ntiles64, 256, dev::Resid64Smem::bytes(false), s, H->tm_uhat, H->tm_rhat, L.tmcls, L.tiles64, L.nx, L.pitch,
-                  L.r32, H->dnorm, H->sep, H->derr));
+      KL(launch_k(dev::k_resid64<false>, dim3(L.ntiles64, nb), 256, dev::Resid64Smem::bytes(false), s, H->tm_uhat, H->tm_rhat,
+                  L.tmcls, L.tiles64, L.nx, L.pitch, L.r32, H->dnorm, H->sep, H->derr, L.npad));
   }
   if (L.n2)
-    KL(launch_k(dev::k_rows_r32, ceil_div(L.n2, 128), 128, 0, s, L.n2, L.W, L.irr_cell, L.ell_col, L.ell64,
-                (const double*)H->uhat, (const double*)H->rhat, L.r32, H->dnorm));
+    KL(launch_k(dev::k_rows_r32, dim3(ceil_div(L.n2, 128), nb), 128, 0, s, L.n2, L.W, L.irr_cell, L.ell_col, L.ell64,
+                (const double*)H->uhat, (const double*)H->rhat, L.r32, H->dnorm, L.npad));
 }
 
 int check_level(ccm_handle* h, int level) {
@@ -703,8 +720,11 @@ void load_level(ccm_handle* h, DevLevel& L, const double* u, const double* r, cu
   if (r) KL(dev::k_pack<T, double><<<pg, 128, 0, s>>>(L.nx, L.ny, L.pitch, L.cls, r, R<T>(L), L.h * L.h));
 }
 
-// 2-D tensor map over a padded level array (pitch x rows elements), zero fill outside
-bool make_tmap(CUtensorMap* map, void* base, int pitch, int rows, CUtensorMapDataType dt, size_t es, int bx, int by) {
+// tensor map over a padded level array (pitch x rows elements), zero fill outside; with
+// depth > 0 it is 3-D over `depth` such arrays one after the other (the right-hand sides of
+// a batch), box depth 1
+bool make_tmap(CUtensorMap* map, void* base, int pitch, int rows, CUtensorMapDataType dt, size_t es, int bx, int by,
+               int depth = 0) {
   static PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
   if (!encode) {
     void* fn = nullptr;
@@ -714,19 +734,20 @@ bool make_tmap(CUtensorMap* map, void* base, int pitch, int rows, CUtensorMapDat
       return false;
     encode = (PFN_cuTensorMapEncodeTiled_v12000)fn;
   }
-  cuuint64_t dims[2] = {(cuuint64_t)pitch, (cuuint64_t)rows};
-  cuuint64_t strides[1] = {(cuuint64_t)pitch * es};
-  cuuint32_t box[2] = {(cuuint32_t)bx, (cuuint32_t)by};
-  cuuint32_t estr[2] = {1, 1};
-  CUresult r = encode(map, dt, 2, base, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+  const cuuint32_t rank = depth > 0 ? 3 : 2;
+  cuuint64_t dims[3] = {(cuuint64_t)pitch, (cuuint64_t)rows, (cuuint64_t)std::max(depth, 1)};
+  cuuint64_t strides[2] = {(cuuint64_t)pitch * es, (cuuint64_t)pitch * rows * es};
+  cuuint32_t box[3] = {(cuuint32_t)bx, (cuuint32_t)by, 1};
+  cuuint32_t estr[3] = {1, 1, 1};
+  CUresult r = encode(map, dt, rank, base, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
                       CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   return r == CUDA_SUCCESS;
 }
 
-// the 68 x 36 halo tile box of the SMO-1 and restriction kernels
-bool make_tmap(CUtensorMap* map, void* base, int pitch, int rows, bool fp64) {
+// the 68 x 36 halo tile box of the smoothing and restriction kernels, over `depth` arrays
+bool make_tmap(CUtensorMap* map, void* base, int pitch, int rows, bool fp64, int depth) {
   return make_tmap(map, base, pitch, rows, fp64 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT64 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32,
-                   fp64 ? 8 : 4, dev::HX, dev::HY);
+                   fp64 ? 8 : 4, dev::HX, dev::HY, depth);
 }
 
 // Device copies of a host hierarchy (every level's arrays, work space, tensor maps, streams)
@@ -820,21 +841,22 @@ int upload_hierarchy(ccm_handle* h) {
     d.u64[1] = A.alloc<double>(d.npad);
     d.r64 = A.alloc<double>(d.npad);
     d.t64 = A.alloc<double>(d.npad);
-    d.u32[0] = A.alloc<float>(d.npad);
-    d.u32[1] = A.alloc<float>(d.npad);
-    d.r32 = A.alloc<float>(d.npad);
+    // the FP32 iterates and right-hand sides hold B right-hand sides one after the other
+    d.u32[0] = A.alloc<float>(h->B * d.npad);
+    d.u32[1] = A.alloc<float>(h->B * d.npad);
+    d.r32 = A.alloc<float>(h->B * d.npad);
     d.t32 = A.alloc<float>(d.npad);
     // TMA-staged smoothing on the large levels (base addresses come from cudaMalloc, so
     // they are 256-byte aligned; the pitch is a multiple of 32 elements)
     d.tma = A.err == cudaSuccess && d.ntiles64 > 0 && d.nx >= 64;
     for (int b = 0; b < 2 && d.tma; ++b)
-      d.tma = make_tmap(&d.tm64[b], d.u64[b], d.pitch, d.rows, true) &&
-              make_tmap(&d.tm32[b], d.u32[b], d.pitch, d.rows, false);
+      d.tma = make_tmap(&d.tm64[b], d.u64[b], d.pitch, d.rows, true, 1) &&
+              make_tmap(&d.tm32[b], d.u32[b], d.pitch, d.rows, false, h->B);
     d.tma = d.tma && make_tmap(&d.tmcls, d.cls, d.pitch, d.rows, CU_TENSOR_MAP_DATA_TYPE_UINT8, 1, dev::CLX, dev::HY) &&
             make_tmap(&d.tmv64, d.vol64, d.pitch, d.rows, CU_TENSOR_MAP_DATA_TYPE_FLOAT64, 8, dev::HX, dev::JY) &&
             make_tmap(&d.tmv32, d.vol32, d.pitch, d.rows, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, dev::HX, dev::JY) &&
-            make_tmap(&d.tmr64, d.r64, d.pitch, d.rows, CU_TENSOR_MAP_DATA_TYPE_FLOAT64, 8, dev::HX, dev::JY) &&
-            make_tmap(&d.tmr32, d.r32, d.pitch, d.rows, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, dev::HX, dev::JY);
+            make_tmap(&d.tmr64, d.r64, d.pitch, d.rows, CU_TENSOR_MAP_DATA_TYPE_FLOAT64, 8, dev::HX, dev::JY, 1) &&
+            make_tmap(&d.tmr32, d.r32, d.pitch, d.rows, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, dev::HX, dev::JY, h->B);
   }
   // SMO-2 blocks that fit in shared memory run as a bulk-staged kernel beside the sweep
   if (cudaStreamCreateWithFlags(&h->side, cudaStreamNonBlocking) != cudaSuccess ||
@@ -882,6 +904,7 @@ int upload_hierarchy(ccm_handle* h) {
       d.smooth_stage[k] = (uint32_t)stage;
       d.smooth_smem[k] = smem;
       d.smooth_grid[k] = std::min(nitems, nsm * occ);
+      d.smooth_cap[k] = nsm * occ;
     }
     cudaGetLastError();
     // parents of the fitted rows' regular columns (the prolongation read by SMO-2 residuals)
@@ -940,8 +963,9 @@ int upload_hierarchy(ccm_handle* h) {
       DevLevel& c = h->L[m + 1];
       d.tma_pro = true;
       for (int b = 0; b < 2 && d.tma_pro; ++b)
-        d.tma_pro = make_tmap(&d.tmuc64[b], c.u64[b], c.pitch, c.rows, CU_TENSOR_MAP_DATA_TYPE_FLOAT64, 8, dev::UCX, dev::UCY) &&
-                    make_tmap(&d.tmuc32[b], c.u32[b], c.pitch, c.rows, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, dev::UCX, dev::UCY);
+        d.tma_pro = make_tmap(&d.tmuc64[b], c.u64[b], c.pitch, c.rows, CU_TENSOR_MAP_DATA_TYPE_FLOAT64, 8, dev::UCX, dev::UCY, 1) &&
+                    make_tmap(&d.tmuc32[b], c.u32[b], c.pitch, c.rows, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, dev::UCX, dev::UCY,
+                              h->B);
       // the persistent restriction: two stages of u, r, class bytes and volumes per tile
       for (int k = 0; k < 2 && d.ntiles64r > 0; ++k) {
         const uint32_t stage = k == 0 ? dev::RestrictStage<double>::bytes : dev::RestrictStage<float>::bytes;
@@ -960,6 +984,7 @@ int upload_hierarchy(ccm_handle* h) {
         d.restrict_ok[k] = true;
         d.restrict_stage[k] = stage;
         d.restrict_grid[k] = std::min(d.ntiles64r, nsm * occ);
+        d.restrict_cap[k] = nsm * occ;
       }
       cudaGetLastError();
     }
@@ -985,8 +1010,8 @@ int upload_hierarchy(ccm_handle* h) {
       if (h->coarse_ctas > 0) h->coarse_first = first;
     }
   }
-  h->rhat = A.alloc<double>(h->L[0].npad);
-  h->uhat = A.alloc<double>(h->L[0].npad);
+  h->rhat = A.alloc<double>(h->B * h->L[0].npad);
+  h->uhat = A.alloc<double>(h->B * h->L[0].npad);
   {
     static const double lap[5] = {-1.0, 16.0, -30.0, 16.0, -1.0};
     static const double grad[5] = {1.0, -8.0, 0.0, 8.0, -1.0};
@@ -1001,16 +1026,17 @@ int upload_hierarchy(ccm_handle* h) {
     cudaFuncSetAttribute(dev::k_resid64<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, dev::Resid64Smem::bytes(true));
     cudaFuncSetAttribute(dev::k_resid64<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, dev::Resid64Smem::bytes(false));
     h->fused_outer = A.err == cudaSuccess && d0.tma && d0.ntiles64 > 0 &&
-                     make_tmap(&h->tm_uhat, h->uhat, d0.pitch, d0.rows, true) &&
-                     make_tmap(&h->tm_rhat, h->rhat, d0.pitch, d0.rows, CU_TENSOR_MAP_DATA_TYPE_FLOAT64, 8, dev::HX, dev::JY);
+                     make_tmap(&h->tm_uhat, h->uhat, d0.pitch, d0.rows, true, h->B) &&
+                     make_tmap(&h->tm_rhat, h->rhat, d0.pitch, d0.rows, CU_TENSOR_MAP_DATA_TYPE_FLOAT64, 8, dev::HX, dev::JY,
+                               h->B);
   }
-  h->dnorm = A.alloc<unsigned long long>(1);
+  h->dnorm = A.alloc<unsigned long long>(h->B);
   h->derr = A.alloc<int>(1);
   if (A.err != cudaSuccess) {
     A.release();
     return A.err == cudaErrorMemoryAllocation ? CCM_ENOMEM : CCM_ECUDA;
   }
-  if (cudaMallocHost(&h->hnorm, sizeof(unsigned long long)) != cudaSuccess ||
+  if (cudaMallocHost(&h->hnorm, h->B * sizeof(unsigned long long)) != cudaSuccess ||
       cudaMallocHost(&h->herr, sizeof(int)) != cudaSuccess) {
     A.release();
     return CCM_ECUDA;
@@ -1046,6 +1072,7 @@ int ccm_default_params(ccm_params* p) {
   p->inner_cycles = 3;
   p->smoother = 1;
   p->coarse_n = 0;
+  p->batch = 1;
   return CCM_OK;
 }
 
@@ -1085,11 +1112,13 @@ int ccm_setup(const ccm_problem* prob, const ccm_params* params, ccm_handle** ou
   if (par.nu1 < 0 || par.nu2 < 0 || par.coarsest < 4 || par.ras_passes < 0 || par.ras_block < 8 ||
       par.ras_block > 128 || par.ras_overlap < 0 || par.ras_overlap > 64 || par.max_iter < 0 ||
       par.ras_exact < 0 || par.ras_exact > 6000 || par.inner_cycles < 1 || par.inner_cycles > 16 || par.smoother < 0 || par.smoother > 1 || par.coarse_n < 0 ||
+      par.batch < 1 || par.batch > 4096 ||
       !(par.theta >= 0 && par.theta < 1) || (par.precision != CCM_FP64 && par.precision != CCM_MIXED))
     return CCM_EINVAL;
   auto t0 = std::chrono::steady_clock::now();
   std::unique_ptr<ccm_handle> h(new ccm_handle());
   h->par = par;
+  h->B = par.precision == CCM_MIXED ? par.batch : 1;
   h->a = prob->a;
   h->b = prob->b;
   h->c = prob->c;
@@ -1122,6 +1151,21 @@ int ccm_setup(const ccm_problem* prob, const ccm_params* params, ccm_handle** ou
   I.n_segments = h->H.nseg;
   I.device_bytes = A.bytes;
   I.plg_cond_max = h->H.cond_max;
+  // batching needs every launch of an outer iteration to take its right-hand side from the
+  // grid: the persistent sweep and restriction on every TMA level, the fused outer residual,
+  // the block-Jacobi smoother and no cluster cycle
+  {
+    bool ok = h->B > 1 && h->fused_outer && h->persistent && par.smoother == 1 && par.ras_passes <= 1 &&
+              h->coarse_first >= nl;
+    for (int m = 0; m < nl && ok; ++m) {
+      const DevLevel& d = h->L[m];
+      if (!d.tma) continue;
+      if (d.nblk + d.ntiles64 > 0 && !d.smooth_ok[1]) ok = false;
+      if (m + 1 < nl && d.ntiles64r > 0 && !d.restrict_ok[1]) ok = false;
+    }
+    h->bmax = ok ? h->B : 1;
+    I.batch = h->bmax;
+  }
   I.setup_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
   *out = h.release();
   return CCM_OK;
@@ -1309,16 +1353,16 @@ static void iteration_body(ccm_handle* h, bool fp64, cudaStream_t s) {
     ucur = start;
   } else if (h->fused_outer) {
     // r32 holds the FP32 image of the residual (previous iteration or the initial one)
-    cudaMemsetAsync(L.u32[L.cur32], 0, np * sizeof(float), s);
+    cudaMemsetAsync(L.u32[L.cur32], 0, h->nb * np * sizeof(float), s);
     for (int c = 0; c < std::max(1, h->par.inner_cycles); ++c) {
       ProfScope ps(h, CCM_PROF_VCYCLE, s);
       vcycle<float>(h, 0, s);
     }
     dim3 blk(dev::TX, dev::TY);
-    KL(launch_k(dev::k_axpy_tiles, L.ntiles, blk, 0, s, L.tiles, L.cls, L.nx, L.ny, L.pitch,
-                (const float*)L.u32[L.cur32], h->uhat));
+    KL(launch_k(dev::k_axpy_tiles, dim3(L.ntiles, h->nb), blk, 0, s, L.tiles, L.cls, L.nx, L.ny, L.pitch,
+                (const float*)L.u32[L.cur32], h->uhat, L.npad));
     outer_residual32(h, s);
-    cudaMemcpyAsync(h->hnorm, h->dnorm, sizeof(unsigned long long), cudaMemcpyDeviceToHost, s);
+    cudaMemcpyAsync(h->hnorm, h->dnorm, h->nb * sizeof(unsigned long long), cudaMemcpyDeviceToHost, s);
     cudaMemcpyAsync(h->herr, h->derr, sizeof(int), cudaMemcpyDeviceToHost, s);
     return;
   } else {
@@ -1339,14 +1383,20 @@ static void iteration_body(ccm_handle* h, bool fp64, cudaStream_t s) {
     KL(launch_k(dev::k_rows<double, double, true, true>, ceil_div(L.n2, 128), 128, 0, s, 
         L.n2, L.W, L.irr_cell, L.ell_col, L.ell64, ucur, h->rhat, L.t64, nullptr, nullptr, nullptr));
   cudaMemsetAsync(h->dnorm, 0, sizeof(unsigned long long), s);
-  KL(launch_k(dev::k_absmax<double>, std::min(ceil_div(np, 256), 1216), 256, 0, s, np, L.cls, L.t64, h->dnorm));
+  KL(launch_k(dev::k_absmax<double>, std::min(ceil_div(np, 256), 1216), 256, 0, s, np, L.cls, L.t64, h->dnorm, 0L));
   cudaMemcpyAsync(h->hnorm, h->dnorm, sizeof(unsigned long long), cudaMemcpyDeviceToHost, s);
   cudaMemcpyAsync(h->herr, h->derr, sizeof(int), cudaMemcpyDeviceToHost, s);
 }
 
 static int capture_iteration(ccm_handle* h, bool fp64, cudaStream_t user) {
   ccm_handle::Graph& G = h->graph[fp64 ? 1 : 0];
-  if (G.exec) return CCM_OK;
+  if (G.exec && G.nb == h->nb) return CCM_OK;
+  if (G.exec) {        // captured for another batch size
+    CCM_CUDA(cudaStreamSynchronize(user));
+    cudaGraphExecDestroy(G.exec);
+    G.exec = nullptr;
+    G.prof_pairs.clear();
+  }
   if (!h->cap_stream) CCM_CUDA(cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking));
   CCM_CUDA(cudaStreamSynchronize(user));
   cudaStream_t s = h->cap_stream;
@@ -1374,6 +1424,7 @@ static int capture_iteration(ccm_handle* h, bool fp64, cudaStream_t user) {
   }
   h->L[0].cur64 = cur64;
   G.u0 = fp64 ? h->L[0].u64[cur64] : h->uhat;
+  G.nb = h->nb;
   return CCM_OK;
 }
 
@@ -1395,51 +1446,76 @@ int ccm_solve(ccm_handle* h, const double* f, const double* g, double* u, int nr
   const double h2 = L.h * L.h;
   dim3 pg(ceil_div(L.nx, 128), L.ny);
   const bool fp64 = h->par.precision == CCM_FP64;
+  const int bmax = fp64 ? 1 : h->bmax;
   int result = CCM_OK;
-  int rc = capture_iteration(h, fp64, s);
-  if (rc) return rc;
-  ccm_handle::Graph& G = h->graph[fp64 ? 1 : 0];
-  for (int k = 0; k < nrhs; ++k) {
-    // r_hat = h^2 (f - N g); u_hat = initial guess
-    CCM_CUDA(cudaMemsetAsync(h->rhat, 0, np * sizeof(double), s));
-    KL(dev::k_pack<double, double><<<pg, 128, 0, s>>>(L.nx, L.ny, L.pitch, L.cls, f + k * nu, h->rhat, h2));
-    if (g && L.n2)
-      KL(dev::k_sub_boundary<<<ceil_div(L.n2, 128), 128, 0, s>>>(L.n2, L.irr_cell, L.nb, L.seg,
-                                                             g + (long)k * h->info.n_segments, h->rhat));
+  std::vector<double> rnorm(bmax), rel(bmax);
+  // right-hand sides [k0, k0 + nb) advance together, in slot b of every batched array
+  for (int k0 = 0; k0 < nrhs; k0 += bmax) {
+    const int nb = std::min(bmax, nrhs - k0);
+    h->nb = nb;
+    int rc = capture_iteration(h, fp64, s);
+    if (rc) {
+      h->nb = 1;
+      return rc;
+    }
+    ccm_handle::Graph& G = h->graph[fp64 ? 1 : 0];
     double* U0 = G.u0;
-    CCM_CUDA(cudaMemsetAsync(U0, 0, np * sizeof(double), s));
-    KL(dev::k_pack<double, double><<<pg, 128, 0, s>>>(L.nx, L.ny, L.pitch, L.cls, u + k * nu, U0, 1.0));
+    // r_hat = h^2 (f - N g); u_hat = initial guess
+    CCM_CUDA(cudaMemsetAsync(h->rhat, 0, nb * np * sizeof(double), s));
+    CCM_CUDA(cudaMemsetAsync(U0, 0, nb * np * sizeof(double), s));
+    for (int b = 0; b < nb; ++b) {
+      const long k = k0 + b;
+      KL(dev::k_pack<double, double><<<pg, 128, 0, s>>>(L.nx, L.ny, L.pitch, L.cls, f + k * nu, h->rhat + b * np, h2));
+      if (g && L.n2)
+        KL(dev::k_sub_boundary<<<ceil_div(L.n2, 128), 128, 0, s>>>(L.n2, L.irr_cell, L.nb, L.seg,
+                                                               g + k * h->info.n_segments, h->rhat + b * np));
+      KL(dev::k_pack<double, double><<<pg, 128, 0, s>>>(L.nx, L.ny, L.pitch, L.cls, u + k * nu, U0 + b * np, 1.0));
+    }
     if (fp64) CCM_CUDA(cudaMemcpyAsync(L.r64, h->rhat, np * sizeof(double), cudaMemcpyDeviceToDevice, s));
-    double rnorm = 0, rel = 0;
-    rc = read_norm(h, L.cls, np, h->rhat, s, rnorm);
-    if (rc) return rc;
-    if (rnorm == 0) rnorm = 1;
+    // ||r_hat|| of every right-hand side
+    CCM_CUDA(cudaMemsetAsync(h->dnorm, 0, nb * sizeof(unsigned long long), s));
+    KL(launch_k(dev::k_absmax<double>, dim3(std::min(ceil_div(np, 256), 1216), nb), 256, 0, s, np, L.cls,
+                (const double*)h->rhat, h->dnorm, np));
+    CCM_CUDA(cudaMemcpyAsync(h->hnorm, h->dnorm, nb * sizeof(unsigned long long), cudaMemcpyDeviceToHost, s));
+    CCM_CUDA(cudaStreamSynchronize(s));
+    for (int b = 0; b < nb; ++b) {
+      std::memcpy(&rnorm[b], &h->hnorm[b], sizeof(double));
+      if (rnorm[b] == 0) rnorm[b] = 1;
+    }
     // initial residual
     if (!fp64 && h->fused_outer) {
       outer_residual32(h, s);
-      CCM_CUDA(cudaMemcpyAsync(h->hnorm, h->dnorm, sizeof(unsigned long long), cudaMemcpyDeviceToHost, s));
+      CCM_CUDA(cudaMemcpyAsync(h->hnorm, h->dnorm, nb * sizeof(unsigned long long), cudaMemcpyDeviceToHost, s));
       CCM_CUDA(cudaStreamSynchronize(s));
-      unsigned long long bits = *h->hnorm;
-      std::memcpy(&rel, &bits, sizeof(double));
+      for (int b = 0; b < nb; ++b) std::memcpy(&rel[b], &h->hnorm[b], sizeof(double));
     } else {
       launch_regular<double>(h, L, U0, h->rhat, L.t64, true, s);
       if (L.n2)
-        KL(launch_k(dev::k_rows<double, double, true, true>, ceil_div(L.n2, 128), 128, 0, s, 
+        KL(launch_k(dev::k_rows<double, double, true, true>, ceil_div(L.n2, 128), 128, 0, s,
             L.n2, L.W, L.irr_cell, L.ell_col, L.ell64, U0, h->rhat, L.t64, nullptr, nullptr, nullptr));
-      rc = read_norm(h, L.cls, np, L.t64, s, rel);
+      rc = read_norm(h, L.cls, np, L.t64, s, rel[0]);
       if (rc) return rc;
     }
-    rel /= rnorm;
+    // the worst right-hand side of the group decides; stats report it
+    auto worst = [&]() {
+      double w = 0;
+      for (int b = 0; b < nb; ++b) {
+        const double r = rel[b] / rnorm[b];
+        if (!std::isfinite(r)) return r;
+        w = std::max(w, r);
+      }
+      return w;
+    };
+    double wr = worst();
     ccm_stats local{};
-    local.history[0] = rel;
+    local.history[0] = wr;
     int it = 0;
-    while (std::isfinite(rel) && rel > h->par.rtol && it < h->par.max_iter) {
+    while (std::isfinite(wr) && wr > h->par.rtol && it < h->par.max_iter) {
       CCM_CUDA(cudaGraphLaunch(G.exec, s));
       g_launches.fetch_add(G.launches);
       CCM_CUDA(cudaStreamSynchronize(s));
-      unsigned long long bits = *h->hnorm;
-      std::memcpy(&rel, &bits, sizeof(double));
-      rel /= rnorm;
+      for (int b = 0; b < nb; ++b) std::memcpy(&rel[b], &h->hnorm[b], sizeof(double));
+      wr = worst();
       ++it;
       if (*h->herr) {
         result = CCM_ETIMEOUT;
@@ -1447,7 +1523,7 @@ int ccm_solve(ccm_handle* h, const double* f, const double* g, double* u, int nr
         cudaMemsetAsync(h->derr, 0, sizeof(int), s);
         break;
       }
-      if (it < 64) local.history[it] = rel;
+      if (it < 64) local.history[it] = wr;
       for (int p : G.prof_pairs) {
         float t = 0;
         if (cudaEventElapsedTime(&t, h->gprof_ev[p], h->gprof_ev[p + 1]) == cudaSuccess) {
@@ -1457,13 +1533,16 @@ int ccm_solve(ccm_handle* h, const double* f, const double* g, double* u, int nr
       }
     }
     if (result == CCM_ETIMEOUT) {
-    } else if (!std::isfinite(rel)) result = CCM_ENOTFINITE;
-    else if (rel > h->par.rtol) result = CCM_ENOCONV;
-    KL(dev::k_unpack<double><<<pg, 128, 0, s>>>(L.nx, L.ny, L.pitch, L.cls, U0, u + k * nu, 1.0));
+    } else if (!std::isfinite(wr)) result = CCM_ENOTFINITE;
+    else if (wr > h->par.rtol && result == CCM_OK) result = CCM_ENOCONV;
+    for (int b = 0; b < nb; ++b)
+      KL(dev::k_unpack<double><<<pg, 128, 0, s>>>(L.nx, L.ny, L.pitch, L.cls, U0 + b * np, u + (k0 + b) * nu, 1.0));
     local.iterations = it;
-    local.rel_residual = rel;
+    local.rel_residual = wr;
     if (st) *st = local;
+    if (result == CCM_ETIMEOUT) break;
   }
+  h->nb = 1;
   CCM_CUDA(cudaGetLastError());
   return result;
 }
