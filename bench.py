@@ -77,6 +77,8 @@ def parse():
     ap.add_argument("--sample-n", type=int, default=256)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64", action="store_true")
+    ap.add_argument("--no-batched", action="store_true",
+                    help="skip the many-right-hand-side workload (disk 512^2, 256 right-hand sides)")
     ap.add_argument("--profile-run", action="store_true",
                     help="only setup, warm-up and the timed solves (for an ncu launch list)")
     return ap.parse_args()
@@ -185,6 +187,48 @@ def run_reference(args, rank: int):
 
 
 # ------------------------------------------------------------------ GPU leg
+
+def batched_workload(stream, flush, nrhs=256, n=512, one_sample=16):
+    """Many right-hand sides on one geometry: the disk domain at n^2, nrhs smoothed N(0,1)
+    right-hand sides, homogeneous Dirichlet data, mixed precision to rel. residual 1e-10.
+    Timed with all right-hand sides advanced together (ccm_params.batch = nrhs) and, for
+    comparison, one at a time on a sample of them."""
+    import torch
+    import paper_2504_00724_gb300 as P
+    import workloads as W
+    prob = W.disk_minus(n)
+    sv = P.Solver(prob, rtol=RTOL, batch=nrhs)
+    mask = sv.cell_map()[0] != 0
+    F = torch.tensor(W.smoothed_normal_rhs(n, nrhs, mask, seed=0), device="cuda")
+    ncell = int(sv.info.n_cells)
+
+    def timed(solver, f, reps):
+        per = []
+        for _ in range(reps):
+            flush.zero_()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            u, st = solver.solve(f, None, stream=stream)
+            e1.record(stream)
+            e1.synchronize()
+            per.append(e0.elapsed_time(e1))
+        return float(np.median(per)), st
+
+    solver_batch = sv.info.batch
+    sv.solve(F, None, stream=stream)                       # captures the batched graph
+    ms, st = timed(sv, F, 3)
+    sv.close()
+    one = P.Solver(prob, rtol=RTOL)
+    one.solve(F[:1], None, stream=stream)
+    ms1, st1 = timed(one, F[:one_sample], 2)
+    one.close()
+    return {"workload": f"Poisson on [0,1]^2 minus the disk r=0.2, {n}x{n} cells, homogeneous Dirichlet, "
+                        f"{nrhs} right-hand sides (N(0,1) cell values, 3 smoothing sweeps, seed 0)",
+            "value": nrhs * ncell / (ms / 1000.0), "unit": UNIT, "ms_per_solve": ms, "batch": solver_batch,
+            "iterations": st.iterations, "rel_residual": st.rel_residual,
+            "one_at_a_time": {"value": one_sample * ncell / (ms1 / 1000.0), "ms": ms1,
+                              "sample": f"{one_sample} of the right-hand sides, batch 1"}}
+
 
 def main():
     args = parse()
@@ -301,6 +345,10 @@ def main():
                 "iterations": st64.iterations, "rel_residual": st64.rel_residual, "max_error": err64}
         s64.close()
 
+    batched = None
+    if not args.no_batched and world == 1:
+        batched = batched_workload(stream, flush)
+
     # roofline of the dominant kernel class (largest total time per step)
     hbm, sm_max, src = peaks()
     clk = clocks.summary()
@@ -357,6 +405,7 @@ def main():
             "iterations": iters, "rel_residual": st.rel_residual, "max_error_vs_exact": err,
             "vcycle_ms": (vc_ms / vc_n) if vc_n else None, "setup_s": setup_s,
             "fp64": fp64, "mixed_over_fp64": (value / world / fp64["value"]) if fp64 else None,
+            "batched": batched,
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(fh.numel() * 8 + gh.numel() * 8),
                     "d2h_bytes_per_step": int(uh.numel() * 8), "ms_per_step": float(np.mean(e2e))},
             "gpu_launches": int(launches), "roofline": roof, "cpu_baseline": cpu, "clocks": clk}
