@@ -187,6 +187,36 @@ def vcycle(H: Hierarchy, m: int, u: np.ndarray, r: np.ndarray, omega=0.5, nu1=3,
     return u
 
 
+def fmg(H: Hierarchy, r: np.ndarray, omega=0.5, nu1=3, nu2=3) -> np.ndarray:
+    """One FMG cycle (Sec. 4, the FMG figure) for L^(0) u = r from a zero guess: the right-hand
+    side is restricted down to the bottom level and solved there; then on every finer level
+    the coarse solution, prolonged, is the initial guess of one V-cycle (Alg. 2)."""
+    M = len(H.levels) - 1
+    rs = [r]
+    for m in range(M):
+        rs.append(restrict(H.levels[m], H.levels[m + 1], rs[m]))
+    u = bottom(H, rs[M])
+    for m in range(M - 1, -1, -1):
+        u = vcycle(H, m, prolong(H.levels[m], H.levels[m + 1], u), rs[m], omega, nu1, nu2)
+    return u
+
+
+def fmg_solve(H: Hierarchy, r: np.ndarray, rtol=1e-10, max_iter=100, omega=0.5, nu1=3, nu2=3,
+              history: Optional[list] = None) -> np.ndarray:
+    """FMG cycles iterated on the residual equation (the paper's "FMG cycle iterations"):
+    u <- u + FMG(r - L u), from u = 0, until the relative residual is <= rtol."""
+    lv = H.levels[0]
+    u = np.zeros_like(r)
+    for it in range(max_iter + 1):
+        rr = rel_residual(lv, u, r)
+        if history is not None:
+            history.append(rr)
+        if rr <= rtol or it == max_iter:
+            return u
+        u = u + fmg(H, residual(lv, u, r), omega, nu1, nu2)
+    return u
+
+
 def rel_residual(lv: Level, u, r) -> float:
     return float(np.abs(residual(lv, u, r)).max() / np.abs(r[lv.ne]).max())
 
