@@ -102,6 +102,10 @@ typedef struct {
                         grid's y index).  Needs the persistent kernels on every level of
                         64^2 cells or more, the block-Jacobi smoother and coarse_n 0; else
                         the handle runs one right-hand side at a time (ccm_info.batch). */
+  int cycle;         /* CCM_MIXED: 0, every inner cycle of an outer iteration is a V-cycle
+                        (Alg. 2); 1, the first one is an FMG cycle (Sec. 4, the FMG figure:
+                        the residual restricted to the bottom level, then one V-cycle per
+                        level from the prolonged coarse solution) and the others V-cycles. */
 } ccm_params;
 
 typedef struct {
@@ -127,7 +131,7 @@ typedef struct ccm_handle ccm_handle;
 
 /* Fill p with the defaults: omega 0.7, nu1 = nu2 = 3, theta 0.3, coarsest 16, CCM_MIXED,
  * rtol 1e-10, max_iter 100, ras_passes 1, ras_block 64, ras_overlap 32, nthreads 0,
- * ras_exact 0, inner_cycles 3, smoother 1, coarse_n 0, batch 1. */
+ * ras_exact 0, inner_cycles 3, smoother 1, coarse_n 0, batch 1, cycle 0. */
 int ccm_default_params(ccm_params* p);
 
 /* Host setup (Sec. 3.1 - 3.4, Sec. 4): cut cells and moments (Green's formula, Sec. 2.4),
@@ -240,6 +244,13 @@ int ccm_level_prolong(ccm_handle* h, int level, const double* uc, double* u, voi
 int ccm_bottom_solve(ccm_handle* h, const double* r, double* u, void* stream);
 /* One V-cycle (Alg. 2) on level 0 for L u = r (physical units, FP64 in and out). */
 int ccm_vcycle(ccm_handle* h, double* u, const double* r, int precision, void* stream);
+
+/* One FMG cycle (Sec. 4, the FMG figure) for L u = r on the finest level, from the zero guess:
+ * r restricted level by level to the bottom level and solved there, then one V-cycle (Alg. 2)
+ * per finer level whose initial guess is the prolonged coarse solution.  r: device [ny][nx]
+ * (unscaled), u: device [ny][nx], output only.  precision CCM_FP64 or CCM_MIXED (FP32 cycle).
+ * Errors: CCM_EINVAL, CCM_ECUDA. */
+int ccm_fmg(ccm_handle* h, double* u, const double* r, int precision, void* stream);
 
 /* ---- accounting and profiling (not part of the method).
  * ccm_launch_count: kernels launched by this library in this process so far (all handles).

@@ -42,7 +42,8 @@ class ccm_params(ctypes.Structure):
                 ("rtol", ctypes.c_double), ("max_iter", ctypes.c_int), ("ras_passes", ctypes.c_int),
                 ("ras_block", ctypes.c_int), ("ras_overlap", ctypes.c_int), ("nthreads", ctypes.c_int),
                 ("ras_exact", ctypes.c_int), ("inner_cycles", ctypes.c_int), ("smoother", ctypes.c_int),
-                ("coarse_n", ctypes.c_int), ("batch", ctypes.c_int)]
+                ("coarse_n", ctypes.c_int), ("batch", ctypes.c_int),
+                ("cycle", ctypes.c_int)]
 
 
 class ccm_info(ctypes.Structure):
@@ -81,6 +82,7 @@ _SIGS = {
     "ccm_level_prolong": (I, [P, I, P, P, P]),
     "ccm_bottom_solve": (I, [P, P, P, P]),
     "ccm_vcycle": (I, [P, P, P, I, P]),
+    "ccm_fmg": (I, [P, P, P, I, P]),
     "ccm_free": (None, [P]),
     "ccm_strerror": (ctypes.c_char_p, [I]),
     "ccm_host_build": (I, [ctypes.POINTER(ccm_problem), ctypes.POINTER(ccm_params), ctypes.POINTER(P)]),
@@ -297,6 +299,13 @@ class Solver:
     def vcycle(self, u, r, precision=CCM_FP64, stream=None):
         u = u.clone()
         _check(lib().ccm_vcycle(self.h, _ptr(u), _ptr(r), precision, _stream(stream)), "ccm_vcycle")
+        return u
+
+    def fmg(self, r, precision=CCM_FP64, stream=None):
+        """One FMG cycle for L u = r from the zero guess (ccm_fmg)."""
+        import torch
+        u = torch.zeros_like(r)
+        _check(lib().ccm_fmg(self.h, _ptr(u), _ptr(r), precision, _stream(stream)), "ccm_fmg")
         return u
 
     # ---- accounting

@@ -653,19 +653,26 @@ int coarse_cluster_ctas(size_t smem) {
 
 // Alg. 2 from level m: solves L^(m) u = r^(m) approximately, u = U<T>(level m)
 template <typename T>
-void vcycle(ccm_handle* H, int m, cudaStream_t s) {
+void vcycle(ccm_handle* H, int m, cudaStream_t s, bool prolong_first = false) {
   const int M = (int)H->L.size() - 1;
   DevLevel& F = H->L[m];
   if (m == M) {
     bottom<T>(H, F, s);
     return;
   }
+  DevLevel& C = H->L[m + 1];
   if (m >= H->coarse_first && M - m + 1 <= dev::MAXC) {
+    if (prolong_first) prolong_from<T>(H, F, C, s);
     coarse_cluster<T>(H, m, s);
     return;
   }
-  DevLevel& C = H->L[m + 1];
-  for (int k = 0; k < H->par.nu1; ++k) smooth_step<T>(H, F, s);
+  // prolong_first: the initial guess is u + P u^(m+1) (the FMG ascent); the first
+  // pre-smoothing sweep reads it on the fly
+  if (prolong_first && H->par.nu1 == 0) prolong_from<T>(H, F, C, s);
+  for (int k = 0; k < H->par.nu1; ++k) {
+    if (k == 0 && prolong_first) smooth_step<T>(H, F, s, U<T>(C), C.pitch);
+    else smooth_step<T>(H, F, s);
+  }
   restrict_to<T>(H, F, C, s);
   vcycle<T>(H, m + 1, s);
   if (H->par.nu2 == 0) {
@@ -674,6 +681,20 @@ void vcycle(ccm_handle* H, int m, cudaStream_t s) {
   }
   smooth_step<T>(H, F, s, U<T>(C), C.pitch);
   for (int k = 1; k < H->par.nu2; ++k) smooth_step<T>(H, F, s);
+}
+
+// One FMG cycle (Sec. 4, the FMG figure) for L^(0) u = r^(0) from the zero guess: the
+// right-hand side is restricted level by level to the bottom level (the restriction of
+// r - L 0 with a zero iterate) and solved there; then every finer level runs one V-cycle
+// (Alg. 2) from the prolonged coarse solution.  u = U<T>(level 0) on return.
+template <typename T>
+void fmg(ccm_handle* H, cudaStream_t s) {
+  const int M = (int)H->L.size() - 1;
+  DevLevel& L0 = H->L[0];
+  cudaMemsetAsync(U<T>(L0), 0, (size_t)H->nb * L0.npad * sizeof(T), s);
+  for (int m = 0; m < M; ++m) restrict_to<T>(H, H->L[m], H->L[m + 1], s);   // also zeroes u^(m+1)
+  bottom<T>(H, H->L[M], s);
+  for (int m = M - 1; m >= 0; --m) vcycle<T>(H, m, s, true);
 }
 
 int read_norm(ccm_handle* H, const uint8_t* cls, long n, const double* x, cudaStream_t s, double& out) {
@@ -1073,6 +1094,7 @@ int ccm_default_params(ccm_params* p) {
   p->smoother = 1;
   p->coarse_n = 0;
   p->batch = 1;
+  p->cycle = 0;
   return CCM_OK;
 }
 
@@ -1112,7 +1134,7 @@ int ccm_setup(const ccm_problem* prob, const ccm_params* params, ccm_handle** ou
   if (par.nu1 < 0 || par.nu2 < 0 || par.coarsest < 4 || par.ras_passes < 0 || par.ras_block < 8 ||
       par.ras_block > 128 || par.ras_overlap < 0 || par.ras_overlap > 64 || par.max_iter < 0 ||
       par.ras_exact < 0 || par.ras_exact > 6000 || par.inner_cycles < 1 || par.inner_cycles > 16 || par.smoother < 0 || par.smoother > 1 || par.coarse_n < 0 ||
-      par.batch < 1 || par.batch > 4096 ||
+      par.batch < 1 || par.batch > 4096 || par.cycle < 0 || par.cycle > 1 ||
       !(par.theta >= 0 && par.theta < 1) || (par.precision != CCM_FP64 && par.precision != CCM_MIXED))
     return CCM_EINVAL;
   auto t0 = std::chrono::steady_clock::now();
@@ -1356,7 +1378,8 @@ static void iteration_body(ccm_handle* h, bool fp64, cudaStream_t s) {
     cudaMemsetAsync(L.u32[L.cur32], 0, h->nb * np * sizeof(float), s);
     for (int c = 0; c < std::max(1, h->par.inner_cycles); ++c) {
       ProfScope ps(h, CCM_PROF_VCYCLE, s);
-      vcycle<float>(h, 0, s);
+      if (c == 0 && h->par.cycle == 1) fmg<float>(h, s);     // FMG, then V-cycles from its result
+      else vcycle<float>(h, 0, s);
     }
     dim3 blk(dev::TX, dev::TY);
     KL(launch_k(dev::k_axpy_tiles, dim3(L.ntiles, h->nb), blk, 0, s, L.tiles, L.cls, L.nx, L.ny, L.pitch,
@@ -1370,7 +1393,8 @@ static void iteration_body(ccm_handle* h, bool fp64, cudaStream_t s) {
     cudaMemsetAsync(L.u32[L.cur32], 0, np * sizeof(float), s);
     for (int c = 0; c < std::max(1, h->par.inner_cycles); ++c) {
       ProfScope ps(h, CCM_PROF_VCYCLE, s);
-      vcycle<float>(h, 0, s);
+      if (c == 0 && h->par.cycle == 1) fmg<float>(h, s);     // FMG, then V-cycles from its result
+      else vcycle<float>(h, 0, s);
     }
     KL(launch_k(dev::k_axpy<float>, std::min(ceil_div(np, 256), 4096), 256, 0, s, np, L.cls, L.u32[L.cur32], h->uhat));
     ucur = h->uhat;
@@ -1661,6 +1685,24 @@ int ccm_vcycle(ccm_handle* h, double* u, const double* r, int precision, void* s
   } else {
     load_level<float>(h, L, u, r, s);
     vcycle<float>(h, 0, s);
+    KL(dev::k_unpack<float><<<pg, 128, 0, s>>>(L.nx, L.ny, L.pitch, L.cls, U<float>(L), u, 1.0));
+  }
+  CCM_CUDA(cudaGetLastError());
+  return CCM_OK;
+}
+
+int ccm_fmg(ccm_handle* h, double* u, const double* r, int precision, void* stream) {
+  if (!h || !u || !r) return CCM_EINVAL;
+  cudaStream_t s = (cudaStream_t)stream;
+  DevLevel& L = h->L[0];
+  dim3 pg(ceil_div(L.nx, 128), L.ny);
+  if (precision == CCM_FP64) {
+    load_level<double>(h, L, u, r, s);
+    fmg<double>(h, s);
+    KL(dev::k_unpack<double><<<pg, 128, 0, s>>>(L.nx, L.ny, L.pitch, L.cls, U<double>(L), u, 1.0));
+  } else {
+    load_level<float>(h, L, u, r, s);
+    fmg<float>(h, s);
     KL(dev::k_unpack<float><<<pg, 128, 0, s>>>(L.nx, L.ny, L.pitch, L.cls, U<float>(L), u, 1.0));
   }
   CCM_CUDA(cudaGetLastError());
