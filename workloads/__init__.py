@@ -251,6 +251,64 @@ CONFIGS = {
 }
 
 
+def paper_problem1(n: int) -> Problem:
+    """The paper's Problem 1 (Sec. 5.1): Poisson on the unit box centred at the origin outside
+    the flower r >= 0.25 + 0.05 cos(6 theta); Dirichlet on the box, Neumann on the flower."""
+    return Problem(1.0, 0.0, 1.0, -0.5, -0.5, 1.0 / n, n, n, DIRICHLET,
+                   [Curve(STAR, (0.0, 0.0, 0.25, 0.05, 6.0), -1, NEUMANN)], name=f"paper_problem1_{n}")
+
+
+def mms_problem1() -> Manufactured:
+    """u = r^4 cos(3 theta) = r (x^3 - 3 x y^2), r = |(x, y)| (Problem 1; smooth away from 0)."""
+    def parts(x, y):
+        s = np.sqrt(x * x + y * y)
+        return s, x ** 3 - 3 * x * y * y
+
+    def u(x, y):
+        s, q = parts(x, y)
+        return s * q
+
+    def ux(x, y):
+        s, q = parts(x, y)
+        return x / s * q + s * (3 * x * x - 3 * y * y)
+
+    def uy(x, y):
+        s, q = parts(x, y)
+        return y / s * q - 6 * s * x * y
+
+    def uxx(x, y):
+        s, q = parts(x, y)
+        return y * y / s ** 3 * q + 2 * x / s * (3 * x * x - 3 * y * y) + 6 * x * s
+
+    def uyy(x, y):
+        s, q = parts(x, y)
+        return x * x / s ** 3 * q - 12 * x * y * y / s - 6 * x * s
+
+    def uxy(x, y):
+        s, q = parts(x, y)
+        return -x * y / s ** 3 * q - 6 * x * x * y / s + y / s * (3 * x * x - 3 * y * y) - 6 * y * s
+
+    return Manufactured(u, ux, uy, uxx, uxy, uyy, "r^4 cos 3theta")
+
+
+def paper_problem3(n: int) -> Problem:
+    """The paper's Problem 3, case (i) (Sec. 5.1): a u_xx + c u_yy = f with (a, b, c) = (1, 0, 2)
+    on the unit box [0,1]^2, Dirichlet on its sides (no curve: every boundary piece is a
+    box wall)."""
+    return Problem(1.0, 0.0, 2.0, 0.0, 0.0, 1.0 / n, n, n, DIRICHLET, [], name=f"paper_problem3_{n}")
+
+
+def mms_problem3() -> Manufactured:
+    """u = sin(4 x) cos(3 y) (Problem 3, case (i))."""
+    return Manufactured(lambda x, y: np.sin(4 * x) * np.cos(3 * y),
+                        lambda x, y: 4 * np.cos(4 * x) * np.cos(3 * y),
+                        lambda x, y: -3 * np.sin(4 * x) * np.sin(3 * y),
+                        lambda x, y: -16 * np.sin(4 * x) * np.cos(3 * y),
+                        lambda x, y: -12 * np.cos(4 * x) * np.sin(3 * y),
+                        lambda x, y: -9 * np.sin(4 * x) * np.cos(3 * y),
+                        "sin 4x cos 3y")
+
+
 def mms_sinsin() -> Manufactured:
     """u = sin(pi x) sin(pi y) (the exact solution of the paper's Problem 2)."""
     P = math.pi
