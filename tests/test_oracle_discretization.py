@@ -185,3 +185,34 @@ def test_paper_problem2_error_magnitudes(case):
     for (c, n, norm, val) in _golden_problem2():
         if c == case and n == 64:
             assert val / 5 <= got[norm] <= val * 5, (norm, got[norm], val)
+
+
+def _golden_problem3():
+    rows = []
+    with open(os.path.join(GOLDEN, "paper_problem3.txt")) as f:
+        for line in f:
+            if line.startswith("#") or not line.strip():
+                continue
+            h, norm, val = line.split()
+            rows.append((int(h.split("/")[1]), norm, float(val)))
+    return rows
+
+
+def test_problem3_box_errors_match_paper():
+    """Problem 3, case (i): the box with no curve (every boundary piece a box wall), errors
+    of the direct solution within a factor 3 of the paper's, and a fourth-order rate."""
+    from oracle import multigrid as MG
+    errs = {}
+    for n in (64, 128):
+        prob, mms = W.paper_problem3(n), W.mms_problem3()
+        H = MG.build_hierarchy(prob)
+        lv = H.levels[0]
+        fa = Q.cell_averages(lv.cg, mms.f(prob.a, prob.b, prob.c))
+        ga = Q.boundary_averages(lv.cg, lv.dz.segs, mms.u, mms.ux, mms.uy)
+        u = MG.direct_solve(lv.dz, fa.ravel() - lv.dz.N @ ga)
+        ua = Q.cell_averages(lv.cg, mms.u).ravel()
+        errs[n] = float(np.abs(u - ua)[lv.ne].max())
+    paper = {n: v for (n, norm, v) in _golden_problem3() if norm == "Linf"}
+    for n, e in errs.items():
+        assert paper[n] / 3 <= e <= paper[n] * 3, (n, e, paper[n])
+    assert np.log2(errs[64] / errs[128]) > 3.5
