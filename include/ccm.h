@@ -245,6 +245,14 @@ int ccm_bottom_solve(ccm_handle* h, const double* r, double* u, void* stream);
 /* One V-cycle (Alg. 2) on level 0 for L u = r (physical units, FP64 in and out). */
 int ccm_vcycle(ccm_handle* h, double* u, const double* r, int precision, void* stream);
 
+/* Change the cycle parameters of a set-up handle (and of its transposed hierarchy, if built)
+ * without repeating the host setup: omega (0, 1.5], nu1, nu2 (0 - 16, nu1 + nu2 >= 1),
+ * inner_cycles (1 - 16), cycle (0 V, 1 FMG first).  Synchronises the device and drops the
+ * captured iteration graphs (the next solve recaptures them).  Used by the autotuner.  The
+ * paper fixes omega = 0.5, nu1 = nu2 = 3 (Sec. 5); these are free parameters of Alg. 2.
+ * Errors: CCM_EINVAL, CCM_ECUDA. */
+int ccm_set_cycle_params(ccm_handle* h, double omega, int nu1, int nu2, int inner_cycles, int cycle);
+
 /* One FMG cycle (Sec. 4, the FMG figure) for L u = r on the finest level, from the zero guess:
  * r restricted level by level to the bottom level and solved there, then one V-cycle (Alg. 2)
  * per finer level whose initial guess is the prolonged coarse solution.  r: device [ny][nx]

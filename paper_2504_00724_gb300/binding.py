@@ -83,6 +83,7 @@ _SIGS = {
     "ccm_bottom_solve": (I, [P, P, P, P]),
     "ccm_vcycle": (I, [P, P, P, I, P]),
     "ccm_fmg": (I, [P, P, P, I, P]),
+    "ccm_set_cycle_params": (I, [P, ctypes.c_double, I, I, I, I]),
     "ccm_free": (None, [P]),
     "ccm_strerror": (ctypes.c_char_p, [I]),
     "ccm_host_build": (I, [ctypes.POINTER(ccm_problem), ctypes.POINTER(ccm_params), ctypes.POINTER(P)]),
@@ -300,6 +301,17 @@ class Solver:
         u = u.clone()
         _check(lib().ccm_vcycle(self.h, _ptr(u), _ptr(r), precision, _stream(stream)), "ccm_vcycle")
         return u
+
+    def set_cycle_params(self, omega=None, nu1=None, nu2=None, inner_cycles=None, cycle=None):
+        """Change omega, nu1, nu2, inner_cycles, cycle without a new setup
+        (ccm_set_cycle_params); unspecified ones keep their values."""
+        p = self.params
+        vals = [p.omega if omega is None else omega, p.nu1 if nu1 is None else nu1,
+                p.nu2 if nu2 is None else nu2, p.inner_cycles if inner_cycles is None else inner_cycles,
+                p.cycle if cycle is None else cycle]
+        _check(lib().ccm_set_cycle_params(self.h, float(vals[0]), *[int(v) for v in vals[1:]]),
+               "ccm_set_cycle_params")
+        p.omega, p.nu1, p.nu2, p.inner_cycles, p.cycle = vals
 
     def fmg(self, r, precision=CCM_FP64, stream=None):
         """One FMG cycle for L u = r from the zero guess (ccm_fmg)."""

@@ -1462,6 +1462,29 @@ static void drop_graphs(ccm_handle* h) {
   h->gprof_ev.clear();
 }
 
+int ccm_set_cycle_params(ccm_handle* h, double omega, int nu1, int nu2, int inner_cycles, int cycle) {
+  if (!h || !(omega > 0 && omega <= 1.5) || nu1 < 0 || nu2 < 0 || nu1 + nu2 < 1 || nu1 > 16 || nu2 > 16 ||
+      inner_cycles < 1 || inner_cycles > 16 || cycle < 0 || cycle > 1)
+    return CCM_EINVAL;
+  if (cudaDeviceSynchronize() != cudaSuccess) return CCM_ECUDA;
+  drop_graphs(h);
+  if (h->adj) drop_graphs(h->adj);
+  for (ccm_handle* t : {h, h->adj}) {
+    if (!t) continue;
+    const double w22 = t->S64.omega_d != 0 ? t->par.omega / t->S64.omega_d : 0.0;   // the stencil's diagonal
+    t->par.omega = omega;
+    t->par.nu1 = nu1;
+    t->par.nu2 = nu2;
+    t->par.inner_cycles = inner_cycles;
+    t->par.cycle = cycle;
+    if (w22 != 0) {
+      t->S64.omega_d = omega / w22;
+      t->S32.omega_d = (float)(omega / w22);
+    }
+  }
+  return CCM_OK;
+}
+
 int ccm_solve(ccm_handle* h, const double* f, const double* g, double* u, int nrhs, void* stream, ccm_stats* st) {
   if (!h || !f || !u || nrhs < 1) return CCM_EINVAL;
   cudaStream_t s = (cudaStream_t)stream;
