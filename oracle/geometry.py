@@ -307,6 +307,10 @@ def _crossings(c: OCurve, idx: int, x0, y0, h, nx, ny):
                     tr = t[s]
                 elif fb == 0.0:
                     tr = t[s + 1]
+                elif fa * fb > 0.0:
+                    # the cell index changed only by the rounding of (v - org) / h: the curve
+                    # stays on one side of the line
+                    continue
                 else:
                     if axis == 0:
                         f = lambda tt: float(c.xy(tt)[0]) - L

@@ -319,6 +319,8 @@ static std::vector<Crossing> curve_crossings(const Curve& c, double x0, double y
             tr = t[s];
           } else if (fb == 0.0) {
             tr = t[s + 1];
+          } else if (fa * fb > 0.0) {
+            continue;   // the cell index changed only by the rounding of (v - org) / h
           } else {
             auto f = [&](double tt) {
               double x, y;

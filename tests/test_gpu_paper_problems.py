@@ -1,8 +1,9 @@
-"""The paper's convergence tests solved on the GPU (Sec. 5.1): Problem 2 (the ellipse hole,
+"""The paper's convergence tests solved on the GPU (Sec. 5.1): Problem 1 (the flower
+exterior, Dirichlet on the box, Neumann on the flower), Problem 2 (the ellipse hole,
 Dirichlet and Neumann on the ellipse) and Problem 3, case (i) (the box with (a, b, c) =
 (1, 0, 2)).  Solution errors against the exact cell averages must lie within a factor of
 the errors the paper prints (tests/golden) - 5 for Problem 2, whose PLG stencils near the
-curve differ from the paper's (the oracle's pin uses the same factor), 3 for the box - fall
+curve differ from the paper's (the oracle's pin uses the same factor), 3 for the others - fall
 at a fourth-order rate, and the mixed form must give the FP64 form's error to two
 significant digits."""
 import os
@@ -53,23 +54,27 @@ def _error(prob, mms, precision):
 
 
 CASES = {
-    "problem2_DD": (lambda n: W.paper_problem2(n, W.DIRICHLET), W.mms_sinsin, "paper_problem2.txt", "DD", 5.0),
-    "problem2_DN": (lambda n: W.paper_problem2(n, W.NEUMANN), W.mms_sinsin, "paper_problem2.txt", "DN", 5.0),
-    "problem3_box": (W.paper_problem3, W.mms_problem3, "paper_problem3.txt", "", 3.0),
+    "problem1_flower": (W.paper_problem1, W.mms_problem1, "paper_problem1.txt", "", 3.0, (40, 80, 160)),
+    "problem2_DD": (lambda n: W.paper_problem2(n, W.DIRICHLET), W.mms_sinsin, "paper_problem2.txt", "DD", 5.0,
+                    (64, 128, 256)),
+    "problem2_DN": (lambda n: W.paper_problem2(n, W.NEUMANN), W.mms_sinsin, "paper_problem2.txt", "DN", 5.0,
+                    (64, 128, 256)),
+    "problem3_box": (W.paper_problem3, W.mms_problem3, "paper_problem3.txt", "", 3.0, (64, 128, 256)),
 }
 
 
 @pytest.mark.parametrize("name", list(CASES))
 def test_paper_errors_and_rates(name):
-    mk, mms, golden, case, factor = CASES[name]
+    mk, mms, golden, case, factor, sizes = CASES[name]
     paper = _golden(golden)
     errs = {}
-    for n in (64, 128, 256):
+    for n in sizes:
         e64 = _error(mk(n), mms(), P.CCM_FP64)
         e32 = _error(mk(n), mms(), P.CCM_MIXED)
         assert abs(e32 - e64) <= 0.05 * e64, (n, e32, e64)     # equal to two significant digits
         errs[n] = e64
         want = paper[(case, n)]
         assert want / factor <= e64 <= want * factor, (n, e64, want)
-    assert np.log2(errs[64] / errs[128]) > 3.3
-    assert np.log2(errs[128] / errs[256]) > 3.3
+    n0, n1, n2 = sizes
+    assert np.log2(errs[n0] / errs[n1]) > 3.3
+    assert np.log2(errs[n1] / errs[n2]) > 3.3

@@ -41,7 +41,8 @@ def _compare_level(hs, level, prob_level):
 
 @pytest.mark.parametrize("mk", [lambda: W.disk_minus(32), lambda: W.star(64),
                                 lambda: W.three_ellipses(64), lambda: W.paper_problem2(32, W.NEUMANN),
-                                lambda: W.star(32, (1.25, -0.8660254037844386, 1.75))])
+                                lambda: W.star(32, (1.25, -0.8660254037844386, 1.75)),
+                                lambda: W.paper_problem1(40)])
 def test_finest_level_matches_oracle(mk):
     prob = mk()
     hs = P.HostSetup(prob)

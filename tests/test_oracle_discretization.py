@@ -216,3 +216,35 @@ def test_problem3_box_errors_match_paper():
     for n, e in errs.items():
         assert paper[n] / 3 <= e <= paper[n] * 3, (n, e, paper[n])
     assert np.log2(errs[64] / errs[128]) > 3.5
+
+
+def _golden_linf(name):
+    rows = {}
+    with open(os.path.join(GOLDEN, name)) as f:
+        for line in f:
+            if line.startswith("#") or not line.strip():
+                continue
+            h, norm, val = line.split()
+            if norm == "Linf":
+                rows[int(h.split("/")[1])] = float(val)
+    return rows
+
+
+def test_problem1_flower_errors_match_paper():
+    """Problem 1: the flower exterior, Dirichlet on the box, Neumann on the flower.  On these
+    grids the flower touches grid lines at grid vertices (theta = 0, pi/2, ...), which the
+    crossing finder must treat as touches, not crossings.  Errors within a factor 3 of the
+    paper's and a fourth-order rate."""
+    paper = _golden_linf("paper_problem1.txt")
+    errs = {}
+    for n in (40, 80):
+        prob, mms = W.paper_problem1(n), W.mms_problem1()
+        H = MG.build_hierarchy(prob)
+        lv = H.levels[0]
+        fa = Q.cell_averages(lv.cg, mms.f(prob.a, prob.b, prob.c))
+        ga = Q.boundary_averages(lv.cg, lv.dz.segs, mms.u, mms.ux, mms.uy)
+        u = MG.direct_solve(lv.dz, fa.ravel() - lv.dz.N @ ga)
+        ua = Q.cell_averages(lv.cg, mms.u).ravel()
+        errs[n] = float(np.abs(u - ua)[lv.ne].max())
+        assert paper[n] / 3 <= errs[n] <= paper[n] * 3, (n, errs[n], paper[n])
+    assert np.log2(errs[40] / errs[80]) > 3.5
