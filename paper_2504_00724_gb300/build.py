@@ -1,7 +1,11 @@
 """Build libccm.so in-tree: host setup (C++17) and CUDA kernels for sm_103a.
 
 Translation units are compiled in parallel and linked with nvcc; the result lands next to
-this file.  Re-running skips the build when no source is newer than the library.
+this file.  Re-running skips the build when no source is newer than the library.  Host code
+is compiled with floating-point contraction off, so that the setup (whose discrete choices,
+such as whether the boundary crosses a cell edge or only touches a grid vertex, can hang on
+the last bit) gives the same result on x86-64 and on AArch64, where GCC would otherwise fuse
+multiply-adds.
 """
 from __future__ import annotations
 
@@ -26,6 +30,7 @@ def _sources():
     out = [os.path.join(CSRC, f) for f in CXX_SOURCES + CU_SOURCES]
     out += [os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith((".h", ".cuh"))]
     out.append(os.path.join(INCLUDE, "ccm.h"))
+    out.append(os.path.abspath(__file__))
     return out
 
 
@@ -50,11 +55,11 @@ def build(force: bool = False, verbose: bool = False) -> str:
     jobs = []
     for f in CXX_SOURCES:
         o = os.path.join(BUILD, f + ".o")
-        jobs.append(["g++", "-std=c++17", "-O3", "-fPIC", "-Wall", "-I", INCLUDE, "-c",
+        jobs.append(["g++", "-std=c++17", "-O3", "-ffp-contract=off", "-fPIC", "-Wall", "-I", INCLUDE, "-c",
                      os.path.join(CSRC, f), "-o", o])
     for f in CU_SOURCES:
         o = os.path.join(BUILD, f + ".o")
-        jobs.append([NVCC, *ARCH, "-lineinfo", "-O3", "-std=c++17", "-Xcompiler", "-fPIC",
+        jobs.append([NVCC, *ARCH, "-lineinfo", "-O3", "-std=c++17", "-Xcompiler", "-fPIC,-ffp-contract=off",
                      "-I", INCLUDE, "-c", os.path.join(CSRC, f), "-o", o])
     with ThreadPoolExecutor(max_workers=len(jobs)) as ex:
         logs = list(ex.map(_run, jobs))
