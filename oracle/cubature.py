@@ -80,7 +80,8 @@ def cell_averages(cg: CutGrid, f: Callable) -> np.ndarray:
 
 
 def boundary_averages(cg: CutGrid, segs, u: Callable, ux: Callable, uy: Callable) -> np.ndarray:
-    """<<N u>>_i over every boundary segment: u (Dirichlet) or grad u . n (Neumann)."""
+    """<<N u>>_i over every boundary segment: u (Dirichlet), grad u . n (Neumann) or
+    gamma1 u + gamma2 grad u . n (Robin)."""
     out = np.zeros(len(segs))
     for k, lin in enumerate(segs):
         lin = int(lin)
@@ -89,8 +90,11 @@ def boundary_averages(cg: CutGrid, segs, u: Callable, ux: Callable, uy: Callable
             x, y, _, dsw, (nx_, ny_) = _piece_nodes(cg, pc)
             if cg.bc[lin] == DIRICHLET:
                 val = u(x, y)
-            else:
+            elif cg.bc[lin] == NEUMANN:
                 val = ux(x, y) * nx_ + uy(x, y) * ny_
+            else:                      # Robin: gamma1 u + gamma2 du/dn
+                g1, g2 = cg.robin[lin]
+                val = g1 * u(x, y) + g2 * (ux(x, y) * nx_ + uy(x, y) * ny_)
             tot += float(np.sum(val * dsw))
             length += float(np.sum(dsw))
         out[k] = tot / length

@@ -188,19 +188,27 @@ def _fit(cg: CutGrid, i: int, j: int, cells, a: float, b: float, c: float):
     w = [max(math.hypot(ci - i, cj - j), 0.5) for (ci, cj) in cells]
     if lin in cg.bpieces:
         S = cg.bm0[lin][0]
+        col_d = shift_moments(cg.bm0[lin], dx, dy) / S
+        gx = shift_moments(cg.bmx[lin], dx, dy)
+        gy = shift_moments(cg.bmy[lin], dx, dy)
+        col_n = np.zeros(15)
+        for k, (p, q) in enumerate(EXPS):
+            v = 0.0
+            if p >= 1:
+                v += p * gx[EIDX[(p - 1, q)]]
+            if q >= 1:
+                v += q * gy[EIDX[(p, q - 1)]]
+            col_n[k] = v / S
         if cg.bc[lin] == DIRICHLET:
-            col = shift_moments(cg.bm0[lin], dx, dy) / S
+            col = col_d
+        elif cg.bc[lin] == NEUMANN:
+            col = col_n
         else:
-            gx = shift_moments(cg.bmx[lin], dx, dy)
-            gy = shift_moments(cg.bmy[lin], dx, dy)
-            col = np.zeros(15)
-            for k, (p, q) in enumerate(EXPS):
-                v = 0.0
-                if p >= 1:
-                    v += p * gx[EIDX[(p - 1, q)]]
-                if q >= 1:
-                    v += q * gy[EIDX[(p, q - 1)]]
-                col[k] = v / S
+            # Robin, N = gamma1 + gamma2 d/dn (Sec. 3.3): <N phi> in the scaled frame is
+            # gamma1 <phi> + (gamma2 / h) <d phi / dn_s>, normalised by |gamma1| + |gamma2| / h
+            # so that gamma2 = 0 gives the Dirichlet column and gamma1 = 0 the Neumann one
+            g1, g2 = cg.robin[lin]
+            col = (g1 * col_d + (g2 / cg.h) * col_n) / _robin_norm(g1, g2, cg.h)
         M = np.concatenate([M, col[:, None]], axis=1)
         w.append(0.5)
     w = np.array(w)
@@ -208,6 +216,11 @@ def _fit(cg: CutGrid, i: int, j: int, cells, a: float, b: float, c: float):
     MW = M * Wd[None, :]
     beta_s = Wd * (M.T @ np.linalg.solve(MW @ M.T, Lhat))
     return beta_s, float(np.sum(w * beta_s * beta_s)), M15
+
+
+def _robin_norm(g1: float, g2: float, h: float) -> float:
+    """Scale of the Robin boundary column, |gamma1| + |gamma2| / h (see _fit)."""
+    return abs(g1) + abs(g2) / h
 
 
 def fit_row(cg: CutGrid, i: int, j: int, a: float, b: float, c: float) -> Row:
@@ -229,7 +242,13 @@ def fit_row(cg: CutGrid, i: int, j: int, a: float, b: float, c: float) -> Row:
     beta = beta_s[:15] / h ** 2
     beta_b = 0.0
     if lin in cg.bpieces:
-        beta_b = beta_s[15] / (h ** 2 if cg.bc[lin] == DIRICHLET else h)
+        if cg.bc[lin] == DIRICHLET:
+            beta_b = beta_s[15] / h ** 2
+        elif cg.bc[lin] == NEUMANN:
+            beta_b = beta_s[15] / h
+        else:
+            g1, g2 = cg.robin[lin]
+            beta_b = beta_s[15] / (_robin_norm(g1, g2, h) * h ** 2)
     return Row(cells, beta, beta_b, cond)
 
 

@@ -33,7 +33,7 @@ import numpy as np
 from scipy.optimize import brentq
 
 CIRCLE, ELLIPSE, STAR = 1, 2, 3
-NONE, DIRICHLET, NEUMANN = 0, 1, 2
+NONE, DIRICHLET, NEUMANN, ROBIN = 0, 1, 2, 3
 EMPTY, PURE, CUT = 0, 1, 2
 
 # graded monomial order used everywhere: (0,0),(1,0),(0,1),(2,0),(1,1),(0,2),...
@@ -53,8 +53,9 @@ class GeometryError(Exception):
 class OCurve:
     """Closed parametric curve gamma(t), t in [0, 2 pi), counter-clockwise."""
 
-    def __init__(self, kind, params, orient, bc):
+    def __init__(self, kind, params, orient, bc, robin=(1.0, 0.0)):
         self.kind, self.p, self.orient, self.bc = int(kind), tuple(float(v) for v in params), int(orient), int(bc)
+        self.robin = (float(robin[0]), float(robin[1]))   # gamma1, gamma2 (Sec. 3.3, the Robin N)
 
     def xy(self, t):
         t = np.asarray(t, dtype=np.float64)
@@ -196,6 +197,7 @@ class CutGrid:
     bmx: Dict[int, np.ndarray] = field(default_factory=dict)
     bmy: Dict[int, np.ndarray] = field(default_factory=dict)
     bc: Dict[int, int] = field(default_factory=dict)
+    robin: Dict[int, tuple] = field(default_factory=dict)   # ROBIN cells: (gamma1, gamma2)
     arcs_of: Dict[int, list] = field(default_factory=dict)   # pre-merge arcs per interface cell
 
     def centre(self, i, j):
@@ -369,7 +371,7 @@ def _sigma_point(s):
 def cut_cells(prob, theta: float = 0.3) -> CutGrid:
     """Cut cells of prob's grid, with Alg. 1 merging (threshold theta)."""
     x0, y0, h, nx, ny = prob.x0, prob.y0, prob.h, prob.nx, prob.ny
-    curves = [OCurve(c.kind, c.params, c.orient, c.bc) for c in prob.curves]
+    curves = [OCurve(c.kind, c.params, c.orient, c.bc, getattr(c, "robin", (1.0, 0.0))) for c in prob.curves]
     walls = prob.box_bc != NONE
 
     # ---- arcs: curve pieces between consecutive grid-line crossings (one cell each)
@@ -640,11 +642,18 @@ def cut_cells(prob, theta: float = 0.3) -> CutGrid:
             continue
         kinds = set()
         for pc in bp:
-            kinds.add(prob.box_bc if pc.kind == 'seg' else curves[pc.curve].bc)
+            if pc.kind == 'seg':
+                kinds.add((prob.box_bc, 1.0, 0.0))
+            else:
+                cv = curves[pc.curve]
+                kinds.add((cv.bc,) + (cv.robin if cv.bc == ROBIN else (1.0, 0.0)))
         if len(kinds) != 1:
             raise GeometryError("a cell mixes boundary-condition types")
         CG.bpieces[lin] = bp
-        CG.bc[lin] = kinds.pop()
+        kind = kinds.pop()
+        CG.bc[lin] = kind[0]
+        if kind[0] == ROBIN:
+            CG.robin[lin] = kind[1:]
         xc, yc = CG.centre(i, j)
         b0, bx, by = np.zeros(15), np.zeros(15), np.zeros(15)
         for pc in bp:

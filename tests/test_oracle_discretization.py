@@ -49,7 +49,9 @@ def test_stencil_sign_reading():
 
 
 CASES = [("disk", lambda: W.disk_minus(32)), ("star", lambda: W.star(64)),
-         ("ellipses", lambda: W.three_ellipses(64)), ("problem2N", lambda: W.paper_problem2(32, W.NEUMANN))]
+         ("ellipses", lambda: W.three_ellipses(64)), ("problem2N", lambda: W.paper_problem2(32, W.NEUMANN)),
+         ("robin", lambda: W.disk_robin(32, (1.0, 0.5))), ("robin_cross", lambda: W.disk_robin(32, (2.0, -0.3),
+                                                                                              abc=(1.0, 0.5, 2.0)))]
 
 
 @pytest.mark.parametrize("name,mk", CASES)
@@ -248,3 +250,45 @@ def test_problem1_flower_errors_match_paper():
         errs[n] = float(np.abs(u - ua)[lv.ne].max())
         assert paper[n] / 3 <= errs[n] <= paper[n] * 3, (n, errs[n], paper[n])
     assert np.log2(errs[40] / errs[80]) > 3.5
+
+
+def _rows(prob):
+    cg = G.cut_cells(prob)
+    return cg, D.discretize(cg, prob.a, prob.b, prob.c)
+
+
+@pytest.mark.parametrize("gamma,bc", [((1.0, 0.0), W.DIRICHLET), ((0.0, 1.0), W.NEUMANN)])
+def test_robin_limits_are_dirichlet_and_neumann(gamma, bc):
+    """N = gamma1 + gamma2 d/dn (Sec. 3.3): with gamma2 = 0 the Robin rows are the Dirichlet
+    rows, with gamma1 = 0 the Neumann rows (same stencils, coefficients to rounding)."""
+    import dataclasses
+    rob = W.disk_robin(32, gamma)
+    ref = dataclasses.replace(rob, curves=[dataclasses.replace(rob.curves[0], bc=bc)])
+    _, dr = _rows(rob)
+    _, dd = _rows(ref)
+    assert sorted(dr.rows) == sorted(dd.rows)
+    for lin, row in dr.rows.items():
+        other = dd.rows[lin]
+        assert row.cells == other.cells
+        scale = np.abs(other.beta).max()
+        assert np.abs(row.beta - other.beta).max() <= 1e-11 * scale
+        assert abs(row.beta_b - other.beta_b) <= 1e-11 * scale
+
+
+def test_robin_polynomial_solution_reproduced():
+    prob = W.disk_robin(32, (1.0, 0.5), abc=(1.0, 0.5, 2.0))
+    cg, dz = _rows(prob)
+    poly = W.mms_polynomial([0.3, -1.0, 0.5, 2.0, -0.7, 1.1, 0.2, -0.4, 0.9, 0.1, 0.6, -0.3, 0.25, 0.8, -0.5])
+    ua = Q.cell_averages(cg, poly.u).ravel()
+    fa = Q.cell_averages(cg, poly.f(prob.a, prob.b, prob.c)).ravel()
+    ga = Q.boundary_averages(cg, dz.segs, poly.u, poly.ux, poly.uy)
+    u = MG.direct_solve(dz, fa - dz.N @ ga)
+    ne = (cg.status != G.EMPTY).ravel()
+    assert np.abs(u - ua)[ne].max() <= 1e-9 * np.abs(ua[ne]).max()
+
+
+def test_robin_fourth_order():
+    """Robin data on the circle: the max-norm solution error falls at fourth order (64 -> 128;
+    the oscillatory solution is pre-asymptotic at 32)."""
+    e = [_solution_error(W.disk_robin(n, (1.0, 0.5)), W.mms_disk())[0] for n in (64, 128)]
+    assert math.log2(e[0] / e[1]) > 3.5, e

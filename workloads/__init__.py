@@ -26,7 +26,7 @@ from typing import Callable, List, Optional, Sequence
 import numpy as np
 
 CIRCLE, ELLIPSE, STAR = 1, 2, 3
-NONE, DIRICHLET, NEUMANN = 0, 1, 2
+NONE, DIRICHLET, NEUMANN, ROBIN = 0, 1, 2, 3
 
 
 @dataclass
@@ -35,6 +35,7 @@ class Curve:
     params: Sequence[float]
     orient: int = -1
     bc: int = DIRICHLET
+    robin: Sequence[float] = (1.0, 0.0)   # ROBIN: (gamma1, gamma2) of gamma1 u + gamma2 du/dn
 
 
 @dataclass
@@ -159,6 +160,15 @@ def disk_minus(n: int, r: float = 0.2) -> Problem:
     """Unit square minus a disk of radius r centred at (0.5, 0.5); Dirichlet everywhere."""
     return Problem(1.0, 0.0, 1.0, 0.0, 0.0, 1.0 / n, n, n, DIRICHLET,
                    [Curve(CIRCLE, (0.5, 0.5, r), -1, DIRICHLET)], name=f"disk_minus_{n}")
+
+
+def disk_robin(n: int, gamma=(1.0, 0.5), r: float = 0.2, abc=(1.0, 0.0, 1.0)) -> Problem:
+    """Unit square minus a disk of radius r centred at (0.5, 0.5): Dirichlet on the box, the
+    Robin condition gamma1 u + gamma2 du/dn = g on the circle (n the outward normal of the
+    domain, pointing into the disk)."""
+    a, b, c = abc
+    return Problem(a, b, c, 0.0, 0.0, 1.0 / n, n, n, DIRICHLET,
+                   [Curve(CIRCLE, (0.5, 0.5, r), -1, ROBIN, tuple(gamma))], name=f"disk_robin_{n}")
 
 
 def star(n: int, abc=(1.0, 0.5, 2.0), r0=0.3, amp=0.08, k=5, centre=(0.5, 0.5)) -> Problem:
