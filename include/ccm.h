@@ -40,15 +40,18 @@ extern "C" {
  *   CCM_ELLIPSE p = (cx, cy, a, b, phi)      gamma = c + Rot(phi) (a cos t, b sin t)
  *   CCM_STAR    p = (cx, cy, r0, amp, k)     gamma = c + (r0 + amp cos k t)(cos t, sin t) */
 enum { CCM_CIRCLE = 1, CCM_ELLIPSE = 2, CCM_STAR = 3 };
-/* boundary conditions (Sec. 3.3): NONE only for box_bc (the box is not part of dOmega) */
-enum { CCM_NONE = 0, CCM_DIRICHLET = 1, CCM_NEUMANN = 2 };
+/* boundary conditions (Sec. 3.3): NONE only for box_bc (the box is not part of dOmega);
+ * ROBIN (curves only) is gamma1 u + gamma2 du/dn = g with the curve's robin[] = (gamma1,
+ * gamma2), n the unit normal pointing out of Omega */
+enum { CCM_NONE = 0, CCM_DIRICHLET = 1, CCM_NEUMANN = 2, CCM_ROBIN = 3 };
 /* arithmetic of the multigrid cycle */
 enum { CCM_FP64 = 0, CCM_MIXED = 1 };
 
 enum {
   CCM_OK = 0,
   CCM_EINVAL = -1,     /* null pointer, b^2-4ac >= 0, h <= 0, bad sizes, nx/ny not divisible */
-  CCM_EGEOM = -2,      /* curve leaves the box, mixed BC types in one cell, isolated pieces */
+  CCM_EGEOM = -2,      /* curve leaves the box, mixed BC types (or Robin coefficients) in one
+                          cell, isolated pieces */
   CCM_EPLG = -3,       /* no poised stencil within the search radius */
   CCM_ESINGULAR = -4,  /* zero pivot in a block or bottom factorisation */
   CCM_ENOCONV = -5,    /* max_iter reached; u holds the last iterate */
@@ -63,7 +66,8 @@ typedef struct {
   int kind;        /* CCM_CIRCLE | CCM_ELLIPSE | CCM_STAR */
   double p[8];     /* parameters, see above */
   int orient;      /* +1: Omega lies inside the curve; -1: the curve bounds a hole */
-  int bc;          /* CCM_DIRICHLET | CCM_NEUMANN */
+  int bc;          /* CCM_DIRICHLET | CCM_NEUMANN | CCM_ROBIN */
+  double robin[2]; /* CCM_ROBIN: (gamma1, gamma2), finite, not both zero; ignored otherwise */
 } ccm_curve;
 
 typedef struct {
@@ -154,9 +158,15 @@ int ccm_query(const ccm_handle* h, ccm_info* info);
 int ccm_cell_map(const ccm_handle* h, int8_t* status, int32_t* owner, int8_t* regular, double* vol);
 
 /* Boundary segments of the finest level in ĝ order (host arrays of n_segments, any may be
- * NULL): cell = linear index of the owning cell, bc = CCM_DIRICHLET | CCM_NEUMANN,
+ * NULL): cell = linear index of the owning cell, bc = CCM_DIRICHLET | CCM_NEUMANN | CCM_ROBIN,
  * length = arc length of the piece (physical units).  Blocking. */
 int ccm_boundary_segments(const ccm_handle* h, int32_t* cell, int32_t* bc, double* length);
+
+/* Boundary operator of every finest-level segment in the general form gamma1 u + gamma2 du/dn
+ * (Sec. 3.3): gamma[2 s] = gamma1, gamma[2 s + 1] = gamma2 of segment s (host array of
+ * 2 n_segments): (1, 0) for Dirichlet, (0, 1) for Neumann, the curve's robin[] for Robin.
+ * The boundary datum g of a segment is the average of that operator applied to u.  Blocking. */
+int ccm_boundary_robin(const ccm_handle* h, double* gamma);
 
 /* Quadrature rules that reproduce the averages the discretisation expects (Sec. 3.2,
  * eq. iteratedIntegral): for every non-pure non-empty cell, nodes and weights whose weighted

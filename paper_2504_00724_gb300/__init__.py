@@ -10,8 +10,8 @@ from __future__ import annotations
 import ctypes
 import os
 
-from .binding import (CCM_DIRICHLET, CCM_FP64, CCM_MIXED, CCM_NEUMANN, CCM_NONE, CcmError,
+from .binding import (CCM_DIRICHLET, CCM_FP64, CCM_MIXED, CCM_NEUMANN, CCM_NONE, CCM_ROBIN, CcmError,
                       HostSetup, Solver, lib, load_library)
 
 __all__ = ["Solver", "HostSetup", "lib", "load_library", "CcmError", "CCM_FP64", "CCM_MIXED", "CCM_NONE",
-           "CCM_DIRICHLET", "CCM_NEUMANN"]
+           "CCM_DIRICHLET", "CCM_NEUMANN", "CCM_ROBIN"]

@@ -12,7 +12,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 LIBPATH = os.path.join(HERE, "libccm.so")
 
 CCM_CIRCLE, CCM_ELLIPSE, CCM_STAR = 1, 2, 3
-CCM_NONE, CCM_DIRICHLET, CCM_NEUMANN = 0, 1, 2
+CCM_NONE, CCM_DIRICHLET, CCM_NEUMANN, CCM_ROBIN = 0, 1, 2, 3
 CCM_FP64, CCM_MIXED = 0, 1
 CCM_PROF_OFF, CCM_PROF_RESID_FP64, CCM_PROF_SMO1_FP32, CCM_PROF_SMO1_FP64, CCM_PROF_VCYCLE = 0, 1, 2, 3, 4
 CCM_PROF_SMO2_FP32, CCM_PROF_PROLONG_SMO1_FP32, CCM_PROF_RESTRICT_FP32 = 5, 6, 7
@@ -26,7 +26,7 @@ class CcmError(RuntimeError):
 
 class ccm_curve(ctypes.Structure):
     _fields_ = [("kind", ctypes.c_int), ("p", ctypes.c_double * 8), ("orient", ctypes.c_int),
-                ("bc", ctypes.c_int)]
+                ("bc", ctypes.c_int), ("robin", ctypes.c_double * 2)]
 
 
 class ccm_problem(ctypes.Structure):
@@ -71,6 +71,7 @@ _SIGS = {
     "ccm_query": (I, [P, ctypes.POINTER(ccm_info)]),
     "ccm_cell_map": (I, [P, P, P, P, P]),
     "ccm_boundary_segments": (I, [P, P, P, P]),
+    "ccm_boundary_robin": (I, [P, P]),
     "ccm_quadrature": (I, [P, I64P, I64P, P, P, P, P, P, P, P]),
     "ccm_apply": (I, [P, P, P, P, I, P]),
     "ccm_apply_T": (I, [P, P, P, P, I, P]),
@@ -148,6 +149,8 @@ def problem_struct(prob) -> tuple:
             arr[k].p[m] = float(v)
         arr[k].orient = int(c.orient)
         arr[k].bc = int(c.bc)
+        g = getattr(c, "robin", (1.0, 0.0))
+        arr[k].robin[0], arr[k].robin[1] = float(g[0]), float(g[1])
     s = ccm_problem(float(prob.a), float(prob.b), float(prob.c), float(prob.x0), float(prob.y0),
                     float(prob.h), int(prob.nx), int(prob.ny), int(prob.box_bc), n, arr)
     return s, arr
@@ -211,6 +214,13 @@ class Solver:
         _check(lib().ccm_boundary_segments(self.h, cell.ctypes.data, bc.ctypes.data, ln.ctypes.data),
                "ccm_boundary_segments")
         return cell, bc, ln
+
+    def boundary_operator(self) -> np.ndarray:
+        """(gamma1, gamma2) per segment [n_segments, 2]: the segment's boundary operator is
+        gamma1 u + gamma2 du/dn."""
+        gam = np.zeros((self.nseg, 2))
+        _check(lib().ccm_boundary_robin(self.h, gam.ctypes.data), "ccm_boundary_robin")
+        return gam
 
     def quadrature(self):
         nc, nb = ctypes.c_int64(0), ctypes.c_int64(0)
@@ -356,13 +366,16 @@ class Solver:
         return out
 
     def boundary_averages(self, u, ux, uy, quad=None) -> np.ndarray:
-        """<<N u>> over every boundary segment (host): u (Dirichlet) or grad u . n (Neumann)."""
-        cell, bc, ln = self.boundary_segments()
+        """<<N u>> over every boundary segment (host): u (Dirichlet), grad u . n (Neumann) or
+        gamma1 u + gamma2 grad u . n (Robin)."""
+        gam = self.boundary_operator()
         q = self.quadrature() if quad is None else quad
         seg, bxy, bw, bn = q[3], q[4], q[5], q[6]
         x, y = bxy[:, 0], bxy[:, 1]
-        sb = bc[seg]
-        val = np.where(sb == CCM_DIRICHLET, u(x, y), ux(x, y) * bn[:, 0] + uy(x, y) * bn[:, 1])
+        g1, g2 = gam[seg, 0], gam[seg, 1]
+        uv = u(x, y)
+        dn = ux(x, y) * bn[:, 0] + uy(x, y) * bn[:, 1]
+        val = np.where(g2 == 0, g1 * uv, np.where(g1 == 0, g2 * dn, g1 * uv + g2 * dn))
         num = np.bincount(seg, weights=val * bw, minlength=self.nseg)
         den = np.bincount(seg, weights=bw, minlength=self.nseg)
         return num / den

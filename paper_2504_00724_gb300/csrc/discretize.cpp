@@ -20,6 +20,9 @@ namespace ccm {
 static const int RADII[3] = {3, 4, 5};
 static const int NCAND = 12;
 
+// scale of the Robin boundary column, |gamma1| + |gamma2| / h
+static double robin_norm(double g1, double g2, double h) { return std::fabs(g1) + std::fabs(g2) / h; }
+
 void regular_stencil(double a, double b, double c, double w[5][5]) {
   static const double lap[5] = {-1.0, 16.0, -30.0, 16.0, -1.0};
   static const double grad[5] = {1.0, -8.0, 0.0, 8.0, -1.0};
@@ -270,17 +273,32 @@ void fit(const CutLevel& cg, int i, int j, const std::array<int, 15>& cells, dou
   if (sit != cg.seg_of.end()) {
     int s = sit->second;
     double S = cg.bm0[s][0];
-    if (cg.seg_bc[s] == CCM_DIRICHLET) {
+    // the boundary column <N phi_k> in the scaled frame: the average of the monomial
+    // (Dirichlet), of its normal derivative (Neumann), or gamma1 times the first plus gamma2 / h
+    // times the second, divided by |gamma1| + |gamma2| / h (Robin), so that the Robin column
+    // reduces to the other two when a coefficient vanishes
+    double cd[NMOM], cn[NMOM];
+    const int bc = cg.seg_bc[s];
+    if (bc != CCM_NEUMANN) {
       Mom g = shift_moments(cg.bm0[s], dx, dy);
-      for (int k = 0; k < NMOM; ++k) M[k][15] = g[k] / S;
-    } else {
+      for (int k = 0; k < NMOM; ++k) cd[k] = g[k] / S;
+    }
+    if (bc != CCM_DIRICHLET) {
       Mom gx = shift_moments(cg.bmx[s], dx, dy), gy = shift_moments(cg.bmy[s], dx, dy);
       for (int k = 0; k < NMOM; ++k) {
         int p = mono_p(k), q = mono_q(k);
         double v = 0;
         if (p >= 1) v += p * gx[mono_index(p - 1, q)];
         if (q >= 1) v += q * gy[mono_index(p, q - 1)];
-        M[k][15] = v / S;
+        cn[k] = v / S;
+      }
+    }
+    for (int k = 0; k < NMOM; ++k) {
+      if (bc == CCM_DIRICHLET) M[k][15] = cd[k];
+      else if (bc == CCM_NEUMANN) M[k][15] = cn[k];
+      else {
+        const double g1 = cg.seg_gamma[s][0], g2 = cg.seg_gamma[s][1];
+        M[k][15] = (g1 * cd[k] + (g2 / cg.h) * cn[k]) / robin_norm(g1, g2, cg.h);
       }
     }
     w[15] = 0.5;
@@ -373,7 +391,12 @@ int discretize_level(const CutLevel& cg, double a, double b, double c, int nthre
       auto sit = cg.seg_of.find(lin);
       if (sit != cg.seg_of.end()) {
         rows.seg[r] = sit->second;
-        rows.nb[r] = cg.seg_bc[sit->second] == CCM_DIRICHLET ? best.beta[15] : best.beta[15] * cg.h;
+        // N g enters the scaled rows (h^2 L) with the column's scale undone: h^0 (Dirichlet),
+        // h (Neumann), 1 / (|gamma1| + |gamma2| / h) (Robin)
+        const int s = sit->second, bc = cg.seg_bc[s];
+        rows.nb[r] = bc == CCM_DIRICHLET ? best.beta[15]
+                     : bc == CCM_NEUMANN ? best.beta[15] * cg.h
+                                         : best.beta[15] / robin_norm(cg.seg_gamma[s][0], cg.seg_gamma[s][1], cg.h);
       }
       conds[r] = cond2(best.M15);
     }

@@ -380,6 +380,23 @@ static double sigma_of(double X, double Y, int edge) {
 static const double CORNER_X[4] = {-0.5, 0.5, 0.5, -0.5};
 static const double CORNER_Y[4] = {-0.5, -0.5, 0.5, 0.5};
 
+int check_problem(const ccm_problem& prob) {
+  if (!(prob.h > 0) || prob.nx < 4 || prob.ny < 4 || prob.ncurves < 0 || (prob.ncurves > 0 && !prob.curves))
+    return CCM_EINVAL;
+  if (!(prob.b * prob.b - 4 * prob.a * prob.c < 0)) return CCM_EINVAL;   // elliptic (Sec. 2)
+  if (prob.box_bc != CCM_NONE && prob.box_bc != CCM_DIRICHLET && prob.box_bc != CCM_NEUMANN) return CCM_EINVAL;
+  for (int k = 0; k < prob.ncurves; ++k) {
+    const ccm_curve& c = prob.curves[k];
+    if (c.kind < CCM_CIRCLE || c.kind > CCM_STAR || (c.orient != 1 && c.orient != -1) ||
+        (c.bc != CCM_DIRICHLET && c.bc != CCM_NEUMANN && c.bc != CCM_ROBIN))
+      return CCM_EINVAL;
+    if (c.bc == CCM_ROBIN && (!std::isfinite(c.robin[0]) || !std::isfinite(c.robin[1]) ||
+                              (c.robin[0] == 0.0 && c.robin[1] == 0.0)))
+      return CCM_EINVAL;
+  }
+  return CCM_OK;
+}
+
 int build_cut_level(const ccm_problem& prob, int nx, int ny, double h, double theta, CutLevel& cg,
                     std::string& err) {
   cg.nx = nx;
@@ -395,6 +412,13 @@ int build_cut_level(const ccm_problem& prob, int nx, int ny, double h, double th
     std::memcpy(c.p, prob.curves[k].p, sizeof(c.p));
     c.orient = prob.curves[k].orient;
     c.bc = prob.curves[k].bc;
+    if (c.bc == CCM_ROBIN) {
+      c.robin[0] = prob.curves[k].robin[0];
+      c.robin[1] = prob.curves[k].robin[1];
+    } else {
+      c.robin[0] = c.bc == CCM_NEUMANN ? 0.0 : 1.0;
+      c.robin[1] = c.bc == CCM_NEUMANN ? 1.0 : 0.0;
+    }
     cg.curves.push_back(c);
   }
   const bool walls = prob.box_bc != CCM_NONE;
@@ -720,11 +744,18 @@ int build_cut_level(const ccm_problem& prob, int nx, int ny, double h, double th
       for (const Piece& pc : r.pieces)
         if (pc.arc || pc.wall) bp.push_back(pc);
     if (bp.empty()) continue;
+    // one operator gamma1 u + gamma2 du/dn per cell: the same type and, for Robin, the same
+    // coefficients on every piece
     int bc = -1;
+    std::array<double, 2> gam{1.0, 0.0};
     for (const Piece& pc : bp) {
-      int b = pc.arc ? cg.curves[pc.curve].bc : prob.box_bc;
-      if (bc < 0) bc = b;
-      else if (bc != b) {
+      const int b = pc.arc ? cg.curves[pc.curve].bc : prob.box_bc;
+      std::array<double, 2> g{b == CCM_NEUMANN ? 0.0 : 1.0, b == CCM_NEUMANN ? 1.0 : 0.0};
+      if (pc.arc) g = {cg.curves[pc.curve].robin[0], cg.curves[pc.curve].robin[1]};
+      if (bc < 0) {
+        bc = b;
+        gam = g;
+      } else if (bc != b || (b == CCM_ROBIN && gam != g)) {
         err = "a cell mixes boundary-condition types";
         return CCM_EGEOM;
       }
@@ -735,6 +766,7 @@ int build_cut_level(const ccm_problem& prob, int nx, int ny, double h, double th
     cg.seg_of[lin] = (int)cg.segs.size();
     cg.segs.push_back(lin);
     cg.seg_bc.push_back(bc);
+    cg.seg_gamma.push_back(gam);
     cg.bm0.push_back(b0);
     cg.bmx.push_back(bx);
     cg.bmy.push_back(by);

@@ -37,6 +37,7 @@ struct Curve {
   double p[8] = {0};
   int orient = -1;
   int bc = CCM_DIRICHLET;
+  double robin[2] = {1.0, 0.0};     // CCM_ROBIN: gamma1, gamma2 of gamma1 u + gamma2 du/dn
   void xy(double t, double& x, double& y) const;
   void dxy(double t, double& x, double& y) const;
   bool inside(double x, double y) const;   // strictly inside the closed curve
@@ -75,6 +76,7 @@ struct CutLevel {
   std::vector<int> segs;
   std::unordered_map<int, int> seg_of;
   std::vector<int> seg_bc;
+  std::vector<std::array<double, 2>> seg_gamma;   // the segment's operator gamma1 u + gamma2 du/dn
   std::vector<Mom> bm0, bmx, bmy;
   std::vector<std::vector<Piece>> seg_pieces;
 
@@ -99,6 +101,8 @@ Mom shift_moments(const Mom& m, double dx, double dy);
 void gauss_legendre(int n, std::vector<double>& x, std::vector<double>& w);
 
 // geometry.cpp
+// CCM_OK, or CCM_EINVAL for a problem the method does not define (sizes, ellipticity, kinds)
+int check_problem(const ccm_problem& prob);
 int build_cut_level(const ccm_problem& prob, int nx, int ny, double h, double theta, CutLevel& out,
                     std::string& err);
 // discretize.cpp

@@ -16,8 +16,7 @@ int ccm_default_params(ccm_params* p);
 int ccm_host_build(const ccm_problem* prob, const ccm_params* params, ccm_host_setup** out) {
   if (!prob || !out) return CCM_EINVAL;
   *out = nullptr;
-  if (!(prob->h > 0) || prob->nx < 4 || prob->ny < 4 || !(prob->b * prob->b - 4 * prob->a * prob->c < 0))
-    return CCM_EINVAL;
+  if (int rc = ccm::check_problem(*prob)) return rc;
   ccm_params par;
   ccm_default_params(&par);
   if (params) par = *params;

@@ -1118,16 +1118,7 @@ const char* ccm_strerror(int code) {
 int ccm_setup(const ccm_problem* prob, const ccm_params* params, ccm_handle** out) {
   if (!prob || !out) return CCM_EINVAL;
   *out = nullptr;
-  if (!(prob->h > 0) || prob->nx < 4 || prob->ny < 4 || prob->ncurves < 0 || (prob->ncurves > 0 && !prob->curves))
-    return CCM_EINVAL;
-  if (!(prob->b * prob->b - 4 * prob->a * prob->c < 0)) return CCM_EINVAL;
-  if (prob->box_bc != CCM_NONE && prob->box_bc != CCM_DIRICHLET && prob->box_bc != CCM_NEUMANN) return CCM_EINVAL;
-  for (int k = 0; k < prob->ncurves; ++k) {
-    const ccm_curve& c = prob->curves[k];
-    if (c.kind < CCM_CIRCLE || c.kind > CCM_STAR || (c.orient != 1 && c.orient != -1) ||
-        (c.bc != CCM_DIRICHLET && c.bc != CCM_NEUMANN))
-      return CCM_EINVAL;
-  }
+  if (int rc = check_problem(*prob)) return rc;
   ccm_params par;
   ccm_default_params(&par);
   if (params) par = *params;
@@ -1220,6 +1211,16 @@ int ccm_boundary_segments(const ccm_handle* h, int32_t* cell, int32_t* bc, doubl
     if (cell) cell[s] = c.segs[s];
     if (bc) bc[s] = c.seg_bc[s];
     if (length) length[s] = c.bm0[s][0] * c.h;
+  }
+  return CCM_OK;
+}
+
+int ccm_boundary_robin(const ccm_handle* h, double* gamma) {
+  if (!h || !gamma) return CCM_EINVAL;
+  const CutLevel& c = h->H.cut[0];
+  for (size_t s = 0; s < c.segs.size(); ++s) {
+    gamma[2 * s] = c.seg_gamma[s][0];
+    gamma[2 * s + 1] = c.seg_gamma[s][1];
   }
   return CCM_OK;
 }

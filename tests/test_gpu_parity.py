@@ -26,6 +26,8 @@ CASES = {
     "star64": (lambda: W.star(64), W.mms_star),
     "disk32": (lambda: W.disk_minus(32), W.mms_disk),
     "ellipses64": (lambda: W.three_ellipses(64), W.mms_ellipses),
+    "robin32": (lambda: W.disk_robin(32, (1.0, 0.5)), W.mms_disk),
+    "robin_cross64": (lambda: W.disk_robin(64, (1.0, 2.0), abc=(1.0, 0.5, 2.0)), W.mms_disk),
 }
 OMEGA = 0.8
 

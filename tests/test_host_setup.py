@@ -42,7 +42,8 @@ def _compare_level(hs, level, prob_level):
 @pytest.mark.parametrize("mk", [lambda: W.disk_minus(32), lambda: W.star(64),
                                 lambda: W.three_ellipses(64), lambda: W.paper_problem2(32, W.NEUMANN),
                                 lambda: W.star(32, (1.25, -0.8660254037844386, 1.75)),
-                                lambda: W.paper_problem1(40)])
+                                lambda: W.paper_problem1(40), lambda: W.disk_robin(32),
+                                lambda: W.disk_robin(32, (2.0, -0.3), abc=(1.0, 0.5, 2.0))])
 def test_finest_level_matches_oracle(mk):
     prob = mk()
     hs = P.HostSetup(prob)
@@ -58,6 +59,14 @@ def test_every_level_matches_oracle():
         _compare_level(hs, m, MG.coarsen(prob, m))
 
 
+def test_robin_every_level_matches_oracle():
+    """The Robin column (scaled by |gamma1| + |gamma2| / h of the level) on every level."""
+    prob = W.disk_robin(64, (1.0, 0.5))
+    hs = P.HostSetup(prob)
+    for m in range(MG.n_levels(prob)):
+        _compare_level(hs, m, MG.coarsen(prob, m))
+
+
 def test_invalid_problems_are_rejected():
     prob = W.star(64)
     bad = W.Problem(1.0, 3.0, 1.0, 0.0, 0.0, 1 / 64, 64, 64, W.NONE, prob.curves)   # b^2 - 4ac > 0
@@ -69,3 +78,7 @@ def test_invalid_problems_are_rejected():
     with pytest.raises(P.CcmError) as e:
         P.HostSetup(off)
     assert e.value.code == -2
+    for gamma in ((0.0, 0.0), (float("nan"), 1.0)):                                 # no Robin operator
+        with pytest.raises(P.CcmError) as e:
+            P.HostSetup(W.disk_robin(32, gamma))
+        assert e.value.code == -1
