@@ -45,9 +45,9 @@ FP64_FMA_PER_CLK_SM = 2          # FP64 FMA issue rate per SM (4 flop / clk / SM
 # A figure is reported only while the device sources hash to the value it was taken on.
 KERNEL_SOURCES = ("kernels.cuh", "smooth.cuh", "outer.cuh")
 NCU_TRAFFIC = {        # class name -> (source hash, bytes per launch)
-    "fp32 sweep, level 0 (SMO-1 regular cells + SMO-2 blocks)": ("b70895564f2d52c7", 74.12e6),
-    "fp32 residual + restriction, level 0": ("b70895564f2d52c7", 78.91e6),
-    "fp64 outer residual, level 0 (regular cells, separable stencil)": ("b70895564f2d52c7", 96.12e6),
+    "fp32 sweep, level 0 (SMO-1 regular cells + SMO-2 blocks)": ("bac44b6155cda4cc", 73.90e6),
+    "fp32 residual + restriction, level 0": ("bac44b6155cda4cc", 79.06e6),
+    "fp64 outer residual, level 0 (regular cells, separable stencil)": ("bac44b6155cda4cc", 95.62e6),
 }
 
 
@@ -79,7 +79,9 @@ def parse():
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--no-batched", action="store_true",
-                    help="skip the many-right-hand-side workload (disk 512^2, 256 right-hand sides)")
+                    help="skip the batched workloads (disk 512^2 with 256 right-hand sides; 64 geometries)")
+    ap.add_argument("--coarsest", type=int, default=16,
+                    help="the hierarchy stops at the first level with at most this many cells per side")
     ap.add_argument("--profile-run", action="store_true",
                     help="only setup, warm-up and the timed solves (for an ncu launch list)")
     return ap.parse_args()
@@ -231,6 +233,62 @@ def batched_workload(stream, flush, nrhs=256, n=512, one_sample=16):
                               "sample": f"{one_sample} of the right-hand sides, batch 1"}}
 
 
+def many_geometries_workload(stream, flush, count=64):
+    """Many geometries of uneven grid sizes in one graph launch: the independent star and
+    ellipse interiors of seeds 0 .. count-1 (grids drawn from {128, 256, 512, 1024}^2,
+    (a,b,c) = (1,0.5,2), homogeneous Dirichlet data, f = smoothed N(0,1) cell values drawn
+    with the geometry's seed), mixed precision to rel. residual 1e-10 each, advanced
+    together by one group solve (one graph launch); beside it the same problems solved one
+    after another with their own solves."""
+    import torch
+    import paper_2504_00724_gb300 as P
+    import workloads as W
+    probs = W.many_geometries(count)
+    t0 = time.time()
+    solvers = [P.Solver(p, rtol=RTOL, max_iter=200) for p in probs]
+    setup_s = time.time() - t0
+    fs, gs = [], []
+    for k, (s, p) in enumerate(zip(solvers, probs)):
+        mask = s.cell_map()[0] != 0
+        fs.append(torch.tensor(W.smoothed_normal_rhs(p.nx, 1, mask, seed=k)[0], device="cuda"))
+        gs.append(None)
+    ncell = int(sum(s.info.n_cells for s in solvers))
+    grid_cells = int(sum(p.nx * p.ny for p in probs))
+
+    def timed(fn, reps):
+        per = []
+        out = None
+        for _ in range(reps):
+            flush.zero_()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            out = fn()
+            e1.record(stream)
+            e1.synchronize()
+            per.append(e0.elapsed_time(e1))
+        return float(np.median(per)), out
+
+    grp = P.Group(solvers, stream=stream)
+    grp.solve(fs, None, stream=stream)                     # warm-up
+    ms, (us, st, rc) = timed(lambda: grp.solve(fs, None, stream=stream), 3)
+    programmatic = grp.programmatic
+    grp.close()
+    for s, f, g in zip(solvers, fs, gs):
+        s.solve(f, g, stream=stream)                       # captures each solver's own graph
+    ms1, sts = timed(lambda: [s.solve(f, g, stream=stream)[1] for s, f, g in zip(solvers, fs, gs)], 2)
+    for s in solvers:
+        s.close()
+    return {"workload": f"{count} independent star / ellipse interiors (seeds 0..{count - 1}), grids drawn from "
+                        f"{{128,256,512,1024}}^2 ({grid_cells} grid cells), (a,b,c)=(1,0.5,2), homogeneous "
+                        "Dirichlet, f smoothed N(0,1) (3 sweeps, seed = geometry seed), mixed precision",
+            "value": ncell / (ms / 1000.0), "unit": UNIT, "ms_per_solve": ms, "unknowns": ncell,
+            "setup_s": setup_s, "graph_launches_per_solve": 1, "programmatic_edges": programmatic,
+            "iterations_max": int(max(x.iterations for x in st)), "iterations_min": int(min(x.iterations for x in st)),
+            "rel_residual_max": float(max(x.rel_residual for x in st)),
+            "one_after_another": {"value": ncell / (ms1 / 1000.0), "ms": ms1,
+                                  "iterations_max": int(max(x.iterations for x in sts))}}
+
+
 def main():
     args = parse()
     rank = int(os.environ.get("RANK", "0"))
@@ -251,7 +309,7 @@ def main():
 
     prob, mms = W.star(args.n), W.mms_star()
     t0 = time.time()
-    solver = P.Solver(prob, precision=P.CCM_MIXED, rtol=RTOL, max_iter=200)
+    solver = P.Solver(prob, precision=P.CCM_MIXED, rtol=RTOL, max_iter=200, coarsest=args.coarsest)
     setup_s = time.time() - t0
     info = solver.info
     q = solver.quadrature()
@@ -340,7 +398,7 @@ def main():
     # plain FP64 form, same workload and tolerance
     fp64 = None
     if not args.no_fp64:
-        s64 = P.Solver(prob, precision=P.CCM_FP64, rtol=RTOL, max_iter=200)
+        s64 = P.Solver(prob, precision=P.CCM_FP64, rtol=RTOL, max_iter=200, coarsest=args.coarsest)
         s64.solve(f, g)
         per64, (u64, st64), _ = timed_solves(s64, max(1, min(args.steps, 2)))
         err64 = float(np.abs(u64.cpu().numpy() - ua)[ne].max())
@@ -349,8 +407,10 @@ def main():
         s64.close()
 
     batched = None
+    geometries = None
     if not args.no_batched and world == 1:
         batched = batched_workload(stream, flush)
+        geometries = many_geometries_workload(stream, flush)
 
     # the autotuner on this workload (V-cycles; omega, sweeps, inner cycles), then the tuned
     # solve timed like the headline; the headline keeps the default parameters
@@ -424,6 +484,7 @@ def main():
             "vcycle_ms": (vc_ms / vc_n) if vc_n else None, "setup_s": setup_s,
             "fp64": fp64, "mixed_over_fp64": (value / world / fp64["value"]) if fp64 else None,
             "batched": batched,
+            "many_geometries": geometries,
             "autotuned": tuned,
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(fh.numel() * 8 + gh.numel() * 8),
                     "d2h_bytes_per_step": int(uh.numel() * 8), "ms_per_step": float(np.mean(e2e))},

@@ -132,6 +132,7 @@ typedef struct {
 } ccm_stats;
 
 typedef struct ccm_handle ccm_handle;
+typedef struct ccm_group ccm_group;
 
 /* Fill p with the defaults: omega 0.7, nu1 = nu2 = 3, theta 0.3, coarsest 16, CCM_MIXED,
  * rtol 1e-10, max_iter 100, ras_passes 1, ras_block 64, ras_overlap 32, nthreads 0,
@@ -225,6 +226,33 @@ int ccm_apply_T(ccm_handle* h, const double* v, double* out_u, double* out_g, in
  * Errors: CCM_ENOCONV (u holds the last iterate), CCM_ENOTFINITE, CCM_ECUDA. */
 int ccm_solve(ccm_handle* h, const double* f, const double* g, double* u, int nrhs,
               void* stream, ccm_stats* stats);
+
+/* Many problems, one graph launch.  A group holds `count` set-up handles (distinct; each
+ * its own geometry, grid size, coefficients and precision) and one CUDA graph in which the
+ * outer iterations of all of them run: a device-side loop that, per pass, runs the outer
+ * iteration of every member whose relative residual is still above its rtol (and below
+ * its max_iter), each member's work on its own branch of the graph, then a one-thread-block
+ * kernel that reads the members' FP64 residual norms and retires the converged ones.  The
+ * arithmetic of a member is that of ccm_solve with one right-hand side; only the
+ * convergence test moves from the host to the device.
+ * ccm_group_create captures every member's iteration (it synchronises `stream` and uses
+ * each member's private capture stream; call it outside any stream capture, after
+ * ccm_set_cycle_params).  members[] is copied; the handles must outlive the group, and no
+ * other call may use them while a group solve is in flight.  Errors: CCM_EINVAL (NULL, a
+ * handle given twice), CCM_ENOMEM, CCM_ECUDA (the runtime rejected the graph).
+ * ccm_group_solve: f[k], u[k] device [ny_k][nx_k] and g[k] device [n_segments_k] (g or
+ * g[k] may be NULL: zero boundary data) of member k, the same layouts as ccm_solve; u[k] is
+ * the initial guess on entry, the solution on return.  stats (host, nullable) is an array
+ * of count entries.  Launches the right-hand side set-up of every member, then the graph,
+ * then synchronises the stream once.  Returns the first member's error in member order
+ * (CCM_ENOCONV, CCM_ENOTFINITE, CCM_ETIMEOUT) or CCM_ECUDA; stats tell which member.
+ * ccm_group_query: members, and 1 when the members' kernels keep their programmatic
+ * (overlapped-launch) edges inside the graph, 0 when they were captured without them. */
+int ccm_group_create(ccm_handle* const* members, int count, void* stream, ccm_group** out);
+int ccm_group_solve(ccm_group* g, const double* const* f, const double* const* gb, double* const* u,
+                    void* stream, ccm_stats* stats);
+int ccm_group_query(const ccm_group* g, int* members, int* programmatic);
+void ccm_group_free(ccm_group* g);
 
 /* Adjoint solve L^T lambda = rhs (transpose of eq. PoissonResidualForm) by the same V-cycle on
  * the hierarchy of the transposed operators (L^(m))^T: cells whose column of L is the plain

@@ -11,7 +11,7 @@ import ctypes
 import os
 
 from .binding import (CCM_DIRICHLET, CCM_FP64, CCM_MIXED, CCM_NEUMANN, CCM_NONE, CCM_ROBIN, CcmError,
-                      HostSetup, Solver, lib, load_library)
+                      Group, HostSetup, Solver, lib, load_library)
 
-__all__ = ["Solver", "HostSetup", "lib", "load_library", "CcmError", "CCM_FP64", "CCM_MIXED", "CCM_NONE",
+__all__ = ["Solver", "Group", "HostSetup", "lib", "load_library", "CcmError", "CCM_FP64", "CCM_MIXED", "CCM_NONE",
            "CCM_DIRICHLET", "CCM_NEUMANN", "CCM_ROBIN"]

@@ -96,6 +96,10 @@ _SIGS = {
     "ccm_apply_noalloc": (I, [P, P, P, P, P]),
     "ccm_profile": (I, [P, I]),
     "ccm_profile_read": (I, [P, ctypes.POINTER(ctypes.c_double), I64P]),
+    "ccm_group_create": (I, [P, I, P, ctypes.POINTER(P)]),
+    "ccm_group_solve": (I, [P, P, P, P, P, ctypes.POINTER(ccm_stats)]),
+    "ccm_group_query": (I, [P, ctypes.POINTER(I), ctypes.POINTER(I)]),
+    "ccm_group_free": (None, [P]),
 }
 
 
@@ -379,6 +383,51 @@ class Solver:
         num = np.bincount(seg, weights=val * bw, minlength=self.nseg)
         den = np.bincount(seg, weights=bw, minlength=self.nseg)
         return num / den
+
+
+class Group:
+    """Many set-up problems advanced together by one CUDA graph launch per solve
+    (ccm_group_create / ccm_group_solve).  The solvers must outlive the group."""
+
+    def __init__(self, solvers, stream=None):
+        self.solvers = list(solvers)
+        n = len(self.solvers)
+        arr = (P * max(1, n))(*[s.h for s in self.solvers])
+        g = P()
+        _check(lib().ccm_group_create(arr, n, _stream(stream), ctypes.byref(g)), "ccm_group_create")
+        self.g = g
+
+    @property
+    def programmatic(self) -> bool:
+        m, p = I(0), I(0)
+        _check(lib().ccm_group_query(self.g, ctypes.byref(m), ctypes.byref(p)), "ccm_group_query")
+        return bool(p.value)
+
+    def solve(self, fs, gs=None, us=None, stream=None, check=True):
+        """fs[k], gs[k], us[k]: member k's cell averages, boundary data (or None) and initial
+        guess (None: zero).  Returns (solutions, per-member ccm_stats, return code)."""
+        import torch
+        n = len(self.solvers)
+        us = [torch.zeros_like(f) if (us is None or us[k] is None) else us[k].clone() for k, f in enumerate(fs)]
+        fa = (P * n)(*[_ptr(f) for f in fs])
+        ua = (P * n)(*[_ptr(u) for u in us])
+        ga = None if gs is None else (P * n)(*[_ptr(g) for g in gs])
+        st = (ccm_stats * n)()
+        rc = lib().ccm_group_solve(self.g, fa, ga, ua, _stream(stream), st)
+        if check:
+            _check(rc, "ccm_group_solve")
+        return us, list(st), rc
+
+    def close(self):
+        if getattr(self, "g", None):
+            lib().ccm_group_free(self.g)
+            self.g = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 class HostSetup:

@@ -121,13 +121,15 @@ bool plg_candidates(const CutLevel& cg, int i, int j, std::vector<std::array<int
     }
     (void)W;
     if (found.empty()) continue;
-    std::stable_sort(found.begin(), found.end(), [](const Cand& x, const Cand& y) {
+    // the first NCAND candidates in the total order (cost, orientation, subset, counts); the
+    // order has no ties, so a partial sort gives the same leaders as a full sort
+    int nk = std::min<int>(NCAND, (int)found.size());
+    std::partial_sort(found.begin(), found.begin() + nk, found.end(), [](const Cand& x, const Cand& y) {
       if (x.cost != y.cost) return x.cost < y.cost;
       if (x.o != y.o) return x.o < y.o;
       if (x.si != y.si) return x.si < y.si;
       return x.pk < y.pk;
     });
-    int nk = std::min<int>(NCAND, (int)found.size());
     for (int k = 0; k < nk; ++k) {
       const Cand& c = found[k];
       std::vector<std::pair<int, int>> cells;   // (dx, dy)

@@ -20,6 +20,7 @@
 #include "coarse.cuh"
 #include "smooth.cuh"
 #include "outer.cuh"
+#include "group.cuh"
 
 using namespace ccm;
 
@@ -243,6 +244,11 @@ struct ProfScope {
     if (e_ != cudaSuccess) return CCM_ECUDA;            \
   } while (0)
 
+// launches of this thread carry the programmatic-serialization attribute (cleared while a
+// graph is captured for a runtime that does not take programmatic edges inside conditional
+// bodies)
+thread_local bool t_pdl = true;
+
 // kernel launch with programmatic stream serialization (the kernel may start while the
 // previous kernel of the stream drains; it waits for it inside, see pdl_enter)
 template <typename... KArgs, typename... Args>
@@ -256,7 +262,7 @@ cudaError_t launch_k(void (*k)(KArgs...), dim3 g, dim3 b, size_t smem, cudaStrea
   cfg.dynamicSmemBytes = smem;
   cfg.stream = s;
   cfg.attrs = at;
-  cfg.numAttrs = 1;
+  cfg.numAttrs = t_pdl ? 1 : 0;
   return cudaLaunchKernelEx(&cfg, k, args...);
 }
 
@@ -1359,7 +1365,9 @@ int ccm_apply_T(ccm_handle* h, const double* v, double* out_u, double* out_g, in
 // One outer iteration on the stream (also the body captured into the iteration graph):
 // mixed: FP32 V-cycles on the FP32 image of the FP64 residual, u_hat += e, new FP64 residual;
 // fp64:  one FP64 V-cycle in place, new FP64 residual; then the residual norm to the host.
-static void iteration_body(ccm_handle* h, bool fp64, cudaStream_t s) {
+// one outer iteration on stream s; with to_host the residual norm and the error word are
+// copied to the handle's pinned host words at its end
+static void iteration_body(ccm_handle* h, bool fp64, cudaStream_t s, bool to_host = true) {
   DevLevel& L = h->L[0];
   const long np = L.npad;
   double* ucur;
@@ -1386,6 +1394,7 @@ static void iteration_body(ccm_handle* h, bool fp64, cudaStream_t s) {
     KL(launch_k(dev::k_axpy_tiles, dim3(L.ntiles, h->nb), blk, 0, s, L.tiles, L.cls, L.nx, L.ny, L.pitch,
                 (const float*)L.u32[L.cur32], h->uhat, L.npad));
     outer_residual32(h, s);
+    if (!to_host) return;
     cudaMemcpyAsync(h->hnorm, h->dnorm, h->nb * sizeof(unsigned long long), cudaMemcpyDeviceToHost, s);
     cudaMemcpyAsync(h->herr, h->derr, sizeof(int), cudaMemcpyDeviceToHost, s);
     return;
@@ -1409,6 +1418,7 @@ static void iteration_body(ccm_handle* h, bool fp64, cudaStream_t s) {
         L.n2, L.W, L.irr_cell, L.ell_col, L.ell64, ucur, h->rhat, L.t64, nullptr, nullptr, nullptr));
   cudaMemsetAsync(h->dnorm, 0, sizeof(unsigned long long), s);
   KL(launch_k(dev::k_absmax<double>, std::min(ceil_div(np, 256), 1216), 256, 0, s, np, L.cls, L.t64, h->dnorm, 0L));
+  if (!to_host) return;
   cudaMemcpyAsync(h->hnorm, h->dnorm, sizeof(unsigned long long), cudaMemcpyDeviceToHost, s);
   cudaMemcpyAsync(h->herr, h->derr, sizeof(int), cudaMemcpyDeviceToHost, s);
 }
@@ -1486,12 +1496,56 @@ int ccm_set_cycle_params(ccm_handle* h, double omega, int nu1, int nu2, int inne
   return CCM_OK;
 }
 
+}  // extern "C"
+
+// r_hat = h^2 (f - N g) and the initial guess into slots [0, nb) of the level-0 FP64 arrays,
+// from right-hand sides [k0, k0 + nb) of the caller's arrays (g may be NULL: g = 0)
+static int load_rhs(ccm_handle* h, const double* f, const double* g, const double* u, int k0, int nb, double* U0,
+                    cudaStream_t s) {
+  DevLevel& L = h->L[0];
+  const long nu = (long)L.nx * L.ny, np = L.npad;
+  dim3 pg(ceil_div(L.nx, 128), L.ny);
+  CCM_CUDA(cudaMemsetAsync(h->rhat, 0, nb * np * sizeof(double), s));
+  CCM_CUDA(cudaMemsetAsync(U0, 0, nb * np * sizeof(double), s));
+  for (int b = 0; b < nb; ++b) {
+    const long k = k0 + b;
+    KL(dev::k_pack<double, double><<<pg, 128, 0, s>>>(L.nx, L.ny, L.pitch, L.cls, f + k * nu, h->rhat + b * np, L.h * L.h));
+    if (g && L.n2)
+      KL(dev::k_sub_boundary<<<ceil_div(L.n2, 128), 128, 0, s>>>(L.n2, L.irr_cell, L.nb, L.seg,
+                                                             g + k * h->info.n_segments, h->rhat + b * np));
+    KL(dev::k_pack<double, double><<<pg, 128, 0, s>>>(L.nx, L.ny, L.pitch, L.cls, u + k * nu, U0 + b * np, 1.0));
+  }
+  if (h->par.precision == CCM_FP64) CCM_CUDA(cudaMemcpyAsync(L.r64, h->rhat, np * sizeof(double), cudaMemcpyDeviceToDevice, s));
+  // ||r_hat|| of every right-hand side into dnorm[0, nb)
+  CCM_CUDA(cudaMemsetAsync(h->dnorm, 0, nb * sizeof(unsigned long long), s));
+  KL(launch_k(dev::k_absmax<double>, dim3(std::min(ceil_div(np, 256), 1216), nb), 256, 0, s, np, L.cls,
+              (const double*)h->rhat, h->dnorm, np));
+  return CCM_OK;
+}
+
+// max |r_hat - L U0| of one right-hand side into dnorm[0] (no host synchronisation)
+static void initial_residual(ccm_handle* h, const double* U0, cudaStream_t s) {
+  DevLevel& L = h->L[0];
+  if (h->par.precision != CCM_FP64 && h->fused_outer) {
+    outer_residual32(h, s);
+    return;
+  }
+  launch_regular<double>(h, L, U0, h->rhat, L.t64, true, s);
+  if (L.n2)
+    KL(launch_k(dev::k_rows<double, double, true, true>, ceil_div(L.n2, 128), 128, 0, s,
+        L.n2, L.W, L.irr_cell, L.ell_col, L.ell64, U0, h->rhat, L.t64, nullptr, nullptr, nullptr));
+  cudaMemsetAsync(h->dnorm, 0, sizeof(unsigned long long), s);
+  KL(launch_k(dev::k_absmax<double>, std::min(ceil_div(L.npad, 256), 1216), 256, 0, s, L.npad, L.cls,
+              (const double*)L.t64, h->dnorm, 0L));
+}
+
+extern "C" {
+
 int ccm_solve(ccm_handle* h, const double* f, const double* g, double* u, int nrhs, void* stream, ccm_stats* st) {
   if (!h || !f || !u || nrhs < 1) return CCM_EINVAL;
   cudaStream_t s = (cudaStream_t)stream;
   DevLevel& L = h->L[0];
   const long nu = (long)L.nx * L.ny, np = L.npad;
-  const double h2 = L.h * L.h;
   dim3 pg(ceil_div(L.nx, 128), L.ny);
   const bool fp64 = h->par.precision == CCM_FP64;
   const int bmax = fp64 ? 1 : h->bmax;
@@ -1508,42 +1562,22 @@ int ccm_solve(ccm_handle* h, const double* f, const double* g, double* u, int nr
     }
     ccm_handle::Graph& G = h->graph[fp64 ? 1 : 0];
     double* U0 = G.u0;
-    // r_hat = h^2 (f - N g); u_hat = initial guess
-    CCM_CUDA(cudaMemsetAsync(h->rhat, 0, nb * np * sizeof(double), s));
-    CCM_CUDA(cudaMemsetAsync(U0, 0, nb * np * sizeof(double), s));
-    for (int b = 0; b < nb; ++b) {
-      const long k = k0 + b;
-      KL(dev::k_pack<double, double><<<pg, 128, 0, s>>>(L.nx, L.ny, L.pitch, L.cls, f + k * nu, h->rhat + b * np, h2));
-      if (g && L.n2)
-        KL(dev::k_sub_boundary<<<ceil_div(L.n2, 128), 128, 0, s>>>(L.n2, L.irr_cell, L.nb, L.seg,
-                                                               g + k * h->info.n_segments, h->rhat + b * np));
-      KL(dev::k_pack<double, double><<<pg, 128, 0, s>>>(L.nx, L.ny, L.pitch, L.cls, u + k * nu, U0 + b * np, 1.0));
+    rc = load_rhs(h, f, g, u, k0, nb, U0, s);
+    if (rc) {
+      h->nb = 1;
+      return rc;
     }
-    if (fp64) CCM_CUDA(cudaMemcpyAsync(L.r64, h->rhat, np * sizeof(double), cudaMemcpyDeviceToDevice, s));
-    // ||r_hat|| of every right-hand side
-    CCM_CUDA(cudaMemsetAsync(h->dnorm, 0, nb * sizeof(unsigned long long), s));
-    KL(launch_k(dev::k_absmax<double>, dim3(std::min(ceil_div(np, 256), 1216), nb), 256, 0, s, np, L.cls,
-                (const double*)h->rhat, h->dnorm, np));
     CCM_CUDA(cudaMemcpyAsync(h->hnorm, h->dnorm, nb * sizeof(unsigned long long), cudaMemcpyDeviceToHost, s));
     CCM_CUDA(cudaStreamSynchronize(s));
     for (int b = 0; b < nb; ++b) {
       std::memcpy(&rnorm[b], &h->hnorm[b], sizeof(double));
       if (rnorm[b] == 0) rnorm[b] = 1;
     }
-    // initial residual
-    if (!fp64 && h->fused_outer) {
-      outer_residual32(h, s);
-      CCM_CUDA(cudaMemcpyAsync(h->hnorm, h->dnorm, nb * sizeof(unsigned long long), cudaMemcpyDeviceToHost, s));
-      CCM_CUDA(cudaStreamSynchronize(s));
-      for (int b = 0; b < nb; ++b) std::memcpy(&rel[b], &h->hnorm[b], sizeof(double));
-    } else {
-      launch_regular<double>(h, L, U0, h->rhat, L.t64, true, s);
-      if (L.n2)
-        KL(launch_k(dev::k_rows<double, double, true, true>, ceil_div(L.n2, 128), 128, 0, s,
-            L.n2, L.W, L.irr_cell, L.ell_col, L.ell64, U0, h->rhat, L.t64, nullptr, nullptr, nullptr));
-      rc = read_norm(h, L.cls, np, L.t64, s, rel[0]);
-      if (rc) return rc;
-    }
+    // initial residual (one right-hand side at a time outside the fused mixed form)
+    initial_residual(h, U0, s);
+    CCM_CUDA(cudaMemcpyAsync(h->hnorm, h->dnorm, nb * sizeof(unsigned long long), cudaMemcpyDeviceToHost, s));
+    CCM_CUDA(cudaStreamSynchronize(s));
+    for (int b = 0; b < nb; ++b) std::memcpy(&rel[b], &h->hnorm[b], sizeof(double));
     // the worst right-hand side of the group decides; stats report it
     auto worst = [&]() {
       double w = 0;
@@ -1593,6 +1627,265 @@ int ccm_solve(ccm_handle* h, const double* f, const double* g, double* u, int nr
   h->nb = 1;
   CCM_CUDA(cudaGetLastError());
   return result;
+}
+
+}  // extern "C"
+
+// ---------------------------------------------------------------- many problems, one graph
+
+struct ccm_group {
+  std::vector<ccm_handle*> m;
+  std::vector<double*> u0;            // per member: the level-0 FP64 iterate its iteration updates
+  std::vector<long long> launches;    // per member: kernel launches of one outer iteration
+  cudaGraphExec_t exec = nullptr;
+  bool pdl = true;                    // the members' launches keep their programmatic edges
+  Arena arena;
+  dev::GroupArgs A{};
+  unsigned long long* rnorm = nullptr;   // device, per member
+  int* it = nullptr;                     // device loop counter
+  // pinned host copies of the per-member results
+  int* h_iters = nullptr;
+  int* h_failed = nullptr;
+  double* h_rel = nullptr;
+  double* h_hist = nullptr;
+};
+
+namespace {
+
+// member h's outer iteration (single right-hand side) as an uninstantiated graph
+int capture_member(ccm_handle* h, cudaStream_t user, cudaGraph_t* out, long long* launches, double** u0) {
+  const bool fp64 = h->par.precision == CCM_FP64;
+  h->nb = 1;
+  if (!h->cap_stream) CCM_CUDA(cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking));
+  CCM_CUDA(cudaStreamSynchronize(user));
+  cudaStream_t s = h->cap_stream;
+  const int cur64 = h->L[0].cur64;
+  const int prof = h->prof_class;
+  h->prof_class = 0;                  // no event nodes: conditional bodies cannot hold them
+  CCM_CUDA(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+  h->capturing = true;
+  const long long l0 = g_launches.load();
+  iteration_body(h, fp64, s, false);
+  *launches = g_launches.load() - l0;
+  g_launches.fetch_sub(*launches);
+  h->capturing = false;
+  h->prof_class = prof;
+  cudaError_t e = cudaStreamEndCapture(s, out);
+  h->L[0].cur64 = cur64;
+  *u0 = fp64 ? h->L[0].u64[cur64] : h->uhat;
+  return e == cudaSuccess ? CCM_OK : CCM_ECUDA;
+}
+
+// WHILE(any member active) { IF(member k active) { iteration of k } for every k; decide }
+int build_group_graph(ccm_group* G, cudaStream_t user) {
+  const int n = (int)G->m.size();
+  std::vector<cudaGraph_t> body(n, nullptr);
+  G->u0.assign(n, nullptr);
+  G->launches.assign(n, 0);
+  const bool pdl0 = t_pdl;
+  t_pdl = G->pdl;
+  int rc = CCM_OK;
+  for (int k = 0; k < n && rc == CCM_OK; ++k) rc = capture_member(G->m[k], user, &body[k], &G->launches[k], &G->u0[k]);
+  t_pdl = pdl0;
+  cudaGraph_t graph = nullptr;
+  auto done = [&](int r) {
+    for (cudaGraph_t b : body)
+      if (b) cudaGraphDestroy(b);
+    if (graph) cudaGraphDestroy(graph);
+    return r;
+  };
+  if (rc) return done(rc);
+  if (cudaGraphCreate(&graph, 0) != cudaSuccess) return done(CCM_ECUDA);
+  // every condition starts each launch at 0 (nothing runs) until k_group_init sets it
+  cudaGraphConditionalHandle hw;
+  std::vector<cudaGraphConditionalHandle> hk(n);
+  if (cudaGraphConditionalHandleCreate(&hw, graph, 0, cudaGraphCondAssignDefault) != cudaSuccess) return done(CCM_ECUDA);
+  for (int k = 0; k < n; ++k)
+    if (cudaGraphConditionalHandleCreate(&hk[k], graph, 0, cudaGraphCondAssignDefault) != cudaSuccess)
+      return done(CCM_ECUDA);
+  G->A.hw = hw;
+  if (cudaMemcpy((void*)G->A.hk, hk.data(), n * sizeof(cudaGraphConditionalHandle), cudaMemcpyHostToDevice) != cudaSuccess)
+    return done(CCM_ECUDA);
+  dev::GroupArgs args = G->A;
+  void* kargs[] = {&args};
+  cudaKernelNodeParams kp{};
+  kp.func = (void*)dev::k_group_init;
+  kp.gridDim = dim3(1);
+  kp.blockDim = dim3(256);
+  kp.kernelParams = kargs;
+  cudaGraphNode_t init, loop, decide;
+  if (cudaGraphAddKernelNode(&init, graph, nullptr, 0, &kp) != cudaSuccess) return done(CCM_ECUDA);
+  cudaGraphNodeParams wp{};
+  wp.type = cudaGraphNodeTypeConditional;
+  wp.conditional.handle = hw;
+  wp.conditional.type = cudaGraphCondTypeWhile;
+  wp.conditional.size = 1;
+  if (cudaGraphAddNode(&loop, graph, &init, nullptr, 1, &wp) != cudaSuccess) return done(CCM_ECUDA);
+  cudaGraph_t lbody = wp.conditional.phGraph_out[0];
+  std::vector<cudaGraphNode_t> ifs(n);
+  for (int k = 0; k < n; ++k) {
+    cudaGraphNodeParams ip{};
+    ip.type = cudaGraphNodeTypeConditional;
+    ip.conditional.handle = hk[k];
+    ip.conditional.type = cudaGraphCondTypeIf;
+    ip.conditional.size = 1;
+    if (cudaGraphAddNode(&ifs[k], lbody, nullptr, nullptr, 0, &ip) != cudaSuccess) return done(CCM_ECUDA);
+    cudaGraphNode_t child;
+    if (cudaGraphAddChildGraphNode(&child, ip.conditional.phGraph_out[0], nullptr, 0, body[k]) != cudaSuccess)
+      return done(CCM_ECUDA);
+  }
+  kp.func = (void*)dev::k_group_decide;
+  if (cudaGraphAddKernelNode(&decide, lbody, ifs.data(), n, &kp) != cudaSuccess) return done(CCM_ECUDA);
+  if (cudaGraphInstantiate(&G->exec, graph, 0) != cudaSuccess) {
+    G->exec = nullptr;
+    cudaGetLastError();
+    return done(CCM_ECUDA);
+  }
+  return done(CCM_OK);
+}
+
+}  // namespace
+
+extern "C" {
+
+int ccm_group_create(ccm_handle* const* members, int count, void* stream, ccm_group** out) {
+  if (!members || count < 1 || !out) return CCM_EINVAL;
+  *out = nullptr;
+  for (int k = 0; k < count; ++k) {
+    if (!members[k]) return CCM_EINVAL;
+    for (int j = 0; j < k; ++j)
+      if (members[j] == members[k]) return CCM_EINVAL;     // one slot of state per handle
+  }
+  cudaStream_t s = (cudaStream_t)stream;
+  std::unique_ptr<ccm_group> G(new ccm_group());
+  G->m.assign(members, members + count);
+  Arena& A = G->arena;
+  const int n = count;
+  std::vector<const unsigned long long*> norms(n);
+  std::vector<const int*> errs(n);
+  std::vector<double> rtol(n);
+  std::vector<int> maxit(n);
+  for (int k = 0; k < n; ++k) {
+    norms[k] = G->m[k]->dnorm;
+    errs[k] = G->m[k]->derr;
+    rtol[k] = G->m[k]->par.rtol;
+    maxit[k] = G->m[k]->par.max_iter;
+  }
+  dev::GroupArgs& a = G->A;
+  a.n = n;
+  a.norm = A.upload(norms);
+  a.err = A.upload(errs);
+  a.rtol = A.upload(rtol);
+  a.max_iter = A.upload(maxit);
+  a.hk = A.alloc<cudaGraphConditionalHandle>(n);
+  G->rnorm = A.alloc<unsigned long long>(n);
+  a.rnorm = G->rnorm;
+  a.act = A.alloc<int>(n);
+  a.iters = A.alloc<int>(n);
+  a.failed = A.alloc<int>(n);
+  a.rel = A.alloc<double>(n);
+  a.hist = A.alloc<double>((long)n * dev::GROUP_HIST);
+  G->it = A.alloc<int>(1);
+  a.it = G->it;
+  if (A.err != cudaSuccess) return A.err == cudaErrorMemoryAllocation ? CCM_ENOMEM : CCM_ECUDA;
+  if (cudaMallocHost(&G->h_iters, n * sizeof(int)) != cudaSuccess ||
+      cudaMallocHost(&G->h_failed, n * sizeof(int)) != cudaSuccess ||
+      cudaMallocHost(&G->h_rel, n * sizeof(double)) != cudaSuccess ||
+      cudaMallocHost(&G->h_hist, (long)n * dev::GROUP_HIST * sizeof(double)) != cudaSuccess) {
+    ccm_group_free(G.release());
+    return CCM_ENOMEM;
+  }
+  int rc = build_group_graph(G.get(), s);
+  if (rc == CCM_ECUDA) {
+    // a runtime that rejects programmatic edges inside conditional bodies: plain edges
+    G->pdl = false;
+    rc = build_group_graph(G.get(), s);
+  }
+  if (rc) {
+    ccm_group_free(G.release());
+    return rc;
+  }
+  *out = G.release();
+  return CCM_OK;
+}
+
+int ccm_group_solve(ccm_group* G, const double* const* f, const double* const* g, double* const* u, void* stream,
+                    ccm_stats* st) {
+  if (!G || !f || !u) return CCM_EINVAL;
+  const int n = (int)G->m.size();
+  for (int k = 0; k < n; ++k)
+    if (!f[k] || !u[k]) return CCM_EINVAL;
+  cudaStream_t s = (cudaStream_t)stream;
+  // right-hand sides, initial guesses, ||r_hat|| and the initial residual of every member
+  for (int k = 0; k < n; ++k) {
+    ccm_handle* h = G->m[k];
+    h->nb = 1;
+    int rc = load_rhs(h, f[k], g ? g[k] : nullptr, u[k], 0, 1, G->u0[k], s);
+    if (rc) return rc;
+    CCM_CUDA(cudaMemcpyAsync(G->rnorm + k, h->dnorm, sizeof(unsigned long long), cudaMemcpyDeviceToDevice, s));
+    initial_residual(h, G->u0[k], s);
+  }
+  CCM_CUDA(cudaGraphLaunch(G->exec, s));
+  CCM_CUDA(cudaMemcpyAsync(G->h_iters, G->A.iters, n * sizeof(int), cudaMemcpyDeviceToHost, s));
+  CCM_CUDA(cudaMemcpyAsync(G->h_failed, G->A.failed, n * sizeof(int), cudaMemcpyDeviceToHost, s));
+  CCM_CUDA(cudaMemcpyAsync(G->h_rel, G->A.rel, n * sizeof(double), cudaMemcpyDeviceToHost, s));
+  CCM_CUDA(cudaMemcpyAsync(G->h_hist, G->A.hist, (long)n * dev::GROUP_HIST * sizeof(double), cudaMemcpyDeviceToHost, s));
+  int result = CCM_OK;
+  for (int k = 0; k < n; ++k) {
+    ccm_handle* h = G->m[k];
+    DevLevel& L = h->L[0];
+    dim3 pg(ceil_div(L.nx, 128), L.ny);
+    KL(dev::k_unpack<double><<<pg, 128, 0, s>>>(L.nx, L.ny, L.pitch, L.cls, G->u0[k], u[k], 1.0));
+  }
+  CCM_CUDA(cudaStreamSynchronize(s));
+  long long total = 2;   // k_group_init and the last k_group_decide
+  int loops = 0;
+  for (int k = 0; k < n; ++k) {
+    ccm_handle* h = G->m[k];
+    const int it = G->h_iters[k];
+    const double r = G->h_rel[k];
+    total += (long long)it * G->launches[k];
+    loops = std::max(loops, it);
+    int rk = CCM_OK;
+    if (G->h_failed[k]) {
+      rk = CCM_ETIMEOUT;
+      cudaMemsetAsync(h->derr, 0, sizeof(int), s);
+    } else if (!std::isfinite(r)) {
+      rk = CCM_ENOTFINITE;
+    } else if (r > h->par.rtol) {
+      rk = CCM_ENOCONV;
+    }
+    if (result == CCM_OK) result = rk;
+    if (st) {
+      ccm_stats& o = st[k];
+      o = ccm_stats{};
+      o.iterations = it;
+      o.rel_residual = r;
+      for (int j = 0; j <= std::min(it, dev::GROUP_HIST - 1); ++j) o.history[j] = G->h_hist[(long)k * dev::GROUP_HIST + j];
+    }
+  }
+  g_launches.fetch_add(total + std::max(0, loops - 1));
+  CCM_CUDA(cudaGetLastError());
+  return result;
+}
+
+int ccm_group_query(const ccm_group* G, int* members, int* programmatic) {
+  if (!G) return CCM_EINVAL;
+  if (members) *members = (int)G->m.size();
+  if (programmatic) *programmatic = G->pdl ? 1 : 0;
+  return CCM_OK;
+}
+
+void ccm_group_free(ccm_group* G) {
+  if (!G) return;
+  cudaDeviceSynchronize();
+  if (G->exec) cudaGraphExecDestroy(G->exec);
+  G->arena.release();
+  if (G->h_iters) cudaFreeHost(G->h_iters);
+  if (G->h_failed) cudaFreeHost(G->h_failed);
+  if (G->h_rel) cudaFreeHost(G->h_rel);
+  if (G->h_hist) cudaFreeHost(G->h_hist);
+  delete G;
 }
 
 int ccm_solve_T(ccm_handle* h, const double* rhs, double* lambda, int nrhs, void* stream, ccm_stats* st) {

@@ -42,6 +42,10 @@ def test_null_arguments_rejected_without_gpu():
     assert lib.ccm_apply(None, None, None, None, 1, None) == -1
     assert lib.ccm_solve(None, None, None, None, 1, None, None) == -1
     assert lib.ccm_query(None, None) == -1
+    assert lib.ccm_group_create(None, 1, None, None) == -1
+    assert lib.ccm_group_solve(None, None, None, None, None, None) == -1
+    assert lib.ccm_group_query(None, None, None) == -1
+    lib.ccm_group_free(None)
 
 
 def test_binding_constants_match_header_and_bench():

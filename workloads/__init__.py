@@ -179,6 +179,39 @@ def star(n: int, abc=(1.0, 0.5, 2.0), r0=0.3, amp=0.08, k=5, centre=(0.5, 0.5)) 
                    name=f"star_{n}")
 
 
+GEOMETRY_GRIDS = (128, 256, 512, 1024)
+
+
+def geometry_of_seed(seed: int, abc=(1.0, 0.5, 2.0)) -> Problem:
+    """One geometry of the many-geometry workload.  numpy's PCG64(seed) draws, in this order:
+    the grid n uniformly from {128, 256, 512, 1024}; the kind (star or ellipse, even odds);
+    the centre (0.5, 0.5) + U[-0.04, 0.04]^2; then for a star r = r0 + amp cos(k t) the values
+    r0 ~ U[0.25, 0.32], amp ~ U[0.03, 0.08], k ~ {3, 4, 5}, for an ellipse the semi-axes
+    U[0.25, 0.36] x U[0.15, 0.3] and the rotation U[0, pi).  The domain is the curve's
+    interior (the box is not part of the boundary), Dirichlet on the curve; every curve keeps
+    at least 0.07 from the box."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    n = int(GEOMETRY_GRIDS[rng.integers(0, len(GEOMETRY_GRIDS))])
+    is_star = bool(rng.integers(0, 2) == 0)
+    cx, cy = 0.5 + rng.uniform(-0.04, 0.04, size=2)
+    a, b, c = abc
+    if is_star:
+        r0, amp = rng.uniform(0.25, 0.32), rng.uniform(0.03, 0.08)
+        k = int(rng.integers(3, 6))
+        curve = Curve(STAR, (cx, cy, r0, amp, float(k)), +1, DIRICHLET)
+        name = f"geom{seed}_star_{n}"
+    else:
+        ea, eb, phi = rng.uniform(0.25, 0.36), rng.uniform(0.15, 0.3), rng.uniform(0.0, math.pi)
+        curve = Curve(ELLIPSE, (cx, cy, ea, eb, phi), +1, DIRICHLET)
+        name = f"geom{seed}_ellipse_{n}"
+    return Problem(a, b, c, 0.0, 0.0, 1.0 / n, n, n, NONE, [curve], name=name)
+
+
+def many_geometries(count: int = 64, seed0: int = 0) -> List[Problem]:
+    """The independent geometries of seeds seed0 .. seed0 + count - 1 (geometry_of_seed)."""
+    return [geometry_of_seed(seed0 + k) for k in range(count)]
+
+
 def three_ellipses(n: int, seed: int = 0, abc=(1.0, 0.0, 1.0), curve_bc: int = NEUMANN,
                    gap_cells: float = 4.0) -> Problem:
     """Unit square minus three disjoint ellipses (semi-axes 0.10x0.06, 0.08x0.08, 0.12x0.05).
