@@ -38,8 +38,12 @@ extern "C" {
 /* curve kinds: parameters p[] (t in [0, 2 pi), counter-clockwise)
  *   CCM_CIRCLE  p = (cx, cy, r)              gamma = c + r (cos t, sin t)
  *   CCM_ELLIPSE p = (cx, cy, a, b, phi)      gamma = c + Rot(phi) (a cos t, b sin t)
- *   CCM_STAR    p = (cx, cy, r0, amp, k)     gamma = c + (r0 + amp cos k t)(cos t, sin t) */
-enum { CCM_CIRCLE = 1, CCM_ELLIPSE = 2, CCM_STAR = 3 };
+ *   CCM_STAR    p = (cx, cy, r0, amp, k)     gamma = c + (r0 + amp cos k t)(cos t, sin t)
+ *   CCM_POLYGON pts = (x0, y0, ..., x_{n-1}, y_{n-1}), npts = n >= 3 vertices in
+ *               counter-clockwise order, no self-intersection; edge k is traversed at
+ *               constant speed for t in [2 pi k / n, 2 pi (k + 1) / n), so corners are kinks
+ *               of gamma and every integral along a piece is split there */
+enum { CCM_CIRCLE = 1, CCM_ELLIPSE = 2, CCM_STAR = 3, CCM_POLYGON = 4 };
 /* boundary conditions (Sec. 3.3): NONE only for box_bc (the box is not part of dOmega);
  * ROBIN (curves only) is gamma1 u + gamma2 du/dn = g with the curve's robin[] = (gamma1,
  * gamma2), n the unit normal pointing out of Omega */
@@ -68,6 +72,8 @@ typedef struct {
   int orient;      /* +1: Omega lies inside the curve; -1: the curve bounds a hole */
   int bc;          /* CCM_DIRICHLET | CCM_NEUMANN | CCM_ROBIN */
   double robin[2]; /* CCM_ROBIN: (gamma1, gamma2), finite, not both zero; ignored otherwise */
+  int npts;        /* CCM_POLYGON: vertex count; ignored otherwise */
+  const double* pts; /* CCM_POLYGON: host array of 2 npts coordinates (copied by ccm_setup) */
 } ccm_curve;
 
 typedef struct {
@@ -110,6 +116,11 @@ typedef struct {
                         (Alg. 2); 1, the first one is an FMG cycle (Sec. 4, the FMG figure:
                         the residual restricted to the bottom level, then one V-cycle per
                         level from the prolonged coarse solution) and the others V-cycles. */
+  int setup_device;  /* ccm_setup: 1, the weighted least-squares fits of every candidate PLG
+                        stencil (Sec. 3.3) and the condition numbers of the chosen ones run on
+                        the GPU (one warp per stencil), the candidates being enumerated on host
+                        threads; 0, everything on host threads.  Same stencils either way,
+                        coefficients equal to rounding. */
 } ccm_params;
 
 typedef struct {
@@ -136,7 +147,7 @@ typedef struct ccm_group ccm_group;
 
 /* Fill p with the defaults: omega 0.7, nu1 = nu2 = 3, theta 0.3, coarsest 16, CCM_MIXED,
  * rtol 1e-10, max_iter 100, ras_passes 1, ras_block 64, ras_overlap 32, nthreads 0,
- * ras_exact 0, inner_cycles 3, smoother 1, coarse_n 0, batch 1, cycle 0. */
+ * ras_exact 0, inner_cycles 3, smoother 1, coarse_n 0, batch 1, cycle 0, setup_device 1. */
 int ccm_default_params(ccm_params* p);
 
 /* Host setup (Sec. 3.1 - 3.4, Sec. 4): cut cells and moments (Green's formula, Sec. 2.4),
@@ -168,6 +179,14 @@ int ccm_boundary_segments(const ccm_handle* h, int32_t* cell, int32_t* bc, doubl
  * 2 n_segments): (1, 0) for Dirichlet, (0, 1) for Neumann, the curve's robin[] for Robin.
  * The boundary datum g of a segment is the average of that operator applied to u.  Blocking. */
 int ccm_boundary_robin(const ccm_handle* h, double* gamma);
+
+/* Fitted rows of level `level` of the handle (host arrays, any may be NULL; call with NULL
+ * arrays to read *n_rows first): cell[n] the row's cell, cols[n][15] its stencil cells
+ * (linear indices of that level's grid), beta[n][15] the coefficients and nb[n] the boundary
+ * coefficient in physical units, seg[n] the boundary segment or -1.  The same layout as
+ * ccm_host_rows, so that a handle's setup can be compared with the host-only one. */
+int ccm_level_rows(const ccm_handle* h, int level, int64_t* n_rows, int32_t* cell, int32_t* cols, double* beta,
+                   double* nb, int32_t* seg);
 
 /* Quadrature rules that reproduce the averages the discretisation expects (Sec. 3.2,
  * eq. iteratedIntegral): for every non-pure non-empty cell, nodes and weights whose weighted

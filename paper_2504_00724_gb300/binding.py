@@ -11,7 +11,7 @@ import numpy as np
 HERE = os.path.dirname(os.path.abspath(__file__))
 LIBPATH = os.path.join(HERE, "libccm.so")
 
-CCM_CIRCLE, CCM_ELLIPSE, CCM_STAR = 1, 2, 3
+CCM_CIRCLE, CCM_ELLIPSE, CCM_STAR, CCM_POLYGON = 1, 2, 3, 4
 CCM_NONE, CCM_DIRICHLET, CCM_NEUMANN, CCM_ROBIN = 0, 1, 2, 3
 CCM_FP64, CCM_MIXED = 0, 1
 CCM_PROF_OFF, CCM_PROF_RESID_FP64, CCM_PROF_SMO1_FP32, CCM_PROF_SMO1_FP64, CCM_PROF_VCYCLE = 0, 1, 2, 3, 4
@@ -26,7 +26,8 @@ class CcmError(RuntimeError):
 
 class ccm_curve(ctypes.Structure):
     _fields_ = [("kind", ctypes.c_int), ("p", ctypes.c_double * 8), ("orient", ctypes.c_int),
-                ("bc", ctypes.c_int), ("robin", ctypes.c_double * 2)]
+                ("bc", ctypes.c_int), ("robin", ctypes.c_double * 2), ("npts", ctypes.c_int),
+                ("pts", ctypes.POINTER(ctypes.c_double))]
 
 
 class ccm_problem(ctypes.Structure):
@@ -43,7 +44,7 @@ class ccm_params(ctypes.Structure):
                 ("ras_block", ctypes.c_int), ("ras_overlap", ctypes.c_int), ("nthreads", ctypes.c_int),
                 ("ras_exact", ctypes.c_int), ("inner_cycles", ctypes.c_int), ("smoother", ctypes.c_int),
                 ("coarse_n", ctypes.c_int), ("batch", ctypes.c_int),
-                ("cycle", ctypes.c_int)]
+                ("cycle", ctypes.c_int), ("setup_device", ctypes.c_int)]
 
 
 class ccm_info(ctypes.Structure):
@@ -72,6 +73,7 @@ _SIGS = {
     "ccm_cell_map": (I, [P, P, P, P, P]),
     "ccm_boundary_segments": (I, [P, P, P, P]),
     "ccm_boundary_robin": (I, [P, P]),
+    "ccm_level_rows": (I, [P, I, I64P, P, P, P, P, P]),
     "ccm_quadrature": (I, [P, I64P, I64P, P, P, P, P, P, P, P]),
     "ccm_apply": (I, [P, P, P, P, I, P]),
     "ccm_apply_T": (I, [P, P, P, P, I, P]),
@@ -147,17 +149,24 @@ def problem_struct(prob) -> tuple:
     """ccm_problem from a workloads.Problem-like object (keeps the curve array alive)."""
     n = len(prob.curves)
     arr = (ccm_curve * max(1, n))()
+    keep = [arr]
     for k, c in enumerate(prob.curves):
         arr[k].kind = int(c.kind)
-        for m, v in enumerate(c.params):
-            arr[k].p[m] = float(v)
+        if int(c.kind) == CCM_POLYGON:
+            pts = (ctypes.c_double * len(c.params))(*[float(v) for v in c.params])
+            keep.append(pts)
+            arr[k].npts = len(c.params) // 2
+            arr[k].pts = ctypes.cast(pts, ctypes.POINTER(ctypes.c_double))
+        else:
+            for m, v in enumerate(c.params):
+                arr[k].p[m] = float(v)
         arr[k].orient = int(c.orient)
         arr[k].bc = int(c.bc)
         g = getattr(c, "robin", (1.0, 0.0))
         arr[k].robin[0], arr[k].robin[1] = float(g[0]), float(g[1])
     s = ccm_problem(float(prob.a), float(prob.b), float(prob.c), float(prob.x0), float(prob.y0),
                     float(prob.h), int(prob.nx), int(prob.ny), int(prob.box_bc), n, arr)
-    return s, arr
+    return s, keep
 
 
 def _ptr(t) -> int:
@@ -218,6 +227,20 @@ class Solver:
         _check(lib().ccm_boundary_segments(self.h, cell.ctypes.data, bc.ctypes.data, ln.ctypes.data),
                "ccm_boundary_segments")
         return cell, bc, ln
+
+    def level_rows(self, level=0):
+        """Fitted rows of a level: (cell, cols[n,15], beta[n,15], nb, seg), physical units."""
+        n = ctypes.c_int64(0)
+        _check(lib().ccm_level_rows(self.h, level, ctypes.byref(n), None, None, None, None, None), "ccm_level_rows")
+        n2 = n.value
+        cell = np.zeros(n2, np.int32)
+        cols = np.zeros((n2, 15), np.int32)
+        beta = np.zeros((n2, 15))
+        nb = np.zeros(n2)
+        seg = np.zeros(n2, np.int32)
+        _check(lib().ccm_level_rows(self.h, level, None, cell.ctypes.data, cols.ctypes.data, beta.ctypes.data,
+                                    nb.ctypes.data, seg.ctypes.data), "ccm_level_rows")
+        return cell, cols, beta, nb, seg
 
     def boundary_operator(self) -> np.ndarray:
         """(gamma1, gamma2) per segment [n_segments, 2]: the segment's boundary operator is

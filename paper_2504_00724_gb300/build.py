@@ -23,7 +23,7 @@ NVCC = os.environ.get("NVCC", "/usr/local/cuda/bin/nvcc")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 CXX_SOURCES = ["geometry.cpp", "discretize.cpp", "hierarchy.cpp", "host_api.cpp"]
-CU_SOURCES = ["solver.cu"]
+CU_SOURCES = ["solver.cu", "fitdev.cu"]
 
 
 def _sources():

@@ -332,7 +332,7 @@ void fit(const CutLevel& cg, int i, int j, const std::array<int, 15>& cells, dou
 }  // namespace
 
 int discretize_level(const CutLevel& cg, double a, double b, double c, int nthreads, Rows& rows,
-                     std::string& err) {
+                     std::string& err, FitBatcher* fb) {
   const int nx = cg.nx, ny = cg.ny;
   const long N = (long)nx * ny;
   rows.regular.assign(N, 0);
@@ -364,6 +364,78 @@ int discretize_level(const CutLevel& cg, double a, double b, double c, int nthre
   std::atomic<size_t> next{0};
   int nt = nthreads > 0 ? nthreads : (int)std::max(1u, std::thread::hardware_concurrency());
   nt = std::min<int>(nt, std::max<size_t>(1, n2 / 16 + 1));
+  // N g enters the scaled rows (h^2 L) with the column's scale undone: h^0 (Dirichlet),
+  // h (Neumann), 1 / (|gamma1| + |gamma2| / h) (Robin)
+  auto set_boundary = [&](size_t r, int lin, double b15) {
+    auto sit = cg.seg_of.find(lin);
+    if (sit == cg.seg_of.end()) return;
+    const int s = sit->second, bc = cg.seg_bc[s];
+    rows.seg[r] = s;
+    rows.nb[r] = bc == CCM_DIRICHLET ? b15
+                 : bc == CCM_NEUMANN ? b15 * cg.h
+                                     : b15 / robin_norm(cg.seg_gamma[s][0], cg.seg_gamma[s][1], cg.h);
+  };
+  if (fb && n2 > 0) {
+    // candidates of every row on the host threads, all fits in one batch, the same choice
+    std::vector<std::vector<std::array<int, 15>>> cands(n2);
+    std::vector<std::thread> th;
+    for (int t = 0; t < nt; ++t)
+      th.emplace_back([&]() {
+        while (true) {
+          const size_t r = next.fetch_add(1);
+          if (r >= n2 || status.load() != CCM_OK) break;
+          const int lin = rows.irr[r];
+          if (!plg_candidates(cg, lin % nx, lin / nx, cands[r])) status.store(CCM_EPLG);
+        }
+      });
+    for (auto& t : th) t.join();
+    if (status.load() != CCM_OK) {
+      err = "no poised PLG stencil within radius 5";
+      return CCM_EPLG;
+    }
+    std::vector<size_t> first(n2 + 1, 0);
+    for (size_t r = 0; r < n2; ++r) first[r + 1] = first[r] + cands[r].size();
+    std::vector<int32_t> prow(first[n2]);
+    std::vector<std::array<int, 15>> pc(first[n2]);
+    for (size_t r = 0; r < n2; ++r)
+      for (size_t k = 0; k < cands[r].size(); ++k) {
+        prow[first[r] + k] = rows.irr[r];
+        pc[first[r] + k] = cands[r][k];
+      }
+    std::vector<double> beta, norm;
+    std::vector<uint8_t> ok;
+    int rc = fb->fit(cg, a, b, c, prow, pc, beta, norm, ok);
+    if (rc) {
+      err = "device fits failed";
+      return rc;
+    }
+    std::vector<int32_t> crow(n2);
+    std::vector<std::array<int, 15>> chosen(n2);
+    for (size_t r = 0; r < n2; ++r) {
+      long bk = -1;
+      for (size_t k = first[r]; k < first[r + 1]; ++k) {
+        if (!ok[k]) continue;
+        if (bk < 0 || norm[k] < norm[bk] * (1.0 - 1e-9)) bk = (long)k;
+      }
+      if (bk < 0) {
+        err = "singular weighted normal equations";
+        return CCM_ESINGULAR;
+      }
+      rows.cols[r] = pc[bk];
+      for (int q = 0; q < 15; ++q) rows.beta[r][q] = beta[16 * bk + q];
+      set_boundary(r, rows.irr[r], beta[16 * bk + 15]);
+      crow[r] = rows.irr[r];
+      chosen[r] = pc[bk];
+    }
+    rc = fb->cond(cg, crow, chosen, conds);
+    if (rc) {
+      err = "device fits failed";
+      return rc;
+    }
+    rows.cond_max = 0;
+    for (double v : conds) rows.cond_max = std::max(rows.cond_max, v);
+    return CCM_OK;
+  }
   auto worker = [&]() {
     std::vector<std::array<int, 15>> cands;
     FitOut fo, best;
@@ -390,16 +462,7 @@ int discretize_level(const CutLevel& cg, double a, double b, double c, int nthre
       }
       rows.cols[r] = cands[bk];
       for (int q = 0; q < 15; ++q) rows.beta[r][q] = best.beta[q];
-      auto sit = cg.seg_of.find(lin);
-      if (sit != cg.seg_of.end()) {
-        rows.seg[r] = sit->second;
-        // N g enters the scaled rows (h^2 L) with the column's scale undone: h^0 (Dirichlet),
-        // h (Neumann), 1 / (|gamma1| + |gamma2| / h) (Robin)
-        const int s = sit->second, bc = cg.seg_bc[s];
-        rows.nb[r] = bc == CCM_DIRICHLET ? best.beta[15]
-                     : bc == CCM_NEUMANN ? best.beta[15] * cg.h
-                                         : best.beta[15] / robin_norm(cg.seg_gamma[s][0], cg.seg_gamma[s][1], cg.h);
-      }
+      set_boundary(r, lin, best.beta[15]);
       conds[r] = cond2(best.M15);
     }
   };

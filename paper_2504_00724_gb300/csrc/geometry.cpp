@@ -11,6 +11,8 @@
 // first, into the non-empty 4-neighbour with the longest common cut face (ties: larger
 // volume, then +x, -x, +y, -y).
 #include <algorithm>
+#include <atomic>
+#include <thread>
 #include <cmath>
 #include <cstring>
 #include <functional>
@@ -24,7 +26,50 @@ static const double TWO_PI = 6.283185307179586476925286766559;
 
 // ------------------------------------------------------------------ curves
 
+// edge of a polygon at parameter t: vertices a -> b and the position s in [0, 1) along it
+static void polygon_edge(const Curve& c, double t, int& a, int& b, double& s) {
+  const int n = (int)(c.V.size() / 2);
+  const double u = t * (n / (2 * M_PI));
+  const double k = std::floor(u);
+  s = u - k;
+  a = (int)(((long)k % n + n) % n);
+  b = (a + 1) % n;
+}
+
+void Curve::subintervals(double t0, double t1, std::vector<std::pair<double, double>>& out) const {
+  out.clear();
+  if (kind != CCM_POLYGON) {
+    out.push_back({t0, t1});
+    return;
+  }
+  const int n = (int)(V.size() / 2);
+  const double lo = std::min(t0, t1), hi = std::max(t0, t1);
+  std::vector<double> cuts;
+  for (int k = 0; k < n; ++k) {
+    const double b = 2 * M_PI * k / n;
+    double v = b + 2 * M_PI * std::ceil((lo - b) / (2 * M_PI));
+    for (; v < hi; v += 2 * M_PI)
+      if (v > lo) cuts.push_back(v);
+  }
+  std::sort(cuts.begin(), cuts.end());
+  if (t1 < t0) std::reverse(cuts.begin(), cuts.end());
+  double a = t0;
+  for (double v : cuts) {
+    out.push_back({a, v});
+    a = v;
+  }
+  out.push_back({a, t1});
+}
+
 void Curve::xy(double t, double& x, double& y) const {
+  if (kind == CCM_POLYGON) {
+    int a, b;
+    double s;
+    polygon_edge(*this, t, a, b, s);
+    x = V[2 * a] + (V[2 * b] - V[2 * a]) * s;
+    y = V[2 * a + 1] + (V[2 * b + 1] - V[2 * a + 1]) * s;
+    return;
+  }
   switch (kind) {
     case CCM_CIRCLE:
       x = p[0] + p[2] * std::cos(t);
@@ -46,6 +91,15 @@ void Curve::xy(double t, double& x, double& y) const {
 }
 
 void Curve::dxy(double t, double& x, double& y) const {
+  if (kind == CCM_POLYGON) {
+    int a, b;
+    double s;
+    polygon_edge(*this, t, a, b, s);
+    const double sc = (double)(V.size() / 2) / (2 * M_PI);
+    x = (V[2 * b] - V[2 * a]) * sc;
+    y = (V[2 * b + 1] - V[2 * a + 1]) * sc;
+    return;
+  }
   switch (kind) {
     case CCM_CIRCLE:
       x = -p[2] * std::sin(t);
@@ -68,6 +122,18 @@ void Curve::dxy(double t, double& x, double& y) const {
 }
 
 bool Curve::inside(double x, double y) const {
+  if (kind == CCM_POLYGON) {
+    // even-odd rule: a ray towards +x crosses the boundary an odd number of times
+    const int n = (int)(V.size() / 2);
+    bool in = false;
+    for (int k = 0; k < n; ++k) {
+      const double xa = V[2 * k], ya = V[2 * k + 1];
+      const double xb = V[2 * ((k + 1) % n)], yb = V[2 * ((k + 1) % n) + 1];
+      if (ya == yb) continue;
+      if ((ya > y) != (yb > y) && x < xa + (y - ya) * (xb - xa) / (yb - ya)) in = !in;
+    }
+    return in;
+  }
   switch (kind) {
     case CCM_CIRCLE: {
       double dx = x - p[0], dy = y - p[1];
@@ -195,17 +261,21 @@ static void piece_moments(const Piece& pc, const std::vector<Curve>& curves, dou
   }
   const Curve& c = curves[pc.curve];
   const GL& g = gl_arc();
-  double tm = 0.5 * (pc.t0 + pc.t1), tr = 0.5 * (pc.t1 - pc.t0);
-  for (int n = 0; n < GL_ARC; ++n) {
-    double t = tm + tr * g.x[n], x, y, dx, dy;
-    c.xy(t, x, y);
-    c.dxy(t, dx, dy);
-    double X = (x - xc) / h, Y = (y - yc) / h, wY = dy / h * tr * g.w[n];
-    double Xp[6] = {1, X, X * X, X * X * X, X * X * X * X, X * X * X * X * X};
-    double Yq[5] = {1, Y, Y * Y, Y * Y * Y, Y * Y * Y * Y};
-    for (int k = 0; k < NMOM; ++k) {
-      int p = mono_p(k), q = mono_q(k);
-      acc[k] += Xp[p + 1] / (p + 1) * Yq[q] * wY;
+  std::vector<std::pair<double, double>> parts;
+  c.subintervals(pc.t0, pc.t1, parts);
+  for (const auto& ab : parts) {
+    double tm = 0.5 * (ab.first + ab.second), tr = 0.5 * (ab.second - ab.first);
+    for (int n = 0; n < GL_ARC; ++n) {
+      double t = tm + tr * g.x[n], x, y, dx, dy;
+      c.xy(t, x, y);
+      c.dxy(t, dx, dy);
+      double X = (x - xc) / h, Y = (y - yc) / h, wY = dy / h * tr * g.w[n];
+      double Xp[6] = {1, X, X * X, X * X * X, X * X * X * X, X * X * X * X * X};
+      double Yq[5] = {1, Y, Y * Y, Y * Y * Y, Y * Y * Y * Y};
+      for (int k = 0; k < NMOM; ++k) {
+        int p = mono_p(k), q = mono_q(k);
+        acc[k] += Xp[p + 1] / (p + 1) * Yq[q] * wY;
+      }
     }
   }
 }
@@ -214,30 +284,7 @@ static void piece_moments(const Piece& pc, const std::vector<Curve>& curves, dou
 static void piece_bmoments(const Piece& pc, const std::vector<Curve>& curves, double xc, double yc,
                            double h, Mom& b0, Mom& bx, Mom& by) {
   const GL& g = gl_arc();
-  for (int n = 0; n < GL_ARC; ++n) {
-    double X, Y, ds, nx, ny;
-    if (!pc.arc) {
-      double s = 0.5 * (g.x[n] + 1.0);
-      double X0 = (pc.ax - xc) / h, Y0 = (pc.ay - yc) / h, X1 = (pc.bx - xc) / h, Y1 = (pc.by - yc) / h;
-      X = X0 + (X1 - X0) * s;
-      Y = Y0 + (Y1 - Y0) * s;
-      double L = std::hypot(X1 - X0, Y1 - Y0);
-      ds = L * 0.5 * g.w[n];
-      nx = (Y1 - Y0) / L;
-      ny = -(X1 - X0) / L;
-    } else {
-      const Curve& c = curves[pc.curve];
-      double tm = 0.5 * (pc.t0 + pc.t1), tr = 0.5 * (pc.t1 - pc.t0);
-      double t = tm + tr * g.x[n], x, y, dx, dy;
-      c.xy(t, x, y);
-      c.dxy(t, dx, dy);
-      X = (x - xc) / h;
-      Y = (y - yc) / h;
-      double sp = std::hypot(dx, dy), sg = tr > 0 ? 1.0 : -1.0;
-      ds = sp / h * std::fabs(tr) * g.w[n];
-      nx = sg * dy / sp;
-      ny = -sg * dx / sp;
-    }
+  auto add = [&](double X, double Y, double ds, double nx, double ny) {
     double Xp[5] = {1, X, X * X, X * X * X, X * X * X * X};
     double Yq[5] = {1, Y, Y * Y, Y * Y * Y, Y * Y * Y * Y};
     for (int k = 0; k < NMOM; ++k) {
@@ -245,6 +292,28 @@ static void piece_bmoments(const Piece& pc, const std::vector<Curve>& curves, do
       b0[k] += v;
       bx[k] += v * nx;
       by[k] += v * ny;
+    }
+  };
+  if (!pc.arc) {
+    for (int n = 0; n < GL_ARC; ++n) {
+      double s = 0.5 * (g.x[n] + 1.0);
+      double X0 = (pc.ax - xc) / h, Y0 = (pc.ay - yc) / h, X1 = (pc.bx - xc) / h, Y1 = (pc.by - yc) / h;
+      double L = std::hypot(X1 - X0, Y1 - Y0);
+      add(X0 + (X1 - X0) * s, Y0 + (Y1 - Y0) * s, L * 0.5 * g.w[n], (Y1 - Y0) / L, -(X1 - X0) / L);
+    }
+    return;
+  }
+  const Curve& c = curves[pc.curve];
+  std::vector<std::pair<double, double>> parts;
+  c.subintervals(pc.t0, pc.t1, parts);
+  for (const auto& ab : parts) {
+    double tm = 0.5 * (ab.first + ab.second), tr = 0.5 * (ab.second - ab.first);
+    for (int n = 0; n < GL_ARC; ++n) {
+      double t = tm + tr * g.x[n], x, y, dx, dy;
+      c.xy(t, x, y);
+      c.dxy(t, dx, dy);
+      double sp = std::hypot(dx, dy), sg = tr > 0 ? 1.0 : -1.0;
+      add((x - xc) / h, (y - yc) / h, sp / h * std::fabs(tr) * g.w[n], sg * dy / sp, -sg * dx / sp);
     }
   }
 }
@@ -387,9 +456,19 @@ int check_problem(const ccm_problem& prob) {
   if (prob.box_bc != CCM_NONE && prob.box_bc != CCM_DIRICHLET && prob.box_bc != CCM_NEUMANN) return CCM_EINVAL;
   for (int k = 0; k < prob.ncurves; ++k) {
     const ccm_curve& c = prob.curves[k];
-    if (c.kind < CCM_CIRCLE || c.kind > CCM_STAR || (c.orient != 1 && c.orient != -1) ||
+    if (c.kind < CCM_CIRCLE || c.kind > CCM_POLYGON || (c.orient != 1 && c.orient != -1) ||
         (c.bc != CCM_DIRICHLET && c.bc != CCM_NEUMANN && c.bc != CCM_ROBIN))
       return CCM_EINVAL;
+    if (c.kind == CCM_POLYGON) {
+      if (c.npts < 3 || !c.pts) return CCM_EINVAL;
+      double area2 = 0;
+      for (int v = 0; v < c.npts; ++v) {
+        const int w = (v + 1) % c.npts;
+        if (!std::isfinite(c.pts[2 * v]) || !std::isfinite(c.pts[2 * v + 1])) return CCM_EINVAL;
+        area2 += c.pts[2 * v] * c.pts[2 * w + 1] - c.pts[2 * w] * c.pts[2 * v + 1];
+      }
+      if (!(area2 > 0)) return CCM_EINVAL;      // counter-clockwise
+    }
     if (c.bc == CCM_ROBIN && (!std::isfinite(c.robin[0]) || !std::isfinite(c.robin[1]) ||
                               (c.robin[0] == 0.0 && c.robin[1] == 0.0)))
       return CCM_EINVAL;
@@ -412,6 +491,7 @@ int build_cut_level(const ccm_problem& prob, int nx, int ny, double h, double th
     std::memcpy(c.p, prob.curves[k].p, sizeof(c.p));
     c.orient = prob.curves[k].orient;
     c.bc = prob.curves[k].bc;
+    if (c.kind == CCM_POLYGON) c.V.assign(prob.curves[k].pts, prob.curves[k].pts + 2 * prob.curves[k].npts);
     if (c.bc == CCM_ROBIN) {
       c.robin[0] = prob.curves[k].robin[0];
       c.robin[1] = prob.curves[k].robin[1];
@@ -483,19 +563,30 @@ int build_cut_level(const ccm_problem& prob, int nx, int ny, double h, double th
     }
   }
 
-  // ---- classification of the other cells by their centres
+  // ---- classification of the other cells by their centres (rows over host threads; every
+  // cell's test is independent)
   cg.status.assign(N, ST_EMPTY);
   cg.iface.assign(N, 0);
-  for (int j = 0; j < ny; ++j)
-    for (int i = 0; i < nx; ++i) {
-      double x = cg.cx(i), y = cg.cy(j);
-      bool in = true;
-      for (const Curve& c : cg.curves) {
-        bool ins = c.inside(x, y);
-        if ((c.orient > 0) != ins) { in = false; break; }
-      }
-      cg.status[(long)j * nx + i] = in ? ST_PURE : ST_EMPTY;
-    }
+  {
+    std::atomic<int> next_row{0};
+    auto work = [&]() {
+      for (int j = next_row.fetch_add(1); j < ny; j = next_row.fetch_add(1))
+        for (int i = 0; i < nx; ++i) {
+          double x = cg.cx(i), y = cg.cy(j);
+          bool in = true;
+          for (const Curve& c : cg.curves) {
+            bool ins = c.inside(x, y);
+            if ((c.orient > 0) != ins) { in = false; break; }
+          }
+          cg.status[(long)j * nx + i] = in ? ST_PURE : ST_EMPTY;
+        }
+    };
+    const int nt = (int)std::min<long>(std::max(1u, std::thread::hardware_concurrency()), std::max(1L, (long)ny / 64));
+    std::vector<std::thread> th;
+    for (int t = 1; t < nt; ++t) th.emplace_back(work);
+    work();
+    for (auto& t : th) t.join();
+  }
   for (auto& kv : arcs) {
     cg.status[kv.first] = ST_CUT;
     cg.iface[kv.first] = 1;
@@ -794,27 +885,33 @@ void cell_quadrature(const CutLevel& cg, std::vector<int32_t>& cell, std::vector
     double xi0 = cg.cx(lin % cg.nx);
     for (const Region& r : cg.regions.at(lin)) {
       for (const Piece& pc : r.pieces) {
-        for (int n = 0; n < GL_ARC; ++n) {
-          double x, y, wy;
-          if (!pc.arc) {
-            if (pc.ay == pc.by) break;
-            double s = 0.5 * (g.x[n] + 1.0);
-            x = pc.ax + (pc.bx - pc.ax) * s;
-            y = pc.ay + (pc.by - pc.ay) * s;
-            wy = (pc.by - pc.ay) * 0.5 * g.w[n];
-          } else {
-            const Curve& c = cg.curves[pc.curve];
-            double tm = 0.5 * (pc.t0 + pc.t1), tr = 0.5 * (pc.t1 - pc.t0), dx, dy;
-            c.xy(tm + tr * g.x[n], x, y);
-            c.dxy(tm + tr * g.x[n], dx, dy);
-            wy = dy * tr * g.w[n];
-          }
+        auto add = [&](double x, double y, double wy) {
           double half = 0.5 * (x - xi0);
           for (size_t l = 0; l < inner.x.size(); ++l) {
             cell.push_back(lin);
             xy.push_back(xi0 + half * (inner.x[l] + 1.0));
             xy.push_back(y);
             w.push_back(inner.w[l] * half * wy);
+          }
+        };
+        if (!pc.arc) {
+          if (pc.ay == pc.by) continue;
+          for (int n = 0; n < GL_ARC; ++n) {
+            double s = 0.5 * (g.x[n] + 1.0);
+            add(pc.ax + (pc.bx - pc.ax) * s, pc.ay + (pc.by - pc.ay) * s, (pc.by - pc.ay) * 0.5 * g.w[n]);
+          }
+          continue;
+        }
+        const Curve& c = cg.curves[pc.curve];
+        std::vector<std::pair<double, double>> parts;
+        c.subintervals(pc.t0, pc.t1, parts);
+        for (const auto& ab : parts) {
+          double tm = 0.5 * (ab.first + ab.second), tr = 0.5 * (ab.second - ab.first);
+          for (int n = 0; n < GL_ARC; ++n) {
+            double x, y, dx, dy;
+            c.xy(tm + tr * g.x[n], x, y);
+            c.dxy(tm + tr * g.x[n], dx, dy);
+            add(x, y, dy * tr * g.w[n]);
           }
         }
       }
@@ -831,32 +928,35 @@ void boundary_quadrature(const CutLevel& cg, std::vector<int32_t>& seg, std::vec
   nrm.clear();
   for (size_t s = 0; s < cg.segs.size(); ++s) {
     for (const Piece& pc : cg.seg_pieces[s]) {
-      for (int n = 0; n < GL_ARC; ++n) {
-        double x, y, ds, nx, ny;
-        if (!pc.arc) {
-          double t = 0.5 * (g.x[n] + 1.0);
-          x = pc.ax + (pc.bx - pc.ax) * t;
-          y = pc.ay + (pc.by - pc.ay) * t;
-          double L = std::hypot(pc.bx - pc.ax, pc.by - pc.ay);
-          ds = L * 0.5 * g.w[n];
-          nx = (pc.by - pc.ay) / L;
-          ny = -(pc.bx - pc.ax) / L;
-        } else {
-          const Curve& c = cg.curves[pc.curve];
-          double tm = 0.5 * (pc.t0 + pc.t1), tr = 0.5 * (pc.t1 - pc.t0), dx, dy;
-          c.xy(tm + tr * g.x[n], x, y);
-          c.dxy(tm + tr * g.x[n], dx, dy);
-          double sp = std::hypot(dx, dy), sg = tr > 0 ? 1.0 : -1.0;
-          ds = sp * std::fabs(tr) * g.w[n];
-          nx = sg * dy / sp;
-          ny = -sg * dx / sp;
-        }
+      auto add = [&](double x, double y, double ds, double nx, double ny) {
         seg.push_back((int32_t)s);
         xy.push_back(x);
         xy.push_back(y);
         w.push_back(ds);
         nrm.push_back(nx);
         nrm.push_back(ny);
+      };
+      if (!pc.arc) {
+        for (int n = 0; n < GL_ARC; ++n) {
+          double t = 0.5 * (g.x[n] + 1.0);
+          double L = std::hypot(pc.bx - pc.ax, pc.by - pc.ay);
+          add(pc.ax + (pc.bx - pc.ax) * t, pc.ay + (pc.by - pc.ay) * t, L * 0.5 * g.w[n], (pc.by - pc.ay) / L,
+              -(pc.bx - pc.ax) / L);
+        }
+        continue;
+      }
+      const Curve& c = cg.curves[pc.curve];
+      std::vector<std::pair<double, double>> parts;
+      c.subintervals(pc.t0, pc.t1, parts);
+      for (const auto& ab : parts) {
+        double tm = 0.5 * (ab.first + ab.second), tr = 0.5 * (ab.second - ab.first);
+        for (int n = 0; n < GL_ARC; ++n) {
+          double x, y, dx, dy;
+          c.xy(tm + tr * g.x[n], x, y);
+          c.dxy(tm + tr * g.x[n], dx, dy);
+          double sp = std::hypot(dx, dy), sg = tr > 0 ? 1.0 : -1.0;
+          add(x, y, sp * std::fabs(tr) * g.w[n], sg * dy / sp, -sg * dx / sp);
+        }
       }
     }
   }

@@ -473,7 +473,26 @@ static PackRows transpose_rows(const CutLevel& cg, const PackRows& F, const doub
   return T;
 }
 
-int build_hierarchy(const ccm_problem& prob, const ccm_params& par, Hierarchy& H, std::string& err) {
+int hierarchy_rows(const Hierarchy& H, int level, int32_t* cell, int32_t* cols, double* beta, double* nb,
+                   int32_t* seg) {
+  if (level < 0 || level >= (int)H.levels.size()) return CCM_EINVAL;
+  const HostLevel& L = H.levels[level];
+  const int n2 = L.n2;
+  const double ih2 = 1.0 / (L.h * L.h);
+  auto unpad = [&](int32_t p) { return (p / L.pitch - 2) * L.nx + (p % L.pitch - 2); };
+  for (int r = 0; r < n2; ++r) {
+    if (cell) cell[r] = unpad(L.irr_cell[r]);
+    for (int k = 0; k < 15; ++k) {
+      if (cols) cols[(long)r * 15 + k] = unpad(L.ell_col[(long)k * n2 + r]);
+      if (beta) beta[(long)r * 15 + k] = L.ell_val[(long)k * n2 + r] * ih2;
+    }
+    if (nb) nb[r] = L.nb[r] * ih2;
+    if (seg) seg[r] = L.seg[r];
+  }
+  return CCM_OK;
+}
+
+int build_hierarchy(const ccm_problem& prob, const ccm_params& par, Hierarchy& H, std::string& err, FitBatcher* fb) {
   H.a = prob.a;
   H.b = prob.b;
   H.c = prob.c;
@@ -490,7 +509,7 @@ int build_hierarchy(const ccm_problem& prob, const ccm_params& par, Hierarchy& H
     int rc = build_cut_level(prob, prob.nx >> m, prob.ny >> m, prob.h * (double)(1 << m), par.theta, cg, err);
     if (rc) return rc;
     Rows fit;
-    rc = discretize_level(cg, prob.a, prob.b, prob.c, par.nthreads, fit, err);
+    rc = discretize_level(cg, prob.a, prob.b, prob.c, par.nthreads, fit, err, fb);
     if (rc) return rc;
     if (m == 0) H.cond_max = fit.cond_max;
     PackRows rows;

@@ -75,7 +75,12 @@ struct Hierarchy {
   int nseg = 0;
 };
 
-int build_hierarchy(const ccm_problem& prob, const ccm_params& par, Hierarchy& H, std::string& err);
+int build_hierarchy(const ccm_problem& prob, const ccm_params& par, Hierarchy& H, std::string& err,
+                    FitBatcher* fb = nullptr);
+// fitted rows of a level in physical units and unpadded cell indices (the layout of
+// ccm_host_rows / ccm_level_rows)
+int hierarchy_rows(const Hierarchy& H, int level, int32_t* cell, int32_t* cols, double* beta, double* nb,
+                   int32_t* seg);
 // the hierarchy of the transposed operators (L^(m))^T, on the same geometry
 int build_transposed(const Hierarchy& H, const ccm_params& par, Hierarchy& T, std::string& err);
 bool dense_inverse(std::vector<double>& A, int n);   // in place, partial pivoting

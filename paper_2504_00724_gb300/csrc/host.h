@@ -2,6 +2,7 @@
 #pragma once
 
 #include <array>
+#include <memory>
 #include <cstdint>
 #include <string>
 #include <unordered_map>
@@ -38,9 +39,12 @@ struct Curve {
   int orient = -1;
   int bc = CCM_DIRICHLET;
   double robin[2] = {1.0, 0.0};     // CCM_ROBIN: gamma1, gamma2 of gamma1 u + gamma2 du/dn
+  std::vector<double> V;            // CCM_POLYGON: vertices (x, y) counter-clockwise
   void xy(double t, double& x, double& y) const;
   void dxy(double t, double& x, double& y) const;
   bool inside(double x, double y) const;   // strictly inside the closed curve
+  // [t0, t1] (either direction) cut at the curve's kinks, in the order of traversal
+  void subintervals(double t0, double t1, std::vector<std::pair<double, double>>& out) const;
 };
 
 // A piece of a cut-cell boundary in global coordinates, traversed with Omega on its left.
@@ -105,9 +109,30 @@ void gauss_legendre(int n, std::vector<double>& x, std::vector<double>& w);
 int check_problem(const ccm_problem& prob);
 int build_cut_level(const ccm_problem& prob, int nx, int ny, double h, double theta, CutLevel& out,
                     std::string& err);
+// Fits of many (fitted row, candidate PLG stencil) pairs in one call, for a setup that runs
+// them off the host threads (fitdev.cu).  Pair k fits the row of cell row_cell[k] over the 15
+// cells cand[k] with the host fit's arithmetic (to rounding): beta[16 k + q], norm[k] (the
+// weighted norm the stencil choice compares) and ok[k] (0: the normal equations are not
+// positive definite).  cond() writes the 2-norm condition number of each pair's 15 x 15 FV
+// sample matrix.  Both return CCM_OK or a CCM_* error code.
+struct FitBatcher {
+  virtual ~FitBatcher() = default;
+  virtual int fit(const CutLevel& cg, double a, double b, double c, const std::vector<int32_t>& row_cell,
+                  const std::vector<std::array<int, 15>>& cand, std::vector<double>& beta, std::vector<double>& norm,
+                  std::vector<uint8_t>& ok) = 0;
+  virtual int cond(const CutLevel& cg, const std::vector<int32_t>& row_cell,
+                   const std::vector<std::array<int, 15>>& cand, std::vector<double>& cond) = 0;
+};
+
+// fitdev.cu: the batched fits on the current CUDA device
+std::unique_ptr<FitBatcher> make_device_fitter();
+
 // discretize.cpp
+// Rows of a level (Sec. 3.2 regular stencil, Sec. 3.3 fitted rows).  With fb, the candidate
+// stencils are enumerated on host threads and their fits run through fb; the choice rule is
+// the same.
 int discretize_level(const CutLevel& cg, double a, double b, double c, int nthreads, Rows& rows,
-                     std::string& err);
+                     std::string& err, FitBatcher* fb = nullptr);
 void regular_stencil(double a, double b, double c, double w[5][5]);
 // quadrature helpers for callers (geometry.cpp)
 void cell_quadrature(const CutLevel& cg, std::vector<int32_t>& cell, std::vector<double>& xy,

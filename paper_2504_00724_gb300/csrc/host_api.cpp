@@ -40,21 +40,8 @@ int ccm_host_level_sizes(const ccm_host_setup* s, int level, int* nx, int* ny, i
 
 int ccm_host_rows(const ccm_host_setup* s, int level, int32_t* cell, int32_t* cols, double* beta, double* nb,
                   int32_t* seg) {
-  if (!s || level < 0 || level >= (int)s->H.levels.size()) return CCM_EINVAL;
-  const ccm::HostLevel& L = s->H.levels[level];
-  const int n2 = L.n2;
-  const double ih2 = 1.0 / (L.h * L.h);
-  auto unpad = [&](int32_t p) { return (p / L.pitch - 2) * L.nx + (p % L.pitch - 2); };
-  for (int r = 0; r < n2; ++r) {
-    if (cell) cell[r] = unpad(L.irr_cell[r]);
-    for (int k = 0; k < 15; ++k) {
-      if (cols) cols[(long)r * 15 + k] = unpad(L.ell_col[(long)k * n2 + r]);
-      if (beta) beta[(long)r * 15 + k] = L.ell_val[(long)k * n2 + r] * ih2;
-    }
-    if (nb) nb[r] = L.nb[r] * ih2;
-    if (seg) seg[r] = L.seg[r];
-  }
-  return CCM_OK;
+  if (!s) return CCM_EINVAL;
+  return ccm::hierarchy_rows(s->H, level, cell, cols, beta, nb, seg);
 }
 
 int ccm_host_cell_map(const ccm_host_setup* s, int level, int8_t* status, int32_t* owner, int8_t* regular,

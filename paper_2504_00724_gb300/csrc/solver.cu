@@ -1101,6 +1101,7 @@ int ccm_default_params(ccm_params* p) {
   p->coarse_n = 0;
   p->batch = 1;
   p->cycle = 0;
+  p->setup_device = 1;
   return CCM_OK;
 }
 
@@ -1146,7 +1147,9 @@ int ccm_setup(const ccm_problem* prob, const ccm_params* params, ccm_handle** ou
   std::string err;
   int rc;
   try {
-    rc = build_hierarchy(*prob, par, h->H, err);
+    std::unique_ptr<FitBatcher> fb;
+    if (par.setup_device) fb = make_device_fitter();
+    rc = build_hierarchy(*prob, par, h->H, err, fb.get());
   } catch (const std::bad_alloc&) {
     return CCM_ENOMEM;
   }
@@ -1219,6 +1222,13 @@ int ccm_boundary_segments(const ccm_handle* h, int32_t* cell, int32_t* bc, doubl
     if (length) length[s] = c.bm0[s][0] * c.h;
   }
   return CCM_OK;
+}
+
+int ccm_level_rows(const ccm_handle* h, int level, int64_t* n_rows, int32_t* cell, int32_t* cols, double* beta,
+                   double* nb, int32_t* seg) {
+  if (!h || level < 0 || level >= (int)h->H.levels.size()) return CCM_EINVAL;
+  if (n_rows) *n_rows = h->H.levels[level].n2;
+  return hierarchy_rows(h->H, level, cell, cols, beta, nb, seg);
 }
 
 int ccm_boundary_robin(const ccm_handle* h, double* gamma) {
