@@ -16,7 +16,7 @@ from typing import Callable
 
 import numpy as np
 
-from .geometry import CutGrid, PURE, CUT, EMPTY, DIRICHLET, NEUMANN, GL_ARC, GL_INNER
+from .geometry import CutGrid, PURE, CUT, EMPTY, DIRICHLET, NEUMANN, GL_ARC, GL_INNER, subintervals
 
 _G5X, _G5W = np.polynomial.legendre.leggauss(5)
 _GAX, _GAW = np.polynomial.legendre.leggauss(GL_ARC)
@@ -35,13 +35,17 @@ def _piece_nodes(cg: CutGrid, pc):
         n = ((pc.P1[1] - pc.P0[1]) / L, -(pc.P1[0] - pc.P0[0]) / L)
         return x, y, dyw, dsw, (np.full_like(x, n[0]), np.full_like(x, n[1]))
     c = cg.curves[pc.curve]
-    tm, tr = 0.5 * (pc.t0 + pc.t1), 0.5 * (pc.t1 - pc.t0)
-    t = tm + tr * _GAX
-    x, y = c.xy(t)
-    dx, dy = c.dxy(t)
-    sp_ = np.hypot(dx, dy)
-    sgn = 1.0 if tr > 0 else -1.0
-    return x, y, dy * tr * _GAW, sp_ * abs(tr) * _GAW, (sgn * dy / sp_, -sgn * dx / sp_)
+    parts = []
+    for (a, b) in subintervals(c, pc.t0, pc.t1):      # one Gauss rule per smooth part
+        tm, tr = 0.5 * (a + b), 0.5 * (b - a)
+        t = tm + tr * _GAX
+        x, y = c.xy(t)
+        dx, dy = c.dxy(t)
+        sp_ = np.hypot(dx, dy)
+        sgn = 1.0 if tr > 0 else -1.0
+        parts.append((x, y, dy * tr * _GAW, sp_ * abs(tr) * _GAW, sgn * dy / sp_, -sgn * dx / sp_))
+    x, y, dyw, dsw, n0, n1 = (np.concatenate([pt[m] for pt in parts]) for m in range(6))
+    return x, y, dyw, dsw, (n0, n1)
 
 
 def region_integral(cg: CutGrid, regions, f: Callable, xi0: float) -> float:

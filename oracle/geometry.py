@@ -32,7 +32,7 @@ from typing import Dict, List, Tuple
 import numpy as np
 from scipy.optimize import brentq
 
-CIRCLE, ELLIPSE, STAR = 1, 2, 3
+CIRCLE, ELLIPSE, STAR, POLYGON = 1, 2, 3, 4
 NONE, DIRICHLET, NEUMANN, ROBIN = 0, 1, 2, 3
 EMPTY, PURE, CUT = 0, 1, 2
 
@@ -51,11 +51,37 @@ class GeometryError(Exception):
 # ------------------------------------------------------------------ curves
 
 class OCurve:
-    """Closed parametric curve gamma(t), t in [0, 2 pi), counter-clockwise."""
+    """Closed parametric curve gamma(t), t in [0, 2 pi), counter-clockwise.
+
+    POLYGON: params = (x0, y0, x1, y1, ...), n >= 3 vertices in counter-clockwise order; edge
+    k is traversed for t in [2 pi k / n, 2 pi (k + 1) / n) at constant speed, so the curve
+    has a kink at every t = 2 pi k / n (breaks())."""
 
     def __init__(self, kind, params, orient, bc, robin=(1.0, 0.0)):
         self.kind, self.p, self.orient, self.bc = int(kind), tuple(float(v) for v in params), int(orient), int(bc)
         self.robin = (float(robin[0]), float(robin[1]))   # gamma1, gamma2 (Sec. 3.3, the Robin N)
+        if self.kind == POLYGON:
+            self.V = np.array(self.p, dtype=np.float64).reshape(-1, 2)
+            if len(self.V) < 3:
+                raise GeometryError("a polygon needs three vertices")
+            x, y = self.V[:, 0], self.V[:, 1]
+            if np.sum(x * np.roll(y, -1) - np.roll(x, -1) * y) <= 0.0:
+                raise GeometryError("polygon vertices must run counter-clockwise")
+
+    def breaks(self):
+        """Parameters in [0, 2 pi) where gamma is not smooth."""
+        if self.kind == POLYGON:
+            n = len(self.V)
+            return [2 * math.pi * k / n for k in range(n)]
+        return []
+
+    def _edge(self, t):
+        n = len(self.V)
+        u = np.asarray(t, dtype=np.float64) * (n / (2 * math.pi))
+        k = np.floor(u)
+        s = u - k
+        k = k.astype(np.int64) % n
+        return k, (k + 1) % n, s, n
 
     def xy(self, t):
         t = np.asarray(t, dtype=np.float64)
@@ -70,6 +96,10 @@ class OCurve:
             cx, cy, r0, amp, k = p
             r = r0 + amp * np.cos(k * t)
             return cx + r * np.cos(t), cy + r * np.sin(t)
+        if self.kind == POLYGON:
+            a, b, s, _ = self._edge(t)
+            A, B = self.V[a], self.V[b]
+            return A[..., 0] + (B[..., 0] - A[..., 0]) * s, A[..., 1] + (B[..., 1] - A[..., 1]) * s
         raise GeometryError("unknown curve kind")
 
     def dxy(self, t):
@@ -86,6 +116,11 @@ class OCurve:
             r = r0 + amp * np.cos(k * t)
             dr = -amp * k * np.sin(k * t)
             return dr * np.cos(t) - r * np.sin(t), dr * np.sin(t) + r * np.cos(t)
+        if self.kind == POLYGON:
+            a, b, _, n = self._edge(t)
+            A, B = self.V[a], self.V[b]
+            sc = n / (2 * math.pi)
+            return (B[..., 0] - A[..., 0]) * sc, (B[..., 1] - A[..., 1]) * sc
         raise GeometryError("unknown curve kind")
 
     def inside(self, x, y):
@@ -104,7 +139,41 @@ class OCurve:
             dx, dy = x - cx, y - cy
             th = np.arctan2(dy, dx)
             return np.hypot(dx, dy) < r0 + amp * np.cos(k * th)
+        if self.kind == POLYGON:
+            # even-odd rule: a ray towards +x crosses the boundary an odd number of times
+            x = np.asarray(x, dtype=np.float64)
+            y = np.asarray(y, dtype=np.float64)
+            ins = np.zeros(np.broadcast(x, y).shape, dtype=bool)
+            n = len(self.V)
+            for k in range(n):
+                (xa, ya), (xb, yb) = self.V[k], self.V[(k + 1) % n]
+                if ya == yb:
+                    continue
+                hit = (ya > y) != (yb > y)
+                xs = xa + (y - ya) * (xb - xa) / (yb - ya)
+                ins ^= hit & (x < xs)
+            return ins
         raise GeometryError("unknown curve kind")
+
+
+def subintervals(c: OCurve, t0: float, t1: float):
+    """[t0, t1] (either direction) cut at the curve's kinks, in the order of traversal, so
+    that a Gauss rule on each part integrates a smooth integrand."""
+    br = c.breaks()
+    if not br:
+        return [(t0, t1)]
+    lo, hi = min(t0, t1), max(t0, t1)
+    cuts = []
+    for b in br:
+        m = math.ceil((lo - b) / (2 * math.pi))
+        v = b + 2 * math.pi * m
+        while v < hi:
+            if v > lo:
+                cuts.append(v)
+            v += 2 * math.pi
+    cuts.sort(reverse=t1 < t0)
+    pts = [t0] + cuts + [t1]
+    return [(pts[k], pts[k + 1]) for k in range(len(pts) - 1)]
 
 
 def in_omega(prob, curves, x, y):
@@ -232,14 +301,15 @@ def piece_moments(pc: Piece, curves, xc, yc, h) -> np.ndarray:
             out[k] = np.sum(X ** (p + 1) / (p + 1) * Y ** q * dY)
         return out
     c = curves[pc.curve]
-    tm, tr = 0.5 * (pc.t0 + pc.t1), 0.5 * (pc.t1 - pc.t0)
-    t = tm + tr * _GLX
-    x, y = c.xy(t)
-    _, dy = c.dxy(t)
-    X, Y = (x - xc) / h, (y - yc) / h
-    dY = dy / h * tr * _GLW
-    for k, (p, q) in enumerate(EXPS):
-        out[k] = np.sum(X ** (p + 1) / (p + 1) * Y ** q * dY)
+    for (a, b) in subintervals(c, pc.t0, pc.t1):
+        tm, tr = 0.5 * (a + b), 0.5 * (b - a)
+        t = tm + tr * _GLX
+        x, y = c.xy(t)
+        _, dy = c.dxy(t)
+        X, Y = (x - xc) / h, (y - yc) / h
+        dY = dy / h * tr * _GLW
+        for k, (p, q) in enumerate(EXPS):
+            out[k] += np.sum(X ** (p + 1) / (p + 1) * Y ** q * dY)
     return out
 
 
@@ -262,15 +332,16 @@ def piece_boundary_moments(pc: Piece, curves, xc, yc, h):
         ny_ = np.full_like(X, ny_)
     else:
         c = curves[pc.curve]
-        tm, tr = 0.5 * (pc.t0 + pc.t1), 0.5 * (pc.t1 - pc.t0)
-        t = tm + tr * _GLX
-        x, y = c.xy(t)
-        dx, dy = c.dxy(t)
-        X, Y = (x - xc) / h, (y - yc) / h
-        sp = np.hypot(dx, dy)
-        sgn = 1.0 if tr > 0 else -1.0
-        ds = sp / h * abs(tr) * _GLW
-        nx_, ny_ = sgn * dy / sp, -sgn * dx / sp
+        parts = []
+        for (a, b) in subintervals(c, pc.t0, pc.t1):
+            tm, tr = 0.5 * (a + b), 0.5 * (b - a)
+            t = tm + tr * _GLX
+            x, y = c.xy(t)
+            dx, dy = c.dxy(t)
+            sp = np.hypot(dx, dy)
+            sgn = 1.0 if tr > 0 else -1.0
+            parts.append(((x - xc) / h, (y - yc) / h, sp / h * abs(tr) * _GLW, sgn * dy / sp, -sgn * dx / sp))
+        X, Y, ds, nx_, ny_ = (np.concatenate([pt[m] for pt in parts]) for m in range(5))
     b0, bx, by = np.zeros(15), np.zeros(15), np.zeros(15)
     for k, (p, q) in enumerate(EXPS):
         mono = X ** p * Y ** q * ds

@@ -55,6 +55,8 @@ def _error(prob, mms, precision):
 
 CASES = {
     "problem1_flower": (W.paper_problem1, W.mms_problem1, "paper_problem1.txt", "", 3.0, (40, 80, 160)),
+    "problem3_rotated": (W.paper_problem3_rotated, W.mms_problem3_rotated, "paper_problem3_rotated.txt", "", 3.0,
+                         (64, 128, 256)),
     "problem2_DD": (lambda n: W.paper_problem2(n, W.DIRICHLET), W.mms_sinsin, "paper_problem2.txt", "DD", 5.0,
                     (64, 128, 256)),
     "problem2_DN": (lambda n: W.paper_problem2(n, W.NEUMANN), W.mms_sinsin, "paper_problem2.txt", "DN", 5.0,

@@ -21,6 +21,7 @@ CASES = {
     "robin64_cross": lambda: W.disk_robin(64, (1.0, 2.0), abc=(1.0, 0.5, 2.0)),
     "problem1_flower80": lambda: W.paper_problem1(80),
     "problem2_ellipse64_neumann": lambda: W.paper_problem2(64, W.NEUMANN),
+    "problem3_rotated_box64": lambda: W.paper_problem3_rotated(64),
 }
 
 

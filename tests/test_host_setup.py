@@ -43,7 +43,8 @@ def _compare_level(hs, level, prob_level):
                                 lambda: W.three_ellipses(64), lambda: W.paper_problem2(32, W.NEUMANN),
                                 lambda: W.star(32, (1.25, -0.8660254037844386, 1.75)),
                                 lambda: W.paper_problem1(40), lambda: W.disk_robin(32),
-                                lambda: W.disk_robin(32, (2.0, -0.3), abc=(1.0, 0.5, 2.0))])
+                                lambda: W.disk_robin(32, (2.0, -0.3), abc=(1.0, 0.5, 2.0)),
+                                lambda: W.paper_problem3_rotated(32)])
 def test_finest_level_matches_oracle(mk):
     prob = mk()
     hs = P.HostSetup(prob)
@@ -56,6 +57,15 @@ def test_every_level_matches_oracle():
     hs = P.HostSetup(prob)
     nl = MG.n_levels(prob)
     for m in range(nl):
+        _compare_level(hs, m, MG.coarsen(prob, m))
+
+
+def test_polygon_every_level_matches_oracle():
+    """The rotated box of Problem 3, case (ii): a polygon curve whose corners fall inside cut
+    cells, (a, b, c) = (5/4, -sqrt(3)/2, 7/4), on every level."""
+    prob = W.paper_problem3_rotated(64)
+    hs = P.HostSetup(prob)
+    for m in range(MG.n_levels(prob)):
         _compare_level(hs, m, MG.coarsen(prob, m))
 
 
@@ -78,6 +88,12 @@ def test_invalid_problems_are_rejected():
     with pytest.raises(P.CcmError) as e:
         P.HostSetup(off)
     assert e.value.code == -2
+    clockwise = (0.2, 0.8, 0.8, 0.8, 0.8, 0.2, 0.2, 0.2)
+    for verts in (clockwise, clockwise[:4]):           # clockwise; two vertices only
+        bad = W.Problem(1.0, 0.0, 1.0, 0.0, 0.0, 1 / 32, 32, 32, W.NONE, [W.Curve(W.POLYGON, verts, +1, W.DIRICHLET)])
+        with pytest.raises(P.CcmError) as e:
+            P.HostSetup(bad)
+        assert e.value.code == -1
     for gamma in ((0.0, 0.0), (float("nan"), 1.0)):                                 # no Robin operator
         with pytest.raises(P.CcmError) as e:
             P.HostSetup(W.disk_robin(32, gamma))

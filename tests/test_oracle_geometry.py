@@ -131,3 +131,62 @@ def test_vertex_and_tangent_degeneracies():
     for n in (32, 64):
         cg = G.cut_cells(W.paper_problem2(n))
         assert abs(cg.vol.sum() * cg.h ** 2 - (1 - math.pi / 32)) < 1e-13
+
+
+def _polygon_moment(V, p, q):
+    """int over the polygon of x^p y^q by Green's formula edge by edge, int x^{p+1}/(p+1) y^q dy,
+    with a Gauss rule exact for the edge polynomial (independent of the cut cells)."""
+    z, w = np.polynomial.legendre.leggauss(8)
+    s = 0.5 * (z + 1.0)
+    tot = 0.0
+    n = len(V)
+    for k in range(n):
+        (xa, ya), (xb, yb) = V[k], V[(k + 1) % n]
+        x = xa + (xb - xa) * s
+        y = ya + (yb - ya) * s
+        tot += np.sum(x ** (p + 1) / (p + 1) * y ** q * (yb - ya) * 0.5 * w)
+    return tot
+
+
+@pytest.mark.parametrize("n", [16, 64])
+def test_rotated_box_polygon_moments(n):
+    """The box rotated by pi/6 (Problem 3, case (ii)): area 1, centroid (1/2, 1/2), and the
+    central moments of a unit square rotated by theta: int x^2 = 1/12, int x y = 0, int x^4 =
+    (c^4 + s^4)/80 + 6 c^2 s^2/144.  Every corner lies inside a cut cell, so this fails unless
+    the integrals along a piece are split at the corners."""
+    cg = G.cut_cells(W.paper_problem3_rotated(n))
+    c, s = math.cos(math.pi / 6), math.sin(math.pi / 6)
+    assert abs(cg.vol.sum() * cg.h ** 2 - 1.0) < 1e-13
+    assert abs(global_moment(cg, 1, 0) - 0.5) < 1e-13 and abs(global_moment(cg, 0, 1) - 0.5) < 1e-13
+    assert abs(global_moment(cg, 2, 0, 0.5, 0.5) - 1 / 12) < 1e-14
+    assert abs(global_moment(cg, 1, 1, 0.5, 0.5)) < 1e-14
+    want4 = (c ** 4 + s ** 4) / 80 + 6 * c * c * s * s / 144
+    assert abs(global_moment(cg, 4, 0, 0.5, 0.5) - want4) < 1e-14
+
+
+@pytest.mark.parametrize("n", [16, 64])
+def test_nonconvex_polygon_moments(n):
+    """A pentagon with a reflex corner (even-odd inside test, a non-convex cut cell): every
+    moment up to degree 4 equals the polygon's own Green integral."""
+    V = [(0.2, 0.2), (0.8, 0.2), (0.8, 0.8), (0.53, 0.45), (0.2, 0.8)]
+    prob = W.Problem(1.0, 0.0, 1.0, 0.0, 0.0, 1.0 / n, n, n, W.NONE,
+                     [W.Curve(W.POLYGON, tuple(v for xy in V for v in xy), +1, W.DIRICHLET)])
+    cg = G.cut_cells(prob)
+    for (p, q) in G.EXPS:
+        assert abs(global_moment(cg, p, q) - _polygon_moment(V, p, q)) < 1e-13, (p, q)
+    ins = G.OCurve(W.POLYGON, prob.curves[0].params, 1, W.DIRICHLET).inside
+    assert ins(0.5, 0.3) and not ins(0.53, 0.6) and ins(0.25, 0.7) and not ins(0.3, 0.7) and not ins(0.9, 0.5)
+
+
+def test_polygon_subintervals():
+    c = G.OCurve(W.POLYGON, (0, 0, 1, 0, 1, 1, 0, 1), 1, W.DIRICHLET)
+    q = math.pi / 2
+    assert G.subintervals(c, 0.1, 0.2) == [(0.1, 0.2)]
+    assert G.subintervals(c, 1.0, 2.0) == [(1.0, q), (q, 2.0)]
+    assert G.subintervals(c, 2.0, 1.0) == [(2.0, q), (q, 1.0)]                  # reversed traversal
+    parts = G.subintervals(c, 6.0, 6.6)                                          # across t = 2 pi
+    assert len(parts) == 2 and abs(parts[0][1] - 2 * math.pi) < 1e-15
+    x, y = c.xy(np.array([0.0, q / 2, q, 3 * q + q / 2]))
+    assert np.allclose(x, [0, 0.5, 1, 0]) and np.allclose(y, [0, 0, 0, 0.5])
+    with pytest.raises(G.GeometryError):
+        G.OCurve(W.POLYGON, (0, 0, 0, 1, 1, 1, 1, 0), 1, W.DIRICHLET)          # clockwise

@@ -25,7 +25,7 @@ from typing import Callable, List, Optional, Sequence
 
 import numpy as np
 
-CIRCLE, ELLIPSE, STAR = 1, 2, 3
+CIRCLE, ELLIPSE, STAR, POLYGON = 1, 2, 3, 4
 NONE, DIRICHLET, NEUMANN, ROBIN = 0, 1, 2, 3
 
 
@@ -350,6 +350,65 @@ def mms_problem3() -> Manufactured:
                         lambda x, y: -12 * np.cos(4 * x) * np.sin(3 * y),
                         lambda x, y: -9 * np.sin(4 * x) * np.cos(3 * y),
                         "sin 4x cos 3y")
+
+
+ROT3 = math.pi / 6          # Problem 3, case (ii): the box rotated counter-clockwise by pi/6
+ROT3_CENTRE = (0.5, 0.5)
+
+
+def paper_problem3_rotated(n: int) -> Problem:
+    """The paper's Problem 3, case (ii) (Sec. 5.1): the unit box rotated counter-clockwise by
+    pi/6 (here about its centre (1/2, 1/2)), with (a, b, c) = (5/4, -sqrt(3)/2, 7/4), the
+    coefficients of case (i) seen in the rotated frame; Dirichlet on the four sides.  The box
+    is a polygon curve; the grid has cell size 1/n on the square [-1/4, 5/4]^2 (3n/2 cells a
+    side), which holds the rotated box with a margin of 0.067."""
+    c, s = math.cos(ROT3), math.sin(ROT3)
+    cx, cy = ROT3_CENTRE
+    verts = []
+    for (X, Y) in ((-0.5, -0.5), (0.5, -0.5), (0.5, 0.5), (-0.5, 0.5)):
+        verts += [cx + c * X - s * Y, cy + s * X + c * Y]
+    m = 3 * n // 2
+    return Problem(1.25, -math.sqrt(3.0) / 2.0, 1.75, -0.25, -0.25, 1.0 / n, m, m, NONE,
+                   [Curve(POLYGON, tuple(verts), +1, DIRICHLET)], name=f"paper_problem3_rotated_{n}")
+
+
+def mms_problem3_rotated() -> Manufactured:
+    """Case (ii)'s exact solution: v(x') = sin(4 x1') cos(3 x2') of case (i) at the pre-image
+    x' = Q^T (x - c) + c of x under the rotation Q by pi/6 about c = (1/2, 1/2); its gradient
+    and Hessian are Q grad v and Q (Hess v) Q^T."""
+    c, s = math.cos(ROT3), math.sin(ROT3)
+    cx, cy = ROT3_CENTRE
+
+    def pre(x, y):
+        dx, dy = x - cx, y - cy
+        return cx + c * dx + s * dy, cy - s * dx + c * dy
+
+    def v(x, y):
+        X, Y = pre(x, y)
+        return np.sin(4 * X) * np.cos(3 * Y), 4 * np.cos(4 * X) * np.cos(3 * Y), -3 * np.sin(4 * X) * np.sin(3 * Y), \
+            -16 * np.sin(4 * X) * np.cos(3 * Y), -12 * np.cos(4 * X) * np.sin(3 * Y), -9 * np.sin(4 * X) * np.cos(3 * Y)
+
+    def ux(x, y):
+        _, v1, v2, *_ = v(x, y)
+        return c * v1 - s * v2
+
+    def uy(x, y):
+        _, v1, v2, *_ = v(x, y)
+        return s * v1 + c * v2
+
+    def uxx(x, y):
+        _, _, _, h11, h12, h22 = v(x, y)
+        return c * c * h11 - 2 * c * s * h12 + s * s * h22
+
+    def uxy(x, y):
+        _, _, _, h11, h12, h22 = v(x, y)
+        return c * s * (h11 - h22) + (c * c - s * s) * h12
+
+    def uyy(x, y):
+        _, _, _, h11, h12, h22 = v(x, y)
+        return s * s * h11 + 2 * c * s * h12 + c * c * h22
+
+    return Manufactured(lambda x, y: v(x, y)[0], ux, uy, uxx, uxy, uyy, "sin 4x' cos 3y', x' rotated by pi/6")
 
 
 def mms_sinsin() -> Manufactured:
