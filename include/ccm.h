@@ -42,8 +42,11 @@ extern "C" {
  *   CCM_POLYGON pts = (x0, y0, ..., x_{n-1}, y_{n-1}), npts = n >= 3 vertices in
  *               counter-clockwise order, no self-intersection; edge k is traversed at
  *               constant speed for t in [2 pi k / n, 2 pi (k + 1) / n), so corners are kinks
- *               of gamma and every integral along a piece is split there */
-enum { CCM_CIRCLE = 1, CCM_ELLIPSE = 2, CCM_STAR = 3, CCM_POLYGON = 4 };
+ *               of gamma and every integral along a piece is split there
+ *   CCM_SPLINE  pts, npts as for CCM_POLYGON: the periodic cubic spline through the points
+ *               (each coordinate), knots at the cumulative chord lengths scaled to [0, 2 pi)
+ *               (boundaries of the Yin sets Y_c, Sec. 2); integrals are split at the knots */
+enum { CCM_CIRCLE = 1, CCM_ELLIPSE = 2, CCM_STAR = 3, CCM_POLYGON = 4, CCM_SPLINE = 5 };
 /* boundary conditions (Sec. 3.3): NONE only for box_bc (the box is not part of dOmega);
  * ROBIN (curves only) is gamma1 u + gamma2 du/dn = g with the curve's robin[] = (gamma1,
  * gamma2), n the unit normal pointing out of Omega */
@@ -72,8 +75,8 @@ typedef struct {
   int orient;      /* +1: Omega lies inside the curve; -1: the curve bounds a hole */
   int bc;          /* CCM_DIRICHLET | CCM_NEUMANN | CCM_ROBIN */
   double robin[2]; /* CCM_ROBIN: (gamma1, gamma2), finite, not both zero; ignored otherwise */
-  int npts;        /* CCM_POLYGON: vertex count; ignored otherwise */
-  const double* pts; /* CCM_POLYGON: host array of 2 npts coordinates (copied by ccm_setup) */
+  int npts;        /* CCM_POLYGON, CCM_SPLINE: point count; ignored otherwise */
+  const double* pts; /* CCM_POLYGON, CCM_SPLINE: host array of 2 npts coordinates (copied) */
 } ccm_curve;
 
 typedef struct {

@@ -32,7 +32,7 @@ from typing import Dict, List, Tuple
 import numpy as np
 from scipy.optimize import brentq
 
-CIRCLE, ELLIPSE, STAR, POLYGON = 1, 2, 3, 4
+CIRCLE, ELLIPSE, STAR, POLYGON, SPLINE = 1, 2, 3, 4, 5
 NONE, DIRICHLET, NEUMANN, ROBIN = 0, 1, 2, 3
 EMPTY, PURE, CUT = 0, 1, 2
 
@@ -55,7 +55,11 @@ class OCurve:
 
     POLYGON: params = (x0, y0, x1, y1, ...), n >= 3 vertices in counter-clockwise order; edge
     k is traversed for t in [2 pi k / n, 2 pi (k + 1) / n) at constant speed, so the curve
-    has a kink at every t = 2 pi k / n (breaks())."""
+    has a kink at every t = 2 pi k / n (breaks()).
+    SPLINE: params = (x0, y0, ...), n >= 3 points in counter-clockwise order; the periodic
+    cubic spline interpolating them in each coordinate, with knots at the cumulative chord
+    lengths scaled to [0, 2 pi) (the curves of the Yin sets Y_c, Sec. 2).  The curve is C^2;
+    its knots are returned by breaks() so that a Gauss rule never spans two cubics."""
 
     def __init__(self, kind, params, orient, bc, robin=(1.0, 0.0)):
         self.kind, self.p, self.orient, self.bc = int(kind), tuple(float(v) for v in params), int(orient), int(bc)
@@ -67,13 +71,60 @@ class OCurve:
             x, y = self.V[:, 0], self.V[:, 1]
             if np.sum(x * np.roll(y, -1) - np.roll(x, -1) * y) <= 0.0:
                 raise GeometryError("polygon vertices must run counter-clockwise")
+        if self.kind == SPLINE:
+            self.V = np.array(self.p, dtype=np.float64).reshape(-1, 2)
+            n = len(self.V)
+            if n < 3:
+                raise GeometryError("a spline needs three points")
+            x, y = self.V[:, 0], self.V[:, 1]
+            if np.sum(x * np.roll(y, -1) - np.roll(x, -1) * y) <= 0.0:
+                raise GeometryError("spline points must run counter-clockwise")
+            chord = np.hypot(np.roll(x, -1) - x, np.roll(y, -1) - y)
+            if np.any(chord <= 0.0):
+                raise GeometryError("repeated spline point")
+            tau = np.concatenate([[0.0], np.cumsum(chord)])
+            self.knots = 2 * math.pi * tau / tau[-1]          # t_0 = 0 .. t_n = 2 pi
+            self.knots[-1] = 2 * math.pi
+            hk = np.diff(self.knots)
+            # second derivatives M of the periodic spline: for every knot k (indices mod n)
+            # h_{k-1} M_{k-1} + 2 (h_{k-1} + h_k) M_k + h_k M_{k+1}
+            #   = 6 ((v_{k+1} - v_k) / h_k - (v_k - v_{k-1}) / h_{k-1})
+            A = np.zeros((n, n))
+            for k in range(n):
+                A[k, (k - 1) % n] += hk[k - 1]
+                A[k, k] += 2 * (hk[k - 1] + hk[k])
+                A[k, (k + 1) % n] += hk[k]
+            self.M = []
+            for v in (x, y):
+                d = (np.roll(v, -1) - v) / hk
+                self.M.append(np.linalg.solve(A, 6 * (d - np.roll(d, 1))))
 
     def breaks(self):
         """Parameters in [0, 2 pi) where gamma is not smooth."""
         if self.kind == POLYGON:
             n = len(self.V)
             return [2 * math.pi * k / n for k in range(n)]
+        if self.kind == SPLINE:
+            return list(self.knots[:-1])
         return []
+
+    def _spline(self, t, deriv):
+        """The spline's coordinates (deriv 0) or their t-derivatives (deriv 1) at t."""
+        n = len(self.V)
+        tt = np.mod(np.asarray(t, dtype=np.float64), 2 * math.pi)
+        k = np.clip(np.searchsorted(self.knots, tt, side="right") - 1, 0, n - 1)
+        k1 = (k + 1) % n
+        hk = self.knots[k + 1] - self.knots[k]
+        a = (self.knots[k + 1] - tt) / hk
+        b = (tt - self.knots[k]) / hk
+        out = []
+        for c, M in enumerate(self.M):
+            v = self.V[:, c]
+            if deriv == 0:
+                out.append(a * v[k] + b * v[k1] + ((a ** 3 - a) * M[k] + (b ** 3 - b) * M[k1]) * hk * hk / 6)
+            else:
+                out.append((v[k1] - v[k]) / hk + ((1 - 3 * a * a) * M[k] + (3 * b * b - 1) * M[k1]) * hk / 6)
+        return out[0], out[1]
 
     def _edge(self, t):
         n = len(self.V)
@@ -100,6 +151,8 @@ class OCurve:
             a, b, s, _ = self._edge(t)
             A, B = self.V[a], self.V[b]
             return A[..., 0] + (B[..., 0] - A[..., 0]) * s, A[..., 1] + (B[..., 1] - A[..., 1]) * s
+        if self.kind == SPLINE:
+            return self._spline(t, 0)
         raise GeometryError("unknown curve kind")
 
     def dxy(self, t):
@@ -121,6 +174,8 @@ class OCurve:
             A, B = self.V[a], self.V[b]
             sc = n / (2 * math.pi)
             return (B[..., 0] - A[..., 0]) * sc, (B[..., 1] - A[..., 1]) * sc
+        if self.kind == SPLINE:
+            return self._spline(t, 1)
         raise GeometryError("unknown curve kind")
 
     def inside(self, x, y):
@@ -153,6 +208,14 @@ class OCurve:
                 xs = xa + (y - ya) * (xb - xa) / (yb - ya)
                 ins ^= hit & (x < xs)
             return ins
+        if self.kind == SPLINE:
+            # even-odd rule against the spline sampled 64 times per cubic: used only for
+            # centres of cells the curve does not enter (h/2 or more from the curve), far
+            # beyond the polyline's deviation from the spline
+            t = np.concatenate([np.linspace(self.knots[k], self.knots[k + 1], 64, endpoint=False)
+                                for k in range(len(self.V))])
+            px, py = self._spline(t, 0)
+            return OCurve(POLYGON, np.column_stack([px, py]).ravel(), 1, self.bc).inside(x, y)
         raise GeometryError("unknown curve kind")
 
 

@@ -11,7 +11,7 @@ import numpy as np
 HERE = os.path.dirname(os.path.abspath(__file__))
 LIBPATH = os.path.join(HERE, "libccm.so")
 
-CCM_CIRCLE, CCM_ELLIPSE, CCM_STAR, CCM_POLYGON = 1, 2, 3, 4
+CCM_CIRCLE, CCM_ELLIPSE, CCM_STAR, CCM_POLYGON, CCM_SPLINE = 1, 2, 3, 4, 5
 CCM_NONE, CCM_DIRICHLET, CCM_NEUMANN, CCM_ROBIN = 0, 1, 2, 3
 CCM_FP64, CCM_MIXED = 0, 1
 CCM_PROF_OFF, CCM_PROF_RESID_FP64, CCM_PROF_SMO1_FP32, CCM_PROF_SMO1_FP64, CCM_PROF_VCYCLE = 0, 1, 2, 3, 4
@@ -152,7 +152,7 @@ def problem_struct(prob) -> tuple:
     keep = [arr]
     for k, c in enumerate(prob.curves):
         arr[k].kind = int(c.kind)
-        if int(c.kind) == CCM_POLYGON:
+        if int(c.kind) in (CCM_POLYGON, CCM_SPLINE):
             pts = (ctypes.c_double * len(c.params))(*[float(v) for v in c.params])
             keep.append(pts)
             arr[k].npts = len(c.params) // 2

@@ -36,9 +36,95 @@ static void polygon_edge(const Curve& c, double t, int& a, int& b, double& s) {
   b = (a + 1) % n;
 }
 
+bool Curve::prepare() {
+  if (kind != CCM_SPLINE) return true;
+  const int n = (int)(V.size() / 2);
+  knots.assign(n + 1, 0.0);
+  for (int k = 0; k < n; ++k) {
+    const int l = (k + 1) % n;
+    const double ch = std::hypot(V[2 * l] - V[2 * k], V[2 * l + 1] - V[2 * k + 1]);
+    if (!(ch > 0)) return false;
+    knots[k + 1] = knots[k] + ch;
+  }
+  const double L = knots[n];
+  for (int k = 0; k <= n; ++k) knots[k] = 2 * M_PI * knots[k] / L;
+  knots[n] = 2 * M_PI;
+  // periodic cubic spline: h_{k-1} M_{k-1} + 2 (h_{k-1} + h_k) M_k + h_k M_{k+1} = 6 (d_k - d_{k-1}),
+  // d_k = (v_{k+1} - v_k) / h_k, indices mod n; dense elimination with partial pivoting
+  for (int c = 0; c < 2; ++c) {
+    std::vector<double> A((size_t)n * n, 0.0), r(n);
+    for (int k = 0; k < n; ++k) {
+      const int km = (k + n - 1) % n, kp = (k + 1) % n;
+      const double hm = knots[km + 1] - knots[km], hk = knots[k + 1] - knots[k];
+      A[(size_t)k * n + km] += hm;
+      A[(size_t)k * n + k] += 2 * (hm + hk);
+      A[(size_t)k * n + kp] += hk;
+      const double dk = (V[2 * kp + c] - V[2 * k + c]) / hk, dm = (V[2 * k + c] - V[2 * km + c]) / hm;
+      r[k] = 6 * (dk - dm);
+    }
+    for (int col = 0; col < n; ++col) {
+      int piv = col;
+      for (int row = col + 1; row < n; ++row)
+        if (std::fabs(A[(size_t)row * n + col]) > std::fabs(A[(size_t)piv * n + col])) piv = row;
+      if (piv != col) {
+        for (int m = 0; m < n; ++m) std::swap(A[(size_t)piv * n + m], A[(size_t)col * n + m]);
+        std::swap(r[piv], r[col]);
+      }
+      const double d = A[(size_t)col * n + col];
+      if (!(std::fabs(d) > 0)) return false;
+      for (int row = col + 1; row < n; ++row) {
+        const double f = A[(size_t)row * n + col] / d;
+        if (f == 0.0) continue;
+        for (int m = col; m < n; ++m) A[(size_t)row * n + m] -= f * A[(size_t)col * n + m];
+        r[row] -= f * r[col];
+      }
+    }
+    M[c].assign(n, 0.0);
+    for (int row = n - 1; row >= 0; --row) {
+      double s = r[row];
+      for (int m = row + 1; m < n; ++m) s -= A[(size_t)row * n + m] * M[c][m];
+      M[c][row] = s / A[(size_t)row * n + row];
+    }
+  }
+  poly.clear();
+  for (int k = 0; k < n; ++k)
+    for (int s = 0; s < 64; ++s) {
+      double x, y;
+      xy(knots[k] + (knots[k + 1] - knots[k]) * s / 64.0, x, y);
+      poly.push_back(x);
+      poly.push_back(y);
+    }
+  return true;
+}
+
+// even-odd rule against a closed polyline (x0, y0, x1, y1, ...)
+static bool inside_polyline(const std::vector<double>& P, double x, double y) {
+  const int n = (int)(P.size() / 2);
+  bool in = false;
+  for (int k = 0; k < n; ++k) {
+    const double xa = P[2 * k], ya = P[2 * k + 1];
+    const double xb = P[2 * ((k + 1) % n)], yb = P[2 * ((k + 1) % n) + 1];
+    if (ya == yb) continue;
+    if ((ya > y) != (yb > y) && x < xa + (y - ya) * (xb - xa) / (yb - ya)) in = !in;
+  }
+  return in;
+}
+
+// spline segment of t (mod 2 pi) and its local coordinates
+static void spline_seg(const Curve& c, double t, int& k, double& hk, double& a, double& b) {
+  const int n = (int)(c.V.size() / 2);
+  double tt = std::fmod(t, 2 * M_PI);
+  if (tt < 0) tt += 2 * M_PI;
+  k = (int)(std::upper_bound(c.knots.begin(), c.knots.end(), tt) - c.knots.begin()) - 1;
+  k = std::min(std::max(k, 0), n - 1);
+  hk = c.knots[k + 1] - c.knots[k];
+  a = (c.knots[k + 1] - tt) / hk;
+  b = (tt - c.knots[k]) / hk;
+}
+
 void Curve::subintervals(double t0, double t1, std::vector<std::pair<double, double>>& out) const {
   out.clear();
-  if (kind != CCM_POLYGON) {
+  if (kind != CCM_POLYGON && kind != CCM_SPLINE) {
     out.push_back({t0, t1});
     return;
   }
@@ -46,7 +132,7 @@ void Curve::subintervals(double t0, double t1, std::vector<std::pair<double, dou
   const double lo = std::min(t0, t1), hi = std::max(t0, t1);
   std::vector<double> cuts;
   for (int k = 0; k < n; ++k) {
-    const double b = 2 * M_PI * k / n;
+    const double b = kind == CCM_SPLINE ? knots[k] : 2 * M_PI * k / n;
     double v = b + 2 * M_PI * std::ceil((lo - b) / (2 * M_PI));
     for (; v < hi; v += 2 * M_PI)
       if (v > lo) cuts.push_back(v);
@@ -62,6 +148,16 @@ void Curve::subintervals(double t0, double t1, std::vector<std::pair<double, dou
 }
 
 void Curve::xy(double t, double& x, double& y) const {
+  if (kind == CCM_SPLINE) {
+    int k;
+    double hk, a, b;
+    spline_seg(*this, t, k, hk, a, b);
+    const int n = (int)(V.size() / 2), k1 = (k + 1) % n;
+    double* o[2] = {&x, &y};
+    for (int c = 0; c < 2; ++c)
+      *o[c] = a * V[2 * k + c] + b * V[2 * k1 + c] + ((a * a * a - a) * M[c][k] + (b * b * b - b) * M[c][k1]) * hk * hk / 6;
+    return;
+  }
   if (kind == CCM_POLYGON) {
     int a, b;
     double s;
@@ -91,6 +187,16 @@ void Curve::xy(double t, double& x, double& y) const {
 }
 
 void Curve::dxy(double t, double& x, double& y) const {
+  if (kind == CCM_SPLINE) {
+    int k;
+    double hk, a, b;
+    spline_seg(*this, t, k, hk, a, b);
+    const int n = (int)(V.size() / 2), k1 = (k + 1) % n;
+    double* o[2] = {&x, &y};
+    for (int c = 0; c < 2; ++c)
+      *o[c] = (V[2 * k1 + c] - V[2 * k + c]) / hk + ((1 - 3 * a * a) * M[c][k] + (3 * b * b - 1) * M[c][k1]) * hk / 6;
+    return;
+  }
   if (kind == CCM_POLYGON) {
     int a, b;
     double s;
@@ -122,18 +228,11 @@ void Curve::dxy(double t, double& x, double& y) const {
 }
 
 bool Curve::inside(double x, double y) const {
-  if (kind == CCM_POLYGON) {
-    // even-odd rule: a ray towards +x crosses the boundary an odd number of times
-    const int n = (int)(V.size() / 2);
-    bool in = false;
-    for (int k = 0; k < n; ++k) {
-      const double xa = V[2 * k], ya = V[2 * k + 1];
-      const double xb = V[2 * ((k + 1) % n)], yb = V[2 * ((k + 1) % n) + 1];
-      if (ya == yb) continue;
-      if ((ya > y) != (yb > y) && x < xa + (y - ya) * (xb - xa) / (yb - ya)) in = !in;
-    }
-    return in;
-  }
+  // even-odd rule: a ray towards +x crosses the boundary an odd number of times; a spline is
+  // tested against its 64-per-cubic polyline (the test only classifies centres of cells the
+  // curve does not enter, h/2 or more from it)
+  if (kind == CCM_POLYGON) return inside_polyline(V, x, y);
+  if (kind == CCM_SPLINE) return inside_polyline(poly, x, y);
   switch (kind) {
     case CCM_CIRCLE: {
       double dx = x - p[0], dy = y - p[1];
@@ -456,10 +555,10 @@ int check_problem(const ccm_problem& prob) {
   if (prob.box_bc != CCM_NONE && prob.box_bc != CCM_DIRICHLET && prob.box_bc != CCM_NEUMANN) return CCM_EINVAL;
   for (int k = 0; k < prob.ncurves; ++k) {
     const ccm_curve& c = prob.curves[k];
-    if (c.kind < CCM_CIRCLE || c.kind > CCM_POLYGON || (c.orient != 1 && c.orient != -1) ||
+    if (c.kind < CCM_CIRCLE || c.kind > CCM_SPLINE || (c.orient != 1 && c.orient != -1) ||
         (c.bc != CCM_DIRICHLET && c.bc != CCM_NEUMANN && c.bc != CCM_ROBIN))
       return CCM_EINVAL;
-    if (c.kind == CCM_POLYGON) {
+    if (c.kind == CCM_POLYGON || c.kind == CCM_SPLINE) {
       if (c.npts < 3 || !c.pts) return CCM_EINVAL;
       double area2 = 0;
       for (int v = 0; v < c.npts; ++v) {
@@ -491,7 +590,13 @@ int build_cut_level(const ccm_problem& prob, int nx, int ny, double h, double th
     std::memcpy(c.p, prob.curves[k].p, sizeof(c.p));
     c.orient = prob.curves[k].orient;
     c.bc = prob.curves[k].bc;
-    if (c.kind == CCM_POLYGON) c.V.assign(prob.curves[k].pts, prob.curves[k].pts + 2 * prob.curves[k].npts);
+    if (c.kind == CCM_POLYGON || c.kind == CCM_SPLINE) {
+      c.V.assign(prob.curves[k].pts, prob.curves[k].pts + 2 * prob.curves[k].npts);
+      if (!c.prepare()) {
+        err = "degenerate spline";
+        return CCM_EGEOM;
+      }
+    }
     if (c.bc == CCM_ROBIN) {
       c.robin[0] = prob.curves[k].robin[0];
       c.robin[1] = prob.curves[k].robin[1];

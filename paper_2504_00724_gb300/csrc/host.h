@@ -39,7 +39,10 @@ struct Curve {
   int orient = -1;
   int bc = CCM_DIRICHLET;
   double robin[2] = {1.0, 0.0};     // CCM_ROBIN: gamma1, gamma2 of gamma1 u + gamma2 du/dn
-  std::vector<double> V;            // CCM_POLYGON: vertices (x, y) counter-clockwise
+  std::vector<double> V;            // CCM_POLYGON, CCM_SPLINE: points (x, y) counter-clockwise
+  std::vector<double> knots, M[2];  // CCM_SPLINE: knots t_0 = 0 .. t_n = 2 pi; second derivatives
+  std::vector<double> poly;         // CCM_SPLINE: 64 samples per cubic (the inside test)
+  bool prepare();                   // CCM_SPLINE: knots and second derivatives from V
   void xy(double t, double& x, double& y) const;
   void dxy(double t, double& x, double& y) const;
   bool inside(double x, double y) const;   // strictly inside the closed curve

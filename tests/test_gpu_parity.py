@@ -28,6 +28,8 @@ CASES = {
     "ellipses64": (lambda: W.three_ellipses(64), W.mms_ellipses),
     "robin32": (lambda: W.disk_robin(32, (1.0, 0.5)), W.mms_disk),
     "robin_cross64": (lambda: W.disk_robin(64, (1.0, 2.0), abc=(1.0, 0.5, 2.0)), W.mms_disk),
+    "spline64": (lambda: W.spline_blob(64), W.mms_star),
+    "rotated_box64": (lambda: W.paper_problem3_rotated(64), W.mms_problem3_rotated),
 }
 OMEGA = 0.8
 

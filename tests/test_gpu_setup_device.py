@@ -22,6 +22,7 @@ CASES = {
     "problem1_flower80": lambda: W.paper_problem1(80),
     "problem2_ellipse64_neumann": lambda: W.paper_problem2(64, W.NEUMANN),
     "problem3_rotated_box64": lambda: W.paper_problem3_rotated(64),
+    "spline128": lambda: W.spline_blob(128),
 }
 
 

@@ -44,7 +44,7 @@ def _compare_level(hs, level, prob_level):
                                 lambda: W.star(32, (1.25, -0.8660254037844386, 1.75)),
                                 lambda: W.paper_problem1(40), lambda: W.disk_robin(32),
                                 lambda: W.disk_robin(32, (2.0, -0.3), abc=(1.0, 0.5, 2.0)),
-                                lambda: W.paper_problem3_rotated(32)])
+                                lambda: W.paper_problem3_rotated(32), lambda: W.spline_blob(64)])
 def test_finest_level_matches_oracle(mk):
     prob = mk()
     hs = P.HostSetup(prob)
@@ -64,6 +64,14 @@ def test_polygon_every_level_matches_oracle():
     """The rotated box of Problem 3, case (ii): a polygon curve whose corners fall inside cut
     cells, (a, b, c) = (5/4, -sqrt(3)/2, 7/4), on every level."""
     prob = W.paper_problem3_rotated(64)
+    hs = P.HostSetup(prob)
+    for m in range(MG.n_levels(prob)):
+        _compare_level(hs, m, MG.coarsen(prob, m))
+
+
+def test_spline_every_level_matches_oracle():
+    """A cubic-spline boundary (knots at chord lengths, integrals split at the knots)."""
+    prob = W.spline_blob(64, seed=3)
     hs = P.HostSetup(prob)
     for m in range(MG.n_levels(prob)):
         _compare_level(hs, m, MG.coarsen(prob, m))

@@ -279,6 +279,13 @@ def test_problem3_rotated_box_errors_match_paper():
     assert np.log2(errs[64] / errs[128]) > 3.5
 
 
+def test_spline_domain_fourth_order():
+    """A Y_c domain (the interior of a closed cubic spline, Sec. 2) with Dirichlet data: the
+    max-norm solution error falls at fourth order (64 -> 128)."""
+    e = [_solution_error(W.spline_blob(n), W.mms_star())[0] for n in (64, 128)]
+    assert math.log2(e[0] / e[1]) > 3.5, e
+
+
 def _rows(prob):
     cg = G.cut_cells(prob)
     return cg, D.discretize(cg, prob.a, prob.b, prob.c)

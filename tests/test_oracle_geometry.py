@@ -190,3 +190,42 @@ def test_polygon_subintervals():
     assert np.allclose(x, [0, 0.5, 1, 0]) and np.allclose(y, [0, 0, 0, 0.5])
     with pytest.raises(G.GeometryError):
         G.OCurve(W.POLYGON, (0, 0, 0, 1, 1, 1, 1, 0), 1, W.DIRICHLET)          # clockwise
+
+
+def _scipy_spline(c):
+    from scipy.interpolate import CubicSpline
+    P = np.vstack([c.V, c.V[:1]])
+    return (CubicSpline(c.knots, P[:, 0], bc_type="periodic"), CubicSpline(c.knots, P[:, 1], bc_type="periodic"))
+
+
+def test_spline_is_the_periodic_cubic_spline():
+    """The oracle's Y_c curve equals scipy's periodic cubic spline on the same knots (values and
+    derivatives), interpolates its points and has chord-length knots."""
+    prob = W.spline_blob(64)
+    c = G.OCurve(W.SPLINE, prob.curves[0].params, 1, W.DIRICHLET)
+    sx, sy = _scipy_spline(c)
+    t = np.linspace(0.0, 2 * math.pi, 2001)
+    x, y = c.xy(t)
+    dx, dy = c.dxy(t)
+    assert np.abs(x - sx(t)).max() < 1e-14 and np.abs(y - sy(t)).max() < 1e-14
+    assert np.abs(dx - sx(t, 1)).max() < 1e-13 and np.abs(dy - sy(t, 1)).max() < 1e-13
+    xk, yk = c.xy(c.knots[:-1])
+    assert np.abs(xk - c.V[:, 0]).max() < 1e-15 and np.abs(yk - c.V[:, 1]).max() < 1e-15
+    ch = np.hypot(*(np.roll(c.V, -1, axis=0) - c.V).T)
+    assert np.allclose(np.diff(c.knots), 2 * math.pi * ch / ch.sum(), rtol=1e-14)
+
+
+@pytest.mark.parametrize("n", [16, 64])
+def test_spline_domain_moments(n):
+    """Every moment up to degree 4 of a spline domain, assembled from the cut cells, equals
+    Green's integral of x^{p+1}/(p+1) y^q dy along scipy's spline, one adaptive quadrature per
+    cubic.  A Gauss rule spanning a knot (where the third derivative jumps) misses this at the
+    1e-13 level."""
+    prob = W.spline_blob(n)
+    cg = G.cut_cells(prob)
+    c = G.OCurve(W.SPLINE, prob.curves[0].params, 1, W.DIRICHLET)
+    sx, sy = _scipy_spline(c)
+    for (p, q) in G.EXPS:
+        want = sum(quad(lambda t: sx(t) ** (p + 1) / (p + 1) * sy(t) ** q * sy(t, 1), c.knots[k], c.knots[k + 1],
+                        epsabs=1e-15, epsrel=1e-13, limit=200)[0] for k in range(len(c.V)))
+        assert abs(global_moment(cg, p, q) - want) < 1e-13, (p, q)

@@ -25,7 +25,7 @@ from typing import Callable, List, Optional, Sequence
 
 import numpy as np
 
-CIRCLE, ELLIPSE, STAR, POLYGON = 1, 2, 3, 4
+CIRCLE, ELLIPSE, STAR, POLYGON, SPLINE = 1, 2, 3, 4, 5
 NONE, DIRICHLET, NEUMANN, ROBIN = 0, 1, 2, 3
 
 
@@ -169,6 +169,20 @@ def disk_robin(n: int, gamma=(1.0, 0.5), r: float = 0.2, abc=(1.0, 0.0, 1.0)) ->
     a, b, c = abc
     return Problem(a, b, c, 0.0, 0.0, 1.0 / n, n, n, DIRICHLET,
                    [Curve(CIRCLE, (0.5, 0.5, r), -1, ROBIN, tuple(gamma))], name=f"disk_robin_{n}")
+
+
+def spline_blob(n: int, npts: int = 12, seed: int = 0, abc=(1.0, 0.5, 2.0), bc: int = DIRICHLET) -> Problem:
+    """Interior of a closed cubic spline (a Y_c boundary, Sec. 2) through npts points
+    (0.5, 0.5) + r_k (cos th_k, sin th_k), th_k = 2 pi (k + u_k) / npts with u_k ~ U[-0.2, 0.2]
+    and r_k ~ U[0.25, 0.35] drawn with numpy's PCG64(seed), inside [0,1]^2; bc on the curve."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    u = rng.uniform(-0.2, 0.2, npts)
+    r = rng.uniform(0.25, 0.35, npts)
+    th = 2 * math.pi * (np.arange(npts) + u) / npts
+    pts = np.column_stack([0.5 + r * np.cos(th), 0.5 + r * np.sin(th)]).ravel()
+    a, b, c = abc
+    return Problem(a, b, c, 0.0, 0.0, 1.0 / n, n, n, NONE, [Curve(SPLINE, tuple(float(v) for v in pts), +1, bc)],
+                   name=f"spline_blob_{n}")
 
 
 def star(n: int, abc=(1.0, 0.5, 2.0), r0=0.3, amp=0.08, k=5, centre=(0.5, 0.5)) -> Problem:
