@@ -249,6 +249,18 @@ int ccm_apply_T(ccm_handle* h, const double* v, double* out_u, double* out_g, in
 int ccm_solve(ccm_handle* h, const double* f, const double* g, double* u, int nrhs,
               void* stream, ccm_stats* stats);
 
+/* ccm_solve with HOST arrays: f [nrhs][ny][nx], g [nrhs][n_segments] (may be NULL) and u
+ * [nrhs][ny][nx] (in: initial guess, out: solution) in host memory, same layouts.  Pinned host
+ * memory (cudaHostAlloc, cudaHostRegister, a pinned torch tensor) is read and written by the
+ * packing kernels directly over the host link, with no staging copy: only the non-empty
+ * cells of f and u are read, every cell of u is written.  Pageable memory is accessed the
+ * same way where the device reads pageable memory coherently (Grace systems), else through
+ * device staging buffers and copies.  Device pointers are accepted too.  Returns after u
+ * is complete on the host (the stream is synchronised).  Errors as ccm_solve, plus
+ * CCM_ENOMEM for a staging buffer. */
+int ccm_solve_host(ccm_handle* h, const double* f, const double* g, double* u, int nrhs,
+                   void* stream, ccm_stats* stats);
+
 /* Many problems, one graph launch.  A group holds `count` set-up handles (distinct; each
  * its own geometry, grid size, coefficients and precision) and one CUDA graph in which the
  * outer iterations of all of them run: a device-side loop that, per pass, runs the outer

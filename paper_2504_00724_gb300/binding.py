@@ -78,6 +78,7 @@ _SIGS = {
     "ccm_apply": (I, [P, P, P, P, I, P]),
     "ccm_apply_T": (I, [P, P, P, P, I, P]),
     "ccm_solve": (I, [P, P, P, P, I, P, ctypes.POINTER(ccm_stats)]),
+    "ccm_solve_host": (I, [P, P, P, P, I, P, ctypes.POINTER(ccm_stats)]),
     "ccm_solve_T": (I, [P, P, P, I, P, ctypes.POINTER(ccm_stats)]),
     "ccm_level_apply": (I, [P, I, P, P, P]),
     "ccm_level_smooth": (I, [P, I, P, P, I, P]),
@@ -290,6 +291,26 @@ class Solver:
         rc = lib().ccm_solve(self.h, _ptr(f), _ptr(g), _ptr(u), nrhs, _stream(stream), ctypes.byref(st))
         if check:
             _check(rc, "ccm_solve")
+        return u, st
+
+    def solve_host(self, f, g=None, u=None, stream=None, check=True):
+        """solve() with host arrays (CPU torch tensors, pinned for the direct path, or numpy
+        float64 arrays); u, if given, is the initial guess and receives the solution in place.
+        Returns (u, stats)."""
+        import torch
+
+        def ptr(a):
+            if a is None:
+                return None
+            return a.data_ptr() if isinstance(a, torch.Tensor) else a.ctypes.data
+
+        nrhs = (f.numel() if isinstance(f, torch.Tensor) else f.size) // (self.nx * self.ny)
+        if u is None:
+            u = torch.zeros(f.shape, dtype=torch.float64)
+        st = ccm_stats()
+        rc = lib().ccm_solve_host(self.h, ptr(f), ptr(g), ptr(u), nrhs, _stream(stream), ctypes.byref(st))
+        if check:
+            _check(rc, "ccm_solve_host")
         return u, st
 
     def solve_T(self, rhs, lam0=None, stream=None, check=True):

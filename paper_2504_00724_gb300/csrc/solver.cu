@@ -1898,6 +1898,92 @@ void ccm_group_free(ccm_group* G) {
   delete G;
 }
 
+}  // extern "C"
+
+namespace {
+
+// a pointer the kernels can dereference for `bytes` bytes: device or managed memory and
+// pinned host memory as they are (pinned host memory through its device address: the GPU
+// reads and writes it over the host link, with no copy), pageable host memory as it is where
+// the device reads pageable memory coherently (Grace's address translation), else a device
+// staging buffer (copied in, and copied back by stage_back)
+struct HostView {
+  void* dev = nullptr;
+  void* staged = nullptr;
+  const void* host = nullptr;
+  size_t bytes = 0;
+};
+
+int host_view(const void* p, size_t bytes, bool read, cudaStream_t s, HostView& v) {
+  v = HostView{};
+  v.host = p;
+  v.bytes = bytes;
+  if (!p) return CCM_OK;
+  cudaPointerAttributes at{};
+  if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+    cudaGetLastError();
+    at.type = cudaMemoryTypeUnregistered;
+  }
+  if (at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged) {
+    v.dev = const_cast<void*>(p);
+    return CCM_OK;
+  }
+  if (at.type == cudaMemoryTypeHost && at.devicePointer) {
+    v.dev = at.devicePointer;
+    return CCM_OK;
+  }
+  int dev = 0, pageable = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&pageable, cudaDevAttrPageableMemoryAccess, dev);
+  if (pageable) {
+    v.dev = const_cast<void*>(p);
+    return CCM_OK;
+  }
+  if (cudaMalloc(&v.staged, bytes) != cudaSuccess) return CCM_ENOMEM;
+  v.dev = v.staged;
+  if (read && cudaMemcpyAsync(v.staged, p, bytes, cudaMemcpyHostToDevice, s) != cudaSuccess) return CCM_ECUDA;
+  return CCM_OK;
+}
+
+int stage_back(HostView& v, cudaStream_t s) {
+  if (!v.staged) return CCM_OK;
+  if (cudaMemcpyAsync(const_cast<void*>(v.host), v.staged, v.bytes, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+      cudaStreamSynchronize(s) != cudaSuccess)
+    return CCM_ECUDA;
+  return CCM_OK;
+}
+
+void release(HostView& v) {
+  if (v.staged) cudaFree(v.staged);
+  v.staged = nullptr;
+}
+
+}  // namespace
+
+extern "C" {
+
+int ccm_solve_host(ccm_handle* h, const double* f, const double* g, double* u, int nrhs, void* stream,
+                   ccm_stats* st) {
+  if (!h || !f || !u || nrhs < 1) return CCM_EINVAL;
+  cudaStream_t s = (cudaStream_t)stream;
+  const size_t cells = (size_t)h->L[0].nx * h->L[0].ny * nrhs;
+  HostView vf, vg, vu;
+  int rc = host_view(f, cells * sizeof(double), true, s, vf);
+  if (!rc) rc = host_view(g, (size_t)h->info.n_segments * nrhs * sizeof(double), true, s, vg);
+  if (!rc) rc = host_view(u, cells * sizeof(double), true, s, vu);
+  if (!rc) {
+    rc = ccm_solve(h, (const double*)vf.dev, (const double*)vg.dev, (double*)vu.dev, nrhs, stream, st);
+    // the solution in u (also after CCM_ENOCONV, where u holds the last iterate)
+    const int rb = stage_back(vu, s);
+    if (rc == CCM_OK || rc == CCM_ENOCONV) rc = rc ? rc : rb;
+    if (!vu.staged && cudaStreamSynchronize(s) != cudaSuccess && rc == CCM_OK) rc = CCM_ECUDA;
+  }
+  release(vf);
+  release(vg);
+  release(vu);
+  return rc;
+}
+
 int ccm_solve_T(ccm_handle* h, const double* rhs, double* lambda, int nrhs, void* stream, ccm_stats* st) {
   if (!h || !rhs || !lambda || nrhs < 1) return CCM_EINVAL;
   if (!h->adj) {

@@ -1,0 +1,46 @@
+"""ccm_solve_host: the solve with host buffers (pinned: read and written by the kernels over the
+host link; pageable: the device's own access or staging copies) gives the device-buffer
+solve's result bit for bit, for one and for several right-hand sides."""
+import numpy as np
+import pytest
+
+import workloads as W
+
+torch = pytest.importorskip("torch")
+P = pytest.importorskip("paper_2504_00724_gb300")
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def setup():
+    prob, mms = W.star(256), W.mms_star()
+    s = P.Solver(prob, rtol=1e-10)
+    q = s.quadrature()
+    fa = s.cell_averages(mms.f(prob.a, prob.b, prob.c), quad=q)
+    ga = s.boundary_averages(mms.u, mms.ux, mms.uy, quad=q)
+    yield s, fa, ga
+    s.close()
+
+
+def test_pinned_host_buffers_equal_device_buffers(setup):
+    s, fa, ga = setup
+    u_dev, st_dev = s.solve(torch.tensor(fa, device="cuda"), torch.tensor(ga, device="cuda"))
+    fh = torch.tensor(fa).pin_memory()
+    gh = torch.tensor(ga).pin_memory()
+    uh = torch.zeros_like(fh).pin_memory()
+    u_host, st = s.solve_host(fh, gh, uh)
+    assert u_host.data_ptr() == uh.data_ptr()
+    assert st.iterations == st_dev.iterations and st.rel_residual == st_dev.rel_residual
+    assert torch.equal(uh, u_dev.cpu())
+
+
+def test_pageable_host_buffers_and_several_rhs(setup):
+    s, fa, ga = setup
+    rng = np.random.default_rng(5)
+    F = np.stack([fa, fa * 0.5 + rng.standard_normal(fa.shape) * (s.cell_map()[0] != 0)])
+    G = np.stack([ga, ga * 0.5])
+    u_dev, _ = s.solve(torch.tensor(F, device="cuda"), torch.tensor(G, device="cuda"))
+    U = np.zeros_like(F)
+    s.solve_host(F, G, U)                        # numpy arrays: pageable memory
+    assert np.array_equal(U, u_dev.cpu().numpy())
