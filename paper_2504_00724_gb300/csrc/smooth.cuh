@@ -30,6 +30,26 @@ struct SmoothArgs {
   uint32_t stage;      // bytes per stage (multiple of 128)
 };
 
+// two adjacent values of T (8 or 16 bytes, aligned)
+template <typename T> struct Pair;
+template <> struct Pair<float> { using type = float2; };
+template <> struct Pair<double> { using type = double2; };
+
+// w[0..5] = row[0..5] as three aligned pair loads (row at an even element offset)
+template <typename T>
+__device__ __forceinline__ void load_six(const T* row, T (&w)[6]) {
+  using V2 = typename Pair<T>::type;
+  const V2 a = *reinterpret_cast<const V2*>(row);
+  const V2 b = *reinterpret_cast<const V2*>(row + 2);
+  const V2 c = *reinterpret_cast<const V2*>(row + 4);
+  w[0] = a.x;
+  w[1] = a.y;
+  w[2] = b.x;
+  w[3] = b.y;
+  w[4] = c.x;
+  w[5] = c.y;
+}
+
 // offsets inside a stage of a tile item
 template <typename T>
 struct TileStage {
@@ -181,35 +201,82 @@ __global__ void __launch_bounds__(256, 3) k_smooth(const __grid_constant__ CUten
           }
         __syncthreads();
       }
-      const int x = threadIdx.x & 63, y0 = (threadIdx.x >> 6) * 8;
-      const int i = cx0 + x;
-      if (i < a.nx) {
-        T w[5][5];
+      if constexpr (sizeof(T) == 8) {
+        // FP64: one cell column of eight rows per thread (the paired form below spills)
+        const int x = threadIdx.x & 63, y0 = (threadIdx.x >> 6) * 8;
+        const int i = cx0 + x;
+        if (i < a.nx) {
+          T w[5][5];
 #pragma unroll
-        for (int q = 0; q < 4; ++q)
+          for (int q = 0; q < 4; ++q)
 #pragma unroll
-          for (int b = 0; b < 5; ++b) w[q][b] = tile[(y0 + q) * HX + x + b];
+            for (int b = 0; b < 5; ++b) w[q][b] = tile[(y0 + q) * HX + x + b];
 #pragma unroll
-        for (int kk = 0; kk < 8; ++kk) {
+          for (int kk = 0; kk < 8; ++kk) {
 #pragma unroll
-          for (int b = 0; b < 5; ++b) w[4][b] = tile[(y0 + kk + 4) * HX + x + b];
-          if (ct[(y0 + kk + 2) * CLX + x + 2] == 1) {
-            T acc = 0;
+            for (int b = 0; b < 5; ++b) w[4][b] = tile[(y0 + kk + 4) * HX + x + b];
+            if (ct[(y0 + kk + 2) * CLX + x + 2] == 1) {
+              T acc = 0;
 #pragma unroll
-            for (int q = 0; q < 5; ++q)
+              for (int q = 0; q < 5; ++q)
 #pragma unroll
-              for (int b = 0; b < 5; ++b) {
-                if (!CROSS && q != 2 && b != 2) continue;
-                acc += a.S.w[q * 5 + b] * w[q][b];
-              }
-            const long p = (long)(cy0 + y0 + kk + 2) * a.pitch + (i + 2);
-            u_new[p] = w[2][2] + a.S.omega_d * (rt[(y0 + kk) * HX + x + 2] - acc);
+                for (int b = 0; b < 5; ++b) {
+                  if (!CROSS && q != 2 && b != 2) continue;
+                  acc += a.S.w[q * 5 + b] * w[q][b];
+                }
+              const long p = (long)(cy0 + y0 + kk + 2) * a.pitch + (i + 2);
+              u_new[p] = w[2][2] + a.S.omega_d * (rt[(y0 + kk) * HX + x + 2] - acc);
+            }
+#pragma unroll
+            for (int q = 0; q < 4; ++q)
+#pragma unroll
+              for (int b = 0; b < 5; ++b) w[q][b] = w[q + 1][b];
+          }
+        }
+      } else {
+      // FP32: two adjacent cells (x0, x0 + 1) in four rows per thread: each staged row is read
+      // as three aligned pairs (x0 - 2 .. x0 + 3) and serves both cells' stencils, and the
+      // class bytes, right-hand sides and new values move in pairs
+      using V2 = typename Pair<T>::type;
+      const int x0 = 2 * (threadIdx.x & 31), y0 = (threadIdx.x >> 5) * 4;
+      const int i0 = cx0 + x0;
+      if (i0 < a.nx) {
+        T w[5][6];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) load_six(tile + (y0 + q) * HX + x0, w[q]);
+#pragma unroll
+        for (int kk = 0; kk < 4; ++kk) {
+          load_six(tile + (y0 + kk + 4) * HX + x0, w[4]);
+          T acc0 = 0, acc1 = 0;
+#pragma unroll
+          for (int q = 0; q < 5; ++q)
+#pragma unroll
+            for (int b = 0; b < 5; ++b) {
+              if (!CROSS && q != 2 && b != 2) continue;
+              acc0 += a.S.w[q * 5 + b] * w[q][b];
+              acc1 += a.S.w[q * 5 + b] * w[q][b + 1];
+            }
+          const uint32_t c2 = *reinterpret_cast<const uint16_t*>(ct + (y0 + kk + 2) * CLX + x0 + 2);
+          const V2 r2 = *reinterpret_cast<const V2*>(rt + (y0 + kk) * HX + x0 + 2);
+          const T v0 = w[2][2] + a.S.omega_d * (r2.x - acc0);
+          const T v1 = w[2][3] + a.S.omega_d * (r2.y - acc1);
+          const bool g0 = (c2 & 0xffu) == 1u, g1 = (c2 >> 8) == 1u && i0 + 1 < a.nx;
+          const long p = (long)(cy0 + y0 + kk + 2) * a.pitch + (i0 + 2);
+          if (g0 && g1) {
+            V2 o;
+            o.x = v0;
+            o.y = v1;
+            *reinterpret_cast<V2*>(u_new + p) = o;
+          } else {
+            if (g0) u_new[p] = v0;
+            if (g1) u_new[p + 1] = v1;
           }
 #pragma unroll
           for (int q = 0; q < 4; ++q)
 #pragma unroll
-            for (int b = 0; b < 5; ++b) w[q][b] = w[q + 1][b];
+            for (int b = 0; b < 6; ++b) w[q][b] = w[q + 1][b];
         }
+      }
       }
     }
     __syncthreads();      // stage sb is free
@@ -339,7 +406,37 @@ __global__ void __launch_bounds__(256, 3) k_restrict_p(const __grid_constant__ C
     const T* rt = reinterpret_cast<const T*>(st + S::r_off);
     const uint8_t* ct = st + S::c_off;
     const T* vt = reinterpret_cast<const T*>(st + S::v_off);
-    {
+    if constexpr (sizeof(T) == 4) {
+      // two adjacent cells in four rows per thread, rows read as aligned pairs (as in k_smooth)
+      const int x0 = 2 * (threadIdx.x & 31), y1 = (threadIdx.x >> 5) * 4;
+      T w[5][6];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) load_six(tile + (y1 + q) * HX + x0, w[q]);
+#pragma unroll
+      for (int kk = 0; kk < 4; ++kk) {
+        load_six(tile + (y1 + kk + 4) * HX + x0, w[4]);
+        T acc0 = 0, acc1 = 0;
+#pragma unroll
+        for (int q = 0; q < 5; ++q)
+#pragma unroll
+          for (int b = 0; b < 5; ++b) {
+            if (!CROSS && q != 2 && b != 2) continue;
+            acc0 += A.S.w[q * 5 + b] * w[q][b];
+            acc1 += A.S.w[q * 5 + b] * w[q][b + 1];
+          }
+        const uint32_t c2 = *reinterpret_cast<const uint16_t*>(ct + (y1 + kk + 2) * CLX + x0 + 2);
+        const typename Pair<T>::type r2 = *reinterpret_cast<const typename Pair<T>::type*>(rt + (y1 + kk) * HX + x0 + 2);
+        const uint32_t cv0 = c2 & 0xffu, cv1 = c2 >> 8;
+        if (cv0 == 1u) res[y1 + kk][x0] = r2.x - acc0;
+        else if (cv0 == 0u) res[y1 + kk][x0] = (T)0;
+        if (cv1 == 1u) res[y1 + kk][x0 + 1] = r2.y - acc1;
+        else if (cv1 == 0u) res[y1 + kk][x0 + 1] = (T)0;
+#pragma unroll
+        for (int q = 0; q < 4; ++q)
+#pragma unroll
+          for (int b = 0; b < 6; ++b) w[q][b] = w[q + 1][b];
+      }
+    } else {
       T w[5][5];
 #pragma unroll
       for (int q = 0; q < 4; ++q)
