@@ -839,6 +839,67 @@ __global__ void k_prolong(const int32_t* __restrict__ tiles, const uint8_t* __re
 }
 
 // bottom solve: u[cell_k] = sum_c inv[c][k] r[cell_c]
+// The bottom solve u = inv(L_bottom) r split over a thread-block cluster of BOTTOM_SPLIT
+// CTAs: CTA q of the cluster takes columns [q n / S, (q + 1) n / S) of the 32 rows of its row
+// block, warps split those columns, and the cluster's rank 0 adds the S partial sums through
+// distributed shared memory in rank order (the same order every run).  Both cluster barriers
+// are passed by every thread of every CTA.
+constexpr int BOTTOM_SPLIT = 8;
+
+__device__ __forceinline__ unsigned bottom_rank() {
+  unsigned r;
+  asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+  return r;
+}
+
+__device__ __forceinline__ void bottom_cluster_sync() {
+  asm volatile("barrier.cluster.arrive.release;\n\tbarrier.cluster.wait.acquire;" ::: "memory");
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_bottom_split(int n, const int32_t* __restrict__ cell, const T* __restrict__ inv,
+                                                      const T* __restrict__ r, T* __restrict__ u, long bs) {
+  __shared__ T part[8][32];
+  __shared__ T tot[32];
+  pdl_enter();
+  r += blockIdx.y * bs;       // right-hand side blockIdx.y of the batch
+  u += blockIdx.y * bs;
+  const unsigned q = bottom_rank();
+  const int rowblk = blockIdx.x / BOTTOM_SPLIT;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int k = rowblk * 32 + lane;
+  const int c0 = (int)((long)n * q / BOTTOM_SPLIT), c1 = (int)((long)n * (q + 1) / BOTTOM_SPLIT);
+  T acc = 0;
+  if (k < n)
+    for (int c = c0 + warp; c < c1; c += 8) acc += inv[(long)c * n + k] * r[cell[c]];
+  part[warp][lane] = acc;
+  __syncthreads();
+  if (warp == 0) {
+    T s = 0;
+#pragma unroll
+    for (int w = 0; w < 8; ++w) s += part[w][lane];
+    tot[lane] = s;
+  }
+  bottom_cluster_sync();          // every CTA's tot is written
+  if (q == 0 && warp == 0) {
+    uint32_t local = (uint32_t)__cvta_generic_to_shared(&tot[lane]);
+    T s = 0;
+    for (unsigned p = 0; p < BOTTOM_SPLIT; ++p) {
+      uint32_t remote;
+      asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(remote) : "r"(local), "r"(p));
+      T v;
+      if constexpr (sizeof(T) == 8) {
+        asm volatile("ld.shared::cluster.f64 %0, [%1];" : "=d"(v) : "r"(remote) : "memory");
+      } else {
+        asm volatile("ld.shared::cluster.f32 %0, [%1];" : "=f"(v) : "r"(remote) : "memory");
+      }
+      s += v;
+    }
+    if (k < n) u[cell[k]] = s;
+  }
+  bottom_cluster_sync();          // the other CTAs keep their shared memory until rank 0 has read it
+}
+
 template <typename T>
 __global__ void k_bottom(int n, const int32_t* __restrict__ cell, const T* __restrict__ inv,
                          const T* __restrict__ r, T* __restrict__ u, long bs) {

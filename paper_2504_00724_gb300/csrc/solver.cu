@@ -586,6 +586,26 @@ void prolong_from(ccm_handle* H, DevLevel& F, DevLevel& C, cudaStream_t s) {
 
 template <typename T>
 void bottom(ccm_handle* H, DevLevel& B, cudaStream_t s) {
+  if (B.nbc >= 256) {
+    // column chunks over a cluster of CTAs (latency of the dense matrix-vector product)
+    cudaLaunchConfig_t cfg{};
+    cudaLaunchAttribute at[2];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = dev::BOTTOM_SPLIT;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    at[1].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[1].val.programmaticStreamSerializationAllowed = 1;
+    cfg.gridDim = dim3(ceil_div(B.nbc, 32) * dev::BOTTOM_SPLIT, H->nb);
+    cfg.blockDim = dim3(256);
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = s;
+    cfg.attrs = at;
+    cfg.numAttrs = t_pdl ? 2 : 1;
+    KL(cudaLaunchKernelEx(&cfg, dev::k_bottom_split<T>, B.nbc, (const int32_t*)B.bot_cell, (const T*)Bot<T>(B),
+                          (const T*)R<T>(B), U<T>(B), B.npad));
+    return;
+  }
   int nw = 8;
   size_t sm = std::max<size_t>(B.nbc, nw * 32) * sizeof(T);
   KL(launch_k(dev::k_bottom<T>, dim3(ceil_div(B.nbc, 32), H->nb), nw * 32, sm, s, B.nbc, B.bot_cell, Bot<T>(B), R<T>(B),

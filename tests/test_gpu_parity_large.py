@@ -156,3 +156,39 @@ def test_large_default_smoother_matches_block_jacobi(big, precision, tol):
     finally:
         s.close()
         hs.close()
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_bottom_64_cluster_split(precision):
+    """A 64^2 bottom level (about 1.2k unknowns on the star, the hierarchy of the benchmark):
+    the dense bottom inverse applied by a cluster of CTAs over column chunks, partial sums added
+    in rank order through distributed shared memory, against the oracle's LU solve of the same
+    level; and a V-cycle through that bottom level against the oracle's (FP64)."""
+    prob = W.star(128)
+    H = MG.build_hierarchy(prob, coarsest=64)
+    assert len(H.levels) == 2 and int(H.levels[-1].ne.sum()) >= 256
+    s = P.Solver(prob, omega=OMEGA, coarsest=64, ras_passes=40, smoother=0, ras_exact=1024)
+    try:
+        last = H.levels[-1]
+        rng = np.random.default_rng(11)
+        r = np.where(last.ne, rng.standard_normal(last.nx * last.ny), 0.0).reshape(last.ny, last.nx) / last.h ** 2
+        want = MG.bottom(H, r.ravel())
+        got = host(s.bottom_solve(cuda(r))).ravel()
+        assert np.abs(got - want).max() <= 1e-10 * np.abs(want).max()
+        if precision == 0:
+            lv = H.levels[0]
+            u0 = np.where(lv.ne, rng.standard_normal(lv.nx * lv.ny), 0.0).reshape(lv.ny, lv.nx)
+            rr = np.where(lv.ne, rng.standard_normal(lv.nx * lv.ny), 0.0).reshape(lv.ny, lv.nx) / lv.h ** 2
+            want = MG.vcycle(H, 0, u0.ravel().copy(), rr.ravel(), omega=OMEGA, nu1=3, nu2=3)
+            got = host(s.vcycle(cuda(u0), cuda(rr), P.CCM_FP64)).ravel()
+            assert np.abs(got - want).max() <= 1e-8 * np.abs(want).max()
+        else:
+            # the FP32 bottom inside the mixed solve: converged to the FP64 tolerance
+            mms = W.mms_star()
+            q = s.quadrature()
+            f = torch.tensor(s.cell_averages(mms.f(prob.a, prob.b, prob.c), quad=q), device="cuda")
+            g = torch.tensor(s.boundary_averages(mms.u, mms.ux, mms.uy, quad=q), device="cuda")
+            _, st = s.solve(f, g)
+            assert st.rel_residual <= 1e-10
+    finally:
+        s.close()
