@@ -95,6 +95,165 @@ __device__ __forceinline__ void smooth_issue(const SmoothArgs<T>& A, const CUten
   }
 }
 
+// SMO-2 residuals of block b's extended rows from u_old (u_old + P uc with PRO) into sres;
+// the block's core start, core size and extended size come back.  CG: u_old is read through
+// L2 only (iterates that other CTAs of the same launch wrote).
+template <typename T, bool PRO, bool CG>
+__device__ __forceinline__ void block_residuals(const SweepArgs<T>& a, int b, const T* __restrict__ u_old,
+                                                const T* __restrict__ rhs, const T* __restrict__ ucs, T* sres,
+                                                int& cs, int& nc, int& ne) {
+  cs = a.blk[4 * b];
+  nc = a.blk[4 * b + 1] - cs;
+  const int es = a.blk[4 * b + 2];
+  ne = a.blk[4 * b + 3] - es;
+  for (int e = threadIdx.x; e < ne; e += blockDim.x) {
+    const int row = es + e;
+    T acc = 0;
+#pragma unroll 15
+    for (int m = 0; m < a.W; ++m) {
+      const int cq = a.col[(long)m * a.n2 + row];
+      T v = CG ? __ldcg(u_old + cq) : u_old[cq];
+      if (PRO) {
+        const int pq = a.par[(long)m * a.n2 + row];
+        if (pq >= 0) v += ucs[pq];
+      }
+      acc += a.val[(long)m * a.n2 + row] * v;
+    }
+    sres[e] = rhs[a.cell[row]] - acc;
+  }
+}
+
+// u_new = u_old + inv(L22[ext, ext]) sres on the block's core cells; As = the staged rows
+// [ne][nc] of the inverse, columns over lanes, extended rows over warps
+template <typename T, bool CG>
+__device__ __forceinline__ void block_apply(const SweepArgs<T>& a, const T* As, const T* sres, int cs, int nc, int ne,
+                                            const T* __restrict__ u_old, T* __restrict__ u_new, T (*part)[32]) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int cb = 0; cb < nc; cb += 32) {
+    const int c = cb + lane;
+    T acc = 0;
+    if (c < nc)
+      for (int e = warp; e < ne; e += 8) acc += As[e * nc + c] * sres[e];
+    part[warp][lane] = acc;
+    __syncthreads();
+    if (warp == 0 && c < nc) {
+      T tot = 0;
+#pragma unroll
+      for (int w = 0; w < 8; ++w) tot += part[w][lane];
+      const long q = a.cell[cs + c];
+      u_new[q] = (CG ? __ldcg(u_old + q) : u_old[q]) + tot;
+    }
+    __syncthreads();
+  }
+}
+
+// SMO-1 on the regular cells of a staged 64 x 32 tile (halo box of u, box of r and class bytes
+// at the TileStage offsets of st; with PRO the coarse box too, whose parent values are first
+// added to the staged regular cells: the sweep then reads u + P uc)
+template <typename T, bool CROSS, bool PRO>
+__device__ __forceinline__ void tile_sweep(const SweepArgs<T>& a, unsigned char* st, int cx0, int cy0,
+                                           T* __restrict__ u_new) {
+  using S = TileStage<T>;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  T* tile = reinterpret_cast<T*>(st);
+  const T* rt = reinterpret_cast<const T*>(st + S::r_off);
+  const uint8_t* ct = st + S::c_off;
+  if (PRO) {
+    // staged cell (y, x) has its parent at (y / 2, x / 2 + 1) of the coarse box; four
+    // cells (one 32-bit word of class bytes, two parents) per step
+    const T* uct = reinterpret_cast<const T*>(st + S::uc_off);
+    for (int y = warp; y < HY; y += 8)
+      if (lane < HX / 4) {
+        const int x0 = 4 * lane;
+        const uint32_t c4 = *reinterpret_cast<const uint32_t*>(ct + y * CLX + x0);
+        const T p0 = uct[(y >> 1) * UCX + 2 * lane + 1], p1 = uct[(y >> 1) * UCX + 2 * lane + 2];
+        T* tr4 = tile + y * HX + x0;
+        if ((c4 & 0xffu) == 1u) tr4[0] += p0;
+        if (((c4 >> 8) & 0xffu) == 1u) tr4[1] += p0;
+        if (((c4 >> 16) & 0xffu) == 1u) tr4[2] += p1;
+        if ((c4 >> 24) == 1u) tr4[3] += p1;
+      }
+    __syncthreads();
+  }
+  if constexpr (sizeof(T) == 8) {
+    // FP64: one cell column of eight rows per thread (the paired form below spills)
+    const int x = threadIdx.x & 63, y0 = (threadIdx.x >> 6) * 8;
+    const int i = cx0 + x;
+    if (i < a.nx) {
+      T w[5][5];
+#pragma unroll
+      for (int q = 0; q < 4; ++q)
+#pragma unroll
+        for (int b = 0; b < 5; ++b) w[q][b] = tile[(y0 + q) * HX + x + b];
+#pragma unroll
+      for (int kk = 0; kk < 8; ++kk) {
+#pragma unroll
+        for (int b = 0; b < 5; ++b) w[4][b] = tile[(y0 + kk + 4) * HX + x + b];
+        if (ct[(y0 + kk + 2) * CLX + x + 2] == 1) {
+          T acc = 0;
+#pragma unroll
+          for (int q = 0; q < 5; ++q)
+#pragma unroll
+            for (int b = 0; b < 5; ++b) {
+              if (!CROSS && q != 2 && b != 2) continue;
+              acc += a.S.w[q * 5 + b] * w[q][b];
+            }
+          const long p = (long)(cy0 + y0 + kk + 2) * a.pitch + (i + 2);
+          u_new[p] = w[2][2] + a.S.omega_d * (rt[(y0 + kk) * HX + x + 2] - acc);
+        }
+#pragma unroll
+        for (int q = 0; q < 4; ++q)
+#pragma unroll
+          for (int b = 0; b < 5; ++b) w[q][b] = w[q + 1][b];
+      }
+    }
+  } else {
+    // FP32: two adjacent cells (x0, x0 + 1) in four rows per thread: each staged row is read
+    // as three aligned pairs (x0 - 2 .. x0 + 3) and serves both cells' stencils, and the
+    // class bytes, right-hand sides and new values move in pairs
+    using V2 = typename Pair<T>::type;
+    const int x0 = 2 * (threadIdx.x & 31), y0 = (threadIdx.x >> 5) * 4;
+    const int i0 = cx0 + x0;
+    if (i0 < a.nx) {
+      T w[5][6];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) load_six(tile + (y0 + q) * HX + x0, w[q]);
+#pragma unroll
+      for (int kk = 0; kk < 4; ++kk) {
+        load_six(tile + (y0 + kk + 4) * HX + x0, w[4]);
+        T acc0 = 0, acc1 = 0;
+#pragma unroll
+        for (int q = 0; q < 5; ++q)
+#pragma unroll
+          for (int b = 0; b < 5; ++b) {
+            if (!CROSS && q != 2 && b != 2) continue;
+            acc0 += a.S.w[q * 5 + b] * w[q][b];
+            acc1 += a.S.w[q * 5 + b] * w[q][b + 1];
+          }
+        const uint32_t c2 = *reinterpret_cast<const uint16_t*>(ct + (y0 + kk + 2) * CLX + x0 + 2);
+        const V2 r2 = *reinterpret_cast<const V2*>(rt + (y0 + kk) * HX + x0 + 2);
+        const T v0 = w[2][2] + a.S.omega_d * (r2.x - acc0);
+        const T v1 = w[2][3] + a.S.omega_d * (r2.y - acc1);
+        const bool g0 = (c2 & 0xffu) == 1u, g1 = (c2 >> 8) == 1u && i0 + 1 < a.nx;
+        const long p = (long)(cy0 + y0 + kk + 2) * a.pitch + (i0 + 2);
+        if (g0 && g1) {
+          V2 o;
+          o.x = v0;
+          o.y = v1;
+          *reinterpret_cast<V2*>(u_new + p) = o;
+        } else {
+          if (g0) u_new[p] = v0;
+          if (g1) u_new[p + 1] = v1;
+        }
+#pragma unroll
+        for (int q = 0; q < 4; ++q)
+#pragma unroll
+          for (int b = 0; b < 6; ++b) w[q][b] = w[q + 1][b];
+      }
+    }
+  }
+}
+
 template <typename T, bool CROSS, bool PRO>
 __global__ void __launch_bounds__(256, 3) k_smooth(const __grid_constant__ CUtensorMap tin,
                                                 const __grid_constant__ CUtensorMap tr,
@@ -123,34 +282,12 @@ __global__ void __launch_bounds__(256, 3) k_smooth(const __grid_constant__ CUten
     smooth_issue<T, PRO>(A, &tin, &tr, &tcls, &tuc, blockIdx.x, smem_raw, &bar[0]);
     if (K > 1) smooth_issue<T, PRO>(A, &tin, &tr, &tcls, &tuc, blockIdx.x + G, smem_raw + A.stage, &bar[1]);
   }
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   for (int k = 0; k < K; ++k) {
     const int item = blockIdx.x + k * G;
     const int sb = k & 1;
     const uint32_t parity = (k >> 1) & 1;
     int cs = 0, nc = 0, ne = 0;
-    if (item < A.nbi) {
-      // residuals of the block's extended rows from the old iterate (u + P uc with PRO)
-      const int b = item;
-      cs = a.blk[4 * b];
-      nc = a.blk[4 * b + 1] - cs;
-      const int es = a.blk[4 * b + 2];
-      ne = a.blk[4 * b + 3] - es;
-      for (int e = threadIdx.x; e < ne; e += blockDim.x) {
-        const int row = es + e;
-        T acc = 0;
-#pragma unroll 15
-        for (int m = 0; m < a.W; ++m) {
-          T v = u_old[a.col[(long)m * a.n2 + row]];
-          if (PRO) {
-            const int pq = a.par[(long)m * a.n2 + row];
-            if (pq >= 0) v += ucs[pq];
-          }
-          acc += a.val[(long)m * a.n2 + row] * v;
-        }
-        sres[e] = rhs[a.cell[row]] - acc;
-      }
-    }
+    if (item < A.nbi) block_residuals<T, PRO, false>(a, item, u_old, rhs, ucs, sres, cs, nc, ne);
     const bool ok = __syncthreads_and(wait_parity(&bar[sb], parity));
     if (!ok) {
       // this copy and the other stage's (if one was issued) must land before the CTA leaves
@@ -160,124 +297,11 @@ __global__ void __launch_bounds__(256, 3) k_smooth(const __grid_constant__ CUten
       return;
     }
     if (item < A.nbi) {
-      const T* As = reinterpret_cast<const T*>(smem_raw + sb * A.stage);      // [ne][nc]
-      for (int cb = 0; cb < nc; cb += 32) {
-        const int c = cb + lane;
-        T acc = 0;
-        if (c < nc)
-          for (int e = warp; e < ne; e += 8) acc += As[e * nc + c] * sres[e];
-        part[warp][lane] = acc;
-        __syncthreads();
-        if (warp == 0 && c < nc) {
-          T tot = 0;
-#pragma unroll
-          for (int w = 0; w < 8; ++w) tot += part[w][lane];
-          const long q = a.cell[cs + c];
-          u_new[q] = u_old[q] + tot;
-        }
-        __syncthreads();
-      }
+      block_apply<T, false>(a, reinterpret_cast<const T*>(smem_raw + sb * A.stage), sres, cs, nc, ne, u_old, u_new,
+                            part);
     } else {
-      using S = TileStage<T>;
       const int t = item - A.nbi;
-      const int cx0 = a.tiles[2 * t] * JX, cy0 = a.tiles[2 * t + 1] * JY;
-      T* tile = reinterpret_cast<T*>((smem_raw + sb * A.stage));
-      const T* rt = reinterpret_cast<const T*>((smem_raw + sb * A.stage) + S::r_off);
-      const uint8_t* ct = (smem_raw + sb * A.stage) + S::c_off;
-      if (PRO) {
-        // staged cell (y, x) has its parent at (y / 2, x / 2 + 1) of the coarse box; four
-        // cells (one 32-bit word of class bytes, two parents) per step
-        const T* uct = reinterpret_cast<const T*>((smem_raw + sb * A.stage) + S::uc_off);
-        for (int y = warp; y < HY; y += 8)
-          if (lane < HX / 4) {
-            const int x0 = 4 * lane;
-            const uint32_t c4 = *reinterpret_cast<const uint32_t*>(ct + y * CLX + x0);
-            const T p0 = uct[(y >> 1) * UCX + 2 * lane + 1], p1 = uct[(y >> 1) * UCX + 2 * lane + 2];
-            T* tr4 = tile + y * HX + x0;
-            if ((c4 & 0xffu) == 1u) tr4[0] += p0;
-            if (((c4 >> 8) & 0xffu) == 1u) tr4[1] += p0;
-            if (((c4 >> 16) & 0xffu) == 1u) tr4[2] += p1;
-            if ((c4 >> 24) == 1u) tr4[3] += p1;
-          }
-        __syncthreads();
-      }
-      if constexpr (sizeof(T) == 8) {
-        // FP64: one cell column of eight rows per thread (the paired form below spills)
-        const int x = threadIdx.x & 63, y0 = (threadIdx.x >> 6) * 8;
-        const int i = cx0 + x;
-        if (i < a.nx) {
-          T w[5][5];
-#pragma unroll
-          for (int q = 0; q < 4; ++q)
-#pragma unroll
-            for (int b = 0; b < 5; ++b) w[q][b] = tile[(y0 + q) * HX + x + b];
-#pragma unroll
-          for (int kk = 0; kk < 8; ++kk) {
-#pragma unroll
-            for (int b = 0; b < 5; ++b) w[4][b] = tile[(y0 + kk + 4) * HX + x + b];
-            if (ct[(y0 + kk + 2) * CLX + x + 2] == 1) {
-              T acc = 0;
-#pragma unroll
-              for (int q = 0; q < 5; ++q)
-#pragma unroll
-                for (int b = 0; b < 5; ++b) {
-                  if (!CROSS && q != 2 && b != 2) continue;
-                  acc += a.S.w[q * 5 + b] * w[q][b];
-                }
-              const long p = (long)(cy0 + y0 + kk + 2) * a.pitch + (i + 2);
-              u_new[p] = w[2][2] + a.S.omega_d * (rt[(y0 + kk) * HX + x + 2] - acc);
-            }
-#pragma unroll
-            for (int q = 0; q < 4; ++q)
-#pragma unroll
-              for (int b = 0; b < 5; ++b) w[q][b] = w[q + 1][b];
-          }
-        }
-      } else {
-      // FP32: two adjacent cells (x0, x0 + 1) in four rows per thread: each staged row is read
-      // as three aligned pairs (x0 - 2 .. x0 + 3) and serves both cells' stencils, and the
-      // class bytes, right-hand sides and new values move in pairs
-      using V2 = typename Pair<T>::type;
-      const int x0 = 2 * (threadIdx.x & 31), y0 = (threadIdx.x >> 5) * 4;
-      const int i0 = cx0 + x0;
-      if (i0 < a.nx) {
-        T w[5][6];
-#pragma unroll
-        for (int q = 0; q < 4; ++q) load_six(tile + (y0 + q) * HX + x0, w[q]);
-#pragma unroll
-        for (int kk = 0; kk < 4; ++kk) {
-          load_six(tile + (y0 + kk + 4) * HX + x0, w[4]);
-          T acc0 = 0, acc1 = 0;
-#pragma unroll
-          for (int q = 0; q < 5; ++q)
-#pragma unroll
-            for (int b = 0; b < 5; ++b) {
-              if (!CROSS && q != 2 && b != 2) continue;
-              acc0 += a.S.w[q * 5 + b] * w[q][b];
-              acc1 += a.S.w[q * 5 + b] * w[q][b + 1];
-            }
-          const uint32_t c2 = *reinterpret_cast<const uint16_t*>(ct + (y0 + kk + 2) * CLX + x0 + 2);
-          const V2 r2 = *reinterpret_cast<const V2*>(rt + (y0 + kk) * HX + x0 + 2);
-          const T v0 = w[2][2] + a.S.omega_d * (r2.x - acc0);
-          const T v1 = w[2][3] + a.S.omega_d * (r2.y - acc1);
-          const bool g0 = (c2 & 0xffu) == 1u, g1 = (c2 >> 8) == 1u && i0 + 1 < a.nx;
-          const long p = (long)(cy0 + y0 + kk + 2) * a.pitch + (i0 + 2);
-          if (g0 && g1) {
-            V2 o;
-            o.x = v0;
-            o.y = v1;
-            *reinterpret_cast<V2*>(u_new + p) = o;
-          } else {
-            if (g0) u_new[p] = v0;
-            if (g1) u_new[p + 1] = v1;
-          }
-#pragma unroll
-          for (int q = 0; q < 4; ++q)
-#pragma unroll
-            for (int b = 0; b < 6; ++b) w[q][b] = w[q + 1][b];
-        }
-      }
-      }
+      tile_sweep<T, CROSS, PRO>(a, smem_raw + sb * A.stage, a.tiles[2 * t] * JX, a.tiles[2 * t + 1] * JY, u_new);
     }
     __syncthreads();      // stage sb is free
     if (threadIdx.x == 0 && k + 2 < K) {
