@@ -332,6 +332,13 @@ int ccm_set_cycle_params(ccm_handle* h, double omega, int nu1, int nu2, int inne
  * Errors: CCM_EINVAL, CCM_ECUDA. */
 int ccm_fmg(ccm_handle* h, double* u, const double* r, int precision, void* stream);
 
+/* Self-test of the failure path of the bounded device waits: one CTA waits, with the wait
+ * helper every TMA-staged kernel uses, on an mbarrier phase that nothing completes.  The wait
+ * runs out after about 4 ms of SM clock, sets the handle's device error word, and the kernel
+ * returns, so the context stays usable.  Returns CCM_ETIMEOUT (the expected outcome; the error
+ * word is cleared again), CCM_OK if the wait did not run out, or CCM_ECUDA.  Blocking. */
+int ccm_wait_selftest(ccm_handle* h, void* stream);
+
 /* ---- accounting and profiling (not part of the method).
  * ccm_launch_count: kernels launched by this library in this process so far (all handles).
  * ccm_profile: record CUDA events on the handle's stream around every launch of one class:

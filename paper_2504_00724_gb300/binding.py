@@ -98,6 +98,7 @@ _SIGS = {
     "ccm_launch_count": (ctypes.c_int64, []),
     "ccm_apply_noalloc": (I, [P, P, P, P, P]),
     "ccm_profile": (I, [P, I]),
+    "ccm_wait_selftest": (I, [P, P]),
     "ccm_profile_read": (I, [P, ctypes.POINTER(ctypes.c_double), I64P]),
     "ccm_group_create": (I, [P, I, P, ctypes.POINTER(P)]),
     "ccm_group_solve": (I, [P, P, P, P, P, ctypes.POINTER(ccm_stats)]),
@@ -377,6 +378,10 @@ class Solver:
         u = torch.zeros_like(r)
         _check(lib().ccm_fmg(self.h, _ptr(u), _ptr(r), precision, _stream(stream)), "ccm_fmg")
         return u
+
+    def wait_selftest(self, stream=None) -> int:
+        """ccm_wait_selftest: the bounded-wait failure path; returns the status code."""
+        return lib().ccm_wait_selftest(self.h, _stream(stream))
 
     # ---- accounting
     def profile(self, kernel_class: int):

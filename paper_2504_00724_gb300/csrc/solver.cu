@@ -2144,6 +2144,37 @@ int ccm_fmg(ccm_handle* h, double* u, const double* r, int precision, void* stre
 
 int64_t ccm_launch_count(void) { return (int64_t)g_launches.load(); }
 
+}  // extern "C"
+
+namespace {
+
+// self-test of the bounded wait: one CTA waits, through the tile-wait helper of the solve
+// kernels, on an mbarrier phase that nothing completes (no copy is issued, nobody arrives), so
+// the wait runs out, sets the error word and the kernel returns
+__global__ void k_wait_selftest(int* err) {
+  __shared__ __align__(8) uint64_t bar;
+  if (threadIdx.x == 0) dev::mbar_init(&bar, 1);
+  __syncthreads();
+  dev::tile_wait(&bar, err);
+}
+
+}  // namespace
+
+extern "C" {
+
+int ccm_wait_selftest(ccm_handle* h, void* stream) {
+  if (!h) return CCM_EINVAL;
+  cudaStream_t s = (cudaStream_t)stream;
+  KL(k_wait_selftest<<<1, 32, 0, s>>>(h->derr));
+  CCM_CUDA(cudaMemcpyAsync(h->herr, h->derr, sizeof(int), cudaMemcpyDeviceToHost, s));
+  CCM_CUDA(cudaStreamSynchronize(s));
+  const int timed_out = *h->herr;
+  *h->herr = 0;
+  CCM_CUDA(cudaMemsetAsync(h->derr, 0, sizeof(int), s));
+  CCM_CUDA(cudaStreamSynchronize(s));
+  return timed_out ? CCM_ETIMEOUT : CCM_OK;
+}
+
 int ccm_profile(ccm_handle* h, int kernel_class) {
   if (!h || kernel_class < 0 || kernel_class > CCM_PROF_RESTRICT_FP32) return CCM_EINVAL;
   if (kernel_class != h->prof_class) {
