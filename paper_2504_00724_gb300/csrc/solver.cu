@@ -5,6 +5,8 @@
 #include <atomic>
 #include <chrono>
 #include <cmath>
+#include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <memory>
 #include <mutex>
@@ -1528,6 +1530,15 @@ int ccm_set_cycle_params(ccm_handle* h, double omega, int nu1, int nu2, int inne
 
 }  // extern "C"
 
+// CCM_LOG=1 in the environment: the solves print their residual history to stderr
+static bool log_enabled() {
+  static const bool on = [] {
+    const char* v = std::getenv("CCM_LOG");
+    return v && v[0] && v[0] != '0';
+  }();
+  return on;
+}
+
 // r_hat = h^2 (f - N g) and the initial guess into slots [0, nb) of the level-0 FP64 arrays,
 // from right-hand sides [k0, k0 + nb) of the caller's arrays (g may be NULL: g = 0)
 static int load_rhs(ccm_handle* h, const double* f, const double* g, const double* u, int k0, int nb, double* U0,
@@ -1652,6 +1663,12 @@ int ccm_solve(ccm_handle* h, const double* f, const double* g, double* u, int nr
     local.iterations = it;
     local.rel_residual = wr;
     if (st) *st = local;
+    if (log_enabled()) {
+      std::fprintf(stderr, "ccm_solve: right-hand sides %d-%d, %s, %d outer iterations, status %d\n", k0,
+                   k0 + nb - 1, fp64 ? "FP64" : "mixed", it, result);
+      for (int j = 0; j <= std::min(it, 63); ++j)
+        std::fprintf(stderr, "ccm_solve:   iteration %2d  rel. residual %.3e\n", j, local.history[j]);
+    }
     if (result == CCM_ETIMEOUT) break;
   }
   h->nb = 1;
@@ -1886,6 +1903,9 @@ int ccm_group_solve(ccm_group* G, const double* const* f, const double* const* g
       rk = CCM_ENOCONV;
     }
     if (result == CCM_OK) result = rk;
+    if (log_enabled())
+      std::fprintf(stderr, "ccm_group_solve: member %d, %d outer iterations, rel. residual %.3e, status %d\n", k, it,
+                   r, rk);
     if (st) {
       ccm_stats& o = st[k];
       o = ccm_stats{};
