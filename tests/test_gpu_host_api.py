@@ -44,3 +44,18 @@ def test_pageable_host_buffers_and_several_rhs(setup):
     U = np.zeros_like(F)
     s.solve_host(F, G, U)                        # numpy arrays: pageable memory
     assert np.array_equal(U, u_dev.cpu().numpy())
+
+
+def test_host_solve_zeroes_cells_outside_the_domain(setup):
+    """The cells outside the domain are written as zero whatever the caller's buffer held there;
+    the non-empty cells hold the solution."""
+    s, fa, ga = setup
+    ne = s.cell_map()[0] != 0
+    u_dev, _ = s.solve(torch.tensor(fa, device="cuda"), torch.tensor(ga, device="cuda"))
+    fh = torch.tensor(fa).pin_memory()
+    gh = torch.tensor(ga).pin_memory()
+    uh = torch.full(fh.shape, 7.0, dtype=torch.float64).pin_memory()
+    uh[torch.from_numpy(ne)] = 0.0
+    s.solve_host(fh, gh, uh)
+    assert torch.equal(uh, u_dev.cpu())
+    assert np.all(uh.numpy()[~ne] == 0.0)
