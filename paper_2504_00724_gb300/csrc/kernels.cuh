@@ -29,6 +29,9 @@ template <typename T>
 struct Stencil {
   T w[25];        // [dj + 2][di + 2]
   T omega_d;      // omega / w[2][2] (SMO-1 weight over the diagonal)
+  // the same stencil factored: w[dj][di] = lx[di] [dj = 0] + ly[dj] [di = 0] + gy[dj] gx[di]
+  // (eq. stdLap along x and y, the product of two eq. stdGrad derivatives for the mixed term)
+  T lx[5], ly[5], gx[5], gy[5], cc;   // cc = lx[2] + ly[2]
 };
 
 // (h^2 L u) at a regular cell: 9-point cross (b = 0) or the full 5 x 5 box

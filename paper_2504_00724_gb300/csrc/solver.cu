@@ -809,6 +809,22 @@ int upload_hierarchy(ccm_handle* h) {
   }
   h->S64.omega_d = h->par.omega / w[2][2];
   h->S32.omega_d = (float)(h->par.omega / w[2][2]);
+  {
+    static const double lap[5] = {-1.0, 16.0, -30.0, 16.0, -1.0};
+    static const double grad[5] = {1.0, -8.0, 0.0, 8.0, -1.0};
+    for (int k = 0; k < 5; ++k) {
+      h->S64.lx[k] = h->a * lap[k] / 12.0;
+      h->S64.ly[k] = h->c * lap[k] / 12.0;
+      h->S64.gx[k] = grad[k] / 12.0;
+      h->S64.gy[k] = h->b * grad[k] / 12.0;
+      h->S32.lx[k] = (float)h->S64.lx[k];
+      h->S32.ly[k] = (float)h->S64.ly[k];
+      h->S32.gx[k] = (float)h->S64.gx[k];
+      h->S32.gy[k] = (float)h->S64.gy[k];
+    }
+    h->S64.cc = h->S64.lx[2] + h->S64.ly[2];
+    h->S32.cc = (float)h->S64.cc;
+  }
 
   Arena& A = h->arena;
   const int nl = (int)h->H.levels.size();
