@@ -30,6 +30,11 @@ struct SmoothArgs {
   uint32_t stage;      // bytes per stage (multiple of 128)
 };
 
+// hint: bring the line holding p into this SM's L1 (static data only)
+__device__ __forceinline__ void prefetch_l1(const void* p) {
+  asm volatile("prefetch.global.L1 [%0];" ::"l"(p));
+}
+
 // two adjacent values of T (8 or 16 bytes, aligned)
 template <typename T> struct Pair;
 template <> struct Pair<float> { using type = float2; };
@@ -285,8 +290,25 @@ __global__ void __launch_bounds__(256, 3) k_smooth(const __grid_constant__ CUten
   extern __shared__ __align__(128) unsigned char smem_raw[];
   __shared__ __align__(8) uint64_t bar[2];
   __shared__ T part[8][32];
-  pdl_enter();
   const SweepArgs<T>& a = A.a;
+  // While the previous launch drains: when the first item is an SMO-2 block, pull its static
+  // fitted-row data (columns, coefficients, cells, parents) into L1, so that the residual
+  // gathers after the wait need one round trip to the iterate instead of two
+  if ((int)blockIdx.x < A.nbi) {
+    const int b = blockIdx.x;
+    const int es = a.blk[4 * b + 2], ne = a.blk[4 * b + 3] - es;
+    for (int e = threadIdx.x; e < ne; e += blockDim.x) {
+      const int row = es + e;
+      prefetch_l1(a.cell + row);
+#pragma unroll 15
+      for (int m = 0; m < a.W; ++m) {
+        prefetch_l1(a.col + (long)m * a.n2 + row);
+        prefetch_l1(a.val + (long)m * a.n2 + row);
+        if (PRO && a.par) prefetch_l1(a.par + (long)m * a.n2 + row);
+      }
+    }
+  }
+  pdl_enter();
   // this CTA's right-hand side of the batch (blockIdx.y)
   const long bo = (long)blockIdx.y * a.bs;
   const T* __restrict__ u_old = a.u_old + bo;
