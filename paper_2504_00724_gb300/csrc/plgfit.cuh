@@ -232,7 +232,8 @@ __global__ void __launch_bounds__(128) k_plg_fit(FitLevel L, FitBatch B) {
 }
 
 // 2-norm condition number of the 15 x 15 FV sample matrix of each pair by one-sided Jacobi
-// (column rotations until every pair of columns is orthogonal to 1e-15); lane r holds row r
+// (column rotations until every pair of columns is orthogonal to 1e-15); lane r samples row
+// r, lanes 1..7 then rotate seven disjoint column pairs at a time
 __global__ void __launch_bounds__(128) k_plg_cond(FitLevel L, FitBatch B) {
   __shared__ FitSmem sm[4];
   const int lane = threadIdx.x & 31, wi = threadIdx.x >> 5;
@@ -244,23 +245,41 @@ __global__ void __launch_bounds__(128) k_plg_cond(FitLevel L, FitBatch B) {
   fit_frame(L, cells, lane, pxi, pyj);
   fit_sample(L, cells, lane, pxi, pyj, S);
   __syncwarp();
+  // parallel cyclic ordering: a round robin over 16 players (player 15 a dummy) pairs the
+  // columns (s + k) mod 15 and (s - k) mod 15, k = 1..7, in step s; those pairs are disjoint,
+  // so lanes 1..7 rotate them at once, and the 15 steps of a sweep visit every pair once
   for (int sweep = 0; sweep < 60; ++sweep) {
     double off = 0;
-    for (int p = 0; p < FNM; ++p)
-      for (int q = p + 1; q < FNM; ++q) {
-        const double up = lane < FNM ? S.M[lane][p] : 0.0, uq = lane < FNM ? S.M[lane][q] : 0.0;
-        const double a = warp_sum(up * up), b = warp_sum(uq * uq), g = warp_sum(up * uq);
-        if (fabs(g) <= 1e-300 || fabs(g) <= 1e-15 * sqrt(a * b)) continue;
-        off = fmax(off, fabs(g) / sqrt(a * b));
-        const double zeta = (b - a) / (2 * g);
-        const double t = (zeta >= 0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1 + zeta * zeta));
-        const double cs = 1 / sqrt(1 + t * t), sn = cs * t;
-        if (lane < FNM) {
-          S.M[lane][p] = cs * up - sn * uq;
-          S.M[lane][q] = sn * up + cs * uq;
+    for (int st = 0; st < FNM; ++st) {
+      if (lane >= 1 && lane <= 7) {
+        int p = (st + lane) % FNM, q = (st + FNM - lane) % FNM;
+        if (p > q) {
+          const int t = p;
+          p = q;
+          q = t;
         }
-        __syncwarp();
+        double a = 0, b = 0, g = 0;
+        for (int r = 0; r < FNM; ++r) {
+          const double up = S.M[r][p], uq = S.M[r][q];
+          a += up * up;
+          b += uq * uq;
+          g += up * uq;
+        }
+        if (!(fabs(g) <= 1e-300 || fabs(g) <= 1e-15 * sqrt(a * b))) {
+          off = fmax(off, fabs(g) / sqrt(a * b));
+          const double zeta = (b - a) / (2 * g);
+          const double t = (zeta >= 0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1 + zeta * zeta));
+          const double cs = 1 / sqrt(1 + t * t), sn = cs * t;
+          for (int r = 0; r < FNM; ++r) {
+            const double up = S.M[r][p], uq = S.M[r][q];
+            S.M[r][p] = cs * up - sn * uq;
+            S.M[r][q] = sn * up + cs * uq;
+          }
+        }
       }
+      __syncwarp();
+    }
+    for (int o = 16; o; o >>= 1) off = fmax(off, __shfl_xor_sync(0xffffffffu, off, o));
     if (off < 1e-15) break;
   }
   double smax = 0, smin = 1e300;
