@@ -175,6 +175,10 @@ def oracle_sample(n: int, steps: int, min_seconds: float = 10.0, max_solves: int
             "seconds": tot, "solves": len(times)}
 
 
+def workload_name(n: int) -> str:
+    return f"star r=0.3+0.08cos5t, (a,b,c)=(1,0.5,2), {n}x{n} cells, Dirichlet, u=exp(x)sin(pi y)+x^4"
+
+
 def run_reference(args, rank: int):
     if rank != 0:
         return
@@ -185,9 +189,8 @@ def run_reference(args, rank: int):
     line = {"impl": "reference", "metric": METRIC, "value": cb["value"], "unit": UNIT, "n_gpus": args.gpus,
             "steps": steps, "warmup": args.warmup, "ms_per_step": 1000 * cb["seconds"] / cb["solves"],
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic", "config": {"workload": f"star (1,0.5,2) {args.n}x{args.n}, oracle on a "
-                                                       f"{args.sample_n}x{args.sample_n} sample",
-                                            "rtol": RTOL},
+            "data": "synthetic", "config": {"workload": workload_name(args.n), "rtol": RTOL,
+                                            "oracle_sample": f"the same star on {args.sample_n}x{args.sample_n} cells"},
             "cpu_baseline": {k: cb[k] for k in ("value", "unit", "cores", "kind", "sample")},
             "e2e": {"value": cb["value"], "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
@@ -480,8 +483,7 @@ def main():
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64+f32", "data": "synthetic",
-            "config": {"workload": f"star r=0.3+0.08cos5t, (a,b,c)=(1,0.5,2), {args.n}x{args.n} cells, Dirichlet, "
-                                   f"u=exp(x)sin(pi y)+x^4", "unknowns": ncell, "irregular": int(info.n_irregular),
+            "config": {"workload": workload_name(args.n), "unknowns": ncell, "irregular": int(info.n_irregular),
                        "levels": int(info.levels), "coarsest": args.coarsest, "rtol": RTOL,
                        "precision": "FP32 V-cycles in FP64 refinement",
                        "l2": "flushed (256 MB write) before every step", "parallelism": f"replicas x{world}"},
