@@ -210,20 +210,22 @@ int ccm_apply(ccm_handle* h, const double* u, const double* g, double* out, int 
 
 /* Allocation-free operator application.  Same result as ccm_apply with nrhs = 1
  * (out = L u + N g on the finest level, physical units; u, out: device [ny][nx] FP64, g:
- * device [n_segments] FP64 or NULL), for callers that cannot allocate device memory at call
- * time: code running inside a CUDA stream capture, which cudaMalloc would break, or under a
- * host framework whose allocator owns all device memory.  The handle is set up beforehand.
- * Unlike ccm_apply, this call does not use the handle's work arrays.  It uses a fixed
- * file-scope device array (the library keeps CCM_NOALLOC_SCRATCH_BYTES = 16 MiB on every
- * device that loads it, until the process exits).  That array holds two padded FP64 grids of
- * at most CCM_NOALLOC_MAX_PADDED cells each, where the padded size is
- * ((nx + 4) rounded up to a multiple of 32) * (ny + 4); larger grids are rejected with
- * CCM_ETOOLARGE before any work is queued.  It calls no cudaMalloc, cudaFree or allocating
- * library routine.  The first call on a device looks up the array's device address (once per
- * device): make that first call outside any stream capture.  Every call shares the array,
- * so calls that overlap on the GPU (other streams, other handles) race; the call clears the
- * part of the array it uses before filling it.  The paper has no counterpart of this entry
- * point: it exists for the memory model of its callers. */
+ * device [n_segments] FP64 or NULL).  It is for callers that must not allocate device memory
+ * at call time: a host framework whose caching allocator owns all device memory (a second
+ * allocator beside it fragments the device and can fail where the framework would not), or a
+ * latency-bound loop that cannot afford cudaMalloc / cudaFree, which may synchronise the
+ * device.  The handle is set up beforehand, and its device must be the current device
+ * (CCM_EINVAL otherwise, before any work is queued).  Unlike ccm_apply, this call does not use
+ * the handle's work arrays.  It uses a fixed file-scope device array (the library keeps
+ * CCM_NOALLOC_SCRATCH_BYTES = 16 MiB on every device that loads it, until the process exits).
+ * That array holds two padded FP64 grids of at most CCM_NOALLOC_MAX_PADDED cells each, where
+ * the padded size is ((nx + 4) rounded up to a multiple of 32) * (ny + 4); larger grids are
+ * rejected with CCM_ETOOLARGE before any work is queued.  It calls no cudaMalloc, cudaFree or
+ * allocating library routine.  The first call on a device looks up the array's device address
+ * (once per device), so make that first call before any stream capture.  Every call shares
+ * the array, so calls that overlap on the GPU (other streams, other handles) race; the call
+ * clears the part of the array it uses before filling it.  The paper has no counterpart of
+ * this entry point: it exists for the memory model of its callers. */
 #define CCM_NOALLOC_MAX_PADDED (1L << 20)
 #define CCM_NOALLOC_SCRATCH_BYTES (2L * CCM_NOALLOC_MAX_PADDED * 8L)
 int ccm_apply_noalloc(const ccm_handle* h, const double* u, const double* g, double* out, void* stream);
@@ -324,6 +326,31 @@ int ccm_vcycle(ccm_handle* h, double* u, const double* r, int precision, void* s
  * paper fixes omega = 0.5, nu1 = nu2 = 3 (Sec. 5); these are free parameters of Alg. 2.
  * Errors: CCM_EINVAL, CCM_ECUDA. */
 int ccm_set_cycle_params(ccm_handle* h, double omega, int nu1, int nu2, int inner_cycles, int cycle);
+
+/* Launch shape of the persistent kernels (testing and tuning; not part of the method).  The
+ * smoothing sweep of a level with TMA-staged tiles is one launch whose work items are the
+ * level's SMO-2 blocks and its 64 x 32 tiles with a regular cell (Sec. 4.1), and the residual
+ * + restriction is one launch over the fine tiles that restriction visits (Alg. 2).  Each CTA
+ * takes items c, c + G, c + 2 G, ... through a two-stage copy ring, G = the CTAs given to one
+ * right-hand side: min(items, resident CTAs of the GPU / nrhs, launch cap).
+ * ccm_set_launch_cap: at most max_ctas CTAs per right-hand side in both kernels on every
+ *   level (0: no cap, the default), so that small grids also run every CTA through many ring
+ *   items.  Results do not depend on it.  Synchronises the device and drops the captured
+ *   iteration graphs.  Errors: CCM_EINVAL, CCM_ECUDA.
+ * ccm_level_launch: the shape of level `level`'s sweep and restriction launches for
+ *   precision CCM_FP64 or CCM_MIXED when nrhs right-hand sides run together (1 for
+ *   ccm_level_smooth, ccm_level_restrict, ccm_vcycle and single solves).  Counts are 0 where
+ *   the level does not use that persistent kernel (small levels, the bottom level, the
+ *   sequential smoother).  Host-only, no device work.  Errors: CCM_EINVAL. */
+typedef struct {
+  int sweep_items;     /* work items of one sweep launch (SMO-2 blocks + tiles) */
+  int sweep_blocks;    /* of which SMO-2 block items */
+  int sweep_ctas;      /* CTAs per right-hand side */
+  int restrict_items;  /* tiles of one residual + restriction launch */
+  int restrict_ctas;   /* CTAs per right-hand side */
+} ccm_launch_info;
+int ccm_set_launch_cap(ccm_handle* h, int max_ctas);
+int ccm_level_launch(const ccm_handle* h, int level, int precision, int nrhs, ccm_launch_info* out);
 
 /* One FMG cycle (Sec. 4, the FMG figure) for L u = r on the finest level, from the zero guess:
  * r restricted level by level to the bottom level and solved there, then one V-cycle (Alg. 2)

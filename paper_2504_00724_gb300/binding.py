@@ -55,6 +55,11 @@ class ccm_info(ctypes.Structure):
                 ("plg_cond_max", ctypes.c_double), ("batch", ctypes.c_int)]
 
 
+class ccm_launch_info(ctypes.Structure):
+    _fields_ = [("sweep_items", ctypes.c_int), ("sweep_blocks", ctypes.c_int), ("sweep_ctas", ctypes.c_int),
+                ("restrict_items", ctypes.c_int), ("restrict_ctas", ctypes.c_int)]
+
+
 class ccm_stats(ctypes.Structure):
     _fields_ = [("iterations", ctypes.c_int), ("rel_residual", ctypes.c_double),
                 ("history", ctypes.c_double * 64)]
@@ -88,6 +93,8 @@ _SIGS = {
     "ccm_vcycle": (I, [P, P, P, I, P]),
     "ccm_fmg": (I, [P, P, P, I, P]),
     "ccm_set_cycle_params": (I, [P, ctypes.c_double, I, I, I, I]),
+    "ccm_set_launch_cap": (I, [P, I]),
+    "ccm_level_launch": (I, [P, I, I, I, ctypes.POINTER(ccm_launch_info)]),
     "ccm_free": (None, [P]),
     "ccm_strerror": (ctypes.c_char_p, [I]),
     "ccm_host_build": (I, [ctypes.POINTER(ccm_problem), ctypes.POINTER(ccm_params), ctypes.POINTER(P)]),
@@ -371,6 +378,16 @@ class Solver:
         _check(lib().ccm_set_cycle_params(self.h, float(vals[0]), *[int(v) for v in vals[1:]]),
                "ccm_set_cycle_params")
         p.omega, p.nu1, p.nu2, p.inner_cycles, p.cycle = vals
+
+    def set_launch_cap(self, max_ctas: int):
+        """At most max_ctas CTAs per right-hand side in the persistent kernels (0: no cap)."""
+        _check(lib().ccm_set_launch_cap(self.h, int(max_ctas)), "ccm_set_launch_cap")
+
+    def level_launch(self, level, precision=CCM_FP64, nrhs=1) -> ccm_launch_info:
+        """Items and CTAs of level `level`'s persistent sweep and restriction launches."""
+        out = ccm_launch_info()
+        _check(lib().ccm_level_launch(self.h, level, precision, nrhs, ctypes.byref(out)), "ccm_level_launch")
+        return out
 
     def fmg(self, r, precision=CCM_FP64, stream=None):
         """One FMG cycle for L u = r from the zero guess (ccm_fmg)."""

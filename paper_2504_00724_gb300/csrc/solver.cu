@@ -176,6 +176,7 @@ struct ccm_handle {
   int coarse_ctas = 0;         // CTAs of that cluster (16, else 8)
   size_t coarse_smem = 0;      // its dynamic shared memory (SMO-2 extended-row residuals)
   bool persistent = true;      // block-Jacobi sweeps of TMA levels as one persistent launch
+  int launch_cap = 0;          // > 0: at most this many CTAs per right-hand side in the persistent kernels
   ccm_handle* adj = nullptr;   // the transposed operators' hierarchy (built by ccm_solve_T)
   // one CUDA graph per outer iteration and precision (captured on first use, on a private
   // stream: the legacy default stream cannot be captured)
@@ -196,6 +197,14 @@ struct ccm_handle {
 namespace {
 
 inline int ceil_div(long a, long b) { return (int)((a + b - 1) / b); }
+
+// CTAs per right-hand side of a persistent launch: every item gets its own CTA up to the
+// resident capacity shared by the nb right-hand sides, and at most the handle's launch cap
+inline int persistent_ctas(int items_grid, int cap, int nb, int launch_cap) {
+  int g = std::min(items_grid, std::max(1, ceil_div(cap, nb)));
+  if (launch_cap > 0) g = std::min(g, launch_cap);
+  return std::max(1, g);
+}
 
 std::atomic<long long> g_launches{0};
 // every kernel launch of the library goes through KL so that launches can be counted
@@ -357,7 +366,7 @@ void sweep_persistent(ccm_handle* H, DevLevel& L, cudaStream_t s, DevLevel* C) {
   a.bs = L.npad;
   a.bsc = C ? C->npad : 0;
   // with a batch, fewer CTAs per right-hand side so that the whole launch stays resident
-  const dim3 grid(std::min(L.smooth_grid[k], std::max(1, ceil_div(L.smooth_cap[k], H->nb))), H->nb);
+  const dim3 grid(persistent_ctas(L.smooth_grid[k], L.smooth_cap[k], H->nb, H->launch_cap), H->nb);
   const size_t smem = L.smooth_smem[k];
   if (C) {
     const CUtensorMap& tu = TmUc<T>(L, *C);
@@ -533,7 +542,7 @@ void restrict_to(ccm_handle* H, DevLevel& F, DevLevel& C, cudaStream_t s) {
     A.bsc = C.npad;
     const CUtensorMap& tv = kk == 0 ? F.tmv64 : F.tmv32;
     const size_t smem = 2 * (size_t)A.stage;
-    const dim3 rgrid(std::min(F.restrict_grid[kk], std::max(1, ceil_div(F.restrict_cap[kk], H->nb))), H->nb);
+    const dim3 rgrid(persistent_ctas(F.restrict_grid[kk], F.restrict_cap[kk], H->nb, H->launch_cap), H->nb);
     if (H->cross)
       KL(launch_k(dev::k_restrict_p<T, true>, rgrid, 256, smem, s, TmU<T>(F), TmR<T>(F), F.tmcls, tv, A));
     else
@@ -1356,6 +1365,10 @@ int ccm_apply_noalloc(const ccm_handle* hc, const double* u, const double* g, do
   ccm_handle* h = const_cast<ccm_handle*>(hc);
   const DevLevel& L = h->L[0];
   if (L.npad > CCM_NOALLOC_MAX_PADDED) return CCM_ETOOLARGE;
+  // the scratch address below is the current device's; the handle's arrays live on h->device
+  int cur = -1;
+  if (cudaGetDevice(&cur) != cudaSuccess) return CCM_ECUDA;
+  if (cur != h->device) return CCM_EINVAL;
   double* scratch = nullptr;
   int rc = noalloc_scratch(&scratch);
   if (rc) return rc;
@@ -1519,6 +1532,39 @@ static void drop_graphs(ccm_handle* h) {
   }
   for (cudaEvent_t e : h->gprof_ev) cudaEventDestroy(e);
   h->gprof_ev.clear();
+}
+
+int ccm_set_launch_cap(ccm_handle* h, int max_ctas) {
+  if (!h || max_ctas < 0) return CCM_EINVAL;
+  if (cudaDeviceSynchronize() != cudaSuccess) return CCM_ECUDA;
+  drop_graphs(h);
+  h->launch_cap = max_ctas;
+  if (h->adj) {
+    drop_graphs(h->adj);
+    h->adj->launch_cap = max_ctas;
+  }
+  return CCM_OK;
+}
+
+int ccm_level_launch(const ccm_handle* h, int level, int precision, int nrhs, ccm_launch_info* out) {
+  if (!h || !out || level < 0 || level >= (int)h->L.size() || nrhs < 1 ||
+      (precision != CCM_FP64 && precision != CCM_MIXED))
+    return CCM_EINVAL;
+  const int k = precision == CCM_FP64 ? 0 : 1;
+  const DevLevel& L = h->L[level];
+  const bool last = level == (int)h->L.size() - 1;
+  const bool bj = h->par.smoother == 1 && h->par.ras_passes <= 1 && h->persistent;
+  *out = ccm_launch_info{};
+  if (!last && bj && L.smooth_ok[k]) {
+    out->sweep_items = L.nblk + L.ntiles64;
+    out->sweep_blocks = L.nblk;
+    out->sweep_ctas = persistent_ctas(L.smooth_grid[k], L.smooth_cap[k], nrhs, h->launch_cap);
+  }
+  if (!last && bj && L.tma && L.ntiles64r && L.restrict_ok[k]) {
+    out->restrict_items = L.ntiles64r;
+    out->restrict_ctas = persistent_ctas(L.restrict_grid[k], L.restrict_cap[k], nrhs, h->launch_cap);
+  }
+  return CCM_OK;
 }
 
 int ccm_set_cycle_params(ccm_handle* h, double omega, int nu1, int nu2, int inner_cycles, int cycle) {

@@ -1,8 +1,8 @@
 """The allocation-free operator application (ccm_apply_noalloc), called through the C ABI.
 
-Callers that cannot allocate device memory at call time (inside a CUDA stream capture, or
-under a framework whose allocator owns the device) use this entry point: its scratch is a
-fixed device array inside the library.  Its result must equal ccm_apply's, also on the
+Callers that must not allocate device memory at call time (a framework whose caching
+allocator owns the device, or a loop that cannot afford cudaMalloc's device synchronisation)
+use this entry point: its scratch is a fixed device array inside the library.  Its result must equal ccm_apply's, also on the
 second of two calls in a row (the scratch keeps the previous call's contents), and grids
 beyond the fixed scratch must be refused cleanly."""
 import ctypes
@@ -58,7 +58,9 @@ def test_noalloc_rejects_grids_beyond_its_scratch():
     s = P.Solver(W.star(1024))
     try:
         u = torch.zeros((1024, 1024), dtype=torch.float64, device="cuda")
-        out = torch.zeros_like(u)
+        out = torch.full_like(u, 7.0)
         assert _noalloc(s, u, None, out) == -10     # CCM_ETOOLARGE, nothing queued
+        torch.cuda.synchronize()
+        assert bool((out == 7.0).all())             # out untouched
     finally:
         s.close()

@@ -21,7 +21,7 @@ from __future__ import annotations
 
 import math
 from dataclasses import dataclass, field
-from typing import Callable, List, Optional, Sequence
+from typing import Callable, List, Optional, Sequence, Tuple
 
 import numpy as np
 
@@ -196,49 +196,48 @@ def star(n: int, abc=(1.0, 0.5, 2.0), r0=0.3, amp=0.08, k=5, centre=(0.5, 0.5)) 
 GEOMETRY_GRIDS = (128, 256, 512, 1024)
 
 
-def geometry_of_seed(seed: int, abc=(1.0, 0.5, 2.0)) -> Problem:
-    """One geometry of the many-geometry workload.  numpy's PCG64(seed) draws, in this order:
-    the grid n uniformly from {128, 256, 512, 1024}; the kind (star or ellipse, even odds);
-    the centre (0.5, 0.5) + U[-0.04, 0.04]^2; then for a star r = r0 + amp cos(k t) the values
-    r0 ~ U[0.25, 0.32], amp ~ U[0.03, 0.08], k ~ {3, 4, 5}, for an ellipse the semi-axes
-    U[0.25, 0.36] x U[0.15, 0.3] and the rotation U[0, pi).  The domain is the curve's
-    interior (the box is not part of the boundary), Dirichlet on the curve; every curve keeps
-    at least 0.07 from the box."""
+def geometry_of_seed(seed: int) -> Tuple[Problem, "Manufactured"]:
+    """One geometry of the many-geometry workload, with its manufactured solution.  numpy's
+    PCG64(seed) draws, in this order: the grid n uniformly from {128, 256, 512, 1024}; the kind
+    (star or three-ellipse domain, even odds); then for a star r = r0 + amp cos(k t) centred at
+    (0.5, 0.5) the values r0 ~ U[0.25, 0.32], amp ~ U[0.05, 0.1], k uniform in {3, ..., 7}
+    with the coefficients and manufactured u of the star workload ((a, b, c) = (1, 0.5, 2),
+    Dirichlet on the curve); for the other kind the unit square minus three ellipses placed
+    with PCG64(seed) (three_ellipses), with the coefficients, boundary conditions and
+    manufactured u of the three-ellipse workload ((1, 0, 1), Neumann on the ellipses,
+    Dirichlet on the box)."""
     rng = np.random.Generator(np.random.PCG64(seed))
     n = int(GEOMETRY_GRIDS[rng.integers(0, len(GEOMETRY_GRIDS))])
-    is_star = bool(rng.integers(0, 2) == 0)
-    cx, cy = 0.5 + rng.uniform(-0.04, 0.04, size=2)
-    a, b, c = abc
-    if is_star:
-        r0, amp = rng.uniform(0.25, 0.32), rng.uniform(0.03, 0.08)
-        k = int(rng.integers(3, 6))
-        curve = Curve(STAR, (cx, cy, r0, amp, float(k)), +1, DIRICHLET)
-        name = f"geom{seed}_star_{n}"
-    else:
-        ea, eb, phi = rng.uniform(0.25, 0.36), rng.uniform(0.15, 0.3), rng.uniform(0.0, math.pi)
-        curve = Curve(ELLIPSE, (cx, cy, ea, eb, phi), +1, DIRICHLET)
-        name = f"geom{seed}_ellipse_{n}"
-    return Problem(a, b, c, 0.0, 0.0, 1.0 / n, n, n, NONE, [curve], name=name)
+    if rng.integers(0, 2) == 0:
+        r0, amp = float(rng.uniform(0.25, 0.32)), float(rng.uniform(0.05, 0.1))
+        k = int(rng.integers(3, 8))
+        p = star(n, (1.0, 0.5, 2.0), r0, amp, k)
+        p.name = f"geom{seed}_star{k}_{n}"
+        return p, mms_star()
+    p = three_ellipses(n, seed=seed, min_gap=1.0 / 8)
+    p.name = f"geom{seed}_ellipses_{n}"
+    return p, mms_ellipses()
 
 
-def many_geometries(count: int = 64, seed0: int = 0) -> List[Problem]:
-    """The independent geometries of seeds seed0 .. seed0 + count - 1 (geometry_of_seed)."""
+def many_geometries(count: int = 64, seed0: int = 0) -> List[Tuple[Problem, "Manufactured"]]:
+    """The independent geometries (with manufactured solutions) of seeds seed0 .. seed0 +
+    count - 1 (geometry_of_seed)."""
     return [geometry_of_seed(seed0 + k) for k in range(count)]
 
 
 def three_ellipses(n: int, seed: int = 0, abc=(1.0, 0.0, 1.0), curve_bc: int = NEUMANN,
-                   gap_cells: float = 4.0) -> Problem:
+                   gap_cells: float = 4.0, min_gap: float = 1.0 / 16) -> Problem:
     """Unit square minus three disjoint ellipses (semi-axes 0.10x0.06, 0.08x0.08, 0.12x0.05).
 
     Centres (uniform in the unit square) and rotations (uniform in [0, pi)) are drawn with
     numpy's PCG64(seed) by rejection, so that every pair of ellipses and every ellipse and
     the box keep a gap of at least max(gap_cells*h, 1/16), checked on 720 samples per
-    curve.  The 1/16 floor keeps the geometry the same for every n >= 64 and leaves the
-    curves separated on the coarse multigrid levels too."""
+    curve.  The floor min_gap (1/16) keeps the geometry the same for every n >= 64 and leaves
+    the curves separated on the coarse multigrid levels too."""
     h = 1.0 / n
     rng = np.random.Generator(np.random.PCG64(seed))
     axes = [(0.10, 0.06), (0.08, 0.08), (0.12, 0.05)]
-    gap = max(gap_cells * h, 1.0 / 16)
+    gap = max(gap_cells * h, min_gap)
     ts = np.linspace(0.0, 2 * math.pi, 721)
     placed, params = [], []
     for (ea, eb) in axes:
@@ -264,20 +263,6 @@ def three_ellipses(n: int, seed: int = 0, abc=(1.0, 0.0, 1.0), curve_bc: int = N
     a, b, c = abc
     curves = [Curve(ELLIPSE, p, -1, curve_bc) for p in params]
     return Problem(a, b, c, 0.0, 0.0, h, n, n, DIRICHLET, curves, name=f"three_ellipses_{n}")
-
-
-def random_geometry(seed: int) -> tuple:
-    """One geometry of the many-geometry batch: a star or a three-ellipse domain.
-
-    Returns (problem, manufactured).  Grids are drawn from {128, 256, 512, 1024}."""
-    rng = np.random.Generator(np.random.PCG64(1000 + seed))
-    n = int(rng.choice([128, 256, 512, 1024]))
-    if seed % 2 == 0:
-        k = int(rng.integers(3, 8))
-        r0 = float(rng.uniform(0.25, 0.32))
-        amp = float(rng.uniform(0.05, 0.1))
-        return star(n, (1.0, 0.5, 2.0), r0, amp, k), mms_star()
-    return three_ellipses(n, seed=seed, abc=(1.0, 0.0, 1.0)), mms_ellipses()
 
 
 def smoothed_normal_rhs(n: int, nrhs: int, mask: np.ndarray, seed: int = 0) -> np.ndarray:
