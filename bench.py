@@ -11,9 +11,21 @@ value:  mixed form (FP32 cycles in FP64 refinement), inputs resident in HBM, CUD
 e2e:    the same through the C ABI with pinned host buffers (ccm_solve_host): the kernels read f,
         g and the initial guess from host memory and write u back, inside the timing.
 fp64:   the plain FP64 form, same workload and tolerance.
-roofline: the dominant kernel class, timed live with CUDA events during the timed steps.
+roofline: the dominant kernel class, timed live with CUDA events during the timed steps;
+        algorithmic bytes per unit as in the method's byte model (12 B per regular cell per
+        FP32 sweep; 16 x 12 B of fitted row plus 2 x 20 x 4 B of banded L22 factors per
+        irregular row), the dense SMO-2 block inverses this build reads instead of the banded
+        factors reported beside them as design overhead.
+vcycle: one FP32 V-cycle, event-timed, against the unfused (120 B per fine cell) and the
+        method-minimum (35 B per fine cell) byte models.
+equal_accuracy: both forms against the exact cell averages and against the discrete solution
+        (solved to rel. residual 1e-13), at rel. residuals 1e-10 and 1e-12.
+configs: the other workloads of the benchmark definition (disk 64^2 FP64; star 256^2 and
+        1024^2 in both forms; three ellipses 2048^2 mixed; the adjoint workload on the star
+        2048^2 with central finite differences in 16 seeded directions).
 cpu_baseline / --impl reference: the CPU oracle (NumPy/SciPy) on a bounded sample of the
-same workload (same domain, coefficients and data at a smaller grid).
+same workload (same domain, coefficients and data at a smaller grid); the baseline also runs
+one oracle process per host core and reports the oracle's setup time separately.
 """
 from __future__ import annotations
 
@@ -79,6 +91,9 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-autotune", action="store_true")
+    ap.add_argument("--no-configs", action="store_true",
+                    help="skip the equal-accuracy comparison and the other workloads (disk 64^2, star 256^2 "
+                         "and 1024^2, three ellipses 2048^2, the adjoint workload)")
     ap.add_argument("--no-batched", action="store_true",
                     help="skip the batched workloads (disk 512^2 with 256 right-hand sides; 64 geometries)")
     ap.add_argument("--coarsest", type=int, default=64,
@@ -149,12 +164,15 @@ class Clocks:
 
 def oracle_sample(n: int, steps: int, min_seconds: float = 10.0, max_solves: int = 400):
     """Time the oracle's multigrid solve (paper parameters) on the star workload at n x n:
-    at least `steps` solves and at least `min_seconds` of solve time (at most max_solves)."""
+    at least `steps` solves and at least `min_seconds` of solve time (at most max_solves).
+    The oracle's setup (cut cells, stencils, fits, hierarchy) is timed separately."""
     import workloads as W
     from oracle import cubature as Q
     from oracle import multigrid as MG
     prob, mms = W.star(n), W.mms_star()
+    t0 = time.perf_counter()
     H = MG.build_hierarchy(prob)
+    setup_s = time.perf_counter() - t0
     lv = H.levels[0]
     fa = Q.cell_averages(lv.cg, mms.f(prob.a, prob.b, prob.c)).ravel()
     ga = Q.boundary_averages(lv.cg, lv.dz.segs, mms.u, mms.ux, mms.uy)
@@ -172,7 +190,31 @@ def oracle_sample(n: int, steps: int, min_seconds: float = 10.0, max_solves: int
     return {"value": ncell * len(times) / tot, "unit": UNIT, "cores": 1, "kind": "oracle",
             "sample": f"star {n}x{n} ({ncell} unknowns), oracle V-cycles (omega 0.5, nu 3) to rtol {RTOL}, "
                       f"{len(times)} solve(s), {np.mean(iters):.0f} cycles each, {tot:.1f} s",
-            "seconds": tot, "solves": len(times)}
+            "seconds": tot, "solves": len(times), "setup_s": setup_s, "unknowns": ncell}
+
+
+def _oracle_worker(args):
+    n, seconds = args
+    out = oracle_sample(n, 1, min_seconds=seconds)
+    return out["unknowns"] * out["solves"], out["seconds"]
+
+
+def oracle_all_cores(n: int, seconds: float = 8.0):
+    """The oracle on every host core: one process per core (spawned, one BLAS thread each),
+    each solving the sample repeatedly for about `seconds`; throughput = unknowns solved by
+    all processes / wall time of the slowest."""
+    import multiprocessing as mp
+    cores = os.cpu_count() or 1
+    ctx = mp.get_context("spawn")
+    t0 = time.perf_counter()
+    with ctx.Pool(cores) as pool:
+        res = pool.map(_oracle_worker, [(n, seconds)] * cores)
+    wall = time.perf_counter() - t0
+    done = sum(r[0] for r in res)
+    busy = max(r[1] for r in res)
+    return {"value": done / busy, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"star {n}x{n}, {cores} processes x 1 BLAS thread, {busy:.1f} s of solves each "
+                      f"({wall:.1f} s wall with setup)"}
 
 
 def workload_name(n: int) -> str:
@@ -255,8 +297,10 @@ def many_geometries_workload(stream, flush, count=64):
     t0 = time.time()
     # bottom levels of about a thousand unknowns (dense inverse): 64^2 cells for a star (the
     # 32^2 level of some 6- and 7-petal stars has an eigenvalue with positive real part), 32^2
-    # for a three-ellipse domain
-    solvers = [P.Solver(p, rtol=RTOL, max_iter=200, coarsest=64 if "star" in p.name else 32) for p in probs]
+    # for a three-ellipse domain, which also takes the GMRES(2) correction (the V-cycle alone
+    # diverges on its larger grids)
+    solvers = [P.Solver(p, rtol=RTOL, max_iter=200, coarsest=64 if "star" in p.name else 32,
+                        krylov=0 if "star" in p.name else 2) for p in probs]
     setup_s = time.time() - t0
     fs, gs, exact = [], [], []
     for s, (p, m) in zip(solvers, drawn):
@@ -296,7 +340,7 @@ def many_geometries_workload(stream, flush, count=64):
                         "r0~U[0.25,0.32], amp~U[0.05,0.1], k in 3..7, (a,b,c)=(1,0.5,2), Dirichlet, "
                         "u=exp(x)sin(pi y)+x^4, and "
                         f"{count - nstar} three-ellipse domains, (1,0,1), Neumann on the ellipses, "
-                        "u=cos(pi x)cos(pi y)+x y^3; grids drawn from "
+                        "u=cos(pi x)cos(pi y)+x y^3, GMRES(2) correction; grids drawn from "
                         f"{{128,256,512,1024}}^2 ({grid_cells} grid cells), mixed precision",
             "max_error_vs_exact": err,
             "value": ncell / (ms / 1000.0), "unit": UNIT, "ms_per_solve": ms, "unknowns": ncell,
@@ -305,6 +349,167 @@ def many_geometries_workload(stream, flush, count=64):
             "rel_residual_max": float(max(x.rel_residual for x in st)),
             "one_after_another": {"value": ncell / (ms1 / 1000.0), "ms": ms1,
                                   "iterations_max": int(max(x.iterations for x in sts))}}
+
+
+def solve_case(prob, mms, precision, stream, flush, rtol=RTOL, coarsest=16, reps=3, **params):
+    """Set up one workload, solve it `reps` times (after one untimed solve that captures the
+    iteration graph) and report unknowns/s (median time), iterations and the max-norm error
+    against the exact cell averages."""
+    import torch
+    import paper_2504_00724_gb300 as P
+    t0 = time.time()
+    sv = P.Solver(prob, precision=precision, rtol=rtol, max_iter=400, coarsest=coarsest, **params)
+    setup_s = time.time() - t0
+    q = sv.quadrature()
+    f = torch.tensor(sv.cell_averages(mms.f(prob.a, prob.b, prob.c), quad=q), device="cuda")
+    g = torch.tensor(sv.boundary_averages(mms.u, mms.ux, mms.uy, quad=q), device="cuda")
+    ua = sv.cell_averages(mms.u, quad=q)
+    ne = sv.cell_map()[0] != 0
+    sv.solve(f, g, stream=stream)
+    per = []
+    for _ in range(reps):
+        flush.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        u, st = sv.solve(f, g, stream=stream)
+        e1.record(stream)
+        e1.synchronize()
+        per.append(e0.elapsed_time(e1))
+    ms = float(np.median(per))
+    out = {"value": int(sv.info.n_cells) / (ms / 1000.0), "unit": UNIT, "ms": ms, "unknowns": int(sv.info.n_cells),
+           "levels": int(sv.info.levels), "iterations": st.iterations, "rel_residual": st.rel_residual,
+           "max_error_vs_exact": float(np.abs(u.cpu().numpy() - ua)[ne].max()), "setup_s": setup_s}
+    sv.close()
+    return out
+
+
+def other_configs(stream, flush):
+    """The benchmark definition's other workloads, each in the form(s) it names."""
+    import paper_2504_00724_gb300 as P
+    import workloads as W
+    out = {}
+    out["disk64_fp64"] = dict(workload="(1,0,1), [0,1]^2 minus the disk r=0.2, 64x64, Dirichlet, "
+                                       "u=sin(2pi x)cos(3pi y)exp(xy), FP64 V-cycles to 16^2",
+                              **solve_case(W.disk_minus(64), W.mms_disk(), P.CCM_FP64, stream, flush))
+    for n in (256, 1024):
+        for prec, tag in ((P.CCM_MIXED, "mixed"), (P.CCM_FP64, "fp64")):
+            out[f"star{n}_{tag}"] = dict(workload=workload_name(n), **solve_case(
+                W.star(n), W.mms_star(), prec, stream, flush, coarsest=64 if n >= 1024 else 16))
+    out["ellipses2048_mixed"] = dict(
+        workload="(1,0,1), [0,1]^2 minus three ellipses (seed 0), 2048x2048, Neumann on the ellipses, "
+                 "Dirichlet on the box, u=cos(pi x)cos(pi y)+x y^3, mixed",
+        krylov="GMRES(2) correction, 3 V-cycles per preconditioner application (the V-cycle alone diverges here)",
+        **solve_case(W.three_ellipses(2048), W.mms_ellipses(), P.CCM_MIXED, stream, flush, coarsest=32, krylov=2))
+    out["star2048_adjoint"] = adjoint_case(stream)
+    return out
+
+
+def adjoint_case(stream, n=2048, ndir=16, eps=1e-6):
+    """The adjoint workload: star at n^2 with (a,b,c) = (1,0.3,1), loss 0.5 ||u - u_obs||^2 with
+    u_obs the exact cell averages plus N(0, (1e-3)^2) noise; the gradient with respect to f and
+    the boundary data by one forward and one adjoint solve (timed), and its agreement with
+    central finite differences in ndir seeded directions (FP64 solves to rel. residual 1e-13)."""
+    import torch
+    import paper_2504_00724_gb300 as P
+    import workloads as W
+    from paper_2504_00724_gb300 import autograd as AG
+    prob, mms = W.star(n, (1.0, 0.3, 1.0)), W.mms_star()
+    s = P.Solver(prob, precision=P.CCM_FP64, rtol=1e-13, max_iter=400)
+    try:
+        q = s.quadrature()
+        fa = s.cell_averages(mms.f(prob.a, prob.b, prob.c), quad=q)
+        ga = s.boundary_averages(mms.u, mms.ux, mms.uy, quad=q)
+        ne = s.cell_map()[0] != 0
+        rng = np.random.Generator(np.random.PCG64(5))
+        uobs = np.where(ne, s.cell_averages(mms.u, quad=q) + 1e-3 * rng.standard_normal(ne.shape), 0.0)
+        ob = torch.tensor(uobs, device="cuda")
+        mask = torch.tensor(ne.astype(np.float64), device="cuda")
+
+        def loss(ff, gg):
+            u = AG.solve(s, ff, gg)
+            return 0.5 * ((u - ob) ** 2 * mask).sum()
+
+        f = torch.tensor(fa, device="cuda", requires_grad=True)
+        g = torch.tensor(ga, device="cuda", requires_grad=True)
+        J = loss(f, g)                 # captures both graphs, untimed
+        J.backward()
+        f.grad = None
+        g.grad = None
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        J = loss(f, g)
+        J.backward()
+        e1.record(stream)
+        e1.synchronize()
+        ms = e0.elapsed_time(e1)
+        gf, gg = f.grad.detach(), g.grad.detach()
+        # the loss is quadratic, so central differences have no truncation error at any step;
+        # what remains is J's rounding and the solves' stopping points, both divided by eps
+        worst = {eps: 0.0, 1e-3: 0.0}
+        for _ in range(ndir):
+            df = torch.tensor(np.where(ne, rng.standard_normal(ne.shape), 0.0), device="cuda")
+            dg = torch.tensor(rng.standard_normal(len(ga)), device="cuda")
+            ad = float((gf * df).sum() + (gg * dg).sum())
+            for e in worst:
+                with torch.no_grad():
+                    jp = loss(f + e * df, g + e * dg).item()
+                    jm = loss(f - e * df, g - e * dg).item()
+                worst[e] = max(worst[e], abs((jp - jm) / (2 * e) - ad) / abs(ad))
+        return {"workload": f"star {n}x{n}, (a,b,c)=(1,0.3,1), loss 0.5||u-u_obs||^2, u_obs = exact cell "
+                            "averages + N(0,1e-3^2) (seed 5), FP64 solves to rel. residual 1e-13",
+                "value": int(s.info.n_cells) / (ms / 1000.0), "unit": "unknowns/s (forward + adjoint solve)",
+                "ms_forward_and_gradient": ms, "fd_directions": ndir, "fd_eps": eps,
+                "fd_max_rel_diff": worst[eps], "fd_max_rel_diff_eps_1e-3": worst[1e-3]}
+    finally:
+        s.close()
+
+
+def equal_accuracy(prob, mms, stream, flush, coarsest, rtols=(1e-10, 1e-12, 1e-13)):
+    """Both forms at equal accuracy: the discrete solution (FP64 to rel. residual 1e-13), each
+    form's time and its max-norm errors against that solution and against the exact cell
+    averages at each rtol; mixed/FP64 at the smallest rtol where the two exact-solution errors
+    agree to two significant digits."""
+    import torch
+    import paper_2504_00724_gb300 as P
+    ref = P.Solver(prob, precision=P.CCM_FP64, rtol=1e-13, max_iter=400, coarsest=coarsest)
+    q = ref.quadrature()
+    f = torch.tensor(ref.cell_averages(mms.f(prob.a, prob.b, prob.c), quad=q), device="cuda")
+    g = torch.tensor(ref.boundary_averages(mms.u, mms.ux, mms.uy, quad=q), device="cuda")
+    ua = ref.cell_averages(mms.u, quad=q)
+    ne = ref.cell_map()[0] != 0
+    ud, std = ref.solve(f, g, stream=stream)
+    ud = ud.cpu().numpy()
+    ref.close()
+    disc = float(np.abs(ud - ua)[ne].max())
+    rows = []
+    for rtol in rtols:
+        row = {"rtol": rtol}
+        for prec, tag in ((P.CCM_MIXED, "mixed"), (P.CCM_FP64, "fp64")):
+            sv = P.Solver(prob, precision=prec, rtol=rtol, max_iter=400, coarsest=coarsest)
+            sv.solve(f, g, stream=stream)
+            per = []
+            for _ in range(2):
+                flush.zero_()
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                u, st = sv.solve(f, g, stream=stream)
+                e1.record(stream)
+                e1.synchronize()
+                per.append(e0.elapsed_time(e1))
+            uu = u.cpu().numpy()
+            row[tag] = {"ms": float(np.median(per)), "iterations": st.iterations, "rel_residual": st.rel_residual,
+                        "err_vs_exact": float(np.abs(uu - ua)[ne].max()),
+                        "err_vs_discrete": float(np.abs(uu - ud)[ne].max())}
+            sv.close()
+        a, b = row["mixed"]["err_vs_exact"], row["fp64"]["err_vs_exact"]
+        row["exact_errors_agree_2_digits"] = float(f"{a:.1e}") == float(f"{b:.1e}")
+        row["mixed_over_fp64"] = row["fp64"]["ms"] / row["mixed"]["ms"]
+        rows.append(row)
+    agree = [r for r in rows if r["exact_errors_agree_2_digits"]]
+    return {"discrete_rel_residual": std.rel_residual, "discrete_err_vs_exact": disc, "by_rtol": rows,
+            "mixed_over_fp64_at_equal_accuracy": agree[0]["mixed_over_fp64"] if agree else None,
+            "equal_accuracy_rtol": agree[0]["rtol"] if agree else None}
 
 
 def main():
@@ -445,20 +650,28 @@ def main():
                  "default_params": defaults}
         solver.set_cycle_params(**defaults)
 
-    # roofline of the dominant kernel class (largest total time per step)
+    # roofline of the dominant kernel class (largest total time per step).  Algorithmic bytes
+    # per unit follow the method's byte model: an FP32 sweep reads u and r and writes u per
+    # regular cell (12 B) and per irregular row reads its fitted row (16 x 12 B: 15 coefficients,
+    # columns and gathered values, plus the cell's own) and the banded L22 factors of its SMO-2
+    # solve (2 x 20 x 4 B, cyclic bandwidth 20); the residual + restriction reads u, r and the
+    # volume per fine cell and writes the coarse r and u (12 + 2 x 4 / 4 B); the FP64 residual is
+    # bound by the FP64 pipe.  The dense block inverses read instead of banded factors are this
+    # build's design overhead and are reported beside the sweep, not counted in it.
     hbm, sm_max, src = peaks()
     clk = clocks.summary()
     n_reg = int(info.n_regular)
     n_irr = int(info.n_irregular)
+    li0 = solver.level_launch(0, P.CCM_MIXED)
     classes = []     # (name, ms per step, avg ms per launch, launches per step, bound, work per launch, unit)
     ms, nl = prof_sweep
     if nl:
-        byts = n_reg * 13.0 + n_irr * 704.0
+        byts = n_reg * 12.0 + n_irr * (16 * 12.0 + 2 * 20 * 4.0)
         classes.append(("fp32 sweep, level 0 (SMO-1 regular cells + SMO-2 blocks)", ms / args.steps, ms / nl,
                         nl / args.steps, "hbm", byts, "GB/s"))
     ms, nl = prof_rst
     if nl:
-        classes.append(("fp32 residual + restriction, level 0", ms, ms / nl, nl, "hbm", ncell * 15.0, "GB/s"))
+        classes.append(("fp32 residual + restriction, level 0", ms, ms / nl, nl, "hbm", ncell * 14.0, "GB/s"))
     ms, nl = prof_res
     if nl:
         # separable form of the regular stencil: 9 FMA along the axes, 4 + 4 for the mixed
@@ -475,22 +688,47 @@ def main():
         else:
             peak = hbm
             achieved = work / (avg_ms / 1000.0) / 1e9
+        traffic = traffic_of(name, args.n)
         roof = {"bound": bound, "achieved": achieved, "peak": peak, "unit": unit, "frac": achieved / peak,
-                "traffic": traffic_of(name, args.n), "kernel": name, "avg_launch_us": avg_ms * 1000.0,
+                "traffic": traffic, "kernel": name, "avg_launch_us": avg_ms * 1000.0,
                 "launches_per_step": per_step, "algorithmic_per_launch": work,
                 "peak_source": ("derived: 152 SMs x 4 FP64 flop/clk x max SM clock" if bound == "alu"
                                 else f"{src} copy bandwidth"),
+                "dram_frac": (traffic / (avg_ms / 1000.0) / 1e9 / peak) if (traffic and bound == "hbm") else None,
                 "others": [{"kernel": c[0], "ms_per_step": c[1], "avg_launch_us": c[2] * 1000.0, "bound": c[4],
                             "achieved": (c[5] / (c[2] / 1000.0) / (1e12 if c[4] == "alu" else 1e9)),
                             "traffic": traffic_of(c[0], args.n)}
                            for c in classes if c[0] != name]}
+        if name.startswith("fp32 sweep"):
+            roof["design_overhead_bytes_per_launch"] = {
+                "smo2_dense_block_inverse_rows": int(li0.block_inv_entries) * 4,
+                "class_bytes": n_reg * 1}
+
+    # the whole V-cycle against the two byte models (N0 fine cells, hierarchy factor 4/3 inside)
+    vc_ms, vc_n = prof_vc
+    vcycle = None
+    if vc_n:
+        t = vc_ms / vc_n / 1000.0
+        vcycle = {"ms": vc_ms / vc_n, "cells": ncell,
+                  "unfused_model": {"bytes_per_cell": 120, "GBs": 120.0 * ncell / t / 1e9,
+                                    "frac": 120.0 * ncell / t / 1e9 / hbm},
+                  "method_minimum_model": {"bytes_per_cell": 35, "GBs": 35.0 * ncell / t / 1e9,
+                                           "frac": 35.0 * ncell / t / 1e9 / hbm},
+                  "peak": hbm, "peak_source": f"{src} copy bandwidth"}
+
+    configs = None
+    eq = None
+    if not args.no_configs and world == 1:
+        eq = equal_accuracy(prob, mms, stream, flush, args.coarsest)
+        configs = other_configs(stream, flush)
 
     cpu = None
     if not args.no_cpu_baseline and rank == 0 and world == 1:
-        cpu = oracle_sample(args.sample_n, 1)
-        cpu = {k: cpu[k] for k in ("value", "unit", "cores", "kind", "sample")}
+        one = oracle_sample(args.sample_n, 1)
+        cpu = {k: one[k] for k in ("value", "unit", "cores", "kind", "sample")}
+        cpu["setup_s"] = one["setup_s"]
+        cpu["all_cores"] = oracle_all_cores(args.sample_n)
 
-    vc_ms, vc_n = prof_vc
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64+f32", "data": "synthetic",
@@ -499,8 +737,10 @@ def main():
                        "precision": "FP32 V-cycles in FP64 refinement",
                        "l2": "flushed (256 MB write) before every step", "parallelism": f"replicas x{world}"},
             "iterations": iters, "rel_residual": st.rel_residual, "max_error_vs_exact": err,
-            "vcycle_ms": (vc_ms / vc_n) if vc_n else None, "setup_s": setup_s,
+            "vcycle_ms": (vc_ms / vc_n) if vc_n else None, "vcycle": vcycle, "setup_s": setup_s,
             "fp64": fp64, "mixed_over_fp64": (value / world / fp64["value"]) if fp64 else None,
+            "equal_accuracy": eq,
+            "configs": configs,
             "batched": batched,
             "many_geometries": geometries,
             "autotuned": tuned,

@@ -124,6 +124,12 @@ typedef struct {
                         the GPU (one warp per stencil), the candidates being enumerated on host
                         threads; 0, everything on host threads.  Same stencils either way,
                         coefficients equal to rounding. */
+  int krylov;        /* CCM_MIXED: 0, the correction of an outer iteration is the inner cycles'
+                        result e = M r (plain iterative refinement); m in 1 - 8, it is the
+                        GMRES(m) solution of L e = r with M as right preconditioner (m
+                        applications of M, FP32 basis, FP64 dot products, all on the device),
+                        for problems where the cycle alone converges slowly or not at all.
+                        One right-hand side at a time (ccm_info.batch = 1). */
 } ccm_params;
 
 typedef struct {
@@ -150,7 +156,7 @@ typedef struct ccm_group ccm_group;
 
 /* Fill p with the defaults: omega 0.7, nu1 = nu2 = 3, theta 0.3, coarsest 16, CCM_MIXED,
  * rtol 1e-10, max_iter 100, ras_passes 1, ras_block 64, ras_overlap 32, nthreads 0,
- * ras_exact 0, inner_cycles 3, smoother 1, coarse_n 0, batch 1, cycle 0, setup_device 1. */
+ * ras_exact 0, inner_cycles 3, smoother 1, coarse_n 0, batch 1, cycle 0, setup_device 1, krylov 0. */
 int ccm_default_params(ccm_params* p);
 
 /* Host setup (Sec. 3.1 - 3.4, Sec. 4): cut cells and moments (Green's formula, Sec. 2.4),
@@ -348,6 +354,7 @@ typedef struct {
   int sweep_ctas;      /* CTAs per right-hand side */
   int restrict_items;  /* tiles of one residual + restriction launch */
   int restrict_ctas;   /* CTAs per right-hand side */
+  int64_t block_inv_entries;  /* entries of the SMO-2 block inverse rows one sweep reads */
 } ccm_launch_info;
 int ccm_set_launch_cap(ccm_handle* h, int max_ctas);
 int ccm_level_launch(const ccm_handle* h, int level, int precision, int nrhs, ccm_launch_info* out);

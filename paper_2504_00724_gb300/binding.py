@@ -44,7 +44,7 @@ class ccm_params(ctypes.Structure):
                 ("ras_block", ctypes.c_int), ("ras_overlap", ctypes.c_int), ("nthreads", ctypes.c_int),
                 ("ras_exact", ctypes.c_int), ("inner_cycles", ctypes.c_int), ("smoother", ctypes.c_int),
                 ("coarse_n", ctypes.c_int), ("batch", ctypes.c_int),
-                ("cycle", ctypes.c_int), ("setup_device", ctypes.c_int)]
+                ("cycle", ctypes.c_int), ("setup_device", ctypes.c_int), ("krylov", ctypes.c_int)]
 
 
 class ccm_info(ctypes.Structure):
@@ -57,7 +57,8 @@ class ccm_info(ctypes.Structure):
 
 class ccm_launch_info(ctypes.Structure):
     _fields_ = [("sweep_items", ctypes.c_int), ("sweep_blocks", ctypes.c_int), ("sweep_ctas", ctypes.c_int),
-                ("restrict_items", ctypes.c_int), ("restrict_ctas", ctypes.c_int)]
+                ("restrict_items", ctypes.c_int), ("restrict_ctas", ctypes.c_int),
+                ("block_inv_entries", ctypes.c_int64)]
 
 
 class ccm_stats(ctypes.Structure):

@@ -35,23 +35,34 @@ bool dense_inverse(std::vector<double>& A, int n) {
         for (int c = k + 1; c < n; ++c) LU[(long)r * n + c] -= f * LU[(long)k * n + c];
     }
   }
-  // solve for the columns of the identity
-  for (int col = 0; col < n; ++col) {
-    std::vector<double> x(n, 0.0);
-    x[col] = 1.0;
-    for (int k = 0; k < n; ++k)
-      if (piv[k] != k) std::swap(x[k], x[piv[k]]);
-    for (int r = 0; r < n; ++r) {
-      double s = x[r];
-      for (int c = 0; c < r; ++c) s -= LU[(long)r * n + c] * x[c];
-      x[r] = s;
+  // solve for the columns of the identity (independent: large matrices split them over threads)
+  auto solve_cols = [&](int c0, int c1) {
+    std::vector<double> x(n);
+    for (int col = c0; col < c1; ++col) {
+      std::fill(x.begin(), x.end(), 0.0);
+      x[col] = 1.0;
+      for (int k = 0; k < n; ++k)
+        if (piv[k] != k) std::swap(x[k], x[piv[k]]);
+      for (int r = 0; r < n; ++r) {
+        double s = x[r];
+        for (int c = 0; c < r; ++c) s -= LU[(long)r * n + c] * x[c];
+        x[r] = s;
+      }
+      for (int r = n - 1; r >= 0; --r) {
+        double s = x[r];
+        for (int c = r + 1; c < n; ++c) s -= LU[(long)r * n + c] * x[c];
+        x[r] = s / LU[(long)r * n + r];
+      }
+      for (int r = 0; r < n; ++r) A[(long)r * n + col] = x[r];
     }
-    for (int r = n - 1; r >= 0; --r) {
-      double s = x[r];
-      for (int c = r + 1; c < n; ++c) s -= LU[(long)r * n + c] * x[c];
-      x[r] = s / LU[(long)r * n + r];
-    }
-    for (int r = 0; r < n; ++r) A[(long)r * n + col] = x[r];
+  };
+  const int nt = n >= 256 ? std::max(1, std::min<int>(64, (int)std::thread::hardware_concurrency())) : 1;
+  if (nt == 1) {
+    solve_cols(0, n);
+  } else {
+    std::vector<std::thread> pool;
+    for (int t = 0; t < nt; ++t) pool.emplace_back(solve_cols, (int)((long)n * t / nt), (int)((long)n * (t + 1) / nt));
+    for (auto& th : pool) th.join();
   }
   return true;
 }

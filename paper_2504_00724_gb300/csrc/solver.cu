@@ -23,6 +23,7 @@
 #include "smooth.cuh"
 #include "outer.cuh"
 #include "group.cuh"
+#include "krylov.cuh"
 
 using namespace ccm;
 
@@ -177,6 +178,11 @@ struct ccm_handle {
   size_t coarse_smem = 0;      // its dynamic shared memory (SMO-2 extended-row residuals)
   bool persistent = true;      // block-Jacobi sweeps of TMA levels as one persistent launch
   int launch_cap = 0;          // > 0: at most this many CTAs per right-hand side in the persistent kernels
+  // GMRES(kry_m) correction of the mixed outer iteration (0: plain iterative refinement)
+  int kry_m = 0;
+  float* kv[dev::KRY_MAXM + 1] = {};   // Krylov basis v_0 .. v_m (padded level-0 FP32 arrays)
+  float* kz[dev::KRY_MAXM] = {};       // preconditioned vectors z_j = M v_j
+  dev::KryScalars* ks = nullptr;
   ccm_handle* adj = nullptr;   // the transposed operators' hierarchy (built by ccm_solve_T)
   // one CUDA graph per outer iteration and precision (captured on first use, on a private
   // stream: the legacy default stream cannot be captured)
@@ -1104,6 +1110,12 @@ int upload_hierarchy(ccm_handle* h) {
                      make_tmap(&h->tm_rhat, h->rhat, d0.pitch, d0.rows, CU_TENSOR_MAP_DATA_TYPE_FLOAT64, 8, dev::HX, dev::JY,
                                h->B);
   }
+  if (h->par.precision == CCM_MIXED && h->par.krylov > 0 && h->fused_outer) {
+    h->kry_m = h->par.krylov;
+    for (int i = 0; i <= h->kry_m; ++i) h->kv[i] = A.alloc<float>(h->L[0].npad);
+    for (int i = 0; i < h->kry_m; ++i) h->kz[i] = A.alloc<float>(h->L[0].npad);
+    h->ks = A.alloc<dev::KryScalars>(1);
+  }
   h->dnorm = A.alloc<unsigned long long>(h->B);
   h->derr = A.alloc<int>(1);
   if (A.err != cudaSuccess) {
@@ -1149,6 +1161,7 @@ int ccm_default_params(ccm_params* p) {
   p->batch = 1;
   p->cycle = 0;
   p->setup_device = 1;
+  p->krylov = 0;
   return CCM_OK;
 }
 
@@ -1179,7 +1192,8 @@ int ccm_setup(const ccm_problem* prob, const ccm_params* params, ccm_handle** ou
   if (par.nu1 < 0 || par.nu2 < 0 || par.coarsest < 4 || par.ras_passes < 0 || par.ras_block < 8 ||
       par.ras_block > 128 || par.ras_overlap < 0 || par.ras_overlap > 64 || par.max_iter < 0 ||
       par.ras_exact < 0 || par.ras_exact > 6000 || par.inner_cycles < 1 || par.inner_cycles > 16 || par.smoother < 0 || par.smoother > 1 || par.coarse_n < 0 ||
-      par.batch < 1 || par.batch > 4096 || par.cycle < 0 || par.cycle > 1 ||
+      par.batch < 1 || par.batch > 4096 || par.cycle < 0 || par.cycle > 1 || par.krylov < 0 ||
+      par.krylov > dev::KRY_MAXM ||
       !(par.theta >= 0 && par.theta < 1) || (par.precision != CCM_FP64 && par.precision != CCM_MIXED))
     return CCM_EINVAL;
   auto t0 = std::chrono::steady_clock::now();
@@ -1225,7 +1239,7 @@ int ccm_setup(const ccm_problem* prob, const ccm_params* params, ccm_handle** ou
   // the block-Jacobi smoother and no cluster cycle
   {
     bool ok = h->B > 1 && h->fused_outer && h->persistent && par.smoother == 1 && par.ras_passes <= 1 &&
-              h->coarse_first >= nl;
+              h->coarse_first >= nl && h->kry_m == 0;
     for (int m = 0; m < nl && ok; ++m) {
       const DevLevel& d = h->L[m];
       if (!d.tma) continue;
@@ -1423,6 +1437,61 @@ int ccm_apply_T(ccm_handle* h, const double* v, double* out_u, double* out_g, in
   return CCM_OK;
 }
 
+// The correction of one mixed outer iteration by GMRES(m) on L e = r32 with the inner FP32
+// V-cycles as right preconditioner (see krylov.cuh); u_hat += e.  Level-0 FP32 vectors only,
+// scalars in device memory, no host synchronisation.
+static void krylov_correction(ccm_handle* h, cudaStream_t s) {
+  DevLevel& L = h->L[0];
+  const int m = h->kry_m, nt = L.ntiles;
+  dev::KryScalars* S = h->ks;
+  dev::KryVecs V{}, Z{}, R{};
+  for (int i = 0; i <= m; ++i) V.v[i] = h->kv[i];
+  for (int i = 0; i < m; ++i) Z.v[i] = h->kz[i];
+  R.v[0] = L.r32;
+  const int KT = dev::KRY_THREADS, KG = dev::KRY_GRID;
+  const int32_t* tl = L.tiles;
+  const uint8_t* cl = L.cls;
+  cudaMemsetAsync(reinterpret_cast<char*>(S) + offsetof(dev::KryScalars, H), 0, sizeof(S->H), s);
+  // beta = ||r||_2, v_0 = r / beta, which is also the first preconditioner input
+  KL(launch_k(dev::k_kdot, KG, KT, 0, s, tl, nt, L.nx, L.ny, L.pitch, (const float*)L.r32, R, 1, S));
+  KL(launch_k(dev::k_kreduce, 1, KT, 0, s, 1, 2, 0, m, S));
+  KL(launch_k(dev::k_kscale, KG, KT, 0, s, tl, nt, L.nx, L.ny, L.pitch, cl, (const float*)L.r32, h->kv[0], L.r32,
+              (const dev::KryScalars*)S));
+  for (int j = 0; j < m; ++j) {
+    // z_j = M v_j: the inner cycles from a zero guess on the right-hand side r32 = v_j
+    cudaMemsetAsync(L.u32[L.cur32], 0, L.npad * sizeof(float), s);
+    for (int c = 0; c < std::max(1, h->par.inner_cycles); ++c) {
+      ProfScope ps(h, CCM_PROF_VCYCLE, s);
+      if (c == 0 && h->par.cycle == 1) fmg<float>(h, s);
+      else vcycle<float>(h, 0, s);
+    }
+    const float* z = L.u32[L.cur32];
+    float* w = h->kv[j + 1];
+    // w = L z (regular stencil, then the fitted rows), z kept as z_j
+    if (h->cross)
+      KL(launch_k(dev::k_kapply<true>, nt, KT, 0, s, tl, L.nx, L.ny, L.pitch, cl, z, w, h->kz[j], h->S32));
+    else
+      KL(launch_k(dev::k_kapply<false>, nt, KT, 0, s, tl, L.nx, L.ny, L.pitch, cl, z, w, h->kz[j], h->S32));
+    if (L.n2)
+      KL(launch_k(dev::k_rows<float, float, false, true>, ceil_div(L.n2, 128), 128, 0, s, L.n2, L.W,
+                  (const int32_t*)L.irr_cell, (const int32_t*)L.ell_col, (const float*)L.ell32, z, (const float*)nullptr, w,
+                  (const double*)nullptr, (const int32_t*)nullptr, (const double*)nullptr));
+    // classical Gram-Schmidt against v_0 .. v_j twice, each subtraction fused with the next
+    // reduction: the second pass's dot products, then ||w||^2
+    KL(launch_k(dev::k_kdot, KG, KT, 0, s, tl, nt, L.nx, L.ny, L.pitch, (const float*)w, V, j + 1, S));
+    KL(launch_k(dev::k_kreduce, 1, KT, 0, s, j + 1, 0, j, m, S));
+    KL(launch_k(dev::k_ksubdot, KG, KT, 0, s, tl, nt, L.nx, L.ny, L.pitch, cl, w, V, j + 1, false, S));
+    KL(launch_k(dev::k_kreduce, 1, KT, 0, s, j + 1, 0, j, m, S));
+    KL(launch_k(dev::k_ksubdot, KG, KT, 0, s, tl, nt, L.nx, L.ny, L.pitch, cl, w, V, j + 1, true, S));
+    // h_{j+1,j} = ||w||, v_{j+1} = w / h_{j+1,j} (and the next preconditioner input)
+    KL(launch_k(dev::k_kreduce, 1, KT, 0, s, 1, 1, j, m, S));
+    KL(launch_k(dev::k_kscale, KG, KT, 0, s, tl, nt, L.nx, L.ny, L.pitch, cl, (const float*)w, w,
+                j + 1 < m ? L.r32 : (float*)nullptr, (const dev::KryScalars*)S));
+  }
+  KL(launch_k(dev::k_klsq, 1, 32, 0, s, m, S));
+  KL(launch_k(dev::k_kupdate, KG, KT, 0, s, tl, nt, L.nx, L.ny, L.pitch, cl, Z, m, (const dev::KryScalars*)S, h->uhat));
+}
+
 // One outer iteration on the stream (also the body captured into the iteration graph):
 // mixed: FP32 V-cycles on the FP32 image of the FP64 residual, u_hat += e, new FP64 residual;
 // fp64:  one FP64 V-cycle in place, new FP64 residual; then the residual norm to the host.
@@ -1443,6 +1512,14 @@ static void iteration_body(ccm_handle* h, bool fp64, cudaStream_t s, bool to_hos
       L.cur64 = 1 - L.cur64;
     }
     ucur = start;
+  } else if (h->fused_outer && h->kry_m > 0) {
+    // r32 holds the FP32 image of the residual; e by GMRES(m) preconditioned by the cycles
+    krylov_correction(h, s);
+    outer_residual32(h, s);
+    if (!to_host) return;
+    cudaMemcpyAsync(h->hnorm, h->dnorm, sizeof(unsigned long long), cudaMemcpyDeviceToHost, s);
+    cudaMemcpyAsync(h->herr, h->derr, sizeof(int), cudaMemcpyDeviceToHost, s);
+    return;
   } else if (h->fused_outer) {
     // r32 holds the FP32 image of the residual (previous iteration or the initial one)
     cudaMemsetAsync(L.u32[L.cur32], 0, h->nb * np * sizeof(float), s);
@@ -1560,6 +1637,9 @@ int ccm_level_launch(const ccm_handle* h, int level, int precision, int nrhs, cc
     out->sweep_blocks = L.nblk;
     out->sweep_ctas = persistent_ctas(L.smooth_grid[k], L.smooth_cap[k], nrhs, h->launch_cap);
   }
+  const HostLevel& hl = h->H.levels[level];
+  for (int b = 0; b < L.nblk; ++b)
+    out->block_inv_entries += (int64_t)(hl.blk[4 * b + 1] - hl.blk[4 * b]) * (hl.blk[4 * b + 3] - hl.blk[4 * b + 2]);
   if (!last && bj && L.tma && L.ntiles64r && L.restrict_ok[k]) {
     out->restrict_items = L.ntiles64r;
     out->restrict_ctas = persistent_ctas(L.restrict_grid[k], L.restrict_cap[k], nrhs, h->launch_cap);

@@ -61,7 +61,8 @@ def test_solve_T_matches_oracle(case, precision):
         s.close()
 
 
-def test_adjoint_dot_product_and_fd_gradients(case):
+@pytest.mark.parametrize("eps,tol", [(1e-6, 2e-7), (1e-3, 2e-9)])
+def test_adjoint_dot_product_and_fd_gradients(case, eps, tol):
     prob, cg, dz = case
     mms = W.mms_star()
     ne = (cg.status != 0)
@@ -91,7 +92,6 @@ def test_adjoint_dot_product_and_fd_gradients(case):
         J = loss(f, g)
         J.backward()
         gf, gg = f.grad.detach().clone(), g.grad.detach().clone()
-        eps = 1e-6
         for k in range(4):
             df = cuda(np.where(ne, rng.standard_normal(ne.shape), 0.0))
             dg = cuda(rng.standard_normal(len(ga)))
@@ -100,6 +100,8 @@ def test_adjoint_dot_product_and_fd_gradients(case):
                 jm = loss(f - eps * df, g - eps * dg).item()
             fd = (jp - jm) / (2 * eps)
             ad = float((gf * df).sum() + (gg * dg).sum())
-            assert abs(fd - ad) <= 1e-5 * abs(ad) + 1e-9, (k, fd, ad)
+            # the loss is quadratic in (f, g): central differences carry no truncation error
+            # at any step, only J's rounding and the solves' stopping points, divided by eps
+            assert abs(fd - ad) <= tol * abs(ad), (k, fd, ad, abs(fd - ad) / abs(ad))
     finally:
         s.close()

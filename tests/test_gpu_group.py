@@ -34,6 +34,12 @@ def coarsest(p):
     return 64 if "star" in p.name else 32
 
 
+def krylov(p):
+    """The three-ellipse domains of the workload take the GMRES correction (their V-cycle alone
+    diverges on the larger grids); the stars keep plain refinement."""
+    return 0 if "star" in p.name else 2
+
+
 def _members():
     """Seeds 0..5 of the many-geometry workload (stars and three-ellipse domains) on uneven
     grids small enough for a test, and the three-ellipse workload at 128^2."""
@@ -53,7 +59,8 @@ def setups():
     members = _members()
     probs = [p for p, _ in members]
     precs = [P.CCM_MIXED] * (len(probs) - 2) + [P.CCM_FP64, P.CCM_MIXED]
-    solvers = [P.Solver(p, rtol=1e-10, max_iter=60, precision=pr, coarsest=coarsest(p)) for p, pr in zip(probs, precs)]
+    solvers = [P.Solver(p, rtol=1e-10, max_iter=60, precision=pr, coarsest=coarsest(p),
+                         krylov=krylov(p)) for p, pr in zip(probs, precs)]
     data = [_inputs(s, p, m) for s, (p, m) in zip(solvers, members)]
     yield probs, solvers, data
     for s in solvers:
@@ -76,7 +83,8 @@ def test_group_members_match_oracle():
             wants.append(MG.direct_solve(dz, fa.ravel() - dz.N @ ga).reshape(p.ny, p.nx))
             fs.append(torch.tensor(fa, dtype=torch.float64, device="cuda"))
             gs.append(torch.tensor(ga, dtype=torch.float64, device="cuda"))
-            solvers.append(P.Solver(p, rtol=1e-12, max_iter=200, precision=pr, coarsest=coarsest(p)))
+            solvers.append(P.Solver(p, rtol=1e-12, max_iter=200, precision=pr, coarsest=coarsest(p),
+                                    krylov=krylov(p)))
         grp = P.Group(solvers)
         try:
             us, st, rc = grp.solve(fs, gs, check=False)
