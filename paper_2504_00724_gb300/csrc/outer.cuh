@@ -115,6 +115,157 @@ __global__ void __launch_bounds__(256, 3) k_resid64(const __grid_constant__ CUte
   if ((threadIdx.x & 31) == 0 && m > 0) atomicMax(norm, m);
 }
 
+// ---- the same residual in float-float arithmetic (pairs of FP32 words, about 48 bits).
+// GB300 issues FP64 at 1/64 of the FP32 rate, so the FP64 kernel above is bound by its
+// arithmetic.  Here the staged FP64 values are split into (hi, lo) FP32 pairs by integer
+// operations (hi = the leading 24 significant bits, lo the next 24, both truncated), and the
+// stencil runs in the integer-weight form of eq. stdLap and eq. stdGrad,
+//   t = r_hat - [ a/12 Lap_x u + c/12 Lap_y u + b/144 Grad_y Grad_x u ],
+//   Lap = 16 (u_-1 + u_+1) - (u_-2 + u_+2) - 30 u_0,  Grad = (u_-2 - u_+2) + 8 (u_+1 - u_-1),
+// with every sum of leading words error-free (TwoSum) and the rounding errors, the low words
+// and the errors of the products (FMA) carried in a second word.  The absolute error of t is
+// about 2^-47 times the sum of the stencil's terms, 1e-13 relative to u here, against
+// rounding at 2^-53 in FP64: good for relative residuals down to about 1e-11.
+
+struct FFStencil {
+  float ah, al;    // a / 12 as hi + lo
+  float ch, cl;    // c / 12
+  float bh, bl;    // b / 144
+};
+
+// hi + lo = x to 48 significant bits, by integer operations only; |x| below 2^-126 gives 0,
+// Inf and NaN pass to hi (lo = 0)
+__device__ __forceinline__ float2 ff_split(double x) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+  const unsigned h32 = (unsigned)(b >> 32), l32 = (unsigned)b;
+  const unsigned sign = h32 & 0x80000000u;
+  const int e = (int)((h32 >> 20) & 0x7ffu);
+  if (e == 0x7ff) return make_float2(__uint_as_float(sign | 0x7f800000u | (((h32 & 0xfffffu) | l32) ? 0x400000u : 0u)), 0.f);
+  const int ef = e - 1023 + 127;
+  if (ef <= 0) return make_float2(__uint_as_float(sign), 0.f);
+  if (ef >= 255) return make_float2(__uint_as_float(sign | 0x7f800000u), 0.f);
+  const unsigned m23 = ((h32 & 0xfffffu) << 3) | (l32 >> 29);
+  const float hi = __uint_as_float(sign | ((unsigned)ef << 23) | m23);
+  const unsigned rem = l32 & 0x1fffffffu;             // the 29 bits below hi, weight 2^(e - 1075)
+  if (rem == 0u) return make_float2(hi, 0.f);
+  const int lz = __clz(rem);                           // >= 3
+  const int el = (31 - lz) + (e - 1075) + 127;
+  if (el <= 0) return make_float2(hi, 0.f);
+  const unsigned ml = ((rem << lz) >> 8) & 0x7fffffu;
+  return make_float2(hi, __uint_as_float(sign | ((unsigned)el << 23) | ml));
+}
+
+struct FF {
+  float s, e;      // value s + e
+};
+
+__device__ __forceinline__ FF ff(float2 v) { return FF{v.x, v.y}; }
+
+// x + y, the sum of the leading words error-free (TwoSum)
+__device__ __forceinline__ FF ff_add(FF x, FF y) {
+  FF r;
+  r.s = x.s + y.s;
+  const float bb = r.s - x.s;
+  r.e = ((x.s - (r.s - bb)) + (y.s - bb)) + (x.e + y.e);
+  return r;
+}
+__device__ __forceinline__ FF ff_sub(FF x, FF y) { return ff_add(x, FF{-y.s, -y.e}); }
+// p x for a power of two p (exact)
+__device__ __forceinline__ FF ff_pow2(FF x, float p) { return FF{x.s * p, x.e * p}; }
+// w x, the product of the leading word error-free (FMA)
+__device__ __forceinline__ FF ff_mul(FF x, float w) {
+  FF r;
+  r.s = x.s * w;
+  r.e = fmaf(x.e, w, fmaf(x.s, w, -r.s));
+  return r;
+}
+// (ch + cl) x
+__device__ __forceinline__ FF ff_mulc(FF x, float ch, float cl) {
+  FF r;
+  r.s = x.s * ch;
+  r.e = fmaf(x.e, ch, fmaf(x.s, cl, fmaf(x.s, ch, -r.s)));
+  return r;
+}
+// eq. stdLap's integer weights along a line: 16 (m1 + p1) - (m2 + p2) - 30 c
+__device__ __forceinline__ FF ff_lap(FF m2, FF m1, FF c, FF p1, FF p2) {
+  return ff_sub(ff_sub(ff_pow2(ff_add(m1, p1), 16.f), ff_add(m2, p2)), ff_mul(c, 30.f));
+}
+// eq. stdGrad's integer weights along a line: (m2 - p2) + 8 (p1 - m1)
+__device__ __forceinline__ FF ff_grad(FF m2, FF m1, FF p1, FF p2) {
+  return ff_add(ff_sub(m2, p2), ff_pow2(ff_sub(p1, m1), 8.f));
+}
+
+template <bool CROSS>
+__global__ void __launch_bounds__(256, 3) k_resid_ff(const __grid_constant__ CUtensorMap tu,
+                                                  const __grid_constant__ CUtensorMap tr,
+                                                  const __grid_constant__ CUtensorMap tcls,
+                                                  const int32_t* __restrict__ tiles, int nx, int pitch,
+                                                  float* __restrict__ r32, unsigned long long* __restrict__ norm,
+                                                  FFStencil S, int* __restrict__ err, long bs) {
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  double* ut = reinterpret_cast<double*>(smem_raw);                               // [HY][HX]
+  const double* rt = reinterpret_cast<const double*>(smem_raw + Resid64Smem::rt_off);   // [JY][HX]
+  const uint8_t* ct = smem_raw + Resid64Smem::ct_off;                             // [HY][CLX]
+  float2* dx = reinterpret_cast<float2*>(smem_raw + Resid64Smem::dx_off);         // [HY][JX]
+  __shared__ __align__(8) uint64_t bar;
+  pdl_enter();
+  const int z = blockIdx.y;          // right-hand side of the batch
+  r32 += (long)z * bs;
+  norm += z;
+  const int cx0 = tiles[2 * blockIdx.x] * JX, cy0 = tiles[2 * blockIdx.x + 1] * JY;
+  if (threadIdx.x == 0) mbar_init(&bar, 1);
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    mbar_expect_tx(&bar, Resid64Smem::tx);
+    tma_load_3d(ut, &tu, &bar, cx0, cy0, z);
+    tma_load_3d(smem_raw + Resid64Smem::rt_off, &tr, &bar, cx0, cy0 + 2, z);
+    tma_load_2d(smem_raw + Resid64Smem::ct_off, &tcls, &bar, cx0, cy0);
+  }
+  const bool ok = __syncthreads_and(tile_wait(&bar, err));
+  if (!ok) return;
+  // every staged value of u becomes its (hi, lo) pair in place
+  float2* uf = reinterpret_cast<float2*>(ut);
+  for (int idx = threadIdx.x; idx < HY * HX; idx += blockDim.x) {
+    const float2 v = ff_split(ut[idx]);
+    uf[idx] = v;
+  }
+  __syncthreads();
+  if (CROSS) {
+    for (int idx = threadIdx.x; idx < HY * JX; idx += blockDim.x) {
+      const int y = idx >> 6, x = idx & 63;
+      const float2* row = uf + y * HX + x + 2;
+      const FF d = ff_grad(ff(row[-2]), ff(row[-1]), ff(row[1]), ff(row[2]));
+      dx[idx] = make_float2(d.s, d.e);
+    }
+    __syncthreads();
+  }
+  const int x = threadIdx.x & 63, y0 = (threadIdx.x >> 6) * 8;
+  const int i = cx0 + x;
+  unsigned m = 0;
+#pragma unroll 2
+  for (int k = 0; k < 8; ++k) {
+    const int y = y0 + k;                 // own row; staged row y + 2
+    const float2* c = uf + (y + 2) * HX + x + 2;
+    const FF c0 = ff(c[0]);
+    const FF lx = ff_lap(ff(c[-2]), ff(c[-1]), c0, ff(c[1]), ff(c[2]));
+    const FF ly = ff_lap(ff(c[-2 * HX]), ff(c[-HX]), c0, ff(c[HX]), ff(c[2 * HX]));
+    FF lu = ff_add(ff_mulc(lx, S.ah, S.al), ff_mulc(ly, S.ch, S.cl));
+    if (CROSS) {
+      const float2* d = dx + (y + 2) * JX + x;
+      lu = ff_add(lu, ff_mulc(ff_grad(ff(d[-2 * JX]), ff(d[-JX]), ff(d[JX]), ff(d[2 * JX])), S.bh, S.bl));
+    }
+    const FF t = ff_sub(ff(ff_split(rt[y * HX + x + 2])), lu);
+    const float tf = t.s + t.e;
+    if (i < nx && ct[(y + 2) * CLX + x + 2] == 1) {
+      r32[(long)(cy0 + y + 2) * pitch + (i + 2)] = tf;
+      unsigned b = __float_as_uint(tf) & 0x7fffffffu;
+      m = max(m, b > 0x7f800000u ? 0x7f800000u : b);
+    }
+  }
+  for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
+  if ((threadIdx.x & 31) == 0 && m > 0) atomicMax(norm, abs_bits((double)__uint_as_float(m)));
+}
+
 // fitted rows of the irregular cells: t = r_hat - sum_k beta_k u_hat(col_k); r32 and max |t|
 __global__ void __launch_bounds__(128, 8) k_rows_r32(int n2, int W, const int32_t* __restrict__ cell, const int32_t* __restrict__ col,
                            const double* __restrict__ val, const double* __restrict__ u,

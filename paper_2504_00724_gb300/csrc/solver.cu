@@ -162,6 +162,7 @@ struct ccm_handle {
   int nb = 1;                  // right-hand sides of the launches being issued (<= bmax)
   CUtensorMap tm_uhat, tm_rhat;  // 68 x 36 box over uhat, 68 x 32 box over rhat
   dev::SepStencil sep{};       // the regular stencil in factored form
+  dev::FFStencil ffs{};        // its three coefficients as FP32 pairs (float-float residual)
   unsigned long long* dnorm = nullptr;
   unsigned long long* hnorm = nullptr;   // pinned
   ccm_info info{};
@@ -750,6 +751,11 @@ int read_norm(ccm_handle* H, const uint8_t* cls, long n, const double* x, cudaSt
   return CCM_OK;
 }
 
+// the regular cells' part of the outer residual runs in float-float arithmetic (about 48
+// bits: good for relative residuals down to about 1e-11) when the tolerance allows, else in
+// FP64
+inline bool resid_float_float(const ccm_handle* H) { return H->par.rtol >= 1e-11; }
+
 // mixed form: t = rhat - L uhat on level 0 into the FP32 right-hand side, max |t| into dnorm
 void outer_residual32(ccm_handle* H, cudaStream_t s) {
   DevLevel& L = H->L[0];
@@ -757,12 +763,21 @@ void outer_residual32(ccm_handle* H, cudaStream_t s) {
   cudaMemsetAsync(H->dnorm, 0, nb * sizeof(unsigned long long), s);
   {
     ProfScope ps(H, CCM_PROF_RESID_FP64, s);
-    if (H->cross)
-      KL(launch_k(dev::k_resid64<true>, dim3(L.ntiles64, nb), 256, dev::Resid64Smem::bytes(true), s, H->tm_uhat, H->tm_rhat,
+    const dim3 g(L.ntiles64, nb);
+    if (resid_float_float(H)) {
+      if (H->cross)
+        KL(launch_k(dev::k_resid_ff<true>, g, 256, dev::Resid64Smem::bytes(true), s, H->tm_uhat, H->tm_rhat, L.tmcls,
+                    L.tiles64, L.nx, L.pitch, L.r32, H->dnorm, H->ffs, H->derr, L.npad));
+      else
+        KL(launch_k(dev::k_resid_ff<false>, g, 256, dev::Resid64Smem::bytes(false), s, H->tm_uhat, H->tm_rhat, L.tmcls,
+                    L.tiles64, L.nx, L.pitch, L.r32, H->dnorm, H->ffs, H->derr, L.npad));
+    } else if (H->cross) {
+      KL(launch_k(dev::k_resid64<true>, g, 256, dev::Resid64Smem::bytes(true), s, H->tm_uhat, H->tm_rhat,
                   L.tmcls, L.tiles64, L.nx, L.pitch, L.r32, H->dnorm, H->sep, H->derr, L.npad));
-    else
-      KL(launch_k(dev::k_resid64<false>, dim3(L.ntiles64, nb), 256, dev::Resid64Smem::bytes(false), s, H->tm_uhat, H->tm_rhat,
+    } else {
+      KL(launch_k(dev::k_resid64<false>, g, 256, dev::Resid64Smem::bytes(false), s, H->tm_uhat, H->tm_rhat,
                   L.tmcls, L.tiles64, L.nx, L.pitch, L.r32, H->dnorm, H->sep, H->derr, L.npad));
+    }
   }
   if (L.n2)
     KL(launch_k(dev::k_rows_r32, dim3(ceil_div(L.n2, 128), nb), 128, 0, s, L.n2, L.W, L.irr_cell, L.ell_col, L.ell64,
@@ -1102,9 +1117,18 @@ int upload_hierarchy(ccm_handle* h) {
       h->sep.gy[k] = h->b * grad[k] / 12.0;
     }
     h->sep.cc = h->sep.lx[2] + h->sep.ly[2];
+    auto split = [](double v, float& hi, float& lo) {
+      hi = (float)v;
+      lo = (float)(v - (double)hi);
+    };
+    split(h->a / 12.0, h->ffs.ah, h->ffs.al);
+    split(h->c / 12.0, h->ffs.ch, h->ffs.cl);
+    split(h->b / 144.0, h->ffs.bh, h->ffs.bl);
     const DevLevel& d0 = h->L[0];
     cudaFuncSetAttribute(dev::k_resid64<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, dev::Resid64Smem::bytes(true));
     cudaFuncSetAttribute(dev::k_resid64<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, dev::Resid64Smem::bytes(false));
+    cudaFuncSetAttribute(dev::k_resid_ff<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, dev::Resid64Smem::bytes(true));
+    cudaFuncSetAttribute(dev::k_resid_ff<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, dev::Resid64Smem::bytes(false));
     h->fused_outer = A.err == cudaSuccess && d0.tma && d0.ntiles64 > 0 &&
                      make_tmap(&h->tm_uhat, h->uhat, d0.pitch, d0.rows, true, h->B) &&
                      make_tmap(&h->tm_rhat, h->rhat, d0.pitch, d0.rows, CU_TENSOR_MAP_DATA_TYPE_FLOAT64, 8, dev::HX, dev::JY,
