@@ -640,14 +640,17 @@ def main():
     if not args.no_autotune:
         from paper_2504_00724_gb300 import autotune as AT
         defaults = {k: getattr(solver.params, k) for k in ("omega", "nu1", "nu2", "inner_cycles", "cycle")}
+        dblock = (solver.params.ras_block, solver.params.ras_overlap)
         cands = [c for c in AT.default_candidates() if c["cycle"] == 0 and c["nu1"] >= 2]
-        best, rec = AT.autotune(solver, f, g, candidates=cands, repeats=3, stream=stream)
+        best, rec = AT.autotune(solver, f, g, candidates=cands, repeats=3, stream=stream,
+                                block_candidates=AT.default_block_candidates())
         per_t, (_, st_t), _ = timed_solves(solver, args.steps)
         value_t, _, _ = replica_throughput(float(ncell * args.steps), sum(per_t) / 1000.0)
         tuned = {"params": best, "value": value_t, "ms_per_step": float(np.mean(per_t)),
                  "iterations": st_t.iterations, "candidates": len(rec),
-                 "default_params": defaults}
+                 "default_params": dict(defaults, ras_block=dblock[0], ras_overlap=dblock[1])}
         solver.set_cycle_params(**defaults)
+        solver.set_smo2_blocks(*dblock)
 
     # roofline of the dominant kernel class (largest total time per step).  Algorithmic bytes
     # per unit follow the method's byte model: an FP32 sweep reads u and r and writes u per

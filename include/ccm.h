@@ -155,7 +155,7 @@ typedef struct ccm_handle ccm_handle;
 typedef struct ccm_group ccm_group;
 
 /* Fill p with the defaults: omega 0.7, nu1 = nu2 = 3, theta 0.3, coarsest 16, CCM_MIXED,
- * rtol 1e-10, max_iter 100, ras_passes 1, ras_block 64, ras_overlap 32, nthreads 0,
+ * rtol 1e-10, max_iter 100, ras_passes 1, ras_block 64, ras_overlap 24, nthreads 0,
  * ras_exact 0, inner_cycles 3, smoother 1, coarse_n 0, batch 1, cycle 0, setup_device 1, krylov 0. */
 int ccm_default_params(ccm_params* p);
 
@@ -332,6 +332,16 @@ int ccm_vcycle(ccm_handle* h, double* u, const double* r, int precision, void* s
  * paper fixes omega = 0.5, nu1 = nu2 = 3 (Sec. 5); these are free parameters of Alg. 2.
  * Errors: CCM_EINVAL, CCM_ECUDA. */
 int ccm_set_cycle_params(ccm_handle* h, double omega, int nu1, int nu2, int inner_cycles, int cycle);
+
+/* Rebuild the SMO-2 blocks of a set-up handle (and of its transposed hierarchy, if built):
+ * on every level with fitted rows, cores of `block` consecutive rows of the boundary order
+ * (Alg. 3) widened by `overlap` rows on each side, with the widened blocks' L22 inverses
+ * (Sec. 4.1, eq. updateByBlock, solved by overlapping dense blocks).  block 8 - 128, overlap
+ * 0 - 64; levels set up with one exact block (ras_exact) keep it.  The host recomputes the
+ * inverses and uploads them, no other setup is repeated.  Blocking; drops the captured
+ * iteration graphs.  Used by the autotuner.  Errors: CCM_EINVAL, CCM_ESINGULAR, CCM_ENOMEM,
+ * CCM_ECUDA. */
+int ccm_set_smo2_blocks(ccm_handle* h, int block, int overlap);
 
 /* Launch shape of the persistent kernels (testing and tuning; not part of the method).  The
  * smoothing sweep of a level with TMA-staged tiles is one launch whose work items are the

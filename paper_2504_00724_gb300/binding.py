@@ -95,6 +95,7 @@ _SIGS = {
     "ccm_fmg": (I, [P, P, P, I, P]),
     "ccm_set_cycle_params": (I, [P, ctypes.c_double, I, I, I, I]),
     "ccm_set_launch_cap": (I, [P, I]),
+    "ccm_set_smo2_blocks": (I, [P, I, I]),
     "ccm_level_launch": (I, [P, I, I, I, ctypes.POINTER(ccm_launch_info)]),
     "ccm_free": (None, [P]),
     "ccm_strerror": (ctypes.c_char_p, [I]),
@@ -379,6 +380,11 @@ class Solver:
         _check(lib().ccm_set_cycle_params(self.h, float(vals[0]), *[int(v) for v in vals[1:]]),
                "ccm_set_cycle_params")
         p.omega, p.nu1, p.nu2, p.inner_cycles, p.cycle = vals
+
+    def set_smo2_blocks(self, block: int, overlap: int):
+        """Rebuild the SMO-2 blocks: cores of `block` rows widened by `overlap` on each side."""
+        _check(lib().ccm_set_smo2_blocks(self.h, int(block), int(overlap)), "ccm_set_smo2_blocks")
+        self.params.ras_block, self.params.ras_overlap = int(block), int(overlap)
 
     def set_launch_cap(self, max_ctas: int):
         """At most max_ctas CTAs per right-hand side in the persistent kernels (0: no cap)."""

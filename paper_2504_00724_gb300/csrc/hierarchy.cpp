@@ -303,70 +303,76 @@ static int pack_level(const CutLevel& cg, const PackRows& rows, const ccm_params
   // SMO-2 blocks over the boundary order
   if (!coarsest && n2 > 0) {
     // the rows were renumbered into the boundary order: blocks are contiguous row ranges
-    std::vector<int> order(n2);
-    for (int p = 0; p < n2; ++p) order[p] = p;
-    L.order.assign(order.begin(), order.end());
-    std::vector<int> pos(n2);
-    for (int p = 0; p < n2; ++p) pos[order[p]] = p;
-    // one exact block when the level is small, else overlapping blocks of the order
+    L.order.resize(n2);
+    for (int p = 0; p < n2; ++p) L.order[p] = p;
     const bool exact = n2 <= par.ras_exact;
-    const int m = exact ? n2 : std::max(8, par.ras_block), dl = exact ? 0 : std::max(0, par.ras_overlap);
-    const int nblk = (n2 + m - 1) / m;
-    L.blk.resize(4L * nblk);
-    L.blk_off.resize(nblk);
-    long off = 0;
-    for (int bk = 0; bk < nblk; ++bk) {
-      int cs = bk * m, ce = std::min(n2, cs + m);
-      int es = std::max(0, cs - dl), ee = std::min(n2, ce + dl);
-      L.blk[4 * bk + 0] = cs;
-      L.blk[4 * bk + 1] = ce;
-      L.blk[4 * bk + 2] = es;
-      L.blk[4 * bk + 3] = ee;
-      L.blk_off[bk] = off;
-      off += (long)(ee - es) * (ce - cs);
-    }
-    L.blk_inv.assign(off, 0.0);
-    // the padded cell of every row, to look up the L22 entries
-    std::vector<int> row_of_pad(np, -1);
-    for (int r = 0; r < n2; ++r) row_of_pad[L.irr_cell[r]] = r;
-    std::atomic<int> bad{0};
-    std::atomic<int> next{0};
-    int nt = par.nthreads > 0 ? par.nthreads : (int)std::max(1u, std::thread::hardware_concurrency());
-    auto worker = [&]() {
-      std::vector<double> A;
-      while (true) {
-        int bk = next.fetch_add(1);
-        if (bk >= nblk) break;
-        int cs = L.blk[4 * bk], ce = L.blk[4 * bk + 1], es = L.blk[4 * bk + 2], ee = L.blk[4 * bk + 3];
-        int ne = ee - es;
-        A.assign((long)ne * ne, 0.0);
-        for (int a = 0; a < ne; ++a) {
-          int r = order[es + a];
-          for (int k = 0; k < W; ++k) {
-            int rc = row_of_pad[L.ell_col[(long)k * n2 + r]];
-            if (rc < 0) continue;                 // a regular column: L21
-            int pc = pos[rc] - es;
-            if (pc < 0 || pc >= ne) continue;     // outside the block
-            A[(long)a * ne + pc] += L.ell_val[(long)k * n2 + r];
-          }
+    return build_smo2_blocks(L, exact ? n2 : par.ras_block, exact ? 0 : par.ras_overlap, par.nthreads, err);
+  }
+  return CCM_OK;
+}
+
+int build_smo2_blocks(HostLevel& L, int block, int overlap, int nthreads, std::string& err) {
+  const int n2 = L.n2, W = L.W;
+  const long np = L.npad();
+  const std::vector<int32_t>& order = L.order;
+  std::vector<int> pos(n2);
+  for (int p = 0; p < n2; ++p) pos[order[p]] = p;
+  const int m = std::max(std::min(8, n2), block), dl = std::max(0, overlap);
+  const int nblk = (n2 + m - 1) / m;
+  L.blk.assign(4L * nblk, 0);
+  L.blk_off.assign(nblk, 0);
+  long off = 0;
+  for (int bk = 0; bk < nblk; ++bk) {
+    int cs = bk * m, ce = std::min(n2, cs + m);
+    int es = std::max(0, cs - dl), ee = std::min(n2, ce + dl);
+    L.blk[4 * bk + 0] = cs;
+    L.blk[4 * bk + 1] = ce;
+    L.blk[4 * bk + 2] = es;
+    L.blk[4 * bk + 3] = ee;
+    L.blk_off[bk] = off;
+    off += (long)(ee - es) * (ce - cs);
+  }
+  L.blk_inv.assign(off, 0.0);
+  // the padded cell of every row, to look up the L22 entries
+  std::vector<int> row_of_pad(np, -1);
+  for (int r = 0; r < n2; ++r) row_of_pad[L.irr_cell[r]] = r;
+  std::atomic<int> bad{0};
+  std::atomic<int> next{0};
+  int nt = nthreads > 0 ? nthreads : (int)std::max(1u, std::thread::hardware_concurrency());
+  auto worker = [&]() {
+    std::vector<double> A;
+    while (true) {
+      int bk = next.fetch_add(1);
+      if (bk >= nblk) break;
+      int cs = L.blk[4 * bk], ce = L.blk[4 * bk + 1], es = L.blk[4 * bk + 2], ee = L.blk[4 * bk + 3];
+      int ne = ee - es;
+      A.assign((long)ne * ne, 0.0);
+      for (int a = 0; a < ne; ++a) {
+        int r = order[es + a];
+        for (int k = 0; k < W; ++k) {
+          int rc = row_of_pad[L.ell_col[(long)k * n2 + r]];
+          if (rc < 0) continue;                 // a regular column: L21
+          int pc = pos[rc] - es;
+          if (pc < 0 || pc >= ne) continue;     // outside the block
+          A[(long)a * ne + pc] += L.ell_val[(long)k * n2 + r];
         }
-        if (!dense_inverse(A, ne)) {
-          bad.store(1);
-          continue;
-        }
-        double* dst = &L.blk_inv[L.blk_off[bk]];
-        int nc = ce - cs;
-        for (int e = 0; e < ne; ++e)
-          for (int c = 0; c < nc; ++c) dst[(long)e * nc + c] = A[(long)(cs - es + c) * ne + e];
       }
-    };
-    std::vector<std::thread> th;
-    for (int t = 0; t < nt; ++t) th.emplace_back(worker);
-    for (auto& t : th) t.join();
-    if (bad.load()) {
-      err = "singular L22 block";
-      return CCM_ESINGULAR;
+      if (!dense_inverse(A, ne)) {
+        bad.store(1);
+        continue;
+      }
+      double* dst = &L.blk_inv[L.blk_off[bk]];
+      int nc = ce - cs;
+      for (int e = 0; e < ne; ++e)
+        for (int c = 0; c < nc; ++c) dst[(long)e * nc + c] = A[(long)(cs - es + c) * ne + e];
     }
+  };
+  std::vector<std::thread> th;
+  for (int t = 0; t < nt; ++t) th.emplace_back(worker);
+  for (auto& t : th) t.join();
+  if (bad.load()) {
+    err = "singular L22 block";
+    return CCM_ESINGULAR;
   }
   return CCM_OK;
 }

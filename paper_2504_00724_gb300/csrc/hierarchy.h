@@ -84,5 +84,8 @@ int hierarchy_rows(const Hierarchy& H, int level, int32_t* cell, int32_t* cols, 
 // the hierarchy of the transposed operators (L^(m))^T, on the same geometry
 int build_transposed(const Hierarchy& H, const ccm_params& par, Hierarchy& T, std::string& err);
 bool dense_inverse(std::vector<double>& A, int n);   // in place, partial pivoting
+// SMO-2 blocks of a level's fitted rows in L.order: cores of `block` consecutive rows widened
+// by `overlap` rows on each side, and the core rows of every widened block's L22 inverse
+int build_smo2_blocks(HostLevel& L, int block, int overlap, int nthreads, std::string& err);
 
 }  // namespace ccm

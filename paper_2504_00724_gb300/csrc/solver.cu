@@ -116,6 +116,7 @@ template <> const float* Bot<float>(const DevLevel& L) { return L.bot32; }
 
 struct Arena {
   std::vector<void*> blocks;
+  std::vector<long> sizes;
   long bytes = 0;
   cudaError_t err = cudaSuccess;
   template <typename T>
@@ -126,8 +127,21 @@ struct Arena {
     if (err != cudaSuccess) return nullptr;
     if (zero) err = cudaMemset(p, 0, n * sizeof(T));
     blocks.push_back(p);
+    sizes.push_back(n * (long)sizeof(T));
     bytes += n * (long)sizeof(T);
     return (T*)p;
+  }
+  // give one earlier allocation back (nullptr: nothing)
+  void free(void* p) {
+    if (!p) return;
+    for (size_t k = 0; k < blocks.size(); ++k)
+      if (blocks[k] == p) {
+        cudaFree(p);
+        bytes -= sizes[k];
+        blocks.erase(blocks.begin() + k);
+        sizes.erase(sizes.begin() + k);
+        return;
+      }
   }
   template <typename T>
   T* upload(const std::vector<T>& v) {
@@ -138,6 +152,7 @@ struct Arena {
   void release() {
     for (void* p : blocks) cudaFree(p);
     blocks.clear();
+    sizes.clear();
   }
 };
 
@@ -829,6 +844,77 @@ bool make_tmap(CUtensorMap* map, void* base, int pitch, int rows, bool fp64, int
                    fp64 ? 8 : 4, dev::HX, dev::HY, depth);
 }
 
+// device copies of level m's SMO-2 blocks (the ones of a previous call are given back)
+int upload_blocks(ccm_handle* h, int m) {
+  Arena& A = h->arena;
+  const HostLevel& hl = h->H.levels[m];
+  DevLevel& d = h->L[m];
+  for (void* p : {(void*)d.order, (void*)d.blk, (void*)d.blk_off, (void*)d.inv64, (void*)d.inv32}) A.free(p);
+  d.order = d.blk = nullptr;
+  d.blk_off = nullptr;
+  d.inv64 = nullptr;
+  d.inv32 = nullptr;
+  d.max_ext = d.max_core = 0;
+  d.nblk = (int)hl.blk.size() / 4;
+  if (!d.nblk) return CCM_OK;
+  d.order = A.upload(hl.order);
+  d.blk = A.upload(hl.blk);
+  d.blk_off = A.upload(hl.blk_off);
+  // 4 trailing zeros: bulk copies round a block's bytes up to a multiple of 16
+  std::vector<double> g(hl.blk_inv.begin(), hl.blk_inv.end());
+  g.resize(g.size() + 4, 0.0);
+  d.inv64 = A.upload(g);
+  std::vector<float> f(g.begin(), g.end());
+  d.inv32 = A.upload(f);
+  for (int b = 0; b < d.nblk; ++b) {
+    d.max_ext = std::max(d.max_ext, hl.blk[4 * b + 3] - hl.blk[4 * b + 2]);
+    d.max_core = std::max(d.max_core, hl.blk[4 * b + 1] - hl.blk[4 * b]);
+  }
+  if ((long)d.max_ext * (long)sizeof(double) > 48 * 1024) return CCM_EINVAL;
+  return A.err == cudaSuccess ? CCM_OK : (A.err == cudaErrorMemoryAllocation ? CCM_ENOMEM : CCM_ECUDA);
+}
+
+// launch shape of a level's persistent sweep: two stages that hold a tile item or a block item,
+// one CTA-wide item at a time (blocks with more core rows than one CTA covers keep the older
+// path), as many CTAs as stay resident
+void configure_sweep(ccm_handle* h, DevLevel& d, int nsm) {
+  const size_t need = (size_t)d.max_ext * d.max_core * sizeof(double) + d.max_ext * sizeof(double) + 16;
+  d.stage_blocks = d.nblk > 0 && need <= 200 * 1024;
+  const int rows_per_cta = d.nblk >= 16 ? std::max(1, d.max_core) : 64;
+  const bool one_chunk = d.nblk == 0 || d.max_core <= rows_per_cta;
+  const int nitems = d.nblk + d.ntiles64;
+  for (int k = 0; k < 2; ++k) d.smooth_ok[k] = false;
+  for (int k = 0; k < 2 && d.tma && one_chunk && nitems > 0; ++k) {
+    const size_t es = k == 0 ? sizeof(double) : sizeof(float);
+    const size_t tile = k == 0 ? dev::TileStage<double>::bytes(true) : dev::TileStage<float>::bytes(true);
+    const size_t blk = ((size_t)d.max_ext * d.max_core * es + 15) & ~(size_t)15;
+    const size_t stage = (std::max(tile, blk) + 127) & ~(size_t)127;
+    const size_t smem = 2 * stage + (((size_t)std::max(1, d.max_ext) * es + 15) & ~(size_t)15);
+    if (smem > 200 * 1024) continue;
+    int occ = 0;
+    if (k == 0) {
+      auto fn = h->cross ? dev::k_smooth<double, true, true> : dev::k_smooth<double, false, true>;
+      cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, 256, smem);
+      for (auto g : {h->cross ? dev::k_smooth<double, true, false> : dev::k_smooth<double, false, false>})
+        cudaFuncSetAttribute(g, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    } else {
+      auto fn = h->cross ? dev::k_smooth<float, true, true> : dev::k_smooth<float, false, true>;
+      cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, 256, smem);
+      for (auto g : {h->cross ? dev::k_smooth<float, true, false> : dev::k_smooth<float, false, false>})
+        cudaFuncSetAttribute(g, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    }
+    if (occ < 1 || nsm < 1) continue;
+    d.smooth_ok[k] = true;
+    d.smooth_stage[k] = (uint32_t)stage;
+    d.smooth_smem[k] = smem;
+    d.smooth_grid[k] = std::min(nitems, nsm * occ);
+    d.smooth_cap[k] = nsm * occ;
+  }
+  cudaGetLastError();
+}
+
 // Device copies of a host hierarchy (every level's arrays, work space, tensor maps, streams)
 int upload_hierarchy(ccm_handle* h) {
   double w[5][5];
@@ -896,25 +982,9 @@ int upload_hierarchy(ccm_handle* h) {
       d.res64 = A.alloc<double>(hl.n2);
       d.res32 = A.alloc<float>(hl.n2);
     }
-    d.nblk = (int)hl.blk.size() / 4;
-    if (d.nblk) {
-      d.order = A.upload(hl.order);
-      d.blk = A.upload(hl.blk);
-      d.blk_off = A.upload(hl.blk_off);
-      // 4 trailing zeros: bulk copies round a block's bytes up to a multiple of 16
-      std::vector<double> g(hl.blk_inv.begin(), hl.blk_inv.end());
-      g.resize(g.size() + 4, 0.0);
-      d.inv64 = A.upload(g);
-      std::vector<float> f(g.begin(), g.end());
-      d.inv32 = A.upload(f);
-      for (int b = 0; b < d.nblk; ++b) {
-        d.max_ext = std::max(d.max_ext, hl.blk[4 * b + 3] - hl.blk[4 * b + 2]);
-        d.max_core = std::max(d.max_core, hl.blk[4 * b + 1] - hl.blk[4 * b]);
-      }
-      if ((long)d.max_ext * (long)sizeof(double) > 48 * 1024) {
-        A.release();
-        return CCM_EINVAL;
-      }
+    if (int rc = upload_blocks(h, m)) {
+      A.release();
+      return rc;
     }
     d.nbc = hl.nb_cells;
     if (d.nbc) {
@@ -966,42 +1036,7 @@ int upload_hierarchy(ccm_handle* h) {
   cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, h->device);
   for (int m = 0; m < nl; ++m) {
     DevLevel& d = h->L[m];
-    const size_t need = (size_t)d.max_ext * d.max_core * sizeof(double) + d.max_ext * sizeof(double) + 16;
-    d.stage_blocks = d.nblk > 0 && need <= 200 * 1024;
-    // the persistent sweep: two stages that hold a tile item or a block item, one CTA-wide
-    // item at a time (blocks with more core rows than one CTA covers keep the older path)
-    const int rows_per_cta = d.nblk >= 16 ? std::max(1, d.max_core) : 64;
-    const bool one_chunk = d.nblk == 0 || d.max_core <= rows_per_cta;
-    const int nitems = d.nblk + d.ntiles64;
-    for (int k = 0; k < 2 && d.tma && one_chunk && nitems > 0; ++k) {
-      const size_t es = k == 0 ? sizeof(double) : sizeof(float);
-      const size_t tile = k == 0 ? dev::TileStage<double>::bytes(true) : dev::TileStage<float>::bytes(true);
-      const size_t blk = ((size_t)d.max_ext * d.max_core * es + 15) & ~(size_t)15;
-      const size_t stage = (std::max(tile, blk) + 127) & ~(size_t)127;
-      const size_t smem = 2 * stage + (((size_t)std::max(1, d.max_ext) * es + 15) & ~(size_t)15);
-      if (smem > 200 * 1024) continue;
-      int occ = 0;
-      if (k == 0) {
-        auto fn = h->cross ? dev::k_smooth<double, true, true> : dev::k_smooth<double, false, true>;
-        cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, 256, smem);
-        for (auto g : {h->cross ? dev::k_smooth<double, true, false> : dev::k_smooth<double, false, false>})
-          cudaFuncSetAttribute(g, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-      } else {
-        auto fn = h->cross ? dev::k_smooth<float, true, true> : dev::k_smooth<float, false, true>;
-        cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, 256, smem);
-        for (auto g : {h->cross ? dev::k_smooth<float, true, false> : dev::k_smooth<float, false, false>})
-          cudaFuncSetAttribute(g, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-      }
-      if (occ < 1 || nsm < 1) continue;
-      d.smooth_ok[k] = true;
-      d.smooth_stage[k] = (uint32_t)stage;
-      d.smooth_smem[k] = smem;
-      d.smooth_grid[k] = std::min(nitems, nsm * occ);
-      d.smooth_cap[k] = nsm * occ;
-    }
-    cudaGetLastError();
+    configure_sweep(h, d, nsm);
     // parents of the fitted rows' regular columns (the prolongation read by SMO-2 residuals)
     if (m + 1 < nl && h->H.levels[m].n2) {
       const HostLevel& hf = h->H.levels[m];
@@ -1176,7 +1211,7 @@ int ccm_default_params(ccm_params* p) {
   p->max_iter = 100;
   p->ras_passes = 1;
   p->ras_block = 64;
-  p->ras_overlap = 32;
+  p->ras_overlap = 24;
   p->nthreads = 0;
   p->ras_exact = 0;
   p->inner_cycles = 3;
@@ -1633,6 +1668,31 @@ static void drop_graphs(ccm_handle* h) {
   }
   for (cudaEvent_t e : h->gprof_ev) cudaEventDestroy(e);
   h->gprof_ev.clear();
+}
+
+int ccm_set_smo2_blocks(ccm_handle* h, int block, int overlap) {
+  if (!h || block < 8 || block > 128 || overlap < 0 || overlap > 64) return CCM_EINVAL;
+  if (cudaDeviceSynchronize() != cudaSuccess) return CCM_ECUDA;
+  int nsm = 0;
+  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, h->device);
+  for (ccm_handle* t : {h, h->adj}) {
+    if (!t) continue;
+    drop_graphs(t);
+    const int nl = (int)t->H.levels.size();
+    for (int m = 0; m + 1 < nl; ++m) {
+      HostLevel& hl = t->H.levels[m];
+      if (hl.n2 == 0 || hl.n2 <= t->par.ras_exact) continue;
+      std::string err;
+      int rc = build_smo2_blocks(hl, block, overlap, t->par.nthreads, err);
+      if (!rc) rc = upload_blocks(t, m);
+      if (rc) return rc;
+      configure_sweep(t, t->L[m], nsm);
+    }
+    t->par.ras_block = block;
+    t->par.ras_overlap = overlap;
+    t->info.device_bytes = t->arena.bytes;
+  }
+  return cudaDeviceSynchronize() == cudaSuccess ? CCM_OK : CCM_ECUDA;
 }
 
 int ccm_set_launch_cap(ccm_handle* h, int max_ctas) {

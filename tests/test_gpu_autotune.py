@@ -25,8 +25,10 @@ def test_autotune_star128():
     try:
         f, g = torch.tensor(fa, device="cuda"), torch.tensor(ga, device="cuda")
         cands = [c for c in AT.default_candidates() if c["omega"] == 0.7 and c["inner_cycles"] in (2, 3)]
-        best, rec = AT.autotune(s, f, g, candidates=cands, repeats=2)
-        assert len(rec) == len(cands) and all(r["ms"] > 0 for r in rec)
+        blocks = [(64, 24), (32, 16)]
+        best, rec = AT.autotune(s, f, g, candidates=cands, repeats=2, block_candidates=blocks)
+        assert len(rec) == len(blocks) + len(cands) and all(r["ms"] > 0 for r in rec)
+        assert (best.pop("ras_block"), best.pop("ras_overlap")) in blocks
         assert best in [{k: c[k] for k in best} for c in cands]
         assert s.params.nu1 == best["nu1"] and s.params.cycle == best["cycle"]
         u, st = s.solve(f, g)

@@ -117,7 +117,7 @@ def test_vcycle_equals_composed_level_calls(n, coarse_n):
         s.close()
 
 
-def _block_jacobi_sweep(lv, cells, u, r, omega, block=64, overlap=32):
+def _block_jacobi_sweep(lv, cells, u, r, omega, block, overlap):
     """One sweep of the device's default smoother written out from its definition: SMO-1 on
     the regular cells and, for each block of `block` consecutive fitted rows (in the product's
     row order, which is Alg. 3's boundary order) widened by `overlap` rows on each side, the
@@ -149,7 +149,7 @@ def test_large_default_smoother_matches_block_jacobi(big, precision, tol):
         rng = np.random.default_rng(31)
         u0 = np.where(lv.ne, rng.standard_normal(lv.nx * lv.ny), 0.0)
         r = np.where(lv.ne, rng.standard_normal(lv.nx * lv.ny), 0.0) / lv.h ** 2
-        want = _block_jacobi_sweep(lv, cells, u0, r, OMEGA)
+        want = _block_jacobi_sweep(lv, cells, u0, r, OMEGA, s.params.ras_block, s.params.ras_overlap)
         got = host(s.level_smooth(0, cuda(u0.reshape(lv.ny, lv.nx)), cuda(r.reshape(lv.ny, lv.nx)),
                                   precision)).ravel()
         assert np.abs(got - want).max() <= tol * np.abs(want).max()

@@ -54,7 +54,7 @@ def level0(prob):
     return lv, coarse
 
 
-def block_jacobi_sweep(lv, cells, u, r, omega, block=64, overlap=32):
+def block_jacobi_sweep(lv, cells, u, r, omega, block, overlap):
     """One sweep of the default smoother from its definition: SMO-1 on the regular cells and,
     for each run of `block` consecutive fitted rows (product row order = Alg. 3's boundary
     order) widened by `overlap` rows on each side, the exact solve of L22 on the widened rows
@@ -78,7 +78,7 @@ def check_sweep(s, lv, seed, precision, tol):
     rng = np.random.default_rng(seed)
     u0 = np.where(lv.ne, rng.standard_normal(lv.nx * lv.ny), 0.0)
     r = np.where(lv.ne, rng.standard_normal(lv.nx * lv.ny), 0.0) / lv.h ** 2
-    want = block_jacobi_sweep(lv, cells, u0, r, OMEGA)
+    want = block_jacobi_sweep(lv, cells, u0, r, OMEGA, s.params.ras_block, s.params.ras_overlap)
     got = host(s.level_smooth(0, cuda(u0.reshape(lv.ny, lv.nx)), cuda(r.reshape(lv.ny, lv.nx)),
                               precision)).ravel()
     assert np.abs(got - want).max() <= tol * np.abs(want).max()
@@ -146,6 +146,25 @@ def test_capped_solve_matches_direct(star288, precision):
             li = s.level_launch(m, precision)
             assert li.sweep_ctas <= CAP and li.restrict_ctas <= CAP
         assert s.level_launch(0, precision).sweep_items > 10 * CAP
+        u, st = s.solve(cuda(fa), cuda(ga))
+        assert st.rel_residual <= 1e-12
+        assert np.abs(host(u) - want).max() <= 1e-10 * np.abs(want).max()
+    finally:
+        s.close()
+
+
+@pytest.mark.parametrize("block,overlap", [(32, 16), (96, 8)])
+def test_rebuilt_smo2_blocks(star288, block, overlap):
+    """ccm_set_smo2_blocks on a set-up handle: the sweep equals the block-Jacobi sweep with the
+    new blocks, under the launch cap, and a solve still equals the direct solution."""
+    prob, lv, coarse, fa, ga, want = star288
+    s = P.Solver(prob, omega=OMEGA, rtol=1e-12, max_iter=200)
+    try:
+        s.set_smo2_blocks(block, overlap)
+        s.set_launch_cap(CAP)
+        assert s.level_launch(0, P.CCM_MIXED).sweep_items > 3 * CAP
+        check_sweep(s, lv, 47, P.CCM_FP64, 1e-10)
+        check_sweep(s, lv, 48, P.CCM_MIXED, 2e-4)
         u, st = s.solve(cuda(fa), cuda(ga))
         assert st.rel_residual <= 1e-12
         assert np.abs(host(u) - want).max() <= 1e-10 * np.abs(want).max()
