@@ -143,6 +143,11 @@ typedef struct {
   double plg_cond_max;  /* largest 2-norm condition number of a chosen FV sample matrix */
   int batch;            /* right-hand sides ccm_solve advances together (1 unless params.batch > 1
                            and the conditions stated there hold) */
+  /* wall time of the phases of ccm_setup (ms), the columns of the paper's setup tables:
+   * cut cells, moments and merging of every level (Sec. 3.1, Alg. 1); PLG stencils and
+   * weighted fits (Sec. 3.3); the boundary order of Alg. 3 with the SMO-2 block inverses and
+   * the packing; the coarsest level's dense inverse; the upload and device configuration */
+  double setup_geometry_ms, setup_fits_ms, setup_blocks_ms, setup_bottom_ms, setup_upload_ms;
 } ccm_info;
 
 typedef struct {
@@ -201,13 +206,31 @@ int ccm_level_rows(const ccm_handle* h, int level, int64_t* n_rows, int32_t* cel
  * eq. iteratedIntegral): for every non-pure non-empty cell, nodes and weights whose weighted
  * sum over f is the integral of f over the (merged) cut cell; for every boundary segment,
  * nodes, arc-length weights and outward unit normals along its pieces.  Pure cells are plain
- * squares (the caller uses a tensor Gauss rule).  Call with NULL arrays to get the counts
+ * squares (ccm_cell_averages applies a tensor Gauss rule to them).  Call with NULL arrays to get the counts
  * in *n_cell_nodes / *n_bdry_nodes, then again with host arrays of those sizes:
  *   cell_of[n]: linear cell index, cxy[2n]: (x, y), cw[n]: weight (area units);
  *   seg_of[m]: segment index, bxy[2m]: (x, y), bw[m]: weight (length), bn[2m]: normal. */
 int ccm_quadrature(const ccm_handle* h, int64_t* n_cell_nodes, int64_t* n_bdry_nodes,
                    int32_t* cell_of, double* cxy, double* cw,
                    int32_t* seg_of, double* bxy, double* bw, double* bn);
+
+/* Input averages the discretisation expects (Sec. 3.2, eq. iteratedIntegral), with the
+ * caller's functions evaluated at the library's nodes.  The library calls f (or g) with host
+ * arrays of n node coordinates, possibly several times, and the function fills out[0, n):
+ *   ccm_field_fn: out = f(x, y);
+ *   ccm_grad_fn:  u, ux, uy = u(x, y) and its gradient.
+ * ccm_cell_averages: out[ny][nx] (host) = the average of f over every non-empty (survivor)
+ *   cell: the 5 x 5 tensor Gauss rule on pure cells, the cut-cell rule of ccm_quadrature on
+ *   cut and merged cells; 0 on the other cells.
+ * ccm_boundary_averages: out[n_segments] (host) = the average over every boundary segment of
+ *   its operator gamma1 u + gamma2 du/dn (ccm_boundary_robin; n the outward unit normal), by
+ *   the rule of ccm_quadrature along the segment's pieces.
+ * Blocking, host only.  Errors: CCM_EINVAL (NULL arguments). */
+typedef void (*ccm_field_fn)(void* ctx, int64_t n, const double* x, const double* y, double* out);
+typedef void (*ccm_grad_fn)(void* ctx, int64_t n, const double* x, const double* y, double* u, double* ux,
+                            double* uy);
+int ccm_cell_averages(const ccm_handle* h, ccm_field_fn f, void* ctx, double* out);
+int ccm_boundary_averages(const ccm_handle* h, ccm_grad_fn g, void* ctx, double* out);
 
 /* out = L u + N g (eq. PoissonLinearDiscretization) on the finest level, physical units.
  * u, out: device [nrhs][ny][nx] FP64; g: device [nrhs][n_segments] FP64 (may be NULL: g = 0).

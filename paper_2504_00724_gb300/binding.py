@@ -52,7 +52,10 @@ class ccm_info(ctypes.Structure):
                 ("n_cells", ctypes.c_int64), ("n_regular", ctypes.c_int64),
                 ("n_irregular", ctypes.c_int64), ("n_segments", ctypes.c_int64),
                 ("device_bytes", ctypes.c_int64), ("setup_ms", ctypes.c_double),
-                ("plg_cond_max", ctypes.c_double), ("batch", ctypes.c_int)]
+                ("plg_cond_max", ctypes.c_double), ("batch", ctypes.c_int),
+                ("setup_geometry_ms", ctypes.c_double), ("setup_fits_ms", ctypes.c_double),
+                ("setup_blocks_ms", ctypes.c_double), ("setup_bottom_ms", ctypes.c_double),
+                ("setup_upload_ms", ctypes.c_double)]
 
 
 class ccm_launch_info(ctypes.Structure):
@@ -68,6 +71,10 @@ class ccm_stats(ctypes.Structure):
 
 _LIB = None
 
+DP = ctypes.POINTER(ctypes.c_double)
+FIELD_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_int64, DP, DP, DP)
+GRAD_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_int64, DP, DP, DP, DP, DP)
+
 P = ctypes.c_void_p
 I = ctypes.c_int
 I64P = ctypes.POINTER(ctypes.c_int64)
@@ -81,6 +88,8 @@ _SIGS = {
     "ccm_boundary_robin": (I, [P, P]),
     "ccm_level_rows": (I, [P, I, I64P, P, P, P, P, P]),
     "ccm_quadrature": (I, [P, I64P, I64P, P, P, P, P, P, P, P]),
+    "ccm_cell_averages": (I, [P, FIELD_FN, P, P]),
+    "ccm_boundary_averages": (I, [P, GRAD_FN, P, P]),
     "ccm_apply": (I, [P, P, P, P, I, P]),
     "ccm_apply_T": (I, [P, P, P, P, I, P]),
     "ccm_solve": (I, [P, P, P, P, I, P, ctypes.POINTER(ccm_stats)]),
@@ -416,46 +425,49 @@ class Solver:
         _check(lib().ccm_profile_read(self.h, ctypes.byref(ms), ctypes.byref(n)), "ccm_profile_read")
         return ms.value, n.value
 
-    # ---- caller-side helpers (input preparation, not part of the solve)
+    # ---- input averages: the library's rules, the caller's functions (marshalled through
+    # ctypes callbacks that only evaluate them at the nodes the library passes)
     def cell_averages(self, fn, quad=None) -> np.ndarray:
-        """<fn> over every non-empty cell [ny, nx] (host): 5 x 5 Gauss on pure cells, the
-        library's cut-cell quadrature elsewhere."""
-        st, ow, rg, vol = self.cell_map()
-        h = self.prob.h
+        """<fn> over every non-empty cell [ny, nx] (host), by ccm_cell_averages; fn(x, y) is
+        vectorised over numpy arrays.  `quad` is accepted for compatibility and unused."""
+        err = []
+
+        def cb(ctx, n, x, y, out):
+            try:
+                X = np.ctypeslib.as_array(x, shape=(n,))
+                Y = np.ctypeslib.as_array(y, shape=(n,))
+                np.ctypeslib.as_array(out, shape=(n,))[:] = fn(X, Y)
+            except Exception as e:      # re-raised after the call
+                err.append(e)
+
         out = np.zeros((self.ny, self.nx))
-        gx, gw = np.polynomial.legendre.leggauss(5)
-        pj, pi = np.nonzero(st == 1)
-        xc = self.prob.x0 + (pi + 0.5) * h
-        yc = self.prob.y0 + (pj + 0.5) * h
-        acc = np.zeros(xc.shape)
-        for a in range(5):
-            for b in range(5):
-                acc += gw[a] * gw[b] * fn(xc + 0.5 * h * gx[a], yc + 0.5 * h * gx[b])
-        out[pj, pi] = acc / 4.0
-        cell, cxy, cw, *_ = self.quadrature() if quad is None else quad
-        if len(cell):
-            vals = fn(cxy[:, 0], cxy[:, 1]) * cw
-            sums = np.bincount(cell, weights=vals, minlength=self.nx * self.ny)
-            cut = (st == 2).ravel()
-            flat = out.ravel()
-            flat[cut] = sums[cut] / (vol.ravel()[cut] * h * h)
-            out = flat.reshape(self.ny, self.nx)
+        c = FIELD_FN(cb)
+        _check(lib().ccm_cell_averages(self.h, c, None, out.ctypes.data), "ccm_cell_averages")
+        if err:
+            raise err[0]
         return out
 
     def boundary_averages(self, u, ux, uy, quad=None) -> np.ndarray:
-        """<<N u>> over every boundary segment (host): u (Dirichlet), grad u . n (Neumann) or
-        gamma1 u + gamma2 grad u . n (Robin)."""
-        gam = self.boundary_operator()
-        q = self.quadrature() if quad is None else quad
-        seg, bxy, bw, bn = q[3], q[4], q[5], q[6]
-        x, y = bxy[:, 0], bxy[:, 1]
-        g1, g2 = gam[seg, 0], gam[seg, 1]
-        uv = u(x, y)
-        dn = ux(x, y) * bn[:, 0] + uy(x, y) * bn[:, 1]
-        val = np.where(g2 == 0, g1 * uv, np.where(g1 == 0, g2 * dn, g1 * uv + g2 * dn))
-        num = np.bincount(seg, weights=val * bw, minlength=self.nseg)
-        den = np.bincount(seg, weights=bw, minlength=self.nseg)
-        return num / den
+        """<<N u>> over every boundary segment (host), by ccm_boundary_averages: u (Dirichlet),
+        grad u . n (Neumann) or gamma1 u + gamma2 grad u . n (Robin).  `quad` is unused."""
+        err = []
+
+        def cb(ctx, n, x, y, pu, pux, puy):
+            try:
+                X = np.ctypeslib.as_array(x, shape=(n,))
+                Y = np.ctypeslib.as_array(y, shape=(n,))
+                np.ctypeslib.as_array(pu, shape=(n,))[:] = u(X, Y)
+                np.ctypeslib.as_array(pux, shape=(n,))[:] = ux(X, Y)
+                np.ctypeslib.as_array(puy, shape=(n,))[:] = uy(X, Y)
+            except Exception as e:
+                err.append(e)
+
+        out = np.zeros(self.nseg)
+        c = GRAD_FN(cb)
+        _check(lib().ccm_boundary_averages(self.h, c, None, out.ctypes.data), "ccm_boundary_averages")
+        if err:
+            raise err[0]
+        return out
 
 
 class Group:

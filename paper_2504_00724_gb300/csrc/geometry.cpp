@@ -1067,4 +1067,85 @@ void boundary_quadrature(const CutLevel& cg, std::vector<int32_t>& seg, std::vec
   }
 }
 
+void cell_averages(const CutLevel& cg, void (*f)(void*, int64_t, const double*, const double*, double*), void* ctx,
+                   double* out) {
+  const long N = (long)cg.nx * cg.ny;
+  std::fill(out, out + N, 0.0);
+  // pure cells: 5 x 5 tensor Gauss-Legendre rule on the square, exact for Q_9
+  std::vector<double> gx, gw;
+  gauss_legendre(5, gx, gw);
+  const long batch_cells = 8192;
+  std::vector<long> cells;
+  std::vector<double> x, y, v;
+  auto flush = [&]() {
+    if (cells.empty()) return;
+    v.resize(x.size());
+    f(ctx, (int64_t)x.size(), x.data(), y.data(), v.data());
+    for (size_t k = 0; k < cells.size(); ++k) {
+      double acc = 0.0;
+      for (int a = 0; a < 5; ++a)
+        for (int b = 0; b < 5; ++b) acc += gw[a] * gw[b] * v[k * 25 + a * 5 + b];
+      out[cells[k]] = 0.25 * acc;
+    }
+    cells.clear();
+    x.clear();
+    y.clear();
+  };
+  for (long q = 0; q < N; ++q) {
+    if (cg.status[q] != ST_PURE) continue;
+    const double xc = cg.cx((int)(q % cg.nx)), yc = cg.cy((int)(q / cg.nx));
+    cells.push_back(q);
+    for (int a = 0; a < 5; ++a)
+      for (int b = 0; b < 5; ++b) {
+        x.push_back(xc + 0.5 * cg.h * gx[a]);
+        y.push_back(yc + 0.5 * cg.h * gx[b]);
+      }
+    if ((long)cells.size() == batch_cells) flush();
+  }
+  flush();
+  // cut and merged cells: the cut-cell rule, divided by the cell's area
+  std::vector<int32_t> cc;
+  std::vector<double> xy, w;
+  cell_quadrature(cg, cc, xy, w);
+  if (cc.empty()) return;
+  const size_t n = cc.size();
+  x.resize(n);
+  y.resize(n);
+  v.resize(n);
+  for (size_t k = 0; k < n; ++k) {
+    x[k] = xy[2 * k];
+    y[k] = xy[2 * k + 1];
+  }
+  f(ctx, (int64_t)n, x.data(), y.data(), v.data());
+  std::vector<double> sum(N, 0.0);
+  for (size_t k = 0; k < n; ++k) sum[cc[k]] += w[k] * v[k];
+  for (long q = 0; q < N; ++q)
+    if (cg.status[q] == ST_CUT) out[q] = sum[q] / (cg.vol[q] * cg.h * cg.h);
+}
+
+void boundary_averages(const CutLevel& cg,
+                       void (*g)(void*, int64_t, const double*, const double*, double*, double*, double*),
+                       void* ctx, double* out) {
+  std::vector<int32_t> seg;
+  std::vector<double> xy, w, nrm;
+  boundary_quadrature(cg, seg, xy, w, nrm);
+  const size_t ns = cg.segs.size(), n = seg.size();
+  std::vector<double> x(n), y(n), u(n), ux(n), uy(n), num(ns, 0.0), den(ns, 0.0);
+  for (size_t k = 0; k < n; ++k) {
+    x[k] = xy[2 * k];
+    y[k] = xy[2 * k + 1];
+  }
+  if (n) g(ctx, (int64_t)n, x.data(), y.data(), u.data(), ux.data(), uy.data());
+  for (size_t k = 0; k < n; ++k) {
+    const int s = seg[k];
+    const double g1 = cg.seg_gamma[s][0], g2 = cg.seg_gamma[s][1];
+    double val = 0.0;
+    if (g1 != 0.0) val += g1 * u[k];
+    if (g2 != 0.0) val += g2 * (ux[k] * nrm[2 * k] + uy[k] * nrm[2 * k + 1]);
+    num[s] += val * w[k];
+    den[s] += w[k];
+  }
+  for (size_t s = 0; s < ns; ++s) out[s] = den[s] > 0.0 ? num[s] / den[s] : 0.0;
+}
+
 }  // namespace ccm

@@ -3,6 +3,7 @@
 // Alg. 3; SMO-2 uses overlapping blocks of that order with precomputed dense inverses of the
 // L22 sub-blocks, and the coarsest level a dense inverse of L^(M).
 #include <algorithm>
+#include <chrono>
 #include <cmath>
 #include <map>
 #include <thread>
@@ -521,13 +522,21 @@ int build_hierarchy(const ccm_problem& prob, const ccm_params& par, Hierarchy& H
   H.cond_max = 0;
   double w[5][5];
   regular_stencil(prob.a, prob.b, prob.c, w);
+  using clk = std::chrono::steady_clock;
+  auto ms_since = [](clk::time_point t) { return std::chrono::duration<double, std::milli>(clk::now() - t).count(); };
+  H.ms_geometry = H.ms_fits = H.ms_blocks = H.ms_bottom = 0;
   for (int m = 0; m < nl; ++m) {
     CutLevel& cg = H.cut[m];
+    auto t0 = clk::now();
     int rc = build_cut_level(prob, prob.nx >> m, prob.ny >> m, prob.h * (double)(1 << m), par.theta, cg, err);
+    H.ms_geometry += ms_since(t0);
     if (rc) return rc;
     Rows fit;
+    t0 = clk::now();
     rc = discretize_level(cg, prob.a, prob.b, prob.c, par.nthreads, fit, err, fb);
+    H.ms_fits += ms_since(t0);
     if (rc) return rc;
+    t0 = clk::now();
     if (m == 0) H.cond_max = fit.cond_max;
     PackRows rows;
     rows.W = 15;
@@ -551,11 +560,14 @@ int build_hierarchy(const ccm_problem& prob, const ccm_params& par, Hierarchy& H
       rows.seg.push_back(fit.seg[r]);
     }
     rc = pack_level(cg, rows, par, m == nl - 1, m == 0, H.levels[m], err);
+    H.ms_blocks += ms_since(t0);
     if (rc) return rc;
     H.rows.push_back(std::move(rows));
     if (m == 0) H.nseg = (int)cg.segs.size();
     if (m == nl - 1) {
+      t0 = clk::now();
       rc = finish_bottom(H.levels[m], cg, w, err);
+      H.ms_bottom += ms_since(t0);
       if (rc) return rc;
     }
   }

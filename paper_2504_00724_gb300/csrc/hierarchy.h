@@ -73,6 +73,9 @@ struct Hierarchy {
   std::vector<PackRows> rows;      // the rows every level was packed from
   double cond_max = 0;
   int nseg = 0;
+  // wall time of the setup phases (ms): cut cells and merging, stencils and fits, the boundary
+  // order with packing and the SMO-2 block inverses, the coarsest level's dense inverse
+  double ms_geometry = 0, ms_fits = 0, ms_blocks = 0, ms_bottom = 0;
 };
 
 int build_hierarchy(const ccm_problem& prob, const ccm_params& par, Hierarchy& H, std::string& err,

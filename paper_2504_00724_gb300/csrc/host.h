@@ -142,5 +142,15 @@ void cell_quadrature(const CutLevel& cg, std::vector<int32_t>& cell, std::vector
                      std::vector<double>& w);
 void boundary_quadrature(const CutLevel& cg, std::vector<int32_t>& seg, std::vector<double>& xy,
                          std::vector<double>& w, std::vector<double>& n);
+// cell averages of f over every non-empty cell into out[ny * nx] (0 elsewhere): the 5 x 5
+// tensor Gauss rule on pure cells, cell_quadrature on cut and merged cells; f evaluated by the
+// caller in batches
+void cell_averages(const CutLevel& cg, void (*f)(void*, int64_t, const double*, const double*, double*), void* ctx,
+                   double* out);
+// averages of gamma1 u + gamma2 du/dn over every boundary segment into out[n_segments], from
+// the caller's u and gradient at the nodes of boundary_quadrature
+void boundary_averages(const CutLevel& cg,
+                       void (*g)(void*, int64_t, const double*, const double*, double*, double*, double*),
+                       void* ctx, double* out);
 
 }  // namespace ccm

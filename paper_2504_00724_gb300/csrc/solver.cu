@@ -1274,8 +1274,14 @@ int ccm_setup(const ccm_problem* prob, const ccm_params* params, ccm_handle** ou
     return CCM_ENOMEM;
   }
   if (rc) return rc;
+  auto t_up = std::chrono::steady_clock::now();
   rc = upload_hierarchy(h.get());
   if (rc) return rc;
+  h->info.setup_upload_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t_up).count();
+  h->info.setup_geometry_ms = h->H.ms_geometry;
+  h->info.setup_fits_ms = h->H.ms_fits;
+  h->info.setup_blocks_ms = h->H.ms_blocks;
+  h->info.setup_bottom_ms = h->H.ms_bottom;
   const int nl = (int)h->H.levels.size();
   Arena& A = h->arena;
   // info
@@ -1383,6 +1389,18 @@ int ccm_quadrature(const ccm_handle* h, int64_t* n_cell_nodes, int64_t* n_bdry_n
   }
   *n_cell_nodes = (int64_t)cc.size();
   *n_bdry_nodes = (int64_t)ss.size();
+  return CCM_OK;
+}
+
+int ccm_cell_averages(const ccm_handle* h, ccm_field_fn f, void* ctx, double* out) {
+  if (!h || !f || !out) return CCM_EINVAL;
+  cell_averages(h->H.cut[0], f, ctx, out);
+  return CCM_OK;
+}
+
+int ccm_boundary_averages(const ccm_handle* h, ccm_grad_fn g, void* ctx, double* out) {
+  if (!h || !g || !out) return CCM_EINVAL;
+  boundary_averages(h->H.cut[0], g, ctx, out);
   return CCM_OK;
 }
 
