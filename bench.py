@@ -445,23 +445,41 @@ def adjoint_case(stream, n=2048, ndir=16, eps=1e-6):
         e1.synchronize()
         ms = e0.elapsed_time(e1)
         gf, gg = f.grad.detach(), g.grad.detach()
+        iters = s.solve(f.detach(), g.detach())[1].iterations
         # the loss is quadratic, so central differences have no truncation error at any step;
-        # what remains is J's rounding and the solves' stopping points, both divided by eps
-        worst = {eps: 0.0, 1e-3: 0.0}
-        for _ in range(ndir):
-            df = torch.tensor(np.where(ne, rng.standard_normal(ne.shape), 0.0), device="cuda")
-            dg = torch.tensor(rng.standard_normal(len(ga)), device="cuda")
-            ad = float((gf * df).sum() + (gg * dg).sum())
-            for e in worst:
+        # what remains is J's rounding and the solves' stopping points, both divided by eps.
+        # The second set of differences takes every solve through the same number of cycles
+        # (the base solve's, plus two), so that the solution map is one linear map
+        fixed = P.Solver(prob, precision=P.CCM_FP64, rtol=0.0, max_iter=iters + 2)
+
+        def loss_fixed(ff, gg_):
+            u, _ = fixed.solve(ff, gg_, check=False)
+            return float((0.5 * ((u - ob) ** 2 * mask).sum()).item())
+
+        worst = {"rtol": 0.0, "fixed": 0.0}
+        try:
+            for _ in range(ndir):
+                df = torch.tensor(np.where(ne, rng.standard_normal(ne.shape), 0.0), device="cuda")
+                dg = torch.tensor(rng.standard_normal(len(ga)), device="cuda")
+                ad = float((gf * df).sum() + (gg * dg).sum())
                 with torch.no_grad():
-                    jp = loss(f + e * df, g + e * dg).item()
-                    jm = loss(f - e * df, g - e * dg).item()
-                worst[e] = max(worst[e], abs((jp - jm) / (2 * e) - ad) / abs(ad))
+                    jp = loss(f + eps * df, g + eps * dg).item()
+                    jm = loss(f - eps * df, g - eps * dg).item()
+                    worst["rtol"] = max(worst["rtol"], abs((jp - jm) / (2 * eps) - ad) / abs(ad))
+                    jp = loss_fixed(f + eps * df, g + eps * dg)
+                    jm = loss_fixed(f - eps * df, g - eps * dg)
+                    worst["fixed"] = max(worst["fixed"], abs((jp - jm) / (2 * eps) - ad) / abs(ad))
+        finally:
+            fixed.close()
         return {"workload": f"star {n}x{n}, (a,b,c)=(1,0.3,1), loss 0.5||u-u_obs||^2, u_obs = exact cell "
                             "averages + N(0,1e-3^2) (seed 5), FP64 solves to rel. residual 1e-13",
                 "value": int(s.info.n_cells) / (ms / 1000.0), "unit": "unknowns/s (forward + adjoint solve)",
                 "ms_forward_and_gradient": ms, "fd_directions": ndir, "fd_eps": eps,
-                "fd_max_rel_diff": worst[eps], "fd_max_rel_diff_eps_1e-3": worst[1e-3]}
+                "fd_max_rel_diff": worst["rtol"],
+                "fd_max_rel_diff_fixed_cycles": worst["fixed"],
+                "fd_note": "fd_max_rel_diff: every solve to rel. residual 1e-13 (its stopping point moves "
+                           "with the data); fixed_cycles: every finite-difference solve runs the base "
+                           "solve's cycle count + 2"}
     finally:
         s.close()
 
@@ -505,10 +523,14 @@ def equal_accuracy(prob, mms, stream, flush, coarsest, rtols=(1e-10, 1e-12, 1e-1
             sv.close()
         a, b = row["mixed"]["err_vs_exact"], row["fp64"]["err_vs_exact"]
         row["exact_errors_agree_2_digits"] = float(f"{a:.1e}") == float(f"{b:.1e}")
+        row["both_within_20pct_of_discretisation_error"] = max(row["mixed"]["err_vs_discrete"],
+                                                               row["fp64"]["err_vs_discrete"]) <= 0.2 * disc
         row["mixed_over_fp64"] = row["fp64"]["ms"] / row["mixed"]["ms"]
         rows.append(row)
-    agree = [r for r in rows if r["exact_errors_agree_2_digits"]]
+    agree = [r for r in rows if r["both_within_20pct_of_discretisation_error"]]
     return {"discrete_rel_residual": std.rel_residual, "discrete_err_vs_exact": disc, "by_rtol": rows,
+            "criterion": "both forms' max-norm errors against the discrete solution below 20 % of the "
+                         "discretisation error",
             "mixed_over_fp64_at_equal_accuracy": agree[0]["mixed_over_fp64"] if agree else None,
             "equal_accuracy_rtol": agree[0]["rtol"] if agree else None}
 
@@ -742,6 +764,8 @@ def main():
                        "l2": "flushed (256 MB write) before every step", "parallelism": f"replicas x{world}"},
             "iterations": iters, "rel_residual": st.rel_residual, "max_error_vs_exact": err,
             "vcycle_ms": (vc_ms / vc_n) if vc_n else None, "vcycle": vcycle, "setup_s": setup_s,
+            "setup_phases_ms": {k: getattr(info, "setup_" + k + "_ms") for k in ("geometry", "fits", "blocks",
+                                                                              "bottom", "upload")},
             "fp64": fp64, "mixed_over_fp64": (value / world / fp64["value"]) if fp64 else None,
             "equal_accuracy": eq,
             "configs": configs,
