@@ -80,17 +80,21 @@ static std::vector<int> boundary_order(const CutLevel& cg, const PackRows& rows)
   };
   std::vector<Key> keys;
   const double W = nx * cg.h, Hh = ny * cg.h;
-  for (long q = 0; q < (long)nx * ny; ++q) {
-    int j = (int)(q / nx), i = (int)(q % nx);
-    if (cg.iface[q]) {
-      keys.push_back({1 + cg.first_curve.at((int)q), cg.arc_param.at((int)q), (int)q});
-    } else if (cg.status[q] == ST_PURE && cg.seg_of.count((int)q)) {
-      double xc = cg.cx(i) - cg.x0, yc = cg.cy(j) - cg.y0;
-      double d[4] = {yc, W - xc, Hh - yc, xc};
-      int e = (int)(std::min_element(d, d + 4) - d);
-      double s[4] = {xc, W + yc, W + Hh + (W - xc), 2 * W + Hh + (Hh - yc)};
-      keys.push_back({0, s[e], (int)q});
-    }
+  // the interface cells and the pure cells with a boundary piece (box walls); the sort below
+  // is a total order, so the order of collection does not matter
+  for (const auto& kv : cg.first_curve) {
+    const int q = kv.first;
+    if (cg.iface[q]) keys.push_back({1 + kv.second, cg.arc_param.at(q), q});
+  }
+  for (const auto& kv : cg.seg_of) {
+    const int q = kv.first;
+    if (cg.iface[q] || cg.status[q] != ST_PURE) continue;
+    const int j = q / nx, i = q % nx;
+    double xc = cg.cx(i) - cg.x0, yc = cg.cy(j) - cg.y0;
+    double d[4] = {yc, W - xc, Hh - yc, xc};
+    int e = (int)(std::min_element(d, d + 4) - d);
+    double s[4] = {xc, W + yc, W + Hh + (W - xc), 2 * W + Hh + (Hh - yc)};
+    keys.push_back({0, s[e], q});
   }
   std::sort(keys.begin(), keys.end(), [](const Key& x, const Key& y) {
     if (x.comp != y.comp) return x.comp < y.comp;
@@ -113,8 +117,14 @@ static std::vector<int> boundary_order(const CutLevel& cg, const PackRows& rows)
         frontier.push_back(q);
       }
     }
+    // only the fitted rows' cells need their nearest source: stop after the first complete
+    // level of the search at which every one of them has been reached (later levels cannot
+    // change the distance or the tie-break of a cell already reached)
+    long unreached = 0;
+    for (int q : rows.irr)
+      if (dist[q] > 0) ++unreached;
     int d = 0;
-    while (!frontier.empty()) {
+    while (!frontier.empty() && unreached > 0) {
       std::vector<int> next;
       for (int q : frontier) {
         int j = q / nx, i = q % nx;
@@ -124,6 +134,7 @@ static std::vector<int> boundary_order(const CutLevel& cg, const PackRows& rows)
             if (ii < 0 || ii >= nx || jj < 0 || jj >= ny) continue;
             int q2 = jj * nx + ii;
             if (dist[q2] > d + 1) {
+              if (dist[q2] == (1 << 30) && rowof[q2] >= 0) --unreached;
               dist[q2] = d + 1;
               who[q2] = who[q];
               next.push_back(q2);
