@@ -300,8 +300,11 @@ def many_geometries_workload(stream, flush, count=64):
     # 32^2 level of some 6- and 7-petal stars has an eigenvalue with positive real part), 32^2
     # for a three-ellipse domain, which also takes the GMRES(2) correction (the V-cycle alone
     # diverges on its larger grids)
-    solvers = [P.Solver(p, rtol=RTOL, max_iter=200, coarsest=64 if "star" in p.name else 32,
-                        krylov=0 if "star" in p.name else 2) for p in probs]
+    # independent setups, four at a time on host threads (ccm_setup releases the interpreter)
+    from concurrent.futures import ThreadPoolExecutor
+    with ThreadPoolExecutor(4) as ex:
+        solvers = list(ex.map(lambda p: P.Solver(p, rtol=RTOL, max_iter=200, coarsest=64 if "star" in p.name else 32,
+                                                 krylov=0 if "star" in p.name else 2), probs))
     setup_s = time.time() - t0
     fs, gs, exact = [], [], []
     for s, (p, m) in zip(solvers, drawn):

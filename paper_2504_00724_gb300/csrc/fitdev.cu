@@ -1,7 +1,9 @@
-// The setup's batched fits on the GPU (FitBatcher of host.h): the level's cut-cell moments,
-// volumes and boundary-piece moments go to the device once per call, the (row, candidate)
-// pairs as index lists, and k_plg_fit / k_plg_cond return the coefficients, the weighted
-// norms and the condition numbers.  Blocking; device memory is released before returning.
+// The setup's work on the GPU.  The batched fits (FitBatcher of host.h): the level's cut-cell
+// moments, volumes and boundary-piece moments go to the device once per call, the (row,
+// candidate) pairs as index lists, and k_plg_fit / k_plg_cond return the coefficients, the
+// weighted norms and the condition numbers.  The centre classification (CentreClassifier):
+// one thread per cell tests its centre against every curve.  Blocking; device memory is
+// released before returning.
 #include <cstring>
 #include <memory>
 #include <unordered_map>
@@ -166,5 +168,89 @@ class DeviceFitter final : public FitBatcher {
 }  // namespace
 
 std::unique_ptr<FitBatcher> make_device_fitter() { return std::unique_ptr<FitBatcher>(new DeviceFitter()); }
+
+namespace dev {
+
+// a curve for the centre test (the inside tests of Curve::inside)
+struct CentreCurve {
+  int kind, orient, npoly;
+  double p[8];
+  const double* poly;   // polygon vertices or the spline's polyline (x0, y0, x1, y1, ...)
+};
+
+__device__ bool centre_inside(const CentreCurve& c, double x, double y) {
+  if (c.kind == CCM_POLYGON || c.kind == CCM_SPLINE) {
+    // even-odd rule: a ray towards +x crosses the closed polyline an odd number of times
+    bool in = false;
+    for (int k = 0; k < c.npoly; ++k) {
+      const double xa = c.poly[2 * k], ya = c.poly[2 * k + 1];
+      const int k1 = k + 1 == c.npoly ? 0 : k + 1;
+      const double xb = c.poly[2 * k1], yb = c.poly[2 * k1 + 1];
+      if (ya == yb) continue;
+      if ((ya > y) != (yb > y) && x < xa + (y - ya) * (xb - xa) / (yb - ya)) in = !in;
+    }
+    return in;
+  }
+  const double dx = x - c.p[0], dy = y - c.p[1];
+  if (c.kind == CCM_CIRCLE) return dx * dx + dy * dy < c.p[2] * c.p[2];
+  if (c.kind == CCM_ELLIPSE) {
+    const double cs = cos(c.p[4]), sn = sin(c.p[4]);
+    const double X = (dx * cs + dy * sn) / c.p[2], Y = (-dx * sn + dy * cs) / c.p[3];
+    return X * X + Y * Y < 1.0;
+  }
+  return hypot(dx, dy) < c.p[2] + c.p[3] * cos(c.p[4] * atan2(dy, dx));
+}
+
+// one thread per cell: ST_PURE when the centre is inside every curve with orient +1 and
+// outside every curve with orient -1, else ST_EMPTY
+__global__ void k_classify_centres(int nx, int ny, double x0, double y0, double h, int nc,
+                                   const CentreCurve* __restrict__ curves, int8_t* __restrict__ status) {
+  const long q = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= (long)nx * ny) return;
+  const int i = (int)(q % nx), j = (int)(q / nx);
+  const double x = x0 + (i + 0.5) * h, y = y0 + (j + 0.5) * h;
+  bool in = true;
+  for (int k = 0; k < nc && in; ++k)
+    if ((curves[k].orient > 0) != centre_inside(curves[k], x, y)) in = false;
+  status[q] = in ? (int8_t)ST_PURE : (int8_t)ST_EMPTY;
+}
+
+}  // namespace dev
+
+namespace {
+
+class DeviceClassifier final : public CentreClassifier {
+ public:
+  int classify(const CutLevel& cg, std::vector<int8_t>& status) override {
+    const long N = (long)cg.nx * cg.ny;
+    status.resize(N);
+    DevBufs D;
+    std::vector<dev::CentreCurve> cv(cg.curves.size());
+    for (size_t k = 0; k < cg.curves.size(); ++k) {
+      const Curve& c = cg.curves[k];
+      dev::CentreCurve& d = cv[k];
+      d.kind = c.kind;
+      d.orient = c.orient;
+      std::memcpy(d.p, c.p, sizeof(d.p));
+      const std::vector<double>* P = c.kind == CCM_POLYGON ? &c.V : c.kind == CCM_SPLINE ? &c.poly : nullptr;
+      d.npoly = P ? (int)(P->size() / 2) : 0;
+      d.poly = P ? D.put(*P) : nullptr;
+    }
+    const dev::CentreCurve* dcv = D.put(cv);
+    int8_t* ds = D.get<int8_t>(N);
+    if (D.err != cudaSuccess) return D.err == cudaErrorMemoryAllocation ? CCM_ENOMEM : CCM_ECUDA;
+    dev::k_classify_centres<<<(unsigned)((N + 255) / 256), 256>>>(cg.nx, cg.ny, cg.x0, cg.y0, cg.h,
+                                                                  (int)cv.size(), dcv, ds);
+    if (cudaGetLastError() != cudaSuccess) return CCM_ECUDA;
+    if (cudaMemcpy(status.data(), ds, N, cudaMemcpyDeviceToHost) != cudaSuccess) return CCM_ECUDA;
+    return CCM_OK;
+  }
+};
+
+}  // namespace
+
+std::unique_ptr<CentreClassifier> make_device_classifier() {
+  return std::unique_ptr<CentreClassifier>(new DeviceClassifier());
+}
 
 }  // namespace ccm

@@ -576,7 +576,7 @@ int check_problem(const ccm_problem& prob) {
 }
 
 int build_cut_level(const ccm_problem& prob, int nx, int ny, double h, double theta, CutLevel& cg,
-                    std::string& err) {
+                    std::string& err, CentreClassifier* cc) {
   cg.nx = nx;
   cg.ny = ny;
   cg.h = h;
@@ -668,11 +668,16 @@ int build_cut_level(const ccm_problem& prob, int nx, int ny, double h, double th
     }
   }
 
-  // ---- classification of the other cells by their centres (rows over host threads; every
-  // cell's test is independent)
+  // ---- classification of the other cells by their centres (on the device when a classifier
+  // is given, else rows over host threads; every cell's test is independent)
   cg.status.assign(N, ST_EMPTY);
   cg.iface.assign(N, 0);
-  {
+  if (cc) {
+    if (int rc = cc->classify(cg, cg.status)) {
+      err = "device centre classification failed";
+      return rc;
+    }
+  } else {
     std::atomic<int> next_row{0};
     auto work = [&]() {
       for (int j = next_row.fetch_add(1); j < ny; j = next_row.fetch_add(1))

@@ -521,7 +521,8 @@ int hierarchy_rows(const Hierarchy& H, int level, int32_t* cell, int32_t* cols, 
   return CCM_OK;
 }
 
-int build_hierarchy(const ccm_problem& prob, const ccm_params& par, Hierarchy& H, std::string& err, FitBatcher* fb) {
+int build_hierarchy(const ccm_problem& prob, const ccm_params& par, Hierarchy& H, std::string& err, FitBatcher* fb,
+                    CentreClassifier* cc) {
   H.a = prob.a;
   H.b = prob.b;
   H.c = prob.c;
@@ -539,7 +540,7 @@ int build_hierarchy(const ccm_problem& prob, const ccm_params& par, Hierarchy& H
   for (int m = 0; m < nl; ++m) {
     CutLevel& cg = H.cut[m];
     auto t0 = clk::now();
-    int rc = build_cut_level(prob, prob.nx >> m, prob.ny >> m, prob.h * (double)(1 << m), par.theta, cg, err);
+    int rc = build_cut_level(prob, prob.nx >> m, prob.ny >> m, prob.h * (double)(1 << m), par.theta, cg, err, cc);
     H.ms_geometry += ms_since(t0);
     if (rc) return rc;
     Rows fit;

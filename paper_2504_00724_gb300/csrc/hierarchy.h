@@ -79,7 +79,7 @@ struct Hierarchy {
 };
 
 int build_hierarchy(const ccm_problem& prob, const ccm_params& par, Hierarchy& H, std::string& err,
-                    FitBatcher* fb = nullptr);
+                    FitBatcher* fb = nullptr, CentreClassifier* cc = nullptr);
 // fitted rows of a level in physical units and unpadded cell indices (the layout of
 // ccm_host_rows / ccm_level_rows)
 int hierarchy_rows(const Hierarchy& H, int level, int32_t* cell, int32_t* cols, double* beta, double* nb,

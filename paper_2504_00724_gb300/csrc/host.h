@@ -107,11 +107,24 @@ const Mom& pure_moments();
 Mom shift_moments(const Mom& m, double dx, double dy);
 void gauss_legendre(int n, std::vector<double>& x, std::vector<double>& w);
 
+// Classification of every cell by its centre (the O(h^-2) scan of the cut-cell setup: a cell
+// the boundary does not enter is pure when its centre is inside every curve that bounds Omega
+// from outside and outside every hole), for a setup that runs it off the host threads
+// (fitdev.cu).  status[j * nx + i] = ST_PURE or ST_EMPTY for the level's curves, box and h.
+// The interface cells, whose status the crossings decide, are overwritten afterwards, and a
+// centre that two evaluations of the curve could classify differently lies on the curve, so
+// inside an interface cell: the result equals the host scan's.
+struct CentreClassifier {
+  virtual ~CentreClassifier() = default;
+  virtual int classify(const CutLevel& cg, std::vector<int8_t>& status) = 0;
+};
+std::unique_ptr<CentreClassifier> make_device_classifier();
+
 // geometry.cpp
 // CCM_OK, or CCM_EINVAL for a problem the method does not define (sizes, ellipticity, kinds)
 int check_problem(const ccm_problem& prob);
 int build_cut_level(const ccm_problem& prob, int nx, int ny, double h, double theta, CutLevel& out,
-                    std::string& err);
+                    std::string& err, CentreClassifier* cc = nullptr);
 // Fits of many (fitted row, candidate PLG stencil) pairs in one call, for a setup that runs
 // them off the host threads (fitdev.cu).  Pair k fits the row of cell row_cell[k] over the 15
 // cells cand[k] with the host fit's arithmetic (to rounding): beta[16 k + q], norm[k] (the

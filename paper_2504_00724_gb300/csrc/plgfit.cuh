@@ -84,6 +84,7 @@ struct FitSmem {
   double Lh[FNM];
   double y[FNM];
   double w[16];
+  double wi[16];                  // 1 / w
 };
 
 // frame of a pair: the centre of the stencil's bounding box (half-integer cell units)
@@ -165,16 +166,20 @@ __global__ void __launch_bounds__(128) k_plg_fit(FitLevel L, FitBatch B) {
     const int lin = cells[2 * lane];
     const int ci = lin % L.nx, cj = lin / L.nx;
     S.w[lane] = fmax(hypot((double)(ci - i), (double)(cj - j)), 0.5);
+    S.wi[lane] = 1.0 / S.w[lane];
   }
-  if (lane == FNM) S.w[15] = 0.5;
+  if (lane == FNM) {
+    S.w[15] = 0.5;
+    S.wi[15] = 2.0;
+  }
   __syncwarp();
-  // A = M W M^T (lower triangle, 120 entries over the lanes)
+  // A = M W M^T (lower triangle, 120 entries over the lanes), W = diag(1 / w)
   for (int e = lane; e < 120; e += 32) {
     int r = 0;
     while ((r + 1) * (r + 2) / 2 <= e) ++r;
     const int s = e - r * (r + 1) / 2;
     double acc = 0;
-    for (int q = 0; q < ncol; ++q) acc += S.M[r][q] * S.M[s][q] / S.w[q];
+    for (int q = 0; q < ncol; ++q) acc += S.M[r][q] * S.M[s][q] * S.wi[q];
     S.A[r][s] = acc;
   }
   __syncwarp();
@@ -203,24 +208,28 @@ __global__ void __launch_bounds__(128) k_plg_fit(FitLevel L, FitBatch B) {
     if (lane == 0) B.ok[pair] = 0;
     return;
   }
-  if (lane == 0) {
+  // the two triangular solves with the Cholesky factor, column by column: once y_r is known,
+  // lane m subtracts its term from its own partial sum
+  {
+    double v = lane < FNM ? S.Lh[lane] : 0.0;
     for (int r = 0; r < FNM; ++r) {
-      double s = S.Lh[r];
-      for (int m = 0; m < r; ++m) s -= S.A[r][m] * S.y[m];
-      S.y[r] = s / S.A[r][r];
+      const double yr = __shfl_sync(0xffffffffu, v, r) / S.A[r][r];
+      if (lane == r) v = yr;
+      else if (lane > r && lane < FNM) v -= S.A[lane][r] * yr;
     }
     for (int r = FNM - 1; r >= 0; --r) {
-      double s = S.y[r];
-      for (int m = r + 1; m < FNM; ++m) s -= S.A[m][r] * S.y[m];
-      S.y[r] = s / S.A[r][r];
+      const double yr = __shfl_sync(0xffffffffu, v, r) / S.A[r][r];
+      if (lane == r) v = yr;
+      else if (lane < r) v -= S.A[r][lane] * yr;
     }
+    if (lane < FNM) S.y[lane] = v;
   }
   __syncwarp();
   double bq = 0, nq = 0;
   if (lane < ncol) {
     double acc = 0;
     for (int r = 0; r < FNM; ++r) acc += S.M[r][lane] * S.y[r];
-    bq = acc / S.w[lane];
+    bq = acc * S.wi[lane];
     nq = S.w[lane] * bq * bq;
   }
   const double nrm = warp_sum(nq);

@@ -1268,8 +1268,12 @@ int ccm_setup(const ccm_problem* prob, const ccm_params* params, ccm_handle** ou
   int rc;
   try {
     std::unique_ptr<FitBatcher> fb;
-    if (par.setup_device) fb = make_device_fitter();
-    rc = build_hierarchy(*prob, par, h->H, err, fb.get());
+    std::unique_ptr<CentreClassifier> cc;
+    if (par.setup_device) {
+      fb = make_device_fitter();
+      cc = make_device_classifier();
+    }
+    rc = build_hierarchy(*prob, par, h->H, err, fb.get(), cc.get());
   } catch (const std::bad_alloc&) {
     return CCM_ENOMEM;
   }

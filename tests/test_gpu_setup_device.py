@@ -1,5 +1,6 @@
-"""The setup's PLG fits on the GPU (ccm_params.setup_device = 1, one warp per candidate
-stencil) against the host fits (the host-only setup, which tests/test_host_setup.py ties to
+"""The setup's work on the GPU (ccm_params.setup_device = 1: the centre classification of every
+cell, one thread per cell, and the PLG fits, one warp per candidate stencil) against the host
+setup (the cell maps of every level equal, and the host fits (the host-only setup, which tests/test_host_setup.py ties to
 the oracle): the same stencils on every level, coefficients equal to rounding (1e-9 of the
 row's largest coefficient, the bound the host setup meets against the oracle: the
 ill-conditioned sample matrices of coarse levels amplify the different summation order; the
@@ -33,6 +34,9 @@ def test_device_fits_equal_host_fits(name):
     s = P.Solver(prob, setup_device=1)
     try:
         levels = int(s.info.levels)
+        dev_map, host_map = s.cell_map(), hs.cell_map(0)
+        for d, h in zip(dev_map, host_map[:4]):
+            assert np.array_equal(d, h)
         for m in range(levels):
             cell, cols, beta, nb, seg = s.level_rows(m)
             hc, hcols, hbeta, hnb, hseg = hs.rows(m)
@@ -63,3 +67,24 @@ def test_device_and_host_setup_solve_alike():
     (u1, c1), (u0, c0) = out
     assert np.abs(u1 - u0).max() <= 1e-10 * np.abs(u0).max()
     assert abs(c1 - c0) <= 1e-6 * c0
+
+
+@pytest.mark.parametrize("mk", [lambda: W.star(1024), lambda: W.three_ellipses(1024), lambda: W.spline_blob(512),
+                                lambda: W.paper_problem3_rotated(256)])
+def test_device_centre_classification_large(mk):
+    """The O(h^-2) scan at sizes where it matters: every level's cells (status, owner, regular
+    flag, volume) equal between the device setup and the host setup (every level's fitted rows
+    too, as a consequence)."""
+    prob = mk()
+    hs = P.HostSetup(prob, coarsest=64)
+    s = P.Solver(prob, setup_device=1, coarsest=64)
+    try:
+        dev_map, host_map = s.cell_map(), hs.cell_map(0)
+        for d, h in zip(dev_map, host_map[:4]):
+            assert np.array_equal(d, h)
+        for m in range(int(s.info.levels)):
+            assert np.array_equal(s.level_rows(m)[0], hs.rows(m)[0]), m
+            assert np.array_equal(s.level_rows(m)[1], hs.rows(m)[1]), m
+    finally:
+        s.close()
+        hs.close()
