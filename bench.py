@@ -448,41 +448,27 @@ def adjoint_case(stream, n=2048, ndir=16, eps=1e-6):
         e1.synchronize()
         ms = e0.elapsed_time(e1)
         gf, gg = f.grad.detach(), g.grad.detach()
-        iters = s.solve(f.detach(), g.detach())[1].iterations
         # the loss is quadratic, so central differences have no truncation error at any step;
-        # what remains is J's rounding and the solves' stopping points, both divided by eps.
-        # The second set of differences takes every solve through the same number of cycles
-        # (the base solve's, plus two), so that the solution map is one linear map
-        fixed = P.Solver(prob, precision=P.CCM_FP64, rtol=0.0, max_iter=iters + 2)
-
-        def loss_fixed(ff, gg_):
-            u, _ = fixed.solve(ff, gg_, check=False)
-            return float((0.5 * ((u - ob) ** 2 * mask).sum()).item())
-
-        worst = {"rtol": 0.0, "fixed": 0.0}
-        try:
-            for _ in range(ndir):
-                df = torch.tensor(np.where(ne, rng.standard_normal(ne.shape), 0.0), device="cuda")
-                dg = torch.tensor(rng.standard_normal(len(ga)), device="cuda")
-                ad = float((gf * df).sum() + (gg * dg).sum())
+        # what remains is rounding: at eps = 1e-6 the change of u (eps |L^-1 d|, about 1e-13
+        # here) is only a thousand times the rounding of u itself, at eps = 1 it dominates
+        worst = {eps: 0.0, 1.0: 0.0}
+        for _ in range(ndir):
+            df = torch.tensor(np.where(ne, rng.standard_normal(ne.shape), 0.0), device="cuda")
+            dg = torch.tensor(rng.standard_normal(len(ga)), device="cuda")
+            ad = float((gf * df).sum() + (gg * dg).sum())
+            for e in worst:
                 with torch.no_grad():
-                    jp = loss(f + eps * df, g + eps * dg).item()
-                    jm = loss(f - eps * df, g - eps * dg).item()
-                    worst["rtol"] = max(worst["rtol"], abs((jp - jm) / (2 * eps) - ad) / abs(ad))
-                    jp = loss_fixed(f + eps * df, g + eps * dg)
-                    jm = loss_fixed(f - eps * df, g - eps * dg)
-                    worst["fixed"] = max(worst["fixed"], abs((jp - jm) / (2 * eps) - ad) / abs(ad))
-        finally:
-            fixed.close()
+                    jp = loss(f + e * df, g + e * dg).item()
+                    jm = loss(f - e * df, g - e * dg).item()
+                worst[e] = max(worst[e], abs((jp - jm) / (2 * e) - ad) / abs(ad))
         return {"workload": f"star {n}x{n}, (a,b,c)=(1,0.3,1), loss 0.5||u-u_obs||^2, u_obs = exact cell "
                             "averages + N(0,1e-3^2) (seed 5), FP64 solves to rel. residual 1e-13",
                 "value": int(s.info.n_cells) / (ms / 1000.0), "unit": "unknowns/s (forward + adjoint solve)",
                 "ms_forward_and_gradient": ms, "fd_directions": ndir, "fd_eps": eps,
-                "fd_max_rel_diff": worst["rtol"],
-                "fd_max_rel_diff_fixed_cycles": worst["fixed"],
-                "fd_note": "fd_max_rel_diff: every solve to rel. residual 1e-13 (its stopping point moves "
-                           "with the data); fixed_cycles: every finite-difference solve runs the base "
-                           "solve's cycle count + 2"}
+                "fd_max_rel_diff": worst[eps], "fd_max_rel_diff_eps_1": worst[1.0],
+                "fd_note": "the loss is quadratic in (f, g): central differences are exact at any step, "
+                           "so the difference at eps 1e-6 is rounding (the change of u is ~1e-13, the "
+                           "rounding of u ~1e-16); at eps 1 it measures the adjoint's own accuracy"}
     finally:
         s.close()
 
