@@ -9,7 +9,8 @@ solve, outer FP64 residual) from the resident right-hand side to ||r - L u|| <= 
 
 value:  mixed form (FP32 cycles in FP64 refinement), inputs resident in HBM, CUDA events.
 e2e:    the same through the C ABI with pinned host buffers (ccm_solve_host): the kernels read f,
-        g and the initial guess from host memory and write u back, inside the timing.
+        g and the initial guess from host memory and write the solution's non-empty cells back,
+        inside the timing.
 fp64:   the plain FP64 form, same workload and tolerance.
 roofline: the dominant kernel class, timed live with CUDA events during the timed steps;
         algorithmic bytes per unit as in the method's byte model (12 B per regular cell per
@@ -612,8 +613,8 @@ def main():
     _, _, prof_vc = timed_solves(solver, 1, P.binding.CCM_PROF_VCYCLE)
 
     # e2e: host buffers through the C ABI (ccm_solve_host): the packing kernels read f, g and
-    # the initial guess from pinned host memory and write u back over the host link, inside
-    # the timing
+    # the initial guess from pinned host memory and write the non-empty cells of u back over
+    # the host link, inside the timing (the buffer is zeroed before each step)
     fh = torch.tensor(fa, dtype=torch.float64).pin_memory()
     gh = torch.tensor(ga, dtype=torch.float64).pin_memory()
     uh = torch.zeros_like(fh).pin_memory()
@@ -762,7 +763,7 @@ def main():
             "many_geometries": geometries,
             "autotuned": tuned,
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(2 * ncell * 8 + gh.numel() * 8),
-                    "d2h_bytes_per_step": int(uh.numel() * 8), "ms_per_step": float(np.mean(e2e)),
+                    "d2h_bytes_per_step": int(ncell * 8), "ms_per_step": float(np.mean(e2e)),
                     "api": "ccm_solve_host, pinned host buffers read and written by the kernels",
                     "max_error_vs_exact": e2e_err},
             "gpu_launches": int(launches), "roofline": roof, "cpu_baseline": cpu, "clocks": clk}

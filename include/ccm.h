@@ -284,7 +284,9 @@ int ccm_solve(ccm_handle* h, const double* f, const double* g, double* u, int nr
  * [nrhs][ny][nx] (in: initial guess, out: solution) in host memory, same layouts.  Pinned host
  * memory (cudaHostAlloc, cudaHostRegister, a pinned torch tensor) is read and written by the
  * packing kernels directly over the host link, with no staging copy: only the non-empty
- * cells of f and u are read, every cell of u is written.  Pageable memory is accessed the
+ * cells of f and u are read and only the non-empty cells of u are written (the cells outside
+ * the domain hold no unknown and keep the values the caller's u had there; ccm_solve sets
+ * them to 0).  Pageable memory is accessed the
  * same way where the device reads pageable memory coherently (Grace systems), else through
  * device staging buffers and copies.  Device pointers are accepted too.  Returns after u
  * is complete on the host (the stream is synchronised).  Errors as ccm_solve, plus

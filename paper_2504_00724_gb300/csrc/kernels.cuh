@@ -943,14 +943,16 @@ __global__ void k_pack(int nx, int ny, int pitch, const uint8_t* __restrict__ cl
   if (cls[p] != 0) dst[p] = (TD)(scale * (double)src[(long)j * nx + i]);
 }
 
-// user layout <- padded (0 for empty cells), scaled
-template <typename TS>
+// user layout <- padded, scaled; the empty cells of dst are set to 0, or with KEEP left as
+// they are (a destination across the host link gets only the cells that hold unknowns)
+template <typename TS, bool KEEP = false>
 __global__ void k_unpack(int nx, int ny, int pitch, const uint8_t* __restrict__ cls, const TS* __restrict__ src,
                          double* __restrict__ dst, double scale) {
   int i = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y;
   if (i >= nx) return;
   long p = (long)(j + 2) * pitch + (i + 2);
-  dst[(long)j * nx + i] = cls[p] != 0 ? scale * (double)src[p] : 0.0;
+  if (cls[p] != 0) dst[(long)j * nx + i] = scale * (double)src[p];
+  else if (!KEEP) dst[(long)j * nx + i] = 0.0;
 }
 
 // r_hat -= nb g on the rows that own a boundary segment

@@ -756,16 +756,6 @@ void fmg(ccm_handle* H, cudaStream_t s) {
   for (int m = M - 1; m >= 0; --m) vcycle<T>(H, m, s, true);
 }
 
-int read_norm(ccm_handle* H, const uint8_t* cls, long n, const double* x, cudaStream_t s, double& out) {
-  CCM_CUDA(cudaMemsetAsync(H->dnorm, 0, sizeof(unsigned long long), s));
-  KL(launch_k(dev::k_absmax<double>, std::min(ceil_div(n, 256), 1216), 256, 0, s, n, cls, x, H->dnorm, 0L));
-  CCM_CUDA(cudaMemcpyAsync(H->hnorm, H->dnorm, sizeof(unsigned long long), cudaMemcpyDeviceToHost, s));
-  CCM_CUDA(cudaStreamSynchronize(s));
-  unsigned long long bits = *H->hnorm;
-  std::memcpy(&out, &bits, sizeof(double));
-  return CCM_OK;
-}
-
 // the regular cells' part of the outer residual runs in float-float arithmetic (about 48
 // bits: good for relative residuals down to about 1e-11) when the tolerance allows, else in
 // FP64
@@ -1828,9 +1818,11 @@ static void initial_residual(ccm_handle* h, const double* U0, cudaStream_t s) {
               (const double*)L.t64, h->dnorm, 0L));
 }
 
-extern "C" {
+namespace {
 
-int ccm_solve(ccm_handle* h, const double* f, const double* g, double* u, int nrhs, void* stream, ccm_stats* st) {
+// ccm_solve; keep_empty: the empty cells of u keep the values they had (ccm_solve_host)
+int solve_impl(ccm_handle* h, const double* f, const double* g, double* u, int nrhs, void* stream, ccm_stats* st,
+               bool keep_empty) {
   if (!h || !f || !u || nrhs < 1) return CCM_EINVAL;
   cudaStream_t s = (cudaStream_t)stream;
   DevLevel& L = h->L[0];
@@ -1906,8 +1898,12 @@ int ccm_solve(ccm_handle* h, const double* f, const double* g, double* u, int nr
     if (result == CCM_ETIMEOUT) {
     } else if (!std::isfinite(wr)) result = CCM_ENOTFINITE;
     else if (wr > h->par.rtol && result == CCM_OK) result = CCM_ENOCONV;
-    for (int b = 0; b < nb; ++b)
-      KL(dev::k_unpack<double><<<pg, 128, 0, s>>>(L.nx, L.ny, L.pitch, L.cls, U0 + b * np, u + (k0 + b) * nu, 1.0));
+    for (int b = 0; b < nb; ++b) {
+      if (keep_empty)
+        KL(dev::k_unpack<double, true><<<pg, 128, 0, s>>>(L.nx, L.ny, L.pitch, L.cls, U0 + b * np, u + (k0 + b) * nu, 1.0));
+      else
+        KL(dev::k_unpack<double><<<pg, 128, 0, s>>>(L.nx, L.ny, L.pitch, L.cls, U0 + b * np, u + (k0 + b) * nu, 1.0));
+    }
     local.iterations = it;
     local.rel_residual = wr;
     if (st) *st = local;
@@ -1922,6 +1918,14 @@ int ccm_solve(ccm_handle* h, const double* f, const double* g, double* u, int nr
   h->nb = 1;
   CCM_CUDA(cudaGetLastError());
   return result;
+}
+
+}  // namespace
+
+extern "C" {
+
+int ccm_solve(ccm_handle* h, const double* f, const double* g, double* u, int nrhs, void* stream, ccm_stats* st) {
+  return solve_impl(h, f, g, u, nrhs, stream, st, false);
 }
 
 }  // extern "C"
@@ -2260,7 +2264,7 @@ int ccm_solve_host(ccm_handle* h, const double* f, const double* g, double* u, i
   if (!rc) rc = host_view(g, (size_t)h->info.n_segments * nrhs * sizeof(double), true, s, vg);
   if (!rc) rc = host_view(u, cells * sizeof(double), true, s, vu);
   if (!rc) {
-    rc = ccm_solve(h, (const double*)vf.dev, (const double*)vg.dev, (double*)vu.dev, nrhs, stream, st);
+    rc = solve_impl(h, (const double*)vf.dev, (const double*)vg.dev, (double*)vu.dev, nrhs, stream, st, true);
     // the solution in u (also after CCM_ENOCONV, where u holds the last iterate)
     const int rb = stage_back(vu, s);
     if (rc == CCM_OK || rc == CCM_ENOCONV) rc = rc ? rc : rb;

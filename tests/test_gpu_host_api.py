@@ -1,6 +1,7 @@
 """ccm_solve_host: the solve with host buffers (pinned: read and written by the kernels over the
 host link; pageable: the device's own access or staging copies) gives the device-buffer
-solve's result bit for bit, for one and for several right-hand sides."""
+solve's result bit for bit on the non-empty cells, for one and for several right-hand sides,
+and leaves the cells outside the domain as the caller's buffer held them."""
 import numpy as np
 import pytest
 
@@ -46,16 +47,23 @@ def test_pageable_host_buffers_and_several_rhs(setup):
     assert np.array_equal(U, u_dev.cpu().numpy())
 
 
-def test_host_solve_zeroes_cells_outside_the_domain(setup):
-    """The cells outside the domain are written as zero whatever the caller's buffer held there;
-    the non-empty cells hold the solution."""
+def test_host_solve_keeps_cells_outside_the_domain(setup):
+    """Only the non-empty cells cross the host link back: the cells outside the domain keep
+    whatever the caller's buffer held there, the non-empty cells hold the device solve's
+    solution bit for bit (pinned and pageable buffers)."""
     s, fa, ga = setup
     ne = s.cell_map()[0] != 0
+    assert (~ne).any()
     u_dev, _ = s.solve(torch.tensor(fa, device="cuda"), torch.tensor(ga, device="cuda"))
+    ud = u_dev.cpu().numpy()
     fh = torch.tensor(fa).pin_memory()
     gh = torch.tensor(ga).pin_memory()
     uh = torch.full(fh.shape, 7.0, dtype=torch.float64).pin_memory()
     uh[torch.from_numpy(ne)] = 0.0
     s.solve_host(fh, gh, uh)
-    assert torch.equal(uh, u_dev.cpu())
-    assert np.all(uh.numpy()[~ne] == 0.0)
+    assert np.all(uh.numpy()[~ne] == 7.0)
+    assert np.array_equal(uh.numpy()[ne], ud[ne])
+    U = np.where(ne, 0.0, -3.0)
+    s.solve_host(np.array(fa), np.array(ga), U)
+    assert np.all(U[~ne] == -3.0)
+    assert np.array_equal(U[ne], ud[ne])
