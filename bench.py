@@ -59,10 +59,9 @@ FP64_FMA_PER_CLK_SM = 2          # FP64 FMA issue rate per SM (4 flop / clk / SM
 # A figure is reported only while the device sources hash to the value it was taken on.
 KERNEL_SOURCES = ("kernels.cuh", "smooth.cuh", "outer.cuh")
 NCU_TRAFFIC = {        # class name -> (source hash, bytes per launch)
-    "fp32 sweep, level 0 (SMO-1 regular cells + SMO-2 blocks)": ("7cbf78d24ee48593", 69.37e6),
-    "fp32 residual + restriction, level 0": ("7cbf78d24ee48593", 76.74e6),
-    # captured on the star 2048^2 (672 tiles, 24.14 MB) and scaled to the 2550 tiles of 4096^2
-    "outer residual, level 0 (regular cells, float-float)": ("7cbf78d24ee48593", 91.61e6),
+    "fp32 sweep, level 0 (SMO-1 regular cells + SMO-2 blocks)": ("e2895f91a4acbeb8", 69.78e6),
+    "fp32 residual + restriction, level 0": ("e2895f91a4acbeb8", 76.79e6),
+    "outer residual, level 0 (regular cells, float-float)": ("e2895f91a4acbeb8", 95.65e6),
 }
 
 
