@@ -28,6 +28,7 @@ struct SmoothArgs {
   int nbi;             // block items (= a.nblk)
   int nitems;          // nbi + a.ntiles
   uint32_t stage;      // bytes per stage (multiple of 128)
+  int max_ext;         // most extended rows of a block (the per-row scratch after the stages)
 };
 
 // hint: bring the line holding p into this SM's L1 (static data only)
@@ -100,16 +101,18 @@ __device__ __forceinline__ void smooth_issue(const SmoothArgs<T>& A, const CUten
   }
 }
 
-// SMO-2 residuals of block b's extended rows from u_old (u_old + P uc with PRO) into sres;
-// the block's core start, core size and extended size come back.  CG: u_old is read through
-// L2 only (iterates that other CTAs of the same launch wrote).
+// SMO-2 residuals of block b's extended rows from u_old (u_old + P uc with PRO) into sres,
+// and each row's cell and old value (an irregular cell: no coarse correction) into scell and
+// sold for the update of the core rows; the block's core start, core size and extended size
+// come back, the core's first row at extended row cs - es.  CG: u_old is read through L2
+// only (iterates that other CTAs of the same launch wrote).
 template <typename T, bool PRO, bool CG>
 __device__ __forceinline__ void block_residuals(const SweepArgs<T>& a, int b, const T* __restrict__ u_old,
                                                 const T* __restrict__ rhs, const T* __restrict__ ucs, T* sres,
-                                                int& cs, int& nc, int& ne) {
+                                                T* sold, int* scell, int& cs, int& nc, int& ne, int& es) {
   cs = a.blk[4 * b];
   nc = a.blk[4 * b + 1] - cs;
-  const int es = a.blk[4 * b + 2];
+  es = a.blk[4 * b + 2];
   ne = a.blk[4 * b + 3] - es;
   for (int e = threadIdx.x; e < ne; e += blockDim.x) {
     const int row = es + e;
@@ -124,15 +127,19 @@ __device__ __forceinline__ void block_residuals(const SweepArgs<T>& a, int b, co
       }
       acc += a.val[(long)m * a.n2 + row] * v;
     }
-    sres[e] = rhs[a.cell[row]] - acc;
+    const int q = a.cell[row];
+    sres[e] = rhs[q] - acc;
+    sold[e] = CG ? __ldcg(u_old + q) : u_old[q];
+    scell[e] = q;
   }
 }
 
 // u_new = u_old + inv(L22[ext, ext]) sres on the block's core cells; As = the staged rows
-// [ne][nc] of the inverse, columns over lanes, extended rows over warps
-template <typename T, bool CG>
-__device__ __forceinline__ void block_apply(const SweepArgs<T>& a, const T* As, const T* sres, int cs, int nc, int ne,
-                                            const T* __restrict__ u_old, T* __restrict__ u_new, T (*part)[32]) {
+// [ne][nc] of the inverse, columns over lanes, extended rows over warps; the core cells and
+// their old values from scell and sold (no global round trip before the stores)
+template <typename T>
+__device__ __forceinline__ void block_apply(const T* As, const T* sres, const T* sold, const int* scell, int c0,
+                                            int nc, int ne, T* __restrict__ u_new, T (*part)[32]) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   for (int cb = 0; cb < nc; cb += 32) {
     const int c = cb + lane;
@@ -145,8 +152,7 @@ __device__ __forceinline__ void block_apply(const SweepArgs<T>& a, const T* As, 
       T tot = 0;
 #pragma unroll
       for (int w = 0; w < 8; ++w) tot += part[w][lane];
-      const long q = a.cell[cs + c];
-      u_new[q] = (CG ? __ldcg(u_old + q) : u_old[q]) + tot;
+      u_new[scell[c0 + c]] = sold[c0 + c] + tot;
     }
     __syncthreads();
   }
@@ -315,7 +321,11 @@ __global__ void __launch_bounds__(256, 3) k_smooth(const __grid_constant__ CUten
   T* __restrict__ u_new = a.u_new + bo;
   const T* __restrict__ rhs = a.r + bo;
   const T* __restrict__ ucs = PRO ? a.uc + (long)blockIdx.y * a.bsc : nullptr;
+  // per extended row of a block item: residual, old value, cell (three slots of max_ext)
+  const uint32_t slot = (uint32_t)(((long)A.max_ext * sizeof(T) + 15) & ~15L);
   T* sres = reinterpret_cast<T*>(smem_raw + 2 * A.stage);
+  T* sold = reinterpret_cast<T*>(smem_raw + 2 * A.stage + slot);
+  int* scell = reinterpret_cast<int*>(smem_raw + 2 * A.stage + 2 * slot);
   const int G = gridDim.x;
   const int K = (A.nitems - (int)blockIdx.x + G - 1) / G;   // items of this CTA (>= 1)
   if (threadIdx.x == 0) {
@@ -331,8 +341,8 @@ __global__ void __launch_bounds__(256, 3) k_smooth(const __grid_constant__ CUten
     const int item = blockIdx.x + k * G;
     const int sb = k & 1;
     const uint32_t parity = (k >> 1) & 1;
-    int cs = 0, nc = 0, ne = 0;
-    if (item < A.nbi) block_residuals<T, PRO, false>(a, item, u_old, rhs, ucs, sres, cs, nc, ne);
+    int cs = 0, nc = 0, ne = 0, es = 0;
+    if (item < A.nbi) block_residuals<T, PRO, false>(a, item, u_old, rhs, ucs, sres, sold, scell, cs, nc, ne, es);
     const bool ok = __syncthreads_and(wait_parity(&bar[sb], parity));
     if (!ok) {
       // this copy and the other stage's (if one was issued) must land before the CTA leaves
@@ -342,8 +352,8 @@ __global__ void __launch_bounds__(256, 3) k_smooth(const __grid_constant__ CUten
       return;
     }
     if (item < A.nbi) {
-      block_apply<T, false>(a, reinterpret_cast<const T*>(smem_raw + sb * A.stage), sres, cs, nc, ne, u_old, u_new,
-                            part);
+      block_apply<T>(reinterpret_cast<const T*>(smem_raw + sb * A.stage), sres, sold, scell, cs - es, nc, ne, u_new,
+                     part);
     } else {
       const int t = item - A.nbi;
       tile_sweep<T, CROSS, PRO>(a, smem_raw + sb * A.stage, a.tiles[2 * t] * JX, a.tiles[2 * t + 1] * JY, u_new);

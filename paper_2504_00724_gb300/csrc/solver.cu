@@ -380,6 +380,7 @@ void sweep_persistent(ccm_handle* H, DevLevel& L, cudaStream_t s, DevLevel* C) {
   A.nbi = L.nblk;
   A.nitems = L.nblk + L.ntiles64;
   A.stage = L.smooth_stage[k];
+  A.max_ext = std::max(1, L.max_ext);
   const bool l0 = &L == &H->L[0];
   ProfScope ps(H, !l0 ? 0 : C ? (sizeof(T) == 4 ? CCM_PROF_PROLONG_SMO1_FP32 : 0)
                               : (sizeof(T) == 4 ? CCM_PROF_SMO1_FP32 : CCM_PROF_SMO1_FP64), s);
@@ -879,7 +880,8 @@ void configure_sweep(ccm_handle* h, DevLevel& d, int nsm) {
     const size_t tile = k == 0 ? dev::TileStage<double>::bytes(true) : dev::TileStage<float>::bytes(true);
     const size_t blk = ((size_t)d.max_ext * d.max_core * es + 15) & ~(size_t)15;
     const size_t stage = (std::max(tile, blk) + 127) & ~(size_t)127;
-    const size_t smem = 2 * stage + (((size_t)std::max(1, d.max_ext) * es + 15) & ~(size_t)15);
+    // two stages, then per extended row of a block: its residual, old value and cell
+    const size_t smem = 2 * stage + 3 * (((size_t)std::max(1, d.max_ext) * es + 15) & ~(size_t)15);
     if (smem > 200 * 1024) continue;
     int occ = 0;
     if (k == 0) {
