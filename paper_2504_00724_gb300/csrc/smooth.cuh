@@ -297,11 +297,10 @@ __global__ void __launch_bounds__(256, 3) k_smooth(const __grid_constant__ CUten
   __shared__ __align__(8) uint64_t bar[2];
   __shared__ T part[8][32];
   const SweepArgs<T>& a = A.a;
-  // While the previous launch drains: when the first item is an SMO-2 block, pull its static
-  // fitted-row data (columns, coefficients, cells, parents) into L1, so that the residual
-  // gathers after the wait need one round trip to the iterate instead of two
-  if ((int)blockIdx.x < A.nbi) {
-    const int b = blockIdx.x;
+  // While the previous launch drains: pull the static fitted-row data (columns, coefficients,
+  // cells, parents) of this CTA's SMO-2 block items into L1, so that each block's residual
+  // gathers need one round trip to the iterate instead of two
+  for (int b = blockIdx.x; b < A.nbi; b += gridDim.x) {
     const int es = a.blk[4 * b + 2], ne = a.blk[4 * b + 3] - es;
     for (int e = threadIdx.x; e < ne; e += blockDim.x) {
       const int row = es + e;
@@ -400,6 +399,10 @@ struct RestrictArgs {
   int* err;
   uint32_t stage;
   long bs, bsc;        // batch strides (elements) of the fine and the coarse level arrays
+  int nrr;             // the tiles' irregular rows in tile order: (cell, position) pairs, and
+  const int32_t* rq;   // the rows' columns and coefficients [W][nrr]
+  const int32_t* rq_col;
+  const T* rq_val;
 };
 
 template <typename T>
@@ -415,6 +418,20 @@ struct RestrictStage {
   static constexpr uint32_t tx = u_bytes + 2 * r_bytes + c_bytes;
 };
 
+// the static data of restriction tile t's irregular rows (cell and position pairs, columns
+// and coefficients, contiguous in tile order) into L1: k0, k1 = the tile's row range
+template <typename T>
+__device__ __forceinline__ void prefetch_tile_rows(const RestrictArgs<T>& A, int k0, int k1) {
+  for (int q = k0 + 16 * (int)threadIdx.x; q < k1; q += 16 * (int)blockDim.x) {
+    prefetch_l1(A.rq + 2 * (long)q);
+#pragma unroll 15
+    for (int m = 0; m < A.W; ++m) {
+      prefetch_l1(A.rq_col + (long)m * A.nrr + q);
+      prefetch_l1(A.rq_val + (long)m * A.nrr + q);
+    }
+  }
+}
+
 template <typename T, bool CROSS>
 __global__ void __launch_bounds__(256, 3) k_restrict_p(const __grid_constant__ CUtensorMap tin,
                                                        const __grid_constant__ CUtensorMap tr,
@@ -424,9 +441,12 @@ __global__ void __launch_bounds__(256, 3) k_restrict_p(const __grid_constant__ C
   extern __shared__ __align__(128) unsigned char smem_raw[];
   __shared__ T res[JY][JX];      // residual of every fine cell of the tile (0 on empty cells)
   __shared__ __align__(8) uint64_t bar[2];
-  pdl_enter();
   const int G = gridDim.x;
   const int K = (A.ntiles - (int)blockIdx.x + G - 1) / G;
+  // the first tile's row range and rows while the previous launch drains
+  int n0 = A.rr_off[blockIdx.x], n1 = A.rr_off[blockIdx.x + 1];
+  prefetch_tile_rows(A, n0, n1);
+  pdl_enter();
   if (threadIdx.x == 0) {
     mbar_init(&bar[0], 1);
     mbar_init(&bar[1], 1);
@@ -457,13 +477,18 @@ __global__ void __launch_bounds__(256, 3) k_restrict_p(const __grid_constant__ C
     const int sb = k & 1;
     const uint32_t parity = (k >> 1) & 1;
     const int cx0 = A.tiles[2 * t] * JX, cy0 = A.tiles[2 * t + 1] * JY;
-    const int k0 = A.rr_off[t], k1 = A.rr_off[t + 1];
+    const int k0 = n0, k1 = n1;
+    // the next tile's row range: loaded now, used after this tile's stencil
+    if (k + 1 < K) {
+      n0 = A.rr_off[t + G];
+      n1 = A.rr_off[t + G + 1];
+    }
     for (int q = k0 + (int)threadIdx.x; q < k1; q += blockDim.x) {
-      const int row = A.rr[2 * q], loc = A.rr[2 * q + 1];
+      const int cell = A.rq[2 * q], loc = A.rq[2 * q + 1];
       T acc = 0;
 #pragma unroll 15
-      for (int m = 0; m < A.W; ++m) acc += A.val[(long)m * A.n2 + row] * uf[A.col[(long)m * A.n2 + row]];
-      res[loc >> 6][loc & 63] = rf[A.irr_cell[row]] - acc;
+      for (int m = 0; m < A.W; ++m) acc += A.rq_val[(long)m * A.nrr + q] * uf[A.rq_col[(long)m * A.nrr + q]];
+      res[loc >> 6][loc & 63] = rf[cell] - acc;
     }
     // class bytes of this thread's two coarse cells (0 outside the coarse level)
     uint8_t cc[2];
@@ -567,6 +592,7 @@ __global__ void __launch_bounds__(256, 3) k_restrict_p(const __grid_constant__ C
         }
       }
     }
+    if (k + 1 < K) prefetch_tile_rows(A, n0, n1);
     __syncthreads();
     // 32 x 16 coarse cells, two per thread
 #pragma unroll

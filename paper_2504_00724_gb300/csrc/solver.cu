@@ -58,6 +58,13 @@ struct DevLevel {
   int restrict_cap[2] = {0, 0};
   int32_t* rr_off = nullptr;    // per restriction tile: its irregular rows [rr_off[t], rr_off[t + 1])
   int32_t* rr = nullptr;        // (row, y * 64 + x in the tile) pairs
+  // the same rows packed in restriction-tile order for k_restrict_p: (cell, y * 64 + x) pairs
+  // and the fitted rows' columns and coefficients [W][nrr], so that one tile's rows are
+  // contiguous (coalesced, and prefetched while the tile before is restricted)
+  int nrr = 0;
+  int32_t *rq = nullptr, *rq_col = nullptr;
+  double* rq_val64 = nullptr;
+  float* rq_val32 = nullptr;
   uint8_t* cls = nullptr;
   double* vol64 = nullptr;
   float* vol32 = nullptr;
@@ -104,6 +111,9 @@ template <> float* Res<float>(DevLevel& L) { return L.res32; }
 template <typename T> const T* Ell(const DevLevel& L);
 template <> const double* Ell<double>(const DevLevel& L) { return L.ell64; }
 template <> const float* Ell<float>(const DevLevel& L) { return L.ell32; }
+template <typename T> const T* RqVal(const DevLevel& L);
+template <> const double* RqVal<double>(const DevLevel& L) { return L.rq_val64; }
+template <> const float* RqVal<float>(const DevLevel& L) { return L.rq_val32; }
 template <typename T> const T* Inv(const DevLevel& L);
 template <> const double* Inv<double>(const DevLevel& L) { return L.inv64; }
 template <> const float* Inv<float>(const DevLevel& L) { return L.inv32; }
@@ -545,6 +555,10 @@ void restrict_to(ccm_handle* H, DevLevel& F, DevLevel& C, cudaStream_t s) {
     A.pitchf = F.pitch;
     A.rr_off = F.rr_off;
     A.rr = F.rr;
+    A.nrr = F.nrr;
+    A.rq = F.rq;
+    A.rq_col = F.rq_col;
+    A.rq_val = RqVal<T>(F);
     A.n2 = F.n2;
     A.W = F.W;
     A.irr_cell = F.irr_cell;
@@ -1080,7 +1094,27 @@ int upload_hierarchy(ccm_handle* h) {
         off.push_back((int32_t)(rr.size() / 2));
       }
       if (d.ntiles64r) d.rr_off = A.upload(off);
-      if (!rr.empty()) d.rr = A.upload(rr);
+      if (!rr.empty()) {
+        d.rr = A.upload(rr);
+        const int nr = (int)rr.size() / 2, W = hf.W;
+        std::vector<int32_t> rq(2 * (size_t)nr), qc((size_t)W * nr);
+        std::vector<double> qv((size_t)W * nr);
+        for (int q = 0; q < nr; ++q) {
+          const int r = rr[2 * q];
+          rq[2 * q] = hf.irr_cell[r];
+          rq[2 * q + 1] = rr[2 * q + 1];
+          for (int k = 0; k < W; ++k) {
+            qc[(size_t)k * nr + q] = hf.ell_col[(size_t)k * hf.n2 + r];
+            qv[(size_t)k * nr + q] = hf.ell_val[(size_t)k * hf.n2 + r];
+          }
+        }
+        std::vector<float> qv32(qv.begin(), qv.end());
+        d.nrr = nr;
+        d.rq = A.upload(rq);
+        d.rq_col = A.upload(qc);
+        d.rq_val64 = A.upload(qv);
+        d.rq_val32 = A.upload(qv32);
+      }
       // the first post-smoothing sweep reads u + P uc through two more boxes
       DevLevel& c = h->L[m + 1];
       d.tma_pro = true;
