@@ -170,20 +170,24 @@ __device__ __forceinline__ void tile_sweep(const SweepArgs<T>& a, unsigned char*
   const T* rt = reinterpret_cast<const T*>(st + S::r_off);
   const uint8_t* ct = st + S::c_off;
   if (PRO) {
-    // staged cell (y, x) has its parent at (y / 2, x / 2 + 1) of the coarse box; four
-    // cells (one 32-bit word of class bytes, two parents) per step
+    // staged cell (y, x) has its parent at (y / 2, x / 2 + 1) of the coarse box; four cells
+    // (one 32-bit word of class bytes, two parents, two aligned pairs of the tile) per step,
+    // the tile's 36 x 17 quads spread over all threads
+    using P2 = typename Pair<T>::type;
     const T* uct = reinterpret_cast<const T*>(st + S::uc_off);
-    for (int y = warp; y < HY; y += 8)
-      if (lane < HX / 4) {
-        const int x0 = 4 * lane;
-        const uint32_t c4 = *reinterpret_cast<const uint32_t*>(ct + y * CLX + x0);
-        const T p0 = uct[(y >> 1) * UCX + 2 * lane + 1], p1 = uct[(y >> 1) * UCX + 2 * lane + 2];
-        T* tr4 = tile + y * HX + x0;
-        if ((c4 & 0xffu) == 1u) tr4[0] += p0;
-        if (((c4 >> 8) & 0xffu) == 1u) tr4[1] += p0;
-        if (((c4 >> 16) & 0xffu) == 1u) tr4[2] += p1;
-        if ((c4 >> 24) == 1u) tr4[3] += p1;
-      }
+    for (int q = threadIdx.x; q < HY * (HX / 4); q += blockDim.x) {
+      const int y = q / (HX / 4), xq = q - y * (HX / 4), x0 = 4 * xq;
+      const uint32_t c4 = *reinterpret_cast<const uint32_t*>(ct + y * CLX + x0);
+      const T p0 = uct[(y >> 1) * UCX + 2 * xq + 1], p1 = uct[(y >> 1) * UCX + 2 * xq + 2];
+      P2* tr = reinterpret_cast<P2*>(tile + y * HX + x0);
+      P2 v0 = tr[0], v1 = tr[1];
+      if ((c4 & 0xffu) == 1u) v0.x += p0;
+      if (((c4 >> 8) & 0xffu) == 1u) v0.y += p0;
+      if (((c4 >> 16) & 0xffu) == 1u) v1.x += p1;
+      if ((c4 >> 24) == 1u) v1.y += p1;
+      tr[0] = v0;
+      tr[1] = v1;
+    }
     __syncthreads();
   }
   if constexpr (sizeof(T) == 8) {
