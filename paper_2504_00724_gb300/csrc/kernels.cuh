@@ -25,6 +25,13 @@ __device__ __forceinline__ void pdl_enter() {
   asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
 }
 
+// hint: bring the line holding p into this SM's L1.  Kernels use it before pdl_enter() on
+// static data (level structure, operator coefficients, tile lists), which no kernel of the
+// solve writes, so that their first dependent loads after the wait hit L1
+__device__ __forceinline__ void prefetch_l1(const void* p) {
+  asm volatile("prefetch.global.L1 [%0];" ::"l"(p));
+}
+
 template <typename T>
 struct Stencil {
   T w[25];        // [dj + 2][di + 2]
@@ -864,14 +871,19 @@ __global__ void __launch_bounds__(256) k_bottom_split(int n, const int32_t* __re
                                                       const T* __restrict__ r, T* __restrict__ u, long bs) {
   __shared__ T part[8][32];
   __shared__ T tot[32];
-  pdl_enter();
-  r += blockIdx.y * bs;       // right-hand side blockIdx.y of the batch
-  u += blockIdx.y * bs;
   const unsigned q = bottom_rank();
   const int rowblk = blockIdx.x / BOTTOM_SPLIT;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int k = rowblk * 32 + lane;
   const int c0 = (int)((long)n * q / BOTTOM_SPLIT), c1 = (int)((long)n * (q + 1) / BOTTOM_SPLIT);
+  // this CTA's part of the inverse and the cells of its columns, while the previous launch
+  // drains (a warp's 32 rows of one column are one line)
+  if (k < n)
+    for (int c = c0 + warp; c < c1; c += 8) prefetch_l1(inv + (long)c * n + k);
+  for (int c = c0 + (int)threadIdx.x * 32; c < c1; c += (int)blockDim.x * 32) prefetch_l1(cell + c);
+  pdl_enter();
+  r += blockIdx.y * bs;       // right-hand side blockIdx.y of the batch
+  u += blockIdx.y * bs;
   T acc = 0;
   if (k < n)
     for (int c = c0 + warp; c < c1; c += 8) acc += inv[(long)c * n + k] * r[cell[c]];

@@ -57,13 +57,14 @@ __global__ void __launch_bounds__(256, 3) k_resid64(const __grid_constant__ CUte
   uint8_t* ct = smem_raw + Resid64Smem::ct_off;                                   // [HY][CLX]
   double* dx = reinterpret_cast<double*>(smem_raw + Resid64Smem::dx_off);         // [HY][JX]
   __shared__ __align__(8) uint64_t bar;
+  // the tile's origin (static) and the copy barrier while the previous launch drains
+  const int cx0 = tiles[2 * blockIdx.x] * JX, cy0 = tiles[2 * blockIdx.x + 1] * JY;
+  if (threadIdx.x == 0) mbar_init(&bar, 1);
+  __syncthreads();
   pdl_enter();
   const int z = blockIdx.y;          // right-hand side of the batch
   r32 += (long)z * bs;
   norm += z;
-  const int cx0 = tiles[2 * blockIdx.x] * JX, cy0 = tiles[2 * blockIdx.x + 1] * JY;
-  if (threadIdx.x == 0) mbar_init(&bar, 1);
-  __syncthreads();
   if (threadIdx.x == 0) {
     mbar_expect_tx(&bar, Resid64Smem::tx);
     tma_load_3d(ut, &tu, &bar, cx0, cy0, z);
@@ -208,13 +209,14 @@ __global__ void __launch_bounds__(256, 3) k_resid_ff(const __grid_constant__ CUt
   const uint8_t* ct = smem_raw + Resid64Smem::ct_off;                             // [HY][CLX]
   float2* dx = reinterpret_cast<float2*>(smem_raw + Resid64Smem::dx_off);         // [HY][JX]
   __shared__ __align__(8) uint64_t bar;
+  // the tile's origin (static) and the copy barrier while the previous launch drains
+  const int cx0 = tiles[2 * blockIdx.x] * JX, cy0 = tiles[2 * blockIdx.x + 1] * JY;
+  if (threadIdx.x == 0) mbar_init(&bar, 1);
+  __syncthreads();
   pdl_enter();
   const int z = blockIdx.y;          // right-hand side of the batch
   r32 += (long)z * bs;
   norm += z;
-  const int cx0 = tiles[2 * blockIdx.x] * JX, cy0 = tiles[2 * blockIdx.x + 1] * JY;
-  if (threadIdx.x == 0) mbar_init(&bar, 1);
-  __syncthreads();
   if (threadIdx.x == 0) {
     mbar_expect_tx(&bar, Resid64Smem::tx);
     tma_load_3d(ut, &tu, &bar, cx0, cy0, z);
@@ -271,18 +273,24 @@ __global__ void __launch_bounds__(128, 8) k_rows_r32(int n2, int W, const int32_
                            const double* __restrict__ val, const double* __restrict__ u,
                            const double* __restrict__ r, float* __restrict__ r32,
                            unsigned long long* __restrict__ norm, long bs) {
+  const int row = blockIdx.x * blockDim.x + threadIdx.x;
+  // the row's cell, columns and coefficients (static) while the previous launch drains
+  const int q = row < n2 ? cell[row] : 0;
+  if (row < n2)
+    for (int k = 0; k < W; ++k) {
+      prefetch_l1(col + (long)k * n2 + row);
+      prefetch_l1(val + (long)k * n2 + row);
+    }
   pdl_enter();
   u += blockIdx.y * bs;       // right-hand side blockIdx.y of the batch
   r += blockIdx.y * bs;
   r32 += blockIdx.y * bs;
   norm += blockIdx.y;
-  const int row = blockIdx.x * blockDim.x + threadIdx.x;
   unsigned long long m = 0;
   if (row < n2) {
     double acc = 0.0;
 #pragma unroll 15
     for (int k = 0; k < W; ++k) acc += val[(long)k * n2 + row] * u[col[(long)k * n2 + row]];
-    const int q = cell[row];
     const double t = r[q] - acc;
     r32[q] = (float)t;
     m = abs_bits(t);
@@ -294,14 +302,15 @@ __global__ void __launch_bounds__(128, 8) k_rows_r32(int n2, int W, const int32_
 // u_hat += e on the non-empty cells of the 32 x 8 tiles that hold one
 __global__ void k_axpy_tiles(const int32_t* __restrict__ tiles, const uint8_t* __restrict__ cls, int nx, int ny,
                              int pitch, const float* __restrict__ e, double* __restrict__ u, long bs) {
+  // the cell and its class (static) while the previous launch drains
+  const int i = tiles[2 * blockIdx.x] * TX + threadIdx.x;
+  const int j = tiles[2 * blockIdx.x + 1] * TY + threadIdx.y;
+  const long p = (long)(j + 2) * pitch + (i + 2);
+  const bool on = i < nx && j < ny && cls[p] != 0;
   pdl_enter();
   e += blockIdx.y * bs;       // right-hand side blockIdx.y of the batch
   u += blockIdx.y * bs;
-  const int i = tiles[2 * blockIdx.x] * TX + threadIdx.x;
-  const int j = tiles[2 * blockIdx.x + 1] * TY + threadIdx.y;
-  if (i >= nx || j >= ny) return;
-  const long p = (long)(j + 2) * pitch + (i + 2);
-  if (cls[p] != 0) u[p] += (double)e[p];
+  if (on) u[p] += (double)e[p];
 }
 
 }  // namespace dev

@@ -31,10 +31,6 @@ struct SmoothArgs {
   int max_ext;         // most extended rows of a block (the per-row scratch after the stages)
 };
 
-// hint: bring the line holding p into this SM's L1 (static data only)
-__device__ __forceinline__ void prefetch_l1(const void* p) {
-  asm volatile("prefetch.global.L1 [%0];" ::"l"(p));
-}
 
 // two adjacent values of T (8 or 16 bytes, aligned)
 template <typename T> struct Pair;
@@ -316,7 +312,21 @@ __global__ void __launch_bounds__(256, 3) k_smooth(const __grid_constant__ CUten
         if (PRO && a.par) prefetch_l1(a.par + (long)m * a.n2 + row);
       }
     }
+    if (threadIdx.x == 0) prefetch_l1(a.blk_off + b);
   }
+  const int G = gridDim.x;
+  const int K = (A.nitems - (int)blockIdx.x + G - 1) / G;   // items of this CTA (>= 1)
+  // also before the wait: the copy barriers, and the origins of the first two items if they
+  // are tiles (static data: the first copies are issued right after the wait)
+  if (threadIdx.x == 0) {
+    mbar_init(&bar[0], 1);
+    mbar_init(&bar[1], 1);
+    for (int k = 0; k < 2 && k < K; ++k) {
+      const int t = (int)blockIdx.x + k * G - A.nbi;
+      if (t >= 0) prefetch_l1(a.tiles + 2 * t);
+    }
+  }
+  __syncthreads();
   pdl_enter();
   // this CTA's right-hand side of the batch (blockIdx.y)
   const long bo = (long)blockIdx.y * a.bs;
@@ -329,13 +339,6 @@ __global__ void __launch_bounds__(256, 3) k_smooth(const __grid_constant__ CUten
   T* sres = reinterpret_cast<T*>(smem_raw + 2 * A.stage);
   T* sold = reinterpret_cast<T*>(smem_raw + 2 * A.stage + slot);
   int* scell = reinterpret_cast<int*>(smem_raw + 2 * A.stage + 2 * slot);
-  const int G = gridDim.x;
-  const int K = (A.nitems - (int)blockIdx.x + G - 1) / G;   // items of this CTA (>= 1)
-  if (threadIdx.x == 0) {
-    mbar_init(&bar[0], 1);
-    mbar_init(&bar[1], 1);
-  }
-  __syncthreads();
   if (threadIdx.x == 0) {
     smooth_issue<T, PRO>(A, &tin, &tr, &tcls, &tuc, blockIdx.x, smem_raw, &bar[0]);
     if (K > 1) smooth_issue<T, PRO>(A, &tin, &tr, &tcls, &tuc, blockIdx.x + G, smem_raw + A.stage, &bar[1]);
@@ -344,8 +347,14 @@ __global__ void __launch_bounds__(256, 3) k_smooth(const __grid_constant__ CUten
     const int item = blockIdx.x + k * G;
     const int sb = k & 1;
     const uint32_t parity = (k >> 1) & 1;
-    int cs = 0, nc = 0, ne = 0, es = 0;
-    if (item < A.nbi) block_residuals<T, PRO, false>(a, item, u_old, rhs, ucs, sres, sold, scell, cs, nc, ne, es);
+    int cs = 0, nc = 0, ne = 0, es = 0, cx0 = 0, cy0 = 0;
+    if (item < A.nbi) {
+      block_residuals<T, PRO, false>(a, item, u_old, rhs, ucs, sres, sold, scell, cs, nc, ne, es);
+    } else {
+      const int t = item - A.nbi;       // the tile's origin, read before the wait
+      cx0 = a.tiles[2 * t] * JX;
+      cy0 = a.tiles[2 * t + 1] * JY;
+    }
     const bool ok = __syncthreads_and(wait_parity(&bar[sb], parity));
     if (!ok) {
       // this copy and the other stage's (if one was issued) must land before the CTA leaves
@@ -358,8 +367,7 @@ __global__ void __launch_bounds__(256, 3) k_smooth(const __grid_constant__ CUten
       block_apply<T>(reinterpret_cast<const T*>(smem_raw + sb * A.stage), sres, sold, scell, cs - es, nc, ne, u_new,
                      part);
     } else {
-      const int t = item - A.nbi;
-      tile_sweep<T, CROSS, PRO>(a, smem_raw + sb * A.stage, a.tiles[2 * t] * JX, a.tiles[2 * t + 1] * JY, u_new);
+      tile_sweep<T, CROSS, PRO>(a, smem_raw + sb * A.stage, cx0, cy0, u_new);
     }
     __syncthreads();      // stage sb is free
     if (threadIdx.x == 0 && k + 2 < K) {
@@ -450,12 +458,16 @@ __global__ void __launch_bounds__(256, 3) k_restrict_p(const __grid_constant__ C
   // the first tile's row range and rows while the previous launch drains
   int n0 = A.rr_off[blockIdx.x], n1 = A.rr_off[blockIdx.x + 1];
   prefetch_tile_rows(A, n0, n1);
-  pdl_enter();
+  // the copy barriers and the first two tiles' origins (for the copies issued right after
+  // the wait) too
   if (threadIdx.x == 0) {
     mbar_init(&bar[0], 1);
     mbar_init(&bar[1], 1);
+    prefetch_l1(A.tiles + 2 * blockIdx.x);
+    if (K > 1) prefetch_l1(A.tiles + 2 * (blockIdx.x + G));
   }
   __syncthreads();
+  pdl_enter();
   // this CTA's right-hand side of the batch (blockIdx.y)
   const int z = blockIdx.y;
   const T* __restrict__ uf = A.u + (long)z * A.bs;
