@@ -57,19 +57,22 @@ __global__ void __launch_bounds__(256, 3) k_resid64(const __grid_constant__ CUte
   uint8_t* ct = smem_raw + Resid64Smem::ct_off;                                   // [HY][CLX]
   double* dx = reinterpret_cast<double*>(smem_raw + Resid64Smem::dx_off);         // [HY][JX]
   __shared__ __align__(8) uint64_t bar;
-  // the tile's origin (static) and the copy barrier while the previous launch drains
+  // while the previous launch drains: the tile's origin, the copy barrier and the class
+  // bytes (static), with the byte count of the whole copy
   const int cx0 = tiles[2 * blockIdx.x] * JX, cy0 = tiles[2 * blockIdx.x + 1] * JY;
-  if (threadIdx.x == 0) mbar_init(&bar, 1);
+  if (threadIdx.x == 0) {
+    mbar_init(&bar, 1);
+    mbar_expect_tx(&bar, Resid64Smem::tx);
+    tma_load_2d(smem_raw + Resid64Smem::ct_off, &tcls, &bar, cx0, cy0);
+  }
   __syncthreads();
   pdl_enter();
   const int z = blockIdx.y;          // right-hand side of the batch
   r32 += (long)z * bs;
   norm += z;
   if (threadIdx.x == 0) {
-    mbar_expect_tx(&bar, Resid64Smem::tx);
     tma_load_3d(ut, &tu, &bar, cx0, cy0, z);
     tma_load_3d(rt, &tr, &bar, cx0, cy0 + 2, z);
-    tma_load_2d(ct, &tcls, &bar, cx0, cy0);
   }
   const bool ok = __syncthreads_and(tile_wait(&bar, err));
   if (!ok) return;
@@ -209,19 +212,22 @@ __global__ void __launch_bounds__(256, 3) k_resid_ff(const __grid_constant__ CUt
   const uint8_t* ct = smem_raw + Resid64Smem::ct_off;                             // [HY][CLX]
   float2* dx = reinterpret_cast<float2*>(smem_raw + Resid64Smem::dx_off);         // [HY][JX]
   __shared__ __align__(8) uint64_t bar;
-  // the tile's origin (static) and the copy barrier while the previous launch drains
+  // while the previous launch drains: the tile's origin, the copy barrier and the class
+  // bytes (static), with the byte count of the whole copy
   const int cx0 = tiles[2 * blockIdx.x] * JX, cy0 = tiles[2 * blockIdx.x + 1] * JY;
-  if (threadIdx.x == 0) mbar_init(&bar, 1);
+  if (threadIdx.x == 0) {
+    mbar_init(&bar, 1);
+    mbar_expect_tx(&bar, Resid64Smem::tx);
+    tma_load_2d(smem_raw + Resid64Smem::ct_off, &tcls, &bar, cx0, cy0);
+  }
   __syncthreads();
   pdl_enter();
   const int z = blockIdx.y;          // right-hand side of the batch
   r32 += (long)z * bs;
   norm += z;
   if (threadIdx.x == 0) {
-    mbar_expect_tx(&bar, Resid64Smem::tx);
     tma_load_3d(ut, &tu, &bar, cx0, cy0, z);
     tma_load_3d(smem_raw + Resid64Smem::rt_off, &tr, &bar, cx0, cy0 + 2, z);
-    tma_load_2d(smem_raw + Resid64Smem::ct_off, &tcls, &bar, cx0, cy0);
   }
   const bool ok = __syncthreads_and(tile_wait(&bar, err));
   if (!ok) return;

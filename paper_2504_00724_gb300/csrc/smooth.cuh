@@ -73,13 +73,18 @@ __device__ __forceinline__ bool wait_parity(uint64_t* bar, uint32_t parity) {
   return false;
 }
 
+// The copy of an item into stage st, completing on bar.  part 0: all of it; part 1: what
+// does not depend on the previous launch (a block's inverse rows; a tile's class bytes, with
+// the byte count of the whole tile), issued before the grid dependency wait; part 2: the rest
+// of a tile (iterate, right-hand side, coarse iterate), after it.
 template <typename T, bool PRO>
 __device__ __forceinline__ void smooth_issue(const SmoothArgs<T>& A, const CUtensorMap* tin, const CUtensorMap* tr,
                                              const CUtensorMap* tcls, const CUtensorMap* tuc, int item,
-                                             unsigned char* st, uint64_t* bar) {
+                                             unsigned char* st, uint64_t* bar, int part = 0) {
   const int z = blockIdx.y;      // right-hand side of the batch
   const SweepArgs<T>& a = A.a;
   if (item < A.nbi) {
+    if (part == 2) return;
     const int b = item;
     const int nc = a.blk[4 * b + 1] - a.blk[4 * b], ne = a.blk[4 * b + 3] - a.blk[4 * b + 2];
     const uint32_t abytes = (uint32_t)(((long)ne * nc * sizeof(T) + 15) & ~15L);
@@ -89,11 +94,15 @@ __device__ __forceinline__ void smooth_issue(const SmoothArgs<T>& A, const CUten
     using S = TileStage<T>;
     const int t = item - A.nbi;
     const int cx0 = a.tiles[2 * t] * JX, cy0 = a.tiles[2 * t + 1] * JY;
-    mbar_expect_tx(bar, S::u_bytes + S::r_bytes + S::c_bytes + (PRO ? S::uc_bytes : 0));
-    tma_load_3d(st, tin, bar, cx0, cy0, z);
-    tma_load_3d(st + S::r_off, tr, bar, cx0, cy0 + 2, z);
-    tma_load_2d(st + S::c_off, tcls, bar, cx0, cy0);
-    if (PRO) tma_load_3d(st + S::uc_off, tuc, bar, cx0 / 2, cy0 / 2 + 1, z);
+    if (part != 2) {
+      mbar_expect_tx(bar, S::u_bytes + S::r_bytes + S::c_bytes + (PRO ? S::uc_bytes : 0));
+      tma_load_2d(st + S::c_off, tcls, bar, cx0, cy0);
+    }
+    if (part != 1) {
+      tma_load_3d(st, tin, bar, cx0, cy0, z);
+      tma_load_3d(st + S::r_off, tr, bar, cx0, cy0 + 2, z);
+      if (PRO) tma_load_3d(st + S::uc_off, tuc, bar, cx0 / 2, cy0 / 2 + 1, z);
+    }
   }
 }
 
@@ -316,15 +325,13 @@ __global__ void __launch_bounds__(256, 3) k_smooth(const __grid_constant__ CUten
   }
   const int G = gridDim.x;
   const int K = (A.nitems - (int)blockIdx.x + G - 1) / G;   // items of this CTA (>= 1)
-  // also before the wait: the copy barriers, and the origins of the first two items if they
-  // are tiles (static data: the first copies are issued right after the wait)
+  // also before the wait: the copy barriers, and the parts of the first two items' copies
+  // that no earlier launch writes (the rest follows the wait)
   if (threadIdx.x == 0) {
     mbar_init(&bar[0], 1);
     mbar_init(&bar[1], 1);
-    for (int k = 0; k < 2 && k < K; ++k) {
-      const int t = (int)blockIdx.x + k * G - A.nbi;
-      if (t >= 0) prefetch_l1(a.tiles + 2 * t);
-    }
+    smooth_issue<T, PRO>(A, &tin, &tr, &tcls, &tuc, blockIdx.x, smem_raw, &bar[0], 1);
+    if (K > 1) smooth_issue<T, PRO>(A, &tin, &tr, &tcls, &tuc, blockIdx.x + G, smem_raw + A.stage, &bar[1], 1);
   }
   __syncthreads();
   pdl_enter();
@@ -340,8 +347,8 @@ __global__ void __launch_bounds__(256, 3) k_smooth(const __grid_constant__ CUten
   T* sold = reinterpret_cast<T*>(smem_raw + 2 * A.stage + slot);
   int* scell = reinterpret_cast<int*>(smem_raw + 2 * A.stage + 2 * slot);
   if (threadIdx.x == 0) {
-    smooth_issue<T, PRO>(A, &tin, &tr, &tcls, &tuc, blockIdx.x, smem_raw, &bar[0]);
-    if (K > 1) smooth_issue<T, PRO>(A, &tin, &tr, &tcls, &tuc, blockIdx.x + G, smem_raw + A.stage, &bar[1]);
+    smooth_issue<T, PRO>(A, &tin, &tr, &tcls, &tuc, blockIdx.x, smem_raw, &bar[0], 2);
+    if (K > 1) smooth_issue<T, PRO>(A, &tin, &tr, &tcls, &tuc, blockIdx.x + G, smem_raw + A.stage, &bar[1], 2);
   }
   for (int k = 0; k < K; ++k) {
     const int item = blockIdx.x + k * G;
@@ -458,34 +465,40 @@ __global__ void __launch_bounds__(256, 3) k_restrict_p(const __grid_constant__ C
   // the first tile's row range and rows while the previous launch drains
   int n0 = A.rr_off[blockIdx.x], n1 = A.rr_off[blockIdx.x + 1];
   prefetch_tile_rows(A, n0, n1);
-  // the copy barriers and the first two tiles' origins (for the copies issued right after
-  // the wait) too
+  // this CTA's right-hand side of the batch (blockIdx.y)
+  const int z = blockIdx.y;
+  // tile t's copy into stage sb.  part 0: all of it; part 1: the class bytes and volumes,
+  // which no launch writes, with the byte count of the whole tile (before the grid
+  // dependency wait); part 2: the iterate and the right-hand side (after it)
+  auto issue = [&](int t, int sb, int part) {
+    unsigned char* st = smem_raw + sb * A.stage;
+    const int cx0 = A.tiles[2 * t] * JX, cy0 = A.tiles[2 * t + 1] * JY;
+    if (part != 2) {
+      mbar_expect_tx(&bar[sb], S::tx);
+      tma_load_2d(st + S::c_off, &tcls, &bar[sb], cx0, cy0);
+      tma_load_2d(st + S::v_off, &tvol, &bar[sb], cx0, cy0 + 2);
+    }
+    if (part != 1) {
+      tma_load_3d(st, &tin, &bar[sb], cx0, cy0, z);
+      tma_load_3d(st + S::r_off, &tr, &bar[sb], cx0, cy0 + 2, z);
+    }
+  };
+  // the copy barriers and the static parts of the first two tiles' copies too
   if (threadIdx.x == 0) {
     mbar_init(&bar[0], 1);
     mbar_init(&bar[1], 1);
-    prefetch_l1(A.tiles + 2 * blockIdx.x);
-    if (K > 1) prefetch_l1(A.tiles + 2 * (blockIdx.x + G));
+    issue(blockIdx.x, 0, 1);
+    if (K > 1) issue(blockIdx.x + G, 1, 1);
   }
   __syncthreads();
   pdl_enter();
-  // this CTA's right-hand side of the batch (blockIdx.y)
-  const int z = blockIdx.y;
   const T* __restrict__ uf = A.u + (long)z * A.bs;
   const T* __restrict__ rf = A.r + (long)z * A.bs;
   T* __restrict__ rcz = A.rc + (long)z * A.bsc;
   T* __restrict__ ucz = A.uc + (long)z * A.bsc;
-  auto issue = [&](int t, int sb) {
-    unsigned char* st = smem_raw + sb * A.stage;
-    const int cx0 = A.tiles[2 * t] * JX, cy0 = A.tiles[2 * t + 1] * JY;
-    mbar_expect_tx(&bar[sb], S::tx);
-    tma_load_3d(st, &tin, &bar[sb], cx0, cy0, z);
-    tma_load_3d(st + S::r_off, &tr, &bar[sb], cx0, cy0 + 2, z);
-    tma_load_2d(st + S::c_off, &tcls, &bar[sb], cx0, cy0);
-    tma_load_2d(st + S::v_off, &tvol, &bar[sb], cx0, cy0 + 2);
-  };
   if (threadIdx.x == 0) {
-    issue(blockIdx.x, 0);
-    if (K > 1) issue(blockIdx.x + G, 1);
+    issue(blockIdx.x, 0, 2);
+    if (K > 1) issue(blockIdx.x + G, 1, 2);
   }
   const int x = threadIdx.x & 63, y0 = (threadIdx.x >> 6) * 8;
   for (int k = 0; k < K; ++k) {
@@ -628,7 +641,7 @@ __global__ void __launch_bounds__(256, 3) k_restrict_p(const __grid_constant__ C
     __syncthreads();      // res and stage sb are free
     if (threadIdx.x == 0 && k + 2 < K) {
       fence_proxy_async();
-      issue(t + 2 * G, sb);
+      issue(t + 2 * G, sb, 0);
     }
   }
 }
