@@ -345,6 +345,15 @@ int ccm_level_smooth(ccm_handle* h, int level, double* u, const double* r, int p
 int ccm_level_restrict(ccm_handle* h, int level, const double* u, const double* r, double* rc, void* stream);
 /* Prolongation (Alg. 2): u += Prolong(uc), uc on level m + 1. */
 int ccm_level_prolong(ccm_handle* h, int level, const double* uc, double* u, void* stream);
+/* The first post-smoothing sweep of Alg. 2 with the prolongation fused, as the V-cycle runs
+ * it: one smoother step on level m (as ccm_level_smooth) from the iterate u + Prolong(uc),
+ * the parent's value added on the regular cells (Sec. 4.1); u (level m) is updated in place,
+ * uc is level m + 1's iterate, r level m's right-hand side, all in the user layout of their
+ * level.  precision as ccm_level_smooth.  Where level m's tiles are staged by TMA this is one
+ * launch (the persistent sweep reads u + Prolong(uc) on the fly), else a prolongation and a
+ * sweep.  Errors: CCM_EINVAL (level out of range or the coarsest, a NULL array), CCM_ECUDA. */
+int ccm_level_prolong_smooth(ccm_handle* h, int level, double* u, const double* uc, const double* r, int precision,
+                             void* stream);
 /* Bottom solve on the coarsest level M: u = (L^(M))^-1 r. */
 int ccm_bottom_solve(ccm_handle* h, const double* r, double* u, void* stream);
 /* One V-cycle (Alg. 2) on level 0 for L u = r (physical units, FP64 in and out). */

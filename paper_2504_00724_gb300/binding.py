@@ -99,6 +99,7 @@ _SIGS = {
     "ccm_level_smooth": (I, [P, I, P, P, I, P]),
     "ccm_level_restrict": (I, [P, I, P, P, P, P]),
     "ccm_level_prolong": (I, [P, I, P, P, P]),
+    "ccm_level_prolong_smooth": (I, [P, I, P, P, P, I, P]),
     "ccm_bottom_solve": (I, [P, P, P, P]),
     "ccm_vcycle": (I, [P, P, P, I, P]),
     "ccm_fmg": (I, [P, P, P, I, P]),
@@ -366,6 +367,13 @@ class Solver:
     def level_prolong(self, level, uc, u, stream=None):
         u = u.clone()
         _check(lib().ccm_level_prolong(self.h, level, _ptr(uc), _ptr(u), _stream(stream)), "ccm_level_prolong")
+        return u
+
+    def level_prolong_smooth(self, level, u, uc, r, precision=CCM_FP64, stream=None):
+        """The first post-smoothing sweep with the prolongation fused: one sweep from u + P uc."""
+        u = u.clone()
+        _check(lib().ccm_level_prolong_smooth(self.h, level, _ptr(u), _ptr(uc), _ptr(r), precision, _stream(stream)),
+               "ccm_level_prolong_smooth")
         return u
 
     def bottom_solve(self, r, stream=None):

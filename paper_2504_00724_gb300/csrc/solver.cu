@@ -2402,6 +2402,28 @@ int ccm_level_prolong(ccm_handle* h, int level, const double* uc, double* u, voi
   return CCM_OK;
 }
 
+int ccm_level_prolong_smooth(ccm_handle* h, int level, double* u, const double* uc, const double* r, int precision,
+                             void* stream) {
+  if (check_level(h, level) || level == (int)h->L.size() - 1 || !u || !uc || !r) return CCM_EINVAL;
+  cudaStream_t s = (cudaStream_t)stream;
+  DevLevel& F = h->L[level];
+  DevLevel& C = h->L[level + 1];
+  dim3 pg(ceil_div(F.nx, 128), F.ny);
+  if (precision == CCM_FP64) {
+    load_level<double>(h, F, u, r, s);
+    load_level<double>(h, C, uc, nullptr, s);
+    smooth_step<double>(h, F, s, U<double>(C), C.pitch);
+    KL(dev::k_unpack<double><<<pg, 128, 0, s>>>(F.nx, F.ny, F.pitch, F.cls, U<double>(F), u, 1.0));
+  } else {
+    load_level<float>(h, F, u, r, s);
+    load_level<float>(h, C, uc, nullptr, s);
+    smooth_step<float>(h, F, s, U<float>(C), C.pitch);
+    KL(dev::k_unpack<float><<<pg, 128, 0, s>>>(F.nx, F.ny, F.pitch, F.cls, U<float>(F), u, 1.0));
+  }
+  CCM_CUDA(cudaGetLastError());
+  return CCM_OK;
+}
+
 int ccm_bottom_solve(ccm_handle* h, const double* r, double* u, void* stream) {
   if (!h || !r || !u) return CCM_EINVAL;
   cudaStream_t s = (cudaStream_t)stream;

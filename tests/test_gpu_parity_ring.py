@@ -11,7 +11,8 @@ the ring really turns.  Three ways to get there:
     FP64 (in FP32, whose three resident CTAs per SM outnumber them, on half the grid);
   * 64 right-hand sides on star 288^2: 456 / 64 = 8 CTAs per right-hand side.
 Expected values come from the oracle: its level-0 operator, the block-Jacobi sweep written out
-on it, its restriction and its sparse direct solve."""
+on it (also from the prolonged iterate, for the first post-smoothing sweep with the
+prolongation fused), its restriction and its sparse direct solve."""
 from types import SimpleNamespace
 
 import numpy as np
@@ -84,6 +85,22 @@ def check_sweep(s, lv, seed, precision, tol):
     assert np.abs(got - want).max() <= tol * np.abs(want).max()
 
 
+def check_prolong_sweep(s, lv, coarse, seed, precision, tol):
+    """The first post-smoothing sweep with the prolongation fused (what the V-cycle runs)
+    against the oracle's prolongation followed by the block-Jacobi sweep."""
+    cells = s.level_rows(0)[0].astype(np.int64)
+    rng = np.random.default_rng(seed)
+    u0 = np.where(lv.ne, rng.standard_normal(lv.nx * lv.ny), 0.0)
+    uc = np.where(coarse.ne, rng.standard_normal(coarse.nx * coarse.ny), 0.0)
+    r = np.where(lv.ne, rng.standard_normal(lv.nx * lv.ny), 0.0) / lv.h ** 2
+    start = u0 + MG.prolong(lv, coarse, uc)
+    assert np.abs(start - u0).max() > 0.5          # the correction reaches the regular cells
+    want = block_jacobi_sweep(lv, cells, start, r, OMEGA, s.params.ras_block, s.params.ras_overlap)
+    got = host(s.level_prolong_smooth(0, cuda(u0.reshape(lv.ny, lv.nx)), cuda(uc.reshape(coarse.ny, coarse.nx)),
+                                      cuda(r.reshape(lv.ny, lv.nx)), precision)).ravel()
+    assert np.abs(got - want).max() <= tol * np.abs(want).max()
+
+
 def check_restrict(s, lv, coarse, seed):
     rng = np.random.default_rng(seed)
     u = np.where(lv.ne, rng.standard_normal(lv.nx * lv.ny), 0.0)
@@ -119,6 +136,19 @@ def test_capped_sweep_matches_block_jacobi(star288, precision, tol):
         li = s.level_launch(0, precision)
         assert li.sweep_ctas == CAP and li.sweep_items >= 3 * CAP and li.sweep_blocks > CAP
         check_sweep(s, lv, 41, precision, tol)
+    finally:
+        s.close()
+
+
+@pytest.mark.parametrize("precision,tol", [(P.CCM_FP64, 1e-10), (P.CCM_MIXED, 2e-4)])
+def test_capped_prolong_sweep_matches_oracle(star288, precision, tol):
+    prob, lv, coarse, *_ = star288
+    s = P.Solver(prob, omega=OMEGA)
+    try:
+        s.set_launch_cap(CAP)
+        li = s.level_launch(0, precision)
+        assert li.sweep_ctas == CAP and li.sweep_items >= 3 * CAP and li.sweep_blocks > CAP
+        check_prolong_sweep(s, lv, coarse, 47, precision, tol)
     finally:
         s.close()
 
@@ -208,6 +238,21 @@ def test_star1024_level0_sweep(star1024, precision, tol):
             li = s.level_launch(0, precision)
         assert li.sweep_items > li.sweep_ctas > 0
         check_sweep(s, lv, 51, precision, tol)
+    finally:
+        s.close()
+
+
+@pytest.mark.parametrize("precision,tol", [(P.CCM_FP64, 1e-10), (P.CCM_MIXED, 2e-4)])
+def test_star1024_level0_prolong_sweep(star1024, precision, tol):
+    prob, lv, coarse = star1024
+    s = P.Solver(prob, omega=OMEGA)
+    try:
+        li = s.level_launch(0, precision)
+        if li.sweep_items <= li.sweep_ctas:
+            s.set_launch_cap(li.sweep_items // 2)
+            li = s.level_launch(0, precision)
+        assert li.sweep_items > li.sweep_ctas > 0
+        check_prolong_sweep(s, lv, coarse, 57, precision, tol)
     finally:
         s.close()
 
