@@ -967,6 +967,54 @@ __global__ void k_unpack(int nx, int ny, int pitch, const uint8_t* __restrict__ 
   else if (!KEEP) dst[(long)j * nx + i] = 0.0;
 }
 
+// k_pack and k_unpack over the level's active 32 x 8 tiles (every non-empty cell lies in one;
+// on a domain that covers a fraction of the box the rest of the grid is not visited).  The
+// tiled unpack writes the non-empty cells only: a caller that wants 0 on the empty cells
+// clears the destination first.
+template <typename TD, typename TS>
+__global__ void k_pack_tiles(const int32_t* __restrict__ tiles, int nx, int ny, int pitch, const uint8_t* __restrict__ cls,
+                             const TS* __restrict__ src, TD* __restrict__ dst, double scale) {
+  const int i = tiles[2 * blockIdx.x] * TX + threadIdx.x, j = tiles[2 * blockIdx.x + 1] * TY + threadIdx.y;
+  if (i >= nx || j >= ny) return;
+  const long p = (long)(j + 2) * pitch + (i + 2);
+  if (cls[p] != 0) dst[p] = (TD)(scale * (double)src[(long)j * nx + i]);
+}
+
+template <typename TS>
+__global__ void k_unpack_tiles(const int32_t* __restrict__ tiles, int nx, int ny, int pitch,
+                               const uint8_t* __restrict__ cls, const TS* __restrict__ src, double* __restrict__ dst,
+                               double scale) {
+  const int i = tiles[2 * blockIdx.x] * TX + threadIdx.x, j = tiles[2 * blockIdx.x + 1] * TY + threadIdx.y;
+  if (i >= nx || j >= ny) return;
+  const long p = (long)(j + 2) * pitch + (i + 2);
+  if (cls[p] != 0) dst[(long)j * nx + i] = scale * (double)src[p];
+}
+
+// max |x| over the non-empty cells of the active 32 x 8 tiles (as k_absmax), CTAs striding
+// over the tiles; right-hand side blockIdx.y of a batch at stride bs
+template <typename T>
+__global__ void k_absmax_tiles(const int32_t* __restrict__ tiles, int ntiles, int nx, int ny, int pitch,
+                               const uint8_t* __restrict__ cls, const T* __restrict__ x,
+                               unsigned long long* __restrict__ out, long bs) {
+  pdl_enter();
+  x += blockIdx.y * bs;
+  out += blockIdx.y;
+  double m = 0.0;
+  for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
+    const int i = tiles[2 * t] * TX + threadIdx.x, j = tiles[2 * t + 1] * TY + threadIdx.y;
+    if (i < nx && j < ny) {
+      const long p = (long)(j + 2) * pitch + (i + 2);
+      if (cls[p] != 0) {
+        double v = fabs((double)x[p]);
+        if (!(v <= 1.7976931348623157e308)) v = __longlong_as_double(0x7ff0000000000000ULL);   // NaN -> Inf
+        m = fmax(m, v);
+      }
+    }
+  }
+  for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+  if (threadIdx.x == 0) atomicMax(out, (unsigned long long)__double_as_longlong(m));
+}
+
 // r_hat -= nb g on the rows that own a boundary segment
 __global__ void k_sub_boundary(int n2, const int32_t* __restrict__ cell, const double* __restrict__ nb,
                                const int32_t* __restrict__ seg, const double* __restrict__ g, double* __restrict__ r) {

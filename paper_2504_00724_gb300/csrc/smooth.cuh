@@ -170,7 +170,6 @@ template <typename T, bool CROSS, bool PRO>
 __device__ __forceinline__ void tile_sweep(const SweepArgs<T>& a, unsigned char* st, int cx0, int cy0,
                                            T* __restrict__ u_new) {
   using S = TileStage<T>;
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   T* tile = reinterpret_cast<T*>(st);
   const T* rt = reinterpret_cast<const T*>(st + S::r_off);
   const uint8_t* ct = st + S::c_off;

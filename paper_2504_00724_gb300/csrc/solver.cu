@@ -1201,13 +1201,13 @@ int upload_hierarchy(ccm_handle* h) {
     for (int i = 0; i < h->kry_m; ++i) h->kz[i] = A.alloc<float>(h->L[0].npad);
     h->ks = A.alloc<dev::KryScalars>(1);
   }
-  h->dnorm = A.alloc<unsigned long long>(h->B);
+  h->dnorm = A.alloc<unsigned long long>(2 * h->B);   // [0, B) residual norms, [B, 2B) ||r_hat||
   h->derr = A.alloc<int>(1);
   if (A.err != cudaSuccess) {
     A.release();
     return A.err == cudaErrorMemoryAllocation ? CCM_ENOMEM : CCM_ECUDA;
   }
-  if (cudaMallocHost(&h->hnorm, h->B * sizeof(unsigned long long)) != cudaSuccess ||
+  if (cudaMallocHost(&h->hnorm, 2 * h->B * sizeof(unsigned long long)) != cudaSuccess ||
       cudaMallocHost(&h->herr, sizeof(int)) != cudaSuccess) {
     A.release();
     return CCM_ECUDA;
@@ -1814,27 +1814,30 @@ static bool log_enabled() {
 }
 
 // r_hat = h^2 (f - N g) and the initial guess into slots [0, nb) of the level-0 FP64 arrays,
-// from right-hand sides [k0, k0 + nb) of the caller's arrays (g may be NULL: g = 0)
+// from right-hand sides [k0, k0 + nb) of the caller's arrays (g may be NULL: g = 0).  The
+// packing visits the active 32 x 8 tiles only.  ||r_hat|| of slot b goes to dnorm[B + b].
 static int load_rhs(ccm_handle* h, const double* f, const double* g, const double* u, int k0, int nb, double* U0,
                     cudaStream_t s) {
   DevLevel& L = h->L[0];
   const long nu = (long)L.nx * L.ny, np = L.npad;
-  dim3 pg(ceil_div(L.nx, 128), L.ny);
+  const dim3 tb(dev::TX, dev::TY);
   CCM_CUDA(cudaMemsetAsync(h->rhat, 0, nb * np * sizeof(double), s));
   CCM_CUDA(cudaMemsetAsync(U0, 0, nb * np * sizeof(double), s));
-  for (int b = 0; b < nb; ++b) {
+  for (int b = 0; b < nb && L.ntiles; ++b) {
     const long k = k0 + b;
-    KL(dev::k_pack<double, double><<<pg, 128, 0, s>>>(L.nx, L.ny, L.pitch, L.cls, f + k * nu, h->rhat + b * np, L.h * L.h));
+    KL(dev::k_pack_tiles<double, double><<<L.ntiles, tb, 0, s>>>(L.tiles, L.nx, L.ny, L.pitch, L.cls, f + k * nu,
+                                                                 h->rhat + b * np, L.h * L.h));
     if (g && L.n2)
       KL(dev::k_sub_boundary<<<ceil_div(L.n2, 128), 128, 0, s>>>(L.n2, L.irr_cell, L.nb, L.seg,
                                                              g + k * h->info.n_segments, h->rhat + b * np));
-    KL(dev::k_pack<double, double><<<pg, 128, 0, s>>>(L.nx, L.ny, L.pitch, L.cls, u + k * nu, U0 + b * np, 1.0));
+    KL(dev::k_pack_tiles<double, double><<<L.ntiles, tb, 0, s>>>(L.tiles, L.nx, L.ny, L.pitch, L.cls, u + k * nu,
+                                                                 U0 + b * np, 1.0));
   }
   if (h->par.precision == CCM_FP64) CCM_CUDA(cudaMemcpyAsync(L.r64, h->rhat, np * sizeof(double), cudaMemcpyDeviceToDevice, s));
-  // ||r_hat|| of every right-hand side into dnorm[0, nb)
-  CCM_CUDA(cudaMemsetAsync(h->dnorm, 0, nb * sizeof(unsigned long long), s));
-  KL(launch_k(dev::k_absmax<double>, dim3(std::min(ceil_div(np, 256), 1216), nb), 256, 0, s, np, L.cls,
-              (const double*)h->rhat, h->dnorm, np));
+  CCM_CUDA(cudaMemsetAsync(h->dnorm + h->B, 0, nb * sizeof(unsigned long long), s));
+  if (L.ntiles)
+    KL(launch_k(dev::k_absmax_tiles<double>, dim3(std::min(L.ntiles, 1216), nb), tb, 0, s, L.tiles, L.ntiles, L.nx, L.ny,
+                L.pitch, L.cls, (const double*)h->rhat, h->dnorm + h->B, np));
   return CCM_OK;
 }
 
@@ -1884,17 +1887,17 @@ int solve_impl(ccm_handle* h, const double* f, const double* g, double* u, int n
       h->nb = 1;
       return rc;
     }
-    CCM_CUDA(cudaMemcpyAsync(h->hnorm, h->dnorm, nb * sizeof(unsigned long long), cudaMemcpyDeviceToHost, s));
-    CCM_CUDA(cudaStreamSynchronize(s));
-    for (int b = 0; b < nb; ++b) {
-      std::memcpy(&rnorm[b], &h->hnorm[b], sizeof(double));
-      if (rnorm[b] == 0) rnorm[b] = 1;
-    }
-    // initial residual (one right-hand side at a time outside the fused mixed form)
+    // initial residual (one right-hand side at a time outside the fused mixed form); its norms
+    // and ||r_hat|| come back in one synchronisation
     initial_residual(h, U0, s);
     CCM_CUDA(cudaMemcpyAsync(h->hnorm, h->dnorm, nb * sizeof(unsigned long long), cudaMemcpyDeviceToHost, s));
+    CCM_CUDA(cudaMemcpyAsync(h->hnorm + h->B, h->dnorm + h->B, nb * sizeof(unsigned long long), cudaMemcpyDeviceToHost, s));
     CCM_CUDA(cudaStreamSynchronize(s));
-    for (int b = 0; b < nb; ++b) std::memcpy(&rel[b], &h->hnorm[b], sizeof(double));
+    for (int b = 0; b < nb; ++b) {
+      std::memcpy(&rnorm[b], &h->hnorm[h->B + b], sizeof(double));
+      if (rnorm[b] == 0) rnorm[b] = 1;
+      std::memcpy(&rel[b], &h->hnorm[b], sizeof(double));
+    }
     // the worst right-hand side of the group decides; stats report it
     auto worst = [&]() {
       double w = 0;
@@ -1934,11 +1937,12 @@ int solve_impl(ccm_handle* h, const double* f, const double* g, double* u, int n
     if (result == CCM_ETIMEOUT) {
     } else if (!std::isfinite(wr)) result = CCM_ENOTFINITE;
     else if (wr > h->par.rtol && result == CCM_OK) result = CCM_ENOCONV;
+    // the non-empty cells over the active tiles; without keep_empty the array is cleared first
     for (int b = 0; b < nb; ++b) {
-      if (keep_empty)
-        KL(dev::k_unpack<double, true><<<pg, 128, 0, s>>>(L.nx, L.ny, L.pitch, L.cls, U0 + b * np, u + (k0 + b) * nu, 1.0));
-      else
-        KL(dev::k_unpack<double><<<pg, 128, 0, s>>>(L.nx, L.ny, L.pitch, L.cls, U0 + b * np, u + (k0 + b) * nu, 1.0));
+      if (!keep_empty) CCM_CUDA(cudaMemsetAsync(u + (k0 + b) * nu, 0, nu * sizeof(double), s));
+      if (L.ntiles)
+        KL(dev::k_unpack_tiles<double><<<L.ntiles, dim3(dev::TX, dev::TY), 0, s>>>(L.tiles, L.nx, L.ny, L.pitch, L.cls,
+                                                                                 U0 + b * np, u + (k0 + b) * nu, 1.0));
     }
     local.iterations = it;
     local.rel_residual = wr;
@@ -2157,7 +2161,7 @@ int ccm_group_solve(ccm_group* G, const double* const* f, const double* const* g
     h->nb = 1;
     int rc = load_rhs(h, f[k], g ? g[k] : nullptr, u[k], 0, 1, G->u0[k], s);
     if (rc) return rc;
-    CCM_CUDA(cudaMemcpyAsync(G->rnorm + k, h->dnorm, sizeof(unsigned long long), cudaMemcpyDeviceToDevice, s));
+    CCM_CUDA(cudaMemcpyAsync(G->rnorm + k, h->dnorm + h->B, sizeof(unsigned long long), cudaMemcpyDeviceToDevice, s));
     initial_residual(h, G->u0[k], s);
   }
   CCM_CUDA(cudaGraphLaunch(G->exec, s));
