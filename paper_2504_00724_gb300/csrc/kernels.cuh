@@ -303,6 +303,11 @@ struct SweepArgs {
   const int32_t* par;    // per ELL slot: padded parent (level m + 1) of a regular column, else -1
   const T* uc;           // coarse iterate: the sweep reads u + P uc (regular cells), or null
   long bs, bsc;          // batch strides (elements) of this level's and the coarse level's arrays
+  // persistent sweep only: zero_u, the old iterate is 0 (it is not read); uhat (FP32 sweep of
+  // level 0, or null), the FP64 solution to which every new value is added (u_hat += e as the
+  // last sweep of an outer iteration writes e), same layout and batch stride
+  int zero_u;
+  double* uhat;
 };
 
 template <typename T>

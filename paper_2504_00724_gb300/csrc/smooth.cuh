@@ -94,12 +94,13 @@ __device__ __forceinline__ void smooth_issue(const SmoothArgs<T>& A, const CUten
     using S = TileStage<T>;
     const int t = item - A.nbi;
     const int cx0 = a.tiles[2 * t] * JX, cy0 = a.tiles[2 * t + 1] * JY;
+    const bool no_u = !PRO && sizeof(T) == 4 && a.zero_u;     // the old iterate is 0
     if (part != 2) {
-      mbar_expect_tx(bar, S::u_bytes + S::r_bytes + S::c_bytes + (PRO ? S::uc_bytes : 0));
+      mbar_expect_tx(bar, (no_u ? 0u : S::u_bytes) + S::r_bytes + S::c_bytes + (PRO ? S::uc_bytes : 0));
       tma_load_2d(st + S::c_off, tcls, bar, cx0, cy0);
     }
     if (part != 1) {
-      tma_load_3d(st, tin, bar, cx0, cy0, z);
+      if (!no_u) tma_load_3d(st, tin, bar, cx0, cy0, z);
       tma_load_3d(st + S::r_off, tr, bar, cx0, cy0 + 2, z);
       if (PRO) tma_load_3d(st + S::uc_off, tuc, bar, cx0 / 2, cy0 / 2 + 1, z);
     }
@@ -121,6 +122,13 @@ __device__ __forceinline__ void block_residuals(const SweepArgs<T>& a, int b, co
   ne = a.blk[4 * b + 3] - es;
   for (int e = threadIdx.x; e < ne; e += blockDim.x) {
     const int row = es + e;
+    const int q = a.cell[row];
+    if (!PRO && sizeof(T) == 4 && a.zero_u) {   // the old iterate is 0: the residual is r
+      sres[e] = rhs[q];
+      sold[e] = (T)0;
+      scell[e] = q;
+      continue;
+    }
     T acc = 0;
 #pragma unroll 15
     for (int m = 0; m < a.W; ++m) {
@@ -132,7 +140,6 @@ __device__ __forceinline__ void block_residuals(const SweepArgs<T>& a, int b, co
       }
       acc += a.val[(long)m * a.n2 + row] * v;
     }
-    const int q = a.cell[row];
     sres[e] = rhs[q] - acc;
     sold[e] = CG ? __ldcg(u_old + q) : u_old[q];
     scell[e] = q;
@@ -144,7 +151,8 @@ __device__ __forceinline__ void block_residuals(const SweepArgs<T>& a, int b, co
 // their old values from scell and sold (no global round trip before the stores)
 template <typename T>
 __device__ __forceinline__ void block_apply(const T* As, const T* sres, const T* sold, const int* scell, int c0,
-                                            int nc, int ne, T* __restrict__ u_new, T (*part)[32]) {
+                                            int nc, int ne, T* __restrict__ u_new, double* __restrict__ uhat,
+                                            T (*part)[32]) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   for (int cb = 0; cb < nc; cb += 32) {
     const int c = cb + lane;
@@ -157,7 +165,10 @@ __device__ __forceinline__ void block_apply(const T* As, const T* sres, const T*
       T tot = 0;
 #pragma unroll
       for (int w = 0; w < 8; ++w) tot += part[w][lane];
-      u_new[scell[c0 + c]] = sold[c0 + c] + tot;
+      const int q = scell[c0 + c];
+      const T v = sold[c0 + c] + tot;
+      u_new[q] = v;
+      if (uhat) uhat[q] += (double)v;
     }
     __syncthreads();
   }
@@ -168,7 +179,7 @@ __device__ __forceinline__ void block_apply(const T* As, const T* sres, const T*
 // added to the staged regular cells: the sweep then reads u + P uc)
 template <typename T, bool CROSS, bool PRO>
 __device__ __forceinline__ void tile_sweep(const SweepArgs<T>& a, unsigned char* st, int cx0, int cy0,
-                                           T* __restrict__ u_new) {
+                                           T* __restrict__ u_new, double* __restrict__ uhat) {
   using S = TileStage<T>;
   T* tile = reinterpret_cast<T*>(st);
   const T* rt = reinterpret_cast<const T*>(st + S::r_off);
@@ -256,6 +267,36 @@ __device__ __forceinline__ void tile_sweep(const SweepArgs<T>& a, unsigned char*
     using V2 = typename Pair<T>::type;
     const int x0 = 2 * (threadIdx.x & 31), y0 = (threadIdx.x >> 5) * 4;
     const int i0 = cx0 + x0;
+    // the new values of row kk's pair: into u_new, and added to u_hat when the sweep folds in
+    // the outer iteration's update
+    auto put = [&](int kk, T v0, T v1, uint32_t c2) {
+      const bool g0 = (c2 & 0xffu) == 1u, g1 = (c2 >> 8) == 1u && i0 + 1 < a.nx;
+      const long p = (long)(cy0 + y0 + kk + 2) * a.pitch + (i0 + 2);
+      if (g0 && g1) {
+        V2 o;
+        o.x = v0;
+        o.y = v1;
+        *reinterpret_cast<V2*>(u_new + p) = o;
+      } else {
+        if (g0) u_new[p] = v0;
+        if (g1) u_new[p + 1] = v1;
+      }
+      if (uhat) {
+        if (g0) uhat[p] += (double)v0;
+        if (g1) uhat[p + 1] += (double)v1;
+      }
+    };
+    if (!PRO && a.zero_u) {
+      // the old iterate is 0 (its tile was not copied): u_new = omega_d r on the regular cells
+      if (i0 < a.nx)
+#pragma unroll
+        for (int kk = 0; kk < 4; ++kk) {
+          const uint32_t c2 = *reinterpret_cast<const uint16_t*>(ct + (y0 + kk + 2) * CLX + x0 + 2);
+          const V2 r2 = *reinterpret_cast<const V2*>(rt + (y0 + kk) * HX + x0 + 2);
+          put(kk, a.S.omega_d * r2.x, a.S.omega_d * r2.y, c2);
+        }
+      return;
+    }
     if (i0 < a.nx) {
       T w[5][6];
 #pragma unroll
@@ -274,19 +315,7 @@ __device__ __forceinline__ void tile_sweep(const SweepArgs<T>& a, unsigned char*
           }
         const uint32_t c2 = *reinterpret_cast<const uint16_t*>(ct + (y0 + kk + 2) * CLX + x0 + 2);
         const V2 r2 = *reinterpret_cast<const V2*>(rt + (y0 + kk) * HX + x0 + 2);
-        const T v0 = w[2][2] + a.S.omega_d * (r2.x - acc0);
-        const T v1 = w[2][3] + a.S.omega_d * (r2.y - acc1);
-        const bool g0 = (c2 & 0xffu) == 1u, g1 = (c2 >> 8) == 1u && i0 + 1 < a.nx;
-        const long p = (long)(cy0 + y0 + kk + 2) * a.pitch + (i0 + 2);
-        if (g0 && g1) {
-          V2 o;
-          o.x = v0;
-          o.y = v1;
-          *reinterpret_cast<V2*>(u_new + p) = o;
-        } else {
-          if (g0) u_new[p] = v0;
-          if (g1) u_new[p + 1] = v1;
-        }
+        put(kk, w[2][2] + a.S.omega_d * (r2.x - acc0), w[2][3] + a.S.omega_d * (r2.y - acc1), c2);
 #pragma unroll
         for (int q = 0; q < 4; ++q)
 #pragma unroll
@@ -338,6 +367,7 @@ __global__ void __launch_bounds__(256, 3) k_smooth(const __grid_constant__ CUten
   const long bo = (long)blockIdx.y * a.bs;
   const T* __restrict__ u_old = a.u_old + bo;
   T* __restrict__ u_new = a.u_new + bo;
+  double* __restrict__ uhat = a.uhat ? a.uhat + bo : nullptr;
   const T* __restrict__ rhs = a.r + bo;
   const T* __restrict__ ucs = PRO ? a.uc + (long)blockIdx.y * a.bsc : nullptr;
   // per extended row of a block item: residual, old value, cell (three slots of max_ext)
@@ -371,9 +401,9 @@ __global__ void __launch_bounds__(256, 3) k_smooth(const __grid_constant__ CUten
     }
     if (item < A.nbi) {
       block_apply<T>(reinterpret_cast<const T*>(smem_raw + sb * A.stage), sres, sold, scell, cs - es, nc, ne, u_new,
-                     part);
+                     uhat, part);
     } else {
-      tile_sweep<T, CROSS, PRO>(a, smem_raw + sb * A.stage, cx0, cy0, u_new);
+      tile_sweep<T, CROSS, PRO>(a, smem_raw + sb * A.stage, cx0, cy0, u_new, uhat);
     }
     __syncthreads();      // stage sb is free
     if (threadIdx.x == 0 && k + 2 < K) {

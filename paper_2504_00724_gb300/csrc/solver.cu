@@ -216,6 +216,11 @@ struct ccm_handle {
   cudaStream_t side = nullptr;          // second stream: SMO-2 blocks beside the regular sweep
   cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
   bool capturing = false;
+  // one-launch requests to the next persistent level-0 FP32 sweep (set while an outer
+  // iteration is issued, cleared when used): zero_u_next, its old iterate is 0 (not read);
+  // fold_next, it also adds its new values to u_hat (the update of the outer iteration).
+  // fold_last marks the last inner cycle; folded reports that a sweep took the update.
+  bool zero_u_next = false, fold_next = false, fold_last = false, folded = false;
   long long cap_launches = 0;
   struct Graph {
     cudaGraphExec_t exec = nullptr;
@@ -391,6 +396,11 @@ void sweep_persistent(ccm_handle* H, DevLevel& L, cudaStream_t s, DevLevel* C) {
   A.nitems = L.nblk + L.ntiles64;
   A.stage = L.smooth_stage[k];
   A.max_ext = std::max(1, L.max_ext);
+  const bool l0f = &L == &H->L[0] && sizeof(T) == 4;
+  a.zero_u = l0f && !C && H->zero_u_next ? 1 : 0;
+  a.uhat = l0f && H->fold_next ? H->uhat : nullptr;
+  if (a.uhat) H->folded = true;
+  H->zero_u_next = H->fold_next = false;
   const bool l0 = &L == &H->L[0];
   ProfScope ps(H, !l0 ? 0 : C ? (sizeof(T) == 4 ? CCM_PROF_PROLONG_SMO1_FP32 : 0)
                               : (sizeof(T) == 4 ? CCM_PROF_SMO1_FP32 : CCM_PROF_SMO1_FP64), s);
@@ -753,8 +763,15 @@ void vcycle(ccm_handle* H, int m, cudaStream_t s, bool prolong_first = false) {
     prolong_from<T>(H, F, C, s);
     return;
   }
+  // the last inner cycle's last level-0 sweep may take the outer update u_hat += e
+  const bool fold = m == 0 && H->fold_last;
+  H->fold_next = fold && H->par.nu2 == 1;
   smooth_step<T>(H, F, s, U<T>(C), C.pitch);
-  for (int k = 1; k < H->par.nu2; ++k) smooth_step<T>(H, F, s);
+  for (int k = 1; k < H->par.nu2; ++k) {
+    H->fold_next = fold && k == H->par.nu2 - 1;
+    smooth_step<T>(H, F, s);
+  }
+  H->fold_next = false;
 }
 
 // One FMG cycle (Sec. 4, the FMG figure) for L^(0) u = r^(0) from the zero guess: the
@@ -1628,16 +1645,29 @@ static void iteration_body(ccm_handle* h, bool fp64, cudaStream_t s, bool to_hos
     cudaMemcpyAsync(h->herr, h->derr, sizeof(int), cudaMemcpyDeviceToHost, s);
     return;
   } else if (h->fused_outer) {
-    // r32 holds the FP32 image of the residual (previous iteration or the initial one)
-    cudaMemsetAsync(L.u32[L.cur32], 0, h->nb * np * sizeof(float), s);
-    for (int c = 0; c < std::max(1, h->par.inner_cycles); ++c) {
+    // r32 holds the FP32 image of the residual (previous iteration or the initial one).  Where
+    // level 0 runs the persistent sweep, its first sweep starts from the zero correction
+    // without reading it (no clearing pass), and the last one adds its new values to u_hat
+    // (no separate update pass)
+    const bool persistent0 = L.smooth_ok[1] && h->persistent && h->par.smoother == 1 && h->par.ras_passes <= 1;
+    const bool zero_first = persistent0 && h->par.nu1 >= 1 && h->par.cycle == 0;
+    if (!zero_first) cudaMemsetAsync(L.u32[L.cur32], 0, h->nb * np * sizeof(float), s);
+    const int ncyc = std::max(1, h->par.inner_cycles);
+    h->folded = false;
+    for (int c = 0; c < ncyc; ++c) {
       ProfScope ps(h, CCM_PROF_VCYCLE, s);
+      h->zero_u_next = c == 0 && zero_first;
+      h->fold_last = c == ncyc - 1 && persistent0;
       if (c == 0 && h->par.cycle == 1) fmg<float>(h, s);     // FMG, then V-cycles from its result
       else vcycle<float>(h, 0, s);
+      h->zero_u_next = h->fold_last = false;
     }
-    dim3 blk(dev::TX, dev::TY);
-    KL(launch_k(dev::k_axpy_tiles, dim3(L.ntiles, h->nb), blk, 0, s, L.tiles, L.cls, L.nx, L.ny, L.pitch,
-                (const float*)L.u32[L.cur32], h->uhat, L.npad));
+    if (!h->folded) {
+      dim3 blk(dev::TX, dev::TY);
+      KL(launch_k(dev::k_axpy_tiles, dim3(L.ntiles, h->nb), blk, 0, s, L.tiles, L.cls, L.nx, L.ny, L.pitch,
+                  (const float*)L.u32[L.cur32], h->uhat, L.npad));
+    }
+    h->folded = false;
     outer_residual32(h, s);
     if (!to_host) return;
     cudaMemcpyAsync(h->hnorm, h->dnorm, h->nb * sizeof(unsigned long long), cudaMemcpyDeviceToHost, s);
