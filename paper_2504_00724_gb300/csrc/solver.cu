@@ -216,9 +216,9 @@ struct ccm_handle {
   cudaStream_t side = nullptr;          // second stream: SMO-2 blocks beside the regular sweep
   cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
   bool capturing = false;
-  // one-launch requests to the next persistent level-0 FP32 sweep (set while an outer
-  // iteration is issued, cleared when used): zero_u_next, its old iterate is 0 (not read);
-  // fold_next, it also adds its new values to u_hat (the update of the outer iteration).
+  // one-launch requests to the next persistent FP32 sweep (set while a V-cycle is issued,
+  // cleared when used): zero_u_next, its old iterate is 0 (not read; a level's first sweep);
+  // fold_next (level 0), it also adds its new values to u_hat (the outer iteration's update).
   // fold_last marks the last inner cycle; folded reports that a sweep took the update.
   bool zero_u_next = false, fold_next = false, fold_last = false, folded = false;
   long long cap_launches = 0;
@@ -397,7 +397,7 @@ void sweep_persistent(ccm_handle* H, DevLevel& L, cudaStream_t s, DevLevel* C) {
   A.stage = L.smooth_stage[k];
   A.max_ext = std::max(1, L.max_ext);
   const bool l0f = &L == &H->L[0] && sizeof(T) == 4;
-  a.zero_u = l0f && !C && H->zero_u_next ? 1 : 0;
+  a.zero_u = sizeof(T) == 4 && !C && H->zero_u_next ? 1 : 0;
   a.uhat = l0f && H->fold_next ? H->uhat : nullptr;
   if (a.uhat) H->folded = true;
   H->zero_u_next = H->fold_next = false;
@@ -751,11 +751,17 @@ void vcycle(ccm_handle* H, int m, cudaStream_t s, bool prolong_first = false) {
     return;
   }
   // prolong_first: the initial guess is u + P u^(m+1) (the FMG ascent); the first
-  // pre-smoothing sweep reads it on the fly
+  // pre-smoothing sweep reads it on the fly.  Otherwise a coarse level's iterate is 0 on entry
+  // (the restriction cleared it), so its first persistent FP32 sweep does not read it; level
+  // 0's first sweep gets the same request from the outer iteration
   if (prolong_first && H->par.nu1 == 0) prolong_from<T>(H, F, C, s);
+  const bool persistent = F.smooth_ok[1] && H->persistent && H->par.smoother == 1 && H->par.ras_passes <= 1;
   for (int k = 0; k < H->par.nu1; ++k) {
+    if (k == 0 && m > 0 && !prolong_first && sizeof(T) == 4 && persistent) H->zero_u_next = true;
+    if (k > 0 || prolong_first) H->zero_u_next = false;
     if (k == 0 && prolong_first) smooth_step<T>(H, F, s, U<T>(C), C.pitch);
     else smooth_step<T>(H, F, s);
+    H->zero_u_next = false;
   }
   restrict_to<T>(H, F, C, s);
   vcycle<T>(H, m + 1, s);
