@@ -59,9 +59,9 @@ FP64_FMA_PER_CLK_SM = 2          # FP64 FMA issue rate per SM (4 flop / clk / SM
 # A figure is reported only while the device sources hash to the value it was taken on.
 KERNEL_SOURCES = ("kernels.cuh", "smooth.cuh", "outer.cuh")
 NCU_TRAFFIC = {        # class name -> (source hash, bytes per launch)
-    "fp32 sweep, level 0 (SMO-1 regular cells + SMO-2 blocks)": ("143818db12d412d0", 69.77e6),
-    "fp32 residual + restriction, level 0": ("143818db12d412d0", 76.65e6),
-    "outer residual, level 0 (regular cells, float-float)": ("143818db12d412d0", 95.41e6),
+    "fp32 sweep, level 0 (SMO-1 regular cells + SMO-2 blocks)": ("87ef3cf0d418f206", 69.69e6),
+    "fp32 residual + restriction, level 0": ("87ef3cf0d418f206", 76.64e6),
+    "outer residual, level 0 (regular cells, float-float)": ("87ef3cf0d418f206", 95.72e6),
 }
 
 
@@ -681,9 +681,18 @@ def main():
     classes = []     # (name, ms per step, avg ms per launch, launches per step, bound, work per launch, unit)
     ms, nl = prof_sweep
     if nl:
-        byts = n_reg * 12.0 + n_irr * (16 * 12.0 + 2 * 20 * 4.0)
+        # per outer iteration one of these launches starts from the zero correction (it reads
+        # no iterate: 8 B per regular cell) and one, the last, also adds its values to the FP64
+        # solution (u_hat read and written: 16 B more per non-empty cell); averaged per launch
+        per_step_l = nl / args.steps
+        pr = solver.params
+        n_zero = iters if (pr.nu1 >= 1 and pr.cycle == 0) else 0
+        n_fold = iters if pr.nu2 >= 2 else 0
+        reg_b = (12.0 * per_step_l - 4.0 * n_zero + 16.0 * n_fold) / per_step_l
+        irr_b = 16 * 12.0 + 2 * 20 * 4.0 + 16.0 * n_fold / per_step_l
+        byts = n_reg * reg_b + n_irr * irr_b
         classes.append(("fp32 sweep, level 0 (SMO-1 regular cells + SMO-2 blocks)", ms / args.steps, ms / nl,
-                        nl / args.steps, "hbm", byts, "GB/s"))
+                        per_step_l, "hbm", byts, "GB/s"))
     ms, nl = prof_rst
     if nl:
         classes.append(("fp32 residual + restriction, level 0", ms, ms / nl, nl, "hbm", ncell * 14.0, "GB/s"))
@@ -715,6 +724,8 @@ def main():
                             "traffic": traffic_of(c[0], args.n)}
                            for c in classes if c[0] != name]}
         if name.startswith("fp32 sweep"):
+            roof["bytes_per_regular_cell"] = reg_b
+            roof["bytes_per_irregular_row"] = irr_b
             roof["design_overhead_bytes_per_launch"] = {
                 "smo2_dense_block_inverse_rows": int(li0.block_inv_entries) * 4,
                 "class_bytes": n_reg * 1}
