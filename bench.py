@@ -81,6 +81,21 @@ def traffic_of(name, n):
     return byts if sha == source_hash() else None
 
 
+def sweep_class_bytes(n_reg, n_irr, launches, iters, nu1, nu2, cycle):
+    """Algorithmic bytes per launch of the level-0 FP32 sweep class, averaged over its
+    `launches` per solve: a regular cell reads u and r and writes u (12 B), an irregular row
+    reads its fitted row (16 x 12 B) and the banded L22 factors of its SMO-2 solve (2 x 20 x
+    4 B).  Per outer iteration (`iters`) the first sweep starts from zero and reads no u (when
+    nu1 >= 1 and V-cycles) and the last one also reads and writes the FP64 solution, 16 B per
+    non-empty cell (when nu2 >= 2; with nu2 = 1 that sweep is the prolongation sweep, another
+    class).  Returns (bytes per launch, bytes per regular cell, bytes per irregular row)."""
+    n_zero = iters if (nu1 >= 1 and cycle == 0) else 0
+    n_fold = iters if nu2 >= 2 else 0
+    reg_b = (12.0 * launches - 4.0 * n_zero + 16.0 * n_fold) / launches
+    irr_b = 16 * 12.0 + 2 * 20 * 4.0 + 16.0 * n_fold / launches
+    return n_reg * reg_b + n_irr * irr_b, reg_b, irr_b
+
+
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -686,11 +701,7 @@ def main():
         # solution (u_hat read and written: 16 B more per non-empty cell); averaged per launch
         per_step_l = nl / args.steps
         pr = solver.params
-        n_zero = iters if (pr.nu1 >= 1 and pr.cycle == 0) else 0
-        n_fold = iters if pr.nu2 >= 2 else 0
-        reg_b = (12.0 * per_step_l - 4.0 * n_zero + 16.0 * n_fold) / per_step_l
-        irr_b = 16 * 12.0 + 2 * 20 * 4.0 + 16.0 * n_fold / per_step_l
-        byts = n_reg * reg_b + n_irr * irr_b
+        byts, reg_b, irr_b = sweep_class_bytes(n_reg, n_irr, per_step_l, iters, pr.nu1, pr.nu2, pr.cycle)
         classes.append(("fp32 sweep, level 0 (SMO-1 regular cells + SMO-2 blocks)", ms / args.steps, ms / nl,
                         per_step_l, "hbm", byts, "GB/s"))
     ms, nl = prof_rst
