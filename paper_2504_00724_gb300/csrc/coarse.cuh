@@ -9,7 +9,7 @@
 //     then residual + volume-weighted restriction and a zero coarse iterate;
 //   bottom: the dense inverse of the bottom operator;
 //   way up, per level: the first post-smoothing sweep reads u + P uc (the coarse correction
-//     added to regular cells, Sec. 4.2) on the fly, then nu2 - 1 plain sweeps.
+//     added to regular cells, Sec. 4.1) on the fly, then nu2 - 1 plain sweeps.
 // The arithmetic is that of the multi-launch path cell by cell.  Every array that some CTA
 // writes inside the launch is read with ld.global.cg (from L2), so that no CTA uses a stale
 // L1 line of another CTA's writes; the cluster barrier's release/acquire orders the writes.

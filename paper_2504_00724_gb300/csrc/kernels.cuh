@@ -425,7 +425,7 @@ __global__ void __launch_bounds__(256) k_sweep(const __grid_constant__ CUtensorM
 // u + P uc: the class bytes of the tile with its halo (80 x 36 box) and the coarse iterate
 // under it (36 x 18 box, x origin cx0 / 2, a multiple of 32 elements) arrive with the same
 // mbarrier, and the coarse correction is added to the regular cells of the staged tile
-// before the stencil runs (Sec. 4.2: prolongation to regular cells only).
+// before the stencil runs (Sec. 4.1: prolongation to regular cells only).
 constexpr int CLX = 80, UCX = 36, UCY = HY / 2;
 
 template <typename T, bool CROSS, bool PRO>

@@ -12,7 +12,12 @@
 //   block item: the block's rows of inv(L22[ext, ext]) by one bulk copy (cp.async.bulk); the
 //               residuals of its extended rows are gathered from global memory meanwhile.
 // With PRO the sweep is the first post-smoothing sweep of Alg. 2 and reads u + P uc, the
-// coarse correction added to regular cells only (Sec. 4.2).
+// coarse correction added to regular cells only (Sec. 4.1).  A level's first sweep may start
+// from a zero iterate (zero_u: no iterate copied or gathered), and the last level-0 sweep of
+// an outer iteration may add its new values to the FP64 solution (uhat).
+// Before the grid dependency wait each CTA does what depends on no earlier launch: copy
+// barriers, prefetches of its blocks' fitted rows, and the copies of its first two items'
+// static parts (inverse rows, class bytes); the iterate and r follow the wait.
 // Waits are bounded by the SM clock; a wait that runs out sets the error word, waits (again
 // bounded) for every copy still in flight, and the CTA leaves, all threads together.
 #pragma once
