@@ -83,18 +83,18 @@ def test_large_level_restrict(big):
         s.close()
 
 
-def _composed_vcycle(s, levels, m, u, r, nu1=3, nu2=3):
+def _composed_vcycle(s, levels, m, u, r, nu1=3, nu2=3, precision=P.CCM_FP64):
     """Alg. 2 spelled out through the per-level entry points (separate prolongation, no
-    coarse-level cluster launch)."""
+    coarse-level cluster launch, every sweep reading its iterate)."""
     if m == levels - 1:
         return s.bottom_solve(r)
     for _ in range(nu1):
-        u = s.level_smooth(m, u, r)
+        u = s.level_smooth(m, u, r, precision)
     rc = s.level_restrict(m, u, r)
-    uc = _composed_vcycle(s, levels, m + 1, torch.zeros_like(rc), rc, nu1, nu2)
+    uc = _composed_vcycle(s, levels, m + 1, torch.zeros_like(rc), rc, nu1, nu2, precision)
     u = s.level_prolong(m, uc, u)
     for _ in range(nu2):
-        u = s.level_smooth(m, u, r)
+        u = s.level_smooth(m, u, r, precision)
     return u
 
 
@@ -113,6 +113,24 @@ def test_vcycle_equals_composed_level_calls(n, coarse_n):
         want = host(_composed_vcycle(s, s.info.levels, 0, u0.clone(), r))
         got = host(s.vcycle(u0.clone(), r, P.CCM_FP64))
         assert np.abs(got - want).max() <= 1e-12 * np.abs(want).max()
+    finally:
+        s.close()
+
+
+def test_mixed_vcycle_close_to_composed_level_calls():
+    """The FP32 V-cycle (every coarse level's first sweep starting from the zero iterate the
+    restriction leaves, without reading it) against the same cycle composed from FP32 level
+    calls that read their iterates (and restrict in FP64): the two differ by FP32 rounding."""
+    prob = W.star(576)
+    s = P.Solver(prob)
+    try:
+        st = s.cell_map()[0]
+        rng = np.random.default_rng(577)
+        u0 = cuda(np.where(st != 0, rng.standard_normal(st.shape), 0.0))
+        r = cuda(np.where(st != 0, rng.standard_normal(st.shape), 0.0) * 576 * 576)
+        want = host(_composed_vcycle(s, s.info.levels, 0, u0.clone(), r, precision=P.CCM_MIXED))
+        got = host(s.vcycle(u0.clone(), r, P.CCM_MIXED))
+        assert np.abs(got - want).max() <= 1e-4 * np.abs(want).max()
     finally:
         s.close()
 
