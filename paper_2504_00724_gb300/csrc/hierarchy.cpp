@@ -265,19 +265,29 @@ static int pack_level(const CutLevel& cg, const PackRows& rows, const ccm_params
       L.ell_colf[(long)k * n2 + r] = (int32_t)v;
     }
   if (finest) {
-    // transposed fitted rows, grouped by column cell
-    std::map<int32_t, std::vector<std::pair<int32_t, double>>> cols;
+    // transposed fitted rows, grouped by column cell (cells ascending; within a cell its
+    // entries in row order, then slot order): a stable sort of the entries by column
+    std::vector<int64_t> ent((size_t)W * n2);
     for (int r = 0; r < n2; ++r)
-      for (int k = 0; k < W; ++k) cols[L.ell_col[(long)k * n2 + r]].push_back({r, L.ell_val[(long)k * n2 + r]});
+      for (int k = 0; k < W; ++k) ent[(size_t)r * W + k] = (size_t)r * W + k;
+    auto col_of = [&](int64_t e) { return L.ell_col[(long)(e % W) * n2 + e / W]; };
+    std::stable_sort(ent.begin(), ent.end(), [&](int64_t x, int64_t y) { return col_of(x) < col_of(y); });
     L.tr_ptr.assign(1, 0);
-    for (auto& kv : cols) {
-      L.tr_cell.push_back(kv.first);
-      for (auto& e : kv.second) {
-        L.tr_row.push_back(e.first);
-        L.tr_val.push_back(e.second);
+    L.tr_cell.clear();
+    L.tr_row.clear();
+    L.tr_val.clear();
+    for (size_t i = 0; i < ent.size(); ++i) {
+      const int64_t e = ent[i];
+      const int r = (int)(e / W), k = (int)(e % W);
+      const int32_t c = L.ell_col[(long)k * n2 + r];
+      if (L.tr_cell.empty() || L.tr_cell.back() != c) {
+        if (!L.tr_cell.empty()) L.tr_ptr.push_back((int32_t)L.tr_row.size());
+        L.tr_cell.push_back(c);
       }
-      L.tr_ptr.push_back((int32_t)L.tr_row.size());
+      L.tr_row.push_back(r);
+      L.tr_val.push_back(L.ell_val[(long)k * n2 + r]);
     }
+    if (!L.tr_cell.empty()) L.tr_ptr.push_back((int32_t)L.tr_row.size());
   }
   if (coarsest) {
     std::vector<int> cells;
